@@ -1,0 +1,204 @@
+/*
+ * rtg.h — C ABI of the masked, depth-split differentiable Gaussian rasterizer
+ * (RTG-SLAM, "on-the-fly Gaussian optimization": Section 3.1 rendering, Section 3.2
+ * optimization, Supplement B masked rendering) for NVIDIA B300 (sm_103a).
+ *
+ * Conventions (Section 3.1, the pixel ray r(u) = (R_g K^-1 u') theta + t_g):
+ *   - A camera pose T_g = [R_g | t_g] maps CAMERA to WORLD; R is row-major, so
+ *     p_world = R * p_cam + t.  Camera axes: x right, y down, z forward.
+ *   - Pixel (x, y) has its centre at integer coordinates; K = [fx 0 cx; 0 fy cy; 0 0 1].
+ *   - Quaternions are (w, x, y, z) and are normalised inside; scales are linear metres;
+ *     Sigma = R(q) diag(s)^2 R(q)^T.  The disc normal is the axis of the smallest scale
+ *     (lowest index on ties).
+ *   - Images are planar: colour [F, C, H, W], depth / alpha / index [F, H, W], float32.
+ *
+ * Memory: every array argument is a caller-owned DEVICE pointer unless marked HOST.
+ * The context owns only its workspace, allocated once by rtg_create; no entry point
+ * allocates device memory afterwards, so the calls can be captured in a CUDA graph.
+ *
+ * Streams: every call is asynchronous on the given cudaStream_t (passed as void*;
+ * NULL = the legacy default stream).  Argument errors are reported synchronously
+ * by the return value; device-side conditions (pair-buffer overflow) are recorded
+ * in a status word that rtg_get_status() returns once the stream has been
+ * synchronised, and the affected kernels skip their work (outputs untouched).
+ * No call aborts or throws.
+ */
+#ifndef RTG_H
+#define RTG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RTG_OK = 0,
+  RTG_ERR_ARG = -1,         /* invalid argument (NULL pointer, size out of range) */
+  RTG_ERR_CUDA = -2,        /* a CUDA runtime call failed; see rtg_last_error */
+  RTG_ERR_WORKSPACE = -3,   /* the (Gaussian, tile) pairs exceeded the capacity */
+  RTG_ERR_TIMEOUT = -4,     /* reserved: a bounded device-side wait gave up */
+  RTG_ERR_UNSUPPORTED = -5, /* a configuration this build does not implement */
+  RTG_ERR_STATE = -6        /* call order violated (backward without a forward) */
+} rtg_status;
+
+#define RTG_MAX_FRAMES 32 /* cameras per call (keyframe batch) */
+#define RTG_TILE 16       /* screen tiles are 16 x 16 pixels (Supplement B) */
+
+/* Pinhole camera and camera-to-world pose T_g (Section 3.1). HOST struct. */
+typedef struct {
+  float fx, fy, cx, cy;
+  int32_t width, height;
+  float R[9]; /* row-major camera-to-world rotation R_g */
+  float t[3]; /* camera centre t_g in world coordinates */
+} rtg_camera;
+
+/* Rendering constants.  delta_alpha and cos_max_angle come from Section 3.1
+ * (e^-0.5 and cos 60 deg); tile_discard_frac from Supplement B (0.5; 0 = off);
+ * the others are the 3DGS conventions the paper builds on: alpha_min = 1/255,
+ * f_max = 0.99, t_eps = 1e-4 (stop before a fragment that would take the
+ * transmission below it), lowpass = 0.3 px^2 added to Sigma_2D, near_z = 0.2 m,
+ * guard_band = 1.3 (cull centres outside 1.3x the half field of view). */
+typedef struct {
+  float near_z, alpha_min, f_max, t_eps, delta_alpha, cos_max_angle, lowpass, guard_band,
+      tile_discard_frac;
+} rtg_render_params;
+
+/* Gaussian arrays (Section 3.1: "all parameters are stored in a flat array indexed
+ * by the Gaussian index i").  Structure-of-arrays, float32, device pointers:
+ * means [n,3], scales [n,3], quats [n,4], opacity [n], colors [n,channels],
+ * unstable [n] (uint8, non-zero = unstable, Section 3.2 state).
+ * Optional compact overrides u_*: when u_means is non-NULL, the parameters of the
+ * k-th unstable Gaussian (ascending index) are read from u_means[k], u_scales[k], ...
+ * instead of the full arrays, so an optimiser can own compact [n_unstable, .] leaves.
+ * Either all five u_* pointers are set or none. */
+typedef struct {
+  int64_t n;
+  int32_t channels; /* 3 (RGB) or 8 (feature channels) */
+  const float *means, *scales, *quats, *opacity, *colors;
+  const uint8_t *unstable;
+  const float *u_means, *u_scales, *u_quats, *u_opacity, *u_colors;
+} rtg_gaussians;
+
+/* Workspace capacity; every later call must stay within it. */
+typedef struct {
+  int64_t max_gaussians;
+  int32_t max_frames;   /* <= RTG_MAX_FRAMES */
+  int32_t max_width, max_height;
+  int32_t max_channels; /* 3 or 8 */
+  int64_t max_pairs;    /* (Gaussian, tile) pairs over all frames of one call */
+} rtg_capacity;
+
+typedef struct rtg_ctx rtg_ctx;
+
+/* Counters of the last completed forward (read after synchronising its stream). */
+typedef struct {
+  int64_t pairs;          /* (Gaussian, tile) pairs emitted over masked tiles */
+  int64_t fragments;      /* composited (pixel, Gaussian) fragments, Eq. 1 terms */
+  int64_t visible;        /* (frame, Gaussian) projections that touch a masked tile */
+  int64_t masked_pixels;  /* pixels rendered */
+  int64_t n_unstable;     /* unstable Gaussians (rows of the compact gradients) */
+  int32_t status;         /* device status word (rtg_status) */
+  int32_t max_tile_pairs; /* longest per-tile list */
+} rtg_stats;
+
+/* Bytes of device workspace rtg_create allocates for `cap`. */
+rtg_status rtg_workspace_size(const rtg_capacity *cap, size_t *bytes);
+
+/* Create a context on the current device; allocates the workspace once.
+ * On failure *out is NULL and the return value says why. */
+rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap);
+
+/* Free a context and its workspace (NULL is accepted). */
+rtg_status rtg_destroy(rtg_ctx *ctx);
+
+/* Unstable-pixel mask (Supplement B, Eq. S2): mask[f,y,x] = 1 where some unstable
+ * Gaussian covers the pixel (f >= alpha_min, i.e. T_unstable < 1), then every 16x16
+ * tile with fewer than tile_discard_frac of its in-image pixels covered is cleared.
+ * cams: HOST array of F cameras sharing width/height; mask: [F,H,W] uint8 output. */
+rtg_status rtg_unstable_mask(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, const rtg_gaussians *g,
+                             const rtg_render_params *prm, uint8_t *mask, void *stream);
+
+/* Forward render over all Gaussians on the masked pixels (Section 3.1):
+ * colour by front-to-back alpha compositing (Eq. 1, 2, 3), depth from the first
+ * processed fragment with f > delta_alpha through the ray/disc-plane intersection
+ * (Eq. 4) with the three cases of Eq. 5, alpha = 1 - final transmission, and the
+ * index map of the depth-hit Gaussian (-1 if none).
+ * cams: HOST array of F cameras (same width/height).  mask: [F,H,W] uint8 or NULL
+ * (all pixels).  Outputs are written on masked pixels only; other pixels keep their
+ * contents.  index_map may be NULL.  The context keeps the sorted lists and
+ * per-pixel state for rtg_render_backward, which must follow before the next forward
+ * on the same context, with the Gaussian arrays unchanged. */
+rtg_status rtg_render_forward(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, const rtg_gaussians *g,
+                              const uint8_t *mask, const rtg_render_params *prm, float *color, float *depth,
+                              float *alpha, int32_t *index_map, void *stream);
+
+/* L1 losses of Section 3.2 (Eq. 7, Eq. 8 with w_reg = 0) on the masked pixels:
+ * L_color = mean |C - C_hat| over masked pixels and channels; L_depth = mean |D - D_hat|
+ * over masked pixels with D_hat != -1 and D > 0 (no depth loss without intersection).
+ * loss_out: device float[3] = (L, L_color, L_depth).  dL_dcolor [F,C,H,W] and
+ * dL_ddepth [F,H,W] receive the gradient of L (sign(0) = 0; zero off the mask). */
+rtg_status rtg_l1_loss(rtg_ctx *ctx, int32_t F, int32_t C, int32_t H, int32_t W, const float *color,
+                       const float *depth, const float *target_color, const float *target_depth,
+                       const uint8_t *mask, float w_color, float w_depth, float *loss_out, float *dL_dcolor,
+                       float *dL_ddepth, void *stream);
+
+/* Backward of the last forward on this context (Section 3.1: the depth is linear in
+ * position and rotation, hence differentiable): replays the compositing back to front
+ * and writes the gradients of the loss for the UNSTABLE Gaussians only, compact, in
+ * ascending original index: g_means [nu,3], g_scales [nu,3] (linear scale),
+ * g_quats [nu,4] (raw quaternion), g_opacity [nu], g_colors [nu,C].
+ * dL_dcolor [F,C,H,W] and dL_ddepth [F,H,W] are read on masked pixels only. */
+rtg_status rtg_render_backward(rtg_ctx *ctx, const float *dL_dcolor, const float *dL_ddepth, float *g_means,
+                               float *g_scales, float *g_quats, float *g_opacity, float *g_colors, void *stream);
+
+/* Adam (Kingma & Ba, Algorithm 1) on compact unstable parameters, in place, with the
+ * per-group learning rates of Supplement C.  The scale is optimised in log space
+ * (s <- s * exp(-step), gradient s * dL/ds).  m and v are [nu, 11 + C] float32
+ * (means 3, scales 3, quats 4, opacity 1, colours C); `step` counts from 1. */
+typedef struct {
+  float lr_means, lr_scales, lr_quats, lr_opacity, lr_colors, beta1, beta2, eps;
+} rtg_adam_params;
+rtg_status rtg_adam_step(int64_t nu, int32_t C, float *means, float *scales, float *quats, float *opacity,
+                         float *colors, const float *g_means, const float *g_scales, const float *g_quats,
+                         const float *g_opacity, const float *g_colors, float *m, float *v, int32_t step,
+                         const rtg_adam_params *hp, void *stream);
+
+/* Unstable-subset helpers: ids[k] = index of the k-th unstable Gaussian (ascending),
+ * *nu_out (device int64) = their count.  gather copies full rows into compact arrays;
+ * scatter writes compact rows back into the full arrays. */
+rtg_status rtg_unstable_index(rtg_ctx *ctx, int64_t n, const uint8_t *unstable, int32_t *ids, int64_t *nu_out,
+                              void *stream);
+rtg_status rtg_gather_unstable(int64_t nu, int32_t C, const int32_t *ids, const float *means, const float *scales,
+                               const float *quats, const float *opacity, const float *colors, float *u_means,
+                               float *u_scales, float *u_quats, float *u_opacity, float *u_colors, void *stream);
+rtg_status rtg_scatter_unstable(int64_t nu, int32_t C, const int32_t *ids, const float *u_means,
+                                const float *u_scales, const float *u_quats, const float *u_opacity,
+                                const float *u_colors, float *means, float *scales, float *quats, float *opacity,
+                                float *colors, void *stream);
+
+/* Counters of the last forward (synchronises the context's last stream). HOST out. */
+rtg_status rtg_get_stats(rtg_ctx *ctx, rtg_stats *out);
+
+/* Device status word (RTG_OK or the first device-side error since the last reset);
+ * call after synchronising the stream.  rtg_reset_status clears it. */
+rtg_status rtg_get_status(rtg_ctx *ctx);
+rtg_status rtg_reset_status(rtg_ctx *ctx);
+
+/* Human-readable message of the last error on this context (never NULL). */
+const char *rtg_last_error(rtg_ctx *ctx);
+
+/* Binning introspection of the last forward (for exactness tests): tile_offsets
+ * [F*T+1] (uint32, T = ceil(W/16)*ceil(H/16) tiles per frame, frame-major, row-major
+ * tiles), sorted_ids [pairs] (uint32 Gaussian index per list entry, each tile's list
+ * in front-to-back order), and per (frame, Gaussian): rect [F*n*4] int32 (first and
+ * last tile column and row touched, or -1 if culled) and zbits [F*n] uint32 (IEEE
+ * bits of the float32 camera depth used as the sort key).  Any output may be NULL. */
+rtg_status rtg_debug_binning(rtg_ctx *ctx, uint32_t *tile_offsets, uint32_t *sorted_ids, int32_t *rect,
+                             uint32_t *zbits, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTG_H */

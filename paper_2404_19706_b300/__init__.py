@@ -1,0 +1,36 @@
+"""B300-native masked, depth-split differentiable Gaussian rasterizer (RTG-SLAM, arxiv 2404.19706).
+
+The compute path is librtg.so (CUDA for sm_103a) behind the C ABI in include/rtg.h;
+this package is its Python binding.  Importing it loads the library and fails loudly
+if it has not been built (there is no CPU fallback).
+"""
+
+from . import _lib
+
+_lib.load()
+
+from .api import (  # noqa: E402,F401
+    AdamSettings,
+    Context,
+    Gaussians,
+    RenderSettings,
+    RTGError,
+    adam_step,
+    debug_binning,
+    gather_unstable,
+    get_stats,
+    get_status,
+    l1_loss,
+    last_error,
+    make_camera,
+    render_backward,
+    render_forward,
+    reset_status,
+    scatter_unstable,
+    unstable_index,
+    unstable_mask,
+    workspace_size,
+)
+from .optim import MaskedStep, RasterState, RTGRasterize, rasterize  # noqa: E402,F401
+
+LIBRARY_PATH = _lib.LIB_PATH

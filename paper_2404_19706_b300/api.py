@@ -1,0 +1,349 @@
+"""Python binding of the C ABI (include/rtg.h): argument marshalling only.
+
+Every function here forwards torch CUDA tensors as raw device pointers to the entry
+point of the same name in librtg.so and raises ``RTGError`` on a non-OK status.  All
+computation happens in the CUDA kernels behind the ABI; PyTorch provides device
+memory and streams.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (rtg_adam_params, rtg_camera, rtg_capacity, rtg_gaussians, rtg_render_params, rtg_stats)
+
+
+class RTGError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {_lib.STATUS_NAMES.get(status, status)} {message}".strip())
+
+
+def _check(status: int, where: str, ctx=None):
+    if status != _lib.RTG_OK:
+        lib = _lib.load()
+        msg = lib.rtg_last_error(ctx).decode() if ctx is not None else ""
+        raise RTGError(status, where, msg)
+
+
+def _ptr(t: Optional[torch.Tensor], dtype=None, name: str = "tensor") -> Optional[int]:
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must live on a CUDA device (there is no CPU path)")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr() if t.numel() > 0 else None
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if isinstance(stream, torch.cuda.Stream) else int(stream)
+
+
+# ----------------------------------------------------------------------------- value types
+
+@dataclasses.dataclass(frozen=True)
+class RenderSettings:
+    """Rendering constants (rtg_render_params): Section 3.1 thresholds, the Supplement B
+    tile rule and the 3DGS conventions for the values the paper leaves open."""
+    near_z: float = 0.2
+    alpha_min: float = 1.0 / 255.0
+    f_max: float = 0.99
+    t_eps: float = 1e-4
+    delta_alpha: float = math.exp(-0.5)
+    cos_max_angle: float = 0.5
+    lowpass: float = 0.3
+    guard_band: float = 1.3
+    tile_discard_frac: float = 0.5
+
+    def to_c(self) -> rtg_render_params:
+        return rtg_render_params(*(float(getattr(self, f.name)) for f in dataclasses.fields(self)))
+
+
+@dataclasses.dataclass(frozen=True)
+class AdamSettings:
+    """Supplement C learning rates (Replica/ScanNet++ set); scale is stepped in log space."""
+    lr_means: float = 1e-3
+    lr_scales: float = 4e-3
+    lr_quats: float = 1e-3
+    lr_opacity: float = 0.0
+    lr_colors: float = 5e-4
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-15
+
+    def to_c(self) -> rtg_adam_params:
+        return rtg_adam_params(*(float(getattr(self, f.name)) for f in dataclasses.fields(self)))
+
+
+def make_camera(cam) -> rtg_camera:
+    """Any object with fx, fy, cx, cy, width, height, R [3,3] (camera-to-world), t [3]."""
+    c = rtg_camera()
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height = int(cam.width), int(cam.height)
+    R = np.asarray(cam.R, dtype=np.float32).reshape(9)
+    t = np.asarray(cam.t, dtype=np.float32).reshape(3)
+    for k in range(9):
+        c.R[k] = float(R[k])
+    for k in range(3):
+        c.t[k] = float(t[k])
+    return c
+
+
+def _cams(cams) -> tuple:
+    if not isinstance(cams, (list, tuple)):
+        cams = [cams]
+    arr = (rtg_camera * len(cams))(*[make_camera(c) for c in cams])
+    return arr, len(cams)
+
+
+@dataclasses.dataclass
+class Gaussians:
+    """Structure-of-arrays Gaussian parameters on the GPU (rtg_gaussians)."""
+    means: torch.Tensor      # [N,3] f32
+    scales: torch.Tensor     # [N,3] f32
+    quats: torch.Tensor      # [N,4] f32 (w,x,y,z)
+    opacity: torch.Tensor    # [N] f32
+    colors: torch.Tensor     # [N,C] f32
+    unstable: torch.Tensor   # [N] u8
+    u_means: Optional[torch.Tensor] = None  # optional compact overrides [Nu, .]
+    u_scales: Optional[torch.Tensor] = None
+    u_quats: Optional[torch.Tensor] = None
+    u_opacity: Optional[torch.Tensor] = None
+    u_colors: Optional[torch.Tensor] = None
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+    @property
+    def channels(self) -> int:
+        return int(self.colors.shape[1])
+
+    @staticmethod
+    def from_scene(scene, device="cuda") -> "Gaussians":
+        def t(a, dt=torch.float32):
+            return torch.as_tensor(np.ascontiguousarray(a)).to(device=device, dtype=dt).contiguous()
+        return Gaussians(t(scene.means), t(scene.scales), t(scene.quats), t(scene.opacity), t(scene.colors),
+                         t(scene.unstable, torch.uint8))
+
+    def to_c(self) -> rtg_gaussians:
+        g = rtg_gaussians()
+        g.n, g.channels = self.n, self.channels
+        for name in ("means", "scales", "quats", "opacity", "colors"):
+            setattr(g, name, _ptr(getattr(self, name), torch.float32, name))
+        g.unstable = _ptr(self.unstable, torch.uint8, "unstable")
+        for name in ("u_means", "u_scales", "u_quats", "u_opacity", "u_colors"):
+            v = getattr(self, name)
+            setattr(g, name, _ptr(v, torch.float32, name) if v is not None else None)
+        if self.u_means is not None and any(getattr(self, k).numel() == 0 for k in ("u_means",)):
+            # an empty compact set is the same as no override
+            for name in ("u_means", "u_scales", "u_quats", "u_opacity", "u_colors"):
+                setattr(g, name, None)
+        return g
+
+
+# ----------------------------------------------------------------------------- context
+
+class Context:
+    """Owns an rtg_ctx (the preallocated workspace) on the current CUDA device."""
+
+    def __init__(self, max_gaussians: int, max_frames: int = 1, max_width: int = 640, max_height: int = 480,
+                 max_channels: int = 3, max_pairs: Optional[int] = None):
+        lib = _lib.load()
+        if max_pairs is None:
+            max_pairs = max(1 << 20, 32 * max_gaussians * max_frames)
+        self.cap = rtg_capacity(int(max_gaussians), int(max_frames), int(max_width), int(max_height),
+                                int(max_channels), int(min(max_pairs, 0xFFFFFFFF)))
+        h = ctypes.c_void_p()
+        st = lib.rtg_create(ctypes.byref(h), ctypes.byref(self.cap))
+        if st != _lib.RTG_OK:
+            raise RTGError(st, "rtg_create", f"capacity {self.cap.max_gaussians} Gaussians, "
+                                             f"{self.cap.max_pairs} pairs")
+        self.handle = h
+
+    def workspace_bytes(self) -> int:
+        n = ctypes.c_size_t()
+        _check(_lib.load().rtg_workspace_size(ctypes.byref(self.cap), ctypes.byref(n)), "rtg_workspace_size")
+        return int(n.value)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _lib.load().rtg_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def ptr(self):
+        return self.handle
+
+
+def workspace_size(max_gaussians, max_frames=1, max_width=640, max_height=480, max_channels=3, max_pairs=1 << 20):
+    cap = rtg_capacity(int(max_gaussians), int(max_frames), int(max_width), int(max_height), int(max_channels),
+                       int(max_pairs))
+    n = ctypes.c_size_t()
+    _check(_lib.load().rtg_workspace_size(ctypes.byref(cap), ctypes.byref(n)), "rtg_workspace_size")
+    return int(n.value)
+
+
+# ----------------------------------------------------------------------------- entry points
+
+def unstable_mask(ctx: Context, cams, g: Gaussians, settings: RenderSettings, mask: torch.Tensor, stream=None):
+    arr, F = _cams(cams)
+    gc = g.to_c()
+    prm = settings.to_c()
+    st = _lib.load().rtg_unstable_mask(ctx.ptr, arr, F, ctypes.byref(gc), ctypes.byref(prm),
+                                       _ptr(mask, torch.uint8, "mask"), _stream(stream))
+    _check(st, "rtg_unstable_mask", ctx.ptr)
+
+
+def render_forward(ctx: Context, cams, g: Gaussians, mask: Optional[torch.Tensor], settings: RenderSettings,
+                   color: torch.Tensor, depth: torch.Tensor, alpha: torch.Tensor,
+                   index_map: Optional[torch.Tensor] = None, stream=None):
+    arr, F = _cams(cams)
+    gc = g.to_c()
+    prm = settings.to_c()
+    st = _lib.load().rtg_render_forward(ctx.ptr, arr, F, ctypes.byref(gc), _ptr(mask, torch.uint8, "mask"),
+                                        ctypes.byref(prm), _ptr(color, torch.float32, "color"),
+                                        _ptr(depth, torch.float32, "depth"), _ptr(alpha, torch.float32, "alpha"),
+                                        _ptr(index_map, torch.int32, "index_map"), _stream(stream))
+    _check(st, "rtg_render_forward", ctx.ptr)
+
+
+def l1_loss(ctx: Context, color, depth, target_color, target_depth, mask, w_color: float, w_depth: float,
+            loss_out, dL_dcolor, dL_ddepth, stream=None):
+    F, C, H, W = color.shape
+    st = _lib.load().rtg_l1_loss(ctx.ptr, F, C, H, W, _ptr(color, torch.float32, "color"),
+                                 _ptr(depth, torch.float32, "depth"), _ptr(target_color, torch.float32, "target_color"),
+                                 _ptr(target_depth, torch.float32, "target_depth"), _ptr(mask, torch.uint8, "mask"),
+                                 float(w_color), float(w_depth), _ptr(loss_out, torch.float32, "loss_out"),
+                                 _ptr(dL_dcolor, torch.float32, "dL_dcolor"), _ptr(dL_ddepth, torch.float32, "dL_ddepth"),
+                                 _stream(stream))
+    _check(st, "rtg_l1_loss", ctx.ptr)
+
+
+_DUMMY = {}
+
+
+def _out_ptr(t: torch.Tensor, name: str):
+    """Gradient outputs may be empty when no Gaussian is unstable; pass a scratch word."""
+    if t.numel() == 0:
+        dev = t.device
+        if dev not in _DUMMY:
+            _DUMMY[dev] = torch.zeros(4, dtype=torch.float32, device=dev)
+        return _DUMMY[dev].data_ptr()
+    return _ptr(t, torch.float32, name)
+
+
+def render_backward(ctx: Context, dL_dcolor, dL_ddepth, g_means, g_scales, g_quats, g_opacity, g_colors,
+                    stream=None):
+    st = _lib.load().rtg_render_backward(ctx.ptr, _ptr(dL_dcolor, torch.float32, "dL_dcolor"),
+                                         _ptr(dL_ddepth, torch.float32, "dL_ddepth"), _out_ptr(g_means, "g_means"),
+                                         _out_ptr(g_scales, "g_scales"), _out_ptr(g_quats, "g_quats"),
+                                         _out_ptr(g_opacity, "g_opacity"), _out_ptr(g_colors, "g_colors"),
+                                         _stream(stream))
+    _check(st, "rtg_render_backward", ctx.ptr)
+
+
+def adam_step(params: Sequence[torch.Tensor], grads: Sequence[torch.Tensor], m: torch.Tensor, v: torch.Tensor,
+              step: int, hp: AdamSettings = AdamSettings(), stream=None):
+    """params/grads: compact (means, scales, quats, opacity, colors); m, v: [nu, 11 + C]."""
+    means, scales, quats, opacity, colors = params
+    nu, C = int(means.shape[0]), int(colors.shape[1])
+    c = hp.to_c()
+    ptrs = [_ptr(t, torch.float32, "param") for t in params] + [_ptr(t, torch.float32, "grad") for t in grads]
+    st = _lib.load().rtg_adam_step(nu, C, *ptrs, _ptr(m, torch.float32, "m"), _ptr(v, torch.float32, "v"),
+                                   int(step), ctypes.byref(c), _stream(stream))
+    _check(st, "rtg_adam_step")
+
+
+def unstable_index(ctx: Context, unstable: torch.Tensor, stream=None):
+    """Returns (ids int32 [nu] on the device, nu).  Synchronises to read the count."""
+    n = int(unstable.shape[0])
+    ids = torch.empty(max(n, 1), dtype=torch.int32, device=unstable.device)
+    nu_t = torch.zeros(1, dtype=torch.int64, device=unstable.device)
+    st = _lib.load().rtg_unstable_index(ctx.ptr, n, _ptr(unstable, torch.uint8, "unstable"),
+                                        ids.data_ptr(), nu_t.data_ptr(), _stream(stream))
+    _check(st, "rtg_unstable_index", ctx.ptr)
+    nu = int(nu_t.item())
+    return ids[:nu], nu
+
+
+def gather_unstable(ids: torch.Tensor, g: Gaussians, stream=None):
+    nu, C = int(ids.shape[0]), g.channels
+    dev = g.means.device
+    out = (torch.empty(nu, 3, device=dev), torch.empty(nu, 3, device=dev), torch.empty(nu, 4, device=dev),
+           torch.empty(nu, device=dev), torch.empty(nu, C, device=dev))
+    if nu:
+        st = _lib.load().rtg_gather_unstable(nu, C, _ptr(ids, torch.int32, "ids"),
+                                             *[_ptr(getattr(g, k), torch.float32, k) for k in
+                                               ("means", "scales", "quats", "opacity", "colors")],
+                                             *[_ptr(t, torch.float32, "out") for t in out], _stream(stream))
+        _check(st, "rtg_gather_unstable")
+    return out
+
+
+def scatter_unstable(ids: torch.Tensor, compact: Sequence[torch.Tensor], g: Gaussians, stream=None):
+    nu, C = int(ids.shape[0]), g.channels
+    if nu == 0:
+        return
+    st = _lib.load().rtg_scatter_unstable(nu, C, _ptr(ids, torch.int32, "ids"),
+                                          *[_ptr(t, torch.float32, "compact") for t in compact],
+                                          *[_ptr(getattr(g, k), torch.float32, k) for k in
+                                            ("means", "scales", "quats", "opacity", "colors")], _stream(stream))
+    _check(st, "rtg_scatter_unstable")
+
+
+def get_stats(ctx: Context) -> dict:
+    s = rtg_stats()
+    _check(_lib.load().rtg_get_stats(ctx.ptr, ctypes.byref(s)), "rtg_get_stats", ctx.ptr)
+    return {f[0]: getattr(s, f[0]) for f in rtg_stats._fields_}
+
+
+def get_status(ctx: Context) -> int:
+    return int(_lib.load().rtg_get_status(ctx.ptr))
+
+
+def reset_status(ctx: Context):
+    _lib.load().rtg_reset_status(ctx.ptr)
+
+
+def last_error(ctx: Context) -> str:
+    return _lib.load().rtg_last_error(ctx.ptr).decode()
+
+
+def debug_binning(ctx: Context, frames: int, width: int, height: int, n: int, stream=None):
+    """Copies of the last forward's bucket offsets, sorted ids, per-(frame, Gaussian) tile
+    rectangles and depth-key bits (for the exactness tests)."""
+    stats = get_stats(ctx)
+    T = ((width + 15) // 16) * ((height + 15) // 16)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    offs = torch.empty(frames * T + 1, dtype=torch.int32, device=dev)
+    ids = torch.empty(max(stats["pairs"], 1), dtype=torch.int32, device=dev)
+    rect = torch.empty(max(frames * n, 1), 4, dtype=torch.int32, device=dev)
+    zb = torch.empty(max(frames * n, 1), dtype=torch.int32, device=dev)
+    st = _lib.load().rtg_debug_binning(ctx.ptr, offs.data_ptr(), ids.data_ptr(), rect.data_ptr(), zb.data_ptr(),
+                                       _stream(stream))
+    _check(st, "rtg_debug_binning", ctx.ptr)
+    torch.cuda.synchronize()
+    u32 = lambda t: t.cpu().numpy().view(np.uint32)  # noqa: E731
+    return dict(tile_offsets=u32(offs), sorted_ids=u32(ids[:stats["pairs"]]), rect=rect[:frames * n].cpu().numpy(),
+                zbits=u32(zb[:frames * n]), pairs=stats["pairs"])

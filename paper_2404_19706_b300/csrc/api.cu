@@ -1,0 +1,473 @@
+// Host side of the C ABI declared in include/rtg.h: context and workspace, argument
+// validation, and the kernel launch sequences of each entry point.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "kernels.cuh"
+
+using namespace rtg;
+
+struct rtg_ctx {
+  rtg_capacity cap;
+  int device;
+  char *slab;
+  size_t bytes;
+  Work w;
+  uint32_t *status_host;
+  char err[512];
+  // state of the last forward, consumed by the backward
+  bool has_fwd;
+  GaussPtrs g;
+  Prm prm;
+  int F, W, H, T, C;
+  const uint8_t *mask;
+  cudaStream_t last_stream;
+};
+
+namespace {
+
+const char *kNoCtx = "rtg: NULL context";
+
+rtg_status fail(rtg_ctx *ctx, rtg_status st, const char *fmt, ...) {
+  if (ctx != nullptr) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+    va_end(ap);
+  }
+  return st;
+}
+
+rtg_status check_launch(rtg_ctx *ctx, const char *what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(ctx, RTG_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  return RTG_OK;
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t cams, counters, rank, ids, block_cnt, rec_hot, rec_cold, ntiles, tile_npix, tile_count, tile_offset,
+      tile_cursor, keys, keys_alt, sorted, px_T, px_last, px_hit, grad2d, loss_part, loss_scal, loss_done, total;
+};
+
+bool capacity_ok(const rtg_capacity *c) {
+  return c != nullptr && c->max_gaussians >= 0 && c->max_frames >= 1 && c->max_frames <= RTG_MAX_FRAMES &&
+         c->max_width >= 1 && c->max_height >= 1 && (c->max_channels == 3 || c->max_channels == 8) &&
+         c->max_pairs >= 1 && c->max_pairs <= 0xffffffffLL;
+}
+
+Layout layout_of(const rtg_capacity *c) {
+  const size_t N = (size_t)(c->max_gaussians > 0 ? c->max_gaussians : 1);
+  const size_t Fm = (size_t)c->max_frames;
+  const size_t tiles = (size_t)((c->max_width + kTile - 1) / kTile) * (size_t)((c->max_height + kTile - 1) / kTile);
+  const size_t FT = Fm * tiles;
+  const size_t P = Fm * (size_t)c->max_width * (size_t)c->max_height;
+  const size_t K = (size_t)c->max_pairs;
+  const size_t H4 = (size_t)hot4_of(c->max_channels), G2 = (size_t)g2_of(c->max_channels);
+  Layout L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o += align256(bytes);
+    return at;
+  };
+  L.cams = take(Fm * sizeof(DevCam));
+  L.counters = take(kNumCounters * sizeof(unsigned long long));
+  L.rank = take(N * 4);
+  L.ids = take(N * 4);
+  L.block_cnt = take((N / kScanBlock + 2) * 4);
+  L.rec_hot = take(Fm * N * H4 * 16);
+  L.rec_cold = take(Fm * N * 32);
+  L.ntiles = take(Fm * N * 4);
+  L.tile_npix = take((FT + 1) * 4);
+  L.tile_count = take((FT + 1) * 4);
+  L.tile_offset = take((FT + 1) * 4);
+  L.tile_cursor = take((FT + 1) * 4);
+  L.keys = take(K * 8);
+  L.keys_alt = take(K * 8);
+  L.sorted = take(K * 4);
+  L.px_T = take(P * 4);
+  L.px_last = take(P * 4);
+  L.px_hit = take(P * 4);
+  L.grad2d = take(Fm * N * G2 * 4);
+  L.loss_part = take(kLossBlocks * 4 * 4);
+  L.loss_scal = take(8 * 4);
+  L.loss_done = take(4);
+  L.total = o;
+  return L;
+}
+
+rtg_status make_frames(rtg_ctx *ctx, const rtg_camera *cams, int F, const rtg_render_params *prm, FrameSet &fs) {
+  if (cams == nullptr) return fail(ctx, RTG_ERR_ARG, "cams is NULL");
+  if (F < 1 || F > ctx->cap.max_frames) return fail(ctx, RTG_ERR_ARG, "F=%d outside [1, %d]", F, ctx->cap.max_frames);
+  memset(&fs, 0, sizeof(fs));
+  fs.F = F;
+  for (int f = 0; f < F; ++f) {
+    const rtg_camera &c = cams[f];
+    if (c.width != cams[0].width || c.height != cams[0].height)
+      return fail(ctx, RTG_ERR_ARG, "all cameras of a call must share width and height");
+    if (c.width < 1 || c.height < 1 || c.width > ctx->cap.max_width || c.height > ctx->cap.max_height)
+      return fail(ctx, RTG_ERR_ARG, "image %dx%d outside capacity %dx%d", c.width, c.height, ctx->cap.max_width,
+                  ctx->cap.max_height);
+    if (!(c.fx > 0.f) || !(c.fy > 0.f) || !isfinite(c.cx) || !isfinite(c.cy))
+      return fail(ctx, RTG_ERR_ARG, "camera %d: focal lengths must be positive and finite", f);
+    DevCam &d = fs.cam[f];
+    d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+    d.W = c.width; d.H = c.height;
+    for (int k = 0; k < 9; ++k) d.R[k] = c.R[k];
+    for (int k = 0; k < 3; ++k) d.t[k] = c.t[k];
+    d.lim_x = prm->guard_band * (0.5f * (float)c.width) / c.fx;
+    d.lim_y = prm->guard_band * (0.5f * (float)c.height) / c.fy;
+    d.tiles_x = (c.width + kTile - 1) / kTile;
+    d.tiles_y = (c.height + kTile - 1) / kTile;
+  }
+  return RTG_OK;
+}
+
+rtg_status make_gauss(rtg_ctx *ctx, const rtg_gaussians *g, GaussPtrs &gp) {
+  if (g == nullptr) return fail(ctx, RTG_ERR_ARG, "gaussians is NULL");
+  if (g->n < 0 || g->n > ctx->cap.max_gaussians)
+    return fail(ctx, RTG_ERR_ARG, "n=%lld outside [0, %lld]", (long long)g->n, (long long)ctx->cap.max_gaussians);
+  if (g->n > 0x7fffffffLL) return fail(ctx, RTG_ERR_UNSUPPORTED, "n above 2^31-1");
+  if (g->channels != 3 && g->channels != 8) return fail(ctx, RTG_ERR_UNSUPPORTED, "channels must be 3 or 8");
+  if (g->channels > ctx->cap.max_channels) return fail(ctx, RTG_ERR_ARG, "channels above capacity");
+  if (g->n > 0 && (!g->means || !g->scales || !g->quats || !g->opacity || !g->colors || !g->unstable))
+    return fail(ctx, RTG_ERR_ARG, "a Gaussian array is NULL");
+  const bool any_u = g->u_means || g->u_scales || g->u_quats || g->u_opacity || g->u_colors;
+  const bool all_u = g->u_means && g->u_scales && g->u_quats && g->u_opacity && g->u_colors;
+  if (any_u && !all_u) return fail(ctx, RTG_ERR_ARG, "set all five compact u_* arrays or none");
+  gp.means = g->means; gp.scales = g->scales; gp.quats = g->quats; gp.opacity = g->opacity; gp.colors = g->colors;
+  gp.unstable = g->unstable;
+  gp.u_means = g->u_means; gp.u_scales = g->u_scales; gp.u_quats = g->u_quats; gp.u_opacity = g->u_opacity;
+  gp.u_colors = g->u_colors;
+  gp.n = g->n;
+  gp.C = g->channels;
+  return RTG_OK;
+}
+
+rtg_status make_prm(rtg_ctx *ctx, const rtg_render_params *p, Prm &o) {
+  if (p == nullptr) return fail(ctx, RTG_ERR_ARG, "params is NULL");
+  if (!(p->alpha_min > 0.f) || !(p->f_max > p->alpha_min) || !(p->f_max < 1.f) || !(p->t_eps > 0.f) ||
+      !(p->delta_alpha > 0.f) || !(p->lowpass >= 0.f) || !(p->guard_band > 0.f) || !(p->near_z > 0.f) ||
+      !(p->tile_discard_frac >= 0.f) || !(p->tile_discard_frac <= 1.f) || !(p->cos_max_angle >= 0.f))
+    return fail(ctx, RTG_ERR_ARG, "render params out of range");
+  o.near_z = p->near_z; o.alpha_min = p->alpha_min; o.f_max = p->f_max; o.t_eps = p->t_eps;
+  o.delta_alpha = p->delta_alpha; o.cos_max = p->cos_max_angle; o.lowpass = p->lowpass; o.guard = p->guard_band;
+  o.discard = p->tile_discard_frac;
+  return RTG_OK;
+}
+
+// rank[i] / ids[k] of the unstable subset, and its count in counters[kNumUnstable]
+rtg_status rank_pass(rtg_ctx *ctx, const uint8_t *unstable, int64_t n, int32_t *rank, int32_t *ids,
+                     unsigned long long *nu_counter, int64_t *nu_out, cudaStream_t s) {
+  launch_rank(unstable, n, ctx->w.block_cnt, rank, ids, nu_counter, nu_out, s);
+  return check_launch(ctx, "unstable index");
+}
+
+__global__ void k_debug_extract(Work w, int64_t N, int F, int32_t *rect, uint32_t *zbits) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N * F) return;
+  const float4 c1 = w.rec_cold[i * 2 + 1];
+  const bool vis = w.ntiles[i] != 0u;
+  const uint32_t lo = __float_as_uint(c1.z), hi = __float_as_uint(c1.w);
+  if (rect != nullptr) {
+    rect[4 * i + 0] = vis ? (int32_t)(lo & 0xffff) : -1;
+    rect[4 * i + 1] = vis ? (int32_t)(lo >> 16) : -1;
+    rect[4 * i + 2] = vis ? (int32_t)(hi & 0xffff) : -1;
+    rect[4 * i + 3] = vis ? (int32_t)(hi >> 16) : -1;
+  }
+  if (zbits != nullptr) zbits[i] = vis ? __float_as_uint(c1.x) : 0u;
+}
+
+}  // namespace
+
+extern "C" {
+
+rtg_status rtg_workspace_size(const rtg_capacity *cap, size_t *bytes) {
+  if (!capacity_ok(cap) || bytes == nullptr) return RTG_ERR_ARG;
+  *bytes = layout_of(cap).total;
+  return RTG_OK;
+}
+
+rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap) {
+  if (out == nullptr) return RTG_ERR_ARG;
+  *out = nullptr;
+  if (!capacity_ok(cap)) return RTG_ERR_ARG;
+  rtg_ctx *ctx = (rtg_ctx *)calloc(1, sizeof(rtg_ctx));
+  if (ctx == nullptr) return RTG_ERR_CUDA;
+  ctx->cap = *cap;
+  cudaGetDevice(&ctx->device);
+  const Layout L = layout_of(cap);
+  ctx->bytes = L.total;
+  if (cudaMalloc((void **)&ctx->slab, L.total) != cudaSuccess) {
+    cudaGetLastError();
+    free(ctx);
+    return RTG_ERR_CUDA;
+  }
+  if (cudaHostAlloc((void **)&ctx->status_host, 4, cudaHostAllocMapped) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(ctx->slab);
+    free(ctx);
+    return RTG_ERR_CUDA;
+  }
+  *ctx->status_host = 0u;
+  uint32_t *status_dev = nullptr;
+  cudaHostGetDevicePointer((void **)&status_dev, ctx->status_host, 0);
+  char *b = ctx->slab;
+  Work &w = ctx->w;
+  w.cams = (DevCam *)(b + L.cams);
+  w.counters = (unsigned long long *)(b + L.counters);
+  w.rank = (int32_t *)(b + L.rank);
+  w.ids = (int32_t *)(b + L.ids);
+  w.block_cnt = (int32_t *)(b + L.block_cnt);
+  w.rec_hot = (float4 *)(b + L.rec_hot);
+  w.rec_cold = (float4 *)(b + L.rec_cold);
+  w.ntiles = (uint32_t *)(b + L.ntiles);
+  w.tile_npix = (uint32_t *)(b + L.tile_npix);
+  w.tile_count = (uint32_t *)(b + L.tile_count);
+  w.tile_offset = (uint32_t *)(b + L.tile_offset);
+  w.tile_cursor = (uint32_t *)(b + L.tile_cursor);
+  w.keys = (unsigned long long *)(b + L.keys);
+  w.keys_alt = (unsigned long long *)(b + L.keys_alt);
+  w.sorted = (uint32_t *)(b + L.sorted);
+  w.px_T = (float *)(b + L.px_T);
+  w.px_last = (uint32_t *)(b + L.px_last);
+  w.px_hit = (int32_t *)(b + L.px_hit);
+  w.grad2d = (float *)(b + L.grad2d);
+  w.loss_part = (float *)(b + L.loss_part);
+  w.loss_scal = (float *)(b + L.loss_scal);
+  w.loss_done = (uint32_t *)(b + L.loss_done);
+  w.status = status_dev;
+  // zero the small bookkeeping region once (counters, loss ticket)
+  cudaMemset(ctx->slab + L.counters, 0, kNumCounters * sizeof(unsigned long long));
+  cudaMemset(ctx->slab + L.loss_done, 0, 4);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeHost(ctx->status_host);
+    cudaFree(ctx->slab);
+    free(ctx);
+    return RTG_ERR_CUDA;
+  }
+  snprintf(ctx->err, sizeof(ctx->err), "ok");
+  *out = ctx;
+  return RTG_OK;
+}
+
+rtg_status rtg_destroy(rtg_ctx *ctx) {
+  if (ctx == nullptr) return RTG_OK;
+  cudaDeviceSynchronize();
+  cudaFree(ctx->slab);
+  cudaFreeHost(ctx->status_host);
+  free(ctx);
+  return RTG_OK;
+}
+
+const char *rtg_last_error(rtg_ctx *ctx) { return ctx == nullptr ? kNoCtx : ctx->err; }
+
+rtg_status rtg_get_status(rtg_ctx *ctx) {
+  if (ctx == nullptr) return RTG_ERR_ARG;
+  return (rtg_status)(int32_t)(*(volatile uint32_t *)ctx->status_host);
+}
+
+rtg_status rtg_reset_status(rtg_ctx *ctx) {
+  if (ctx == nullptr) return RTG_ERR_ARG;
+  *(volatile uint32_t *)ctx->status_host = 0u;
+  return RTG_OK;
+}
+
+rtg_status rtg_render_forward(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, const rtg_gaussians *g,
+                              const uint8_t *mask, const rtg_render_params *prm, float *color, float *depth,
+                              float *alpha, int32_t *index_map, void *stream) {
+  if (ctx == nullptr) return RTG_ERR_ARG;
+  ctx->has_fwd = false;
+  Prm P;
+  rtg_status st = make_prm(ctx, prm, P);
+  if (st != RTG_OK) return st;
+  FrameSet fs;
+  if ((st = make_frames(ctx, cams, F, prm, fs)) != RTG_OK) return st;
+  GaussPtrs gp;
+  if ((st = make_gauss(ctx, g, gp)) != RTG_OK) return st;
+  if (color == nullptr || depth == nullptr || alpha == nullptr) return fail(ctx, RTG_ERR_ARG, "output is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int T = fs.cam[0].tiles_x * fs.cam[0].tiles_y;
+  const int FT = F * T;
+  const int64_t n = gp.n;
+  Work &w = ctx->w;
+  launch_tile_mask(fs, w, mask, T, s);
+  if ((st = rank_pass(ctx, gp.unstable, n, w.rank, w.ids, w.counters, nullptr, s)) != RTG_OK) return st;
+  launch_project(gp, w, P, F, T, s);
+  launch_scan_tiles(w, FT, ctx->cap.max_pairs, s);
+  launch_emit(w, n, F, T, s);
+  launch_sort_tiles(w, FT, s);
+  launch_forward(gp.C, w, P, n, F, T, mask, color, depth, alpha, index_map, s);
+  if ((st = check_launch(ctx, "render_forward")) != RTG_OK) return st;
+  ctx->has_fwd = true;
+  ctx->g = gp;
+  ctx->prm = P;
+  ctx->F = F;
+  ctx->W = fs.cam[0].W;
+  ctx->H = fs.cam[0].H;
+  ctx->T = T;
+  ctx->C = gp.C;
+  ctx->mask = mask;
+  ctx->last_stream = s;
+  return RTG_OK;
+}
+
+rtg_status rtg_render_backward(rtg_ctx *ctx, const float *dL_dcolor, const float *dL_ddepth, float *g_means,
+                               float *g_scales, float *g_quats, float *g_opacity, float *g_colors, void *stream) {
+  if (ctx == nullptr) return RTG_ERR_ARG;
+  if (!ctx->has_fwd) return fail(ctx, RTG_ERR_STATE, "render_backward without a preceding render_forward");
+  if (dL_dcolor == nullptr || dL_ddepth == nullptr) return fail(ctx, RTG_ERR_ARG, "image gradient is NULL");
+  if (!g_means || !g_scales || !g_quats || !g_opacity || !g_colors)
+    return fail(ctx, RTG_ERR_ARG, "gradient output is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int FT = ctx->F * ctx->T;
+  const int64_t n = ctx->g.n;
+  (void)FT;
+  launch_backward(ctx->C, ctx->w, ctx->prm, n, ctx->F, ctx->T, ctx->mask, dL_dcolor, dL_ddepth, s);
+  launch_project_backward(ctx->g, ctx->w, ctx->prm, ctx->F, g_means, g_scales, g_quats, g_opacity, g_colors, s);
+  ctx->last_stream = s;
+  return check_launch(ctx, "render_backward");
+}
+
+rtg_status rtg_l1_loss(rtg_ctx *ctx, int32_t F, int32_t C, int32_t H, int32_t W, const float *color,
+                       const float *depth, const float *target_color, const float *target_depth,
+                       const uint8_t *mask, float w_color, float w_depth, float *loss_out, float *dL_dcolor,
+                       float *dL_ddepth, void *stream) {
+  if (ctx == nullptr) return RTG_ERR_ARG;
+  if (F < 1 || C < 1 || H < 1 || W < 1) return fail(ctx, RTG_ERR_ARG, "l1_loss: bad sizes");
+  if (!color || !depth || !target_color || !target_depth || !loss_out || !dL_dcolor || !dL_ddepth)
+    return fail(ctx, RTG_ERR_ARG, "l1_loss: NULL pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  launch_l1_loss(ctx->w, F, C, H, W, color, depth, target_color, target_depth, mask, w_color, w_depth, loss_out,
+                 dL_dcolor, dL_ddepth, s);
+  ctx->last_stream = s;
+  return check_launch(ctx, "l1_loss");
+}
+
+rtg_status rtg_adam_step(int64_t nu, int32_t C, float *means, float *scales, float *quats, float *opacity,
+                         float *colors, const float *g_means, const float *g_scales, const float *g_quats,
+                         const float *g_opacity, const float *g_colors, float *m, float *v, int32_t step,
+                         const rtg_adam_params *hp, void *stream) {
+  if (nu < 0 || C < 1 || C > 64 || step < 1 || hp == nullptr) return RTG_ERR_ARG;
+  if (nu == 0) return RTG_OK;
+  if (!means || !scales || !quats || !opacity || !colors || !g_means || !g_scales || !g_quats || !g_opacity ||
+      !g_colors || !m || !v)
+    return RTG_ERR_ARG;
+  const double bc1 = 1.0 / (1.0 - pow((double)hp->beta1, step));
+  const double bc2s = 1.0 / sqrt(1.0 - pow((double)hp->beta2, step));
+  launch_adam(nu, C, means, scales, quats, opacity, colors, g_means, g_scales, g_quats, g_opacity, g_colors, m, v,
+              *hp, (float)bc1, (float)bc2s, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? RTG_OK : RTG_ERR_CUDA;
+}
+
+rtg_status rtg_unstable_index(rtg_ctx *ctx, int64_t n, const uint8_t *unstable, int32_t *ids, int64_t *nu_out,
+                              void *stream) {
+  if (ctx == nullptr) return RTG_ERR_ARG;
+  if (n < 0 || n > ctx->cap.max_gaussians) return fail(ctx, RTG_ERR_ARG, "n outside capacity");
+  if (n > 0 && (unstable == nullptr || ids == nullptr)) return fail(ctx, RTG_ERR_ARG, "NULL pointer");
+  if (nu_out == nullptr) return fail(ctx, RTG_ERR_ARG, "nu_out is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n == 0) {
+    cudaMemsetAsync(nu_out, 0, sizeof(int64_t), s);
+    return check_launch(ctx, "unstable_index");
+  }
+  return rank_pass(ctx, unstable, n, nullptr, ids, nullptr, nu_out, s);
+}
+
+rtg_status rtg_gather_unstable(int64_t nu, int32_t C, const int32_t *ids, const float *means, const float *scales,
+                               const float *quats, const float *opacity, const float *colors, float *u_means,
+                               float *u_scales, float *u_quats, float *u_opacity, float *u_colors, void *stream) {
+  if (nu < 0 || C < 1) return RTG_ERR_ARG;
+  if (nu == 0) return RTG_OK;
+  if (!ids || !means || !scales || !quats || !opacity || !colors || !u_means || !u_scales || !u_quats ||
+      !u_opacity || !u_colors)
+    return RTG_ERR_ARG;
+  launch_gather(nu, C, ids, means, scales, quats, opacity, colors, u_means, u_scales, u_quats, u_opacity, u_colors,
+                (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? RTG_OK : RTG_ERR_CUDA;
+}
+
+rtg_status rtg_scatter_unstable(int64_t nu, int32_t C, const int32_t *ids, const float *u_means,
+                                const float *u_scales, const float *u_quats, const float *u_opacity,
+                                const float *u_colors, float *means, float *scales, float *quats, float *opacity,
+                                float *colors, void *stream) {
+  if (nu < 0 || C < 1) return RTG_ERR_ARG;
+  if (nu == 0) return RTG_OK;
+  if (!ids || !means || !scales || !quats || !opacity || !colors || !u_means || !u_scales || !u_quats ||
+      !u_opacity || !u_colors)
+    return RTG_ERR_ARG;
+  launch_scatter(nu, C, ids, u_means, u_scales, u_quats, u_opacity, u_colors, means, scales, quats, opacity, colors,
+                 (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? RTG_OK : RTG_ERR_CUDA;
+}
+
+rtg_status rtg_unstable_mask(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, const rtg_gaussians *g,
+                             const rtg_render_params *prm, uint8_t *mask, void *stream) {
+  if (ctx == nullptr) return RTG_ERR_ARG;
+  Prm P;
+  rtg_status st = make_prm(ctx, prm, P);
+  if (st != RTG_OK) return st;
+  FrameSet fs;
+  if ((st = make_frames(ctx, cams, F, prm, fs)) != RTG_OK) return st;
+  GaussPtrs gp;
+  if ((st = make_gauss(ctx, g, gp)) != RTG_OK) return st;
+  if (mask == nullptr) return fail(ctx, RTG_ERR_ARG, "mask is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int T = fs.cam[0].tiles_x * fs.cam[0].tiles_y;
+  const size_t npx = (size_t)F * fs.cam[0].W * fs.cam[0].H;
+  ctx->has_fwd = false;  // the mask pass reuses the forward's workspace
+  cudaMemsetAsync(mask, 0, npx, s);
+  launch_tile_mask(fs, ctx->w, nullptr, T, s);
+  if (gp.u_means != nullptr)
+    if ((st = rank_pass(ctx, gp.unstable, gp.n, ctx->w.rank, ctx->w.ids, ctx->w.counters, nullptr, s)) != RTG_OK)
+      return st;
+  launch_unstable_mask(gp, ctx->w, P, F, T, mask, s);
+  ctx->last_stream = s;
+  return check_launch(ctx, "unstable_mask");
+}
+
+rtg_status rtg_get_stats(rtg_ctx *ctx, rtg_stats *out) {
+  if (ctx == nullptr || out == nullptr) return RTG_ERR_ARG;
+  if (cudaStreamSynchronize(ctx->last_stream) != cudaSuccess) {
+    cudaError_t e = cudaGetLastError();
+    return fail(ctx, RTG_ERR_CUDA, "get_stats: %s", cudaGetErrorString(e));
+  }
+  unsigned long long c[kNumCounters];
+  if (cudaMemcpy(c, ctx->w.counters, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaError_t e = cudaGetLastError();
+    return fail(ctx, RTG_ERR_CUDA, "get_stats: %s", cudaGetErrorString(e));
+  }
+  out->pairs = (int64_t)c[kPairs];
+  out->fragments = (int64_t)c[kFragments];
+  out->visible = (int64_t)c[kVisible];
+  out->masked_pixels = (int64_t)c[kMaskedPix];
+  out->n_unstable = (int64_t)c[kNumUnstable];
+  out->max_tile_pairs = (int32_t)c[kMaxTilePairs];
+  out->status = (int32_t)*(volatile uint32_t *)ctx->status_host;
+  return RTG_OK;
+}
+
+rtg_status rtg_debug_binning(rtg_ctx *ctx, uint32_t *tile_offsets, uint32_t *sorted_ids, int32_t *rect,
+                             uint32_t *zbits, void *stream) {
+  if (ctx == nullptr) return RTG_ERR_ARG;
+  if (!ctx->has_fwd) return fail(ctx, RTG_ERR_STATE, "debug_binning without a forward");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaStreamSynchronize(ctx->last_stream) != cudaSuccess) return fail(ctx, RTG_ERR_CUDA, "sync failed");
+  unsigned long long pairs = 0;
+  cudaMemcpy(&pairs, ctx->w.counters + kPairs, sizeof(pairs), cudaMemcpyDeviceToHost);
+  const size_t FT = (size_t)ctx->F * ctx->T;
+  if (tile_offsets) cudaMemcpyAsync(tile_offsets, ctx->w.tile_offset, (FT + 1) * 4, cudaMemcpyDeviceToDevice, s);
+  if (sorted_ids && pairs) cudaMemcpyAsync(sorted_ids, ctx->w.sorted, pairs * 4, cudaMemcpyDeviceToDevice, s);
+  const int64_t NF = ctx->g.n * ctx->F;
+  if ((rect || zbits) && NF > 0)
+    k_debug_extract<<<(unsigned)((NF + 255) / 256), 256, 0, s>>>(ctx->w, ctx->g.n, ctx->F, rect, zbits);
+  return check_launch(ctx, "debug_binning");
+}
+
+}  // extern "C"

@@ -1,0 +1,409 @@
+// Backward pass of the masked render (Section 3.1: "the depth ... is linearly computed
+// from the position and rotation of the Gaussian ... fully differentiable"; Section 3.2:
+// only the unstable Gaussians are optimised).
+//
+// k_backward replays each masked pixel's composited fragments back to front, recovering
+// the transmission by division (T_j = T_{j+1} / (1 - f_j)) instead of storing it, and
+// accumulates, for unstable Gaussians only, the screen-space gradients
+//   dC/dc_j = f_j T_j,   dC/df_j = c_j T_j - S_j / (1 - f_j),   S_j = sum_{i>j} c_i f_i T_i
+// (no background term), chained through f = min(f_max, alpha 2^-q), q = |U (u - mu)|^2.
+// The depth depends on f only through the choice of the hit fragment, so it adds no
+// gradient to f; its gradient goes to the hit Gaussian's plane record (d0, n_c) or to
+// its centre depth.  Sums over a warp's 32 pixels are formed with shuffles and added
+// with one vector atomic per warp.
+//
+// k_project_backward chains those screen-space gradients to position, linear scale,
+// raw quaternion, opacity and colour through Sigma_2D = J W R S^2 R^T W^T J^T + lowpass I,
+// the conic inverse, the perspective centre, the plane offset d0 = p_c . n_c and the
+// normal n_c = W R e_k.
+#include "kernels.cuh"
+#include "project.cuh"
+
+namespace rtg {
+
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int C>
+__global__ void __launch_bounds__(kTilePix) k_backward(Work w, Prm prm, int64_t N, int T,
+                                                       const uint8_t *__restrict__ mask,
+                                                       const float *__restrict__ dL_dcolor,
+                                                       const float *__restrict__ dL_ddepth) {
+  constexpr int H4 = (C <= 4) ? 3 : 4;
+  constexpr int G2 = (C <= 5) ? 16 : 20;
+  __shared__ float4 s_rec[H4][kTilePix];
+  __shared__ int s_rank[kTilePix];
+  __shared__ int s_pix[kTilePix];
+  __shared__ int s_wcnt[kTilePix / 32];
+  __shared__ unsigned s_maxlast;
+  if (w.counters[kSkip] != 0ull) return;
+  const int tile = blockIdx.x;
+  if (w.tile_npix[tile] == 0u) return;
+  const int f = tile / T, lt = tile - f * T;
+  const DevCam &cam = w.cams[f];
+  const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  {
+    const int px = tx * kTile + (tid & (kTile - 1)), py = ty * kTile + tid / kTile;
+    bool act = px < cam.W && py < cam.H;
+    if (act && mask != nullptr) act = mask[((int64_t)f * cam.H + py) * cam.W + px] != 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, act);
+    if (lane == 0) s_wcnt[wid] = __popc(bal);
+    if (tid == 0) s_maxlast = 0u;
+    __syncthreads();
+    int before = 0;
+    for (int k = 0; k < wid; ++k) before += s_wcnt[k];
+    if (act) s_pix[before + __popc(bal & lanemask_lt())] = tid;
+    __syncthreads();
+  }
+  const int npix = (int)w.tile_npix[tile];
+  const bool has = tid < npix;
+  const int my = has ? s_pix[tid] : 0;
+  const int px = tx * kTile + (my & (kTile - 1)), py = ty * kTile + my / kTile;
+  const float fpx = (float)px, fpy = (float)py;
+  const int64_t HW = (int64_t)cam.H * cam.W;
+  const int64_t pix = (int64_t)f * HW + (int64_t)py * cam.W + px;
+  const uint32_t off = w.tile_offset[tile];
+  float T_ = 1.f, dLdD = 0.f;
+  uint32_t last = 0;
+  int hit = -1;
+  float dC[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) dC[c] = 0.f;
+  if (has) {
+    T_ = w.px_T[pix];
+    last = w.px_last[pix];
+    hit = w.px_hit[pix];
+#pragma unroll
+    for (int c = 0; c < C; ++c) dC[c] = dL_dcolor[((int64_t)f * C + c) * HW + (int64_t)py * cam.W + px];
+    dLdD = dL_ddepth[pix];
+    atomicMax(&s_maxlast, last);
+  }
+  float *__restrict__ g2base = w.grad2d + (int64_t)f * N * G2;
+
+  // ---- depth: gradient to the hit Gaussian's plane record or centre depth (Eq. 4/5)
+  {
+    int key = -1;
+    float gd0 = 0.f, gn0 = 0.f, gn1 = 0.f, gn2 = 0.f, gz = 0.f;
+    if (has && hit >= 0 && dLdD != 0.f) {
+      const float4 c0 = w.rec_cold[((int64_t)f * N + hit) * 2];
+      const float4 c1 = w.rec_cold[((int64_t)f * N + hit) * 2 + 1];
+      const int rk = __float_as_int(c1.y);
+      if (rk >= 0) {
+        key = rk;
+        const float ux = (fpx - cam.cx) / cam.fx, uy = (fpy - cam.cy) / cam.fy;
+        const float den = fmaf(c0.x, ux, fmaf(c0.y, uy, c0.z));
+        const float nu = sqrtf(fmaf(ux, ux, fmaf(uy, uy, 1.f)));
+        if (fabsf(den) >= prm.cos_max * nu) {
+          // D = d0 / (n_c . u~): dD/dd0 = 1/den, dD/dn_c = -d0 u~ / den^2
+          const float id = 1.f / den;
+          gd0 = dLdD * id;
+          const float s = -dLdD * c0.w * id * id;
+          gn0 = s * ux;
+          gn1 = s * uy;
+          gn2 = s;
+        } else {
+          gz = dLdD;
+        }
+      }
+    }
+    // aggregate lanes that share a hit Gaussian, one atomic group per distinct Gaussian
+    unsigned pending = __ballot_sync(0xffffffffu, key >= 0);
+    while (pending) {
+      const int leader = __ffs(pending) - 1;
+      const int k = __shfl_sync(0xffffffffu, key, leader);
+      const bool in = key == k;
+      const float a0 = warp_sum(in ? gd0 : 0.f), a1 = warp_sum(in ? gn0 : 0.f), a2 = warp_sum(in ? gn1 : 0.f),
+                  a3 = warp_sum(in ? gn2 : 0.f), a4 = warp_sum(in ? gz : 0.f);
+      if (lane == leader) {
+        float *row = g2base + (int64_t)k * G2;
+        atomicAdd(row + g2_d0(C), a0);
+        atomicAdd(row + g2_nc(C) + 0, a1);
+        atomicAdd(row + g2_nc(C) + 1, a2);
+        atomicAdd(row + g2_nc(C) + 2, a3);
+        atomicAdd(row + g2_z(C), a4);
+      }
+      pending &= ~__ballot_sync(0xffffffffu, in);
+    }
+  }
+  __syncthreads();
+  const uint32_t maxlast = s_maxlast;
+  const float4 *__restrict__ rec = w.rec_hot + (int64_t)f * N * H4;
+  float S[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) S[c] = 0.f;
+  const bool warp_has = __any_sync(0xffffffffu, has);
+
+  for (int b_end = (int)maxlast; b_end > 0; b_end -= kTilePix) {
+    const int b_beg = max(0, b_end - kTilePix);
+    __syncthreads();
+    {
+      const int j = b_beg + tid;
+      if (j < b_end) {
+        const uint32_t gid = w.sorted[off + j];
+        const float4 *r = rec + (int64_t)gid * H4;
+#pragma unroll
+        for (int k = 0; k < H4; ++k) s_rec[k][tid] = r[k];
+        s_rank[tid] = __float_as_int(w.rec_cold[((int64_t)f * N + gid) * 2 + 1].y);
+      }
+    }
+    __syncthreads();
+    if (!warp_has) continue;
+    for (int j = b_end - 1; j >= b_beg; --j) {
+      const int k = j - b_beg;
+      bool act = has && (uint32_t)j < last;
+      const float4 r0 = s_rec[0][k], r1 = s_rec[1][k];
+      float dx = 0.f, dy = 0.f, t1 = 0.f, t2 = 0.f, g = 0.f, fa = 0.f;
+      if (act) {
+        fa = footprint(fpx, fpy, r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, prm.f_max, dx, dy, t1, t2, g);
+        act = fa >= prm.alpha_min;
+      }
+      const int rk = s_rank[k];
+      float gmx = 0.f, gmy = 0.f, gca = 0.f, gcb = 0.f, gcc = 0.f, gal = 0.f;
+      float gcol[C];
+#pragma unroll
+      for (int c = 0; c < C; ++c) gcol[c] = 0.f;
+      if (act) {
+        const float om = 1.f - fa;
+        T_ = T_ / om;  // transmission in front of fragment j
+        const float wgt = fa * T_;
+        const float4 c0 = s_rec[2][k];
+        float cw[8] = {c0.x, c0.y, c0.z, c0.w, 0.f, 0.f, 0.f, 0.f};
+        if (H4 == 4) {
+          const float4 c1 = s_rec[3 % H4][k];
+          cw[4] = c1.x; cw[5] = c1.y; cw[6] = c1.z; cw[7] = c1.w;
+        }
+        float dLdf = 0.f;
+        const float iom = 1.f / om;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          gcol[c] = wgt * dC[c];
+          dLdf = fmaf(dC[c], fmaf(cw[c], T_, -S[c] * iom), dLdf);
+          S[c] = fmaf(cw[c], wgt, S[c]);
+        }
+        if (rk >= 0 && r1.w * g < prm.f_max) {  // unclamped branch of min(f_max, alpha g)
+          gal = dLdf * g;
+          const float dLdq = -dLdf * r1.w * g * kLn2;  // g = 2^-q
+          gmx = -2.f * dLdq * (r1.x * t1);
+          gmy = -2.f * dLdq * fmaf(r1.y, t1, r1.z * t2);
+          const float dLdp = dLdq * kQScale2;  // q = kQScale2 * d^T conic d
+          gca = dLdp * dx * dx;
+          gcb = dLdp * 2.f * dx * dy;
+          gcc = dLdp * dy * dy;
+        }
+      }
+      if (rk >= 0 && __any_sync(0xffffffffu, act)) {
+        gmx = warp_sum(gmx); gmy = warp_sum(gmy);
+        gca = warp_sum(gca); gcb = warp_sum(gcb); gcc = warp_sum(gcc);
+        gal = warp_sum(gal);
+#pragma unroll
+        for (int c = 0; c < C; ++c) gcol[c] = warp_sum(gcol[c]);
+        if (lane == 0) {
+          float4 *row = reinterpret_cast<float4 *>(g2base + (int64_t)rk * G2);
+          float v[4 * ((6 + C + 3) / 4)];
+          v[0] = gmx; v[1] = gmy; v[2] = gca; v[3] = gcb; v[4] = gcc; v[5] = gal;
+#pragma unroll
+          for (int c = 0; c < C; ++c) v[6 + c] = gcol[c];
+#pragma unroll
+          for (int c = 6 + C; c < 4 * ((6 + C + 3) / 4); ++c) v[c] = 0.f;
+#pragma unroll
+          for (int q4 = 0; q4 < (6 + C + 3) / 4; ++q4)
+            atomicAdd(row + q4, make_float4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]));
+        }
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------------------- 2D -> 3D
+template <int C>
+__global__ void __launch_bounds__(256) k_project_backward(GaussPtrs g, Work w, Prm prm, int F,
+                                                          float *__restrict__ g_means, float *__restrict__ g_scales,
+                                                          float *__restrict__ g_quats, float *__restrict__ g_opacity,
+                                                          float *__restrict__ g_colors) {
+  constexpr int G2 = (C <= 5) ? 16 : 20;
+  const int64_t nu = (int64_t)w.counters[kNumUnstable];
+  const int64_t N = g.n;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nu; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = w.ids[k];
+    GParams P;
+    const bool ok = load_params(g, w.rank, i, P);
+    float gp[3] = {0, 0, 0}, gs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, ga = 0.f, gc[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) gc[c] = 0.f;
+    if (ok) {
+      const float qn = sqrtf(P.q[0] * P.q[0] + P.q[1] * P.q[1] + P.q[2] * P.q[2] + P.q[3] * P.q[3]);
+      const float qw = P.q[0] / qn, qx = P.q[1] / qn, qy = P.q[2] / qn, qz = P.q[3] / qn;
+      float R[9];
+      quat_to_rot(qw, qx, qy, qz, R);
+      const int kmin = argmin3(P.s[0], P.s[1], P.s[2]);
+      float gR[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+      for (int f = 0; f < F; ++f) {
+        if (w.ntiles[(int64_t)f * N + i] == 0u) continue;
+        const DevCam &cam = w.cams[f];
+        const float *row = w.grad2d + ((int64_t)f * N + k) * G2;
+        const float gmx = row[kG2Mu], gmy = row[kG2Mu + 1];
+        const float gA = row[kG2Conic], gB = row[kG2Conic + 1], gCc = row[kG2Conic + 2];
+        ga += row[kG2Alpha];
+#pragma unroll
+        for (int c = 0; c < C; ++c) gc[c] += row[kG2Col + c];
+        const float gd0 = row[g2_d0(C)], gn[3] = {row[g2_nc(C)], row[g2_nc(C) + 1], row[g2_nc(C) + 2]};
+        const float gz = row[g2_z(C)];
+        // forward quantities (FP32 recomputation)
+        const float d[3] = {P.p[0] - cam.t[0], P.p[1] - cam.t[1], P.p[2] - cam.t[2]};
+        float pc[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) pc[r] = cam.R[r] * d[0] + cam.R[3 + r] * d[1] + cam.R[6 + r] * d[2];
+        float A[9];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) A[3 * r + c] = cam.R[r] * R[c] + cam.R[3 + r] * R[3 + c] + cam.R[6 + r] * R[6 + c];
+        const float X = pc[0], Y = pc[1], Z = pc[2], iz = 1.f / Z;
+        const float j00 = cam.fx * iz, j02 = -cam.fx * X * iz * iz, j11 = cam.fy * iz, j12 = -cam.fy * Y * iz * iz;
+        // Sigma_c = A S^2 A^T (camera-frame covariance); cov = J Sigma_c J^T + lowpass I
+        float Sc[9];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            float acc = 0.f;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) acc += A[3 * r + m] * P.s[m] * P.s[m] * A[3 * c + m];
+            Sc[3 * r + c] = acc;
+          }
+        const float J[6] = {j00, 0.f, j02, 0.f, j11, j12};
+        float JS[6];  // J Sigma_c (2x3)
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) JS[3 * r + c] = J[3 * r] * Sc[c] + J[3 * r + 1] * Sc[3 + c] + J[3 * r + 2] * Sc[6 + c];
+        const float a = JS[0] * J[0] + JS[1] * J[1] + JS[2] * J[2] + prm.lowpass;
+        const float b = JS[0] * J[3] + JS[1] * J[4] + JS[2] * J[5];
+        const float cc = JS[3] * J[3] + JS[4] * J[4] + JS[5] * J[5] + prm.lowpass;
+        const float det = a * cc - b * b;
+        const float id2 = 1.f / (det * det);
+        // conic (a', b', c') = (c, -b, a) / det  ->  gradient w.r.t. (a, b, c) of Sigma_2D
+        const float ga_ = (-cc * cc * gA + b * cc * gB - b * b * gCc) * id2;
+        const float gb_ = (2.f * b * cc * gA - (a * cc + b * b) * gB + 2.f * a * b * gCc) * id2;
+        const float gc_ = (-b * b * gA + a * b * gB - a * a * gCc) * id2;
+        // symmetric matrix gradient G = [[ga, gb/2], [gb/2, gc]]
+        const float G[4] = {ga_, 0.5f * gb_, 0.5f * gb_, gc_};
+        // dL/dSigma_c = J^T G J ; dL/dJ = 2 G J Sigma_c
+        float GJ[6];
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) GJ[3 * r + c] = G[2 * r] * J[c] + G[2 * r + 1] * J[3 + c];
+        float gSc[9];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) gSc[3 * r + c] = J[r] * GJ[c] + J[3 + r] * GJ[3 + c];
+        float gJ[6];
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            gJ[3 * r + c] = 2.f * (GJ[3 * r] * Sc[c] + GJ[3 * r + 1] * Sc[3 + c] + GJ[3 * r + 2] * Sc[6 + c]);
+        // camera-frame centre: J entries, mu, depth terms
+        float gpc[3];
+        gpc[0] = gJ[2] * (-cam.fx * iz * iz) + gmx * cam.fx * iz;
+        gpc[1] = gJ[5] * (-cam.fy * iz * iz) + gmy * cam.fy * iz;
+        gpc[2] = gJ[0] * (-cam.fx * iz * iz) + gJ[2] * (2.f * cam.fx * X * iz * iz * iz) +
+                 gJ[4] * (-cam.fy * iz * iz) + gJ[5] * (2.f * cam.fy * Y * iz * iz * iz) -
+                 (gmx * cam.fx * X + gmy * cam.fy * Y) * iz * iz + gz;
+        const float nc[3] = {A[kmin], A[3 + kmin], A[6 + kmin]};
+#pragma unroll
+        for (int r = 0; r < 3; ++r) gpc[r] += gd0 * nc[r];
+        float gnc[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) gnc[r] = gd0 * pc[r] + gn[r];
+        // p_c = W (p - t)  ->  dL/dp = W^T dL/dp_c = R_g dL/dp_c
+#pragma unroll
+        for (int r = 0; r < 3; ++r) gp[r] += cam.R[3 * r] * gpc[0] + cam.R[3 * r + 1] * gpc[1] + cam.R[3 * r + 2] * gpc[2];
+        // Sigma_c = W Sigma W^T -> dL/dSigma = W^T gSc W ; Sigma = R S^2 R^T
+        float gS[9];  // dL/dSigma (world), = R_g gSc R_g^T
+        {
+          float tmp[9];
+#pragma unroll
+          for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              tmp[3 * r + c] = cam.R[3 * r] * gSc[c] + cam.R[3 * r + 1] * gSc[3 + c] + cam.R[3 * r + 2] * gSc[6 + c];
+#pragma unroll
+          for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              gS[3 * r + c] = tmp[3 * r] * cam.R[3 * c] + tmp[3 * r + 1] * cam.R[3 * c + 1] + tmp[3 * r + 2] * cam.R[3 * c + 2];
+        }
+        // dL/dR += 2 gS R D (D = diag s^2), dL/ds_m += 2 s_m (R^T gS R)_mm
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float gSR = gS[3 * r] * R[c] + gS[3 * r + 1] * R[3 + c] + gS[3 * r + 2] * R[6 + c];
+            gR[3 * r + c] += 2.f * gSR * P.s[c] * P.s[c];
+          }
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          float acc = 0.f;
+#pragma unroll
+          for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc += R[3 * r + m] * gS[3 * r + c] * R[3 * c + m];
+          gs[m] += 2.f * P.s[m] * acc;
+        }
+        // n_c = W R e_k -> dL/dR[:, k] += W^T dL/dn_c = R_g dL/dn_c
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+          gR[3 * r + kmin] += cam.R[3 * r] * gnc[0] + cam.R[3 * r + 1] * gnc[1] + cam.R[3 * r + 2] * gnc[2];
+      }
+      // R(q) -> unit quaternion -> raw quaternion
+      const float G01 = gR[1], G02 = gR[2], G10 = gR[3], G12 = gR[5], G20 = gR[6], G21 = gR[7];
+      const float G00 = gR[0], G11 = gR[4], G22 = gR[8];
+      float gqn[4];
+      gqn[0] = 2.f * (-qz * G01 + qy * G02 + qz * G10 - qx * G12 - qy * G20 + qx * G21);
+      gqn[1] = 2.f * (qy * G01 + qz * G02 + qy * G10 - 2.f * qx * G11 - qw * G12 + qz * G20 + qw * G21 - 2.f * qx * G22);
+      gqn[2] = 2.f * (-2.f * qy * G00 + qx * G01 + qw * G02 + qx * G10 + qz * G12 - qw * G20 + qz * G21 - 2.f * qy * G22);
+      gqn[3] = 2.f * (-2.f * qz * G00 - qw * G01 + qx * G02 + qw * G10 - 2.f * qz * G11 + qy * G12 + qx * G20 + qy * G21);
+      const float qh[4] = {qw, qx, qy, qz};
+      const float dotq = qh[0] * gqn[0] + qh[1] * gqn[1] + qh[2] * gqn[2] + qh[3] * gqn[3];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) gq[m] = (gqn[m] - qh[m] * dotq) / qn;
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      g_means[3 * k + r] = gp[r];
+      g_scales[3 * k + r] = gs[r];
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) g_quats[4 * k + m] = gq[m];
+    g_opacity[k] = ga;
+#pragma unroll
+    for (int c = 0; c < C; ++c) g_colors[(int64_t)C * k + c] = gc[c];
+  }
+}
+
+void launch_backward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const uint8_t *mask,
+                     const float *dL_dcolor, const float *dL_ddepth, cudaStream_t s) {
+  if (C == 3)
+    k_backward<3><<<F * T, kTilePix, 0, s>>>(w, prm, N, T, mask, dL_dcolor, dL_ddepth);
+  else
+    k_backward<8><<<F * T, kTilePix, 0, s>>>(w, prm, N, T, mask, dL_dcolor, dL_ddepth);
+}
+
+void launch_project_backward(const GaussPtrs &g, const Work &w, const Prm &prm, int F, float *g_means,
+                             float *g_scales, float *g_quats, float *g_opacity, float *g_colors, cudaStream_t s) {
+  if (g.n <= 0) return;
+  if (g.C == 3)
+    k_project_backward<3><<<kPersistBlocks, 256, 0, s>>>(g, w, prm, F, g_means, g_scales, g_quats, g_opacity,
+                                                         g_colors);
+  else
+    k_project_backward<8><<<kPersistBlocks, 256, 0, s>>>(g, w, prm, F, g_means, g_scales, g_quats, g_opacity,
+                                                         g_colors);
+}
+
+}  // namespace rtg

@@ -1,0 +1,74 @@
+// Kernel declarations and small block-level helpers shared by the translation units.
+#pragma once
+
+#include "rtg_internal.cuh"
+
+namespace rtg {
+
+constexpr int kScanBlock = 1024;   // threads per block of the unstable-index scan
+constexpr int kSortThreads = 256;  // threads per tile-sort CTA
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortCap = 2048;     // keys a tile-sort CTA sorts entirely in shared memory
+constexpr int kLossBlocks = 296;   // 2 x 148 SMs
+constexpr int kPersistBlocks = 148 * 8;
+
+// Cameras of one call, passed by value to the first kernel of a forward.
+struct FrameSet {
+  int F;
+  DevCam cam[kMaxFrames];
+};
+
+__device__ __forceinline__ int block_sum_int(int v, int *s_warp) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) s_warp[wid] = v;
+  __syncthreads();
+  int t = 0;
+  for (int k = 0; k < nw; ++k) t += s_warp[k];
+  __syncthreads();
+  return t;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// ---- host launchers (each defined in the translation unit of its kernels)
+// bin.cu
+void launch_tile_mask(const FrameSet &fs, const Work &w, const uint8_t *mask, int T, cudaStream_t s);
+void launch_rank(const uint8_t *unstable, int64_t n, int32_t *block_cnt, int32_t *rank, int32_t *ids,
+                 unsigned long long *nu_counter, int64_t *nu_out, cudaStream_t s);
+void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, int T, cudaStream_t s);
+void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, cudaStream_t s);
+void launch_emit(const Work &w, int64_t N, int F, int T, cudaStream_t s);
+// sort.cu
+void launch_sort_tiles(const Work &w, int FT, cudaStream_t s);
+// forward.cu
+void launch_forward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const uint8_t *mask, float *color,
+                    float *depth, float *alpha, int32_t *index_map, cudaStream_t s);
+// backward.cu
+void launch_backward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const uint8_t *mask,
+                     const float *dL_dcolor, const float *dL_ddepth, cudaStream_t s);
+void launch_project_backward(const GaussPtrs &g, const Work &w, const Prm &prm, int F, float *g_means,
+                             float *g_scales, float *g_quats, float *g_opacity, float *g_colors, cudaStream_t s);
+// loss_adam_mask.cu
+void launch_l1_loss(const Work &w, int F, int C, int H, int W, const float *color, const float *depth,
+                    const float *tcolor, const float *tdepth, const uint8_t *mask, float w_c, float w_d,
+                    float *loss_out, float *dL_dcolor, float *dL_ddepth, cudaStream_t s);
+void launch_adam(int64_t nu, int C, float *means, float *scales, float *quats, float *opacity, float *colors,
+                 const float *g_means, const float *g_scales, const float *g_quats, const float *g_opacity,
+                 const float *g_colors, float *m, float *v, const rtg_adam_params &hp, float bc1, float bc2_sqrt,
+                 cudaStream_t s);
+void launch_gather(int64_t nu, int C, const int32_t *ids, const float *means, const float *scales,
+                   const float *quats, const float *opacity, const float *colors, float *um, float *us, float *uq,
+                   float *uo, float *uc, cudaStream_t s);
+void launch_scatter(int64_t nu, int C, const int32_t *ids, const float *um, const float *us, const float *uq,
+                    const float *uo, const float *uc, float *means, float *scales, float *quats, float *opacity,
+                    float *colors, cudaStream_t s);
+void launch_unstable_mask(const GaussPtrs &g, const Work &w, const Prm &prm, int F, int T, uint8_t *mask,
+                          cudaStream_t s);
+
+}  // namespace rtg

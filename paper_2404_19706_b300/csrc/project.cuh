@@ -1,0 +1,116 @@
+// EWA projection of one Gaussian into one camera (Section 3.1, Eq. 2 footprint and the
+// disc-plane record used by Eq. 4/5).  Shared by the forward projection kernel and the
+// unstable-mask kernel so that both evaluate exactly the same footprint.
+#pragma once
+
+#include "rtg_internal.cuh"
+
+namespace rtg {
+
+struct Projected {
+  df mux, muy;          // pixel-space centre (double-float)
+  float u11, u12, u22;  // U with U^T U = Sigma_2D^-1 * kQScale^2 (upper triangular)
+  float a, c;           // Sigma_2D diagonal (support bounds)
+  float X, Y, Z;        // camera-frame centre
+  float n[3];           // camera-frame disc normal (axis of the smallest scale)
+  float d0;             // p_c . n_c
+  int x0, y0, x1, y1;   // pixel bounding box of the alpha_min support (inclusive)
+};
+
+// Returns false when the Gaussian is culled (behind the near plane, outside the guard
+// band, or with an empty support inside the image).  R is R(q) of the unit quaternion.
+__device__ __forceinline__ bool project_gaussian(const DevCam &cam, const Prm &prm, const GParams &P,
+                                                 const float R[9], int kmin, Projected &o) {
+  // world -> camera, p_c = R_g^T (p - t_g), carried in double-float
+  df d0 = two_sum(P.p[0], -cam.t[0]);
+  df d1 = two_sum(P.p[1], -cam.t[1]);
+  df d2 = two_sum(P.p[2], -cam.t[2]);
+  df X = df_add(df_add(df_mul_f(d0, cam.R[0]), df_mul_f(d1, cam.R[3])), df_mul_f(d2, cam.R[6]));
+  df Y = df_add(df_add(df_mul_f(d0, cam.R[1]), df_mul_f(d1, cam.R[4])), df_mul_f(d2, cam.R[7]));
+  df Z = df_add(df_add(df_mul_f(d0, cam.R[2]), df_mul_f(d1, cam.R[5])), df_mul_f(d2, cam.R[8]));
+  if (!(Z.hi > prm.near_z)) return false;
+  df tx = df_div(X, Z), ty = df_div(Y, Z);
+  if (!(fabsf(tx.hi) <= cam.lim_x) || !(fabsf(ty.hi) <= cam.lim_y)) return false;
+  o.mux = df_add(df_mul_f(tx, cam.fx), df{cam.cx, 0.f});
+  o.muy = df_add(df_mul_f(ty, cam.fy), df{cam.cy, 0.f});
+  const float Xf = X.hi, Yf = Y.hi, Zf = Z.hi;
+  o.X = Xf; o.Y = Yf; o.Z = Zf;
+  // A = W R with W = R_g^T: the Gaussian's axes in camera coordinates
+  float A[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc)
+      A[3 * r + cc] = cam.R[r] * R[cc] + cam.R[3 + r] * R[3 + cc] + cam.R[6 + r] * R[6 + cc];
+  // M = J A S with J the perspective Jacobian at the centre; Sigma_2D = M M^T + lowpass I
+  const float iz = 1.f / Zf;
+  const float j00 = cam.fx * iz, j02 = -cam.fx * Xf * iz * iz;
+  const float j11 = cam.fy * iz, j12 = -cam.fy * Yf * iz * iz;
+  float a0 = 0.f, b0 = 0.f, c0 = 0.f;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    float m0 = (j00 * A[j] + j02 * A[6 + j]) * P.s[j];
+    float m1 = (j11 * A[3 + j] + j12 * A[6 + j]) * P.s[j];
+    a0 = fmaf(m0, m0, a0);
+    b0 = fmaf(m0, m1, b0);
+    c0 = fmaf(m1, m1, c0);
+  }
+  // det(M M^T) by Cauchy-Binet: the 2x2 minors of J A equal (fx fy / Z^3) times the
+  // components of v = R^T (p - t) (A is a rotation), so the determinant is a sum of
+  // squares and keeps full relative accuracy for thin, tilted footprints.
+  float v[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) v[j] = R[j] * d0.hi + R[3 + j] * d1.hi + R[6 + j] * d2.hi;
+  const float kk = cam.fx * cam.fy * iz * iz * iz;
+  const float w0 = kk * v[0] * P.s[1] * P.s[2];
+  const float w1 = kk * v[1] * P.s[0] * P.s[2];
+  const float w2 = kk * v[2] * P.s[0] * P.s[1];
+  const float lam = prm.lowpass;
+  const float a = a0 + lam, c = c0 + lam;
+  const float det = fmaf(w0, w0, fmaf(w1, w1, w2 * w2)) + lam * (a0 + c0) + lam * lam;
+  float b = b0;
+  if (2.f * b0 * b0 > a * c) b = copysignf(sqrtf(fmaxf(fmaf(a, c, -det), 0.f)), b0);
+  if (!(det > 0.f)) return false;
+  // Cholesky factor of the conic: Sigma_2D^-1 = U^T U, U = [[sqrt(c/det), -b/sqrt(c det)], [0, 1/sqrt(c)]]
+  const float sc = sqrtf(c), sd = sqrtf(det);
+  o.u11 = kQScale * (sc / sd);
+  o.u12 = -kQScale * (b / (sc * sd));
+  o.u22 = kQScale / sc;
+  o.a = a;
+  o.c = c;
+  // support f >= alpha_min  <=>  d^T Sigma_2D^-1 d <= 2 ln(alpha / alpha_min); its x extent is
+  // sqrt(that * a), its y extent sqrt(that * c).  A small margin keeps the box a superset.
+  if (!(P.alpha >= prm.alpha_min)) return false;
+  const float pthr = 2.f * logf(P.alpha / prm.alpha_min);
+  const float rx = sqrtf(pthr * a) * 1.0001f + 1e-3f;
+  const float ry = sqrtf(pthr * c) * 1.0001f + 1e-3f;
+  const float mx = o.mux.hi, my = o.muy.hi;
+  float fx0 = ceilf(mx - rx), fx1 = floorf(mx + rx), fy0 = ceilf(my - ry), fy1 = floorf(my + ry);
+  fx0 = fmaxf(fx0, 0.f);
+  fy0 = fmaxf(fy0, 0.f);
+  fx1 = fminf(fx1, (float)(cam.W - 1));
+  fy1 = fminf(fy1, (float)(cam.H - 1));
+  if (!(fx0 <= fx1) || !(fy0 <= fy1)) return false;
+  o.x0 = (int)fx0; o.x1 = (int)fx1; o.y0 = (int)fy0; o.y1 = (int)fy1;
+  o.n[0] = A[kmin];
+  o.n[1] = A[3 + kmin];
+  o.n[2] = A[6 + kmin];
+  o.d0 = Xf * o.n[0] + Yf * o.n[1] + Zf * o.n[2];
+  return true;
+}
+
+// Footprint value f = min(f_max, alpha 2^-q) at pixel (px, py); q = |U d|^2, d = u - mu.
+// The forward, the backward and the mask all use this expression, so their decisions agree.
+__device__ __forceinline__ float footprint(float px, float py, float mxh, float myh, float mxl, float myl, float u11,
+                                           float u12, float u22, float alpha, float f_max, float &dx, float &dy,
+                                           float &t1, float &t2, float &g) {
+  dx = (px - mxh) - mxl;
+  dy = (py - myh) - myl;
+  t1 = fmaf(u11, dx, u12 * dy);
+  t2 = u22 * dy;
+  const float q = fmaf(t1, t1, t2 * t2);
+  g = ex2_approx(-q);
+  return fminf(f_max, alpha * g);
+}
+
+}  // namespace rtg

@@ -1,0 +1,202 @@
+// Internal definitions shared by the rasterizer's CUDA translation units.
+//
+// Data layout in HBM (all owned by the context workspace):
+//   rec_hot  [F][N][HOT4] float4  per-(frame, Gaussian) compositing record:
+//            {mu_x_hi, mu_y_hi, mu_x_lo, mu_y_lo}  double-float pixel-space centre
+//            {u11, u12, u22, alpha}                Cholesky factor of Sigma_2D^-1 (scaled)
+//            {colour 0..3}, {colour 4..7}          C = 3 uses one colour vector, C = 8 two
+//   rec_cold [F][N][2] float4     {n_c.x, n_c.y, n_c.z, d0 = p_c . n_c},
+//                                 {z_c, rank (int bits), rect lo (tx0|ty0<<16), rect hi}
+//   ntiles   [F][N] uint32        masked tiles touched (0 = culled or off-mask)
+//   keys     [pairs] uint64       (float bits of z_c) << 32 | Gaussian index, bucketed by tile
+//   sorted   [pairs] uint32       Gaussian index, each tile's bucket in front-to-back order
+//   px_*     [F][H][W]            per-pixel state saved by the forward for the backward
+//   grad2d   [F][N][G2] float     per-(frame, unstable Gaussian) screen-space gradients
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rtg.h"
+
+namespace rtg {
+
+constexpr int kTile = RTG_TILE;              // 16 x 16 pixel tiles
+constexpr int kTilePix = kTile * kTile;      // 256 pixels = 256 threads per tile CTA
+constexpr int kMaxFrames = RTG_MAX_FRAMES;
+// q = t1^2 + t2^2 with t = U d and U scaled by sqrt(log2(e) / 2), so exp(-p/2) = 2^-q
+constexpr float kQScale = 0.84932180028801904272f;   // sqrt(0.5 * log2(e))
+constexpr float kLn2 = 0.69314718055994530942f;
+constexpr float kQScale2 = 0.72134752044448170368f;  // kQScale^2 = 0.5 * log2(e)
+
+// Counter slots in Work::counters (uint64).
+enum Counter {
+  kPairs = 0,
+  kFragments = 1,
+  kVisible = 2,
+  kMaskedPix = 3,
+  kNumUnstable = 4,
+  kMaxTilePairs = 5,
+  kSkip = 6,  // non-zero: pairs overflowed, downstream kernels skip
+  kNumCounters = 8
+};
+
+struct DevCam {
+  float fx, fy, cx, cy;
+  int W, H;
+  float R[9];  // camera-to-world, row-major
+  float t[3];
+  float lim_x, lim_y;  // guard band on |X/Z| and |Y/Z|
+  int tiles_x, tiles_y;
+};
+
+struct Prm {
+  float near_z, alpha_min, f_max, t_eps, delta_alpha, cos_max, lowpass, guard, discard;
+};
+
+struct GaussPtrs {
+  const float *means, *scales, *quats, *opacity, *colors;
+  const uint8_t *unstable;
+  const float *u_means, *u_scales, *u_quats, *u_opacity, *u_colors;
+  int64_t n;
+  int C;
+};
+
+struct Work {
+  DevCam *cams;
+  unsigned long long *counters;
+  int32_t *rank;        // [N] compact unstable index, -1 if stable
+  int32_t *ids;         // [N] compact -> original index
+  int32_t *block_cnt;   // [ceil(N / kScanBlock)]
+  float4 *rec_hot;
+  float4 *rec_cold;
+  uint32_t *ntiles;
+  uint32_t *tile_npix;  // [F*T] masked pixels per tile
+  uint32_t *tile_count; // [F*T + 1]
+  uint32_t *tile_offset;// [F*T + 1]
+  uint32_t *tile_cursor;// [F*T]
+  unsigned long long *keys;
+  unsigned long long *keys_alt;
+  uint32_t *sorted;
+  float *px_T;
+  uint32_t *px_last;
+  int32_t *px_hit;
+  float *grad2d;
+  float *loss_part;     // [kLossBlocks * 4]
+  float *loss_scal;     // [4]: L, Lc, Ld, (unused); [4..5] gradient scales
+  uint32_t *loss_done;
+  uint32_t *status;     // host-mapped status word (device pointer)
+};
+
+// ----------------------------------------------------------------------------- sizes
+
+__host__ __device__ inline int hot4_of(int C) { return C <= 4 ? 3 : 4; }
+__host__ __device__ inline int g2_of(int C) { return C <= 5 ? 16 : 20; }  // 11 + C padded to float4
+// grad2d row: [0..1] dL/dmu, [2..4] dL/d(conic a', b', c'), [5] dL/dalpha, [6..6+C) dL/dcolour,
+// then the depth terms [6+C] dL/dd0, [7+C..9+C] dL/dn_c, [10+C] dL/dz_c.
+constexpr int kG2Mu = 0, kG2Conic = 2, kG2Alpha = 5, kG2Col = 6;
+__host__ __device__ inline int g2_d0(int C) { return 6 + C; }
+__host__ __device__ inline int g2_nc(int C) { return 7 + C; }
+__host__ __device__ inline int g2_z(int C) { return 10 + C; }
+
+// ----------------------------------------------------------------------------- double-float
+// Error-free transformations (Knuth's TwoSum, Dekker's product via FMA) and the
+// "double-float" arithmetic built on them (Dekker 1971; Hida, Li & Bailey, QD library).
+// Used to keep the world->camera transform and the pixel-space centre accurate to
+// ~2^-44 relative, so that d = u - mu is exact to FP32 rounding even at |mu| ~ 10^3 px.
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ df quick_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  float lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return quick_two_sum(s.hi, lo);
+}
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+  df p = two_prod(a.hi, b);
+  p.lo = __fmaf_rn(a.lo, b, p.lo);
+  return quick_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ df df_div(df a, df b) {
+  float q1 = __fdiv_rn(a.hi, b.hi);
+  df r = df_add(a, df_mul_f(b, -q1));
+  float q2 = __fdiv_rn(r.hi, b.hi);
+  return quick_two_sum(q1, q2);
+}
+
+// ----------------------------------------------------------------------------- small math
+
+// 2^x with the hardware approximation (relative error ~2^-22), flushing denormals.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ void quat_to_rot(float w, float x, float y, float z, float R[9]) {
+  R[0] = 1.f - 2.f * (y * y + z * z);
+  R[1] = 2.f * (x * y - w * z);
+  R[2] = 2.f * (x * z + w * y);
+  R[3] = 2.f * (x * y + w * z);
+  R[4] = 1.f - 2.f * (x * x + z * z);
+  R[5] = 2.f * (y * z - w * x);
+  R[6] = 2.f * (x * z - w * y);
+  R[7] = 2.f * (y * z + w * x);
+  R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+__device__ __forceinline__ int argmin3(float a, float b, float c) {
+  return (a <= b && a <= c) ? 0 : (b <= c ? 1 : 2);
+}
+
+// Parameters of Gaussian i, from the compact override when it is unstable and one is given.
+struct GParams {
+  float p[3], s[3], q[4], alpha;
+};
+
+__device__ __forceinline__ bool load_params(const GaussPtrs &g, const int32_t *rank, int64_t i, GParams &P) {
+  const float *pm = g.means + 3 * i, *ps = g.scales + 3 * i, *pq = g.quats + 4 * i, *po = g.opacity + i;
+  if (g.u_means != nullptr) {
+    int r = rank[i];
+    if (r >= 0) {
+      pm = g.u_means + 3 * (int64_t)r;
+      ps = g.u_scales + 3 * (int64_t)r;
+      pq = g.u_quats + 4 * (int64_t)r;
+      po = g.u_opacity + r;
+    }
+  }
+  P.p[0] = pm[0]; P.p[1] = pm[1]; P.p[2] = pm[2];
+  P.s[0] = ps[0]; P.s[1] = ps[1]; P.s[2] = ps[2];
+  P.q[0] = pq[0]; P.q[1] = pq[1]; P.q[2] = pq[2]; P.q[3] = pq[3];
+  P.alpha = *po;
+  bool ok = isfinite(P.p[0]) && isfinite(P.p[1]) && isfinite(P.p[2]) && isfinite(P.s[0]) && isfinite(P.s[1]) &&
+            isfinite(P.s[2]) && isfinite(P.q[0]) && isfinite(P.q[1]) && isfinite(P.q[2]) && isfinite(P.q[3]) &&
+            isfinite(P.alpha);
+  float qq = P.q[0] * P.q[0] + P.q[1] * P.q[1] + P.q[2] * P.q[2] + P.q[3] * P.q[3];
+  return ok && qq > 0.f;
+}
+
+__device__ __forceinline__ const float *color_ptr(const GaussPtrs &g, const int32_t *rank, int64_t i) {
+  if (g.u_colors != nullptr) {
+    int r = rank[i];
+    if (r >= 0) return g.u_colors + (int64_t)g.C * r;
+  }
+  return g.colors + (int64_t)g.C * i;
+}
+
+}  // namespace rtg

@@ -1,0 +1,119 @@
+"""The masked on-the-fly optimisation step (Section 3.2, "Gaussian optimization"; Supplement B)
+on top of the C ABI: forward over all Gaussians on the unstable pixels, L1 colour and
+depth losses, backward to the unstable Gaussians only, Adam on their compact parameters.
+
+Two front ends:
+  * ``RTGRasterize``: a torch.autograd.Function whose differentiable inputs are the
+    compact unstable parameters [Nu, .]; its backward returns their gradients.
+  * ``MaskedStep``: the whole iteration (forward, loss, backward, Adam) as five C-ABI
+    calls on preallocated buffers, with no allocation and no host synchronisation.
+"""
+
+from __future__ import annotations
+
+import dataclasses
+from typing import Optional, Sequence
+
+import torch
+
+from . import api
+from .api import AdamSettings, Context, Gaussians, RenderSettings
+
+
+@dataclasses.dataclass
+class RasterState:
+    """Non-differentiable inputs of one render: context, full arrays, cameras, mask."""
+    ctx: Context
+    g: Gaussians
+    cams: Sequence
+    mask: Optional[torch.Tensor]
+    settings: RenderSettings
+    color: torch.Tensor = None   # outputs, reused across calls; off-mask pixels keep their fill
+    depth: torch.Tensor = None
+    alpha: torch.Tensor = None
+    index_map: Optional[torch.Tensor] = None
+
+    def __post_init__(self):
+        cams = self.cams if isinstance(self.cams, (list, tuple)) else [self.cams]
+        F, H, W, C = len(cams), int(cams[0].height), int(cams[0].width), self.g.channels
+        dev = self.g.means.device
+        if self.color is None:
+            self.color = torch.zeros(F, C, H, W, device=dev)
+            self.depth = torch.full((F, H, W), -1.0, device=dev)
+            self.alpha = torch.zeros(F, H, W, device=dev)
+            self.index_map = torch.full((F, H, W), -1, dtype=torch.int32, device=dev)
+
+
+class RTGRasterize(torch.autograd.Function):
+    """(u_means, u_scales, u_quats, u_opacity, u_colors) -> (colour, depth, alpha)."""
+
+    @staticmethod
+    def forward(ctx, u_means, u_scales, u_quats, u_opacity, u_colors, state: RasterState):
+        g = dataclasses.replace(state.g, u_means=u_means.detach().contiguous(),
+                                u_scales=u_scales.detach().contiguous(), u_quats=u_quats.detach().contiguous(),
+                                u_opacity=u_opacity.detach().contiguous(), u_colors=u_colors.detach().contiguous())
+        api.render_forward(state.ctx, state.cams, g, state.mask, state.settings, state.color, state.depth,
+                           state.alpha, state.index_map)
+        ctx.state = state
+        ctx.shapes = (u_means.shape, u_scales.shape, u_quats.shape, u_opacity.shape, u_colors.shape)
+        ctx.mark_non_differentiable(state.alpha)
+        return state.color.clone(), state.depth.clone(), state.alpha.clone()
+
+    @staticmethod
+    def backward(ctx, d_color, d_depth, d_alpha):
+        st: RasterState = ctx.state
+        dev = st.color.device
+        if d_color is None:
+            d_color = torch.zeros_like(st.color)
+        if d_depth is None:
+            d_depth = torch.zeros_like(st.depth)
+        grads = [torch.empty(s, device=dev) for s in ctx.shapes]
+        api.render_backward(st.ctx, d_color.contiguous().float(), d_depth.contiguous().float(), *grads)
+        return (*grads, None)
+
+
+def rasterize(u_params: Sequence[torch.Tensor], state: RasterState):
+    return RTGRasterize.apply(*u_params, state)
+
+
+class MaskedStep:
+    """One masked optimisation iteration per ``step()`` call, on preallocated buffers."""
+
+    def __init__(self, ctx: Context, g: Gaussians, cams, mask: Optional[torch.Tensor], target_color: torch.Tensor,
+                 target_depth: torch.Tensor, settings: RenderSettings = RenderSettings(),
+                 adam: AdamSettings = AdamSettings(), w_color: float = 1.0, w_depth: float = 1.0):
+        self.ctx, self.settings, self.adam = ctx, settings, adam
+        self.cams = cams if isinstance(cams, (list, tuple)) else [cams]
+        self.mask = mask
+        self.w_color, self.w_depth = w_color, w_depth
+        self.ids, self.nu = api.unstable_index(ctx, g.unstable)
+        self.u = api.gather_unstable(self.ids, g)
+        self.g = dataclasses.replace(g, u_means=self.u[0], u_scales=self.u[1], u_quats=self.u[2],
+                                     u_opacity=self.u[3], u_colors=self.u[4])
+        self.state = RasterState(ctx, self.g, self.cams, mask, settings)
+        dev = g.means.device
+        C = g.channels
+        self.target_color, self.target_depth = target_color, target_depth
+        self.loss = torch.zeros(3, device=dev)
+        self.dL_dcolor = torch.zeros_like(self.state.color)
+        self.dL_ddepth = torch.zeros_like(self.state.depth)
+        self.grads = [torch.zeros_like(t) for t in self.u]
+        self.m = torch.zeros(self.nu, 11 + C, device=dev)
+        self.v = torch.zeros(self.nu, 11 + C, device=dev)
+        self.t = 0
+
+    def step(self, stream=None):
+        """Forward, L1 loss, backward and Adam; returns the device loss tensor (L, Lc, Ld)."""
+        s = self.state
+        api.render_forward(self.ctx, self.cams, self.g, self.mask, self.settings, s.color, s.depth, s.alpha, None,
+                           stream)
+        api.l1_loss(self.ctx, s.color, s.depth, self.target_color, self.target_depth, self.mask, self.w_color,
+                    self.w_depth, self.loss, self.dL_dcolor, self.dL_ddepth, stream)
+        api.render_backward(self.ctx, self.dL_dcolor, self.dL_ddepth, *self.grads, stream=stream)
+        self.t += 1
+        api.adam_step(self.u, self.grads, self.m, self.v, self.t, self.adam, stream)
+        return self.loss
+
+    def write_back(self, stream=None):
+        """Scatter the optimised compact parameters into the full arrays (end of a window)."""
+        api.scatter_unstable(self.ids, self.u, self.g, stream)

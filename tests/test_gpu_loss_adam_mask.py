@@ -1,0 +1,137 @@
+"""GPU L1 loss, Adam and unstable-pixel mask vs the oracle; the full MaskedStep; device-side
+capacity overflow reported without a hang."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import ctx_for, gpu_forward, rtg
+
+pytestmark = pytest.mark.gpu
+ST = oracle.Settings()
+
+
+def test_l1_loss_matches_oracle():
+    m = rtg()
+    rng = np.random.default_rng(1)
+    F, C, H, W = 2, 3, 37, 53
+    color = rng.uniform(0, 1, (F, C, H, W)).astype(np.float32)
+    depth = np.where(rng.random((F, H, W)) < 0.2, -1.0, rng.uniform(1, 5, (F, H, W))).astype(np.float32)
+    tcol = rng.uniform(0, 1, (F, C, H, W)).astype(np.float32)
+    tdep = np.where(rng.random((F, H, W)) < 0.1, 0.0, rng.uniform(1, 5, (F, H, W))).astype(np.float32)
+    mask = (rng.random((F, H, W)) < 0.6).astype(np.uint8)
+    ctx = ctx_for(10, synth.identity_camera(W, H, 50, 10, 10), channels=3)
+    t = lambda a: torch.tensor(a).cuda()  # noqa: E731
+    loss = torch.zeros(3, device="cuda")
+    dc, dd = torch.zeros(F, C, H, W, device="cuda"), torch.zeros(F, H, W, device="cuda")
+    m.l1_loss(ctx, t(color), t(depth), t(tcol), t(tdep), t(mask), 1.0, 1.0, loss, dc, dd)
+    sel = mask.astype(bool)
+    L, Lc, Ld, P, Pd = oracle.l1_loss(np.moveaxis(color, 1, -1)[sel], depth[sel], np.moveaxis(tcol, 1, -1)[sel],
+                                      tdep[sel])
+    got = loss.cpu().numpy()
+    assert got == pytest.approx([float(L), float(Lc), float(Ld)], rel=1e-5)
+    # gradient images: sign / count on the masked (and depth-valid) pixels, zero elsewhere
+    sgn = np.sign(color - tcol) * sel[:, None]
+    np.testing.assert_allclose(dc.cpu().numpy(), sgn / (P * C), rtol=1e-6)
+    vd = sel & (depth != -1) & (tdep > 0)
+    np.testing.assert_allclose(dd.cpu().numpy(), np.sign(depth - tdep) * vd / Pd, rtol=1e-6)
+
+
+def test_adam_matches_oracle_three_steps():
+    """Three Adam steps on 1,000 compact Gaussians; the oracle runs Algorithm 1 in FP64 on the
+    same gradients (scale in log space)."""
+    m = rtg()
+    rng = np.random.default_rng(2)
+    nu, C = 1000, 3
+    p = dict(means=rng.normal(size=(nu, 3)), scales=np.exp(rng.normal(-4, 0.5, (nu, 3))),
+             quats=rng.normal(size=(nu, 4)), opacity=rng.uniform(0, 1, nu), colors=rng.uniform(0, 1, (nu, 3)))
+    p = {k: v.astype(np.float32) for k, v in p.items()}
+    tp = [torch.tensor(p[k]).cuda() for k in oracle.adam.GROUPS]
+    mm = torch.zeros(nu, 11 + C, device="cuda")
+    vv = torch.zeros(nu, 11 + C, device="cuda")
+    hp = oracle.AdamHyper()
+    cur = {k: v.astype(np.float64) for k, v in p.items()}
+    om = {k: np.zeros_like(v) for k, v in cur.items()}
+    ov = {k: np.zeros_like(v) for k, v in cur.items()}
+    for step in range(1, 4):
+        gr = {k: rng.normal(size=v.shape).astype(np.float32) for k, v in p.items()}
+        m.adam_step(tp, [torch.tensor(gr[k]).cuda() for k in oracle.adam.GROUPS], mm, vv, step)
+        cur, om, ov = oracle.adam_step(cur, gr, om, ov, step, hp)
+        torch.cuda.synchronize()
+        for k, t in zip(oracle.adam.GROUPS, tp):
+            np.testing.assert_allclose(t.cpu().numpy(), cur[k], rtol=1e-5, atol=1e-6, err_msg=f"{k} step {step}")
+
+
+def test_unstable_mask_matches_oracle():
+    m = rtg()
+    scene, layout = synth.room_scene(2020, 20000)
+    cam = next(synth.room_camera_candidates(2021, layout, 120, 90, 110.0))
+    scene.unstable = synth.flag_blobs(scene, [cam], 4000, 3, seed=5)
+    for frac in (0.0, 0.5):
+        st = oracle.Settings(tile_discard_frac=frac)
+        ref, border = oracle.unstable_mask(scene, cam, st)
+        ctx = ctx_for(scene.n, cam)
+        out = torch.zeros(1, cam.height, cam.width, dtype=torch.uint8, device="cuda")
+        m.unstable_mask(ctx, cam, m.Gaussians.from_scene(scene), m.RenderSettings(tile_discard_frac=frac), out)
+        got = out[0].cpu().numpy().astype(bool)
+        assert border.mean() < 0.01
+        np.testing.assert_array_equal(got[~border], ref[~border])
+        assert 0.05 < ref.mean() < 0.95
+
+
+def test_masked_step_reduces_loss_and_keeps_stable_fixed():
+    m = rtg()
+    scene, layout = synth.room_scene(2030, 20000)
+    cam = next(synth.room_camera_candidates(2031, layout, 128, 96, 120.0))
+    scene.unstable = synth.flag_blobs(scene, [cam], 4000, 3, seed=6)
+    target = synth.jitter_scene(scene, 7)
+    tref = gpu_forward(target, cam)  # a fixed target input for the loss (not a compared value)
+    ctx = ctx_for(scene.n, cam)
+    g = m.Gaussians.from_scene(scene)
+    mask = torch.zeros(1, 96, 128, dtype=torch.uint8, device="cuda")
+    m.unstable_mask(ctx, cam, g, m.RenderSettings(), mask)
+    tc = torch.tensor(tref["color"]).cuda()
+    td = torch.tensor(np.where(tref["depth"] > 0, tref["depth"], 0)).cuda()
+    stable_before = g.means[g.unstable == 0].clone()
+    step = m.MaskedStep(ctx, g, [cam], mask, tc, td)
+    losses = [float(step.step()[0]) for _ in range(30)]
+    assert losses[-1] < losses[0]
+    step.write_back()
+    torch.cuda.synchronize()
+    assert torch.equal(g.means[g.unstable == 0], stable_before)
+    assert m.get_status(ctx) == 0
+
+
+def test_pair_overflow_is_reported_and_outputs_untouched():
+    m = rtg()
+    scene, cam = synth.scatter_scene(1000, n=2000)
+    ctx = ctx_for(scene.n, cam, max_pairs=100)
+    g = m.Gaussians.from_scene(scene)
+    color = torch.full((1, 3, cam.height, cam.width), 7.0, device="cuda")
+    depth = torch.full((1, cam.height, cam.width), 7.0, device="cuda")
+    alpha = torch.full((1, cam.height, cam.width), 7.0, device="cuda")
+    m.render_forward(ctx, cam, g, None, m.RenderSettings(), color, depth, alpha)
+    torch.cuda.synchronize()
+    assert m.get_status(ctx) == m._lib.RTG_ERR_WORKSPACE
+    assert (color == 7.0).all() and (depth == 7.0).all()
+    m.reset_status(ctx)
+    assert m.get_status(ctx) == 0
+
+
+def test_argument_errors_raise():
+    m = rtg()
+    scene, cam = synth.scatter_scene(1000, n=100)
+    ctx = ctx_for(scene.n, cam)
+    g = m.Gaussians.from_scene(scene)
+    out = [torch.zeros(1, 3, 120, 160, device="cuda"), torch.zeros(1, 120, 160, device="cuda"),
+           torch.zeros(1, 120, 160, device="cuda")]
+    big = synth.identity_camera(4000, 120, 150, 79.5, 59.5)
+    with pytest.raises(m.RTGError):
+        m.render_forward(ctx, big, g, None, m.RenderSettings(), *out)
+    with pytest.raises(m.RTGError):
+        m.render_forward(ctx, cam, g, None, m.RenderSettings(alpha_min=0.0), *out)
+    fresh = ctx_for(scene.n, cam)
+    with pytest.raises(m.RTGError):  # backward before any forward
+        m.render_backward(fresh, out[0], out[1], *[torch.zeros(1, device="cuda")] * 5)
