@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""Benchmark: the masked on-the-fly optimisation step of RTG-SLAM on one B300.
+
+Workload (the masked 640x480 step): a synthetic 6x5x3 m box room with 20 boxes covered by
+1,000,000 flattened Gaussians (85% opaque, 15% transparent), 200,000 of them unstable in
+3 spatial blobs; a 640x480 camera (f = 600) whose unstable-pixel mask (with the 16x16
+tile rule) covers 25-40% of the frame; an L1 colour + depth target rendered from a
+jittered copy of the scene.  One step is one pass of the whole hot path: unstable mask,
+forward render, L1 losses, backward, Adam on the unstable subset.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead (bounded
+pixel samples per step, extrapolated to the masked pixel count).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "masked fwd+bwd iterations/sec and fragments/sec at 640×480; % HBM roofline"
+WORKLOAD = dict(name="masked-step room 1M Gaussians (20% unstable, 3 blobs) 640x480, tile rule 0.5",
+                seed=3000, n=1_000_000, n_unstable=200_000, blobs=3, width=640, height=480, f=600.0,
+                coverage=(0.25, 0.40))
+C = 3
+P_IN, R_REC, Q_PIX, G2 = 44 + 4 * C, 36 + 4 * C, 4 * C + 16, 4 * (11 + C)  # bytes per unit
+KERNELS_PER_STEP = 16  # mask 3, forward 8, loss 2, backward 2, adam 1
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--candidate", type=int, default=-1, help="camera candidate index (-1: search)")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- workload
+
+def scene_and_candidates():
+    scene, layout = synth.room_scene(WORKLOAD["seed"], WORKLOAD["n"])
+    cams = synth.room_camera_candidates(WORKLOAD["seed"] + 1, layout, WORKLOAD["width"], WORKLOAD["height"],
+                                        WORKLOAD["f"])
+    return scene, cams
+
+
+def flags_for(scene, cam, k):
+    return synth.flag_blobs(scene, [cam], WORKLOAD["n_unstable"], WORKLOAD["blobs"], seed=WORKLOAD["seed"] + 100 + k)
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "_fallback": True}
+
+
+class ClockSampler:
+    """Polls NVML (read-only) for SM clock and throttle reasons while running."""
+
+    def __init__(self, index):
+        self.index, self.samples, self._stop = index, [], threading.Event()
+        self.max_mhz, self.ok = None, False
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            self.nv = pynvml
+            self.h = pynvml.nvmlDeviceGetHandleByIndex(index)
+            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
+            self.ok = True
+        except Exception:
+            self.ok = False
+
+    def _run(self):
+        nv = self.nv
+        while not self._stop.is_set():
+            try:
+                self.samples.append((nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM),
+                                     nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)))
+            except Exception:
+                pass
+            time.sleep(0.002)
+
+    def __enter__(self):
+        if self.ok:
+            self.t = threading.Thread(target=self._run, daemon=True)
+            self.t.start()
+        return self
+
+    def __exit__(self, *a):
+        if self.ok:
+            self._stop.set()
+            self.t.join()
+
+    def summary(self):
+        if not self.ok or not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unavailable"], "samples": 0}
+        nv = self.nv
+        names = {"hw_slowdown": getattr(nv, "nvmlClocksEventReasonHwSlowdown", 0x8),
+                 "hw_thermal_slowdown": getattr(nv, "nvmlClocksEventReasonHwThermalSlowdown", 0x40),
+                 "sw_thermal_slowdown": getattr(nv, "nvmlClocksEventReasonSwThermalSlowdown", 0x20),
+                 "sw_power_cap": getattr(nv, "nvmlClocksEventReasonSwPowerCap", 0x4)}
+        reasons = sorted({k for _, r in self.samples for k, bit in names.items() if r & bit})
+        return {"sm_mhz": float(np.median([s for s, _ in self.samples])), "sm_max_mhz": self.max_mhz,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle timing
+
+def oracle_rate(scene, cam, masked_pixels, n_masked, targets, seconds_budget=25.0):
+    """Iterations/s of the FP64 oracle (forward + L1 loss + autograd gradient) as it stands,
+    from two bounded pixel samples: time = fixed (projection) + n_masked * per-pixel."""
+    import torch
+    import oracle
+    st = oracle.Settings()
+    tc, td = targets
+    rng = np.random.default_rng(0)
+
+    def timed(k):
+        sel = rng.choice(len(masked_pixels), size=k, replace=False)
+        pix = masked_pixels[sel]
+        t0 = time.perf_counter()
+        oracle.loss_and_grads(scene, cam, st, pix, tc[sel], td[sel])
+        return time.perf_counter() - t0
+
+    s1, s2 = 4, 12
+    t1 = timed(s1)
+    t2 = timed(s2)
+    per_px = max((t2 - t1) / (s2 - s1), 1e-9)
+    fixed = max(t1 - s1 * per_px, 0.0)
+    it_s = fixed + n_masked * per_px
+    return dict(value=1.0 / it_s, unit="iter/s", cores=int(torch.get_num_threads()), kind="oracle",
+                sample=f"FP64 oracle forward+L1+autograd on {s1} and {s2} random masked pixels of the same "
+                       f"workload ({t1 + t2:.1f} s CPU); iteration time = fixed {fixed:.2f} s + "
+                       f"{n_masked} masked px x {per_px * 1e3:.1f} ms (extrapolated)")
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_ours(args):
+    import torch
+    import paper_2404_19706_b300 as rtg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    scene, cams = scene_and_candidates()
+    settings = rtg.RenderSettings()
+    ctx = rtg.Context(max_gaussians=scene.n, max_width=WORKLOAD["width"], max_height=WORKLOAD["height"],
+                      max_pairs=24 * scene.n)
+    H, W = WORKLOAD["height"], WORKLOAD["width"]
+    mask = torch.zeros(1, H, W, dtype=torch.uint8, device=dev)
+    chosen = None
+    for k in range(200):
+        cam = next(cams)
+        if args.candidate >= 0 and k != args.candidate:
+            continue
+        scene.unstable = flags_for(scene, cam, k)
+        g = rtg.Gaussians.from_scene(scene, device=dev)
+        rtg.unstable_mask(ctx, cam, g, settings, mask)
+        cov = float(mask.float().mean())
+        if WORKLOAD["coverage"][0] <= cov <= WORKLOAD["coverage"][1] or args.candidate >= 0:
+            chosen = (k, cam, cov)
+            break
+    assert chosen is not None, "no camera candidate with coverage in range"
+    k_cam, cam, coverage = chosen
+
+    # target: jittered copy rendered full-frame (a fixed input of the loss)
+    target = synth.jitter_scene(scene, WORKLOAD["seed"] + 7)
+    gt = rtg.Gaussians.from_scene(target, device=dev)
+    tcol = torch.zeros(1, C, H, W, device=dev)
+    tdep = torch.full((1, H, W), -1.0, device=dev)
+    talp = torch.zeros(1, H, W, device=dev)
+    rtg.render_forward(ctx, cam, gt, None, settings, tcol, tdep, talp)
+    tdep = torch.where(tdep > 0, tdep, torch.zeros_like(tdep))
+    del gt
+
+    g = rtg.Gaussians.from_scene(scene, device=dev)
+    step = rtg.MaskedStep(ctx, g, [cam], mask, tcol, tdep, settings)
+    stream = torch.cuda.current_stream()
+
+    def one_step():
+        rtg.unstable_mask(ctx, [cam], step.g, settings, mask)
+        return step.step()
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 126 MB L2
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    stats = rtg.get_stats(ctx)
+    assert stats["status"] == 0, stats
+
+    # ---- timed region: device time of each step, L2 flushed before each (not timed)
+    rtg.profile_enable(ctx, True)
+    rtg.profile_read(ctx)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    adam_ev = []
+    orig_adam = rtg.api.adam_step
+
+    def adam_timed(*a, **kw):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        orig_adam(*a, **kw)
+        e1.record(stream)
+        adam_ev.append((e0, e1))
+
+    import paper_2404_19706_b300.optim as optim_mod
+    optim_mod.api.adam_step = adam_timed
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        wall0 = time.perf_counter()
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            one_step()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    optim_mod.api.adam_step = orig_adam
+    if dist is not None:
+        dist.barrier()
+    ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    prof = rtg.profile_read(ctx)
+    rtg.profile_enable(ctx, False)
+    prof["adam"] = (len(adam_ev), sum(a.elapsed_time(b) for a, b in adam_ev))
+    stats = rtg.get_stats(ctx)
+    assert stats["status"] == 0, stats
+    ms_step = float(np.mean(ms))
+    if dist is not None:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+
+    # ---- algorithmic bytes (per launch) of each kernel kind, from the step's own counters
+    N, V, K, P, Nu = scene.n, stats["visible"], stats["pairs"], stats["masked_pixels"], stats["n_unstable"]
+    FT = ((W + 15) // 16) * ((H + 15) // 16)
+    alg = {
+        "unstable_mask": Nu * P_IN + H * W,
+        "tile_mask": H * W,
+        "unstable_index": N * 9,
+        "project": N * P_IN + V * R_REC,
+        "scan_tiles": FT * 16,
+        "emit": K * 12,
+        "sort_tiles": K * 24,
+        "forward": K * R_REC + P * Q_PIX,
+        "l1_loss": 3 * P * (4 * C + 4),
+        "backward": K * R_REC + P * (Q_PIX + 4 * C + 4) + Nu * G2,
+        "project_backward": Nu * (G2 + 2 * P_IN),
+        "adam": Nu * P_IN * 7,
+    }
+    per_launch = {k: (v[1] / v[0] if v[0] else 0.0) for k, v in prof.items()}
+    single = ["project", "emit", "sort_tiles", "forward", "backward", "project_backward", "adam", "scan_tiles",
+              "tile_mask"]
+    dom = max(single, key=lambda k: per_launch.get(k, 0.0))
+    pk = peaks()
+    achieved = alg[dom] / (per_launch[dom] * 1e-3) / 1e9
+    b_step = sum(alg.values())
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": None,
+                "peak_source": "fallback" if pk.get("_fallback") else "measured (MEASURED_PEAKS.json hbm_gbs)",
+                "alg_bytes_per_launch": int(alg[dom]), "ms_per_launch": round(per_launch[dom], 5)}
+
+    # ---- end to end through the public API with host buffers
+    hc = torch.empty_like(tcol, device="cpu").pin_memory()
+    hd = torch.empty_like(tdep, device="cpu").pin_memory()
+    hc.copy_(tcol.cpu())
+    hd.copy_(tdep.cpu())
+    hloss = torch.empty(3, pin_memory=True)
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step.target_color.copy_(hc, non_blocking=True)
+        step.target_depth.copy_(hd, non_blocking=True)
+        loss = one_step()
+        hloss.copy_(loss, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        if i >= args.warmup:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_step = float(np.mean(e2e_ms))
+    if dist is not None:
+        t = torch.tensor([e2e_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_step = float(t.item())
+
+    result = None
+    if rank == 0:
+        value = world * 1e3 / ms_step
+        clk = clocks.summary()
+        result = {
+            "metric": METRIC, "value": round(value, 2), "unit": "iter/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "gaussians": N, "unstable": Nu, "width": W, "height": H,
+                       "camera_candidate": k_cam, "mask_coverage": round(coverage, 4), "masked_pixels": P,
+                       "pairs": K, "visible": V, "fragments_per_step": stats["fragments"],
+                       "fragments_per_sec": round(world * stats["fragments"] * 1e3 / ms_step, 1),
+                       "alg_bytes_per_step": int(b_step),
+                       "step_hbm_roofline_frac": round(b_step / (ms_step * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
+                       "l2": "256 MB buffer written before every step, outside the timed spans",
+                       "wall_s_timed_region": round(wall, 3),
+                       "kernel_ms_per_launch": {k: round(v, 5) for k, v in per_launch.items()},
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "e2e": {"value": round(world * 1e3 / e2e_step, 2), "unit": "iter/s",
+                    "h2d_bytes_per_step": int(hc.numel() * 4 + hd.numel() * 4), "d2h_bytes_per_step": 12},
+            "gpu_launches": KERNELS_PER_STEP * args.steps,
+            "clocks": clk,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            result["cpu_baseline"] = cpu_baseline_from_gpu(scene, cam, mask, tcol, tdep, P)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    ctx.close()
+    return result
+
+
+def cpu_baseline_from_gpu(scene, cam, mask, tcol, tdep, n_masked):
+    m = mask[0].cpu().numpy().astype(bool)
+    ys, xs = np.nonzero(m)
+    pix = np.stack([xs, ys], 1)
+    tc = tcol[0].cpu().numpy()[:, ys, xs].T
+    td = tdep[0].cpu().numpy()[ys, xs]
+    return oracle_rate(scene, cam, pix, n_masked, (tc, td))
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    """The FP64 CPU oracle on the same workload: each step times the oracle on a bounded
+    random sample of masked pixels and extrapolates to the full masked pixel count."""
+    import torch
+    import oracle
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    st = oracle.Settings()
+    scene, cams = scene_and_candidates()
+    k_cam = args.candidate if args.candidate >= 0 else DEFAULT_CANDIDATE
+    for k in range(k_cam + 1):
+        cam = next(cams)
+    scene.unstable = flags_for(scene, cam, k_cam)
+    rng = np.random.default_rng(1)
+    # masked pixels: covered by an unstable Gaussian (oracle render of the unstable subset)
+    cand = np.stack([rng.integers(0, cam.width, 48), rng.integers(0, cam.height, 48)], 1)
+    unst = scene.subset(np.flatnonzero(scene.unstable))
+    cov = oracle.render(unst, cam, st, pixels=cand, need_borderline=False).alpha.numpy() > 0
+    pix = cand[cov]
+    n_masked = int(round(cov.mean() * cam.width * cam.height))
+    tc = rng.uniform(0, 1, (len(pix), 3))
+    td = rng.uniform(1, 5, len(pix))
+    t0 = time.perf_counter()
+    oracle.project(*[torch.as_tensor(np.asarray(getattr(scene, k), np.float64)) for k in
+                     ("means", "scales", "quats", "opacity", "colors")], cam, st)
+    fixed = time.perf_counter() - t0
+    S = 3
+    times = []
+    for i in range(args.warmup + args.steps):
+        sel = rng.choice(len(pix), size=min(S, len(pix)), replace=False)
+        t0 = time.perf_counter()
+        oracle.loss_and_grads(scene, cam, st, pix[sel], tc[sel], td[sel])
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(fixed + max(dt - fixed, 0.0) * n_masked / len(sel))
+    ms = float(np.mean(times)) * 1e3
+    value = 1e3 / ms
+    cores = int(torch.get_num_threads())
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "camera_candidate": k_cam, "masked_pixels_est": n_masked},
+            "cpu_baseline": {"value": value, "unit": "iter/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step: FP64 oracle on {S} random masked pixels, extrapolated to "
+                                       f"{n_masked} masked pixels plus a {fixed:.2f} s projection"},
+            "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+DEFAULT_CANDIDATE = 0
+
+
+def main():
+    args = parse()
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -189,6 +189,17 @@ rtg_status rtg_reset_status(rtg_ctx *ctx);
 /* Human-readable message of the last error on this context (never NULL). */
 const char *rtg_last_error(rtg_ctx *ctx);
 
+/* Tracing (per-kernel device time).  While enabled (off by default), every kernel
+ * launcher of this context's entry points is bracketed by CUDA events on the stream it
+ * runs on; do not enable it while capturing a CUDA graph.  rtg_profile_read waits for
+ * the recorded events, then fills launches[k] and total_ms[k] for each kernel kind k
+ * (names from rtg_profile_kind_name, count from rtg_profile_kinds) since the previous
+ * read, and clears the record list.  Arrays are HOST, n_kinds >= rtg_profile_kinds(). */
+rtg_status rtg_profile_enable(rtg_ctx *ctx, int32_t on);
+int32_t rtg_profile_kinds(void);
+const char *rtg_profile_kind_name(int32_t kind);
+rtg_status rtg_profile_read(rtg_ctx *ctx, int64_t *launches, double *total_ms, int32_t n_kinds);
+
 /* Binning introspection of the last forward (for exactness tests): tile_offsets
  * [F*T+1] (uint32, T = ceil(W/16)*ceil(H/16) tiles per frame, frame-major, row-major
  * tiles), sorted_ids [pairs] (uint32 Gaussian index per list entry, each tile's list

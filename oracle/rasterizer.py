@@ -397,7 +397,8 @@ def loss_and_grads(scene, cam, st: Settings, pixels, target_color, target_depth,
     tc = torch.as_tensor(np.asarray(target_color), dtype=DT)
     td = torch.as_tensor(np.asarray(target_depth), dtype=DT)
     L, Lc, Ld, P, Pd = l1_loss(out["color"], out["depth"], tc, td, w_c, w_d)
-    L.backward()
+    if L.requires_grad:  # otherwise no unstable Gaussian reaches these pixels: zero gradients
+        L.backward()
     sel = torch.nonzero(unstable).flatten()
     grads = {name: (leaf.grad if leaf.grad is not None else torch.zeros_like(leaf))[sel].numpy()
              for name, leaf in zip(("means", "scales", "quats", "opacity", "colors"), leaves)}

@@ -23,6 +23,8 @@ from .api import (  # noqa: E402,F401
     l1_loss,
     last_error,
     make_camera,
+    profile_enable,
+    profile_read,
     render_backward,
     render_forward,
     reset_status,

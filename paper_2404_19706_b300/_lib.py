@@ -77,6 +77,10 @@ SIGNATURES = [
     ("rtg_get_status", c_int32, [c_void_p]),
     ("rtg_reset_status", c_int32, [c_void_p]),
     ("rtg_last_error", c_char_p, [c_void_p]),
+    ("rtg_profile_enable", c_int32, [c_void_p, c_int32]),
+    ("rtg_profile_kinds", c_int32, []),
+    ("rtg_profile_kind_name", c_char_p, [c_int32]),
+    ("rtg_profile_read", c_int32, [c_void_p, POINTER(c_int64), POINTER(ctypes.c_double), c_int32]),
     ("rtg_debug_binning", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
 ]
 

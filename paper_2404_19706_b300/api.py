@@ -347,3 +347,18 @@ def debug_binning(ctx: Context, frames: int, width: int, height: int, n: int, st
     u32 = lambda t: t.cpu().numpy().view(np.uint32)  # noqa: E731
     return dict(tile_offsets=u32(offs), sorted_ids=u32(ids[:stats["pairs"]]), rect=rect[:frames * n].cpu().numpy(),
                 zbits=u32(zb[:frames * n]), pairs=stats["pairs"])
+
+
+def profile_enable(ctx: Context, on: bool = True):
+    """Per-kernel device timing (CUDA events around each kernel launcher of the context)."""
+    _check(_lib.load().rtg_profile_enable(ctx.ptr, 1 if on else 0), "rtg_profile_enable", ctx.ptr)
+
+
+def profile_read(ctx: Context) -> dict:
+    """{kernel kind: (launches, total milliseconds)} since the last read (synchronises)."""
+    lib = _lib.load()
+    k = int(lib.rtg_profile_kinds())
+    launches = (ctypes.c_int64 * k)()
+    ms = (ctypes.c_double * k)()
+    _check(lib.rtg_profile_read(ctx.ptr, launches, ms, k), "rtg_profile_read", ctx.ptr)
+    return {lib.rtg_profile_kind_name(i).decode(): (int(launches[i]), float(ms[i])) for i in range(k)}

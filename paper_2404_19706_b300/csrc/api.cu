@@ -25,7 +25,57 @@ struct rtg_ctx {
   int F, W, H, T, C;
   const uint8_t *mask;
   cudaStream_t last_stream;
+  // tracing: (start, end) event pairs of the kernels launched while profiling is on
+  bool prof;
+  struct ProfRec *recs;
+  int nrec, caprec;
 };
+
+// Kernel kinds reported by the tracing interface (one launcher each).
+enum ProfKind {
+  kPTileMask, kPUnstableIndex, kPProject, kPScanTiles, kPEmit, kPSortTiles, kPForward, kPL1Loss, kPBackward,
+  kPProjectBackward, kPUnstableMask, kPNumKinds
+};
+static const char *kProfNames[kPNumKinds] = {"tile_mask", "unstable_index", "project", "scan_tiles",
+                                             "emit", "sort_tiles", "forward", "l1_loss",
+                                             "backward", "project_backward", "unstable_mask"};
+constexpr int kProfMaxRecords = 1 << 16;
+
+struct ProfRec {
+  cudaEvent_t a, b;
+  int kind;
+};
+
+namespace {
+// Records the launches between construction and destruction under `kind` when the
+// context's tracing is on; no-op otherwise.
+struct ProfScope {
+  rtg_ctx *c;
+  int idx;
+  cudaStream_t s;
+  ProfScope(rtg_ctx *ctx, int kind, cudaStream_t st) : c(ctx), idx(-1), s(st) {
+    if (c == nullptr || !c->prof) return;
+    if (c->nrec == c->caprec) {
+      if (c->caprec >= kProfMaxRecords) return;
+      const int nc = c->caprec ? 2 * c->caprec : 256;
+      ProfRec *r = (ProfRec *)realloc(c->recs, sizeof(ProfRec) * nc);
+      if (r == nullptr) return;
+      for (int k = c->caprec; k < nc; ++k) {
+        cudaEventCreate(&r[k].a);
+        cudaEventCreate(&r[k].b);
+      }
+      c->recs = r;
+      c->caprec = nc;
+    }
+    idx = c->nrec++;
+    c->recs[idx].kind = kind;
+    cudaEventRecord(c->recs[idx].a, s);
+  }
+  ~ProfScope() {
+    if (idx >= 0) cudaEventRecord(c->recs[idx].b, s);
+  }
+};
+}  // namespace
 
 namespace {
 
@@ -164,7 +214,10 @@ rtg_status make_prm(rtg_ctx *ctx, const rtg_render_params *p, Prm &o) {
 // rank[i] / ids[k] of the unstable subset, and its count in counters[kNumUnstable]
 rtg_status rank_pass(rtg_ctx *ctx, const uint8_t *unstable, int64_t n, int32_t *rank, int32_t *ids,
                      unsigned long long *nu_counter, int64_t *nu_out, cudaStream_t s) {
-  launch_rank(unstable, n, ctx->w.block_cnt, rank, ids, nu_counter, nu_out, s);
+  {
+    ProfScope ps(ctx, kPUnstableIndex, s);
+    launch_rank(unstable, n, ctx->w.block_cnt, rank, ids, nu_counter, nu_out, s);
+  }
   return check_launch(ctx, "unstable index");
 }
 
@@ -260,9 +313,50 @@ rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap) {
 rtg_status rtg_destroy(rtg_ctx *ctx) {
   if (ctx == nullptr) return RTG_OK;
   cudaDeviceSynchronize();
+  for (int k = 0; k < ctx->caprec; ++k) {
+    cudaEventDestroy(ctx->recs[k].a);
+    cudaEventDestroy(ctx->recs[k].b);
+  }
+  free(ctx->recs);
   cudaFree(ctx->slab);
   cudaFreeHost(ctx->status_host);
   free(ctx);
+  return RTG_OK;
+}
+
+rtg_status rtg_profile_enable(rtg_ctx *ctx, int32_t on) {
+  if (ctx == nullptr) return RTG_ERR_ARG;
+  ctx->prof = on != 0;
+  return RTG_OK;
+}
+
+int32_t rtg_profile_kinds(void) { return kPNumKinds; }
+
+const char *rtg_profile_kind_name(int32_t kind) {
+  return (kind >= 0 && kind < kPNumKinds) ? kProfNames[kind] : "";
+}
+
+rtg_status rtg_profile_read(rtg_ctx *ctx, int64_t *launches, double *total_ms, int32_t n_kinds) {
+  if (ctx == nullptr || launches == nullptr || total_ms == nullptr || n_kinds < kPNumKinds)
+    return RTG_ERR_ARG;
+  for (int k = 0; k < kPNumKinds; ++k) {
+    launches[k] = 0;
+    total_ms[k] = 0.0;
+  }
+  for (int r = 0; r < ctx->nrec; ++r) {
+    if (cudaEventSynchronize(ctx->recs[r].b) != cudaSuccess) {
+      cudaError_t e = cudaGetLastError();
+      return fail(ctx, RTG_ERR_CUDA, "profile_read: %s", cudaGetErrorString(e));
+    }
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->recs[r].a, ctx->recs[r].b) == cudaSuccess) {
+      launches[ctx->recs[r].kind] += 1;
+      total_ms[ctx->recs[r].kind] += ms;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  ctx->nrec = 0;
   return RTG_OK;
 }
 
@@ -297,13 +391,31 @@ rtg_status rtg_render_forward(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, c
   const int FT = F * T;
   const int64_t n = gp.n;
   Work &w = ctx->w;
-  launch_tile_mask(fs, w, mask, T, s);
+  {
+    ProfScope ps(ctx, kPTileMask, s);
+    launch_tile_mask(fs, w, mask, T, s);
+  }
   if ((st = rank_pass(ctx, gp.unstable, n, w.rank, w.ids, w.counters, nullptr, s)) != RTG_OK) return st;
-  launch_project(gp, w, P, F, T, s);
-  launch_scan_tiles(w, FT, ctx->cap.max_pairs, s);
-  launch_emit(w, n, F, T, s);
-  launch_sort_tiles(w, FT, s);
-  launch_forward(gp.C, w, P, n, F, T, mask, color, depth, alpha, index_map, s);
+  {
+    ProfScope ps(ctx, kPProject, s);
+    launch_project(gp, w, P, F, T, s);
+  }
+  {
+    ProfScope ps(ctx, kPScanTiles, s);
+    launch_scan_tiles(w, FT, ctx->cap.max_pairs, s);
+  }
+  {
+    ProfScope ps(ctx, kPEmit, s);
+    launch_emit(w, n, F, T, s);
+  }
+  {
+    ProfScope ps(ctx, kPSortTiles, s);
+    launch_sort_tiles(w, FT, s);
+  }
+  {
+    ProfScope ps(ctx, kPForward, s);
+    launch_forward(gp.C, w, P, n, F, T, mask, color, depth, alpha, index_map, s);
+  }
   if ((st = check_launch(ctx, "render_forward")) != RTG_OK) return st;
   ctx->has_fwd = true;
   ctx->g = gp;
@@ -329,8 +441,14 @@ rtg_status rtg_render_backward(rtg_ctx *ctx, const float *dL_dcolor, const float
   const int FT = ctx->F * ctx->T;
   const int64_t n = ctx->g.n;
   (void)FT;
-  launch_backward(ctx->C, ctx->w, ctx->prm, n, ctx->F, ctx->T, ctx->mask, dL_dcolor, dL_ddepth, s);
-  launch_project_backward(ctx->g, ctx->w, ctx->prm, ctx->F, g_means, g_scales, g_quats, g_opacity, g_colors, s);
+  {
+    ProfScope ps(ctx, kPBackward, s);
+    launch_backward(ctx->C, ctx->w, ctx->prm, n, ctx->F, ctx->T, ctx->mask, dL_dcolor, dL_ddepth, s);
+  }
+  {
+    ProfScope ps(ctx, kPProjectBackward, s);
+    launch_project_backward(ctx->g, ctx->w, ctx->prm, ctx->F, g_means, g_scales, g_quats, g_opacity, g_colors, s);
+  }
   ctx->last_stream = s;
   return check_launch(ctx, "render_backward");
 }
@@ -344,6 +462,7 @@ rtg_status rtg_l1_loss(rtg_ctx *ctx, int32_t F, int32_t C, int32_t H, int32_t W,
   if (!color || !depth || !target_color || !target_depth || !loss_out || !dL_dcolor || !dL_ddepth)
     return fail(ctx, RTG_ERR_ARG, "l1_loss: NULL pointer");
   cudaStream_t s = (cudaStream_t)stream;
+  ProfScope ps(ctx, kPL1Loss, s);
   launch_l1_loss(ctx->w, F, C, H, W, color, depth, target_color, target_depth, mask, w_color, w_depth, loss_out,
                  dL_dcolor, dL_ddepth, s);
   ctx->last_stream = s;
@@ -422,6 +541,7 @@ rtg_status rtg_unstable_mask(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, co
   const int T = fs.cam[0].tiles_x * fs.cam[0].tiles_y;
   const size_t npx = (size_t)F * fs.cam[0].W * fs.cam[0].H;
   ctx->has_fwd = false;  // the mask pass reuses the forward's workspace
+  ProfScope ps(ctx, kPUnstableMask, s);
   cudaMemsetAsync(mask, 0, npx, s);
   launch_tile_mask(fs, ctx->w, nullptr, T, s);
   if (gp.u_means != nullptr)

@@ -15,19 +15,20 @@ GROUPS = ("means", "scales", "quats", "opacity", "colors")
 
 
 def crop_problem(seed, n_keep=200, win=48, frac_unstable=0.5):
-    """200 surfels nearest to a visible surface point and a win x win pixel window of the
-    640x480 camera centred on it (the window is a camera with a shifted principal point)."""
+    """200 surfels nearest to a visible surface point, seen by a win x win camera at the
+    640x480 camera's position aimed at that point (focal length 600 kept)."""
+    import math
     scene, layout = synth.room_scene(seed, 60000)
     cams = synth.room_camera_candidates(seed + 1, layout)
     rng = np.random.default_rng(seed)
+    p = scene.means.astype(np.float64)
     while True:
         cam = next(cams)
-        p = scene.means.astype(np.float64)
         pc = (p - cam.t.astype(np.float64)) @ cam.R.astype(np.float64)
         with np.errstate(divide="ignore", invalid="ignore"):
             u = cam.fx * pc[:, 0] / pc[:, 2] + cam.cx
             v = cam.fy * pc[:, 1] / pc[:, 2] + cam.cy
-        vis = (pc[:, 2] > 0.8) & (np.abs(u - 320) < 200) & (np.abs(v - 240) < 150) & (scene.opacity > 0.5)
+        vis = (pc[:, 2] > 0.8) & (np.abs(u - 320) < 150) & (np.abs(v - 240) < 100) & (scene.opacity > 0.5)
         if vis.sum() > 100:
             break
     c = rng.choice(np.flatnonzero(vis))
@@ -35,9 +36,9 @@ def crop_problem(seed, n_keep=200, win=48, frac_unstable=0.5):
     keep = np.sort(np.argpartition(d, n_keep)[:n_keep])
     crop = scene.subset(keep)
     crop.unstable = (rng.random(n_keep) < frac_unstable).astype(np.uint8)
-    x0, y0 = int(round(u[c])) - win // 2, int(round(v[c])) - win // 2
-    wcam = synth.Camera(fx=cam.fx, fy=cam.fy, cx=cam.cx - x0, cy=cam.cy - y0, width=win, height=win,
-                        R=cam.R.copy(), t=cam.t.copy())
+    ray = p[c] - cam.t.astype(np.float64)
+    ray /= np.linalg.norm(ray)
+    wcam = synth.look_at_camera(cam.t, math.atan2(ray[1], ray[0]), math.asin(ray[2]), win, win, cam.fx)
     target = synth.jitter_scene(crop, seed + 2)
     tref = oracle.render_image(target, wcam, ST)
     tc = tref["color"]

@@ -27,11 +27,11 @@ def test_scatter_scene_160x120_matches_oracle():
 def test_room_crop_ragged_matches_oracle():
     """Flattened surfel Gaussians on a box room seen by a ragged 100x75 camera
     (partial tiles on the right and bottom edges)."""
-    scene, layout = synth.room_scene(2002, 20000)
+    scene, layout = synth.room_scene(2002, 50000)
     cam = next(synth.room_camera_candidates(2003, layout, 100, 75, 94.0))
     ref = oracle.render_image(scene, cam, ST)
     got = gpu_forward(scene, cam)
-    assert (ref["depth"] > 0).mean() > 0.5  # mostly opaque surfaces
+    assert (ref["depth"] > 0).mean() > 0.3  # opaque surfaces cover a good part of the view
     assert_forward_matches(ref, got["color"][0], got["depth"][0], got["alpha"][0], got["index"][0])
 
 
