@@ -59,7 +59,8 @@ def scene_and_candidates():
 
 
 def flags_for(scene, cam, k):
-    return synth.flag_blobs(scene, [cam], WORKLOAD["n_unstable"], WORKLOAD["blobs"], seed=WORKLOAD["seed"] + 100 + k)
+    return synth.flag_blobs(scene, [cam], WORKLOAD["n_unstable"], WORKLOAD["blobs"], seed=WORKLOAD["seed"] + 100 + k,
+                            n_in_view=1)
 
 
 def peaks():
@@ -82,33 +83,55 @@ class ClockSampler:
             self.h = pynvml.nvmlDeviceGetHandleByIndex(index)
             self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
             self.ok = True
-        except Exception:
+        except Exception as e:  # report why, then fall back to nvidia-smi sampling
+            print(f"NVML clock sampling unavailable: {e!r}", file=sys.stderr)
             self.ok = False
 
     def _run(self):
         nv = self.nv
+        get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or getattr(
+            nv, "nvmlDeviceGetCurrentClocksThrottleReasons")
         while not self._stop.is_set():
             try:
-                self.samples.append((nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM),
-                                     nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)))
-            except Exception:
-                pass
-            time.sleep(0.002)
+                self.samples.append((nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM), get_reasons(self.h)))
+            except Exception as e:
+                self.errors = repr(e)
+            time.sleep(0.001)
 
     def __enter__(self):
         if self.ok:
             self.t = threading.Thread(target=self._run, daemon=True)
             self.t.start()
+        else:
+            import subprocess
+            q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "20", "-i", str(self.index)], stdout=subprocess.PIPE, text=True)
         return self
 
     def __exit__(self, *a):
         if self.ok:
             self._stop.set()
             self.t.join()
+        else:
+            time.sleep(0.05)
+            self.proc.terminate()
+            out = self.proc.communicate()[0]
+            self.smi = [ln.split(", ") for ln in out.strip().splitlines() if ln.count(",") == 5]
 
     def summary(self):
-        if not self.ok or not self.samples:
-            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unavailable"], "samples": 0}
+        if not self.ok:
+            rows = getattr(self, "smi", [])
+            if not rows:
+                return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            reasons = sorted({names[i] for r in rows for i in range(4) if r[2 + i].strip() == "Active"})
+            return {"sm_mhz": float(np.median([float(r[0]) for r in rows])), "sm_max_mhz": float(rows[0][1]),
+                    "reasons": reasons, "samples": len(rows), "source": "nvidia-smi"}
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unavailable"], "samples": 0,
+                    "error": getattr(self, "errors", "")}
         nv = self.nv
         names = {"hw_slowdown": getattr(nv, "nvmlClocksEventReasonHwSlowdown", 0x8),
                  "hw_thermal_slowdown": getattr(nv, "nvmlClocksEventReasonHwThermalSlowdown", 0x40),
@@ -137,7 +160,8 @@ def oracle_rate(scene, cam, masked_pixels, n_masked, targets, seconds_budget=25.
         oracle.loss_and_grads(scene, cam, st, pix, tc[sel], td[sel])
         return time.perf_counter() - t0
 
-    s1, s2 = 4, 12
+    s1, s2 = 1, 48
+    timed(s1)  # warm the allocator and caches
     t1 = timed(s1)
     t2 = timed(s2)
     per_px = max((t2 - t1) / (s2 - s1), 1e-9)
@@ -172,14 +196,16 @@ def run_ours(args):
     H, W = WORKLOAD["height"], WORKLOAD["width"]
     mask = torch.zeros(1, H, W, dtype=torch.uint8, device=dev)
     chosen = None
-    for k in range(200):
+    start = args.candidate if args.candidate >= 0 else DEFAULT_CANDIDATE
+    for k in range(start + 400):
         cam = next(cams)
-        if args.candidate >= 0 and k != args.candidate:
+        if k < start:
             continue
         scene.unstable = flags_for(scene, cam, k)
         g = rtg.Gaussians.from_scene(scene, device=dev)
         rtg.unstable_mask(ctx, cam, g, settings, mask)
         cov = float(mask.float().mean())
+        print(f"camera candidate {k}: unstable-mask coverage {cov:.3f}", file=sys.stderr)
         if WORKLOAD["coverage"][0] <= cov <= WORKLOAD["coverage"][1] or args.candidate >= 0:
             chosen = (k, cam, cov)
             break
@@ -366,7 +392,8 @@ def run_reference(args):
         cam = next(cams)
     scene.unstable = flags_for(scene, cam, k_cam)
     rng = np.random.default_rng(1)
-    # masked pixels: covered by an unstable Gaussian (oracle render of the unstable subset)
+    # masked pixels: covered by an unstable Gaussian (oracle render of the unstable subset);
+    # the 16x16 tile rule is not applied to this estimate
     cand = np.stack([rng.integers(0, cam.width, 48), rng.integers(0, cam.height, 48)], 1)
     unst = scene.subset(np.flatnonzero(scene.unstable))
     cov = oracle.render(unst, cam, st, pixels=cand, need_borderline=False).alpha.numpy() > 0
@@ -374,11 +401,12 @@ def run_reference(args):
     n_masked = int(round(cov.mean() * cam.width * cam.height))
     tc = rng.uniform(0, 1, (len(pix), 3))
     td = rng.uniform(1, 5, len(pix))
+    # fixed (pixel-independent) cost: the same call on a single pixel
+    oracle.loss_and_grads(scene, cam, st, pix[:1], tc[:1], td[:1])
     t0 = time.perf_counter()
-    oracle.project(*[torch.as_tensor(np.asarray(getattr(scene, k), np.float64)) for k in
-                     ("means", "scales", "quats", "opacity", "colors")], cam, st)
+    oracle.loss_and_grads(scene, cam, st, pix[:1], tc[:1], td[:1])
     fixed = time.perf_counter() - t0
-    S = 3
+    S = 16
     times = []
     for i in range(args.warmup + args.steps):
         sel = rng.choice(len(pix), size=min(S, len(pix)), replace=False)
@@ -400,7 +428,7 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-DEFAULT_CANDIDATE = 0
+DEFAULT_CANDIDATE = 7  # first pose of the seeded stream with 25-40% mask coverage (measured on the GPU)
 
 
 def main():

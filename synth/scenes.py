@@ -329,12 +329,13 @@ def room_camera_candidates(seed: int, layout: Layout, width: int = 640, height: 
 
 
 def flag_blobs(scene: Scene, cameras: Sequence[Camera], n_unstable: int, n_blobs: int,
-               seed: int) -> np.ndarray:
-    """Flag the ``n_unstable`` Gaussians nearest to ``n_blobs`` centres seen by the cameras.
+               seed: int, n_in_view: Optional[int] = None) -> np.ndarray:
+    """Flag the ``n_unstable`` Gaussians nearest to ``n_blobs`` centres.
 
-    Blob centres are the positions of random Gaussians that lie in front of one of
-    the cameras inside its field of view (a plain pinhole containment test used only
-    to choose inputs).
+    The first ``n_in_view`` centres (default: all) are the positions of random Gaussians
+    that lie in front of one of the cameras inside its field of view (a plain pinhole
+    containment test used only to choose inputs); the others are random Gaussians
+    anywhere in the scene.
     """
     rng = np.random.default_rng(seed)
     p = scene.means.astype(np.float64)
@@ -350,8 +351,13 @@ def flag_blobs(scene: Scene, cameras: Sequence[Camera], n_unstable: int, n_blobs
     pool = np.flatnonzero(cand)
     if pool.size == 0:
         pool = np.arange(scene.n)
-    centers = p[rng.choice(pool, size=n_blobs, replace=False)]
-    dist = np.min(np.linalg.norm(p[:, None, :] - centers[None, :, :], axis=2), axis=1)
+    k_view = n_blobs if n_in_view is None else min(n_in_view, n_blobs)
+    picks = list(rng.choice(pool, size=k_view, replace=False))
+    if n_blobs > k_view:
+        picks += list(rng.choice(scene.n, size=n_blobs - k_view, replace=False))
+    centers = p[np.array(picks)].astype(np.float32)
+    p32 = scene.means.astype(np.float32)
+    dist = np.min(np.stack([np.linalg.norm(p32 - c, axis=1) for c in centers], 1), axis=1)
     flags = np.zeros(scene.n, dtype=np.uint8)
     flags[np.argpartition(dist, n_unstable - 1)[:n_unstable]] = 1
     return flags
