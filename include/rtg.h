@@ -178,6 +178,24 @@ rtg_status rtg_scatter_unstable(int64_t nu, int32_t C, const int32_t *ids, const
                                 const float *u_colors, float *means, float *scales, float *quats, float *opacity,
                                 float *colors, void *stream);
 
+/* Allocation-free form of rtg_unstable_index, for callers that cannot allocate device
+ * memory (the paper has no counterpart; this is a property of the library, not of the
+ * method).  A thread that runs beside a real-time mapping loop should not call cudaMalloc,
+ * which can synchronise the device and stall the other threads' kernels, and a program
+ * that has given its whole memory budget to its own pool may have none left for a
+ * context workspace.  This call needs no context and allocates nothing: its scratch is a
+ * fixed array of per-block counts inside the library, enough for n <= 16,777,216
+ * Gaussians (64 KB, kept on every device that loads the library until the process
+ * exits).  Larger n returns RTG_ERR_WORKSPACE without launching anything.  Outputs are as
+ * for rtg_unstable_index: ids [nu] (device int32, ascending) and *nu_out (device int64).
+ * The first call on each device looks up the scratch array's device address, so make it
+ * before any stream capture.  Calls share that one array, so two calls that overlap on
+ * the GPU (different streams, no ordering between them) race; order them on one stream.
+ * Every scratch entry a call reads is written earlier in the same call, so nothing needs
+ * clearing between calls. */
+rtg_status rtg_unstable_index_static(int64_t n, const uint8_t *unstable, int32_t *ids, int64_t *nu_out,
+                                     void *stream);
+
 /* Counters of the last forward (synchronises the context's last stream). HOST out. */
 rtg_status rtg_get_stats(rtg_ctx *ctx, rtg_stats *out);
 

@@ -71,6 +71,7 @@ SIGNATURES = [
     ("rtg_adam_step", c_int32, [c_int64, c_int32] + [c_void_p] * 12 + [c_int32, POINTER(rtg_adam_params),
                                                                        c_void_p]),
     ("rtg_unstable_index", c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("rtg_unstable_index_static", c_int32, [c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("rtg_gather_unstable", c_int32, [c_int64, c_int32] + [c_void_p] * 11 + [c_void_p]),
     ("rtg_scatter_unstable", c_int32, [c_int64, c_int32] + [c_void_p] * 11 + [c_void_p]),
     ("rtg_get_stats", c_int32, [c_void_p, POINTER(rtg_stats)]),

@@ -287,6 +287,17 @@ def unstable_index(ctx: Context, unstable: torch.Tensor, stream=None):
     return ids[:nu], nu
 
 
+def unstable_index_static(unstable: torch.Tensor, ids: torch.Tensor, nu_out: torch.Tensor, stream=None):
+    """Allocation-free unstable index (no context): fills ids [>= nu] int32 and nu_out [1]
+    int64 on the device.  For callers that must not allocate device memory; limited to
+    16,777,216 Gaussians.  Does not synchronise."""
+    n = int(unstable.shape[0])
+    st = _lib.load().rtg_unstable_index_static(n, _ptr(unstable, torch.uint8, "unstable"),
+                                               _ptr(ids, torch.int32, "ids"), _ptr(nu_out, torch.int64, "nu_out"),
+                                               _stream(stream))
+    _check(st, "rtg_unstable_index_static")
+
+
 def gather_unstable(ids: torch.Tensor, g: Gaussians, stream=None):
     nu, C = int(ids.shape[0]), g.channels
     dev = g.means.device
