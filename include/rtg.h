@@ -155,8 +155,9 @@ rtg_status rtg_render_backward(rtg_ctx *ctx, const float *dL_dcolor, const float
 
 /* Adam (Kingma & Ba, Algorithm 1) on compact unstable parameters, in place, with the
  * per-group learning rates of Supplement C.  The scale is optimised in log space
- * (s <- s * exp(-step), gradient s * dL/ds).  m and v are [nu, 11 + C] float32
- * (means 3, scales 3, quats 4, opacity 1, colours C); `step` counts from 1. */
+ * (s <- s * exp(-step), gradient s * dL/ds).  m and v hold nu * (11 + C) float32 each,
+ * laid out group by group like the parameters: means [nu,3], then scales [nu,3], quats
+ * [nu,4], opacity [nu], colours [nu,C]; start them at zero.  `step` counts from 1. */
 typedef struct {
   float lr_means, lr_scales, lr_quats, lr_opacity, lr_colors, beta1, beta2, eps;
 } rtg_adam_params;

@@ -265,7 +265,8 @@ def render_backward(ctx: Context, dL_dcolor, dL_ddepth, g_means, g_scales, g_qua
 
 def adam_step(params: Sequence[torch.Tensor], grads: Sequence[torch.Tensor], m: torch.Tensor, v: torch.Tensor,
               step: int, hp: AdamSettings = AdamSettings(), stream=None):
-    """params/grads: compact (means, scales, quats, opacity, colors); m, v: [nu, 11 + C]."""
+    """params/grads: compact (means, scales, quats, opacity, colors); m, v: nu * (11 + C) floats
+    each, zero at the start, laid out group by group like the parameters."""
     means, scales, quats, opacity, colors = params
     nu, C = int(means.shape[0]), int(colors.shape[1])
     c = hp.to_c()

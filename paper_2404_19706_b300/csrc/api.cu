@@ -541,13 +541,17 @@ rtg_status rtg_unstable_mask(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, co
   const int T = fs.cam[0].tiles_x * fs.cam[0].tiles_y;
   const size_t npx = (size_t)F * fs.cam[0].W * fs.cam[0].H;
   ctx->has_fwd = false;  // the mask pass reuses the forward's workspace
+  (void)npx;
   ProfScope ps(ctx, kPUnstableMask, s);
-  cudaMemsetAsync(mask, 0, npx, s);
+  // every in-image tile is active: the unstable Gaussians are bucketed into all tiles
   launch_tile_mask(fs, ctx->w, nullptr, T, s);
   if (gp.u_means != nullptr)
     if ((st = rank_pass(ctx, gp.unstable, gp.n, ctx->w.rank, ctx->w.ids, ctx->w.counters, nullptr, s)) != RTG_OK)
       return st;
-  launch_unstable_mask(gp, ctx->w, P, F, T, mask, s);
+  launch_project_unstable(gp, ctx->w, P, F, T, s);
+  launch_scan_tiles(ctx->w, F * T, ctx->cap.max_pairs, s);
+  launch_emit(ctx->w, gp.n, F, T, s);
+  launch_mask_cover_tiles(ctx->w, P, gp.n, F, T, gp.C, mask, s);
   ctx->last_stream = s;
   return check_launch(ctx, "unstable_mask");
 }

@@ -74,11 +74,17 @@ __global__ void __launch_bounds__(kScanBlock) k_rank_write(const uint8_t *__rest
 }
 
 // --------------------------------------------------------------------------- projection
-template <int C>
+// kMask = true projects only the unstable Gaussians (for the unstable-pixel mask): no
+// gradient rows are cleared and no visibility is counted.
+template <int C, bool kMask>
 __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, int F, int T) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.n) return;
   const int64_t N = g.n;
+  if (kMask && g.unstable[i] == 0) {
+    for (int f = 0; f < F; ++f) w.ntiles[(int64_t)f * N + i] = 0u;
+    return;
+  }
   GParams P;
   bool ok = load_params(g, w.rank, i, P);
   const float *cp = color_ptr(g, w.rank, i);
@@ -128,7 +134,7 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
         cold[0] = make_float4(o.n[0], o.n[1], o.n[2], o.d0);
         cold[1] = make_float4(o.Z, __int_as_float(rk), __uint_as_float((uint32_t)tx0 | ((uint32_t)ty0 << 16)),
                               __uint_as_float((uint32_t)tx1 | ((uint32_t)ty1 << 16)));
-        if (rk >= 0) {
+        if (!kMask && rk >= 0) {
           float4 *g2 = reinterpret_cast<float4 *>(w.grad2d + ((int64_t)f * N + rk) * G2);
 #pragma unroll
           for (int k = 0; k < G2 / 4; ++k) g2[k] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -138,7 +144,7 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
     }
     w.ntiles[(int64_t)f * N + i] = nt;
   }
-  if (visible_frames) atomicAdd(w.counters + kVisible, (unsigned long long)visible_frames);
+  if (!kMask && visible_frames) atomicAdd(w.counters + kVisible, (unsigned long long)visible_frames);
 }
 
 // --------------------------------------------------------------------------- tile scan
@@ -249,9 +255,18 @@ void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, in
   if (g.n <= 0) return;
   const unsigned nb = (unsigned)((g.n + 255) / 256);
   if (g.C == 3)
-    k_project<3><<<nb, 256, 0, s>>>(g, w, prm, F, T);
+    k_project<3, false><<<nb, 256, 0, s>>>(g, w, prm, F, T);
   else
-    k_project<8><<<nb, 256, 0, s>>>(g, w, prm, F, T);
+    k_project<8, false><<<nb, 256, 0, s>>>(g, w, prm, F, T);
+}
+
+void launch_project_unstable(const GaussPtrs &g, const Work &w, const Prm &prm, int F, int T, cudaStream_t s) {
+  if (g.n <= 0) return;
+  const unsigned nb = (unsigned)((g.n + 255) / 256);
+  if (g.C == 3)
+    k_project<3, true><<<nb, 256, 0, s>>>(g, w, prm, F, T);
+  else
+    k_project<8, true><<<nb, 256, 0, s>>>(g, w, prm, F, T);
 }
 
 void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, cudaStream_t s) {

@@ -42,6 +42,7 @@ void launch_tile_mask(const FrameSet &fs, const Work &w, const uint8_t *mask, in
 void launch_rank(const uint8_t *unstable, int64_t n, int32_t *block_cnt, int32_t *rank, int32_t *ids,
                  unsigned long long *nu_counter, int64_t *nu_out, cudaStream_t s);
 void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, int T, cudaStream_t s);
+void launch_project_unstable(const GaussPtrs &g, const Work &w, const Prm &prm, int F, int T, cudaStream_t s);
 void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, cudaStream_t s);
 void launch_emit(const Work &w, int64_t N, int F, int T, cudaStream_t s);
 // sort.cu
@@ -68,7 +69,7 @@ void launch_gather(int64_t nu, int C, const int32_t *ids, const float *means, co
 void launch_scatter(int64_t nu, int C, const int32_t *ids, const float *um, const float *us, const float *uq,
                     const float *uo, const float *uc, float *means, float *scales, float *quats, float *opacity,
                     float *colors, cudaStream_t s);
-void launch_unstable_mask(const GaussPtrs &g, const Work &w, const Prm &prm, int F, int T, uint8_t *mask,
-                          cudaStream_t s);
+void launch_mask_cover_tiles(const Work &w, const Prm &prm, int64_t N, int F, int T, int C, uint8_t *mask,
+                             cudaStream_t s);
 
 }  // namespace rtg

@@ -1,6 +1,8 @@
 // L1 losses (Section 3.2, Eq. 7/8), Adam on the unstable subset (Supplement C learning
 // rates), unstable-subset gather/scatter, and the unstable-pixel mask (Supplement B,
 // Eq. S2 plus the 50% tile rule).
+#include <algorithm>
+
 #include "kernels.cuh"
 #include "project.cuh"
 
@@ -52,18 +54,32 @@ __global__ void __launch_bounds__(256) k_loss_reduce(Work w, int F, int C, int H
   if (threadIdx.x == 0) s_last = atomicAdd(w.loss_done, 1u) == gridDim.x - 1;
   __syncthreads();
   if (!s_last) return;
+  // last block: every thread sums a strided share of the block partials (fixed order), then
+  // a fixed-order reduction across the threads keeps the result deterministic
+  __threadfence();
+  __shared__ double s_tot[4][256];
+  double t[4] = {0, 0, 0, 0};
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) t[k] += (double)__ldcg(w.loss_part + b * 4 + k);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) s_tot[k][threadIdx.x] = t[k];
+  __syncthreads();
+  for (int stride = 128; stride > 0; stride >>= 1) {
+    if ((int)threadIdx.x < stride)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) s_tot[k][threadIdx.x] += s_tot[k][threadIdx.x + stride];
+    __syncthreads();
+  }
   if (threadIdx.x == 0) {
-    __threadfence();
-    double t[4] = {0, 0, 0, 0};
-    for (int b = 0; b < (int)gridDim.x; ++b)
-      for (int k = 0; k < 4; ++k) t[k] += (double)((volatile float *)w.loss_part)[b * 4 + k];
-    const double Lc = t[2] > 0 ? t[0] / (t[2] * C) : 0.0;
-    const double Ld = t[3] > 0 ? t[1] / t[3] : 0.0;
+    const double sc = s_tot[0][0], sd = s_tot[1][0], np = s_tot[2][0], nd = s_tot[3][0];
+    const double Lc = np > 0 ? sc / (np * C) : 0.0;
+    const double Ld = nd > 0 ? sd / nd : 0.0;
     loss_out[0] = (float)(w_c * Lc + w_d * Ld);
     loss_out[1] = (float)Lc;
     loss_out[2] = (float)Ld;
-    w.loss_scal[4] = t[2] > 0 ? (float)(w_c / (t[2] * C)) : 0.f;
-    w.loss_scal[5] = t[3] > 0 ? (float)(w_d / t[3]) : 0.f;
+    w.loss_scal[4] = np > 0 ? (float)(w_c / (np * C)) : 0.f;
+    w.loss_scal[5] = nd > 0 ? (float)(w_d / nd) : 0.f;
     *w.loss_done = 0u;
   }
 }
@@ -99,6 +115,8 @@ __device__ __forceinline__ float adam_delta(float g, float &m, float &v, float l
   return lr * (m * bc1) / (sqrtf(v) * bc2_sqrt + hp.eps);
 }
 
+// One thread per scalar parameter.  m and v are laid out group by group (means [nu,3],
+// scales [nu,3], quats [nu,4], opacity [nu], colours [nu,C]), so every stream is coalesced.
 __global__ void __launch_bounds__(256) k_adam(int64_t nu, int C, float *__restrict__ means, float *__restrict__ scales,
                                               float *__restrict__ quats, float *__restrict__ opacity,
                                               float *__restrict__ colors, const float *__restrict__ g_means,
@@ -106,41 +124,32 @@ __global__ void __launch_bounds__(256) k_adam(int64_t nu, int C, float *__restri
                                               const float *__restrict__ g_opacity, const float *__restrict__ g_colors,
                                               float *__restrict__ m, float *__restrict__ v, rtg_adam_params hp,
                                               float bc1, float bc2_sqrt) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nu) return;
-  const int D = 11 + C;
-  float *mr = m + k * D, *vr = v + k * D;
-  for (int j = 0; j < 3; ++j) {
-    float mm = mr[j], vv = vr[j];
-    means[3 * k + j] -= adam_delta(g_means[3 * k + j], mm, vv, hp.lr_means, hp, bc1, bc2_sqrt);
-    mr[j] = mm;
-    vr[j] = vv;
-  }
-  for (int j = 0; j < 3; ++j) {  // log-space scale: theta = log s, dL/dtheta = s dL/ds
-    const float s = scales[3 * k + j];
-    float mm = mr[3 + j], vv = vr[3 + j];
-    const float step = adam_delta(g_scales[3 * k + j] * s, mm, vv, hp.lr_scales, hp, bc1, bc2_sqrt);
-    scales[3 * k + j] = s * expf(-step);
-    mr[3 + j] = mm;
-    vr[3 + j] = vv;
-  }
-  for (int j = 0; j < 4; ++j) {
-    float mm = mr[6 + j], vv = vr[6 + j];
-    quats[4 * k + j] -= adam_delta(g_quats[4 * k + j], mm, vv, hp.lr_quats, hp, bc1, bc2_sqrt);
-    mr[6 + j] = mm;
-    vr[6 + j] = vv;
-  }
-  {
-    float mm = mr[10], vv = vr[10];
-    opacity[k] -= adam_delta(g_opacity[k], mm, vv, hp.lr_opacity, hp, bc1, bc2_sqrt);
-    mr[10] = mm;
-    vr[10] = vv;
-  }
-  for (int c = 0; c < C; ++c) {
-    float mm = mr[11 + c], vv = vr[11 + c];
-    colors[(int64_t)C * k + c] -= adam_delta(g_colors[(int64_t)C * k + c], mm, vv, hp.lr_colors, hp, bc1, bc2_sqrt);
-    mr[11 + c] = mm;
-    vr[11 + c] = vv;
+  const int64_t total = nu * (11 + C);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    float *param;
+    const float *grad;
+    float lr;
+    int64_t j;
+    bool log_space = false;
+    if (i < 3 * nu) {
+      param = means; grad = g_means; lr = hp.lr_means; j = i;
+    } else if (i < 6 * nu) {
+      param = scales; grad = g_scales; lr = hp.lr_scales; j = i - 3 * nu; log_space = true;
+    } else if (i < 10 * nu) {
+      param = quats; grad = g_quats; lr = hp.lr_quats; j = i - 6 * nu;
+    } else if (i < 11 * nu) {
+      param = opacity; grad = g_opacity; lr = hp.lr_opacity; j = i - 10 * nu;
+    } else {
+      param = colors; grad = g_colors; lr = hp.lr_colors; j = i - 11 * nu;
+    }
+    float mm = m[i], vv = v[i];
+    const float x = param[j];
+    // log-space scale: theta = log s, dL/dtheta = s dL/ds, s <- s exp(-step)
+    const float g = log_space ? grad[j] * x : grad[j];
+    const float step = adam_delta(g, mm, vv, lr, hp, bc1, bc2_sqrt);
+    param[j] = log_space ? x * expf(-step) : x - step;
+    m[i] = mm;
+    v[i] = vv;
   }
 }
 
@@ -178,51 +187,57 @@ __global__ void k_scatter(int64_t nu, int C, const int32_t *__restrict__ ids, co
 }
 
 // --------------------------------------------------------------------------- unstable mask
-// Coverage: a pixel is covered when an unstable Gaussian's footprint reaches alpha_min
-// there (T_unstable < 1 in Eq. S2).  The footprint is evaluated with the same
-// projection and expression as the forward, over the Gaussian's support box.
-__global__ void __launch_bounds__(256) k_mask_cover(GaussPtrs g, Work w, Prm prm, int F, uint8_t *__restrict__ mask) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= g.n || g.unstable[i] == 0) return;
-  GParams P;
-  bool ok = load_params(g, w.rank, i, P);
-  if (!ok) return;
-  const float *cp = color_ptr(g, w.rank, i);
-  for (int c = 0; c < g.C; ++c) ok = ok && isfinite(cp[c]);
-  if (!ok) return;
-  const float qn = sqrtf(P.q[0] * P.q[0] + P.q[1] * P.q[1] + P.q[2] * P.q[2] + P.q[3] * P.q[3]);
-  float R[9];
-  quat_to_rot(P.q[0] / qn, P.q[1] / qn, P.q[2] / qn, P.q[3] / qn, R);
-  const int kmin = argmin3(P.s[0], P.s[1], P.s[2]);
-  for (int f = 0; f < F; ++f) {
-    const DevCam &cam = w.cams[f];
-    Projected o;
-    if (!project_gaussian(cam, prm, P, R, kmin, o)) continue;
-    uint8_t *mf = mask + (int64_t)f * cam.H * cam.W;
-    for (int y = o.y0; y <= o.y1; ++y)
-      for (int x = o.x0; x <= o.x1; ++x) {
-        float dx, dy, t1, t2, gg;
-        const float fa = footprint((float)x, (float)y, o.mux.hi, o.muy.hi, o.mux.lo, o.muy.lo, o.u11, o.u12, o.u22,
-                                   P.alpha, prm.f_max, dx, dy, t1, t2, gg);
-        if (fa >= prm.alpha_min) mf[(int64_t)y * cam.W + x] = 1;
-      }
-  }
-}
-
-// Tile rule (Supplement B): clear every 16x16 tile in which fewer than `discard` of the
-// in-image pixels are covered.
-__global__ void __launch_bounds__(kTilePix) k_mask_tiles(Work w, Prm prm, int T, uint8_t *__restrict__ mask) {
+// One CTA per 16x16 tile (the tile grid of the rule).  The unstable Gaussians were
+// projected and bucketed into every tile their support box touches; each pixel scans its
+// tile's bucket until one footprint reaches alpha_min there (T_unstable < 1 in Eq. S2),
+// with the same projection and footprint expression as the forward, and the whole tile
+// stops as soon as all its pixels are covered.  The tile rule (Supplement B) is applied in
+// the same kernel: a tile with fewer than `discard` of its in-image pixels covered is
+// cleared.  Every in-image pixel of the mask is written.
+__global__ void __launch_bounds__(kTilePix) k_mask_cover_tiles(Work w, Prm prm, int64_t N, int T, int H4,
+                                                               uint8_t *__restrict__ mask) {
+  __shared__ float4 s_rec[2][kTilePix];
+  if (w.counters[kSkip] != 0ull) return;
   const int tile = blockIdx.x;
   const int f = tile / T, lt = tile - f * T;
   const DevCam &cam = w.cams[f];
   const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-  const int px = tx * kTile + (threadIdx.x & (kTile - 1)), py = ty * kTile + threadIdx.x / kTile;
+  const int tid = threadIdx.x;
+  const int px = tx * kTile + (tid & (kTile - 1)), py = ty * kTile + tid / kTile;
   const bool in = px < cam.W && py < cam.H;
-  const int64_t o = ((int64_t)f * cam.H + py) * cam.W + px;
-  const bool cov = in && mask[o] != 0;
+  const float fpx = (float)px, fpy = (float)py;
+  const uint32_t off = w.tile_offset[tile];
+  const uint32_t n = w.tile_offset[tile + 1] - off;
+  const float4 *__restrict__ rec = w.rec_hot + (int64_t)f * N * H4;
+  bool cov = false;
+  for (uint32_t b0 = 0; b0 < n; b0 += kTilePix) {
+    if (__syncthreads_and(cov || !in)) break;
+    const uint32_t j = b0 + tid;
+    if (j < n) {
+      const uint32_t gid = (uint32_t)w.keys[off + j];
+      s_rec[0][tid] = rec[(int64_t)gid * H4];
+      s_rec[1][tid] = rec[(int64_t)gid * H4 + 1];
+    }
+    __syncthreads();
+    if (in && !cov) {
+      const int m = (int)min((uint32_t)kTilePix, n - b0);
+      for (int k = 0; k < m; ++k) {
+        const float4 r0 = s_rec[0][k], r1 = s_rec[1][k];
+        float dx, dy, t1, t2, g;
+        if (footprint(fpx, fpy, r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, prm.f_max, dx, dy, t1, t2, g) >=
+            prm.alpha_min) {
+          cov = true;
+          break;
+        }
+      }
+    }
+  }
   const int n_in = __syncthreads_count(in);
   const int n_cov = __syncthreads_count(cov);
-  if (prm.discard > 0.f && !((float)n_cov >= prm.discard * (float)n_in) && cov) mask[o] = 0;
+  if (in) {
+    const bool keep = !(prm.discard > 0.f) || (float)n_cov >= prm.discard * (float)n_in;
+    mask[((int64_t)f * cam.H + py) * cam.W + px] = (cov && keep) ? 1 : 0;
+  }
 }
 
 void launch_l1_loss(const Work &w, int F, int C, int H, int W, const float *color, const float *depth,
@@ -237,7 +252,9 @@ void launch_adam(int64_t nu, int C, float *means, float *scales, float *quats, f
                  const float *g_colors, float *m, float *v, const rtg_adam_params &hp, float bc1, float bc2_sqrt,
                  cudaStream_t s) {
   if (nu <= 0) return;
-  k_adam<<<(unsigned)((nu + 255) / 256), 256, 0, s>>>(nu, C, means, scales, quats, opacity, colors, g_means, g_scales,
+  const int64_t total = nu * (11 + C);
+  const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)kPersistBlocks * 4);
+  k_adam<<<blocks, 256, 0, s>>>(nu, C, means, scales, quats, opacity, colors, g_means, g_scales,
                                                       g_quats, g_opacity, g_colors, m, v, hp, bc1, bc2_sqrt);
 }
 
@@ -257,10 +274,9 @@ void launch_scatter(int64_t nu, int C, const int32_t *ids, const float *um, cons
                                                          opacity, colors);
 }
 
-void launch_unstable_mask(const GaussPtrs &g, const Work &w, const Prm &prm, int F, int T, uint8_t *mask,
-                          cudaStream_t s) {
-  if (g.n > 0) k_mask_cover<<<(unsigned)((g.n + 255) / 256), 256, 0, s>>>(g, w, prm, F, mask);
-  k_mask_tiles<<<F * T, kTilePix, 0, s>>>(w, prm, T, mask);
+void launch_mask_cover_tiles(const Work &w, const Prm &prm, int64_t N, int F, int T, int C, uint8_t *mask,
+                             cudaStream_t s) {
+  k_mask_cover_tiles<<<F * T, kTilePix, 0, s>>>(w, prm, N, T, hot4_of(C), mask);
 }
 
 }  // namespace rtg
