@@ -100,7 +100,7 @@ rtg_status check_launch(rtg_ctx *ctx, const char *what) {
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t cams, counters, rank, ids, block_cnt, rec_hot, rec_cold, ntiles, tile_npix, tile_count, tile_offset,
+  size_t cams, counters, rank, ids, block_cnt, rec_hot, rec_cold, rec_box, ntiles, tile_npix, tile_count, tile_offset,
       tile_cursor, keys, keys_alt, sorted, px_T, px_last, px_hit, grad2d, loss_part, loss_scal, loss_done, total;
 };
 
@@ -132,6 +132,7 @@ Layout layout_of(const rtg_capacity *c) {
   L.block_cnt = take((N / kScanBlock + 2) * 4);
   L.rec_hot = take(Fm * N * H4 * 16);
   L.rec_cold = take(Fm * N * 32);
+  L.rec_box = take(Fm * N * 8);
   L.ntiles = take(Fm * N * 4);
   L.tile_npix = take((FT + 1) * 4);
   L.tile_count = take((FT + 1) * 4);
@@ -279,6 +280,7 @@ rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap) {
   w.block_cnt = (int32_t *)(b + L.block_cnt);
   w.rec_hot = (float4 *)(b + L.rec_hot);
   w.rec_cold = (float4 *)(b + L.rec_cold);
+  w.rec_box = (float2 *)(b + L.rec_box);
   w.ntiles = (uint32_t *)(b + L.ntiles);
   w.tile_npix = (uint32_t *)(b + L.tile_npix);
   w.tile_count = (uint32_t *)(b + L.tile_count);

@@ -9,8 +9,9 @@
 // (no background term), chained through f = min(f_max, alpha 2^-q), q = |U (u - mu)|^2.
 // The depth depends on f only through the choice of the hit fragment, so it adds no
 // gradient to f; its gradient goes to the hit Gaussian's plane record (d0, n_c) or to
-// its centre depth.  Sums over a warp's 32 pixels are formed with shuffles and added
-// with one vector atomic per warp.
+// its centre depth.  Each warp works alone on 32 compacted pixels and skips the records
+// whose support box misses its pixel box (the forward's test); sums over the warp are
+// formed by a halving reduce-scatter and added with vector atomics.
 //
 // k_project_backward chains those screen-space gradients to position, linear scale,
 // raw quaternion, opacity and colour through Sigma_2D = J W R S^2 R^T W^T J^T + lowpass I,
@@ -26,6 +27,40 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// Sums up to 16 per-lane values over the warp by halving exchanges (a reduce-scatter:
+// 8 + 4 + 2 + 1 + 1 shuffles instead of 5 per value).  Lane L returns the warp total of
+// value L >> 1; values at or beyond NV count as zero.
+template <int NV>
+__device__ __forceinline__ float warp_transpose_sum(const float (&in)[NV]) {
+  const int lane = threadIdx.x & 31;
+  float v8[8];
+  {
+    const bool up = lane & 16;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float lo = i < NV ? in[i] : 0.f, hi = (8 + i) < NV ? in[8 + i] : 0.f;
+      v8[i] = (up ? hi : lo) + __shfl_xor_sync(0xffffffffu, up ? lo : hi, 16);
+    }
+  }
+  float v4[4];
+  {
+    const bool up = lane & 8;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      v4[i] = (up ? v8[4 + i] : v8[i]) + __shfl_xor_sync(0xffffffffu, up ? v8[i] : v8[4 + i], 8);
+  }
+  float v2[2];
+  {
+    const bool up = lane & 4;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+      v2[i] = (up ? v4[2 + i] : v4[i]) + __shfl_xor_sync(0xffffffffu, up ? v4[i] : v4[2 + i], 4);
+  }
+  const bool up = lane & 2;
+  float v = (up ? v2[1] : v2[0]) + __shfl_xor_sync(0xffffffffu, up ? v2[0] : v2[1], 2);
+  return v + __shfl_xor_sync(0xffffffffu, v, 1);
+}
+
 template <int C>
 __global__ void __launch_bounds__(kTilePix) k_backward(Work w, Prm prm, int64_t N, int T,
                                                        const uint8_t *__restrict__ mask,
@@ -33,11 +68,14 @@ __global__ void __launch_bounds__(kTilePix) k_backward(Work w, Prm prm, int64_t 
                                                        const float *__restrict__ dL_ddepth) {
   constexpr int H4 = (C <= 4) ? 3 : 4;
   constexpr int G2 = (C <= 5) ? 16 : 20;
-  __shared__ float4 s_rec[H4][kTilePix];
-  __shared__ int s_rank[kTilePix];
+  constexpr int NV = 6 + C;            // d mu (2), d conic (3), d alpha, d colour (C)
+  constexpr int NG = (NV + 3) / 4;     // float4 groups of a grad2d row they occupy
+  constexpr int NW = kTilePix / 32;
+  __shared__ float4 s_rec[NW][H4][32];
+  __shared__ uint32_t s_j[NW][32];
+  __shared__ int s_rank[NW][32];
   __shared__ int s_pix[kTilePix];
-  __shared__ int s_wcnt[kTilePix / 32];
-  __shared__ unsigned s_maxlast;
+  __shared__ int s_wcnt[NW];
   if (w.counters[kSkip] != 0ull) return;
   const int tile = blockIdx.x;
   if (w.tile_npix[tile] == 0u) return;
@@ -51,14 +89,15 @@ __global__ void __launch_bounds__(kTilePix) k_backward(Work w, Prm prm, int64_t 
     if (act && mask != nullptr) act = mask[((int64_t)f * cam.H + py) * cam.W + px] != 0;
     const unsigned bal = __ballot_sync(0xffffffffu, act);
     if (lane == 0) s_wcnt[wid] = __popc(bal);
-    if (tid == 0) s_maxlast = 0u;
     __syncthreads();
     int before = 0;
     for (int k = 0; k < wid; ++k) before += s_wcnt[k];
     if (act) s_pix[before + __popc(bal & lanemask_lt())] = tid;
     __syncthreads();
   }
+  // every warp works alone on its 32 compacted pixels from here on
   const int npix = (int)w.tile_npix[tile];
+  if (wid * 32 >= npix) return;
   const bool has = tid < npix;
   const int my = has ? s_pix[tid] : 0;
   const int px = tx * kTile + (my & (kTile - 1)), py = ty * kTile + my / kTile;
@@ -79,7 +118,6 @@ __global__ void __launch_bounds__(kTilePix) k_backward(Work w, Prm prm, int64_t 
 #pragma unroll
     for (int c = 0; c < C; ++c) dC[c] = dL_dcolor[((int64_t)f * C + c) * HW + (int64_t)py * cam.W + px];
     dLdD = dL_ddepth[pix];
-    atomicMax(&s_maxlast, last);
   }
   float *__restrict__ g2base = w.grad2d + (int64_t)f * N * G2;
 
@@ -128,92 +166,100 @@ __global__ void __launch_bounds__(kTilePix) k_backward(Work w, Prm prm, int64_t 
       pending &= ~__ballot_sync(0xffffffffu, in);
     }
   }
-  __syncthreads();
-  const uint32_t maxlast = s_maxlast;
+
+  // bounding box of the warp's pixels (records whose support misses it were skipped by the
+  // forward's identical test and contribute nothing here)
+  const int bx0 = __reduce_min_sync(0xffffffffu, has ? px : 0x7fffffff);
+  const int bx1 = __reduce_max_sync(0xffffffffu, has ? px : -1);
+  const int by0 = __reduce_min_sync(0xffffffffu, has ? py : 0x7fffffff);
+  const int by1 = __reduce_max_sync(0xffffffffu, has ? py : -1);
+  const float wcx = 0.5f * (float)(bx0 + bx1), whx = 0.5f * (float)(bx1 - bx0);
+  const float wcy = 0.5f * (float)(by0 + by1), why = 0.5f * (float)(by1 - by0);
+  const uint32_t maxlast = __reduce_max_sync(0xffffffffu, last);
   const float4 *__restrict__ rec = w.rec_hot + (int64_t)f * N * H4;
+  const float2 *__restrict__ box = w.rec_box + (int64_t)f * N;
   float S[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) S[c] = 0.f;
-  const bool warp_has = __any_sync(0xffffffffu, has);
 
-  for (int b_end = (int)maxlast; b_end > 0; b_end -= kTilePix) {
-    const int b_beg = max(0, b_end - kTilePix);
-    __syncthreads();
-    {
-      const int j = b_beg + tid;
-      if (j < b_end) {
-        const uint32_t gid = w.sorted[off + j];
-        const float4 *r = rec + (int64_t)gid * H4;
+  for (int b_end = (int)maxlast; b_end > 0; b_end -= 32) {
+    const int b_beg = max(0, b_end - 32);
+    const int j = b_beg + lane;
+    bool keep = false;
+    float4 r[H4];
+    int rk = -1;
+    if (j < b_end) {
+      const uint32_t gid = w.sorted[off + j];
+      const float4 *rp = rec + (int64_t)gid * H4;
 #pragma unroll
-        for (int k = 0; k < H4; ++k) s_rec[k][tid] = r[k];
-        s_rank[tid] = __float_as_int(w.rec_cold[((int64_t)f * N + gid) * 2 + 1].y);
-      }
+      for (int k = 0; k < H4; ++k) r[k] = rp[k];
+      const float2 bb = box[gid];
+      keep = fabsf(r[0].x - wcx) <= whx + bb.x && fabsf(r[0].y - wcy) <= why + bb.y;
+      rk = __float_as_int(w.rec_cold[((int64_t)f * N + gid) * 2 + 1].y);
     }
-    __syncthreads();
-    if (!warp_has) continue;
-    for (int j = b_end - 1; j >= b_beg; --j) {
-      const int k = j - b_beg;
-      bool act = has && (uint32_t)j < last;
-      const float4 r0 = s_rec[0][k], r1 = s_rec[1][k];
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (keep) {
+      const int slot = __popc(bal & lanemask_lt());
+#pragma unroll
+      for (int k = 0; k < H4; ++k) s_rec[wid][k][slot] = r[k];
+      s_j[wid][slot] = (uint32_t)j;
+      s_rank[wid][slot] = rk;
+    }
+    __syncwarp();
+    for (int k = __popc(bal) - 1; k >= 0; --k) {
+      const uint32_t jj = s_j[wid][k];
+      bool act = has && jj < last;
+      const float4 r0 = s_rec[wid][0][k], r1 = s_rec[wid][1][k];
       float dx = 0.f, dy = 0.f, t1 = 0.f, t2 = 0.f, g = 0.f, fa = 0.f;
       if (act) {
         fa = footprint(fpx, fpy, r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, prm.f_max, dx, dy, t1, t2, g);
         act = fa >= prm.alpha_min;
       }
-      const int rk = s_rank[k];
-      float gmx = 0.f, gmy = 0.f, gca = 0.f, gcb = 0.f, gcc = 0.f, gal = 0.f;
-      float gcol[C];
+      const int rkk = s_rank[wid][k];
+      float v[NV];
 #pragma unroll
-      for (int c = 0; c < C; ++c) gcol[c] = 0.f;
+      for (int q = 0; q < NV; ++q) v[q] = 0.f;
       if (act) {
         const float om = 1.f - fa;
-        T_ = T_ / om;  // transmission in front of fragment j
+        T_ = T_ / om;  // transmission in front of fragment jj
         const float wgt = fa * T_;
-        const float4 c0 = s_rec[2][k];
+        const float4 c0 = s_rec[wid][2][k];
         float cw[8] = {c0.x, c0.y, c0.z, c0.w, 0.f, 0.f, 0.f, 0.f};
         if (H4 == 4) {
-          const float4 c1 = s_rec[3 % H4][k];
+          const float4 c1 = s_rec[wid][3 % H4][k];
           cw[4] = c1.x; cw[5] = c1.y; cw[6] = c1.z; cw[7] = c1.w;
         }
         float dLdf = 0.f;
         const float iom = 1.f / om;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          gcol[c] = wgt * dC[c];
+          v[6 + c] = wgt * dC[c];
           dLdf = fmaf(dC[c], fmaf(cw[c], T_, -S[c] * iom), dLdf);
           S[c] = fmaf(cw[c], wgt, S[c]);
         }
-        if (rk >= 0 && r1.w * g < prm.f_max) {  // unclamped branch of min(f_max, alpha g)
-          gal = dLdf * g;
+        if (rkk >= 0 && r1.w * g < prm.f_max) {  // unclamped branch of min(f_max, alpha g)
+          v[5] = dLdf * g;
           const float dLdq = -dLdf * r1.w * g * kLn2;  // g = 2^-q
-          gmx = -2.f * dLdq * (r1.x * t1);
-          gmy = -2.f * dLdq * fmaf(r1.y, t1, r1.z * t2);
+          v[0] = -2.f * dLdq * (r1.x * t1);
+          v[1] = -2.f * dLdq * fmaf(r1.y, t1, r1.z * t2);
           const float dLdp = dLdq * kQScale2;  // q = kQScale2 * d^T conic d
-          gca = dLdp * dx * dx;
-          gcb = dLdp * 2.f * dx * dy;
-          gcc = dLdp * dy * dy;
+          v[2] = dLdp * dx * dx;
+          v[3] = dLdp * 2.f * dx * dy;
+          v[4] = dLdp * dy * dy;
         }
       }
-      if (rk >= 0 && __any_sync(0xffffffffu, act)) {
-        gmx = warp_sum(gmx); gmy = warp_sum(gmy);
-        gca = warp_sum(gca); gcb = warp_sum(gcb); gcc = warp_sum(gcc);
-        gal = warp_sum(gal);
-#pragma unroll
-        for (int c = 0; c < C; ++c) gcol[c] = warp_sum(gcol[c]);
-        if (lane == 0) {
-          float4 *row = reinterpret_cast<float4 *>(g2base + (int64_t)rk * G2);
-          float v[4 * ((6 + C + 3) / 4)];
-          v[0] = gmx; v[1] = gmy; v[2] = gca; v[3] = gcb; v[4] = gcc; v[5] = gal;
-#pragma unroll
-          for (int c = 0; c < C; ++c) v[6 + c] = gcol[c];
-#pragma unroll
-          for (int c = 6 + C; c < 4 * ((6 + C + 3) / 4); ++c) v[c] = 0.f;
-#pragma unroll
-          for (int q4 = 0; q4 < (6 + C + 3) / 4; ++q4)
-            atomicAdd(row + q4, make_float4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]));
+      if (rkk >= 0 && __any_sync(0xffffffffu, act)) {
+        const float tot = warp_transpose_sum<NV>(v);  // lane L: total of value L >> 1
+        const float t1v = __shfl_down_sync(0xffffffffu, tot, 2);
+        const float t2v = __shfl_down_sync(0xffffffffu, tot, 4);
+        const float t3v = __shfl_down_sync(0xffffffffu, tot, 6);
+        if ((lane & 7) == 0 && (lane >> 3) < NG) {
+          float4 *row = reinterpret_cast<float4 *>(g2base + (int64_t)rkk * G2);
+          atomicAdd(row + (lane >> 3), make_float4(tot, t1v, t2v, t3v));
         }
       }
     }
+    __syncwarp();
   }
 }
 

@@ -130,6 +130,7 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
         for (int c = 0; c < C; ++c) cc[c] = col[c];
         hot[2] = make_float4(cc[0], cc[1], cc[2], cc[3]);
         if (H4 == 4) hot[3] = make_float4(cc[4], cc[5], cc[6], cc[7]);
+        w.rec_box[(int64_t)f * N + i] = make_float2(o.rx, o.ry);
         float4 *cold = w.rec_cold + ((int64_t)f * N + i) * 2;
         cold[0] = make_float4(o.n[0], o.n[1], o.n[2], o.d0);
         cold[1] = make_float4(o.Z, __int_as_float(rk), __uint_as_float((uint32_t)tx0 | ((uint32_t)ty0 << 16)),

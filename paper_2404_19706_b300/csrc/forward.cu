@@ -5,7 +5,11 @@
 // with f > delta_alpha (the opaque-disc hit), through the ray/disc-plane intersection
 // of Eq. 4 and the cases of Eq. 5.  The masked pixels of a tile are compacted onto the
 // lowest threads, so warps without pixels skip the compositing loop (only pixels
-// covered by unstable Gaussians are rendered, Supplement B).
+// covered by unstable Gaussians are rendered, Supplement B).  After the compaction each
+// warp works alone on its 32 pixels: it walks the tile's list in batches of 32 records,
+// keeps only the records whose support box reaches the warp's pixel box (a conservative
+// test, so the result is that of the per-pixel alpha_min test), and stops as soon as all
+// its pixels have stopped.
 #include "kernels.cuh"
 #include "project.cuh"
 
@@ -17,10 +21,11 @@ __global__ void __launch_bounds__(kTilePix) k_forward(Work w, Prm prm, int64_t N
                                                       float *__restrict__ depth, float *__restrict__ alpha,
                                                       int32_t *__restrict__ index_map) {
   constexpr int H4 = (C <= 4) ? 3 : 4;
-  __shared__ float4 s_rec[H4][kTilePix];
+  constexpr int NW = kTilePix / 32;
+  __shared__ float4 s_rec[NW][H4][32];
+  __shared__ uint32_t s_j[NW][32];
   __shared__ int s_pix[kTilePix];
-  __shared__ int s_wcnt[kTilePix / 32];
-  __shared__ unsigned long long s_frag;
+  __shared__ int s_wcnt[NW];
   if (w.counters[kSkip] != 0ull) return;
   const int tile = blockIdx.x;
   if (w.tile_npix[tile] == 0u) return;
@@ -28,28 +33,37 @@ __global__ void __launch_bounds__(kTilePix) k_forward(Work w, Prm prm, int64_t N
   const DevCam &cam = w.cams[f];
   const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  // compact the masked pixels of the tile onto threads 0..npix-1
+  // compact the masked pixels of the tile onto threads 0..npix-1 (the only block barriers)
   {
     const int px = tx * kTile + (tid & (kTile - 1)), py = ty * kTile + tid / kTile;
     bool act = px < cam.W && py < cam.H;
     if (act && mask != nullptr) act = mask[((int64_t)f * cam.H + py) * cam.W + px] != 0;
     const unsigned bal = __ballot_sync(0xffffffffu, act);
     if (lane == 0) s_wcnt[wid] = __popc(bal);
-    if (tid == 0) s_frag = 0ull;
     __syncthreads();
     int before = 0;
     for (int k = 0; k < wid; ++k) before += s_wcnt[k];
     if (act) s_pix[before + __popc(bal & lanemask_lt())] = tid;
     __syncthreads();
   }
+  // From here on every warp works alone on its 32 compacted pixels.
   const int npix = (int)w.tile_npix[tile];
+  if (wid * 32 >= npix) return;
   const bool has = tid < npix;
   const int my = has ? s_pix[tid] : 0;
   const int px = tx * kTile + (my & (kTile - 1)), py = ty * kTile + my / kTile;
   const float fpx = (float)px, fpy = (float)py;
+  // bounding box of the warp's pixels: records whose support box misses it are skipped
+  const int bx0 = __reduce_min_sync(0xffffffffu, has ? px : 0x7fffffff);
+  const int bx1 = __reduce_max_sync(0xffffffffu, has ? px : -1);
+  const int by0 = __reduce_min_sync(0xffffffffu, has ? py : 0x7fffffff);
+  const int by1 = __reduce_max_sync(0xffffffffu, has ? py : -1);
+  const float wcx = 0.5f * (float)(bx0 + bx1), whx = 0.5f * (float)(bx1 - bx0);
+  const float wcy = 0.5f * (float)(by0 + by1), why = 0.5f * (float)(by1 - by0);
   const uint32_t off = w.tile_offset[tile];
   const uint32_t n = w.tile_offset[tile + 1] - off;
   const float4 *__restrict__ rec = w.rec_hot + (int64_t)f * N * H4;
+  const float2 *__restrict__ box = w.rec_box + (int64_t)f * N;
 
   float T_ = 1.f;
   float acc[C];
@@ -58,20 +72,33 @@ __global__ void __launch_bounds__(kTilePix) k_forward(Work w, Prm prm, int64_t N
   uint32_t last = 0, nfrag = 0;
   int hit_j = -1;
   bool done = !has;
-  for (uint32_t b0 = 0; b0 < n; b0 += kTilePix) {
-    if (__syncthreads_and(done)) break;
-    const uint32_t j = b0 + tid;
+  for (uint32_t b0 = 0; b0 < n; b0 += 32) {
+    if (__all_sync(0xffffffffu, done)) break;
+    // each lane fetches one record of the batch; the warp keeps those near its pixels,
+    // compacted in list order
+    const uint32_t j = b0 + lane;
+    bool keep = false;
+    float4 r[H4];
     if (j < n) {
       const uint32_t gid = w.sorted[off + j];
-      const float4 *r = rec + (int64_t)gid * H4;
+      const float4 *rp = rec + (int64_t)gid * H4;
 #pragma unroll
-      for (int k = 0; k < H4; ++k) s_rec[k][tid] = r[k];
+      for (int k = 0; k < H4; ++k) r[k] = rp[k];
+      const float2 bb = box[gid];
+      keep = fabsf(r[0].x - wcx) <= whx + bb.x && fabsf(r[0].y - wcy) <= why + bb.y;
     }
-    __syncthreads();
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (keep) {
+      const int slot = __popc(bal & lanemask_lt());
+#pragma unroll
+      for (int k = 0; k < H4; ++k) s_rec[wid][k][slot] = r[k];
+      s_j[wid][slot] = j;
+    }
+    __syncwarp();
     if (!done) {
-      const int m = (int)min((uint32_t)kTilePix, n - b0);
-      for (int k = 0; k < m; ++k) {
-        const float4 r0 = s_rec[0][k], r1 = s_rec[1][k];
+      const int cnt = __popc(bal);
+      for (int k = 0; k < cnt; ++k) {
+        const float4 r0 = s_rec[wid][0][k], r1 = s_rec[wid][1][k];
         float dx, dy, t1, t2, g;
         const float fa = footprint(fpx, fpy, r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, prm.f_max, dx, dy, t1,
                                    t2, g);
@@ -82,23 +109,22 @@ __global__ void __launch_bounds__(kTilePix) k_forward(Work w, Prm prm, int64_t N
           break;
         }
         const float wgt = fa * T_;
-        const float4 c0 = s_rec[2][k];
-        const float cv[8] = {c0.x, c0.y, c0.z, c0.w, 0.f, 0.f, 0.f, 0.f};
-        float cw[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) cw[c] = cv[c];
+        const float4 c0 = s_rec[wid][2][k];
+        float cw[8] = {c0.x, c0.y, c0.z, c0.w, 0.f, 0.f, 0.f, 0.f};
         if (H4 == 4) {
-          const float4 c1 = s_rec[3 % H4][k];
+          const float4 c1 = s_rec[wid][3 % H4][k];
           cw[4] = c1.x; cw[5] = c1.y; cw[6] = c1.z; cw[7] = c1.w;
         }
 #pragma unroll
         for (int c = 0; c < C; ++c) acc[c] = fmaf(cw[c], wgt, acc[c]);
-        if (hit_j < 0 && fa > prm.delta_alpha) hit_j = (int)(b0 + k);
+        const uint32_t jj = s_j[wid][k];
+        if (hit_j < 0 && fa > prm.delta_alpha) hit_j = (int)jj;
         T_ = Tn;
-        last = b0 + k + 1;
+        last = jj + 1;
         ++nfrag;
       }
     }
+    __syncwarp();
   }
   if (has) {
     const int64_t HW = (int64_t)cam.H * cam.W;
@@ -123,12 +149,9 @@ __global__ void __launch_bounds__(kTilePix) k_forward(Work w, Prm prm, int64_t N
     w.px_last[pix] = last;
     w.px_hit[pix] = hit_gid;
   }
-  // fragment counter (one atomic per CTA)
-  unsigned long long fr = nfrag;
-  for (int o = 16; o > 0; o >>= 1) fr += __shfl_xor_sync(0xffffffffu, fr, o);
-  if (lane == 0 && fr) atomicAdd(&s_frag, fr);
-  __syncthreads();
-  if (tid == 0 && s_frag) atomicAdd(w.counters + kFragments, s_frag);
+  // fragment counter: one atomic per warp
+  const unsigned fr = __reduce_add_sync(0xffffffffu, nfrag);
+  if (lane == 0 && fr) atomicAdd(w.counters + kFragments, (unsigned long long)fr);
 }
 
 void launch_forward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const uint8_t *mask, float *color,

@@ -15,6 +15,7 @@ struct Projected {
   float n[3];           // camera-frame disc normal (axis of the smallest scale)
   float d0;             // p_c . n_c
   int x0, y0, x1, y1;   // pixel bounding box of the alpha_min support (inclusive)
+  float rx, ry;         // half-extents of that support around mu, with a safety margin
 };
 
 // Returns false when the Gaussian is culled (behind the near plane, outside the guard
@@ -84,6 +85,8 @@ __device__ __forceinline__ bool project_gaussian(const DevCam &cam, const Prm &p
   const float pthr = 2.f * logf(P.alpha / prm.alpha_min);
   const float rx = sqrtf(pthr * a) * 1.0001f + 1e-3f;
   const float ry = sqrtf(pthr * c) * 1.0001f + 1e-3f;
+  o.rx = rx;
+  o.ry = ry;
   const float mx = o.mux.hi, my = o.muy.hi;
   float fx0 = ceilf(mx - rx), fx1 = floorf(mx + rx), fy0 = ceilf(my - ry), fy1 = floorf(my + ry);
   fx0 = fmaxf(fx0, 0.f);

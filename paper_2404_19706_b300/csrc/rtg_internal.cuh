@@ -7,6 +7,7 @@
 //            {colour 0..3}, {colour 4..7}          C = 3 uses one colour vector, C = 8 two
 //   rec_cold [F][N][2] float4     {n_c.x, n_c.y, n_c.z, d0 = p_c . n_c},
 //                                 {z_c, rank (int bits), rect lo (tx0|ty0<<16), rect hi}
+//   rec_box  [F][N] float2        half-extents of the alpha_min support box around mu
 //   ntiles   [F][N] uint32        masked tiles touched (0 = culled or off-mask)
 //   keys     [pairs] uint64       (float bits of z_c) << 32 | Gaussian index, bucketed by tile
 //   sorted   [pairs] uint32       Gaussian index, each tile's bucket in front-to-back order
@@ -70,6 +71,7 @@ struct Work {
   int32_t *block_cnt;   // [ceil(N / kScanBlock)]
   float4 *rec_hot;
   float4 *rec_cold;
+  float2 *rec_box;      // [F][N] support half-extents (rx, ry) around mu
   uint32_t *ntiles;
   uint32_t *tile_npix;  // [F*T] masked pixels per tile
   uint32_t *tile_count; // [F*T + 1]
