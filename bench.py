@@ -35,7 +35,7 @@ WORKLOAD = dict(name="masked-step room 1M Gaussians (20% unstable, 3 blobs) 640x
                 coverage=(0.25, 0.40))
 C = 3
 P_IN, R_REC, Q_PIX, G2 = 44 + 4 * C, 36 + 4 * C, 4 * C + 16, 4 * (11 + C)  # bytes per unit
-KERNELS_PER_STEP = 20  # mask 7, forward 8, loss 2, backward 2, adam 1
+KERNELS_PER_STEP = 22  # mask 8, forward 9, loss 2, backward 2, adam 1
 
 
 def parse():

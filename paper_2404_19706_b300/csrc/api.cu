@@ -100,14 +100,15 @@ rtg_status check_launch(rtg_ctx *ctx, const char *what) {
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t cams, counters, rank, ids, block_cnt, rec_hot, rec_cold, rec_box, ntiles, tile_npix, tile_count, tile_offset,
-      tile_cursor, keys, keys_alt, sorted, px_T, px_last, px_hit, grad2d, loss_part, loss_scal, loss_done, total;
+  size_t cams, counters, rank, ids, block_cnt, cand, rec_hot, rec_cold, rec_box, ntiles, tile_npix, tile_count, tile_offset,
+      tile_cursor, keys, keys_alt, stage, sorted, px_T, px_last, px_hit, grad2d, loss_part, loss_scal, loss_done, total;
 };
 
 bool capacity_ok(const rtg_capacity *c) {
   return c != nullptr && c->max_gaussians >= 0 && c->max_frames >= 1 && c->max_frames <= RTG_MAX_FRAMES &&
          c->max_width >= 1 && c->max_height >= 1 && (c->max_channels == 3 || c->max_channels == 8) &&
-         c->max_pairs >= 1 && c->max_pairs <= 0xffffffffLL;
+         c->max_pairs >= 1 && c->max_pairs <= 0xffffffffLL &&
+         (int64_t)c->max_frames * c->max_gaussians < 0xffffffffLL;
 }
 
 Layout layout_of(const rtg_capacity *c) {
@@ -130,6 +131,7 @@ Layout layout_of(const rtg_capacity *c) {
   L.rank = take(N * 4);
   L.ids = take(N * 4);
   L.block_cnt = take((N / kScanBlock + 2) * 4);
+  L.cand = take(Fm * N * 4);
   L.rec_hot = take(Fm * N * H4 * 16);
   L.rec_cold = take(Fm * N * 32);
   L.rec_box = take(Fm * N * 8);
@@ -140,6 +142,7 @@ Layout layout_of(const rtg_capacity *c) {
   L.tile_cursor = take((FT + 1) * 4);
   L.keys = take(K * 8);
   L.keys_alt = take(K * 8);
+  L.stage = take(K * 16);
   L.sorted = take(K * 4);
   L.px_T = take(P * 4);
   L.px_last = take(P * 4);
@@ -278,6 +281,7 @@ rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap) {
   w.rank = (int32_t *)(b + L.rank);
   w.ids = (int32_t *)(b + L.ids);
   w.block_cnt = (int32_t *)(b + L.block_cnt);
+  w.cand = (uint32_t *)(b + L.cand);
   w.rec_hot = (float4 *)(b + L.rec_hot);
   w.rec_cold = (float4 *)(b + L.rec_cold);
   w.rec_box = (float2 *)(b + L.rec_box);
@@ -288,6 +292,7 @@ rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap) {
   w.tile_cursor = (uint32_t *)(b + L.tile_cursor);
   w.keys = (unsigned long long *)(b + L.keys);
   w.keys_alt = (unsigned long long *)(b + L.keys_alt);
+  w.stage = (uint4 *)(b + L.stage);
   w.sorted = (uint32_t *)(b + L.sorted);
   w.px_T = (float *)(b + L.px_T);
   w.px_last = (uint32_t *)(b + L.px_last);
@@ -400,7 +405,7 @@ rtg_status rtg_render_forward(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, c
   if ((st = rank_pass(ctx, gp.unstable, n, w.rank, w.ids, w.counters, nullptr, s)) != RTG_OK) return st;
   {
     ProfScope ps(ctx, kPProject, s);
-    launch_project(gp, w, P, F, T, s);
+    launch_project(gp, w, P, F, T, false, ctx->cap.max_pairs, s);
   }
   {
     ProfScope ps(ctx, kPScanTiles, s);
@@ -408,7 +413,7 @@ rtg_status rtg_render_forward(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, c
   }
   {
     ProfScope ps(ctx, kPEmit, s);
-    launch_emit(w, n, F, T, s);
+    launch_emit(w, s);
   }
   {
     ProfScope ps(ctx, kPSortTiles, s);
@@ -550,9 +555,9 @@ rtg_status rtg_unstable_mask(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, co
   if (gp.u_means != nullptr)
     if ((st = rank_pass(ctx, gp.unstable, gp.n, ctx->w.rank, ctx->w.ids, ctx->w.counters, nullptr, s)) != RTG_OK)
       return st;
-  launch_project_unstable(gp, ctx->w, P, F, T, s);
+  launch_project(gp, ctx->w, P, F, T, true, ctx->cap.max_pairs, s);
   launch_scan_tiles(ctx->w, F * T, ctx->cap.max_pairs, s);
-  launch_emit(ctx->w, gp.n, F, T, s);
+  launch_emit(ctx->w, s);
   launch_mask_cover_tiles(ctx->w, P, gp.n, F, T, gp.C, mask, s);
   ctx->last_stream = s;
   return check_launch(ctx, "unstable_mask");

@@ -221,7 +221,8 @@ __global__ void __launch_bounds__(kTilePix) k_backward(Work w, Prm prm, int64_t 
       for (int q = 0; q < NV; ++q) v[q] = 0.f;
       if (act) {
         const float om = 1.f - fa;
-        T_ = T_ / om;  // transmission in front of fragment jj
+        const float iom = __frcp_rn(om);
+        T_ = T_ * iom;  // transmission in front of fragment jj
         const float wgt = fa * T_;
         const float4 c0 = s_rec[wid][2][k];
         float cw[8] = {c0.x, c0.y, c0.z, c0.w, 0.f, 0.f, 0.f, 0.f};
@@ -230,7 +231,6 @@ __global__ void __launch_bounds__(kTilePix) k_backward(Work w, Prm prm, int64_t 
           cw[4] = c1.x; cw[5] = c1.y; cw[6] = c1.z; cw[7] = c1.w;
         }
         float dLdf = 0.f;
-        const float iom = 1.f / om;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
           v[6 + c] = wgt * dC[c];

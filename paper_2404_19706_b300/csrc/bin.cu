@@ -33,119 +33,224 @@ __global__ void __launch_bounds__(kTilePix) k_tile_mask(FrameSet fs, Work w, con
 
 // --------------------------------------------------------------------------- unstable index
 // Two-kernel scan: per-block counts, then each block adds its predecessors' counts.
-__global__ void __launch_bounds__(kScanBlock) k_rank_count(const uint8_t *__restrict__ unstable, int64_t n,
-                                                           int32_t *__restrict__ block_cnt) {
-  const int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
-  const bool u = i < n && unstable[i] != 0;
-  const int c = __syncthreads_count(u);
+// Each thread handles kRankPer consecutive flags (one 16-byte load when aligned), so a
+// block of kRankThreads covers kRankPerBlock Gaussians.
+constexpr int kRankThreads = 256, kRankPer = 16, kRankPerBlock = kRankThreads * kRankPer;
+
+__device__ __forceinline__ uint32_t load_flags(const uint8_t *__restrict__ unstable, int64_t n, int64_t i0,
+                                               uint8_t (&f)[kRankPer]) {
+  uint32_t cnt = 0;
+  if (i0 + kRankPer <= n && ((reinterpret_cast<uintptr_t>(unstable + i0) & 15u) == 0)) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(unstable + i0);
+    const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < kRankPer; ++k) f[k] = (uint8_t)((wv[k >> 2] >> (8 * (k & 3))) & 0xffu);
+  } else {
+#pragma unroll
+    for (int k = 0; k < kRankPer; ++k) f[k] = (i0 + k < n) ? unstable[i0 + k] : (uint8_t)0;
+  }
+#pragma unroll
+  for (int k = 0; k < kRankPer; ++k) cnt += f[k] != 0;
+  return cnt;
+}
+
+__global__ void __launch_bounds__(kRankThreads) k_rank_count(const uint8_t *__restrict__ unstable, int64_t n,
+                                                             int32_t *__restrict__ block_cnt) {
+  __shared__ int s_warp[kRankThreads / 32];
+  uint8_t fl[kRankPer];
+  const int64_t i0 = ((int64_t)blockIdx.x * kRankThreads + threadIdx.x) * kRankPer;
+  const int c = block_sum_int((int)load_flags(unstable, n, i0, fl), s_warp);
   if (threadIdx.x == 0) block_cnt[blockIdx.x] = c;
 }
 
-__global__ void __launch_bounds__(kScanBlock) k_rank_write(const uint8_t *__restrict__ unstable, int64_t n,
-                                                           const int32_t *__restrict__ block_cnt,
-                                                           int32_t *__restrict__ rank, int32_t *__restrict__ ids,
-                                                           unsigned long long *nu_counter, int64_t *nu_out) {
-  __shared__ int s_warp[kScanBlock / 32];
+__global__ void __launch_bounds__(kRankThreads) k_rank_write(const uint8_t *__restrict__ unstable, int64_t n,
+                                                             const int32_t *__restrict__ block_cnt,
+                                                             int32_t *__restrict__ rank, int32_t *__restrict__ ids,
+                                                             unsigned long long *nu_counter, int64_t *nu_out) {
+  __shared__ int s_warp[kRankThreads / 32];
   __shared__ int s_base;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   // predecessors' total
   int acc = 0;
-  for (int b = threadIdx.x; b < (int)blockIdx.x; b += kScanBlock) acc += block_cnt[b];
+  for (int b = threadIdx.x; b < (int)blockIdx.x; b += kRankThreads) acc += block_cnt[b];
   acc = block_sum_int(acc, s_warp);
   if (threadIdx.x == 0) s_base = acc;
   __syncthreads();
-  const int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
-  const bool u = i < n && unstable[i] != 0;
-  const unsigned bal = __ballot_sync(0xffffffffu, u);
-  if (lane == 0) s_warp[wid] = __popc(bal);
-  __syncthreads();
-  int before = s_base;
-  for (int k = 0; k < wid; ++k) before += s_warp[k];
-  before += __popc(bal & ((1u << lane) - 1u));
-  if (i < n) {
-    if (rank != nullptr) rank[i] = u ? before : -1;
-    if (u && ids != nullptr) ids[before] = (int32_t)i;
+  uint8_t fl[kRankPer];
+  const int64_t i0 = ((int64_t)blockIdx.x * kRankThreads + threadIdx.x) * kRankPer;
+  const int mine = (int)load_flags(unstable, n, i0, fl);
+  // exclusive scan of the per-thread counts across the block
+  int inc = mine;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
   }
-  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanBlock - 1) {
-    int total = before + (u ? 1 : 0);
-    if (nu_counter != nullptr) nu_counter[kNumUnstable] = (unsigned long long)total;
-    if (nu_out != nullptr) *nu_out = total;
+  if (lane == 31) s_warp[wid] = inc;
+  __syncthreads();
+  int before = s_base + inc - mine;
+  for (int k = 0; k < wid; ++k) before += s_warp[k];
+#pragma unroll
+  for (int k = 0; k < kRankPer; ++k) {
+    const int64_t i = i0 + k;
+    if (i < n) {
+      const bool u = fl[k] != 0;
+      if (rank != nullptr) rank[i] = u ? before : -1;
+      if (u && ids != nullptr) ids[before] = (int32_t)i;
+      before += u;
+    }
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kRankThreads - 1) {
+    if (nu_counter != nullptr) nu_counter[kNumUnstable] = (unsigned long long)before;
+    if (nu_out != nullptr) *nu_out = before;
   }
 }
 
 // --------------------------------------------------------------------------- projection
-// kMask = true projects only the unstable Gaussians (for the unstable-pixel mask): no
-// gradient rows are cleared and no visibility is counted.
-template <int C, bool kMask>
-__global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, int F, int T) {
+// Two stages.  k_cull tests every (frame, Gaussian) with plain FP32 against the near plane
+// and the guard band, with a relative margin so that it never drops a pair the exact test
+// keeps, clears the tile count of the pairs it drops, and appends the rest to a dense
+// candidate list (one atomic per warp).  k_project then runs the exact double-float
+// projection over that list only, so its warps stay full.
+template <bool kMask>
+__global__ void __launch_bounds__(256) k_cull(GaussPtrs g, Work w, Prm prm, int F) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= g.n) return;
   const int64_t N = g.n;
-  if (kMask && g.unstable[i] == 0) {
-    for (int f = 0; f < F; ++f) w.ntiles[(int64_t)f * N + i] = 0u;
-    return;
+  const int lane = threadIdx.x & 31;
+  bool live = i < N;
+  if (kMask && live) live = g.unstable[i] != 0;
+  float p[3] = {0.f, 0.f, 0.f};
+  if (live) {
+    const float *pm = g.means + 3 * i;
+    if (g.u_means != nullptr) {
+      const int r = w.rank[i];
+      if (r >= 0) pm = g.u_means + 3 * (int64_t)r;
+    }
+    p[0] = pm[0]; p[1] = pm[1]; p[2] = pm[2];
   }
-  GParams P;
-  bool ok = load_params(g, w.rank, i, P);
-  const float *cp = color_ptr(g, w.rank, i);
-  float col[C];
-#pragma unroll
-  for (int c = 0; c < C; ++c) {
-    col[c] = cp[c];
-    ok = ok && isfinite(col[c]);
+  for (int f = 0; f < F; ++f) {
+    bool cand = false;
+    if (live) {
+      const DevCam &cam = w.cams[f];
+      const float d0 = p[0] - cam.t[0], d1 = p[1] - cam.t[1], d2 = p[2] - cam.t[2];
+      const float X = cam.R[0] * d0 + cam.R[3] * d1 + cam.R[6] * d2;
+      const float Y = cam.R[1] * d0 + cam.R[4] * d1 + cam.R[7] * d2;
+      const float Z = cam.R[2] * d0 + cam.R[5] * d1 + cam.R[8] * d2;
+      const float tol = 1e-4f * (fabsf(d0) + fabsf(d1) + fabsf(d2)) + 1e-6f;
+      cand = Z > prm.near_z - tol && fabsf(X) <= cam.lim_x * (Z + tol) + tol &&
+             fabsf(Y) <= cam.lim_y * (Z + tol) + tol;
+    }
+    if (i < N && !cand) w.ntiles[(int64_t)f * N + i] = 0u;
+    const unsigned bal = __ballot_sync(0xffffffffu, cand);
+    if (bal) {
+      const int leader = __ffs(bal) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(w.counters + kCand, (unsigned long long)__popc(bal));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (cand) w.cand[base + __popc(bal & lanemask_lt())] = (uint32_t)((int64_t)f * N + i);
+    }
   }
-  const int rk = w.rank[i];
-  float R[9];
-  int kmin = 0;
-  if (ok) {
-    const float qn = sqrtf(P.q[0] * P.q[0] + P.q[1] * P.q[1] + P.q[2] * P.q[2] + P.q[3] * P.q[3]);
-    quat_to_rot(P.q[0] / qn, P.q[1] / qn, P.q[2] / qn, P.q[3] / qn, R);
-    kmin = argmin3(P.s[0], P.s[1], P.s[2]);
-  }
+}
+
+// kMask = true: the unstable-mask pass (only unstable Gaussians reach this kernel through
+// k_cull<true>); no gradient rows are cleared and no visibility is counted.
+// Every pair (candidate, masked tile) is staged as (tile, slot, key): the warp reserves its
+// staging range with one atomic, and each pair's slot in its tile bucket is the value the
+// tile counter returns, so the later scatter into buckets needs no atomics.
+template <int C, bool kMask>
+__global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, int T, int64_t max_pairs) {
   constexpr int H4 = (C <= 4) ? 3 : 4;
   constexpr int G2 = (C <= 5) ? 16 : 20;
-  unsigned visible_frames = 0;
-  for (int f = 0; f < F; ++f) {
-    const DevCam &cam = w.cams[f];
-    uint32_t nt = 0;
+  const int64_t N = g.n;
+  const int64_t ncand = (int64_t)w.counters[kCand];
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < ncand; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = base + threadIdx.x;
+    uint32_t nt = 0, e = 0;
+    int f = 0, tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
+    int64_t i = 0;
+    bool ok = false;
     Projected o;
-    if (ok && project_gaussian(cam, prm, P, R, kmin, o)) {
-      const int tx0 = o.x0 / kTile, tx1 = o.x1 / kTile, ty0 = o.y0 / kTile, ty1 = o.y1 / kTile;
+    GParams P;
+    float col[C];
+    if (k < ncand) {
+      e = w.cand[k];
+      f = (int)(e / (uint64_t)N);
+      i = (int64_t)e - (int64_t)f * N;
+      ok = load_params(g, w.rank, i, P);
+      const float *cp = color_ptr(g, w.rank, i);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        col[c] = cp[c];
+        ok = ok && isfinite(col[c]);
+      }
+      if (ok) {
+        float R[9];
+        const float rq = rsqrtf(P.q[0] * P.q[0] + P.q[1] * P.q[1] + P.q[2] * P.q[2] + P.q[3] * P.q[3]);
+        quat_to_rot(P.q[0] * rq, P.q[1] * rq, P.q[2] * rq, P.q[3] * rq, R);
+        const int kmin = argmin3(P.s[0], P.s[1], P.s[2]);
+        ok = project_gaussian(w.cams[f], prm, P, R, kmin, o);
+      }
+      if (ok) {
+        const int tiles_x = w.cams[f].tiles_x;
+        tx0 = o.x0 / kTile; tx1 = o.x1 / kTile; ty0 = o.y0 / kTile; ty1 = o.y1 / kTile;
+        const uint32_t *npix = w.tile_npix + (int64_t)f * T;
+        for (int ty = ty0; ty <= ty1; ++ty)
+          for (int tx = tx0; tx <= tx1; ++tx) nt += npix[ty * tiles_x + tx] != 0u;
+      }
+    }
+    // warp-level reservation of the staging range
+    uint32_t incl = nt;
+    for (int o2 = 1; o2 < 32; o2 <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o2);
+      if (lane >= o2) incl += v;
+    }
+    const uint32_t wtotal = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned long long wbase = 0;
+    if (lane == 0 && wtotal) wbase = atomicAdd(w.counters + kStaged, (unsigned long long)wtotal);
+    wbase = __shfl_sync(0xffffffffu, wbase, 0);
+    if (ok && nt > 0) {
+      const DevCam &cam = w.cams[f];
       const uint32_t *npix = w.tile_npix + (int64_t)f * T;
       uint32_t *tcount = w.tile_count + (int64_t)f * T;
+      const unsigned long long key = ((unsigned long long)__float_as_uint(o.Z) << 32) | (unsigned long long)(uint32_t)i;
+      unsigned long long idx = wbase + incl - nt;
       for (int ty = ty0; ty <= ty1; ++ty)
         for (int tx = tx0; tx <= tx1; ++tx) {
           const int t = ty * cam.tiles_x + tx;
           if (npix[t] != 0u) {
-            ++nt;
-            atomicAdd(tcount + t, 1u);
+            const uint32_t slot = atomicAdd(tcount + t, 1u);
+            if (idx < (unsigned long long)max_pairs)
+              w.stage[idx] = make_uint4((uint32_t)((int64_t)f * T + t), slot, (uint32_t)(key & 0xffffffffull),
+                                        (uint32_t)(key >> 32));
+            ++idx;
           }
         }
-      if (nt > 0) {
-        float4 *hot = w.rec_hot + ((int64_t)f * N + i) * H4;
-        hot[0] = make_float4(o.mux.hi, o.muy.hi, o.mux.lo, o.muy.lo);
-        hot[1] = make_float4(o.u11, o.u12, o.u22, P.alpha);
-        float cc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      const int rk = w.rank[i];
+      float4 *hot = w.rec_hot + ((int64_t)f * N + i) * H4;
+      hot[0] = make_float4(o.mux.hi, o.muy.hi, o.mux.lo, o.muy.lo);
+      hot[1] = make_float4(o.u11, o.u12, o.u22, P.alpha);
+      float cc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
-        for (int c = 0; c < C; ++c) cc[c] = col[c];
-        hot[2] = make_float4(cc[0], cc[1], cc[2], cc[3]);
-        if (H4 == 4) hot[3] = make_float4(cc[4], cc[5], cc[6], cc[7]);
-        w.rec_box[(int64_t)f * N + i] = make_float2(o.rx, o.ry);
-        float4 *cold = w.rec_cold + ((int64_t)f * N + i) * 2;
-        cold[0] = make_float4(o.n[0], o.n[1], o.n[2], o.d0);
-        cold[1] = make_float4(o.Z, __int_as_float(rk), __uint_as_float((uint32_t)tx0 | ((uint32_t)ty0 << 16)),
-                              __uint_as_float((uint32_t)tx1 | ((uint32_t)ty1 << 16)));
-        if (!kMask && rk >= 0) {
-          float4 *g2 = reinterpret_cast<float4 *>(w.grad2d + ((int64_t)f * N + rk) * G2);
+      for (int c = 0; c < C; ++c) cc[c] = col[c];
+      hot[2] = make_float4(cc[0], cc[1], cc[2], cc[3]);
+      if (H4 == 4) hot[3] = make_float4(cc[4], cc[5], cc[6], cc[7]);
+      w.rec_box[(int64_t)f * N + i] = make_float2(o.rx, o.ry);
+      float4 *cold = w.rec_cold + ((int64_t)f * N + i) * 2;
+      cold[0] = make_float4(o.n[0], o.n[1], o.n[2], o.d0);
+      cold[1] = make_float4(o.Z, __int_as_float(rk), __uint_as_float((uint32_t)tx0 | ((uint32_t)ty0 << 16)),
+                            __uint_as_float((uint32_t)tx1 | ((uint32_t)ty1 << 16)));
+      if (!kMask && rk >= 0) {
+        float4 *g2 = reinterpret_cast<float4 *>(w.grad2d + ((int64_t)f * N + rk) * G2);
 #pragma unroll
-          for (int k = 0; k < G2 / 4; ++k) g2[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        ++visible_frames;
+        for (int q = 0; q < G2 / 4; ++q) g2[q] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
-    w.ntiles[(int64_t)f * N + i] = nt;
+    if (k < ncand) w.ntiles[e] = nt;
+    if (!kMask) {
+      const unsigned vis = __ballot_sync(0xffffffffu, nt > 0);
+      if (lane == 0 && vis) atomicAdd(w.counters + kVisible, (unsigned long long)__popc(vis));
+    }
   }
-  if (!kMask && visible_frames) atomicAdd(w.counters + kVisible, (unsigned long long)visible_frames);
 }
 
 // --------------------------------------------------------------------------- tile scan
@@ -188,7 +293,6 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Work w, int FT, int64_t max
   unsigned long long run = (wid > 0 ? s_warp[wid - 1] : 0ull) + inc - local;
   for (int t = b; t < e; ++t) {
     w.tile_offset[t] = (uint32_t)run;
-    w.tile_cursor[t] = 0u;
     run += w.tile_count[t];
   }
   // total masked pixels
@@ -214,29 +318,15 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Work w, int FT, int64_t max
 }
 
 // --------------------------------------------------------------------------- emission
-// Writes key = (IEEE bits of z_c) << 32 | i into the bucket of every masked tile the
-// Gaussian's support box touches.  Positive floats order like their bit patterns, so
-// sorting a bucket by key orders it by depth, then by index.
-__global__ void __launch_bounds__(256) k_emit(Work w, int64_t N, int F, int T) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N || w.counters[kSkip] != 0ull) return;
-  for (int f = 0; f < F; ++f) {
-    if (w.ntiles[(int64_t)f * N + i] == 0u) continue;
-    const int tiles_x = w.cams[f].tiles_x;
-    const float4 c1 = w.rec_cold[((int64_t)f * N + i) * 2 + 1];
-    const uint32_t lo = __float_as_uint(c1.z), hi = __float_as_uint(c1.w);
-    const int tx0 = lo & 0xffff, ty0 = lo >> 16, tx1 = hi & 0xffff, ty1 = hi >> 16;
-    const unsigned long long key = ((unsigned long long)__float_as_uint(c1.x) << 32) | (unsigned long long)(uint32_t)i;
-    const uint32_t *npix = w.tile_npix + (int64_t)f * T;
-    for (int ty = ty0; ty <= ty1; ++ty)
-      for (int tx = tx0; tx <= tx1; ++tx) {
-        const int t = ty * tiles_x + tx;
-        if (npix[t] != 0u) {
-          const int64_t gt = (int64_t)f * T + t;
-          const uint32_t slot = atomicAdd(w.tile_cursor + gt, 1u);
-          w.keys[(int64_t)w.tile_offset[gt] + slot] = key;
-        }
-      }
+// Scatters every staged pair into its tile bucket: key = (IEEE bits of z_c) << 32 | i.
+// Positive floats order like their bit patterns, so sorting a bucket by key orders it by
+// depth, then by index.
+__global__ void __launch_bounds__(256) k_emit(Work w) {
+  if (w.counters[kSkip] != 0ull) return;
+  const int64_t npairs = (int64_t)w.counters[kStaged];
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < npairs; k += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 st = w.stage[k];
+    w.keys[(int64_t)w.tile_offset[st.x] + st.y] = ((unsigned long long)st.w << 32) | (unsigned long long)st.z;
   }
 }
 
@@ -247,36 +337,34 @@ void launch_tile_mask(const FrameSet &fs, const Work &w, const uint8_t *mask, in
 void launch_rank(const uint8_t *unstable, int64_t n, int32_t *block_cnt, int32_t *rank, int32_t *ids,
                  unsigned long long *nu_counter, int64_t *nu_out, cudaStream_t s) {
   if (n <= 0) return;
-  const int nb = (int)((n + kScanBlock - 1) / kScanBlock);
-  k_rank_count<<<nb, kScanBlock, 0, s>>>(unstable, n, block_cnt);
-  k_rank_write<<<nb, kScanBlock, 0, s>>>(unstable, n, block_cnt, rank, ids, nu_counter, nu_out);
+  const int nb = (int)((n + kRankPerBlock - 1) / kRankPerBlock);  // <= ceil(n / kScanBlock) entries of block_cnt
+  k_rank_count<<<nb, kRankThreads, 0, s>>>(unstable, n, block_cnt);
+  k_rank_write<<<nb, kRankThreads, 0, s>>>(unstable, n, block_cnt, rank, ids, nu_counter, nu_out);
 }
 
-void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, int T, cudaStream_t s) {
+void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, int T, bool unstable_only,
+                    int64_t max_pairs, cudaStream_t s) {
   if (g.n <= 0) return;
   const unsigned nb = (unsigned)((g.n + 255) / 256);
-  if (g.C == 3)
-    k_project<3, false><<<nb, 256, 0, s>>>(g, w, prm, F, T);
-  else
-    k_project<8, false><<<nb, 256, 0, s>>>(g, w, prm, F, T);
-}
-
-void launch_project_unstable(const GaussPtrs &g, const Work &w, const Prm &prm, int F, int T, cudaStream_t s) {
-  if (g.n <= 0) return;
-  const unsigned nb = (unsigned)((g.n + 255) / 256);
-  if (g.C == 3)
-    k_project<3, true><<<nb, 256, 0, s>>>(g, w, prm, F, T);
-  else
-    k_project<8, true><<<nb, 256, 0, s>>>(g, w, prm, F, T);
+  if (unstable_only) {
+    k_cull<true><<<nb, 256, 0, s>>>(g, w, prm, F);
+    if (g.C == 3)
+      k_project<3, true><<<kPersistBlocks, 256, 0, s>>>(g, w, prm, T, max_pairs);
+    else
+      k_project<8, true><<<kPersistBlocks, 256, 0, s>>>(g, w, prm, T, max_pairs);
+  } else {
+    k_cull<false><<<nb, 256, 0, s>>>(g, w, prm, F);
+    if (g.C == 3)
+      k_project<3, false><<<kPersistBlocks, 256, 0, s>>>(g, w, prm, T, max_pairs);
+    else
+      k_project<8, false><<<kPersistBlocks, 256, 0, s>>>(g, w, prm, T, max_pairs);
+  }
 }
 
 void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, cudaStream_t s) {
   k_scan_tiles<<<1, 1024, 0, s>>>(w, FT, max_pairs);
 }
 
-void launch_emit(const Work &w, int64_t N, int F, int T, cudaStream_t s) {
-  if (N <= 0) return;
-  k_emit<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(w, N, F, T);
-}
+void launch_emit(const Work &w, cudaStream_t s) { k_emit<<<kPersistBlocks, 256, 0, s>>>(w); }
 
 }  // namespace rtg

@@ -41,10 +41,10 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 void launch_tile_mask(const FrameSet &fs, const Work &w, const uint8_t *mask, int T, cudaStream_t s);
 void launch_rank(const uint8_t *unstable, int64_t n, int32_t *block_cnt, int32_t *rank, int32_t *ids,
                  unsigned long long *nu_counter, int64_t *nu_out, cudaStream_t s);
-void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, int T, cudaStream_t s);
-void launch_project_unstable(const GaussPtrs &g, const Work &w, const Prm &prm, int F, int T, cudaStream_t s);
+void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, int T, bool unstable_only,
+                    int64_t max_pairs, cudaStream_t s);
 void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, cudaStream_t s);
-void launch_emit(const Work &w, int64_t N, int F, int T, cudaStream_t s);
+void launch_emit(const Work &w, cudaStream_t s);
 // sort.cu
 void launch_sort_tiles(const Work &w, int FT, cudaStream_t s);
 // forward.cu

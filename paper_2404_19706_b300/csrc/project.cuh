@@ -30,7 +30,8 @@ __device__ __forceinline__ bool project_gaussian(const DevCam &cam, const Prm &p
   df Y = df_add(df_add(df_mul_f(d0, cam.R[1]), df_mul_f(d1, cam.R[4])), df_mul_f(d2, cam.R[7]));
   df Z = df_add(df_add(df_mul_f(d0, cam.R[2]), df_mul_f(d1, cam.R[5])), df_mul_f(d2, cam.R[8]));
   if (!(Z.hi > prm.near_z)) return false;
-  df tx = df_div(X, Z), ty = df_div(Y, Z);
+  const float rz = __fdividef(1.f, Z.hi);
+  df tx = df_div_rcp(X, Z, rz), ty = df_div_rcp(Y, Z, rz);
   if (!(fabsf(tx.hi) <= cam.lim_x) || !(fabsf(ty.hi) <= cam.lim_y)) return false;
   o.mux = df_add(df_mul_f(tx, cam.fx), df{cam.cx, 0.f});
   o.muy = df_add(df_mul_f(ty, cam.fy), df{cam.cy, 0.f});
@@ -44,7 +45,7 @@ __device__ __forceinline__ bool project_gaussian(const DevCam &cam, const Prm &p
     for (int cc = 0; cc < 3; ++cc)
       A[3 * r + cc] = cam.R[r] * R[cc] + cam.R[3 + r] * R[3 + cc] + cam.R[6 + r] * R[6 + cc];
   // M = J A S with J the perspective Jacobian at the centre; Sigma_2D = M M^T + lowpass I
-  const float iz = 1.f / Zf;
+  const float iz = rz;
   const float j00 = cam.fx * iz, j02 = -cam.fx * Xf * iz * iz;
   const float j11 = cam.fy * iz, j12 = -cam.fy * Yf * iz * iz;
   float a0 = 0.f, b0 = 0.f, c0 = 0.f;
@@ -73,16 +74,16 @@ __device__ __forceinline__ bool project_gaussian(const DevCam &cam, const Prm &p
   if (2.f * b0 * b0 > a * c) b = copysignf(sqrtf(fmaxf(fmaf(a, c, -det), 0.f)), b0);
   if (!(det > 0.f)) return false;
   // Cholesky factor of the conic: Sigma_2D^-1 = U^T U, U = [[sqrt(c/det), -b/sqrt(c det)], [0, 1/sqrt(c)]]
-  const float sc = sqrtf(c), sd = sqrtf(det);
-  o.u11 = kQScale * (sc / sd);
-  o.u12 = -kQScale * (b / (sc * sd));
-  o.u22 = kQScale / sc;
+  const float isc = rsqrtf(c), isd = rsqrtf(det);
+  o.u11 = kQScale * (c * isc * isd);
+  o.u12 = -kQScale * (b * isc * isd);
+  o.u22 = kQScale * isc;
   o.a = a;
   o.c = c;
   // support f >= alpha_min  <=>  d^T Sigma_2D^-1 d <= 2 ln(alpha / alpha_min); its x extent is
   // sqrt(that * a), its y extent sqrt(that * c).  A small margin keeps the box a superset.
   if (!(P.alpha >= prm.alpha_min)) return false;
-  const float pthr = 2.f * logf(P.alpha / prm.alpha_min);
+  const float pthr = 2.f * __logf(P.alpha / prm.alpha_min);
   const float rx = sqrtf(pthr * a) * 1.0001f + 1e-3f;
   const float ry = sqrtf(pthr * c) * 1.0001f + 1e-3f;
   o.rx = rx;

@@ -9,6 +9,8 @@
 //                                 {z_c, rank (int bits), rect lo (tx0|ty0<<16), rect hi}
 //   rec_box  [F][N] float2        half-extents of the alpha_min support box around mu
 //   ntiles   [F][N] uint32        masked tiles touched (0 = culled or off-mask)
+//   cand     [F*N] uint32         (frame, Gaussian) pairs f * N + i that passed the coarse cull
+//   stage    [pairs] uint4        (tile, slot, key) of every pair, written by the projection
 //   keys     [pairs] uint64       (float bits of z_c) << 32 | Gaussian index, bucketed by tile
 //   sorted   [pairs] uint32       Gaussian index, each tile's bucket in front-to-back order
 //   px_*     [F][H][W]            per-pixel state saved by the forward for the backward
@@ -39,7 +41,9 @@ enum Counter {
   kNumUnstable = 4,
   kMaxTilePairs = 5,
   kSkip = 6,  // non-zero: pairs overflowed, downstream kernels skip
-  kNumCounters = 8
+  kCand = 7,  // (frame, Gaussian) candidates that passed the coarse cull
+  kStaged = 8,  // (Gaussian, tile) pairs staged by the projection for the scatter into buckets
+  kNumCounters = 16
 };
 
 struct DevCam {
@@ -69,6 +73,7 @@ struct Work {
   int32_t *rank;        // [N] compact unstable index, -1 if stable
   int32_t *ids;         // [N] compact -> original index
   int32_t *block_cnt;   // [ceil(N / kScanBlock)]
+  uint32_t *cand;       // [F*N] candidates f * N + i of the coarse cull, dense, in no particular order
   float4 *rec_hot;
   float4 *rec_cold;
   float2 *rec_box;      // [F][N] support half-extents (rx, ry) around mu
@@ -79,6 +84,7 @@ struct Work {
   uint32_t *tile_cursor;// [F*T]
   unsigned long long *keys;
   unsigned long long *keys_alt;
+  uint4 *stage;         // [pairs] (global tile, slot in its bucket, key lo, key hi)
   uint32_t *sorted;
   float *px_T;
   uint32_t *px_last;
@@ -139,6 +145,13 @@ __device__ __forceinline__ df df_div(df a, df b) {
   df r = df_add(a, df_mul_f(b, -q1));
   float q2 = __fdiv_rn(r.hi, b.hi);
   return quick_two_sum(q1, q2);
+}
+
+// a / b in double-float given rb ~ 1/b.hi (a few ulp suffice: the remainder step corrects q1)
+__device__ __forceinline__ df df_div_rcp(df a, df b, float rb) {
+  const float q1 = __fmul_rn(a.hi, rb);
+  const df r = df_add(a, df_mul_f(b, -q1));
+  return quick_two_sum(q1, __fmul_rn(r.hi, rb));
 }
 
 // ----------------------------------------------------------------------------- small math
