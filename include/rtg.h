@@ -166,6 +166,14 @@ rtg_status rtg_adam_step(int64_t nu, int32_t C, float *means, float *scales, flo
                          const float *g_opacity, const float *g_colors, float *m, float *v, int32_t step,
                          const rtg_adam_params *hp, void *stream);
 
+/* The same Adam step with its count kept on the device: *step_counter (device int32,
+ * start it at 0) is incremented first and the bias corrections use the new value, so the
+ * call needs no host-side step number and can be replayed from a captured CUDA graph. */
+rtg_status rtg_adam_step_counted(int64_t nu, int32_t C, float *means, float *scales, float *quats, float *opacity,
+                                 float *colors, const float *g_means, const float *g_scales, const float *g_quats,
+                                 const float *g_opacity, const float *g_colors, float *m, float *v,
+                                 int32_t *step_counter, const rtg_adam_params *hp, void *stream);
+
 /* Unstable-subset helpers: ids[k] = index of the k-th unstable Gaussian (ascending),
  * *nu_out (device int64) = their count.  gather copies full rows into compact arrays;
  * scatter writes compact rows back into the full arrays. */

@@ -16,6 +16,7 @@ from .api import (  # noqa: E402,F401
     RenderSettings,
     RTGError,
     adam_step,
+    adam_step_counted,
     debug_binning,
     gather_unstable,
     get_stats,

@@ -70,6 +70,8 @@ SIGNATURES = [
     ("rtg_render_backward", c_int32, [c_void_p] + [c_void_p] * 7 + [c_void_p]),
     ("rtg_adam_step", c_int32, [c_int64, c_int32] + [c_void_p] * 12 + [c_int32, POINTER(rtg_adam_params),
                                                                        c_void_p]),
+    ("rtg_adam_step_counted", c_int32, [c_int64, c_int32] + [c_void_p] * 13 + [POINTER(rtg_adam_params),
+                                                                                c_void_p]),
     ("rtg_unstable_index", c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("rtg_unstable_index_static", c_int32, [c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("rtg_gather_unstable", c_int32, [c_int64, c_int32] + [c_void_p] * 11 + [c_void_p]),

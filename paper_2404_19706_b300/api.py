@@ -276,6 +276,19 @@ def adam_step(params: Sequence[torch.Tensor], grads: Sequence[torch.Tensor], m: 
     _check(st, "rtg_adam_step")
 
 
+def adam_step_counted(params: Sequence[torch.Tensor], grads: Sequence[torch.Tensor], m: torch.Tensor,
+                      v: torch.Tensor, step_counter: torch.Tensor, hp: AdamSettings = AdamSettings(), stream=None):
+    """Adam with the step count in device memory (int32 [1], incremented by the call)."""
+    means, scales, quats, opacity, colors = params
+    nu, C = int(means.shape[0]), int(colors.shape[1])
+    c = hp.to_c()
+    ptrs = [_ptr(t, torch.float32, "param") for t in params] + [_ptr(t, torch.float32, "grad") for t in grads]
+    st = _lib.load().rtg_adam_step_counted(nu, C, *ptrs, _ptr(m, torch.float32, "m"), _ptr(v, torch.float32, "v"),
+                                           _ptr(step_counter, torch.int32, "step_counter"), ctypes.byref(c),
+                                           _stream(stream))
+    _check(st, "rtg_adam_step_counted")
+
+
 def unstable_index(ctx: Context, unstable: torch.Tensor, stream=None):
     """Returns (ids int32 [nu] on the device, nu).  Synchronises to read the count."""
     n = int(unstable.shape[0])

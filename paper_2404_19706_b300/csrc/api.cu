@@ -305,6 +305,7 @@ rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap) {
   // zero the small bookkeeping region once (counters, loss ticket)
   cudaMemset(ctx->slab + L.counters, 0, kNumCounters * sizeof(unsigned long long));
   cudaMemset(ctx->slab + L.loss_done, 0, 4);
+  init_sort_attributes();
   if (cudaDeviceSynchronize() != cudaSuccess) {
     cudaGetLastError();
     cudaFreeHost(ctx->status_host);
@@ -488,7 +489,21 @@ rtg_status rtg_adam_step(int64_t nu, int32_t C, float *means, float *scales, flo
   const double bc1 = 1.0 / (1.0 - pow((double)hp->beta1, step));
   const double bc2s = 1.0 / sqrt(1.0 - pow((double)hp->beta2, step));
   launch_adam(nu, C, means, scales, quats, opacity, colors, g_means, g_scales, g_quats, g_opacity, g_colors, m, v,
-              *hp, (float)bc1, (float)bc2s, (cudaStream_t)stream);
+              *hp, (float)bc1, (float)bc2s, nullptr, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? RTG_OK : RTG_ERR_CUDA;
+}
+
+rtg_status rtg_adam_step_counted(int64_t nu, int32_t C, float *means, float *scales, float *quats, float *opacity,
+                                 float *colors, const float *g_means, const float *g_scales, const float *g_quats,
+                                 const float *g_opacity, const float *g_colors, float *m, float *v,
+                                 int32_t *step_counter, const rtg_adam_params *hp, void *stream) {
+  if (nu < 0 || C < 1 || C > 64 || hp == nullptr || step_counter == nullptr) return RTG_ERR_ARG;
+  if (nu == 0) return RTG_OK;
+  if (!means || !scales || !quats || !opacity || !colors || !g_means || !g_scales || !g_quats || !g_opacity ||
+      !g_colors || !m || !v)
+    return RTG_ERR_ARG;
+  launch_adam(nu, C, means, scales, quats, opacity, colors, g_means, g_scales, g_quats, g_opacity, g_colors, m, v,
+              *hp, 1.f, 1.f, step_counter, (cudaStream_t)stream);
   return cudaGetLastError() == cudaSuccess ? RTG_OK : RTG_ERR_CUDA;
 }
 

@@ -47,6 +47,7 @@ void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, cudaStream_t s)
 void launch_emit(const Work &w, cudaStream_t s);
 // sort.cu
 void launch_sort_tiles(const Work &w, int FT, cudaStream_t s);
+void init_sort_attributes();
 // forward.cu
 void launch_forward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const uint8_t *mask, float *color,
                     float *depth, float *alpha, int32_t *index_map, cudaStream_t s);
@@ -62,7 +63,7 @@ void launch_l1_loss(const Work &w, int F, int C, int H, int W, const float *colo
 void launch_adam(int64_t nu, int C, float *means, float *scales, float *quats, float *opacity, float *colors,
                  const float *g_means, const float *g_scales, const float *g_quats, const float *g_opacity,
                  const float *g_colors, float *m, float *v, const rtg_adam_params &hp, float bc1, float bc2_sqrt,
-                 cudaStream_t s);
+                 int32_t *step_dev, cudaStream_t s);
 void launch_gather(int64_t nu, int C, const int32_t *ids, const float *means, const float *scales,
                    const float *quats, const float *opacity, const float *colors, float *um, float *us, float *uq,
                    float *uo, float *uc, cudaStream_t s);

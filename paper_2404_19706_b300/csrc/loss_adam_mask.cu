@@ -123,7 +123,12 @@ __global__ void __launch_bounds__(256) k_adam(int64_t nu, int C, float *__restri
                                               const float *__restrict__ g_scales, const float *__restrict__ g_quats,
                                               const float *__restrict__ g_opacity, const float *__restrict__ g_colors,
                                               float *__restrict__ m, float *__restrict__ v, rtg_adam_params hp,
-                                              float bc1, float bc2_sqrt) {
+                                              float bc1, float bc2_sqrt, const int32_t *__restrict__ step_dev) {
+  if (step_dev != nullptr) {  // bias corrections from the device step counter
+    const float t = (float)*step_dev;
+    bc1 = 1.f / (1.f - powf(hp.beta1, t));
+    bc2_sqrt = rsqrtf(1.f - powf(hp.beta2, t));
+  }
   const int64_t total = nu * (11 + C);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     float *param;
@@ -247,15 +252,19 @@ void launch_l1_loss(const Work &w, int F, int C, int H, int W, const float *colo
   k_loss_grad<<<kLossBlocks, 256, 0, s>>>(w, F, C, H, W, color, depth, tcolor, tdepth, mask, dL_dcolor, dL_ddepth);
 }
 
+__global__ void k_step_increment(int32_t *step) { *step += 1; }
+
 void launch_adam(int64_t nu, int C, float *means, float *scales, float *quats, float *opacity, float *colors,
                  const float *g_means, const float *g_scales, const float *g_quats, const float *g_opacity,
                  const float *g_colors, float *m, float *v, const rtg_adam_params &hp, float bc1, float bc2_sqrt,
-                 cudaStream_t s) {
+                 int32_t *step_dev, cudaStream_t s) {
+  if (step_dev != nullptr) k_step_increment<<<1, 1, 0, s>>>(step_dev);
   if (nu <= 0) return;
   const int64_t total = nu * (11 + C);
   const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)kPersistBlocks * 4);
   k_adam<<<blocks, 256, 0, s>>>(nu, C, means, scales, quats, opacity, colors, g_means, g_scales,
-                                                      g_quats, g_opacity, g_colors, m, v, hp, bc1, bc2_sqrt);
+                                                      g_quats, g_opacity, g_colors, m, v, hp, bc1, bc2_sqrt,
+                                    step_dev);
 }
 
 void launch_gather(int64_t nu, int C, const int32_t *ids, const float *means, const float *scales,

@@ -187,12 +187,11 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(Work w) {
   for (uint32_t j = threadIdx.x; j < n; j += kSortThreads) w.sorted[off + j] = (uint32_t)src[j];
 }
 
+void init_sort_attributes() {
+  cudaFuncSetAttribute(k_sort_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SortSmem));
+}
+
 void launch_sort_tiles(const Work &w, int FT, cudaStream_t s) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_sort_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SortSmem));
-    attr_set = true;
-  }
   k_sort_tiles<<<FT, kSortThreads, sizeof(SortSmem), s>>>(w);
 }
 

@@ -77,14 +77,25 @@ def rasterize(u_params: Sequence[torch.Tensor], state: RasterState):
 
 
 class MaskedStep:
-    """One masked optimisation iteration per ``step()`` call, on preallocated buffers."""
+    """One masked optimisation iteration per ``step()`` call, on preallocated buffers.
+
+    With ``recompute_mask`` the unstable-pixel mask (Supplement B) is rebuilt from the
+    current unstable parameters at the start of every iteration, so one call runs the whole
+    path: mask, forward, L1 loss, backward, Adam.  ``capture()`` records one iteration in a
+    CUDA graph; later ``step()`` calls replay it (same cameras and buffers; the Adam step
+    count lives on the device).
+    """
 
     def __init__(self, ctx: Context, g: Gaussians, cams, mask: Optional[torch.Tensor], target_color: torch.Tensor,
                  target_depth: torch.Tensor, settings: RenderSettings = RenderSettings(),
-                 adam: AdamSettings = AdamSettings(), w_color: float = 1.0, w_depth: float = 1.0):
+                 adam: AdamSettings = AdamSettings(), w_color: float = 1.0, w_depth: float = 1.0,
+                 recompute_mask: bool = False):
         self.ctx, self.settings, self.adam = ctx, settings, adam
         self.cams = cams if isinstance(cams, (list, tuple)) else [cams]
         self.mask = mask
+        self.recompute_mask = recompute_mask
+        if recompute_mask and mask is None:
+            raise ValueError("recompute_mask needs a mask buffer")
         self.w_color, self.w_depth = w_color, w_depth
         self.ids, self.nu = api.unstable_index(ctx, g.unstable)
         self.u = api.gather_unstable(self.ids, g)
@@ -98,21 +109,39 @@ class MaskedStep:
         self.dL_dcolor = torch.zeros_like(self.state.color)
         self.dL_ddepth = torch.zeros_like(self.state.depth)
         self.grads = [torch.zeros_like(t) for t in self.u]
-        self.m = torch.zeros(self.nu, 11 + C, device=dev)
-        self.v = torch.zeros(self.nu, 11 + C, device=dev)
-        self.t = 0
+        self.m = torch.zeros(self.nu * (11 + C), device=dev)
+        self.v = torch.zeros(self.nu * (11 + C), device=dev)
+        self.step_counter = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.graph = None
 
-    def step(self, stream=None):
-        """Forward, L1 loss, backward and Adam; returns the device loss tensor (L, Lc, Ld)."""
+    def _body(self, stream=None):
         s = self.state
+        if self.recompute_mask:
+            api.unstable_mask(self.ctx, self.cams, self.g, self.settings, self.mask, stream)
         api.render_forward(self.ctx, self.cams, self.g, self.mask, self.settings, s.color, s.depth, s.alpha, None,
                            stream)
         api.l1_loss(self.ctx, s.color, s.depth, self.target_color, self.target_depth, self.mask, self.w_color,
                     self.w_depth, self.loss, self.dL_dcolor, self.dL_ddepth, stream)
         api.render_backward(self.ctx, self.dL_dcolor, self.dL_ddepth, *self.grads, stream=stream)
-        self.t += 1
-        api.adam_step(self.u, self.grads, self.m, self.v, self.t, self.adam, stream)
+        api.adam_step_counted(self.u, self.grads, self.m, self.v, self.step_counter, self.adam, stream)
         return self.loss
+
+    def step(self, stream=None):
+        """Mask (optional), forward, L1 loss, backward and Adam; returns the device loss (L, Lc, Ld)."""
+        if self.graph is not None:
+            self.graph.replay()
+            return self.loss
+        return self._body(stream)
+
+    def capture(self):
+        """Record one iteration in a CUDA graph (run at least one eager step() first)."""
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            self._body()
+        torch.cuda.synchronize()
+        self.graph = graph
+        return graph
 
     def write_back(self, stream=None):
         """Scatter the optimised compact parameters into the full arrays (end of a window)."""
