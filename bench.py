@@ -35,7 +35,7 @@ WORKLOAD = dict(name="masked-step room 1M Gaussians (20% unstable, 3 blobs) 640x
                 coverage=(0.25, 0.40))
 C = 3
 P_IN, R_REC, Q_PIX, G2 = 44 + 4 * C, 36 + 4 * C, 4 * C + 16, 4 * (11 + C)  # bytes per unit
-KERNELS_PER_STEP = 23  # mask 8, forward 9, loss 2, backward 2, adam 2
+KERNELS_PER_STEP = 19  # mask 6, forward 7, loss finalize 1, backward 2, adam 2, scatter 1
 
 
 def parse():
@@ -297,9 +297,9 @@ def run_ours(args):
         "scan_tiles": FT * 16,
         "emit": K * 12,
         "sort_tiles": K * 24,
-        "forward": K * R_REC + P * Q_PIX,
-        "l1_loss": 3 * P * (4 * C + 4),
-        "backward": K * R_REC + P * (Q_PIX + 4 * C + 4) + Nu * G2,
+        "forward": K * R_REC + P * (Q_PIX + 4 * C + 4),
+        "l1_loss": FT * 8 * 12,
+        "backward": K * R_REC + P * (Q_PIX + 2 * (4 * C + 4)) + Nu * G2,
         "project_backward": Nu * (G2 + 2 * P_IN),
         "adam": Nu * P_IN * 7,
     }

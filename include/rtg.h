@@ -72,13 +72,19 @@ typedef struct {
  * Optional compact overrides u_*: when u_means is non-NULL, the parameters of the
  * k-th unstable Gaussian (ascending index) are read from u_means[k], u_scales[k], ...
  * instead of the full arrays, so an optimiser can own compact [n_unstable, .] leaves.
- * Either all five u_* pointers are set or none. */
+ * Either all five u_* pointers are set or none.
+ * Optional precomputed unstable index (from rtg_unstable_rank, valid while the flags do
+ * not change, e.g. for a whole optimisation window): rank_map [n] int32 (compact index of
+ * Gaussian i, -1 if stable), unstable_ids [n_unstable] int32 ascending, and their count.
+ * When rank_map is non-NULL the calls skip recomputing the index. */
 typedef struct {
   int64_t n;
   int32_t channels; /* 3 (RGB) or 8 (feature channels) */
   const float *means, *scales, *quats, *opacity, *colors;
   const uint8_t *unstable;
   const float *u_means, *u_scales, *u_quats, *u_opacity, *u_colors;
+  const int32_t *rank_map, *unstable_ids;
+  int64_t n_unstable;
 } rtg_gaussians;
 
 /* Workspace capacity; every later call must stay within it. */
@@ -153,6 +159,19 @@ rtg_status rtg_l1_loss(rtg_ctx *ctx, int32_t F, int32_t C, int32_t H, int32_t W,
 rtg_status rtg_render_backward(rtg_ctx *ctx, const float *dL_dcolor, const float *dL_ddepth, float *g_means,
                                float *g_scales, float *g_quats, float *g_opacity, float *g_colors, void *stream);
 
+/* The forward fused with the L1 losses: renders as rtg_render_forward and, in the same
+ * pass, accumulates the terms of Eq. 7 against target_color [F,C,H,W] and target_depth
+ * [F,H,W] (device); loss_out (device float[3]) receives (L, L_color, L_depth) exactly as
+ * rtg_l1_loss defines them.  rtg_render_backward_l1 is then the backward of that loss: it
+ * forms dL/dC_hat and dL/dD_hat per pixel itself, so no gradient images are written or
+ * read.  The targets and outputs must stay unchanged until that backward has run. */
+rtg_status rtg_render_forward_l1(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, const rtg_gaussians *g,
+                                 const uint8_t *mask, const rtg_render_params *prm, const float *target_color,
+                                 const float *target_depth, float w_color, float w_depth, float *color, float *depth,
+                                 float *alpha, int32_t *index_map, float *loss_out, void *stream);
+rtg_status rtg_render_backward_l1(rtg_ctx *ctx, float *g_means, float *g_scales, float *g_quats, float *g_opacity,
+                                  float *g_colors, void *stream);
+
 /* Adam (Kingma & Ba, Algorithm 1) on compact unstable parameters, in place, with the
  * per-group learning rates of Supplement C.  The scale is optimised in log space
  * (s <- s * exp(-step), gradient s * dL/ds).  m and v hold nu * (11 + C) float32 each,
@@ -179,6 +198,10 @@ rtg_status rtg_adam_step_counted(int64_t nu, int32_t C, float *means, float *sca
  * scatter writes compact rows back into the full arrays. */
 rtg_status rtg_unstable_index(rtg_ctx *ctx, int64_t n, const uint8_t *unstable, int32_t *ids, int64_t *nu_out,
                               void *stream);
+/* As rtg_unstable_index, and also rank[n] (device int32): the compact index of Gaussian i
+ * among the unstable ones, -1 if it is stable.  Feeds rtg_gaussians.rank_map. */
+rtg_status rtg_unstable_rank(rtg_ctx *ctx, int64_t n, const uint8_t *unstable, int32_t *rank, int32_t *ids,
+                             int64_t *nu_out, void *stream);
 rtg_status rtg_gather_unstable(int64_t nu, int32_t C, const int32_t *ids, const float *means, const float *scales,
                                const float *quats, const float *opacity, const float *colors, float *u_means,
                                float *u_scales, float *u_quats, float *u_opacity, float *u_colors, void *stream);

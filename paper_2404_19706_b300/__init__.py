@@ -27,10 +27,13 @@ from .api import (  # noqa: E402,F401
     profile_enable,
     profile_read,
     render_backward,
+    render_backward_l1,
+    render_forward_l1,
     render_forward,
     reset_status,
     scatter_unstable,
     unstable_index,
+    unstable_rank,
     unstable_mask,
     workspace_size,
 )

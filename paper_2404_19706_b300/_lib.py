@@ -38,7 +38,8 @@ class rtg_render_params(Structure):
 class rtg_gaussians(Structure):
     _fields_ = [("n", c_int64), ("channels", c_int32)] + [
         (k, c_void_p) for k in ("means", "scales", "quats", "opacity", "colors", "unstable",
-                                "u_means", "u_scales", "u_quats", "u_opacity", "u_colors")]
+                                "u_means", "u_scales", "u_quats", "u_opacity", "u_colors",
+                                "rank_map", "unstable_ids")] + [("n_unstable", c_int64)]
 
 
 class rtg_capacity(Structure):
@@ -67,12 +68,17 @@ SIGNATURES = [
                                      POINTER(rtg_render_params), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("rtg_l1_loss", c_int32, [c_void_p, c_int32, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
                               c_void_p, c_float, c_float, c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("rtg_render_forward_l1", c_int32, [c_void_p, POINTER(rtg_camera), c_int32, POINTER(rtg_gaussians), c_void_p,
+                                        POINTER(rtg_render_params), c_void_p, c_void_p, c_float, c_float, c_void_p,
+                                        c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("rtg_render_backward_l1", c_int32, [c_void_p] + [c_void_p] * 5 + [c_void_p]),
     ("rtg_render_backward", c_int32, [c_void_p] + [c_void_p] * 7 + [c_void_p]),
     ("rtg_adam_step", c_int32, [c_int64, c_int32] + [c_void_p] * 12 + [c_int32, POINTER(rtg_adam_params),
                                                                        c_void_p]),
     ("rtg_adam_step_counted", c_int32, [c_int64, c_int32] + [c_void_p] * 13 + [POINTER(rtg_adam_params),
                                                                                 c_void_p]),
     ("rtg_unstable_index", c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("rtg_unstable_rank", c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("rtg_unstable_index_static", c_int32, [c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("rtg_gather_unstable", c_int32, [c_int64, c_int32] + [c_void_p] * 11 + [c_void_p]),
     ("rtg_scatter_unstable", c_int32, [c_int64, c_int32] + [c_void_p] * 11 + [c_void_p]),

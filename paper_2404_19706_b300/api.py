@@ -124,6 +124,9 @@ class Gaussians:
     u_quats: Optional[torch.Tensor] = None
     u_opacity: Optional[torch.Tensor] = None
     u_colors: Optional[torch.Tensor] = None
+    rank_map: Optional[torch.Tensor] = None      # optional precomputed unstable index (int32 [N])
+    unstable_ids: Optional[torch.Tensor] = None  # int32 [Nu], ascending
+    n_unstable: int = 0
 
     @property
     def n(self) -> int:
@@ -149,6 +152,10 @@ class Gaussians:
         for name in ("u_means", "u_scales", "u_quats", "u_opacity", "u_colors"):
             v = getattr(self, name)
             setattr(g, name, _ptr(v, torch.float32, name) if v is not None else None)
+        if self.rank_map is not None:
+            g.rank_map = _ptr(self.rank_map, torch.int32, "rank_map")
+            g.unstable_ids = _ptr(self.unstable_ids, torch.int32, "unstable_ids") if self.n_unstable else None
+            g.n_unstable = int(self.n_unstable)
         if self.u_means is not None and any(getattr(self, k).numel() == 0 for k in ("u_means",)):
             # an empty compact set is the same as no override
             for name in ("u_means", "u_scales", "u_quats", "u_opacity", "u_colors"):
@@ -226,6 +233,28 @@ def render_forward(ctx: Context, cams, g: Gaussians, mask: Optional[torch.Tensor
                                         _ptr(depth, torch.float32, "depth"), _ptr(alpha, torch.float32, "alpha"),
                                         _ptr(index_map, torch.int32, "index_map"), _stream(stream))
     _check(st, "rtg_render_forward", ctx.ptr)
+
+
+def render_forward_l1(ctx: Context, cams, g: Gaussians, mask: Optional[torch.Tensor], settings: RenderSettings,
+                      target_color, target_depth, w_color: float, w_depth: float, color, depth, alpha, loss_out,
+                      index_map: Optional[torch.Tensor] = None, stream=None):
+    arr, F = _cams(cams)
+    gc = g.to_c()
+    prm = settings.to_c()
+    st = _lib.load().rtg_render_forward_l1(
+        ctx.ptr, arr, F, ctypes.byref(gc), _ptr(mask, torch.uint8, "mask"), ctypes.byref(prm),
+        _ptr(target_color, torch.float32, "target_color"), _ptr(target_depth, torch.float32, "target_depth"),
+        float(w_color), float(w_depth), _ptr(color, torch.float32, "color"), _ptr(depth, torch.float32, "depth"),
+        _ptr(alpha, torch.float32, "alpha"), _ptr(index_map, torch.int32, "index_map"),
+        _ptr(loss_out, torch.float32, "loss_out"), _stream(stream))
+    _check(st, "rtg_render_forward_l1", ctx.ptr)
+
+
+def render_backward_l1(ctx: Context, g_means, g_scales, g_quats, g_opacity, g_colors, stream=None):
+    st = _lib.load().rtg_render_backward_l1(ctx.ptr, _out_ptr(g_means, "g_means"), _out_ptr(g_scales, "g_scales"),
+                                            _out_ptr(g_quats, "g_quats"), _out_ptr(g_opacity, "g_opacity"),
+                                            _out_ptr(g_colors, "g_colors"), _stream(stream))
+    _check(st, "rtg_render_backward_l1", ctx.ptr)
 
 
 def l1_loss(ctx: Context, color, depth, target_color, target_depth, mask, w_color: float, w_depth: float,
@@ -310,6 +339,20 @@ def unstable_index_static(unstable: torch.Tensor, ids: torch.Tensor, nu_out: tor
                                                _ptr(ids, torch.int32, "ids"), _ptr(nu_out, torch.int64, "nu_out"),
                                                _stream(stream))
     _check(st, "rtg_unstable_index_static")
+
+
+def unstable_rank(ctx: Context, unstable: torch.Tensor, stream=None):
+    """(rank int32 [N], ids int32 [nu], nu): the unstable index for rtg_gaussians.rank_map.
+    Synchronises to read the count."""
+    n = int(unstable.shape[0])
+    rank = torch.empty(max(n, 1), dtype=torch.int32, device=unstable.device)
+    ids = torch.empty(max(n, 1), dtype=torch.int32, device=unstable.device)
+    nu_t = torch.zeros(1, dtype=torch.int64, device=unstable.device)
+    st = _lib.load().rtg_unstable_rank(ctx.ptr, n, _ptr(unstable, torch.uint8, "unstable"), rank.data_ptr(),
+                                       ids.data_ptr(), nu_t.data_ptr(), _stream(stream))
+    _check(st, "rtg_unstable_rank", ctx.ptr)
+    nu = int(nu_t.item())
+    return rank[:n], ids[:nu], nu
 
 
 def gather_unstable(ids: torch.Tensor, g: Gaussians, stream=None):

@@ -20,10 +20,12 @@ struct rtg_ctx {
   char err[512];
   // state of the last forward, consumed by the backward
   bool has_fwd;
+  Work w_fwd;  // the forward's view of the workspace (rank / ids may be the caller's)
   GaussPtrs g;
   Prm prm;
   int F, W, H, T, C;
   const uint8_t *mask;
+  L1Fused l1;  // targets of the last rtg_render_forward_l1 (tcolor == nullptr otherwise)
   cudaStream_t last_stream;
   // tracing: (start, end) event pairs of the kernels launched while profiling is on
   bool prof;
@@ -101,7 +103,8 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t cams, counters, rank, ids, block_cnt, cand, rec_hot, rec_cold, rec_box, ntiles, tile_npix, tile_count, tile_offset,
-      tile_cursor, keys, keys_alt, stage, sorted, px_T, px_last, px_hit, grad2d, loss_part, loss_scal, loss_done, total;
+      tile_cursor, keys, keys_alt, stage, sorted, px_T, px_last, px_hit, grad2d, loss_part, loss_scal, loss_done, tile_loss,
+      total;
 };
 
 bool capacity_ok(const rtg_capacity *c) {
@@ -151,6 +154,7 @@ Layout layout_of(const rtg_capacity *c) {
   L.loss_part = take(kLossBlocks * 4 * 4);
   L.loss_scal = take(8 * 4);
   L.loss_done = take(4);
+  L.tile_loss = take(FT * (kTilePix / 32) * 4 * 4);
   L.total = o;
   return L;
 }
@@ -200,6 +204,12 @@ rtg_status make_gauss(rtg_ctx *ctx, const rtg_gaussians *g, GaussPtrs &gp) {
   gp.u_colors = g->u_colors;
   gp.n = g->n;
   gp.C = g->channels;
+  gp.rank_map = g->rank_map;
+  gp.unstable_ids = g->unstable_ids;
+  gp.n_unstable = g->rank_map ? g->n_unstable : 0;
+  if (g->rank_map != nullptr &&
+      (g->n_unstable < 0 || g->n_unstable > g->n || (g->n_unstable > 0 && g->unstable_ids == nullptr)))
+    return fail(ctx, RTG_ERR_ARG, "precomputed unstable index: bad n_unstable or NULL unstable_ids");
   return RTG_OK;
 }
 
@@ -301,6 +311,7 @@ rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap) {
   w.loss_part = (float *)(b + L.loss_part);
   w.loss_scal = (float *)(b + L.loss_scal);
   w.loss_done = (uint32_t *)(b + L.loss_done);
+  w.tile_loss = (float *)(b + L.tile_loss);
   w.status = status_dev;
   // zero the small bookkeeping region once (counters, loss ticket)
   cudaMemset(ctx->slab + L.counters, 0, kNumCounters * sizeof(unsigned long long));
@@ -381,9 +392,12 @@ rtg_status rtg_reset_status(rtg_ctx *ctx) {
   return RTG_OK;
 }
 
-rtg_status rtg_render_forward(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, const rtg_gaussians *g,
-                              const uint8_t *mask, const rtg_render_params *prm, float *color, float *depth,
-                              float *alpha, int32_t *index_map, void *stream) {
+}  // extern "C"
+
+static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, const rtg_gaussians *g,
+                               const uint8_t *mask, const rtg_render_params *prm, float *color, float *depth,
+                               float *alpha, int32_t *index_map, const float *tcolor, const float *tdepth, float w_c,
+                               float w_d, float *loss_out, void *stream) {
   if (ctx == nullptr) return RTG_ERR_ARG;
   ctx->has_fwd = false;
   Prm P;
@@ -398,12 +412,17 @@ rtg_status rtg_render_forward(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, c
   const int T = fs.cam[0].tiles_x * fs.cam[0].tiles_y;
   const int FT = F * T;
   const int64_t n = gp.n;
-  Work &w = ctx->w;
+  Work w = ctx->w;
+  if (gp.rank_map != nullptr) {
+    w.rank = const_cast<int32_t *>(gp.rank_map);
+    w.ids = const_cast<int32_t *>(gp.unstable_ids);
+  }
   {
     ProfScope ps(ctx, kPTileMask, s);
-    launch_tile_mask(fs, w, mask, T, s);
+    launch_tile_mask(fs, w, mask, T, gp.rank_map ? (long long)gp.n_unstable : -1ll, s);
   }
-  if ((st = rank_pass(ctx, gp.unstable, n, w.rank, w.ids, w.counters, nullptr, s)) != RTG_OK) return st;
+  if (gp.rank_map == nullptr)
+    if ((st = rank_pass(ctx, gp.unstable, n, w.rank, w.ids, w.counters, nullptr, s)) != RTG_OK) return st;
   {
     ProfScope ps(ctx, kPProject, s);
     launch_project(gp, w, P, F, T, false, ctx->cap.max_pairs, s);
@@ -422,10 +441,15 @@ rtg_status rtg_render_forward(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, c
   }
   {
     ProfScope ps(ctx, kPForward, s);
-    launch_forward(gp.C, w, P, n, F, T, mask, color, depth, alpha, index_map, s);
+    launch_forward(gp.C, w, P, n, F, T, mask, color, depth, alpha, index_map, tcolor, tdepth, s);
+  }
+  if (tcolor != nullptr) {
+    ProfScope ps(ctx, kPL1Loss, s);
+    launch_loss_finalize(w, FT, gp.C, w_c, w_d, loss_out, s);
   }
   if ((st = check_launch(ctx, "render_forward")) != RTG_OK) return st;
   ctx->has_fwd = true;
+  ctx->w_fwd = w;
   ctx->g = gp;
   ctx->prm = P;
   ctx->F = F;
@@ -434,8 +458,51 @@ rtg_status rtg_render_forward(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, c
   ctx->T = T;
   ctx->C = gp.C;
   ctx->mask = mask;
+  ctx->l1 = L1Fused{tcolor, tdepth, color, depth};
   ctx->last_stream = s;
   return RTG_OK;
+}
+
+extern "C" {
+
+rtg_status rtg_render_forward(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, const rtg_gaussians *g,
+                              const uint8_t *mask, const rtg_render_params *prm, float *color, float *depth,
+                              float *alpha, int32_t *index_map, void *stream) {
+  return forward_impl(ctx, cams, F, g, mask, prm, color, depth, alpha, index_map, nullptr, nullptr, 0.f, 0.f,
+                      nullptr, stream);
+}
+
+rtg_status rtg_render_forward_l1(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, const rtg_gaussians *g,
+                                 const uint8_t *mask, const rtg_render_params *prm, const float *target_color,
+                                 const float *target_depth, float w_color, float w_depth, float *color, float *depth,
+                                 float *alpha, int32_t *index_map, float *loss_out, void *stream) {
+  if (ctx == nullptr) return RTG_ERR_ARG;
+  if (target_color == nullptr || target_depth == nullptr || loss_out == nullptr)
+    return fail(ctx, RTG_ERR_ARG, "render_forward_l1: NULL target or loss_out");
+  return forward_impl(ctx, cams, F, g, mask, prm, color, depth, alpha, index_map, target_color, target_depth, w_color,
+                      w_depth, loss_out, stream);
+}
+
+rtg_status rtg_render_backward_l1(rtg_ctx *ctx, float *g_means, float *g_scales, float *g_quats, float *g_opacity,
+                                  float *g_colors, void *stream) {
+  if (ctx == nullptr) return RTG_ERR_ARG;
+  if (!ctx->has_fwd || ctx->l1.tcolor == nullptr)
+    return fail(ctx, RTG_ERR_STATE, "render_backward_l1 without a preceding render_forward_l1");
+  if (!g_means || !g_scales || !g_quats || !g_opacity || !g_colors)
+    return fail(ctx, RTG_ERR_ARG, "gradient output is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = ctx->g.n;
+  {
+    ProfScope ps(ctx, kPBackward, s);
+    launch_backward(ctx->C, ctx->w_fwd, ctx->prm, n, ctx->F, ctx->T, ctx->mask, nullptr, nullptr, ctx->l1, s);
+  }
+  {
+    ProfScope ps(ctx, kPProjectBackward, s);
+    launch_project_backward(ctx->g, ctx->w_fwd, ctx->prm, ctx->F, g_means, g_scales, g_quats, g_opacity, g_colors,
+                            s);
+  }
+  ctx->last_stream = s;
+  return check_launch(ctx, "render_backward_l1");
 }
 
 rtg_status rtg_render_backward(rtg_ctx *ctx, const float *dL_dcolor, const float *dL_ddepth, float *g_means,
@@ -451,11 +518,13 @@ rtg_status rtg_render_backward(rtg_ctx *ctx, const float *dL_dcolor, const float
   (void)FT;
   {
     ProfScope ps(ctx, kPBackward, s);
-    launch_backward(ctx->C, ctx->w, ctx->prm, n, ctx->F, ctx->T, ctx->mask, dL_dcolor, dL_ddepth, s);
+    launch_backward(ctx->C, ctx->w_fwd, ctx->prm, n, ctx->F, ctx->T, ctx->mask, dL_dcolor, dL_ddepth,
+                    L1Fused{nullptr, nullptr, nullptr, nullptr}, s);
   }
   {
     ProfScope ps(ctx, kPProjectBackward, s);
-    launch_project_backward(ctx->g, ctx->w, ctx->prm, ctx->F, g_means, g_scales, g_quats, g_opacity, g_colors, s);
+    launch_project_backward(ctx->g, ctx->w_fwd, ctx->prm, ctx->F, g_means, g_scales, g_quats, g_opacity, g_colors,
+                            s);
   }
   ctx->last_stream = s;
   return check_launch(ctx, "render_backward");
@@ -521,6 +590,20 @@ rtg_status rtg_unstable_index(rtg_ctx *ctx, int64_t n, const uint8_t *unstable, 
   return rank_pass(ctx, unstable, n, nullptr, ids, nullptr, nu_out, s);
 }
 
+rtg_status rtg_unstable_rank(rtg_ctx *ctx, int64_t n, const uint8_t *unstable, int32_t *rank, int32_t *ids,
+                             int64_t *nu_out, void *stream) {
+  if (ctx == nullptr) return RTG_ERR_ARG;
+  if (n < 0 || n > ctx->cap.max_gaussians) return fail(ctx, RTG_ERR_ARG, "n outside capacity");
+  if (n > 0 && (unstable == nullptr || ids == nullptr || rank == nullptr)) return fail(ctx, RTG_ERR_ARG, "NULL pointer");
+  if (nu_out == nullptr) return fail(ctx, RTG_ERR_ARG, "nu_out is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n == 0) {
+    cudaMemsetAsync(nu_out, 0, sizeof(int64_t), s);
+    return check_launch(ctx, "unstable_rank");
+  }
+  return rank_pass(ctx, unstable, n, rank, ids, nullptr, nu_out, s);
+}
+
 rtg_status rtg_gather_unstable(int64_t nu, int32_t C, const int32_t *ids, const float *means, const float *scales,
                                const float *quats, const float *opacity, const float *colors, float *u_means,
                                float *u_scales, float *u_quats, float *u_opacity, float *u_colors, void *stream) {
@@ -566,14 +649,18 @@ rtg_status rtg_unstable_mask(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, co
   (void)npx;
   ProfScope ps(ctx, kPUnstableMask, s);
   // every in-image tile is active: the unstable Gaussians are bucketed into all tiles
-  launch_tile_mask(fs, ctx->w, nullptr, T, s);
-  if (gp.u_means != nullptr)
-    if ((st = rank_pass(ctx, gp.unstable, gp.n, ctx->w.rank, ctx->w.ids, ctx->w.counters, nullptr, s)) != RTG_OK)
-      return st;
-  launch_project(gp, ctx->w, P, F, T, true, ctx->cap.max_pairs, s);
-  launch_scan_tiles(ctx->w, F * T, ctx->cap.max_pairs, s);
-  launch_emit(ctx->w, s);
-  launch_mask_cover_tiles(ctx->w, P, gp.n, F, T, gp.C, mask, s);
+  Work w = ctx->w;
+  if (gp.rank_map != nullptr) {
+    w.rank = const_cast<int32_t *>(gp.rank_map);
+    w.ids = const_cast<int32_t *>(gp.unstable_ids);
+  }
+  launch_tile_mask(fs, w, nullptr, T, gp.rank_map ? (long long)gp.n_unstable : -1ll, s);
+  if (gp.u_means != nullptr && gp.rank_map == nullptr)
+    if ((st = rank_pass(ctx, gp.unstable, gp.n, w.rank, w.ids, w.counters, nullptr, s)) != RTG_OK) return st;
+  launch_project(gp, w, P, F, T, true, ctx->cap.max_pairs, s);
+  launch_scan_tiles(w, F * T, ctx->cap.max_pairs, s);
+  launch_emit(w, s);
+  launch_mask_cover_tiles(w, P, gp.n, F, T, gp.C, mask, s);
   ctx->last_stream = s;
   return check_launch(ctx, "unstable_mask");
 }

@@ -65,7 +65,7 @@ template <int C>
 __global__ void __launch_bounds__(kTilePix) k_backward(Work w, Prm prm, int64_t N, int T,
                                                        const uint8_t *__restrict__ mask,
                                                        const float *__restrict__ dL_dcolor,
-                                                       const float *__restrict__ dL_ddepth) {
+                                                       const float *__restrict__ dL_ddepth, L1Fused l1) {
   constexpr int H4 = (C <= 4) ? 3 : 4;
   constexpr int G2 = (C <= 5) ? 16 : 20;
   constexpr int NV = 6 + C;            // d mu (2), d conic (3), d alpha, d colour (C)
@@ -115,9 +115,22 @@ __global__ void __launch_bounds__(kTilePix) k_backward(Work w, Prm prm, int64_t 
     T_ = w.px_T[pix];
     last = w.px_last[pix];
     hit = w.px_hit[pix];
+    if (l1.tcolor != nullptr) {  // gradient of the fused L1 loss, formed here (sign(0) = 0)
+      const float sc = w.loss_scal[4], sd = w.loss_scal[5];
 #pragma unroll
-    for (int c = 0; c < C; ++c) dC[c] = dL_dcolor[((int64_t)f * C + c) * HW + (int64_t)py * cam.W + px];
-    dLdD = dL_ddepth[pix];
+      for (int c = 0; c < C; ++c) {
+        const int64_t o = ((int64_t)f * C + c) * HW + (int64_t)py * cam.W + px;
+        const float d = l1.color[o] - l1.tcolor[o];
+        dC[c] = d > 0.f ? sc : (d < 0.f ? -sc : 0.f);
+      }
+      const float Dh = l1.depth[pix], td = l1.tdepth[pix];
+      const float d = Dh - td;
+      dLdD = (Dh != -1.f && td > 0.f) ? (d > 0.f ? sd : (d < 0.f ? -sd : 0.f)) : 0.f;
+    } else {
+#pragma unroll
+      for (int c = 0; c < C; ++c) dC[c] = dL_dcolor[((int64_t)f * C + c) * HW + (int64_t)py * cam.W + px];
+      dLdD = dL_ddepth[pix];
+    }
   }
   float *__restrict__ g2base = w.grad2d + (int64_t)f * N * G2;
 
@@ -182,21 +195,33 @@ __global__ void __launch_bounds__(kTilePix) k_backward(Work w, Prm prm, int64_t 
 #pragma unroll
   for (int c = 0; c < C; ++c) S[c] = 0.f;
 
+  // batches run back to front; the records of the next (earlier) batch are fetched while
+  // the current one is replayed
+  auto fetch = [&](int b_end_, float4 (&rr)[H4], float2 &bx, int &rank_, bool &v_) {
+    const int jq = max(0, b_end_ - 32) + lane;
+    v_ = b_end_ > 0 && jq < b_end_;
+    if (v_) {
+      const uint32_t gid = w.sorted[off + jq];
+#pragma unroll
+      for (int k = 0; k < H4; ++k) rr[k] = rec[(int64_t)gid * H4 + k];
+      bx = box[gid];
+      rank_ = (H4 == 3) ? __float_as_int(rr[2].w) : __float_as_int(w.rec_cold[((int64_t)f * N + gid) * 2 + 1].y);
+    }
+  };
+  float4 r[H4];
+  float2 bb = make_float2(0.f, 0.f);
+  int rk = -1;
+  bool valid = false;
+  fetch((int)maxlast, r, bb, rk, valid);
   for (int b_end = (int)maxlast; b_end > 0; b_end -= 32) {
     const int b_beg = max(0, b_end - 32);
     const int j = b_beg + lane;
-    bool keep = false;
-    float4 r[H4];
-    int rk = -1;
-    if (j < b_end) {
-      const uint32_t gid = w.sorted[off + j];
-      const float4 *rp = rec + (int64_t)gid * H4;
-#pragma unroll
-      for (int k = 0; k < H4; ++k) r[k] = rp[k];
-      const float2 bb = box[gid];
-      keep = fabsf(r[0].x - wcx) <= whx + bb.x && fabsf(r[0].y - wcy) <= why + bb.y;
-      rk = __float_as_int(w.rec_cold[((int64_t)f * N + gid) * 2 + 1].y);
-    }
+    float4 rn[H4];
+    float2 bn = make_float2(0.f, 0.f);
+    int rkn = -1;
+    bool vnext = false;
+    fetch(b_beg, rn, bn, rkn, vnext);
+    const bool keep = valid && fabsf(r[0].x - wcx) <= whx + bb.x && fabsf(r[0].y - wcy) <= why + bb.y;
     const unsigned bal = __ballot_sync(0xffffffffu, keep);
     if (keep) {
       const int slot = __popc(bal & lanemask_lt());
@@ -260,6 +285,11 @@ __global__ void __launch_bounds__(kTilePix) k_backward(Work w, Prm prm, int64_t 
       }
     }
     __syncwarp();
+#pragma unroll
+    for (int k = 0; k < H4; ++k) r[k] = rn[k];
+    bb = bn;
+    rk = rkn;
+    valid = vnext;
   }
 }
 
@@ -434,11 +464,11 @@ __global__ void __launch_bounds__(256) k_project_backward(GaussPtrs g, Work w, P
 }
 
 void launch_backward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const uint8_t *mask,
-                     const float *dL_dcolor, const float *dL_ddepth, cudaStream_t s) {
+                     const float *dL_dcolor, const float *dL_ddepth, const L1Fused &l1, cudaStream_t s) {
   if (C == 3)
-    k_backward<3><<<F * T, kTilePix, 0, s>>>(w, prm, N, T, mask, dL_dcolor, dL_ddepth);
+    k_backward<3><<<F * T, kTilePix, 0, s>>>(w, prm, N, T, mask, dL_dcolor, dL_ddepth, l1);
   else
-    k_backward<8><<<F * T, kTilePix, 0, s>>>(w, prm, N, T, mask, dL_dcolor, dL_ddepth);
+    k_backward<8><<<F * T, kTilePix, 0, s>>>(w, prm, N, T, mask, dL_dcolor, dL_ddepth, l1);
 }
 
 void launch_project_backward(const GaussPtrs &g, const Work &w, const Prm &prm, int F, float *g_means,

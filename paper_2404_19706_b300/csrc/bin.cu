@@ -12,13 +12,14 @@ namespace rtg {
 // compacted pixel set of that tile) and clears its pair counter.  Block 0 also
 // publishes the cameras and clears the per-call counters.
 __global__ void __launch_bounds__(kTilePix) k_tile_mask(FrameSet fs, Work w, const uint8_t *__restrict__ mask,
-                                                        int T) {
+                                                        int T, long long nu_preset) {
   const int tile = blockIdx.x;
   const int f = tile / T, lt = tile - f * T;
   const DevCam &cam = fs.cam[f];
   if (blockIdx.x == 0) {
     for (int i = threadIdx.x; i < fs.F; i += blockDim.x) w.cams[i] = fs.cam[i];
-    if (threadIdx.x < kNumCounters) w.counters[threadIdx.x] = 0ull;
+    if (threadIdx.x < kNumCounters)
+      w.counters[threadIdx.x] = (threadIdx.x == kNumUnstable && nu_preset >= 0) ? (unsigned long long)nu_preset : 0ull;
   }
   const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
   const int px = tx * kTile + (threadIdx.x & (kTile - 1)), py = ty * kTile + (threadIdx.x / kTile);
@@ -111,13 +112,24 @@ __global__ void __launch_bounds__(kRankThreads) k_rank_write(const uint8_t *__re
 // keeps, clears the tile count of the pairs it drops, and appends the rest to a dense
 // candidate list (one atomic per warp).  k_project then runs the exact double-float
 // projection over that list only, so its warps stay full.
+// With `ids` (unstable-mask pass only) the threads walk that list of unstable Gaussians
+// instead of all N; pairs of other Gaussians keep stale tile counts, which nothing reads
+// before the next forward projection rewrites them.
 template <bool kMask>
-__global__ void __launch_bounds__(256) k_cull(GaussPtrs g, Work w, Prm prm, int F) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_cull(GaussPtrs g, Work w, Prm prm, int F, const int32_t *__restrict__ ids,
+                                              int64_t count) {
+  __shared__ uint32_t s_w[8];
+  __shared__ unsigned long long s_base;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t N = g.n;
-  const int lane = threadIdx.x & 31;
-  bool live = i < N;
-  if (kMask && live) live = g.unstable[i] != 0;
+  int64_t i = t;
+  bool live = t < N;
+  if (ids != nullptr) {
+    live = t < count;
+    i = live ? (int64_t)ids[t] : 0;
+  } else if (kMask && live) {
+    live = g.unstable[i] != 0;
+  }
   float p[3] = {0.f, 0.f, 0.f};
   if (live) {
     const float *pm = g.means + 3 * i;
@@ -139,15 +151,9 @@ __global__ void __launch_bounds__(256) k_cull(GaussPtrs g, Work w, Prm prm, int 
       cand = Z > prm.near_z - tol && fabsf(X) <= cam.lim_x * (Z + tol) + tol &&
              fabsf(Y) <= cam.lim_y * (Z + tol) + tol;
     }
-    if (i < N && !cand) w.ntiles[(int64_t)f * N + i] = 0u;
-    const unsigned bal = __ballot_sync(0xffffffffu, cand);
-    if (bal) {
-      const int leader = __ffs(bal) - 1;
-      unsigned long long base = 0;
-      if (lane == leader) base = atomicAdd(w.counters + kCand, (unsigned long long)__popc(bal));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (cand) w.cand[base + __popc(bal & lanemask_lt())] = (uint32_t)((int64_t)f * N + i);
-    }
+    if ((ids != nullptr ? live : i < N) && !cand) w.ntiles[(int64_t)f * N + i] = 0u;
+    const unsigned long long slot = block_reserve(w.counters + kCand, cand ? 1u : 0u, s_w, &s_base);
+    if (cand) w.cand[slot] = (uint32_t)((int64_t)f * N + i);
   }
 }
 
@@ -160,9 +166,10 @@ template <int C, bool kMask>
 __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, int T, int64_t max_pairs) {
   constexpr int H4 = (C <= 4) ? 3 : 4;
   constexpr int G2 = (C <= 5) ? 16 : 20;
+  __shared__ uint32_t s_w[8];
+  __shared__ unsigned long long s_base;
   const int64_t N = g.n;
   const int64_t ncand = (int64_t)w.counters[kCand];
-  const int lane = threadIdx.x & 31;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < ncand; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = base + threadIdx.x;
     uint32_t nt = 0, e = 0;
@@ -198,22 +205,18 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
           for (int tx = tx0; tx <= tx1; ++tx) nt += npix[ty * tiles_x + tx] != 0u;
       }
     }
-    // warp-level reservation of the staging range
-    uint32_t incl = nt;
-    for (int o2 = 1; o2 < 32; o2 <<= 1) {
-      const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o2);
-      if (lane >= o2) incl += v;
+    // block-level reservation of the staging range (one atomic per block)
+    const unsigned long long first = block_reserve(w.counters + kStaged, nt, s_w, &s_base);
+    if (!kMask) {
+      const unsigned long long vbase = block_reserve(w.counters + kVisible, nt > 0 ? 1u : 0u, s_w, &s_base);
+      (void)vbase;
     }
-    const uint32_t wtotal = __shfl_sync(0xffffffffu, incl, 31);
-    unsigned long long wbase = 0;
-    if (lane == 0 && wtotal) wbase = atomicAdd(w.counters + kStaged, (unsigned long long)wtotal);
-    wbase = __shfl_sync(0xffffffffu, wbase, 0);
     if (ok && nt > 0) {
       const DevCam &cam = w.cams[f];
       const uint32_t *npix = w.tile_npix + (int64_t)f * T;
       uint32_t *tcount = w.tile_count + (int64_t)f * T;
       const unsigned long long key = ((unsigned long long)__float_as_uint(o.Z) << 32) | (unsigned long long)(uint32_t)i;
-      unsigned long long idx = wbase + incl - nt;
+      unsigned long long idx = first;
       for (int ty = ty0; ty <= ty1; ++ty)
         for (int tx = tx0; tx <= tx1; ++tx) {
           const int t = ty * cam.tiles_x + tx;
@@ -232,7 +235,8 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
       float cc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
       for (int c = 0; c < C; ++c) cc[c] = col[c];
-      hot[2] = make_float4(cc[0], cc[1], cc[2], cc[3]);
+      // C = 3: the spare fourth slot carries the unstable rank for the backward
+      hot[2] = make_float4(cc[0], cc[1], cc[2], C == 3 ? __int_as_float(rk) : cc[3]);
       if (H4 == 4) hot[3] = make_float4(cc[4], cc[5], cc[6], cc[7]);
       w.rec_box[(int64_t)f * N + i] = make_float2(o.rx, o.ry);
       float4 *cold = w.rec_cold + ((int64_t)f * N + i) * 2;
@@ -246,10 +250,6 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
       }
     }
     if (k < ncand) w.ntiles[e] = nt;
-    if (!kMask) {
-      const unsigned vis = __ballot_sync(0xffffffffu, nt > 0);
-      if (lane == 0 && vis) atomicAdd(w.counters + kVisible, (unsigned long long)__popc(vis));
-    }
   }
 }
 
@@ -330,8 +330,9 @@ __global__ void __launch_bounds__(256) k_emit(Work w) {
   }
 }
 
-void launch_tile_mask(const FrameSet &fs, const Work &w, const uint8_t *mask, int T, cudaStream_t s) {
-  k_tile_mask<<<fs.F * T, kTilePix, 0, s>>>(fs, w, mask, T);
+void launch_tile_mask(const FrameSet &fs, const Work &w, const uint8_t *mask, int T, long long nu_preset,
+                      cudaStream_t s) {
+  k_tile_mask<<<fs.F * T, kTilePix, 0, s>>>(fs, w, mask, T, nu_preset);
 }
 
 void launch_rank(const uint8_t *unstable, int64_t n, int32_t *block_cnt, int32_t *rank, int32_t *ids,
@@ -347,13 +348,19 @@ void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, in
   if (g.n <= 0) return;
   const unsigned nb = (unsigned)((g.n + 255) / 256);
   if (unstable_only) {
-    k_cull<true><<<nb, 256, 0, s>>>(g, w, prm, F);
+    if (g.rank_map != nullptr) {
+      if (g.n_unstable > 0)
+        k_cull<true><<<(unsigned)((g.n_unstable + 255) / 256), 256, 0, s>>>(g, w, prm, F, g.unstable_ids,
+                                                                          g.n_unstable);
+    } else {
+      k_cull<true><<<nb, 256, 0, s>>>(g, w, prm, F, nullptr, 0);
+    }
     if (g.C == 3)
       k_project<3, true><<<kPersistBlocks, 256, 0, s>>>(g, w, prm, T, max_pairs);
     else
       k_project<8, true><<<kPersistBlocks, 256, 0, s>>>(g, w, prm, T, max_pairs);
   } else {
-    k_cull<false><<<nb, 256, 0, s>>>(g, w, prm, F);
+    k_cull<false><<<nb, 256, 0, s>>>(g, w, prm, F, nullptr, 0);
     if (g.C == 3)
       k_project<3, false><<<kPersistBlocks, 256, 0, s>>>(g, w, prm, T, max_pairs);
     else

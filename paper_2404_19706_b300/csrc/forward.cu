@@ -19,7 +19,9 @@ template <int C>
 __global__ void __launch_bounds__(kTilePix) k_forward(Work w, Prm prm, int64_t N, int T,
                                                       const uint8_t *__restrict__ mask, float *__restrict__ color,
                                                       float *__restrict__ depth, float *__restrict__ alpha,
-                                                      int32_t *__restrict__ index_map) {
+                                                      int32_t *__restrict__ index_map,
+                                                      const float *__restrict__ tcolor,
+                                                      const float *__restrict__ tdepth) {
   constexpr int H4 = (C <= 4) ? 3 : 4;
   constexpr int NW = kTilePix / 32;
   __shared__ float4 s_rec[NW][H4][32];
@@ -72,21 +74,31 @@ __global__ void __launch_bounds__(kTilePix) k_forward(Work w, Prm prm, int64_t N
   uint32_t last = 0, nfrag = 0;
   int hit_j = -1;
   bool done = !has;
+  // the records of batch b0 are fetched while batch b0 - 32 is composited
+  float4 r[H4];
+  float2 bb = make_float2(0.f, 0.f);
+  bool valid = lane < (int)n;
+  if (valid) {
+    const uint32_t gid = w.sorted[off + lane];
+#pragma unroll
+    for (int k = 0; k < H4; ++k) r[k] = rec[(int64_t)gid * H4 + k];
+    bb = box[gid];
+  }
   for (uint32_t b0 = 0; b0 < n; b0 += 32) {
     if (__all_sync(0xffffffffu, done)) break;
-    // each lane fetches one record of the batch; the warp keeps those near its pixels,
-    // compacted in list order
     const uint32_t j = b0 + lane;
-    bool keep = false;
-    float4 r[H4];
-    if (j < n) {
-      const uint32_t gid = w.sorted[off + j];
-      const float4 *rp = rec + (int64_t)gid * H4;
+    const uint32_t jn = j + 32;
+    const bool vnext = jn < n;
+    float4 rn[H4];
+    float2 bn = make_float2(0.f, 0.f);
+    if (vnext) {
+      const uint32_t gid = w.sorted[off + jn];
 #pragma unroll
-      for (int k = 0; k < H4; ++k) r[k] = rp[k];
-      const float2 bb = box[gid];
-      keep = fabsf(r[0].x - wcx) <= whx + bb.x && fabsf(r[0].y - wcy) <= why + bb.y;
+      for (int k = 0; k < H4; ++k) rn[k] = rec[(int64_t)gid * H4 + k];
+      bn = box[gid];
     }
+    // keep the records whose support box reaches the warp's pixel box, in list order
+    const bool keep = valid && fabsf(r[0].x - wcx) <= whx + bb.x && fabsf(r[0].y - wcy) <= why + bb.y;
     const unsigned bal = __ballot_sync(0xffffffffu, keep);
     if (keep) {
       const int slot = __popc(bal & lanemask_lt());
@@ -125,7 +137,12 @@ __global__ void __launch_bounds__(kTilePix) k_forward(Work w, Prm prm, int64_t N
       }
     }
     __syncwarp();
+#pragma unroll
+    for (int k = 0; k < H4; ++k) r[k] = rn[k];
+    bb = bn;
+    valid = vnext;
   }
+  float lc = 0.f, ld = 0.f, nd = 0.f;
   if (has) {
     const int64_t HW = (int64_t)cam.H * cam.W;
     const int64_t pix = (int64_t)f * HW + (int64_t)py * cam.W + px;
@@ -148,6 +165,29 @@ __global__ void __launch_bounds__(kTilePix) k_forward(Work w, Prm prm, int64_t N
     w.px_T[pix] = T_;
     w.px_last[pix] = last;
     w.px_hit[pix] = hit_gid;
+    if (tcolor != nullptr) {  // fused L1 terms of this pixel (Eq. 7)
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+        lc += fabsf(acc[c] - tcolor[((int64_t)f * C + c) * HW + (int64_t)py * cam.W + px]);
+      const float td = tdepth[pix];
+      if (D != -1.f && td > 0.f) {
+        ld = fabsf(D - td);
+        nd = 1.f;
+      }
+    }
+  }
+  if (tcolor != nullptr) {  // fixed-order per-warp partials, summed by k_loss_finalize
+    for (int o = 16; o > 0; o >>= 1) {
+      lc += __shfl_xor_sync(0xffffffffu, lc, o);
+      ld += __shfl_xor_sync(0xffffffffu, ld, o);
+      nd += __shfl_xor_sync(0xffffffffu, nd, o);
+    }
+    if (lane == 0) {
+      float *lp = w.tile_loss + ((int64_t)tile * (kTilePix / 32) + wid) * 4;
+      lp[0] = lc;
+      lp[1] = ld;
+      lp[2] = nd;
+    }
   }
   // fragment counter: one atomic per warp
   const unsigned fr = __reduce_add_sync(0xffffffffu, nfrag);
@@ -155,11 +195,12 @@ __global__ void __launch_bounds__(kTilePix) k_forward(Work w, Prm prm, int64_t N
 }
 
 void launch_forward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const uint8_t *mask, float *color,
-                    float *depth, float *alpha, int32_t *index_map, cudaStream_t s) {
+                    float *depth, float *alpha, int32_t *index_map, const float *tcolor, const float *tdepth,
+                    cudaStream_t s) {
   if (C == 3)
-    k_forward<3><<<F * T, kTilePix, 0, s>>>(w, prm, N, T, mask, color, depth, alpha, index_map);
+    k_forward<3><<<F * T, kTilePix, 0, s>>>(w, prm, N, T, mask, color, depth, alpha, index_map, tcolor, tdepth);
   else
-    k_forward<8><<<F * T, kTilePix, 0, s>>>(w, prm, N, T, mask, color, depth, alpha, index_map);
+    k_forward<8><<<F * T, kTilePix, 0, s>>>(w, prm, N, T, mask, color, depth, alpha, index_map, tcolor, tdepth);
 }
 
 }  // namespace rtg

@@ -30,6 +30,35 @@ __device__ __forceinline__ int block_sum_int(int v, int *s_warp) {
   return t;
 }
 
+// Reserves `cnt` consecutive slots of a global counter for every thread of the block with a
+// single atomic per block (same-address atomics serialise in one L2 slice, so one per warp
+// over a million threads is slow).  Returns this thread's first slot.  All threads of the
+// block must call it; s_w must hold blockDim.x / 32 entries.
+__device__ __forceinline__ unsigned long long block_reserve(unsigned long long *counter, uint32_t cnt, uint32_t *s_w,
+                                                            unsigned long long *s_base) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t incl = cnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) s_w[wid] = incl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int k = 0; k < nw; ++k) {
+      const uint32_t c = s_w[k];
+      s_w[k] = run;
+      run += c;
+    }
+    *s_base = run ? atomicAdd(counter, (unsigned long long)run) : 0ull;
+  }
+  __syncthreads();
+  const unsigned long long r = *s_base + s_w[wid] + incl - cnt;
+  __syncthreads();
+  return r;
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -38,7 +67,8 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 
 // ---- host launchers (each defined in the translation unit of its kernels)
 // bin.cu
-void launch_tile_mask(const FrameSet &fs, const Work &w, const uint8_t *mask, int T, cudaStream_t s);
+void launch_tile_mask(const FrameSet &fs, const Work &w, const uint8_t *mask, int T, long long nu_preset,
+                      cudaStream_t s);
 void launch_rank(const uint8_t *unstable, int64_t n, int32_t *block_cnt, int32_t *rank, int32_t *ids,
                  unsigned long long *nu_counter, int64_t *nu_out, cudaStream_t s);
 void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, int T, bool unstable_only,
@@ -50,10 +80,12 @@ void launch_sort_tiles(const Work &w, int FT, cudaStream_t s);
 void init_sort_attributes();
 // forward.cu
 void launch_forward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const uint8_t *mask, float *color,
-                    float *depth, float *alpha, int32_t *index_map, cudaStream_t s);
+                    float *depth, float *alpha, int32_t *index_map, const float *tcolor, const float *tdepth,
+                    cudaStream_t s);
 // backward.cu
 void launch_backward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const uint8_t *mask,
-                     const float *dL_dcolor, const float *dL_ddepth, cudaStream_t s);
+                     const float *dL_dcolor, const float *dL_ddepth, const L1Fused &l1, cudaStream_t s);
+void launch_loss_finalize(const Work &w, int FT, int C, float w_c, float w_d, float *loss_out, cudaStream_t s);
 void launch_project_backward(const GaussPtrs &g, const Work &w, const Prm &prm, int F, float *g_means,
                              float *g_scales, float *g_quats, float *g_opacity, float *g_colors, cudaStream_t s);
 // loss_adam_mask.cu

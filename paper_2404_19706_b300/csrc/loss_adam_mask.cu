@@ -57,11 +57,11 @@ __global__ void __launch_bounds__(256) k_loss_reduce(Work w, int F, int C, int H
   // last block: every thread sums a strided share of the block partials (fixed order), then
   // a fixed-order reduction across the threads keeps the result deterministic
   __threadfence();
-  __shared__ double s_tot[4][256];
-  double t[4] = {0, 0, 0, 0};
+  __shared__ float s_tot[4][256];
+  float t[4] = {0.f, 0.f, 0.f, 0.f};
   for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
 #pragma unroll
-    for (int k = 0; k < 4; ++k) t[k] += (double)__ldcg(w.loss_part + b * 4 + k);
+    for (int k = 0; k < 4; ++k) t[k] += __ldcg(w.loss_part + b * 4 + k);
 #pragma unroll
   for (int k = 0; k < 4; ++k) s_tot[k][threadIdx.x] = t[k];
   __syncthreads();
@@ -72,16 +72,62 @@ __global__ void __launch_bounds__(256) k_loss_reduce(Work w, int F, int C, int H
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const double sc = s_tot[0][0], sd = s_tot[1][0], np = s_tot[2][0], nd = s_tot[3][0];
-    const double Lc = np > 0 ? sc / (np * C) : 0.0;
-    const double Ld = nd > 0 ? sd / nd : 0.0;
-    loss_out[0] = (float)(w_c * Lc + w_d * Ld);
-    loss_out[1] = (float)Lc;
-    loss_out[2] = (float)Ld;
-    w.loss_scal[4] = np > 0 ? (float)(w_c / (np * C)) : 0.f;
-    w.loss_scal[5] = nd > 0 ? (float)(w_d / nd) : 0.f;
+    const float sc = s_tot[0][0], sd = s_tot[1][0], np = s_tot[2][0], nd = s_tot[3][0];
+    const float Lc = np > 0.f ? sc / (np * (float)C) : 0.f;
+    const float Ld = nd > 0.f ? sd / nd : 0.f;
+    loss_out[0] = w_c * Lc + w_d * Ld;
+    loss_out[1] = Lc;
+    loss_out[2] = Ld;
+    w.loss_scal[4] = np > 0.f ? w_c / (np * (float)C) : 0.f;
+    w.loss_scal[5] = nd > 0.f ? w_d / nd : 0.f;
     *w.loss_done = 0u;
   }
+}
+
+// Fused L1 (Eq. 7/8): sums the forward's per-(tile, warp) partials in a fixed order (only
+// the warps that held masked pixels wrote them), then the loss and its gradient scales.
+// B300's FP64 rate is a small fraction of FP32 and this runs on one SM, so the sums are
+// FP32 with Kahan compensation per thread and a fixed-order tree across threads.
+__global__ void __launch_bounds__(1024) k_loss_finalize(Work w, int FT, int C, float w_c, float w_d,
+                                                        float *__restrict__ loss_out) {
+  __shared__ float s_t[3][1024];
+  float t[3] = {0.f, 0.f, 0.f}, comp[3] = {0.f, 0.f, 0.f};
+  for (int tile = threadIdx.x; tile < FT; tile += 1024) {
+    const int nw = (int)((w.tile_npix[tile] + 31u) / 32u);
+    for (int k = 0; k < nw; ++k) {
+      const float *lp = w.tile_loss + ((int64_t)tile * (kTilePix / 32) + k) * 4;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {  // Kahan summation
+        const float y = lp[q] - comp[q];
+        const float tt = t[q] + y;
+        comp[q] = (tt - t[q]) - y;
+        t[q] = tt;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) s_t[q][threadIdx.x] = t[q];
+  __syncthreads();
+  for (int stride = 512; stride > 0; stride >>= 1) {
+    if ((int)threadIdx.x < stride)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) s_t[q][threadIdx.x] += s_t[q][threadIdx.x + stride];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const float np = (float)w.counters[kMaskedPix], nd = s_t[2][0];
+    const float Lc = np > 0.f ? s_t[0][0] / (np * (float)C) : 0.f;
+    const float Ld = nd > 0.f ? s_t[1][0] / nd : 0.f;
+    loss_out[0] = w_c * Lc + w_d * Ld;
+    loss_out[1] = Lc;
+    loss_out[2] = Ld;
+    w.loss_scal[4] = np > 0.f ? w_c / (np * (float)C) : 0.f;
+    w.loss_scal[5] = nd > 0.f ? w_d / nd : 0.f;
+  }
+}
+
+void launch_loss_finalize(const Work &w, int FT, int C, float w_c, float w_d, float *loss_out, cudaStream_t s) {
+  k_loss_finalize<<<1, 1024, 0, s>>>(w, FT, C, w_c, w_d, loss_out);
 }
 
 __device__ __forceinline__ float signf_(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
@@ -124,10 +170,16 @@ __global__ void __launch_bounds__(256) k_adam(int64_t nu, int C, float *__restri
                                               const float *__restrict__ g_opacity, const float *__restrict__ g_colors,
                                               float *__restrict__ m, float *__restrict__ v, rtg_adam_params hp,
                                               float bc1, float bc2_sqrt, const int32_t *__restrict__ step_dev) {
-  if (step_dev != nullptr) {  // bias corrections from the device step counter
-    const float t = (float)*step_dev;
-    bc1 = 1.f / (1.f - powf(hp.beta1, t));
-    bc2_sqrt = rsqrtf(1.f - powf(hp.beta2, t));
+  if (step_dev != nullptr) {  // bias corrections from the device step counter, once per block
+    __shared__ float s_bc[2];
+    if (threadIdx.x == 0) {
+      const float t = (float)*step_dev;
+      s_bc[0] = 1.f / (1.f - powf(hp.beta1, t));
+      s_bc[1] = rsqrtf(1.f - powf(hp.beta2, t));
+    }
+    __syncthreads();
+    bc1 = s_bc[0];
+    bc2_sqrt = s_bc[1];
   }
   const int64_t total = nu * (11 + C);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {

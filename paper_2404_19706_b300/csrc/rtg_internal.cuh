@@ -65,6 +65,14 @@ struct GaussPtrs {
   const float *u_means, *u_scales, *u_quats, *u_opacity, *u_colors;
   int64_t n;
   int C;
+  const int32_t *rank_map, *unstable_ids;  // optional precomputed unstable index
+  int64_t n_unstable;
+};
+
+// Inputs of the L1 loss fused into the forward / backward (tcolor == nullptr: not fused).
+struct L1Fused {
+  const float *tcolor, *tdepth;  // targets [F,C,H,W], [F,H,W]
+  const float *color, *depth;    // the forward's rendered colour and depth
 };
 
 struct Work {
@@ -91,6 +99,7 @@ struct Work {
   int32_t *px_hit;
   float *grad2d;
   float *loss_part;     // [kLossBlocks * 4]
+  float *tile_loss;     // [F*T*8*4] per-(tile, warp) fused L1 partials (colour sum, depth sum, depth count)
   float *loss_scal;     // [4]: L, Lc, Ld, (unused); [4..5] gradient scales
   uint32_t *loss_done;
   uint32_t *status;     // host-mapped status word (device pointer)

@@ -97,17 +97,17 @@ class MaskedStep:
         if recompute_mask and mask is None:
             raise ValueError("recompute_mask needs a mask buffer")
         self.w_color, self.w_depth = w_color, w_depth
-        self.ids, self.nu = api.unstable_index(ctx, g.unstable)
+        # the unstable index is fixed for the life of this step object (one window)
+        self.rank, self.ids, self.nu = api.unstable_rank(ctx, g.unstable)
+        # the optimiser owns compact copies of the unstable parameters; after every Adam step
+        # they are scattered into the full arrays, which the renderer reads directly
         self.u = api.gather_unstable(self.ids, g)
-        self.g = dataclasses.replace(g, u_means=self.u[0], u_scales=self.u[1], u_quats=self.u[2],
-                                     u_opacity=self.u[3], u_colors=self.u[4])
+        self.g = dataclasses.replace(g, rank_map=self.rank, unstable_ids=self.ids, n_unstable=self.nu)
         self.state = RasterState(ctx, self.g, self.cams, mask, settings)
         dev = g.means.device
         C = g.channels
         self.target_color, self.target_depth = target_color, target_depth
         self.loss = torch.zeros(3, device=dev)
-        self.dL_dcolor = torch.zeros_like(self.state.color)
-        self.dL_ddepth = torch.zeros_like(self.state.depth)
         self.grads = [torch.zeros_like(t) for t in self.u]
         self.m = torch.zeros(self.nu * (11 + C), device=dev)
         self.v = torch.zeros(self.nu * (11 + C), device=dev)
@@ -118,12 +118,13 @@ class MaskedStep:
         s = self.state
         if self.recompute_mask:
             api.unstable_mask(self.ctx, self.cams, self.g, self.settings, self.mask, stream)
-        api.render_forward(self.ctx, self.cams, self.g, self.mask, self.settings, s.color, s.depth, s.alpha, None,
-                           stream)
-        api.l1_loss(self.ctx, s.color, s.depth, self.target_color, self.target_depth, self.mask, self.w_color,
-                    self.w_depth, self.loss, self.dL_dcolor, self.dL_ddepth, stream)
-        api.render_backward(self.ctx, self.dL_dcolor, self.dL_ddepth, *self.grads, stream=stream)
+        # forward with the L1 loss fused in, then its backward (no gradient images)
+        api.render_forward_l1(self.ctx, self.cams, self.g, self.mask, self.settings, self.target_color,
+                              self.target_depth, self.w_color, self.w_depth, s.color, s.depth, s.alpha, self.loss,
+                              None, stream)
+        api.render_backward_l1(self.ctx, *self.grads, stream=stream)
         api.adam_step_counted(self.u, self.grads, self.m, self.v, self.step_counter, self.adam, stream)
+        api.scatter_unstable(self.ids, self.u, self.g, stream)
         return self.loss
 
     def step(self, stream=None):
@@ -144,5 +145,6 @@ class MaskedStep:
         return graph
 
     def write_back(self, stream=None):
-        """Scatter the optimised compact parameters into the full arrays (end of a window)."""
+        """Scatter the optimised compact parameters into the full arrays (every step already
+        does this; kept for callers that modify the compact copies themselves)."""
         api.scatter_unstable(self.ids, self.u, self.g, stream)

@@ -164,3 +164,78 @@ def test_masked_step_graph_replay_matches_eager():
     for a, b in zip(eager.u, graphed.u):
         np.testing.assert_allclose(b.cpu().numpy(), a.cpu().numpy(), rtol=1e-4, atol=1e-6)
     assert int(graphed.step_counter.item()) == 6 and int(eager.step_counter.item()) == 6
+
+
+def test_precomputed_unstable_index_is_bitwise_identical():
+    import dataclasses
+    m = rtg()
+    scene, layout = synth.room_scene(2050, 20000)
+    cam = next(synth.room_camera_candidates(2051, layout, 112, 80, 100.0))
+    scene.unstable = synth.flag_blobs(scene, [cam], 3000, 3, seed=10)
+    ctx = ctx_for(scene.n, cam)
+    g = m.Gaussians.from_scene(scene)
+    rank, ids, nu = m.unstable_rank(ctx, g.unstable)
+    assert nu == int(scene.unstable.sum())
+    np.testing.assert_array_equal(ids.cpu().numpy(), np.flatnonzero(scene.unstable))
+    flags = scene.unstable.astype(np.int64)
+    exp_rank = np.where(flags > 0, np.cumsum(flags) - 1, -1)
+    np.testing.assert_array_equal(rank.cpu().numpy(), exp_rank)
+    g2 = dataclasses.replace(g, rank_map=rank, unstable_ids=ids, n_unstable=nu)
+    outs = []
+    for gg in (g, g2):
+        mask = torch.zeros(1, 80, 112, dtype=torch.uint8, device="cuda")
+        m.unstable_mask(ctx, cam, gg, m.RenderSettings(), mask)
+        col = torch.zeros(1, 3, 80, 112, device="cuda")
+        dep = torch.full((1, 80, 112), -1.0, device="cuda")
+        alp = torch.zeros(1, 80, 112, device="cuda")
+        m.render_forward(ctx, cam, gg, mask, m.RenderSettings(), col, dep, alp)
+        dc = torch.sign(col - 0.5) / 1000.0
+        dd = torch.where(dep > 0, torch.ones_like(dep), torch.zeros_like(dep)) / 1000.0
+        grads = [torch.zeros(nu, 3, device="cuda"), torch.zeros(nu, 3, device="cuda"), torch.zeros(nu, 4, device="cuda"),
+                 torch.zeros(nu, device="cuda"), torch.zeros(nu, 3, device="cuda")]
+        m.render_backward(ctx, dc, dd, *grads)
+        torch.cuda.synchronize()
+        outs.append([mask.cpu(), col.cpu(), dep.cpu()] + [t.cpu() for t in grads])
+    for a, b in zip(outs[0][:3], outs[1][:3]):
+        assert torch.equal(a, b)
+    assert outs[0][0].float().mean() > 0.05
+    for a, b in zip(outs[0][3:], outs[1][3:]):  # atomics: equal up to summation order
+        np.testing.assert_allclose(b.numpy(), a.numpy(), rtol=1e-5, atol=1e-9)
+
+
+def test_fused_l1_forward_backward_match_separate_calls():
+    """rtg_render_forward_l1 + rtg_render_backward_l1 give the loss and gradients of
+    rtg_render_forward + rtg_l1_loss + rtg_render_backward."""
+    m = rtg()
+    scene, layout = synth.room_scene(2060, 20000)
+    cam = next(synth.room_camera_candidates(2061, layout, 112, 80, 100.0))
+    scene.unstable = synth.flag_blobs(scene, [cam], 3000, 3, seed=11)
+    tref = gpu_forward(synth.jitter_scene(scene, 12), cam)
+    tc = torch.tensor(tref["color"]).cuda()
+    td = torch.tensor(np.where(tref["depth"] > 0, tref["depth"], 0)).cuda()
+    ctx = ctx_for(scene.n, cam)
+    g = m.Gaussians.from_scene(scene)
+    mask = torch.zeros(1, 80, 112, dtype=torch.uint8, device="cuda")
+    m.unstable_mask(ctx, cam, g, m.RenderSettings(), mask)
+    nu = int(scene.unstable.sum())
+
+    def bufs():
+        return (torch.zeros(1, 3, 80, 112, device="cuda"), torch.full((1, 80, 112), -1.0, device="cuda"),
+                torch.zeros(1, 80, 112, device="cuda"), torch.zeros(3, device="cuda"),
+                [torch.zeros(nu, 3, device="cuda"), torch.zeros(nu, 3, device="cuda"),
+                 torch.zeros(nu, 4, device="cuda"), torch.zeros(nu, device="cuda"), torch.zeros(nu, 3, device="cuda")])
+
+    c1, d1, a1, l1, g1 = bufs()
+    m.render_forward(ctx, cam, g, mask, m.RenderSettings(), c1, d1, a1)
+    dc, dd = torch.zeros_like(c1), torch.zeros_like(d1)
+    m.l1_loss(ctx, c1, d1, tc, td, mask, 1.0, 1.0, l1, dc, dd)
+    m.render_backward(ctx, dc, dd, *g1)
+    c2, d2, a2, l2, g2 = bufs()
+    m.render_forward_l1(ctx, cam, g, mask, m.RenderSettings(), tc, td, 1.0, 1.0, c2, d2, a2, l2)
+    m.render_backward_l1(ctx, *g2)
+    torch.cuda.synchronize()
+    assert torch.equal(c1, c2) and torch.equal(d1, d2)
+    np.testing.assert_allclose(l2.cpu().numpy(), l1.cpu().numpy(), rtol=1e-5)
+    for a, b in zip(g1, g2):
+        np.testing.assert_allclose(b.cpu().numpy(), a.cpu().numpy(), rtol=1e-5, atol=1e-9)
+    assert float(l1[0]) > 0
