@@ -35,7 +35,7 @@ WORKLOAD = dict(name="masked-step room 1M Gaussians (20% unstable, 3 blobs) 640x
                 coverage=(0.25, 0.40))
 C = 3
 P_IN, R_REC, Q_PIX, G2 = 44 + 4 * C, 36 + 4 * C, 4 * C + 16, 4 * (11 + C)  # bytes per unit
-KERNELS_PER_STEP = 19  # mask 6, forward 7, loss finalize 1, backward 2, adam 2, scatter 1
+KERNELS_PER_STEP = 17  # masked forward 11, loss finalize 1, backward 2, adam 2, scatter 1
 
 
 def parse():
@@ -296,6 +296,7 @@ def run_ours(args):
         "project": N * P_IN + V * R_REC,
         "scan_tiles": FT * 16,
         "emit": K * 12,
+        "bin": V * 32 + K * 16,
         "sort_tiles": K * 24,
         "forward": K * R_REC + P * (Q_PIX + 4 * C + 4),
         "l1_loss": FT * 8 * 12,
@@ -305,7 +306,7 @@ def run_ours(args):
     }
     per_launch = {k: (v[1] / v[0] if v[0] else 0.0) for k, v in prof.items()}
     single = ["project", "emit", "sort_tiles", "forward", "backward", "project_backward", "adam", "scan_tiles",
-              "tile_mask"]
+              "tile_mask", "bin"]
     dom = max(single, key=lambda k: per_launch.get(k, 0.0))
     pk = peaks()
     achieved = alg[dom] / (per_launch[dom] * 1e-3) / 1e9

@@ -172,6 +172,17 @@ rtg_status rtg_render_forward_l1(rtg_ctx *ctx, const rtg_camera *cams, int32_t F
 rtg_status rtg_render_backward_l1(rtg_ctx *ctx, float *g_means, float *g_scales, float *g_quats, float *g_opacity,
                                   float *g_colors, void *stream);
 
+/* The unstable-pixel mask and the forward in one pass (Supplement B with Section 3.1):
+ * builds the mask exactly as rtg_unstable_mask does and writes it to mask_out [F,H,W]
+ * (every in-image pixel), then renders exactly those pixels as rtg_render_forward does,
+ * sharing one projection of the Gaussians between the two.  With both targets (and
+ * loss_out) it also fuses the L1 losses as rtg_render_forward_l1 does, so either
+ * rtg_render_backward_l1 (targets given) or rtg_render_backward may follow. */
+rtg_status rtg_render_forward_masked(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, const rtg_gaussians *g,
+                                     const rtg_render_params *prm, uint8_t *mask_out, const float *target_color,
+                                     const float *target_depth, float w_color, float w_depth, float *color,
+                                     float *depth, float *alpha, int32_t *index_map, float *loss_out, void *stream);
+
 /* Adam (Kingma & Ba, Algorithm 1) on compact unstable parameters, in place, with the
  * per-group learning rates of Supplement C.  The scale is optimised in log space
  * (s <- s * exp(-step), gradient s * dL/ds).  m and v hold nu * (11 + C) float32 each,

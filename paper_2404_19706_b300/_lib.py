@@ -71,6 +71,9 @@ SIGNATURES = [
     ("rtg_render_forward_l1", c_int32, [c_void_p, POINTER(rtg_camera), c_int32, POINTER(rtg_gaussians), c_void_p,
                                         POINTER(rtg_render_params), c_void_p, c_void_p, c_float, c_float, c_void_p,
                                         c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("rtg_render_forward_masked", c_int32, [c_void_p, POINTER(rtg_camera), c_int32, POINTER(rtg_gaussians),
+                                            POINTER(rtg_render_params), c_void_p, c_void_p, c_void_p, c_float,
+                                            c_float, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("rtg_render_backward_l1", c_int32, [c_void_p] + [c_void_p] * 5 + [c_void_p]),
     ("rtg_render_backward", c_int32, [c_void_p] + [c_void_p] * 7 + [c_void_p]),
     ("rtg_adam_step", c_int32, [c_int64, c_int32] + [c_void_p] * 12 + [c_int32, POINTER(rtg_adam_params),

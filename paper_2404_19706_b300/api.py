@@ -250,6 +250,22 @@ def render_forward_l1(ctx: Context, cams, g: Gaussians, mask: Optional[torch.Ten
     _check(st, "rtg_render_forward_l1", ctx.ptr)
 
 
+def render_forward_masked(ctx: Context, cams, g: Gaussians, settings: RenderSettings, mask_out, color, depth, alpha,
+                          target_color=None, target_depth=None, w_color: float = 1.0, w_depth: float = 1.0,
+                          loss_out=None, index_map: Optional[torch.Tensor] = None, stream=None):
+    """Unstable-pixel mask (written to mask_out) and the forward on it, in one pass."""
+    arr, F = _cams(cams)
+    gc = g.to_c()
+    prm = settings.to_c()
+    st = _lib.load().rtg_render_forward_masked(
+        ctx.ptr, arr, F, ctypes.byref(gc), ctypes.byref(prm), _ptr(mask_out, torch.uint8, "mask_out"),
+        _ptr(target_color, torch.float32, "target_color"), _ptr(target_depth, torch.float32, "target_depth"),
+        float(w_color), float(w_depth), _ptr(color, torch.float32, "color"), _ptr(depth, torch.float32, "depth"),
+        _ptr(alpha, torch.float32, "alpha"), _ptr(index_map, torch.int32, "index_map"),
+        _ptr(loss_out, torch.float32, "loss_out"), _stream(stream))
+    _check(st, "rtg_render_forward_masked", ctx.ptr)
+
+
 def render_backward_l1(ctx: Context, g_means, g_scales, g_quats, g_opacity, g_colors, stream=None):
     st = _lib.load().rtg_render_backward_l1(ctx.ptr, _out_ptr(g_means, "g_means"), _out_ptr(g_scales, "g_scales"),
                                             _out_ptr(g_quats, "g_quats"), _out_ptr(g_opacity, "g_opacity"),

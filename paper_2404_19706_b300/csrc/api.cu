@@ -36,11 +36,11 @@ struct rtg_ctx {
 // Kernel kinds reported by the tracing interface (one launcher each).
 enum ProfKind {
   kPTileMask, kPUnstableIndex, kPProject, kPScanTiles, kPEmit, kPSortTiles, kPForward, kPL1Loss, kPBackward,
-  kPProjectBackward, kPUnstableMask, kPNumKinds
+  kPProjectBackward, kPUnstableMask, kPBin, kPNumKinds
 };
 static const char *kProfNames[kPNumKinds] = {"tile_mask", "unstable_index", "project", "scan_tiles",
                                              "emit", "sort_tiles", "forward", "l1_loss",
-                                             "backward", "project_backward", "unstable_mask"};
+                                             "backward", "project_backward", "unstable_mask", "bin"};
 constexpr int kProfMaxRecords = 1 << 16;
 
 struct ProfRec {
@@ -395,7 +395,8 @@ rtg_status rtg_reset_status(rtg_ctx *ctx) {
 }  // extern "C"
 
 static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, const rtg_gaussians *g,
-                               const uint8_t *mask, const rtg_render_params *prm, float *color, float *depth,
+                               const uint8_t *mask, uint8_t *mask_out, const rtg_render_params *prm, float *color,
+                               float *depth,
                                float *alpha, int32_t *index_map, const float *tcolor, const float *tdepth, float w_c,
                                float w_d, float *loss_out, void *stream) {
   if (ctx == nullptr) return RTG_ERR_ARG;
@@ -423,9 +424,27 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
   }
   if (gp.rank_map == nullptr)
     if ((st = rank_pass(ctx, gp.unstable, n, w.rank, w.ids, w.counters, nullptr, s)) != RTG_OK) return st;
-  {
+  if (mask_out != nullptr) {
+    // unstable mask in the same pass: bin the unstable Gaussians into every tile, test
+    // coverage and the tile rule, then bin everything into the surviving tiles
+    {
+      ProfScope ps(ctx, kPProject, s);
+      launch_project(gp, w, P, F, T, kProjFused, ctx->cap.max_pairs, s);
+    }
+    {
+      ProfScope ps(ctx, kPUnstableMask, s);  // coverage pass: scan, scatter, cover + tile rule
+      launch_scan_tiles(w, FT, ctx->cap.max_pairs, s);
+      launch_emit(w, s);
+      launch_mask_cover_tiles(w, P, n, F, T, gp.C, mask_out, true, s);
+    }
+    {
+      ProfScope ps(ctx, kPBin, s);
+      launch_bin(w, n, T, ctx->cap.max_pairs, s);
+    }
+    mask = mask_out;
+  } else {
     ProfScope ps(ctx, kPProject, s);
-    launch_project(gp, w, P, F, T, false, ctx->cap.max_pairs, s);
+    launch_project(gp, w, P, F, T, kProjForward, ctx->cap.max_pairs, s);
   }
   {
     ProfScope ps(ctx, kPScanTiles, s);
@@ -468,8 +487,8 @@ extern "C" {
 rtg_status rtg_render_forward(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, const rtg_gaussians *g,
                               const uint8_t *mask, const rtg_render_params *prm, float *color, float *depth,
                               float *alpha, int32_t *index_map, void *stream) {
-  return forward_impl(ctx, cams, F, g, mask, prm, color, depth, alpha, index_map, nullptr, nullptr, 0.f, 0.f,
-                      nullptr, stream);
+  return forward_impl(ctx, cams, F, g, mask, nullptr, prm, color, depth, alpha, index_map, nullptr, nullptr, 0.f,
+                      0.f, nullptr, stream);
 }
 
 rtg_status rtg_render_forward_l1(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, const rtg_gaussians *g,
@@ -479,8 +498,20 @@ rtg_status rtg_render_forward_l1(rtg_ctx *ctx, const rtg_camera *cams, int32_t F
   if (ctx == nullptr) return RTG_ERR_ARG;
   if (target_color == nullptr || target_depth == nullptr || loss_out == nullptr)
     return fail(ctx, RTG_ERR_ARG, "render_forward_l1: NULL target or loss_out");
-  return forward_impl(ctx, cams, F, g, mask, prm, color, depth, alpha, index_map, target_color, target_depth, w_color,
-                      w_depth, loss_out, stream);
+  return forward_impl(ctx, cams, F, g, mask, nullptr, prm, color, depth, alpha, index_map, target_color,
+                      target_depth, w_color, w_depth, loss_out, stream);
+}
+
+rtg_status rtg_render_forward_masked(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, const rtg_gaussians *g,
+                                     const rtg_render_params *prm, uint8_t *mask_out, const float *target_color,
+                                     const float *target_depth, float w_color, float w_depth, float *color,
+                                     float *depth, float *alpha, int32_t *index_map, float *loss_out, void *stream) {
+  if (ctx == nullptr) return RTG_ERR_ARG;
+  if (mask_out == nullptr) return fail(ctx, RTG_ERR_ARG, "render_forward_masked: mask_out is NULL");
+  if ((target_color == nullptr) != (target_depth == nullptr) || (target_color != nullptr && loss_out == nullptr))
+    return fail(ctx, RTG_ERR_ARG, "render_forward_masked: give both targets and loss_out, or none");
+  return forward_impl(ctx, cams, F, g, nullptr, mask_out, prm, color, depth, alpha, index_map, target_color,
+                      target_depth, w_color, w_depth, loss_out, stream);
 }
 
 rtg_status rtg_render_backward_l1(rtg_ctx *ctx, float *g_means, float *g_scales, float *g_quats, float *g_opacity,
@@ -657,10 +688,10 @@ rtg_status rtg_unstable_mask(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, co
   launch_tile_mask(fs, w, nullptr, T, gp.rank_map ? (long long)gp.n_unstable : -1ll, s);
   if (gp.u_means != nullptr && gp.rank_map == nullptr)
     if ((st = rank_pass(ctx, gp.unstable, gp.n, w.rank, w.ids, w.counters, nullptr, s)) != RTG_OK) return st;
-  launch_project(gp, w, P, F, T, true, ctx->cap.max_pairs, s);
+  launch_project(gp, w, P, F, T, kProjMask, ctx->cap.max_pairs, s);
   launch_scan_tiles(w, F * T, ctx->cap.max_pairs, s);
   launch_emit(w, s);
-  launch_mask_cover_tiles(w, P, gp.n, F, T, gp.C, mask, s);
+  launch_mask_cover_tiles(w, P, gp.n, F, T, gp.C, mask, false, s);
   ctx->last_stream = s;
   return check_launch(ctx, "unstable_mask");
 }

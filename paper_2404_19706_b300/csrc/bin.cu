@@ -157,13 +157,18 @@ __global__ void __launch_bounds__(256) k_cull(GaussPtrs g, Work w, Prm prm, int 
   }
 }
 
-// kMask = true: the unstable-mask pass (only unstable Gaussians reach this kernel through
-// k_cull<true>); no gradient rows are cleared and no visibility is counted.
+// kMode = kProjForward: records and pairs for the masked tiles of a forward.
+// kMode = kProjMask: the unstable-mask pass (only unstable Gaussians reach this kernel
+//   through k_cull<true>); no gradient rows are cleared and no visibility is counted.
+// kMode = kProjFused: first half of rtg_render_forward_masked: every projected candidate
+//   gets its records (its tile count is set later by k_bin, once the mask is known), and
+//   only the unstable ones are binned, into every tile, for the coverage test.
 // Every pair (candidate, masked tile) is staged as (tile, slot, key): the warp reserves its
 // staging range with one atomic, and each pair's slot in its tile bucket is the value the
 // tile counter returns, so the later scatter into buckets needs no atomics.
-template <int C, bool kMask>
+template <int C, int kMode>
 __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, int T, int64_t max_pairs) {
+  constexpr bool kMask = kMode == kProjMask;
   constexpr int H4 = (C <= 4) ? 3 : 4;
   constexpr int G2 = (C <= 5) ? 16 : 20;
   __shared__ uint32_t s_w[8];
@@ -201,33 +206,35 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
         const int tiles_x = w.cams[f].tiles_x;
         tx0 = o.x0 / kTile; tx1 = o.x1 / kTile; ty0 = o.y0 / kTile; ty1 = o.y1 / kTile;
         const uint32_t *npix = w.tile_npix + (int64_t)f * T;
-        for (int ty = ty0; ty <= ty1; ++ty)
-          for (int tx = tx0; tx <= tx1; ++tx) nt += npix[ty * tiles_x + tx] != 0u;
+        if (kMode != kProjFused || g.unstable[i] != 0)
+          for (int ty = ty0; ty <= ty1; ++ty)
+            for (int tx = tx0; tx <= tx1; ++tx) nt += npix[ty * tiles_x + tx] != 0u;
       }
     }
     // block-level reservation of the staging range (one atomic per block)
     const unsigned long long first = block_reserve(w.counters + kStaged, nt, s_w, &s_base);
-    if (!kMask) {
+    if (kMode == kProjForward) {
       const unsigned long long vbase = block_reserve(w.counters + kVisible, nt > 0 ? 1u : 0u, s_w, &s_base);
       (void)vbase;
     }
-    if (ok && nt > 0) {
+    if (ok && (nt > 0 || kMode == kProjFused)) {
       const DevCam &cam = w.cams[f];
       const uint32_t *npix = w.tile_npix + (int64_t)f * T;
       uint32_t *tcount = w.tile_count + (int64_t)f * T;
       const unsigned long long key = ((unsigned long long)__float_as_uint(o.Z) << 32) | (unsigned long long)(uint32_t)i;
       unsigned long long idx = first;
-      for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1; ++tx) {
-          const int t = ty * cam.tiles_x + tx;
-          if (npix[t] != 0u) {
-            const uint32_t slot = atomicAdd(tcount + t, 1u);
-            if (idx < (unsigned long long)max_pairs)
-              w.stage[idx] = make_uint4((uint32_t)((int64_t)f * T + t), slot, (uint32_t)(key & 0xffffffffull),
-                                        (uint32_t)(key >> 32));
-            ++idx;
+      if (nt > 0)  // kProjFused: stable Gaussians get records but no pairs here
+        for (int ty = ty0; ty <= ty1; ++ty)
+          for (int tx = tx0; tx <= tx1; ++tx) {
+            const int t = ty * cam.tiles_x + tx;
+            if (npix[t] != 0u) {
+              const uint32_t slot = atomicAdd(tcount + t, 1u);
+              if (idx < (unsigned long long)max_pairs)
+                w.stage[idx] = make_uint4((uint32_t)((int64_t)f * T + t), slot, (uint32_t)(key & 0xffffffffull),
+                                          (uint32_t)(key >> 32));
+              ++idx;
+            }
           }
-        }
       const int rk = w.rank[i];
       float4 *hot = w.rec_hot + ((int64_t)f * N + i) * H4;
       hot[0] = make_float4(o.mux.hi, o.muy.hi, o.mux.lo, o.muy.lo);
@@ -243,11 +250,60 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
       cold[0] = make_float4(o.n[0], o.n[1], o.n[2], o.d0);
       cold[1] = make_float4(o.Z, __int_as_float(rk), __uint_as_float((uint32_t)tx0 | ((uint32_t)ty0 << 16)),
                             __uint_as_float((uint32_t)tx1 | ((uint32_t)ty1 << 16)));
-      if (!kMask && rk >= 0) {
+      if (kMode != kProjMask && rk >= 0) {
         float4 *g2 = reinterpret_cast<float4 *>(w.grad2d + ((int64_t)f * N + rk) * G2);
 #pragma unroll
         for (int q = 0; q < G2 / 4; ++q) g2[q] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
+    }
+    // kProjFused: 1 marks "projected" for k_bin, which writes the final masked-tile count
+    if (k < ncand) w.ntiles[e] = (kMode == kProjFused) ? (ok ? 1u : 0u) : nt;
+  }
+}
+
+// Second half of rtg_render_forward_masked: bins every projected candidate into the tiles
+// that survived the unstable mask (tile_npix now holds each tile's masked-pixel count).
+__global__ void __launch_bounds__(256) k_bin(Work w, int64_t N, int T, int64_t max_pairs) {
+  __shared__ uint32_t s_w[8];
+  __shared__ unsigned long long s_base;
+  if (w.counters[kSkip] != 0ull) return;
+  const int64_t ncand = (int64_t)w.counters[kCand];
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < ncand; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = base + threadIdx.x;
+    uint32_t nt = 0, e = 0;
+    int f = 0, tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1, tiles_x = 0;
+    float4 c1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (k < ncand) {
+      e = w.cand[k];
+      if (w.ntiles[e] != 0u) {
+        f = (int)(e / (uint64_t)N);
+        tiles_x = w.cams[f].tiles_x;
+        c1 = w.rec_cold[(int64_t)e * 2 + 1];
+        const uint32_t lo = __float_as_uint(c1.z), hi = __float_as_uint(c1.w);
+        tx0 = lo & 0xffff; ty0 = lo >> 16; tx1 = hi & 0xffff; ty1 = hi >> 16;
+        const uint32_t *npix = w.tile_npix + (int64_t)f * T;
+        for (int ty = ty0; ty <= ty1; ++ty)
+          for (int tx = tx0; tx <= tx1; ++tx) nt += npix[ty * tiles_x + tx] != 0u;
+      }
+    }
+    const unsigned long long first = block_reserve(w.counters + kStaged, nt, s_w, &s_base);
+    const unsigned long long vbase = block_reserve(w.counters + kVisible, nt > 0 ? 1u : 0u, s_w, &s_base);
+    (void)vbase;
+    if (nt > 0) {
+      const int64_t i = (int64_t)e - (int64_t)f * N;
+      const uint32_t *npix = w.tile_npix + (int64_t)f * T;
+      uint32_t *tcount = w.tile_count + (int64_t)f * T;
+      const uint32_t klo = (uint32_t)i, khi = __float_as_uint(c1.x);
+      unsigned long long idx = first;
+      for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0; tx <= tx1; ++tx) {
+          const int t = ty * tiles_x + tx;
+          if (npix[t] != 0u) {
+            const uint32_t slot = atomicAdd(tcount + t, 1u);
+            if (idx < (unsigned long long)max_pairs) w.stage[idx] = make_uint4((uint32_t)((int64_t)f * T + t), slot, klo, khi);
+            ++idx;
+          }
+        }
     }
     if (k < ncand) w.ntiles[e] = nt;
   }
@@ -343,11 +399,11 @@ void launch_rank(const uint8_t *unstable, int64_t n, int32_t *block_cnt, int32_t
   k_rank_write<<<nb, kRankThreads, 0, s>>>(unstable, n, block_cnt, rank, ids, nu_counter, nu_out);
 }
 
-void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, int T, bool unstable_only,
-                    int64_t max_pairs, cudaStream_t s) {
+void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, int T, int mode, int64_t max_pairs,
+                    cudaStream_t s) {
   if (g.n <= 0) return;
   const unsigned nb = (unsigned)((g.n + 255) / 256);
-  if (unstable_only) {
+  if (mode == kProjMask) {
     if (g.rank_map != nullptr) {
       if (g.n_unstable > 0)
         k_cull<true><<<(unsigned)((g.n_unstable + 255) / 256), 256, 0, s>>>(g, w, prm, F, g.unstable_ids,
@@ -355,17 +411,25 @@ void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, in
     } else {
       k_cull<true><<<nb, 256, 0, s>>>(g, w, prm, F, nullptr, 0);
     }
-    if (g.C == 3)
-      k_project<3, true><<<kPersistBlocks, 256, 0, s>>>(g, w, prm, T, max_pairs);
-    else
-      k_project<8, true><<<kPersistBlocks, 256, 0, s>>>(g, w, prm, T, max_pairs);
   } else {
     k_cull<false><<<nb, 256, 0, s>>>(g, w, prm, F, nullptr, 0);
-    if (g.C == 3)
-      k_project<3, false><<<kPersistBlocks, 256, 0, s>>>(g, w, prm, T, max_pairs);
-    else
-      k_project<8, false><<<kPersistBlocks, 256, 0, s>>>(g, w, prm, T, max_pairs);
   }
+#define RTG_PROJ(CC, MM) k_project<CC, MM><<<kPersistBlocks, 256, 0, s>>>(g, w, prm, T, max_pairs)
+  if (g.C == 3) {
+    if (mode == kProjForward) RTG_PROJ(3, kProjForward);
+    else if (mode == kProjMask) RTG_PROJ(3, kProjMask);
+    else RTG_PROJ(3, kProjFused);
+  } else {
+    if (mode == kProjForward) RTG_PROJ(8, kProjForward);
+    else if (mode == kProjMask) RTG_PROJ(8, kProjMask);
+    else RTG_PROJ(8, kProjFused);
+  }
+#undef RTG_PROJ
+}
+
+void launch_bin(const Work &w, int64_t N, int T, int64_t max_pairs, cudaStream_t s) {
+  if (N <= 0) return;
+  k_bin<<<kPersistBlocks, 256, 0, s>>>(w, N, T, max_pairs);
 }
 
 void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, cudaStream_t s) {

@@ -71,8 +71,10 @@ void launch_tile_mask(const FrameSet &fs, const Work &w, const uint8_t *mask, in
                       cudaStream_t s);
 void launch_rank(const uint8_t *unstable, int64_t n, int32_t *block_cnt, int32_t *rank, int32_t *ids,
                  unsigned long long *nu_counter, int64_t *nu_out, cudaStream_t s);
-void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, int T, bool unstable_only,
-                    int64_t max_pairs, cudaStream_t s);
+enum ProjMode { kProjForward = 0, kProjMask = 1, kProjFused = 2 };
+void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, int T, int mode, int64_t max_pairs,
+                    cudaStream_t s);
+void launch_bin(const Work &w, int64_t N, int T, int64_t max_pairs, cudaStream_t s);
 void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, cudaStream_t s);
 void launch_emit(const Work &w, cudaStream_t s);
 // sort.cu
@@ -103,6 +105,6 @@ void launch_scatter(int64_t nu, int C, const int32_t *ids, const float *um, cons
                     const float *uo, const float *uc, float *means, float *scales, float *quats, float *opacity,
                     float *colors, cudaStream_t s);
 void launch_mask_cover_tiles(const Work &w, const Prm &prm, int64_t N, int F, int T, int C, uint8_t *mask,
-                             cudaStream_t s);
+                             bool fused, cudaStream_t s);
 
 }  // namespace rtg

@@ -251,6 +251,9 @@ __global__ void k_scatter(int64_t nu, int C, const int32_t *__restrict__ ids, co
 // stops as soon as all its pixels are covered.  The tile rule (Supplement B) is applied in
 // the same kernel: a tile with fewer than `discard` of its in-image pixels covered is
 // cleared.  Every in-image pixel of the mask is written.
+// kFused (rtg_render_forward_masked): the tile's masked-pixel count replaces the coverage
+// pass's tile activity and the pair counters are cleared for the second binning.
+template <bool kFused>
 __global__ void __launch_bounds__(kTilePix) k_mask_cover_tiles(Work w, Prm prm, int64_t N, int T, int H4,
                                                                uint8_t *__restrict__ mask) {
   __shared__ float4 s_rec[2][kTilePix];
@@ -291,9 +294,12 @@ __global__ void __launch_bounds__(kTilePix) k_mask_cover_tiles(Work w, Prm prm, 
   }
   const int n_in = __syncthreads_count(in);
   const int n_cov = __syncthreads_count(cov);
-  if (in) {
-    const bool keep = !(prm.discard > 0.f) || (float)n_cov >= prm.discard * (float)n_in;
-    mask[((int64_t)f * cam.H + py) * cam.W + px] = (cov && keep) ? 1 : 0;
+  const bool keep = !(prm.discard > 0.f) || (float)n_cov >= prm.discard * (float)n_in;
+  if (in) mask[((int64_t)f * cam.H + py) * cam.W + px] = (cov && keep) ? 1 : 0;
+  if (kFused && tid == 0) {
+    w.tile_npix[tile] = keep ? (uint32_t)n_cov : 0u;
+    w.tile_count[tile] = 0u;
+    if (tile == 0) w.counters[kStaged] = 0ull;
   }
 }
 
@@ -336,8 +342,11 @@ void launch_scatter(int64_t nu, int C, const int32_t *ids, const float *um, cons
 }
 
 void launch_mask_cover_tiles(const Work &w, const Prm &prm, int64_t N, int F, int T, int C, uint8_t *mask,
-                             cudaStream_t s) {
-  k_mask_cover_tiles<<<F * T, kTilePix, 0, s>>>(w, prm, N, T, hot4_of(C), mask);
+                             bool fused, cudaStream_t s) {
+  if (fused)
+    k_mask_cover_tiles<true><<<F * T, kTilePix, 0, s>>>(w, prm, N, T, hot4_of(C), mask);
+  else
+    k_mask_cover_tiles<false><<<F * T, kTilePix, 0, s>>>(w, prm, N, T, hot4_of(C), mask);
 }
 
 }  // namespace rtg

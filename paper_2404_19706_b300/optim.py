@@ -117,11 +117,15 @@ class MaskedStep:
     def _body(self, stream=None):
         s = self.state
         if self.recompute_mask:
-            api.unstable_mask(self.ctx, self.cams, self.g, self.settings, self.mask, stream)
-        # forward with the L1 loss fused in, then its backward (no gradient images)
-        api.render_forward_l1(self.ctx, self.cams, self.g, self.mask, self.settings, self.target_color,
-                              self.target_depth, self.w_color, self.w_depth, s.color, s.depth, s.alpha, self.loss,
-                              None, stream)
+            # mask, forward and L1 loss in one pass sharing a single projection
+            api.render_forward_masked(self.ctx, self.cams, self.g, self.settings, self.mask, s.color, s.depth,
+                                      s.alpha, self.target_color, self.target_depth, self.w_color, self.w_depth,
+                                      self.loss, None, stream)
+        else:
+            # forward with the L1 loss fused in (no gradient images)
+            api.render_forward_l1(self.ctx, self.cams, self.g, self.mask, self.settings, self.target_color,
+                                  self.target_depth, self.w_color, self.w_depth, s.color, s.depth, s.alpha,
+                                  self.loss, None, stream)
         api.render_backward_l1(self.ctx, *self.grads, stream=stream)
         api.adam_step_counted(self.u, self.grads, self.m, self.v, self.step_counter, self.adam, stream)
         api.scatter_unstable(self.ids, self.u, self.g, stream)

@@ -239,3 +239,35 @@ def test_fused_l1_forward_backward_match_separate_calls():
     for a, b in zip(g1, g2):
         np.testing.assert_allclose(b.cpu().numpy(), a.cpu().numpy(), rtol=1e-5, atol=1e-9)
     assert float(l1[0]) > 0
+
+
+def test_forward_masked_equals_mask_then_forward():
+    """rtg_render_forward_masked gives bit for bit the mask of rtg_unstable_mask and the
+    render of rtg_render_forward on it (and the fused loss of rtg_render_forward_l1)."""
+    m = rtg()
+    scene, layout = synth.room_scene(2070, 20000)
+    cams = [c for _, c in zip(range(2), synth.room_camera_candidates(2071, layout, 112, 80, 100.0))]
+    scene.unstable = synth.flag_blobs(scene, cams, 3000, 3, seed=13)
+    tref = gpu_forward(synth.jitter_scene(scene, 14), cams)
+    tc = torch.tensor(tref["color"]).cuda()
+    td = torch.tensor(np.where(tref["depth"] > 0, tref["depth"], 0)).cuda()
+    ctx = ctx_for(scene.n, cams)
+    g = m.Gaussians.from_scene(scene)
+
+    def bufs():
+        return (torch.zeros(2, 80, 112, dtype=torch.uint8, device="cuda"), torch.zeros(2, 3, 80, 112, device="cuda"),
+                torch.full((2, 80, 112), -1.0, device="cuda"), torch.zeros(2, 80, 112, device="cuda"),
+                torch.full((2, 80, 112), -1, dtype=torch.int32, device="cuda"), torch.zeros(3, device="cuda"))
+
+    mk1, c1, d1, a1, i1, l1 = bufs()
+    m.unstable_mask(ctx, cams, g, m.RenderSettings(), mk1)
+    m.render_forward_l1(ctx, cams, g, mk1, m.RenderSettings(), tc, td, 1.0, 1.0, c1, d1, a1, l1, i1)
+    s1 = m.get_stats(ctx)
+    mk2, c2, d2, a2, i2, l2 = bufs()
+    m.render_forward_masked(ctx, cams, g, m.RenderSettings(), mk2, c2, d2, a2, tc, td, 1.0, 1.0, l2, i2)
+    s2 = m.get_stats(ctx)
+    torch.cuda.synchronize()
+    for a, b in ((mk1, mk2), (c1, c2), (d1, d2), (a1, a2), (i1, i2), (l1, l2)):
+        assert torch.equal(a, b)
+    assert s1["pairs"] == s2["pairs"] and s1["fragments"] == s2["fragments"] and s1["visible"] == s2["visible"]
+    assert s2["masked_pixels"] == int(mk2.sum()) > 0 and s2["status"] == 0
