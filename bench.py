@@ -33,9 +33,12 @@ METRIC = "masked fwd+bwd iterations/sec and fragments/sec at 640×480; % HBM roo
 WORKLOAD = dict(name="masked-step room 1M Gaussians (20% unstable, 3 blobs) 640x480, tile rule 0.5",
                 seed=3000, n=1_000_000, n_unstable=200_000, blobs=3, width=640, height=480, f=600.0,
                 coverage=(0.25, 0.40))
+KF_METRIC = "batched keyframe fwd+bwd frames/sec at 1200×680 (8 keyframes in one graph) vs per-frame launches"
+KEYFRAMES = dict(name="batched keyframes: 8 x 1200x680 (f 600), multi-room 12x10x3 m (2x2 rooms, 40 boxes), "
+                      "2M Gaussians (10% unstable, 8 blobs), mask coverage 10-60%",
+                 seed=4000, n=2_000_000, n_unstable=200_000, blobs=8, frames=8, width=1200, height=680, f=600.0,
+                 coverage=(0.10, 0.60), max_pairs=48 << 20)
 C = 3
-P_IN, R_REC, Q_PIX, G2 = 44 + 4 * C, 36 + 4 * C, 4 * C + 16, 4 * (11 + C)  # bytes per unit
-KERNELS_PER_STEP = 17  # masked forward 11, loss finalize 1, backward 2, adam 2, scatter 1
 
 
 def parse():
@@ -46,6 +49,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--candidate", type=int, default=-1, help="camera candidate index (-1: search)")
+    ap.add_argument("--workload", default="masked-step", choices=["masked-step", "keyframes"],
+                    help="masked-step: the 640x480 masked iteration (default); keyframes: 8 batched 1200x680 "
+                         "keyframes vs per-frame launches")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch configuration")
+    ap.add_argument("--tune-table", default="", help="write the autotuner's candidate table (JSON) to this path")
     return ap.parse_args()
 
 
@@ -173,7 +181,143 @@ def oracle_rate(scene, cam, masked_pixels, n_masked, targets, seconds_budget=25.
                        f"{n_masked} masked px x {per_px * 1e3:.1f} ms (extrapolated)")
 
 
-# ----------------------------------------------------------------------------- GPU arm
+# ----------------------------------------------------------------------------- GPU arm helpers
+
+class Snapshot:
+    """Copies of the tensors an optimisation step moves, put back after every tuning
+    candidate so that each candidate times the same workload."""
+
+    def __init__(self, tensors):
+        self.src = [t for t in tensors if t is not None and t.numel() > 0]
+        self.copy = [t.clone() for t in self.src]
+
+    def restore(self):
+        for t, c in zip(self.src, self.copy):
+            t.copy_(c)
+
+
+def step_state(step):
+    g = step.g
+    return [g.means, g.scales, g.quats, g.opacity, g.colors, *step.u, step.m, step.v, step.step_counter]
+
+
+def run_tuner(ctx, body, check, tensors, args, label):
+    """Autotunes the context's launch configuration on this workload (unless --no-tune)."""
+    if args.no_tune:
+        return None
+    from paper_2404_19706_b300.tune import autotune
+    snap = Snapshot(tensors)
+    t0 = time.perf_counter()
+    res = autotune(ctx, body, check, snap.restore)
+    snap.restore()
+    print(f"[{label}] autotune {time.perf_counter() - t0:.1f} s: best {res.best.as_dict()} {res.best_ms:.4f} ms "
+          f"(default {res.default_ms:.4f} ms)", file=sys.stderr)
+    if args.tune_table:
+        with open(args.tune_table if label == "step" else f"{args.tune_table}.{label}", "w") as fh:
+            json.dump({"label": label, "summary": res.summary(), "table": res.table}, fh, indent=1)
+    return res
+
+
+def kernel_profile(rtg, ctx, step, steps, flush, stream):
+    """Per-kernel device ms per launch from `steps` eager iterations with the library's
+    event tracing on (and events around the Adam call, which has no context)."""
+    import paper_2404_19706_b300.optim as optim_mod
+    graph, step.graph = step.graph, None
+    adam_ev = []
+    orig_adam = rtg.api.adam_step_counted
+
+    def adam_timed(*a, **kw):
+        import torch
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        orig_adam(*a, **kw)
+        e1.record(stream)
+        adam_ev.append((e0, e1))
+
+    import torch
+    optim_mod.api.adam_step_counted = adam_timed
+    try:
+        rtg.profile_enable(ctx, True)
+        rtg.profile_read(ctx)
+        for _ in range(steps):
+            flush.zero_()
+            step.step()
+        torch.cuda.synchronize()
+        prof = rtg.profile_read(ctx)
+        rtg.profile_enable(ctx, False)
+    finally:
+        optim_mod.api.adam_step_counted = orig_adam
+        step.graph = graph
+    prof["adam"] = (len(adam_ev), sum(a.elapsed_time(b) for a, b in adam_ev))
+    return {k: (v[1] / v[0] if v[0] else 0.0) for k, v in prof.items()}
+
+
+def alg_bytes(stats, N, F, H, W, Cc=C):
+    """Algorithmic bytes per launch of each kernel kind, from the step's own counters."""
+    p_in, r_rec, q_pix, g2 = 44 + 4 * Cc, 36 + 4 * Cc, 4 * Cc + 16, 4 * (11 + Cc)
+    V, K, P, Nu = stats["visible"], stats["pairs"], stats["masked_pixels"], stats["n_unstable"]
+    tw, th = stats["tile_w"], stats["tile_h"]
+    FT = F * ((W + tw - 1) // tw) * ((H + th - 1) // th)
+    return {
+        "unstable_mask": Nu * p_in + F * H * W,
+        "tile_mask": F * H * W,
+        "unstable_index": N * 9,
+        "project": N * p_in + V * r_rec,
+        "scan_tiles": FT * 16,
+        "emit": K * 12,
+        "bin": V * 32 + K * 16,
+        "sort_tiles": K * 24,
+        "forward": K * r_rec + P * (q_pix + 4 * Cc + 4),
+        "l1_loss": FT * 8 * 12,
+        "backward": K * r_rec + P * (q_pix + 2 * (4 * Cc + 4)) + Nu * g2,
+        "project_backward": Nu * (g2 + 2 * p_in),
+        "adam": Nu * p_in * 7,
+    }
+
+
+def roofline_of(per_launch, alg):
+    single = ["project", "emit", "sort_tiles", "forward", "backward", "project_backward", "adam", "scan_tiles",
+              "tile_mask", "bin"]
+    dom = max(single, key=lambda k: per_launch.get(k, 0.0))
+    pk = peaks()
+    achieved = alg[dom] / (per_launch[dom] * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": pk["hbm_gbs"],
+            "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": None,
+            "peak_source": "fallback" if pk.get("_fallback") else "measured (MEASURED_PEAKS.json hbm_gbs)",
+            "alg_bytes_per_launch": int(alg[dom]), "ms_per_launch": round(per_launch[dom], 5)}, pk
+
+
+def kernels_per_step(stats, per_frame_calls=1):
+    """Kernels one masked step launches: the fused masked forward (11, plus a render-grid
+    tile-mask pass when the render tile is not 16 x 16) and loss finalize per forward call,
+    backward 2 per call, then Adam 2 and the scatter 1."""
+    extra = 0 if (stats["tile_w"], stats["tile_h"]) == (16, 16) else 1
+    return per_frame_calls * (11 + extra + 1 + 2) + 3
+
+
+def timed_replays(step, steps, flush, stream, local, dist=None):
+    """K graph replays, each between CUDA events on the launching stream, L2 flushed before each."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        wall0 = time.perf_counter()
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            step.step()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if dist is not None:
+        dist.barrier()
+    ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    return float(np.mean(ms)), wall, clocks
+
+
+# ----------------------------------------------------------------------------- GPU arm: masked step
 
 def run_ours(args):
     import torch
@@ -226,6 +370,17 @@ def run_ours(args):
     step = rtg.MaskedStep(ctx, g, [cam], mask, tcol, tdep, settings, recompute_mask=True)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 126 MB L2
+
+    # ---- launch configuration: autotuned on this workload (renders checked bit-identical)
+    ck = dict(mask=torch.zeros_like(mask), color=torch.zeros_like(tcol), depth=torch.zeros_like(tdep),
+              alpha=torch.zeros_like(talp))
+
+    def check():
+        rtg.render_forward_masked(ctx, [cam], step.g, settings, ck["mask"], ck["color"], ck["depth"], ck["alpha"])
+        return [ck["mask"], ck["color"], ck["depth"], ck["alpha"]]
+
+    tuned = run_tuner(ctx, step._body, check, step_state(step), args, "step")
+
     for _ in range(args.warmup):
         step.step()
     torch.cuda.synchronize()
@@ -235,86 +390,21 @@ def run_ours(args):
     step.step()
     torch.cuda.synchronize()
 
-    # ---- timed region: K graph replays, each bracketed by CUDA events; L2 flushed before each
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clocks:
-        wall0 = time.perf_counter()
-        for e0, e1 in ev:
-            flush.zero_()
-            e0.record(stream)
-            step.step()
-            e1.record(stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - wall0
-    if dist is not None:
-        dist.barrier()
-    ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    # ---- timed region: K graph replays
+    ms_step, wall, clocks = timed_replays(step, args.steps, flush, stream, local, dist)
     stats = rtg.get_stats(ctx)
     assert stats["status"] == 0, stats
-    ms_step = float(np.mean(ms))
     if dist is not None:
         t = torch.tensor([ms_step], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
 
-    # ---- per-kernel device time, live: K eager steps with the library's event tracing on
-    import paper_2404_19706_b300.optim as optim_mod
-    graph, step.graph = step.graph, None
-    adam_ev = []
-    orig_adam = rtg.api.adam_step_counted
-
-    def adam_timed(*a, **kw):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        orig_adam(*a, **kw)
-        e1.record(stream)
-        adam_ev.append((e0, e1))
-
-    optim_mod.api.adam_step_counted = adam_timed
-    rtg.profile_enable(ctx, True)
-    rtg.profile_read(ctx)
-    for _ in range(args.steps):
-        flush.zero_()
-        step.step()
-    torch.cuda.synchronize()
-    prof = rtg.profile_read(ctx)
-    rtg.profile_enable(ctx, False)
-    optim_mod.api.adam_step_counted = orig_adam
-    step.graph = graph
-    prof["adam"] = (len(adam_ev), sum(a.elapsed_time(b) for a, b in adam_ev))
-
-    # ---- algorithmic bytes (per launch) of each kernel kind, from the step's own counters
+    # ---- per-kernel device time, live, and the roofline of the dominant kernel
+    per_launch = kernel_profile(rtg, ctx, step, args.steps, flush, stream)
     N, V, K, P, Nu = scene.n, stats["visible"], stats["pairs"], stats["masked_pixels"], stats["n_unstable"]
-    FT = ((W + 15) // 16) * ((H + 15) // 16)
-    alg = {
-        "unstable_mask": Nu * P_IN + H * W,
-        "tile_mask": H * W,
-        "unstable_index": N * 9,
-        "project": N * P_IN + V * R_REC,
-        "scan_tiles": FT * 16,
-        "emit": K * 12,
-        "bin": V * 32 + K * 16,
-        "sort_tiles": K * 24,
-        "forward": K * R_REC + P * (Q_PIX + 4 * C + 4),
-        "l1_loss": FT * 8 * 12,
-        "backward": K * R_REC + P * (Q_PIX + 2 * (4 * C + 4)) + Nu * G2,
-        "project_backward": Nu * (G2 + 2 * P_IN),
-        "adam": Nu * P_IN * 7,
-    }
-    per_launch = {k: (v[1] / v[0] if v[0] else 0.0) for k, v in prof.items()}
-    single = ["project", "emit", "sort_tiles", "forward", "backward", "project_backward", "adam", "scan_tiles",
-              "tile_mask", "bin"]
-    dom = max(single, key=lambda k: per_launch.get(k, 0.0))
-    pk = peaks()
-    achieved = alg[dom] / (per_launch[dom] * 1e-3) / 1e9
+    alg = alg_bytes(stats, N, 1, H, W)
+    roofline, pk = roofline_of(per_launch, alg)
     b_step = sum(alg.values())
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": pk["hbm_gbs"],
-                "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": None,
-                "peak_source": "fallback" if pk.get("_fallback") else "measured (MEASURED_PEAKS.json hbm_gbs)",
-                "alg_bytes_per_launch": int(alg[dom]), "ms_per_launch": round(per_launch[dom], 5)}
 
     # ---- end to end through the public API with host buffers (graph replay per step)
     hc = torch.empty_like(tcol, device="cpu").pin_memory()
@@ -353,6 +443,8 @@ def run_ours(args):
                        "fragments_per_sec": round(world * stats["fragments"] * 1e3 / ms_step, 1),
                        "alg_bytes_per_step": int(b_step),
                        "step_hbm_roofline_frac": round(b_step / (ms_step * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
+                       "tuning": ctx.get_tuning().as_dict(),
+                       "autotune": tuned.summary() if tuned is not None else "off (--no-tune)",
                        "l2": "256 MB buffer written before every step, outside the timed spans",
                        "timing": "timed steps replay one CUDA graph of the whole step; kernel_ms_per_launch and "
                                  "the roofline come from a second live pass of the same number of eager steps "
@@ -363,7 +455,7 @@ def run_ours(args):
             "roofline": roofline,
             "e2e": {"value": round(world * 1e3 / e2e_step, 2), "unit": "iter/s",
                     "h2d_bytes_per_step": int(hc.numel() * 4 + hd.numel() * 4), "d2h_bytes_per_step": 12},
-            "gpu_launches": KERNELS_PER_STEP * args.steps,
+            "gpu_launches": kernels_per_step(stats) * args.steps,
             "clocks": clk,
         }
         if world == 1 and not args.no_cpu_baseline:
@@ -373,6 +465,240 @@ def run_ours(args):
         dist.destroy_process_group()
     ctx.close()
     return result
+
+
+# ----------------------------------------------------------------------------- GPU arm: batched keyframes
+
+class PerFrameStep:
+    """The masked iteration over F keyframes as F single-frame calls: for each frame the
+    fused mask + forward + L1 and its backward (gradients accumulated over the frames),
+    then one Adam step and the scatter, exactly what MaskedStep does for all F at once."""
+
+    def __init__(self, rtg, ctx1, g, cams, masks, tcol, tdep, settings):
+        from paper_2404_19706_b300 import api
+        self.api, self.ctx, self.cams, self.settings = api, ctx1, cams, settings
+        self.masks, self.tcol, self.tdep = masks, tcol, tdep
+        self.inner = rtg.MaskedStep(ctx1, g, [cams[0]], masks[0:1], tcol[0:1], tdep[0:1], settings,
+                                    recompute_mask=True)
+        self.g, self.u, self.m, self.v, self.step_counter = (self.inner.g, self.inner.u, self.inner.m,
+                                                             self.inner.v, self.inner.step_counter)
+        F, Cc, H, W = tcol.shape
+        dev = tcol.device
+        self.color = torch_zeros((1, Cc, H, W), dev)
+        self.depth = torch_zeros((1, H, W), dev)
+        self.alpha = torch_zeros((1, H, W), dev)
+        self.loss = torch_zeros((F, 3), dev)
+        self.graph = None
+
+    def _body(self, stream=None):
+        api, s = self.api, self.inner
+        for f, cam in enumerate(self.cams):
+            api.render_forward_masked(self.ctx, [cam], s.g, self.settings, self.masks[f:f + 1], self.color,
+                                      self.depth, self.alpha, self.tcol[f:f + 1], self.tdep[f:f + 1], 1.0, 1.0,
+                                      self.loss[f], None, stream)
+            api.render_backward_l1(self.ctx, *s.grads, accumulate=f > 0, stream=stream)
+        api.adam_step_counted(s.u, s.grads, s.m, s.v, s.step_counter, s.adam, stream)
+        api.scatter_unstable(s.ids, s.u, s.g, stream)
+        return self.loss
+
+    def step(self):
+        if self.graph is not None:
+            self.graph.replay()
+            return self.loss
+        return self._body()
+
+    def capture(self):
+        import torch
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            self._body()
+        torch.cuda.synchronize()
+        self.graph = graph
+
+
+def torch_zeros(shape, dev):
+    import torch
+    return torch.zeros(shape, device=dev)
+
+
+def keyframes_workload(rtg, dev, settings):
+    """Scene, unstable flags, the F keyframes (coverage spread over the range) and targets."""
+    import torch
+    kw = KEYFRAMES
+    F, H, W = kw["frames"], kw["height"], kw["width"]
+    t0 = time.perf_counter()
+    scene, layout = synth.multiroom_scene(kw["seed"], kw["n"])
+    scene.unstable = synth.flag_blobs(scene, [], kw["n_unstable"], kw["blobs"], seed=kw["seed"] + 100, n_in_view=0)
+    print(f"keyframes: scene {time.perf_counter() - t0:.1f} s", file=sys.stderr)
+    ctx = rtg.Context(max_gaussians=scene.n, max_frames=F, max_width=W, max_height=H, max_pairs=kw["max_pairs"])
+    g = rtg.Gaussians.from_scene(scene, device=dev)
+    cams = synth.room_camera_candidates(kw["seed"] + 1, layout, W, H, kw["f"])
+    lo, hi = kw["coverage"]
+    edges = np.linspace(lo, hi, F // 2 + 1)  # two frames per coverage band, for uneven masks
+    per_band = {b: [] for b in range(F // 2)}
+    masks = torch.zeros(F, H, W, dtype=torch.uint8, device=dev)
+    drawn = 0
+    while sum(len(v) for v in per_band.values()) < F and drawn < 64 * F:
+        batch = [next(cams) for _ in range(F)]
+        drawn += F
+        rtg.unstable_mask(ctx, batch, g, settings, masks)
+        covs = masks.float().mean(dim=(1, 2)).tolist()
+        for c, v in zip(batch, covs):
+            if lo <= v <= hi:
+                bnd = min(int(np.searchsorted(edges, v, side="right")) - 1, F // 2 - 1)
+                if len(per_band[bnd]) < 2:
+                    per_band[bnd].append((c, v))
+    chosen = [cv for b in range(F // 2) for cv in per_band[b]]
+    assert len(chosen) == F, f"only {len(chosen)} keyframes with coverage in [{lo}, {hi}] after {drawn} poses"
+    kcams = [c for c, _ in chosen]
+    rtg.unstable_mask(ctx, kcams, g, settings, masks)
+    covs = masks.float().mean(dim=(1, 2)).tolist()
+    target = synth.jitter_scene(scene, kw["seed"] + 7)
+    gt = rtg.Gaussians.from_scene(target, device=dev)
+    tcol = torch.zeros(F, C, H, W, device=dev)
+    tdep = torch.full((F, H, W), -1.0, device=dev)
+    talp = torch.zeros(F, H, W, device=dev)
+    for f in range(F):  # full frames, one at a time (the largest pair count of the run)
+        rtg.render_forward(ctx, [kcams[f]], gt, None, settings, tcol[f:f + 1], tdep[f:f + 1], talp[f:f + 1])
+    torch.cuda.synchronize()
+    assert rtg.get_status(ctx) == 0
+    tdep = torch.where(tdep > 0, tdep, torch.zeros_like(tdep))
+    del gt
+    print(f"keyframes: {drawn} poses drawn, coverages {[round(c, 3) for c in covs]}, "
+          f"setup {time.perf_counter() - t0:.1f} s", file=sys.stderr)
+    return scene, ctx, kcams, covs, tcol, tdep
+
+
+def run_keyframes(args):
+    """Batched keyframes: one graph over F frames vs F per-frame launch sequences."""
+    import torch
+    import paper_2404_19706_b300 as rtg
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    settings = rtg.RenderSettings()
+    kw = KEYFRAMES
+    F, H, W = kw["frames"], kw["height"], kw["width"]
+    scene, ctx, kcams, covs, tcol, tdep = keyframes_workload(rtg, dev, settings)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    # batched: every frame in one call per kernel, one graph
+    masks_b = torch.zeros(F, H, W, dtype=torch.uint8, device=dev)
+    gb = rtg.Gaussians.from_scene(scene, device=dev)
+    batched = rtg.MaskedStep(ctx, gb, kcams, masks_b, tcol, tdep, settings, recompute_mask=True)
+    ckb = dict(mask=torch.zeros_like(masks_b), color=torch.zeros_like(tcol), depth=torch.zeros_like(tdep),
+               alpha=torch.zeros_like(tdep))
+
+    def check_b():
+        for t in ckb.values():
+            t.zero_()
+        rtg.render_forward_masked(ctx, kcams, batched.g, settings, ckb["mask"], ckb["color"], ckb["depth"],
+                                  ckb["alpha"])
+        return [ckb["mask"], ckb["color"], ckb["depth"], ckb["alpha"]]
+
+    tuned_b = run_tuner(ctx, batched._body, check_b, step_state(batched), args, "batched")
+
+    # per frame: the same iteration as F single-frame call sequences
+    ctx1 = rtg.Context(max_gaussians=scene.n, max_frames=1, max_width=W, max_height=H, max_pairs=kw["max_pairs"])
+    masks_p = torch.zeros(F, H, W, dtype=torch.uint8, device=dev)
+    gp = rtg.Gaussians.from_scene(scene, device=dev)
+    perframe = PerFrameStep(rtg, ctx1, gp, kcams, masks_p, tcol, tdep, settings)
+    ckp = dict(mask=torch.zeros(1, H, W, dtype=torch.uint8, device=dev), color=torch.zeros(1, C, H, W, device=dev),
+               depth=torch.zeros(1, H, W, device=dev), alpha=torch.zeros(1, H, W, device=dev))
+
+    def check_p():
+        rtg.render_forward_masked(ctx1, [kcams[0]], perframe.g, settings, ckp["mask"], ckp["color"], ckp["depth"],
+                                  ckp["alpha"])
+        return [ckp["mask"], ckp["color"], ckp["depth"], ckp["alpha"]]
+
+    tuned_p = run_tuner(ctx1, perframe._body, check_p, step_state(perframe), args, "per_frame")
+
+    # before any optimiser step the two arms render the same thing: the batched call gives
+    # every frame bit for bit what a call with that frame alone gives (masks and images)
+    check_b()
+    for f in range(F):
+        for t in ckp.values():  # outputs are written on masked pixels only
+            t.zero_()
+        rtg.render_forward_masked(ctx1, [kcams[f]], perframe.g, settings, ckp["mask"], ckp["color"], ckp["depth"],
+                                  ckp["alpha"])
+        for k in ("mask", "color", "depth", "alpha"):
+            assert torch.equal(ckp[k][0], ckb[k][f]), f"frame {f}: batched and per-frame {k} differ"
+    torch.cuda.synchronize()
+
+    results = {}
+    for name, st, c in (("batched", batched, ctx), ("per_frame", perframe, ctx1)):
+        for _ in range(args.warmup):
+            st.step()
+        torch.cuda.synchronize()
+        assert rtg.get_status(c) == 0, name
+        st.capture()
+        st.step()
+        torch.cuda.synchronize()
+        ms, wall, clocks = timed_replays(st, args.steps, flush, stream, local)
+        assert rtg.get_status(c) == 0, name
+        results[name] = dict(ms=ms, wall=wall, clocks=clocks, stats=rtg.get_stats(c))
+
+    per_launch = kernel_profile(rtg, ctx, batched, args.steps, flush, stream)
+    sb = results["batched"]["stats"]
+    alg = alg_bytes(sb, scene.n, F, H, W)
+    roofline, pk = roofline_of(per_launch, alg)
+    b_step = sum(alg.values())
+
+    # end to end: targets uploaded from pinned host memory and the losses read back each step
+    hc = torch.empty_like(tcol, device="cpu").pin_memory()
+    hd = torch.empty_like(tdep, device="cpu").pin_memory()
+    hc.copy_(tcol.cpu())
+    hd.copy_(tdep.cpu())
+    hloss = torch.empty(3, pin_memory=True)
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        batched.target_color.copy_(hc, non_blocking=True)
+        batched.target_depth.copy_(hd, non_blocking=True)
+        loss = batched.step()
+        hloss.copy_(loss, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        if i >= args.warmup:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_step = float(np.mean(e2e_ms))
+
+    if rank != 0:
+        return None
+    msb, msp = results["batched"]["ms"], results["per_frame"]["ms"]
+    return {
+        "metric": KF_METRIC, "value": round(F * 1e3 / msb, 2), "unit": "frames/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(msb, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": kw["name"], "gaussians": scene.n, "unstable": sb["n_unstable"], "frames": F,
+                   "width": W, "height": H, "mask_coverage": [round(c, 4) for c in covs],
+                   "masked_pixels": sb["masked_pixels"], "pairs": sb["pairs"], "visible": sb["visible"],
+                   "fragments_per_step": sb["fragments"],
+                   "fragments_per_sec": round(sb["fragments"] * 1e3 / msb, 1),
+                   "alg_bytes_per_step": int(b_step),
+                   "step_hbm_roofline_frac": round(b_step / (msb * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
+                   "tuning": ctx.get_tuning().as_dict(),
+                   "autotune": tuned_b.summary() if tuned_b is not None else "off (--no-tune)",
+                   "per_frame": {"value": round(F * 1e3 / msp, 2), "unit": "frames/s", "ms_per_step": round(msp, 4),
+                                 "tuning": ctx1.get_tuning().as_dict(),
+                                 "autotune": tuned_p.summary() if tuned_p is not None else "off (--no-tune)",
+                                 "gpu_launches_per_step": kernels_per_step(results["per_frame"]["stats"], F)},
+                   "batched_over_per_frame": round(msp / msb, 3),
+                   "l2": "256 MB buffer written before every step, outside the timed spans",
+                   "timing": "each arm replays one CUDA graph of its whole step (F-frame calls, or F single-frame "
+                             "call sequences); kernel_ms_per_launch from a live eager pass of the batched step",
+                   "kernel_ms_per_launch": {k: round(v, 5) for k, v in per_launch.items()},
+                   "parallelism": "replicas x1"},
+        "roofline": roofline,
+        "e2e": {"value": round(F * 1e3 / e2e_step, 2), "unit": "frames/s",
+                "h2d_bytes_per_step": int(hc.numel() * 4 + hd.numel() * 4), "d2h_bytes_per_step": 12},
+        "gpu_launches": kernels_per_step(sb) * args.steps,
+        "clocks": results["batched"]["clocks"].summary(),
+    }
 
 
 def cpu_baseline_from_gpu(scene, cam, mask, tcol, tdep, n_masked):
@@ -443,7 +769,12 @@ DEFAULT_CANDIDATE = 7  # first pose of the seeded stream with 25-40% mask covera
 
 def main():
     args = parse()
-    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.impl == "reference":
+        out = run_reference(args)
+    elif args.workload == "keyframes":
+        out = run_keyframes(args)
+    else:
+        out = run_ours(args)
     if out is not None:
         print(json.dumps(out))
 

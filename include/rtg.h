@@ -44,7 +44,7 @@ typedef enum {
 } rtg_status;
 
 #define RTG_MAX_FRAMES 32 /* cameras per call (keyframe batch) */
-#define RTG_TILE 16       /* screen tiles are 16 x 16 pixels (Supplement B) */
+#define RTG_TILE 16       /* tile grid of the unstable-mask rule: 16 x 16 pixels (Supplement B) */
 
 /* Pinhole camera and camera-to-world pose T_g (Section 3.1). HOST struct. */
 typedef struct {
@@ -107,7 +107,37 @@ typedef struct {
   int64_t n_unstable;     /* unstable Gaussians (rows of the compact gradients) */
   int32_t status;         /* device status word (rtg_status) */
   int32_t max_tile_pairs; /* longest per-tile list */
+  int32_t tile_w, tile_h; /* render tile of that forward (rtg_tuning) */
 } rtg_stats;
+
+/* Launch configuration of the render path.  Section 3.1 rasterises by screen tiles but
+ * fixes neither their size nor how the work is spread over the GPU, so these are free
+ * choices for an autotuner.  None of them changes a rendered value: colour, depth, alpha,
+ * index map and unstable mask are bit-identical under every valid setting; the loss and
+ * the gradients agree to float32 rounding (their summation order changes).
+ *   tile_w x tile_h   render tile: 8x8, 8x16, 16x8, 16x16 or 32x8 pixels.  The tile rule
+ *                     of the unstable mask stays on its own 16x16 grid (RTG_TILE).
+ *   batch             records a warp tests against its pixel box and stages per step:
+ *                     32 or 64.
+ *   schedule          0: one CTA per tile, one warp per 32 masked pixels of it;
+ *                     1: persistent warps that take (tile, 32-pixel group) items from a
+ *                     queue ordered by tile list length, longest first, spanning every
+ *                     frame of the call.
+ *   persist_ctas_per_sm  schedule 1: CTAs of 256 threads per SM, 1..8.
+ *   sort_digit_bits   radix digit width of the per-tile depth sort: 4 or 8.
+ *   sort_rank_max     buckets of at most this many keys are ordered by ranking (a key's
+ *                     position is the number of smaller keys) instead of radix passes;
+ *                     0..2048, 0 = never.
+ * Defaults: 16x16, 32, schedule 0, 4, 8, 0.  A setting takes effect at the next forward;
+ * the backward always uses the setting of the forward it follows. */
+typedef struct {
+  int32_t tile_w, tile_h;
+  int32_t batch;
+  int32_t schedule;
+  int32_t persist_ctas_per_sm;
+  int32_t sort_digit_bits;
+  int32_t sort_rank_max;
+} rtg_tuning;
 
 /* Bytes of device workspace rtg_create allocates for `cap`. */
 rtg_status rtg_workspace_size(const rtg_capacity *cap, size_t *bytes);
@@ -118,6 +148,13 @@ rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap);
 
 /* Free a context and its workspace (NULL is accepted). */
 rtg_status rtg_destroy(rtg_ctx *ctx);
+
+/* Replace / read the context's launch configuration (HOST structs).  An invalid setting
+ * returns RTG_ERR_ARG and leaves the current one in place.  The workspace is sized for
+ * every valid setting, but smaller tiles make more (Gaussian, tile) pairs, so a forward
+ * can overflow max_pairs under one tiling and not another (RTG_ERR_WORKSPACE status). */
+rtg_status rtg_set_tuning(rtg_ctx *ctx, const rtg_tuning *t);
+rtg_status rtg_get_tuning(rtg_ctx *ctx, rtg_tuning *out);
 
 /* Unstable-pixel mask (Supplement B, Eq. S2): mask[f,y,x] = 1 where some unstable
  * Gaussian covers the pixel (f >= alpha_min, i.e. T_unstable < 1), then every 16x16
@@ -135,7 +172,8 @@ rtg_status rtg_unstable_mask(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, co
  * (all pixels).  Outputs are written on masked pixels only; other pixels keep their
  * contents.  index_map may be NULL.  The context keeps the sorted lists and
  * per-pixel state for rtg_render_backward, which must follow before the next forward
- * on the same context, with the Gaussian arrays unchanged. */
+ * on the same context, with the Gaussian arrays unchanged; it may be called more than
+ * once for one forward (each call starts from zero screen-space gradients). */
 rtg_status rtg_render_forward(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, const rtg_gaussians *g,
                               const uint8_t *mask, const rtg_render_params *prm, float *color, float *depth,
                               float *alpha, int32_t *index_map, void *stream);
@@ -155,9 +193,13 @@ rtg_status rtg_l1_loss(rtg_ctx *ctx, int32_t F, int32_t C, int32_t H, int32_t W,
  * and writes the gradients of the loss for the UNSTABLE Gaussians only, compact, in
  * ascending original index: g_means [nu,3], g_scales [nu,3] (linear scale),
  * g_quats [nu,4] (raw quaternion), g_opacity [nu], g_colors [nu,C].
- * dL_dcolor [F,C,H,W] and dL_ddepth [F,H,W] are read on masked pixels only. */
+ * dL_dcolor [F,C,H,W] and dL_ddepth [F,H,W] are read on masked pixels only.
+ * accumulate = 0 overwrites the gradient arrays; non-zero adds to their contents (so the
+ * gradients of several forward/backward calls, e.g. one keyframe each, can be summed
+ * before one optimiser step). */
 rtg_status rtg_render_backward(rtg_ctx *ctx, const float *dL_dcolor, const float *dL_ddepth, float *g_means,
-                               float *g_scales, float *g_quats, float *g_opacity, float *g_colors, void *stream);
+                               float *g_scales, float *g_quats, float *g_opacity, float *g_colors,
+                               int32_t accumulate, void *stream);
 
 /* The forward fused with the L1 losses: renders as rtg_render_forward and, in the same
  * pass, accumulates the terms of Eq. 7 against target_color [F,C,H,W] and target_depth
@@ -170,7 +212,7 @@ rtg_status rtg_render_forward_l1(rtg_ctx *ctx, const rtg_camera *cams, int32_t F
                                  const float *target_depth, float w_color, float w_depth, float *color, float *depth,
                                  float *alpha, int32_t *index_map, float *loss_out, void *stream);
 rtg_status rtg_render_backward_l1(rtg_ctx *ctx, float *g_means, float *g_scales, float *g_quats, float *g_opacity,
-                                  float *g_colors, void *stream);
+                                  float *g_colors, int32_t accumulate, void *stream);
 
 /* The unstable-pixel mask and the forward in one pass (Supplement B with Section 3.1):
  * builds the mask exactly as rtg_unstable_mask does and writes it to mask_out [F,H,W]
@@ -262,11 +304,12 @@ const char *rtg_profile_kind_name(int32_t kind);
 rtg_status rtg_profile_read(rtg_ctx *ctx, int64_t *launches, double *total_ms, int32_t n_kinds);
 
 /* Binning introspection of the last forward (for exactness tests): tile_offsets
- * [F*T+1] (uint32, T = ceil(W/16)*ceil(H/16) tiles per frame, frame-major, row-major
- * tiles), sorted_ids [pairs] (uint32 Gaussian index per list entry, each tile's list
- * in front-to-back order), and per (frame, Gaussian): rect [F*n*4] int32 (first and
- * last tile column and row touched, or -1 if culled) and zbits [F*n] uint32 (IEEE
- * bits of the float32 camera depth used as the sort key).  Any output may be NULL. */
+ * [F*T+1] (uint32, T = ceil(W/tile_w)*ceil(H/tile_h) render tiles per frame under the
+ * forward's tuning, frame-major, row-major tiles), sorted_ids [pairs] (uint32 Gaussian
+ * index per list entry, each tile's list in front-to-back order), and per (frame,
+ * Gaussian): rect [F*n*4] int32 (first and last render-tile column and row touched, or -1
+ * if culled) and zbits [F*n] uint32 (IEEE bits of the float32 camera depth used as the
+ * sort key).  Any output may be NULL. */
 rtg_status rtg_debug_binning(rtg_ctx *ctx, uint32_t *tile_offsets, uint32_t *sorted_ids, int32_t *rect,
                              uint32_t *zbits, void *stream);
 

@@ -14,6 +14,7 @@ from .api import (  # noqa: E402,F401
     Context,
     Gaussians,
     RenderSettings,
+    Tuning,
     RTGError,
     adam_step,
     adam_step_counted,

@@ -49,7 +49,13 @@ class rtg_capacity(Structure):
 
 class rtg_stats(Structure):
     _fields_ = [("pairs", c_int64), ("fragments", c_int64), ("visible", c_int64), ("masked_pixels", c_int64),
-                ("n_unstable", c_int64), ("status", c_int32), ("max_tile_pairs", c_int32)]
+                ("n_unstable", c_int64), ("status", c_int32), ("max_tile_pairs", c_int32), ("tile_w", c_int32),
+                ("tile_h", c_int32)]
+
+
+class rtg_tuning(Structure):
+    _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("batch", c_int32), ("schedule", c_int32),
+                ("persist_ctas_per_sm", c_int32), ("sort_digit_bits", c_int32), ("sort_rank_max", c_int32)]
 
 
 class rtg_adam_params(Structure):
@@ -74,8 +80,10 @@ SIGNATURES = [
     ("rtg_render_forward_masked", c_int32, [c_void_p, POINTER(rtg_camera), c_int32, POINTER(rtg_gaussians),
                                             POINTER(rtg_render_params), c_void_p, c_void_p, c_void_p, c_float,
                                             c_float, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
-    ("rtg_render_backward_l1", c_int32, [c_void_p] + [c_void_p] * 5 + [c_void_p]),
-    ("rtg_render_backward", c_int32, [c_void_p] + [c_void_p] * 7 + [c_void_p]),
+    ("rtg_render_backward_l1", c_int32, [c_void_p] + [c_void_p] * 5 + [c_int32, c_void_p]),
+    ("rtg_render_backward", c_int32, [c_void_p] + [c_void_p] * 7 + [c_int32, c_void_p]),
+    ("rtg_set_tuning", c_int32, [c_void_p, POINTER(rtg_tuning)]),
+    ("rtg_get_tuning", c_int32, [c_void_p, POINTER(rtg_tuning)]),
     ("rtg_adam_step", c_int32, [c_int64, c_int32] + [c_void_p] * 12 + [c_int32, POINTER(rtg_adam_params),
                                                                        c_void_p]),
     ("rtg_adam_step_counted", c_int32, [c_int64, c_int32] + [c_void_p] * 13 + [POINTER(rtg_adam_params),

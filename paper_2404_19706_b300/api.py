@@ -202,6 +202,37 @@ class Context:
     def ptr(self):
         return self.handle
 
+    def set_tuning(self, t: "Tuning"):
+        c = t.to_c()
+        _check(_lib.load().rtg_set_tuning(self.ptr, ctypes.byref(c)), "rtg_set_tuning", self.ptr)
+
+    def get_tuning(self) -> "Tuning":
+        c = _lib.rtg_tuning()
+        _check(_lib.load().rtg_get_tuning(self.ptr, ctypes.byref(c)), "rtg_get_tuning", self.ptr)
+        return Tuning(c.tile_w, c.tile_h, c.batch, c.schedule, c.persist_ctas_per_sm, c.sort_digit_bits,
+                      c.sort_rank_max)
+
+
+@dataclasses.dataclass(frozen=True)
+class Tuning:
+    """Launch configuration of the render path (rtg_tuning); never changes a rendered value."""
+    tile_w: int = 16
+    tile_h: int = 16
+    batch: int = 32
+    schedule: int = 0          # 0: CTA per tile; 1: persistent warps over the cost-ordered queue
+    persist_ctas_per_sm: int = 4
+    sort_digit_bits: int = 8
+    sort_rank_max: int = 0
+
+    def to_c(self):
+        return _lib.rtg_tuning(self.tile_w, self.tile_h, self.batch, self.schedule, self.persist_ctas_per_sm,
+                               self.sort_digit_bits, self.sort_rank_max)
+
+    def as_dict(self) -> dict:
+        return {"tile": f"{self.tile_w}x{self.tile_h}", "batch": self.batch, "schedule": self.schedule,
+                "persist_ctas_per_sm": self.persist_ctas_per_sm, "sort_digit_bits": self.sort_digit_bits,
+                "sort_rank_max": self.sort_rank_max}
+
 
 def workspace_size(max_gaussians, max_frames=1, max_width=640, max_height=480, max_channels=3, max_pairs=1 << 20):
     cap = rtg_capacity(int(max_gaussians), int(max_frames), int(max_width), int(max_height), int(max_channels),
@@ -266,10 +297,12 @@ def render_forward_masked(ctx: Context, cams, g: Gaussians, settings: RenderSett
     _check(st, "rtg_render_forward_masked", ctx.ptr)
 
 
-def render_backward_l1(ctx: Context, g_means, g_scales, g_quats, g_opacity, g_colors, stream=None):
+def render_backward_l1(ctx: Context, g_means, g_scales, g_quats, g_opacity, g_colors, accumulate: bool = False,
+                       stream=None):
     st = _lib.load().rtg_render_backward_l1(ctx.ptr, _out_ptr(g_means, "g_means"), _out_ptr(g_scales, "g_scales"),
                                             _out_ptr(g_quats, "g_quats"), _out_ptr(g_opacity, "g_opacity"),
-                                            _out_ptr(g_colors, "g_colors"), _stream(stream))
+                                            _out_ptr(g_colors, "g_colors"), 1 if accumulate else 0,
+                                            _stream(stream))
     _check(st, "rtg_render_backward_l1", ctx.ptr)
 
 
@@ -299,12 +332,12 @@ def _out_ptr(t: torch.Tensor, name: str):
 
 
 def render_backward(ctx: Context, dL_dcolor, dL_ddepth, g_means, g_scales, g_quats, g_opacity, g_colors,
-                    stream=None):
+                    accumulate: bool = False, stream=None):
     st = _lib.load().rtg_render_backward(ctx.ptr, _ptr(dL_dcolor, torch.float32, "dL_dcolor"),
                                          _ptr(dL_ddepth, torch.float32, "dL_ddepth"), _out_ptr(g_means, "g_means"),
                                          _out_ptr(g_scales, "g_scales"), _out_ptr(g_quats, "g_quats"),
                                          _out_ptr(g_opacity, "g_opacity"), _out_ptr(g_colors, "g_colors"),
-                                         _stream(stream))
+                                         1 if accumulate else 0, _stream(stream))
     _check(st, "rtg_render_backward", ctx.ptr)
 
 
@@ -418,7 +451,8 @@ def debug_binning(ctx: Context, frames: int, width: int, height: int, n: int, st
     """Copies of the last forward's bucket offsets, sorted ids, per-(frame, Gaussian) tile
     rectangles and depth-key bits (for the exactness tests)."""
     stats = get_stats(ctx)
-    T = ((width + 15) // 16) * ((height + 15) // 16)
+    tw, th = stats["tile_w"], stats["tile_h"]
+    T = ((width + tw - 1) // tw) * ((height + th - 1) // th)
     dev = torch.device("cuda", torch.cuda.current_device())
     offs = torch.empty(frames * T + 1, dtype=torch.int32, device=dev)
     ids = torch.empty(max(stats["pairs"], 1), dtype=torch.int32, device=dev)

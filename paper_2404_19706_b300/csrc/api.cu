@@ -27,6 +27,9 @@ struct rtg_ctx {
   const uint8_t *mask;
   L1Fused l1;  // targets of the last rtg_render_forward_l1 (tcolor == nullptr otherwise)
   cudaStream_t last_stream;
+  Tuning tune;      // launch configuration of the next forward
+  Tuning tune_fwd;  // ... and of the last one, which its backward follows
+  bool bwd_done;    // a backward of the last forward has run (its 2D gradient rows are used)
   // tracing: (start, end) event pairs of the kernels launched while profiling is on
   bool prof;
   struct ProfRec *recs;
@@ -104,21 +107,25 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
   size_t cams, counters, rank, ids, block_cnt, cand, rec_hot, rec_cold, rec_box, ntiles, tile_npix, tile_count, tile_offset,
       tile_cursor, keys, keys_alt, stage, sorted, px_T, px_last, px_hit, grad2d, loss_part, loss_scal, loss_done, tile_loss,
-      total;
+      px_list, items, total;
 };
 
 bool capacity_ok(const rtg_capacity *c) {
   return c != nullptr && c->max_gaussians >= 0 && c->max_frames >= 1 && c->max_frames <= RTG_MAX_FRAMES &&
          c->max_width >= 1 && c->max_height >= 1 && (c->max_channels == 3 || c->max_channels == 8) &&
-         c->max_pairs >= 1 && c->max_pairs <= 0xffffffffLL &&
+         c->max_pairs >= 1 && c->max_pairs <= 0xffffffffLL && c->max_width <= 32768 && c->max_height <= 32768 &&
          (int64_t)c->max_frames * c->max_gaussians < 0xffffffffLL;
 }
 
 Layout layout_of(const rtg_capacity *c) {
   const size_t N = (size_t)(c->max_gaussians > 0 ? c->max_gaussians : 1);
   const size_t Fm = (size_t)c->max_frames;
-  const size_t tiles = (size_t)((c->max_width + kTile - 1) / kTile) * (size_t)((c->max_height + kTile - 1) / kTile);
+  // tile arrays for the finest tiling (8 x 8); pixel lists, work items and loss partials
+  // for the padded image of any tiling (tiles of at most 32 x 16 pixels)
+  const size_t tiles = (size_t)((c->max_width + 7) / 8) * (size_t)((c->max_height + 7) / 8);
   const size_t FT = Fm * tiles;
+  const size_t padded = Fm * (size_t)(c->max_width + 31) * (size_t)(c->max_height + 15);
+  const size_t groups = padded / 32 + 1;
   const size_t P = Fm * (size_t)c->max_width * (size_t)c->max_height;
   const size_t K = (size_t)c->max_pairs;
   const size_t H4 = (size_t)hot4_of(c->max_channels), G2 = (size_t)g2_of(c->max_channels);
@@ -154,7 +161,9 @@ Layout layout_of(const rtg_capacity *c) {
   L.loss_part = take(kLossBlocks * 4 * 4);
   L.loss_scal = take(8 * 4);
   L.loss_done = take(4);
-  L.tile_loss = take(FT * (kTilePix / 32) * 4 * 4);
+  L.tile_loss = take(groups * 4 * 4);
+  L.px_list = take(padded);
+  L.items = take(groups * 4);
   L.total = o;
   return L;
 }
@@ -180,10 +189,41 @@ rtg_status make_frames(rtg_ctx *ctx, const rtg_camera *cams, int F, const rtg_re
     for (int k = 0; k < 3; ++k) d.t[k] = c.t[k];
     d.lim_x = prm->guard_band * (0.5f * (float)c.width) / c.fx;
     d.lim_y = prm->guard_band * (0.5f * (float)c.height) / c.fy;
-    d.tiles_x = (c.width + kTile - 1) / kTile;
-    d.tiles_y = (c.height + kTile - 1) / kTile;
+    d.tws = ctx->tune.tws;
+    d.ths = ctx->tune.ths;
+    d.tiles_x = (c.width + (1 << d.tws) - 1) >> d.tws;
+    d.tiles_y = (c.height + (1 << d.ths) - 1) >> d.ths;
+    d.mtiles_x = (c.width + kTile - 1) / kTile;
+    d.mtiles_y = (c.height + kTile - 1) / kTile;
   }
   return RTG_OK;
+}
+
+int log2_exact(int v) {
+  for (int k = 0; k < 31; ++k)
+    if (v == (1 << k)) return k;
+  return -1;
+}
+
+// rtg_tuning -> Tuning, or false if the setting is not one this build implements
+bool make_tuning(const rtg_tuning *t, int num_sms, Tuning &o) {
+  if (t == nullptr) return false;
+  const int tws = log2_exact(t->tile_w), ths = log2_exact(t->tile_h);
+  if (tws < 3 || tws > 5 || ths < 3 || ths > 4 || tws + ths > 8) return false;
+  if (t->batch != 32 && t->batch != 64) return false;
+  if (t->schedule != 0 && t->schedule != 1) return false;
+  if (t->persist_ctas_per_sm < 1 || t->persist_ctas_per_sm > 8) return false;
+  if (t->sort_digit_bits != 4 && t->sort_digit_bits != 8) return false;
+  if (t->sort_rank_max < 0 || t->sort_rank_max > kSortCap) return false;
+  o.tws = tws;
+  o.ths = ths;
+  o.batch = t->batch;
+  o.schedule = t->schedule;
+  o.ctas_per_sm = t->persist_ctas_per_sm;
+  o.sort_bits = t->sort_digit_bits;
+  o.sort_rank_max = t->sort_rank_max;
+  o.num_sms = num_sms;
+  return true;
 }
 
 rtg_status make_gauss(rtg_ctx *ctx, const rtg_gaussians *g, GaussPtrs &gp) {
@@ -241,11 +281,12 @@ __global__ void k_debug_extract(Work w, int64_t N, int F, int32_t *rect, uint32_
   const float4 c1 = w.rec_cold[i * 2 + 1];
   const bool vis = w.ntiles[i] != 0u;
   const uint32_t lo = __float_as_uint(c1.z), hi = __float_as_uint(c1.w);
-  if (rect != nullptr) {
-    rect[4 * i + 0] = vis ? (int32_t)(lo & 0xffff) : -1;
-    rect[4 * i + 1] = vis ? (int32_t)(lo >> 16) : -1;
-    rect[4 * i + 2] = vis ? (int32_t)(hi & 0xffff) : -1;
-    rect[4 * i + 3] = vis ? (int32_t)(hi >> 16) : -1;
+  if (rect != nullptr) {  // pixel rect -> render tiles
+    const DevCam &cam = w.cams[i / N];
+    rect[4 * i + 0] = vis ? (int32_t)(lo & 0xffffu) >> cam.tws : -1;
+    rect[4 * i + 1] = vis ? (int32_t)(lo >> 16) >> cam.ths : -1;
+    rect[4 * i + 2] = vis ? (int32_t)(hi & 0xffffu) >> cam.tws : -1;
+    rect[4 * i + 3] = vis ? (int32_t)(hi >> 16) >> cam.ths : -1;
   }
   if (zbits != nullptr) zbits[i] = vis ? __float_as_uint(c1.x) : 0u;
 }
@@ -312,7 +353,19 @@ rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap) {
   w.loss_scal = (float *)(b + L.loss_scal);
   w.loss_done = (uint32_t *)(b + L.loss_done);
   w.tile_loss = (float *)(b + L.tile_loss);
+  w.px_list = (uint8_t *)(b + L.px_list);
+  w.items = (uint32_t *)(b + L.items);
   w.status = status_dev;
+  {
+    int sms = 148;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || sms < 1) {
+      cudaGetLastError();
+      sms = 148;
+    }
+    const rtg_tuning def = {16, 16, 32, 0, 4, 8, 0};
+    make_tuning(&def, sms, ctx->tune);
+    ctx->tune_fwd = ctx->tune;
+  }
   // zero the small bookkeeping region once (counters, loss ticket)
   cudaMemset(ctx->slab + L.counters, 0, kNumCounters * sizeof(unsigned long long));
   cudaMemset(ctx->slab + L.loss_done, 0, 4);
@@ -340,6 +393,27 @@ rtg_status rtg_destroy(rtg_ctx *ctx) {
   cudaFree(ctx->slab);
   cudaFreeHost(ctx->status_host);
   free(ctx);
+  return RTG_OK;
+}
+
+rtg_status rtg_set_tuning(rtg_ctx *ctx, const rtg_tuning *t) {
+  if (ctx == nullptr) return RTG_ERR_ARG;
+  Tuning o;
+  if (!make_tuning(t, ctx->tune.num_sms, o)) return fail(ctx, RTG_ERR_ARG, "set_tuning: unsupported setting");
+  ctx->tune = o;
+  return RTG_OK;
+}
+
+rtg_status rtg_get_tuning(rtg_ctx *ctx, rtg_tuning *out) {
+  if (ctx == nullptr || out == nullptr) return RTG_ERR_ARG;
+  const Tuning &t = ctx->tune;
+  out->tile_w = 1 << t.tws;
+  out->tile_h = 1 << t.ths;
+  out->batch = t.batch;
+  out->schedule = t.schedule;
+  out->persist_ctas_per_sm = t.ctas_per_sm;
+  out->sort_digit_bits = t.sort_bits;
+  out->sort_rank_max = t.sort_rank_max;
   return RTG_OK;
 }
 
@@ -410,32 +484,39 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
   if ((st = make_gauss(ctx, g, gp)) != RTG_OK) return st;
   if (color == nullptr || depth == nullptr || alpha == nullptr) return fail(ctx, RTG_ERR_ARG, "output is NULL");
   cudaStream_t s = (cudaStream_t)stream;
-  const int T = fs.cam[0].tiles_x * fs.cam[0].tiles_y;
+  const Tuning tn = ctx->tune;
+  const DevCam &c0 = fs.cam[0];
+  const int T = c0.tiles_x * c0.tiles_y;   // render tiles per frame
+  const int TM = c0.mtiles_x * c0.mtiles_y;  // 16 x 16 mask-rule tiles per frame
   const int FT = F * T;
+  const bool same_grid = tn.tws == kTileShift && tn.ths == kTileShift;
   const int64_t n = gp.n;
+  const long long nu_preset = gp.rank_map ? (long long)gp.n_unstable : -1ll;
   Work w = ctx->w;
   if (gp.rank_map != nullptr) {
     w.rank = const_cast<int32_t *>(gp.rank_map);
     w.ids = const_cast<int32_t *>(gp.unstable_ids);
   }
-  {
-    ProfScope ps(ctx, kPTileMask, s);
-    launch_tile_mask(fs, w, mask, T, gp.rank_map ? (long long)gp.n_unstable : -1ll, s);
-  }
-  if (gp.rank_map == nullptr)
-    if ((st = rank_pass(ctx, gp.unstable, n, w.rank, w.ids, w.counters, nullptr, s)) != RTG_OK) return st;
   if (mask_out != nullptr) {
-    // unstable mask in the same pass: bin the unstable Gaussians into every tile, test
-    // coverage and the tile rule, then bin everything into the surviving tiles
+    // unstable mask in the same pass: bin the unstable Gaussians into every 16 x 16 tile,
+    // test coverage and the tile rule, then bin everything into the surviving render tiles
+    {
+      ProfScope ps(ctx, kPTileMask, s);
+      launch_tile_mask(fs, w, nullptr, TM, c0.mtiles_x, kTileShift, kTileShift, true, false, nu_preset, s);
+    }
+    if (gp.rank_map == nullptr)
+      if ((st = rank_pass(ctx, gp.unstable, n, w.rank, w.ids, w.counters, nullptr, s)) != RTG_OK) return st;
     {
       ProfScope ps(ctx, kPProject, s);
-      launch_project(gp, w, P, F, T, kProjFused, ctx->cap.max_pairs, s);
+      launch_project(gp, w, P, F, TM, kProjFused, ctx->cap.max_pairs, s);
     }
     {
       ProfScope ps(ctx, kPUnstableMask, s);  // coverage pass: scan, scatter, cover + tile rule
-      launch_scan_tiles(w, FT, ctx->cap.max_pairs, s);
+      launch_scan_tiles(w, F * TM, ctx->cap.max_pairs, -1, s);
       launch_emit(w, s);
-      launch_mask_cover_tiles(w, P, n, F, T, gp.C, mask_out, true, s);
+      launch_mask_cover_tiles(w, P, n, F, TM, gp.C, mask_out, same_grid ? kCoverFusedSame : kCoverFusedOther, s);
+      if (!same_grid)
+        launch_tile_mask(fs, w, mask_out, T, c0.tiles_x, tn.tws, tn.ths, false, true, -1ll, s);
     }
     {
       ProfScope ps(ctx, kPBin, s);
@@ -443,12 +524,18 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
     }
     mask = mask_out;
   } else {
+    {
+      ProfScope ps(ctx, kPTileMask, s);
+      launch_tile_mask(fs, w, mask, T, c0.tiles_x, tn.tws, tn.ths, true, true, nu_preset, s);
+    }
+    if (gp.rank_map == nullptr)
+      if ((st = rank_pass(ctx, gp.unstable, n, w.rank, w.ids, w.counters, nullptr, s)) != RTG_OK) return st;
     ProfScope ps(ctx, kPProject, s);
     launch_project(gp, w, P, F, T, kProjForward, ctx->cap.max_pairs, s);
   }
   {
     ProfScope ps(ctx, kPScanTiles, s);
-    launch_scan_tiles(w, FT, ctx->cap.max_pairs, s);
+    launch_scan_tiles(w, FT, ctx->cap.max_pairs, tn.schedule == 1 ? tn.gshift() : -1, s);
   }
   {
     ProfScope ps(ctx, kPEmit, s);
@@ -456,15 +543,15 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
   }
   {
     ProfScope ps(ctx, kPSortTiles, s);
-    launch_sort_tiles(w, FT, s);
+    launch_sort_tiles(w, FT, tn.sort_bits, tn.sort_rank_max, s);
   }
   {
     ProfScope ps(ctx, kPForward, s);
-    launch_forward(gp.C, w, P, n, F, T, mask, color, depth, alpha, index_map, tcolor, tdepth, s);
+    launch_forward(gp.C, w, P, n, F, T, tn, color, depth, alpha, index_map, tcolor, tdepth, s);
   }
   if (tcolor != nullptr) {
     ProfScope ps(ctx, kPL1Loss, s);
-    launch_loss_finalize(w, FT, gp.C, w_c, w_d, loss_out, s);
+    launch_loss_finalize(w, FT, tn.gshift(), gp.C, w_c, w_d, loss_out, s);
   }
   if ((st = check_launch(ctx, "render_forward")) != RTG_OK) return st;
   ctx->has_fwd = true;
@@ -478,7 +565,21 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
   ctx->C = gp.C;
   ctx->mask = mask;
   ctx->l1 = L1Fused{tcolor, tdepth, color, depth};
+  ctx->tune_fwd = tn;
+  ctx->bwd_done = false;
   ctx->last_stream = s;
+  return RTG_OK;
+}
+
+// The forward's projection zeroes the 2D gradient rows its backward accumulates into; a
+// second backward of the same forward clears them itself first.
+static rtg_status prepare_backward(rtg_ctx *ctx, cudaStream_t s) {
+  if (ctx->bwd_done) {
+    const size_t bytes = (size_t)ctx->F * (size_t)ctx->g.n * (size_t)g2_of(ctx->C) * sizeof(float);
+    if (bytes > 0 && cudaMemsetAsync(ctx->w_fwd.grad2d, 0, bytes, s) != cudaSuccess)
+      return check_launch(ctx, "clear 2D gradients");
+  }
+  ctx->bwd_done = true;
   return RTG_OK;
 }
 
@@ -515,7 +616,7 @@ rtg_status rtg_render_forward_masked(rtg_ctx *ctx, const rtg_camera *cams, int32
 }
 
 rtg_status rtg_render_backward_l1(rtg_ctx *ctx, float *g_means, float *g_scales, float *g_quats, float *g_opacity,
-                                  float *g_colors, void *stream) {
+                                  float *g_colors, int32_t accumulate, void *stream) {
   if (ctx == nullptr) return RTG_ERR_ARG;
   if (!ctx->has_fwd || ctx->l1.tcolor == nullptr)
     return fail(ctx, RTG_ERR_STATE, "render_backward_l1 without a preceding render_forward_l1");
@@ -523,39 +624,42 @@ rtg_status rtg_render_backward_l1(rtg_ctx *ctx, float *g_means, float *g_scales,
     return fail(ctx, RTG_ERR_ARG, "gradient output is NULL");
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = ctx->g.n;
+  rtg_status st = prepare_backward(ctx, s);
+  if (st != RTG_OK) return st;
   {
     ProfScope ps(ctx, kPBackward, s);
-    launch_backward(ctx->C, ctx->w_fwd, ctx->prm, n, ctx->F, ctx->T, ctx->mask, nullptr, nullptr, ctx->l1, s);
+    launch_backward(ctx->C, ctx->w_fwd, ctx->prm, n, ctx->F, ctx->T, ctx->tune_fwd, nullptr, nullptr, ctx->l1, s);
   }
   {
     ProfScope ps(ctx, kPProjectBackward, s);
     launch_project_backward(ctx->g, ctx->w_fwd, ctx->prm, ctx->F, g_means, g_scales, g_quats, g_opacity, g_colors,
-                            s);
+                            accumulate != 0, s);
   }
   ctx->last_stream = s;
   return check_launch(ctx, "render_backward_l1");
 }
 
 rtg_status rtg_render_backward(rtg_ctx *ctx, const float *dL_dcolor, const float *dL_ddepth, float *g_means,
-                               float *g_scales, float *g_quats, float *g_opacity, float *g_colors, void *stream) {
+                               float *g_scales, float *g_quats, float *g_opacity, float *g_colors,
+                               int32_t accumulate, void *stream) {
   if (ctx == nullptr) return RTG_ERR_ARG;
   if (!ctx->has_fwd) return fail(ctx, RTG_ERR_STATE, "render_backward without a preceding render_forward");
   if (dL_dcolor == nullptr || dL_ddepth == nullptr) return fail(ctx, RTG_ERR_ARG, "image gradient is NULL");
   if (!g_means || !g_scales || !g_quats || !g_opacity || !g_colors)
     return fail(ctx, RTG_ERR_ARG, "gradient output is NULL");
   cudaStream_t s = (cudaStream_t)stream;
-  const int FT = ctx->F * ctx->T;
   const int64_t n = ctx->g.n;
-  (void)FT;
+  rtg_status st = prepare_backward(ctx, s);
+  if (st != RTG_OK) return st;
   {
     ProfScope ps(ctx, kPBackward, s);
-    launch_backward(ctx->C, ctx->w_fwd, ctx->prm, n, ctx->F, ctx->T, ctx->mask, dL_dcolor, dL_ddepth,
+    launch_backward(ctx->C, ctx->w_fwd, ctx->prm, n, ctx->F, ctx->T, ctx->tune_fwd, dL_dcolor, dL_ddepth,
                     L1Fused{nullptr, nullptr, nullptr, nullptr}, s);
   }
   {
     ProfScope ps(ctx, kPProjectBackward, s);
     launch_project_backward(ctx->g, ctx->w_fwd, ctx->prm, ctx->F, g_means, g_scales, g_quats, g_opacity, g_colors,
-                            s);
+                            accumulate != 0, s);
   }
   ctx->last_stream = s;
   return check_launch(ctx, "render_backward");
@@ -674,10 +778,8 @@ rtg_status rtg_unstable_mask(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, co
   if ((st = make_gauss(ctx, g, gp)) != RTG_OK) return st;
   if (mask == nullptr) return fail(ctx, RTG_ERR_ARG, "mask is NULL");
   cudaStream_t s = (cudaStream_t)stream;
-  const int T = fs.cam[0].tiles_x * fs.cam[0].tiles_y;
-  const size_t npx = (size_t)F * fs.cam[0].W * fs.cam[0].H;
+  const int T = fs.cam[0].mtiles_x * fs.cam[0].mtiles_y;  // 16 x 16 tiles of the rule
   ctx->has_fwd = false;  // the mask pass reuses the forward's workspace
-  (void)npx;
   ProfScope ps(ctx, kPUnstableMask, s);
   // every in-image tile is active: the unstable Gaussians are bucketed into all tiles
   Work w = ctx->w;
@@ -685,13 +787,14 @@ rtg_status rtg_unstable_mask(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, co
     w.rank = const_cast<int32_t *>(gp.rank_map);
     w.ids = const_cast<int32_t *>(gp.unstable_ids);
   }
-  launch_tile_mask(fs, w, nullptr, T, gp.rank_map ? (long long)gp.n_unstable : -1ll, s);
+  launch_tile_mask(fs, w, nullptr, T, fs.cam[0].mtiles_x, kTileShift, kTileShift, true, false,
+                   gp.rank_map ? (long long)gp.n_unstable : -1ll, s);
   if (gp.u_means != nullptr && gp.rank_map == nullptr)
     if ((st = rank_pass(ctx, gp.unstable, gp.n, w.rank, w.ids, w.counters, nullptr, s)) != RTG_OK) return st;
   launch_project(gp, w, P, F, T, kProjMask, ctx->cap.max_pairs, s);
-  launch_scan_tiles(w, F * T, ctx->cap.max_pairs, s);
+  launch_scan_tiles(w, F * T, ctx->cap.max_pairs, -1, s);
   launch_emit(w, s);
-  launch_mask_cover_tiles(w, P, gp.n, F, T, gp.C, mask, false, s);
+  launch_mask_cover_tiles(w, P, gp.n, F, T, gp.C, mask, kCoverPlain, s);
   ctx->last_stream = s;
   return check_launch(ctx, "unstable_mask");
 }
@@ -714,6 +817,8 @@ rtg_status rtg_get_stats(rtg_ctx *ctx, rtg_stats *out) {
   out->n_unstable = (int64_t)c[kNumUnstable];
   out->max_tile_pairs = (int32_t)c[kMaxTilePairs];
   out->status = (int32_t)*(volatile uint32_t *)ctx->status_host;
+  out->tile_w = 1 << ctx->tune_fwd.tws;
+  out->tile_h = 1 << ctx->tune_fwd.ths;
   return RTG_OK;
 }
 

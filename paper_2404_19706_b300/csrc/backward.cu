@@ -9,9 +9,10 @@
 // (no background term), chained through f = min(f_max, alpha 2^-q), q = |U (u - mu)|^2.
 // The depth depends on f only through the choice of the hit fragment, so it adds no
 // gradient to f; its gradient goes to the hit Gaussian's plane record (d0, n_c) or to
-// its centre depth.  Each warp works alone on 32 compacted pixels and skips the records
-// whose support box misses its pixel box (the forward's test); sums over the warp are
-// formed by a halving reduce-scatter and added with vector atomics.
+// its centre depth.  Each warp works alone on the forward's 32-pixel groups and skips the
+// records whose support box misses its pixel box (the forward's test); sums over the
+// warp are formed by a halving reduce-scatter and added with vector atomics.  The two
+// schedules of the forward (CTA per tile, persistent warps over the item queue) apply.
 //
 // k_project_backward chains those screen-space gradients to position, linear scale,
 // raw quaternion, opacity and colour through Sigma_2D = J W R S^2 R^T W^T J^T + lowpass I,
@@ -61,46 +62,27 @@ __device__ __forceinline__ float warp_transpose_sum(const float (&in)[NV]) {
   return v + __shfl_xor_sync(0xffffffffu, v, 1);
 }
 
-template <int C>
-__global__ void __launch_bounds__(kTilePix) k_backward(Work w, Prm prm, int64_t N, int T,
-                                                       const uint8_t *__restrict__ mask,
-                                                       const float *__restrict__ dL_dcolor,
-                                                       const float *__restrict__ dL_ddepth, L1Fused l1) {
+// Replays the pixels of group `grp` of render tile `tile` (the forward's pixel grouping)
+// back to front.  Called by a whole warp; s_rec / s_j / s_rank are the warp's staging.
+template <int C, int B>
+__device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, int64_t N, int T, int tile, int grp,
+                                               float4 (*s_rec)[B], uint32_t *s_j, int *s_rank,
+                                               const float *__restrict__ dL_dcolor,
+                                               const float *__restrict__ dL_ddepth, const L1Fused &l1) {
   constexpr int H4 = (C <= 4) ? 3 : 4;
   constexpr int G2 = (C <= 5) ? 16 : 20;
   constexpr int NV = 6 + C;            // d mu (2), d conic (3), d alpha, d colour (C)
   constexpr int NG = (NV + 3) / 4;     // float4 groups of a grad2d row they occupy
-  constexpr int NW = kTilePix / 32;
-  __shared__ float4 s_rec[NW][H4][32];
-  __shared__ uint32_t s_j[NW][32];
-  __shared__ int s_rank[NW][32];
-  __shared__ int s_pix[kTilePix];
-  __shared__ int s_wcnt[NW];
-  if (w.counters[kSkip] != 0ull) return;
-  const int tile = blockIdx.x;
-  if (w.tile_npix[tile] == 0u) return;
+  constexpr int R = B / 32;
+  const int lane = threadIdx.x & 31;
   const int f = tile / T, lt = tile - f * T;
   const DevCam &cam = w.cams[f];
+  const int tws = cam.tws, ths = cam.ths;
   const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  {
-    const int px = tx * kTile + (tid & (kTile - 1)), py = ty * kTile + tid / kTile;
-    bool act = px < cam.W && py < cam.H;
-    if (act && mask != nullptr) act = mask[((int64_t)f * cam.H + py) * cam.W + px] != 0;
-    const unsigned bal = __ballot_sync(0xffffffffu, act);
-    if (lane == 0) s_wcnt[wid] = __popc(bal);
-    __syncthreads();
-    int before = 0;
-    for (int k = 0; k < wid; ++k) before += s_wcnt[k];
-    if (act) s_pix[before + __popc(bal & lanemask_lt())] = tid;
-    __syncthreads();
-  }
-  // every warp works alone on its 32 compacted pixels from here on
-  const int npix = (int)w.tile_npix[tile];
-  if (wid * 32 >= npix) return;
-  const bool has = tid < npix;
-  const int my = has ? s_pix[tid] : 0;
-  const int px = tx * kTile + (my & (kTile - 1)), py = ty * kTile + my / kTile;
+  const int q = grp * 32 + lane;
+  const bool has = q < (int)w.tile_npix[tile];
+  const int my = has ? (int)w.px_list[((int64_t)tile << (tws + ths)) + q] : 0;
+  const int px = (tx << tws) + (my & ((1 << tws) - 1)), py = (ty << ths) + (my >> tws);
   const float fpx = (float)px, fpy = (float)py;
   const int64_t HW = (int64_t)cam.H * cam.W;
   const int64_t pix = (int64_t)f * HW + (int64_t)py * cam.W + px;
@@ -195,64 +177,76 @@ __global__ void __launch_bounds__(kTilePix) k_backward(Work w, Prm prm, int64_t 
 #pragma unroll
   for (int c = 0; c < C; ++c) S[c] = 0.f;
 
-  // batches run back to front; the records of the next (earlier) batch are fetched while
-  // the current one is replayed
-  auto fetch = [&](int b_end_, float4 (&rr)[H4], float2 &bx, int &rank_, bool &v_) {
-    const int jq = max(0, b_end_ - 32) + lane;
-    v_ = b_end_ > 0 && jq < b_end_;
-    if (v_) {
-      const uint32_t gid = w.sorted[off + jq];
+  // batches of B records run back to front; the records of the next (earlier) batch are
+  // fetched while the current one is replayed
+  auto fetch = [&](int b_end_, float4 (&rr)[R][H4], float2 (&bx)[R], int (&rank_)[R], bool (&v_)[R]) {
+    const int b_beg_ = max(0, b_end_ - B);
 #pragma unroll
-      for (int k = 0; k < H4; ++k) rr[k] = rec[(int64_t)gid * H4 + k];
-      bx = box[gid];
-      rank_ = (H4 == 3) ? __float_as_int(rr[2].w) : __float_as_int(w.rec_cold[((int64_t)f * N + gid) * 2 + 1].y);
+    for (int u = 0; u < R; ++u) {
+      const int jq = b_beg_ + u * 32 + lane;
+      v_[u] = jq < b_end_;
+      bx[u] = make_float2(0.f, 0.f);
+      rank_[u] = -1;
+      if (v_[u]) {
+        const uint32_t gid = w.sorted[off + jq];
+#pragma unroll
+        for (int k = 0; k < H4; ++k) rr[u][k] = rec[(int64_t)gid * H4 + k];
+        bx[u] = box[gid];
+        rank_[u] =
+            (H4 == 3) ? __float_as_int(rr[u][2].w) : __float_as_int(w.rec_cold[((int64_t)f * N + gid) * 2 + 1].y);
+      }
     }
   };
-  float4 r[H4];
-  float2 bb = make_float2(0.f, 0.f);
-  int rk = -1;
-  bool valid = false;
+  float4 r[R][H4];
+  float2 bb[R];
+  int rk[R];
+  bool valid[R];
   fetch((int)maxlast, r, bb, rk, valid);
-  for (int b_end = (int)maxlast; b_end > 0; b_end -= 32) {
-    const int b_beg = max(0, b_end - 32);
-    const int j = b_beg + lane;
-    float4 rn[H4];
-    float2 bn = make_float2(0.f, 0.f);
-    int rkn = -1;
-    bool vnext = false;
+  for (int b_end = (int)maxlast; b_end > 0; b_end -= B) {
+    const int b_beg = max(0, b_end - B);
+    float4 rn[R][H4];
+    float2 bn[R];
+    int rkn[R];
+    bool vnext[R];
     fetch(b_beg, rn, bn, rkn, vnext);
-    const bool keep = valid && fabsf(r[0].x - wcx) <= whx + bb.x && fabsf(r[0].y - wcy) <= why + bb.y;
-    const unsigned bal = __ballot_sync(0xffffffffu, keep);
-    if (keep) {
-      const int slot = __popc(bal & lanemask_lt());
+    int cnt = 0;
 #pragma unroll
-      for (int k = 0; k < H4; ++k) s_rec[wid][k][slot] = r[k];
-      s_j[wid][slot] = (uint32_t)j;
-      s_rank[wid][slot] = rk;
+    for (int u = 0; u < R; ++u) {
+      const bool keep =
+          valid[u] && fabsf(r[u][0].x - wcx) <= whx + bb[u].x && fabsf(r[u][0].y - wcy) <= why + bb[u].y;
+      const unsigned bal = __ballot_sync(0xffffffffu, keep);
+      if (keep) {
+        const int slot = cnt + __popc(bal & lanemask_lt());
+#pragma unroll
+        for (int k = 0; k < H4; ++k) s_rec[k][slot] = r[u][k];
+        s_j[slot] = (uint32_t)(b_beg + u * 32 + lane);
+        s_rank[slot] = rk[u];
+      }
+      cnt += __popc(bal);
     }
     __syncwarp();
-    for (int k = __popc(bal) - 1; k >= 0; --k) {
-      const uint32_t jj = s_j[wid][k];
+    for (int k = cnt - 1; k >= 0; --k) {
+      const uint32_t jj = s_j[k];
       bool act = has && jj < last;
-      const float4 r0 = s_rec[wid][0][k], r1 = s_rec[wid][1][k];
+      const float4 r0 = s_rec[0][k], r1 = s_rec[1][k];
       float dx = 0.f, dy = 0.f, t1 = 0.f, t2 = 0.f, g = 0.f, fa = 0.f;
       if (act) {
         fa = footprint(fpx, fpy, r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, prm.f_max, dx, dy, t1, t2, g);
         act = fa >= prm.alpha_min;
       }
-      const int rkk = s_rank[wid][k];
+      const int rkk = s_rank[k];
       float v[NV];
 #pragma unroll
-      for (int q = 0; q < NV; ++q) v[q] = 0.f;
+      for (int qq = 0; qq < NV; ++qq) v[qq] = 0.f;
       if (act) {
         const float om = 1.f - fa;
         const float iom = __frcp_rn(om);
         T_ = T_ * iom;  // transmission in front of fragment jj
         const float wgt = fa * T_;
-        const float4 c0 = s_rec[wid][2][k];
+        const float4 c0 = s_rec[2][k];
         float cw[8] = {c0.x, c0.y, c0.z, c0.w, 0.f, 0.f, 0.f, 0.f};
         if (H4 == 4) {
-          const float4 c1 = s_rec[wid][3 % H4][k];
+          const float4 c1 = s_rec[3 % H4][k];
           cw[4] = c1.x; cw[5] = c1.y; cw[6] = c1.z; cw[7] = c1.w;
         }
         float dLdf = 0.f;
@@ -286,22 +280,69 @@ __global__ void __launch_bounds__(kTilePix) k_backward(Work w, Prm prm, int64_t 
     }
     __syncwarp();
 #pragma unroll
-    for (int k = 0; k < H4; ++k) r[k] = rn[k];
-    bb = bn;
-    rk = rkn;
-    valid = vnext;
+    for (int u = 0; u < R; ++u) {
+#pragma unroll
+      for (int k = 0; k < H4; ++k) r[u][k] = rn[u][k];
+      bb[u] = bn[u];
+      rk[u] = rkn[u];
+      valid[u] = vnext[u];
+    }
+  }
+}
+
+struct BwdIn {
+  const float *dL_dcolor, *dL_ddepth;
+  L1Fused l1;
+};
+
+// Schedule 0: CTA `tile` with one warp per 32-pixel group of the tile's pixel list.
+template <int C, int B>
+__global__ void __launch_bounds__(kMaxTilePix) k_backward(Work w, Prm prm, int64_t N, int T, BwdIn in) {
+  constexpr int H4 = (C <= 4) ? 3 : 4;
+  __shared__ float4 s_rec[kMaxTilePix / 32][H4][B];
+  __shared__ uint32_t s_j[kMaxTilePix / 32][B];
+  __shared__ int s_rank[kMaxTilePix / 32][B];
+  if (w.counters[kSkip] != 0ull) return;
+  const int tile = blockIdx.x, wid = threadIdx.x >> 5;
+  if (wid * 32 >= (int)w.tile_npix[tile]) return;
+  backward_group<C, B>(w, prm, N, T, tile, wid, s_rec[wid], s_j[wid], s_rank[wid], in.dL_dcolor, in.dL_ddepth,
+                       in.l1);
+}
+
+// Schedule 1: persistent warps over the forward's item queue (its own counter).
+template <int C, int B>
+__global__ void __launch_bounds__(256) k_backward_queue(Work w, Prm prm, int64_t N, int T, BwdIn in) {
+  constexpr int H4 = (C <= 4) ? 3 : 4;
+  __shared__ float4 s_rec[8][H4][B];
+  __shared__ uint32_t s_j[8][B];
+  __shared__ int s_rank[8][B];
+  if (w.counters[kSkip] != 0ull) return;
+  const uint32_t nitems = (uint32_t)w.counters[kItems];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t nwarps = gridDim.x * 8u;
+  uint32_t it = blockIdx.x * 8u + (uint32_t)wid;
+  while (it < nitems) {
+    const uint32_t item = w.items[it];
+    backward_group<C, B>(w, prm, N, T, (int)(item >> 3), (int)(item & 7u), s_rec[wid], s_j[wid], s_rank[wid],
+                         in.dL_dcolor, in.dL_ddepth, in.l1);
+    uint32_t nx = 0;
+    if (lane == 0) nx = nwarps + (uint32_t)atomicAdd(w.counters + kQBwd, 1ull);
+    it = __shfl_sync(0xffffffffu, nx, 0);
   }
 }
 
 // --------------------------------------------------------------------------- 2D -> 3D
+// The persistent backward's queue counter is cleared here (this kernel always follows the
+// backward), so a second backward of the same forward finds the queue full again.
 template <int C>
 __global__ void __launch_bounds__(256) k_project_backward(GaussPtrs g, Work w, Prm prm, int F,
                                                           float *__restrict__ g_means, float *__restrict__ g_scales,
                                                           float *__restrict__ g_quats, float *__restrict__ g_opacity,
-                                                          float *__restrict__ g_colors) {
+                                                          float *__restrict__ g_colors, int accumulate) {
   constexpr int G2 = (C <= 5) ? 16 : 20;
   const int64_t nu = (int64_t)w.counters[kNumUnstable];
   const int64_t N = g.n;
+  if (blockIdx.x == 0 && threadIdx.x == 0) w.counters[kQBwd] = 0ull;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nu; k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = w.ids[k];
     GParams P;
@@ -327,6 +368,7 @@ __global__ void __launch_bounds__(256) k_project_backward(GaussPtrs g, Work w, P
         for (int c = 0; c < C; ++c) gc[c] += row[kG2Col + c];
         const float gd0 = row[g2_d0(C)], gn[3] = {row[g2_nc(C)], row[g2_nc(C) + 1], row[g2_nc(C) + 2]};
         const float gz = row[g2_z(C)];
+
         // forward quantities (FP32 recomputation)
         const float d[3] = {P.p[0] - cam.t[0], P.p[1] - cam.t[1], P.p[2] - cam.t[2]};
         float pc[3];
@@ -450,6 +492,18 @@ __global__ void __launch_bounds__(256) k_project_backward(GaussPtrs g, Work w, P
 #pragma unroll
       for (int m = 0; m < 4; ++m) gq[m] = (gqn[m] - qh[m] * dotq) / qn;
     }
+    if (accumulate) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        gp[r] += g_means[3 * k + r];
+        gs[r] += g_scales[3 * k + r];
+      }
+#pragma unroll
+      for (int m = 0; m < 4; ++m) gq[m] += g_quats[4 * k + m];
+      ga += g_opacity[k];
+#pragma unroll
+      for (int c = 0; c < C; ++c) gc[c] += g_colors[(int64_t)C * k + c];
+    }
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       g_means[3 * k + r] = gp[r];
@@ -463,23 +517,38 @@ __global__ void __launch_bounds__(256) k_project_backward(GaussPtrs g, Work w, P
   }
 }
 
-void launch_backward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const uint8_t *mask,
-                     const float *dL_dcolor, const float *dL_ddepth, const L1Fused &l1, cudaStream_t s) {
-  if (C == 3)
-    k_backward<3><<<F * T, kTilePix, 0, s>>>(w, prm, N, T, mask, dL_dcolor, dL_ddepth, l1);
+template <int C, int B>
+static void launch_backward_cb(const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn,
+                               const BwdIn &in, cudaStream_t s) {
+  if (tn.schedule == 1)
+    k_backward_queue<C, B><<<tn.num_sms * tn.ctas_per_sm, 256, 0, s>>>(w, prm, N, T, in);
   else
-    k_backward<8><<<F * T, kTilePix, 0, s>>>(w, prm, N, T, mask, dL_dcolor, dL_ddepth, l1);
+    k_backward<C, B><<<F * T, 1 << (tn.tws + tn.ths), 0, s>>>(w, prm, N, T, in);
+}
+
+void launch_backward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn,
+                     const float *dL_dcolor, const float *dL_ddepth, const L1Fused &l1, cudaStream_t s) {
+  const BwdIn in{dL_dcolor, dL_ddepth, l1};
+  if (C == 3) {
+    if (tn.batch == 64) launch_backward_cb<3, 64>(w, prm, N, F, T, tn, in, s);
+    else launch_backward_cb<3, 32>(w, prm, N, F, T, tn, in, s);
+  } else {
+    if (tn.batch == 64) launch_backward_cb<8, 64>(w, prm, N, F, T, tn, in, s);
+    else launch_backward_cb<8, 32>(w, prm, N, F, T, tn, in, s);
+  }
 }
 
 void launch_project_backward(const GaussPtrs &g, const Work &w, const Prm &prm, int F, float *g_means,
-                             float *g_scales, float *g_quats, float *g_opacity, float *g_colors, cudaStream_t s) {
+                             float *g_scales, float *g_quats, float *g_opacity, float *g_colors, bool accumulate,
+                             cudaStream_t s) {
   if (g.n <= 0) return;
+  const int acc = accumulate ? 1 : 0;
   if (g.C == 3)
     k_project_backward<3><<<kPersistBlocks, 256, 0, s>>>(g, w, prm, F, g_means, g_scales, g_quats, g_opacity,
-                                                         g_colors);
+                                                         g_colors, acc);
   else
     k_project_backward<8><<<kPersistBlocks, 256, 0, s>>>(g, w, prm, F, g_means, g_scales, g_quats, g_opacity,
-                                                         g_colors);
+                                                         g_colors, acc);
 }
 
 }  // namespace rtg

@@ -1,33 +1,49 @@
-// Projection and tile binning (Section 3.1 rendering; tiles of 16 x 16 pixels as in
-// Supplement B): per-tile masked-pixel counts, the unstable index, the EWA projection
-// of every Gaussian into every frame, the exclusive scan of per-tile pair counts and
-// the emission of (depth, index) keys into per-tile buckets.
+// Projection and tile binning (Section 3.1 rendering on screen tiles; the unstable-mask
+// passes use the 16 x 16 tiles of Supplement B, the render passes the tuned tile):
+// per-tile masked-pixel counts and pixel lists, the unstable index, the EWA projection
+// of every Gaussian into every frame, the exclusive scan of per-tile pair counts (and
+// the work queue of the persistent schedule) and the emission of (depth, index) keys
+// into per-tile buckets.
 #include "kernels.cuh"
 #include "project.cuh"
 
 namespace rtg {
 
 // --------------------------------------------------------------------------- setup + tile mask
-// One CTA per (frame, tile).  Counts the masked in-image pixels of the tile (the
-// compacted pixel set of that tile) and clears its pair counter.  Block 0 also
-// publishes the cameras and clears the per-call counters.
-__global__ void __launch_bounds__(kTilePix) k_tile_mask(FrameSet fs, Work w, const uint8_t *__restrict__ mask,
-                                                        int T, long long nu_preset) {
+// One CTA of 2^(tws+ths) threads per (frame, tile) of a grid of 2^tws x 2^ths pixel tiles.
+// Counts the masked in-image pixels of the tile, clears its pair counter and, with
+// `lists`, writes the tile's masked pixels (index within the tile) compacted in raster
+// order: the forward and backward give each 32 of them to one warp.  With `setup`, block 0
+// also publishes the cameras and clears the per-call counters.
+__global__ void __launch_bounds__(kMaxTilePix) k_tile_mask(FrameSet fs, Work w, const uint8_t *__restrict__ mask,
+                                                           int T, int tiles_x, int tws, int ths, int setup,
+                                                           int lists, long long nu_preset) {
+  __shared__ int s_wcnt[kMaxTilePix / 32];
   const int tile = blockIdx.x;
   const int f = tile / T, lt = tile - f * T;
   const DevCam &cam = fs.cam[f];
-  if (blockIdx.x == 0) {
+  if (setup && blockIdx.x == 0) {
     for (int i = threadIdx.x; i < fs.F; i += blockDim.x) w.cams[i] = fs.cam[i];
     if (threadIdx.x < kNumCounters)
       w.counters[threadIdx.x] = (threadIdx.x == kNumUnstable && nu_preset >= 0) ? (unsigned long long)nu_preset : 0ull;
   }
-  const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-  const int px = tx * kTile + (threadIdx.x & (kTile - 1)), py = ty * kTile + (threadIdx.x / kTile);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tx = lt % tiles_x, ty = lt / tiles_x;
+  const int px = (tx << tws) + (tid & ((1 << tws) - 1)), py = (ty << ths) + (tid >> tws);
   bool in = px < cam.W && py < cam.H;
   if (in && mask != nullptr) in = mask[((int64_t)f * cam.H + py) * cam.W + px] != 0;
-  const int cnt = __syncthreads_count(in);
-  if (threadIdx.x == 0) {
-    w.tile_npix[tile] = (uint32_t)cnt;
+  const unsigned bal = __ballot_sync(0xffffffffu, in);
+  if (lane == 0) s_wcnt[wid] = __popc(bal);
+  __syncthreads();
+  int before = 0, total = 0;
+  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+    const int c = s_wcnt[k];
+    before += k < wid ? c : 0;
+    total += c;
+  }
+  if (lists && in) w.px_list[((int64_t)tile << (tws + ths)) + before + __popc(bal & lanemask_lt())] = (uint8_t)tid;
+  if (tid == 0) {
+    w.tile_npix[tile] = (uint32_t)total;
     w.tile_count[tile] = 0u;
   }
 }
@@ -203,8 +219,12 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
         ok = project_gaussian(w.cams[f], prm, P, R, kmin, o);
       }
       if (ok) {
-        const int tiles_x = w.cams[f].tiles_x;
-        tx0 = o.x0 / kTile; tx1 = o.x1 / kTile; ty0 = o.y0 / kTile; ty1 = o.y1 / kTile;
+        // the forward bins into the render grid, the mask passes into the 16 x 16 rule grid
+        const DevCam &cam = w.cams[f];
+        const int tws = kMode == kProjForward ? cam.tws : kTileShift;
+        const int ths = kMode == kProjForward ? cam.ths : kTileShift;
+        const int tiles_x = kMode == kProjForward ? cam.tiles_x : cam.mtiles_x;
+        tx0 = o.x0 >> tws; tx1 = o.x1 >> tws; ty0 = o.y0 >> ths; ty1 = o.y1 >> ths;
         const uint32_t *npix = w.tile_npix + (int64_t)f * T;
         if (kMode != kProjFused || g.unstable[i] != 0)
           for (int ty = ty0; ty <= ty1; ++ty)
@@ -219,6 +239,7 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
     }
     if (ok && (nt > 0 || kMode == kProjFused)) {
       const DevCam &cam = w.cams[f];
+      const int tiles_x = kMode == kProjForward ? cam.tiles_x : cam.mtiles_x;
       const uint32_t *npix = w.tile_npix + (int64_t)f * T;
       uint32_t *tcount = w.tile_count + (int64_t)f * T;
       const unsigned long long key = ((unsigned long long)__float_as_uint(o.Z) << 32) | (unsigned long long)(uint32_t)i;
@@ -226,7 +247,7 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
       if (nt > 0)  // kProjFused: stable Gaussians get records but no pairs here
         for (int ty = ty0; ty <= ty1; ++ty)
           for (int tx = tx0; tx <= tx1; ++tx) {
-            const int t = ty * cam.tiles_x + tx;
+            const int t = ty * tiles_x + tx;
             if (npix[t] != 0u) {
               const uint32_t slot = atomicAdd(tcount + t, 1u);
               if (idx < (unsigned long long)max_pairs)
@@ -248,8 +269,8 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
       w.rec_box[(int64_t)f * N + i] = make_float2(o.rx, o.ry);
       float4 *cold = w.rec_cold + ((int64_t)f * N + i) * 2;
       cold[0] = make_float4(o.n[0], o.n[1], o.n[2], o.d0);
-      cold[1] = make_float4(o.Z, __int_as_float(rk), __uint_as_float((uint32_t)tx0 | ((uint32_t)ty0 << 16)),
-                            __uint_as_float((uint32_t)tx1 | ((uint32_t)ty1 << 16)));
+      cold[1] = make_float4(o.Z, __int_as_float(rk), __uint_as_float((uint32_t)o.x0 | ((uint32_t)o.y0 << 16)),
+                            __uint_as_float((uint32_t)o.x1 | ((uint32_t)o.y1 << 16)));
       if (kMode != kProjMask && rk >= 0) {
         float4 *g2 = reinterpret_cast<float4 *>(w.grad2d + ((int64_t)f * N + rk) * G2);
 #pragma unroll
@@ -277,10 +298,12 @@ __global__ void __launch_bounds__(256) k_bin(Work w, int64_t N, int T, int64_t m
       e = w.cand[k];
       if (w.ntiles[e] != 0u) {
         f = (int)(e / (uint64_t)N);
-        tiles_x = w.cams[f].tiles_x;
+        const DevCam &cam = w.cams[f];
+        tiles_x = cam.tiles_x;
         c1 = w.rec_cold[(int64_t)e * 2 + 1];
         const uint32_t lo = __float_as_uint(c1.z), hi = __float_as_uint(c1.w);
-        tx0 = lo & 0xffff; ty0 = lo >> 16; tx1 = hi & 0xffff; ty1 = hi >> 16;
+        tx0 = (int)(lo & 0xffffu) >> cam.tws; ty0 = (int)(lo >> 16) >> cam.ths;
+        tx1 = (int)(hi & 0xffffu) >> cam.tws; ty1 = (int)(hi >> 16) >> cam.ths;
         const uint32_t *npix = w.tile_npix + (int64_t)f * T;
         for (int ty = ty0; ty <= ty1; ++ty)
           for (int tx = tx0; tx <= tx1; ++tx) nt += npix[ty * tiles_x + tx] != 0u;
@@ -310,8 +333,22 @@ __global__ void __launch_bounds__(256) k_bin(Work w, int64_t N, int T, int64_t m
 }
 
 // --------------------------------------------------------------------------- tile scan
+// Cost class of a tile list of n records for the persistent schedule's queue: 0 for an
+// empty list, else four classes per octave of n (so the order is by n to within 19%).
+constexpr int kQueueClasses = 4 * 32 + 4;
+__device__ __forceinline__ int queue_class(uint32_t n) {
+  if (n == 0u) return 0;
+  const int lg = 31 - __clz(n);
+  const int sub = lg >= 2 ? (int)((n >> (lg - 2)) & 3u) : (int)((n << (2 - lg)) & 3u);
+  return 1 + 4 * lg + sub;
+}
+
 // One CTA: exclusive scan of the per-tile pair counts into bucket offsets, capacity check.
-__global__ void __launch_bounds__(1024) k_scan_tiles(Work w, int FT, int64_t max_pairs) {
+// With gshift >= 0 it also lays out the persistent schedule's work: one item per 32
+// masked pixels of each tile (2^gshift groups per tile at most), ordered by the tile's
+// list length, longest first (a counting sort on queue_class; the order within a class
+// is arbitrary and does not affect any result).
+__global__ void __launch_bounds__(1024) k_scan_tiles(Work w, int FT, int64_t max_pairs, int gshift) {
   __shared__ unsigned long long s_warp[32];
   __shared__ uint32_t s_wmax[32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -371,6 +408,35 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Work w, int FT, int64_t max
       atomicCAS(w.status, 0u, (uint32_t)(int32_t)RTG_ERR_WORKSPACE);
     }
   }
+  if (gshift < 0) return;
+  // ---- item queue
+  __shared__ uint32_t s_cls[kQueueClasses];
+  for (int k = tid; k < kQueueClasses; k += 1024) s_cls[k] = 0u;
+  __syncthreads();
+  for (int t = b; t < e; ++t) {
+    const uint32_t np = w.tile_npix[t];
+    if (np != 0u) atomicAdd(&s_cls[queue_class(w.tile_count[t])], (np + 31u) >> 5);
+  }
+  __syncthreads();
+  if (tid == 0) {  // start of each class, classes in decreasing cost
+    uint32_t run = 0;
+    for (int k = kQueueClasses - 1; k >= 0; --k) {
+      const uint32_t c = s_cls[k];
+      s_cls[k] = run;
+      run += c;
+    }
+    w.counters[kItems] = run;
+    w.counters[kQFwd] = 0ull;
+    w.counters[kQBwd] = 0ull;
+  }
+  __syncthreads();
+  for (int t = b; t < e; ++t) {
+    const uint32_t np = w.tile_npix[t];
+    if (np == 0u) continue;
+    const uint32_t ng = (np + 31u) >> 5;
+    const uint32_t pos = atomicAdd(&s_cls[queue_class(w.tile_count[t])], ng);
+    for (uint32_t g = 0; g < ng; ++g) w.items[pos + g] = ((uint32_t)t << 3) | g;
+  }
 }
 
 // --------------------------------------------------------------------------- emission
@@ -386,9 +452,10 @@ __global__ void __launch_bounds__(256) k_emit(Work w) {
   }
 }
 
-void launch_tile_mask(const FrameSet &fs, const Work &w, const uint8_t *mask, int T, long long nu_preset,
-                      cudaStream_t s) {
-  k_tile_mask<<<fs.F * T, kTilePix, 0, s>>>(fs, w, mask, T, nu_preset);
+void launch_tile_mask(const FrameSet &fs, const Work &w, const uint8_t *mask, int T, int tiles_x, int tws, int ths,
+                      bool setup, bool lists, long long nu_preset, cudaStream_t s) {
+  k_tile_mask<<<fs.F * T, 1 << (tws + ths), 0, s>>>(fs, w, mask, T, tiles_x, tws, ths, setup ? 1 : 0, lists ? 1 : 0,
+                                                    nu_preset);
 }
 
 void launch_rank(const uint8_t *unstable, int64_t n, int32_t *block_cnt, int32_t *rank, int32_t *ids,
@@ -432,8 +499,8 @@ void launch_bin(const Work &w, int64_t N, int T, int64_t max_pairs, cudaStream_t
   k_bin<<<kPersistBlocks, 256, 0, s>>>(w, N, T, max_pairs);
 }
 
-void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, cudaStream_t s) {
-  k_scan_tiles<<<1, 1024, 0, s>>>(w, FT, max_pairs);
+void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, int gshift, cudaStream_t s) {
+  k_scan_tiles<<<1, 1024, 0, s>>>(w, FT, max_pairs, gshift);
 }
 
 void launch_emit(const Work &w, cudaStream_t s) { k_emit<<<kPersistBlocks, 256, 0, s>>>(w); }

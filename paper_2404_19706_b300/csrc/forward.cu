@@ -1,59 +1,44 @@
-// Forward compositing (Section 3.1): per 16x16 tile, the masked pixels composite the
-// tile's front-to-back list — colour by alpha blending (Eq. 1) with the footprint of
+// Forward compositing (Section 3.1): per render tile, the masked pixels composite the
+// tile's front-to-back list: colour by alpha blending (Eq. 1) with the footprint of
 // Eq. 2 and transmission of Eq. 3, stopping before a fragment that would take the
-// transmission below t_eps — and take their depth from the first processed fragment
-// with f > delta_alpha (the opaque-disc hit), through the ray/disc-plane intersection
-// of Eq. 4 and the cases of Eq. 5.  The masked pixels of a tile are compacted onto the
-// lowest threads, so warps without pixels skip the compositing loop (only pixels
-// covered by unstable Gaussians are rendered, Supplement B).  After the compaction each
-// warp works alone on its 32 pixels: it walks the tile's list in batches of 32 records,
-// keeps only the records whose support box reaches the warp's pixel box (a conservative
-// test, so the result is that of the per-pixel alpha_min test), and stops as soon as all
-// its pixels have stopped.
+// transmission below t_eps.  Each pixel takes its depth from the first processed
+// fragment with f > delta_alpha (the opaque-disc hit), through the ray/disc-plane
+// intersection of Eq. 4 and the cases of Eq. 5.  Only the masked pixels of a tile are
+// rendered (only pixels covered by unstable Gaussians, Supplement B): the tile-mask pass
+// compacted them into a list, and each warp works alone on 32 of them.  It walks the
+// tile's list in batches of B records and keeps only the records whose support box
+// reaches the warp's pixel box.  That test is conservative, so the result is that of the
+// per-pixel alpha_min test.  A warp stops as soon as all its pixels have stopped.
+// Two schedules share that per-warp body: one CTA per tile (one warp per 32 masked
+// pixels), or persistent warps that take (tile, group) items from the cost-ordered queue
+// spanning every frame of the call.
 #include "kernels.cuh"
 #include "project.cuh"
 
 namespace rtg {
 
-template <int C>
-__global__ void __launch_bounds__(kTilePix) k_forward(Work w, Prm prm, int64_t N, int T,
-                                                      const uint8_t *__restrict__ mask, float *__restrict__ color,
-                                                      float *__restrict__ depth, float *__restrict__ alpha,
-                                                      int32_t *__restrict__ index_map,
-                                                      const float *__restrict__ tcolor,
-                                                      const float *__restrict__ tdepth) {
+struct FwdOut {
+  float *color, *depth, *alpha;
+  int32_t *index_map;
+  const float *tcolor, *tdepth;  // fused L1 targets (nullptr: not fused)
+};
+
+// Renders the pixels of group `grp` (32 consecutive entries of the tile's pixel list) of
+// render tile `tile`.  Called by a whole warp; s_rec / s_j are the warp's own staging.
+template <int C, int B>
+__device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int64_t N, int T, int tile, int grp,
+                                              float4 (*s_rec)[B], uint32_t *s_j, const FwdOut &out) {
   constexpr int H4 = (C <= 4) ? 3 : 4;
-  constexpr int NW = kTilePix / 32;
-  __shared__ float4 s_rec[NW][H4][32];
-  __shared__ uint32_t s_j[NW][32];
-  __shared__ int s_pix[kTilePix];
-  __shared__ int s_wcnt[NW];
-  if (w.counters[kSkip] != 0ull) return;
-  const int tile = blockIdx.x;
-  if (w.tile_npix[tile] == 0u) return;
+  constexpr int R = B / 32;  // records per lane per batch
+  const int lane = threadIdx.x & 31;
   const int f = tile / T, lt = tile - f * T;
   const DevCam &cam = w.cams[f];
+  const int tws = cam.tws, ths = cam.ths;
   const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  // compact the masked pixels of the tile onto threads 0..npix-1 (the only block barriers)
-  {
-    const int px = tx * kTile + (tid & (kTile - 1)), py = ty * kTile + tid / kTile;
-    bool act = px < cam.W && py < cam.H;
-    if (act && mask != nullptr) act = mask[((int64_t)f * cam.H + py) * cam.W + px] != 0;
-    const unsigned bal = __ballot_sync(0xffffffffu, act);
-    if (lane == 0) s_wcnt[wid] = __popc(bal);
-    __syncthreads();
-    int before = 0;
-    for (int k = 0; k < wid; ++k) before += s_wcnt[k];
-    if (act) s_pix[before + __popc(bal & lanemask_lt())] = tid;
-    __syncthreads();
-  }
-  // From here on every warp works alone on its 32 compacted pixels.
-  const int npix = (int)w.tile_npix[tile];
-  if (wid * 32 >= npix) return;
-  const bool has = tid < npix;
-  const int my = has ? s_pix[tid] : 0;
-  const int px = tx * kTile + (my & (kTile - 1)), py = ty * kTile + my / kTile;
+  const int q = grp * 32 + lane;
+  const bool has = q < (int)w.tile_npix[tile];
+  const int my = has ? (int)w.px_list[((int64_t)tile << (tws + ths)) + q] : 0;
+  const int px = (tx << tws) + (my & ((1 << tws) - 1)), py = (ty << ths) + (my >> tws);
   const float fpx = (float)px, fpy = (float)py;
   // bounding box of the warp's pixels: records whose support box misses it are skipped
   const int bx0 = __reduce_min_sync(0xffffffffu, has ? px : 0x7fffffff);
@@ -74,43 +59,58 @@ __global__ void __launch_bounds__(kTilePix) k_forward(Work w, Prm prm, int64_t N
   uint32_t last = 0, nfrag = 0;
   int hit_j = -1;
   bool done = !has;
-  // the records of batch b0 are fetched while batch b0 - 32 is composited
-  float4 r[H4];
-  float2 bb = make_float2(0.f, 0.f);
-  bool valid = lane < (int)n;
-  if (valid) {
-    const uint32_t gid = w.sorted[off + lane];
+  // the records of batch b0 + B are fetched while batch b0 is composited
+  float4 r[R][H4];
+  float2 bb[R];
+  bool valid[R];
 #pragma unroll
-    for (int k = 0; k < H4; ++k) r[k] = rec[(int64_t)gid * H4 + k];
-    bb = box[gid];
+  for (int u = 0; u < R; ++u) {
+    const uint32_t j = (uint32_t)(u * 32 + lane);
+    valid[u] = j < n;
+    bb[u] = make_float2(0.f, 0.f);
+    if (valid[u]) {
+      const uint32_t gid = w.sorted[off + j];
+#pragma unroll
+      for (int k = 0; k < H4; ++k) r[u][k] = rec[(int64_t)gid * H4 + k];
+      bb[u] = box[gid];
+    }
   }
-  for (uint32_t b0 = 0; b0 < n; b0 += 32) {
+  for (uint32_t b0 = 0; b0 < n; b0 += B) {
     if (__all_sync(0xffffffffu, done)) break;
-    const uint32_t j = b0 + lane;
-    const uint32_t jn = j + 32;
-    const bool vnext = jn < n;
-    float4 rn[H4];
-    float2 bn = make_float2(0.f, 0.f);
-    if (vnext) {
-      const uint32_t gid = w.sorted[off + jn];
+    float4 rn[R][H4];
+    float2 bn[R];
+    bool vn[R];
 #pragma unroll
-      for (int k = 0; k < H4; ++k) rn[k] = rec[(int64_t)gid * H4 + k];
-      bn = box[gid];
+    for (int u = 0; u < R; ++u) {
+      const uint32_t jn = b0 + B + (uint32_t)(u * 32 + lane);
+      vn[u] = jn < n;
+      bn[u] = make_float2(0.f, 0.f);
+      if (vn[u]) {
+        const uint32_t gid = w.sorted[off + jn];
+#pragma unroll
+        for (int k = 0; k < H4; ++k) rn[u][k] = rec[(int64_t)gid * H4 + k];
+        bn[u] = box[gid];
+      }
     }
     // keep the records whose support box reaches the warp's pixel box, in list order
-    const bool keep = valid && fabsf(r[0].x - wcx) <= whx + bb.x && fabsf(r[0].y - wcy) <= why + bb.y;
-    const unsigned bal = __ballot_sync(0xffffffffu, keep);
-    if (keep) {
-      const int slot = __popc(bal & lanemask_lt());
+    int cnt = 0;
 #pragma unroll
-      for (int k = 0; k < H4; ++k) s_rec[wid][k][slot] = r[k];
-      s_j[wid][slot] = j;
+    for (int u = 0; u < R; ++u) {
+      const bool keep =
+          valid[u] && fabsf(r[u][0].x - wcx) <= whx + bb[u].x && fabsf(r[u][0].y - wcy) <= why + bb[u].y;
+      const unsigned bal = __ballot_sync(0xffffffffu, keep);
+      if (keep) {
+        const int slot = cnt + __popc(bal & lanemask_lt());
+#pragma unroll
+        for (int k = 0; k < H4; ++k) s_rec[k][slot] = r[u][k];
+        s_j[slot] = b0 + (uint32_t)(u * 32 + lane);
+      }
+      cnt += __popc(bal);
     }
     __syncwarp();
     if (!done) {
-      const int cnt = __popc(bal);
       for (int k = 0; k < cnt; ++k) {
-        const float4 r0 = s_rec[wid][0][k], r1 = s_rec[wid][1][k];
+        const float4 r0 = s_rec[0][k], r1 = s_rec[1][k];
         float dx, dy, t1, t2, g;
         const float fa = footprint(fpx, fpy, r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, prm.f_max, dx, dy, t1,
                                    t2, g);
@@ -121,15 +121,15 @@ __global__ void __launch_bounds__(kTilePix) k_forward(Work w, Prm prm, int64_t N
           break;
         }
         const float wgt = fa * T_;
-        const float4 c0 = s_rec[wid][2][k];
+        const float4 c0 = s_rec[2][k];
         float cw[8] = {c0.x, c0.y, c0.z, c0.w, 0.f, 0.f, 0.f, 0.f};
         if (H4 == 4) {
-          const float4 c1 = s_rec[wid][3 % H4][k];
+          const float4 c1 = s_rec[3 % H4][k];
           cw[4] = c1.x; cw[5] = c1.y; cw[6] = c1.z; cw[7] = c1.w;
         }
 #pragma unroll
         for (int c = 0; c < C; ++c) acc[c] = fmaf(cw[c], wgt, acc[c]);
-        const uint32_t jj = s_j[wid][k];
+        const uint32_t jj = s_j[k];
         if (hit_j < 0 && fa > prm.delta_alpha) hit_j = (int)jj;
         T_ = Tn;
         last = jj + 1;
@@ -138,17 +138,20 @@ __global__ void __launch_bounds__(kTilePix) k_forward(Work w, Prm prm, int64_t N
     }
     __syncwarp();
 #pragma unroll
-    for (int k = 0; k < H4; ++k) r[k] = rn[k];
-    bb = bn;
-    valid = vnext;
+    for (int u = 0; u < R; ++u) {
+#pragma unroll
+      for (int k = 0; k < H4; ++k) r[u][k] = rn[u][k];
+      bb[u] = bn[u];
+      valid[u] = vn[u];
+    }
   }
   float lc = 0.f, ld = 0.f, nd = 0.f;
   if (has) {
     const int64_t HW = (int64_t)cam.H * cam.W;
     const int64_t pix = (int64_t)f * HW + (int64_t)py * cam.W + px;
 #pragma unroll
-    for (int c = 0; c < C; ++c) color[((int64_t)f * C + c) * HW + (int64_t)py * cam.W + px] = acc[c];
-    alpha[pix] = 1.f - T_;
+    for (int c = 0; c < C; ++c) out.color[((int64_t)f * C + c) * HW + (int64_t)py * cam.W + px] = acc[c];
+    out.alpha[pix] = 1.f - T_;
     int hit_gid = -1;
     float D = -1.f;
     if (hit_j >= 0) {
@@ -160,30 +163,30 @@ __global__ void __launch_bounds__(kTilePix) k_forward(Work w, Prm prm, int64_t N
       const float nu = sqrtf(fmaf(ux, ux, fmaf(uy, uy, 1.f)));
       D = (fabsf(den) >= prm.cos_max * nu) ? c0.w / den : c1.x;
     }
-    depth[pix] = D;
-    if (index_map != nullptr) index_map[pix] = hit_gid;
+    out.depth[pix] = D;
+    if (out.index_map != nullptr) out.index_map[pix] = hit_gid;
     w.px_T[pix] = T_;
     w.px_last[pix] = last;
     w.px_hit[pix] = hit_gid;
-    if (tcolor != nullptr) {  // fused L1 terms of this pixel (Eq. 7)
+    if (out.tcolor != nullptr) {  // fused L1 terms of this pixel (Eq. 7)
 #pragma unroll
       for (int c = 0; c < C; ++c)
-        lc += fabsf(acc[c] - tcolor[((int64_t)f * C + c) * HW + (int64_t)py * cam.W + px]);
-      const float td = tdepth[pix];
+        lc += fabsf(acc[c] - out.tcolor[((int64_t)f * C + c) * HW + (int64_t)py * cam.W + px]);
+      const float td = out.tdepth[pix];
       if (D != -1.f && td > 0.f) {
         ld = fabsf(D - td);
         nd = 1.f;
       }
     }
   }
-  if (tcolor != nullptr) {  // fixed-order per-warp partials, summed by k_loss_finalize
+  if (out.tcolor != nullptr) {  // fixed-order per-group partials, summed by k_loss_finalize
     for (int o = 16; o > 0; o >>= 1) {
       lc += __shfl_xor_sync(0xffffffffu, lc, o);
       ld += __shfl_xor_sync(0xffffffffu, ld, o);
       nd += __shfl_xor_sync(0xffffffffu, nd, o);
     }
     if (lane == 0) {
-      float *lp = w.tile_loss + ((int64_t)tile * (kTilePix / 32) + wid) * 4;
+      float *lp = w.tile_loss + (((int64_t)tile << (tws + ths - 5)) + grp) * 4;
       lp[0] = lc;
       lp[1] = ld;
       lp[2] = nd;
@@ -194,13 +197,60 @@ __global__ void __launch_bounds__(kTilePix) k_forward(Work w, Prm prm, int64_t N
   if (lane == 0 && fr) atomicAdd(w.counters + kFragments, (unsigned long long)fr);
 }
 
-void launch_forward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const uint8_t *mask, float *color,
+// Schedule 0: CTA `tile` with one warp per 32-pixel group of the tile's pixel list.
+template <int C, int B>
+__global__ void __launch_bounds__(kMaxTilePix) k_forward(Work w, Prm prm, int64_t N, int T, FwdOut out) {
+  constexpr int H4 = (C <= 4) ? 3 : 4;
+  __shared__ float4 s_rec[kMaxTilePix / 32][H4][B];
+  __shared__ uint32_t s_j[kMaxTilePix / 32][B];
+  if (w.counters[kSkip] != 0ull) return;
+  const int tile = blockIdx.x, wid = threadIdx.x >> 5;
+  if (wid * 32 >= (int)w.tile_npix[tile]) return;
+  forward_group<C, B>(w, prm, N, T, tile, wid, s_rec[wid], s_j[wid], out);
+}
+
+// Schedule 1: persistent warps.  Warp k of the grid starts with item k; later items come
+// from a shared counter, so warps that finish early take the remaining work.  The queue
+// holds the longest lists first.
+template <int C, int B>
+__global__ void __launch_bounds__(256) k_forward_queue(Work w, Prm prm, int64_t N, int T, FwdOut out) {
+  constexpr int H4 = (C <= 4) ? 3 : 4;
+  __shared__ float4 s_rec[8][H4][B];
+  __shared__ uint32_t s_j[8][B];
+  if (w.counters[kSkip] != 0ull) return;
+  const uint32_t nitems = (uint32_t)w.counters[kItems];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t nwarps = gridDim.x * 8u;
+  uint32_t it = blockIdx.x * 8u + (uint32_t)wid;
+  while (it < nitems) {
+    const uint32_t item = w.items[it];
+    forward_group<C, B>(w, prm, N, T, (int)(item >> 3), (int)(item & 7u), s_rec[wid], s_j[wid], out);
+    uint32_t nx = 0;
+    if (lane == 0) nx = nwarps + (uint32_t)atomicAdd(w.counters + kQFwd, 1ull);
+    it = __shfl_sync(0xffffffffu, nx, 0);
+  }
+}
+
+template <int C, int B>
+static void launch_forward_cb(const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn,
+                              const FwdOut &out, cudaStream_t s) {
+  if (tn.schedule == 1)
+    k_forward_queue<C, B><<<tn.num_sms * tn.ctas_per_sm, 256, 0, s>>>(w, prm, N, T, out);
+  else
+    k_forward<C, B><<<F * T, 1 << (tn.tws + tn.ths), 0, s>>>(w, prm, N, T, out);
+}
+
+void launch_forward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn, float *color,
                     float *depth, float *alpha, int32_t *index_map, const float *tcolor, const float *tdepth,
                     cudaStream_t s) {
-  if (C == 3)
-    k_forward<3><<<F * T, kTilePix, 0, s>>>(w, prm, N, T, mask, color, depth, alpha, index_map, tcolor, tdepth);
-  else
-    k_forward<8><<<F * T, kTilePix, 0, s>>>(w, prm, N, T, mask, color, depth, alpha, index_map, tcolor, tdepth);
+  const FwdOut out{color, depth, alpha, index_map, tcolor, tdepth};
+  if (C == 3) {
+    if (tn.batch == 64) launch_forward_cb<3, 64>(w, prm, N, F, T, tn, out, s);
+    else launch_forward_cb<3, 32>(w, prm, N, F, T, tn, out, s);
+  } else {
+    if (tn.batch == 64) launch_forward_cb<8, 64>(w, prm, N, F, T, tn, out, s);
+    else launch_forward_cb<8, 32>(w, prm, N, F, T, tn, out, s);
+  }
 }
 
 }  // namespace rtg

@@ -12,6 +12,19 @@ constexpr int kSortCap = 2048;     // keys a tile-sort CTA sorts entirely in sha
 constexpr int kLossBlocks = 296;   // 2 x 148 SMs
 constexpr int kPersistBlocks = 148 * 8;
 
+// Launch configuration of the render path (the C ABI's rtg_tuning, validated, with the
+// tile sides as shifts).
+struct Tuning {
+  int tws, ths;       // render tile 2^tws x 2^ths pixels
+  int batch;          // records per warp batch: 32 or 64
+  int schedule;       // 0: CTA per tile; 1: persistent warps over the item queue
+  int ctas_per_sm;    // schedule 1
+  int sort_bits;      // 4 or 8
+  int sort_rank_max;  // 0..kSortCap
+  int num_sms;        // of the context's device
+  int gshift() const { return tws + ths - 5; }  // log2(32-pixel groups per tile)
+};
+
 // Cameras of one call, passed by value to the first kernel of a forward.
 struct FrameSet {
   int F;
@@ -67,29 +80,35 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 
 // ---- host launchers (each defined in the translation unit of its kernels)
 // bin.cu
-void launch_tile_mask(const FrameSet &fs, const Work &w, const uint8_t *mask, int T, long long nu_preset,
-                      cudaStream_t s);
+// Per-tile masked-pixel counts over a grid of 2^tws x 2^ths tiles (tiles_x per row), and,
+// with `lists`, the compacted pixel lists.  `setup`: also publish the cameras and clear
+// the per-call counters (the first kernel of every call).
+void launch_tile_mask(const FrameSet &fs, const Work &w, const uint8_t *mask, int T, int tiles_x, int tws, int ths,
+                      bool setup, bool lists, long long nu_preset, cudaStream_t s);
 void launch_rank(const uint8_t *unstable, int64_t n, int32_t *block_cnt, int32_t *rank, int32_t *ids,
                  unsigned long long *nu_counter, int64_t *nu_out, cudaStream_t s);
 enum ProjMode { kProjForward = 0, kProjMask = 1, kProjFused = 2 };
 void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, int T, int mode, int64_t max_pairs,
                     cudaStream_t s);
 void launch_bin(const Work &w, int64_t N, int T, int64_t max_pairs, cudaStream_t s);
-void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, cudaStream_t s);
+// gshift >= 0: also build the persistent schedule's item queue (2^gshift groups per tile)
+void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, int gshift, cudaStream_t s);
 void launch_emit(const Work &w, cudaStream_t s);
 // sort.cu
-void launch_sort_tiles(const Work &w, int FT, cudaStream_t s);
+void launch_sort_tiles(const Work &w, int FT, int bits, int rank_max, cudaStream_t s);
 void init_sort_attributes();
 // forward.cu
-void launch_forward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const uint8_t *mask, float *color,
+void launch_forward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn, float *color,
                     float *depth, float *alpha, int32_t *index_map, const float *tcolor, const float *tdepth,
                     cudaStream_t s);
 // backward.cu
-void launch_backward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const uint8_t *mask,
+void launch_backward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn,
                      const float *dL_dcolor, const float *dL_ddepth, const L1Fused &l1, cudaStream_t s);
-void launch_loss_finalize(const Work &w, int FT, int C, float w_c, float w_d, float *loss_out, cudaStream_t s);
+void launch_loss_finalize(const Work &w, int FT, int gshift, int C, float w_c, float w_d, float *loss_out,
+                          cudaStream_t s);
 void launch_project_backward(const GaussPtrs &g, const Work &w, const Prm &prm, int F, float *g_means,
-                             float *g_scales, float *g_quats, float *g_opacity, float *g_colors, cudaStream_t s);
+                             float *g_scales, float *g_quats, float *g_opacity, float *g_colors, bool accumulate,
+                             cudaStream_t s);
 // loss_adam_mask.cu
 void launch_l1_loss(const Work &w, int F, int C, int H, int W, const float *color, const float *depth,
                     const float *tcolor, const float *tdepth, const uint8_t *mask, float w_c, float w_d,
@@ -104,7 +123,10 @@ void launch_gather(int64_t nu, int C, const int32_t *ids, const float *means, co
 void launch_scatter(int64_t nu, int C, const int32_t *ids, const float *um, const float *us, const float *uq,
                     const float *uo, const float *uc, float *means, float *scales, float *quats, float *opacity,
                     float *colors, cudaStream_t s);
+// mode 0: rtg_unstable_mask; 1: fused, and the render grid is the 16 x 16 mask grid, so the
+// kernel also writes the render tiles' pixel counts and lists; 2: fused, other render grid.
+enum CoverMode { kCoverPlain = 0, kCoverFusedSame = 1, kCoverFusedOther = 2 };
 void launch_mask_cover_tiles(const Work &w, const Prm &prm, int64_t N, int F, int T, int C, uint8_t *mask,
-                             bool fused, cudaStream_t s);
+                             int mode, cudaStream_t s);
 
 }  // namespace rtg

@@ -84,18 +84,19 @@ __global__ void __launch_bounds__(256) k_loss_reduce(Work w, int F, int C, int H
   }
 }
 
-// Fused L1 (Eq. 7/8): sums the forward's per-(tile, warp) partials in a fixed order (only
-// the warps that held masked pixels wrote them), then the loss and its gradient scales.
+// Fused L1 (Eq. 7/8): sums the forward's per-(tile, 32-pixel group) partials in a fixed
+// order (only groups that held masked pixels wrote them), then the loss and its gradient
+// scales.  2^gshift groups per tile.
 // B300's FP64 rate is a small fraction of FP32 and this runs on one SM, so the sums are
 // FP32 with Kahan compensation per thread and a fixed-order tree across threads.
-__global__ void __launch_bounds__(1024) k_loss_finalize(Work w, int FT, int C, float w_c, float w_d,
+__global__ void __launch_bounds__(1024) k_loss_finalize(Work w, int FT, int gshift, int C, float w_c, float w_d,
                                                         float *__restrict__ loss_out) {
   __shared__ float s_t[3][1024];
   float t[3] = {0.f, 0.f, 0.f}, comp[3] = {0.f, 0.f, 0.f};
   for (int tile = threadIdx.x; tile < FT; tile += 1024) {
     const int nw = (int)((w.tile_npix[tile] + 31u) / 32u);
     for (int k = 0; k < nw; ++k) {
-      const float *lp = w.tile_loss + ((int64_t)tile * (kTilePix / 32) + k) * 4;
+      const float *lp = w.tile_loss + (((int64_t)tile << gshift) + k) * 4;
 #pragma unroll
       for (int q = 0; q < 3; ++q) {  // Kahan summation
         const float y = lp[q] - comp[q];
@@ -126,8 +127,9 @@ __global__ void __launch_bounds__(1024) k_loss_finalize(Work w, int FT, int C, f
   }
 }
 
-void launch_loss_finalize(const Work &w, int FT, int C, float w_c, float w_d, float *loss_out, cudaStream_t s) {
-  k_loss_finalize<<<1, 1024, 0, s>>>(w, FT, C, w_c, w_d, loss_out);
+void launch_loss_finalize(const Work &w, int FT, int gshift, int C, float w_c, float w_d, float *loss_out,
+                          cudaStream_t s) {
+  k_loss_finalize<<<1, 1024, 0, s>>>(w, FT, gshift, C, w_c, w_d, loss_out);
 }
 
 __device__ __forceinline__ float signf_(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
@@ -251,17 +253,20 @@ __global__ void k_scatter(int64_t nu, int C, const int32_t *__restrict__ ids, co
 // stops as soon as all its pixels are covered.  The tile rule (Supplement B) is applied in
 // the same kernel: a tile with fewer than `discard` of its in-image pixels covered is
 // cleared.  Every in-image pixel of the mask is written.
-// kFused (rtg_render_forward_masked): the tile's masked-pixel count replaces the coverage
-// pass's tile activity and the pair counters are cleared for the second binning.
-template <bool kFused>
+// kMode = kCoverFusedSame (rtg_render_forward_masked, render tiles = 16 x 16): the tile's
+// masked-pixel count and pixel list replace the coverage pass's, and the pair counters are
+// cleared for the second binning.  kCoverFusedOther (other render tiles): only the staging
+// counter is cleared; a tile-mask pass over the render grid follows.
+template <int kMode>
 __global__ void __launch_bounds__(kTilePix) k_mask_cover_tiles(Work w, Prm prm, int64_t N, int T, int H4,
                                                                uint8_t *__restrict__ mask) {
   __shared__ float4 s_rec[2][kTilePix];
+  __shared__ int s_wcnt[kTilePix / 32];
   if (w.counters[kSkip] != 0ull) return;
   const int tile = blockIdx.x;
   const int f = tile / T, lt = tile - f * T;
   const DevCam &cam = w.cams[f];
-  const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
+  const int tx = lt % cam.mtiles_x, ty = lt / cam.mtiles_x;
   const int tid = threadIdx.x;
   const int px = tx * kTile + (tid & (kTile - 1)), py = ty * kTile + tid / kTile;
   const bool in = px < cam.W && py < cam.H;
@@ -296,11 +301,21 @@ __global__ void __launch_bounds__(kTilePix) k_mask_cover_tiles(Work w, Prm prm, 
   const int n_cov = __syncthreads_count(cov);
   const bool keep = !(prm.discard > 0.f) || (float)n_cov >= prm.discard * (float)n_in;
   if (in) mask[((int64_t)f * cam.H + py) * cam.W + px] = (cov && keep) ? 1 : 0;
-  if (kFused && tid == 0) {
-    w.tile_npix[tile] = keep ? (uint32_t)n_cov : 0u;
-    w.tile_count[tile] = 0u;
-    if (tile == 0) w.counters[kStaged] = 0ull;
+  if (kMode == kCoverFusedSame) {  // compacted pixel list of the render tile (raster order)
+    const bool act = in && cov && keep;
+    const int lane = tid & 31, wid = tid >> 5;
+    const unsigned bal = __ballot_sync(0xffffffffu, act);
+    if (lane == 0) s_wcnt[wid] = __popc(bal);
+    __syncthreads();
+    int before = 0;
+    for (int k = 0; k < wid; ++k) before += s_wcnt[k];
+    if (act) w.px_list[((int64_t)tile << (2 * kTileShift)) + before + __popc(bal & lanemask_lt())] = (uint8_t)tid;
+    if (tid == 0) {
+      w.tile_npix[tile] = keep ? (uint32_t)n_cov : 0u;
+      w.tile_count[tile] = 0u;
+    }
   }
+  if (kMode != kCoverPlain && tile == 0 && tid == 0) w.counters[kStaged] = 0ull;
 }
 
 void launch_l1_loss(const Work &w, int F, int C, int H, int W, const float *color, const float *depth,
@@ -342,11 +357,13 @@ void launch_scatter(int64_t nu, int C, const int32_t *ids, const float *um, cons
 }
 
 void launch_mask_cover_tiles(const Work &w, const Prm &prm, int64_t N, int F, int T, int C, uint8_t *mask,
-                             bool fused, cudaStream_t s) {
-  if (fused)
-    k_mask_cover_tiles<true><<<F * T, kTilePix, 0, s>>>(w, prm, N, T, hot4_of(C), mask);
+                             int mode, cudaStream_t s) {
+  if (mode == kCoverFusedSame)
+    k_mask_cover_tiles<kCoverFusedSame><<<F * T, kTilePix, 0, s>>>(w, prm, N, T, hot4_of(C), mask);
+  else if (mode == kCoverFusedOther)
+    k_mask_cover_tiles<kCoverFusedOther><<<F * T, kTilePix, 0, s>>>(w, prm, N, T, hot4_of(C), mask);
   else
-    k_mask_cover_tiles<false><<<F * T, kTilePix, 0, s>>>(w, prm, N, T, hot4_of(C), mask);
+    k_mask_cover_tiles<kCoverPlain><<<F * T, kTilePix, 0, s>>>(w, prm, N, T, hot4_of(C), mask);
 }
 
 }  // namespace rtg

@@ -6,13 +6,16 @@
 //            {u11, u12, u22, alpha}                Cholesky factor of Sigma_2D^-1 (scaled)
 //            {colour 0..3}, {colour 4..7}          C = 3 uses one colour vector, C = 8 two
 //   rec_cold [F][N][2] float4     {n_c.x, n_c.y, n_c.z, d0 = p_c . n_c},
-//                                 {z_c, rank (int bits), rect lo (tx0|ty0<<16), rect hi}
+//                                 {z_c, rank (int bits), pixel rect lo (x0|y0<<16), hi (x1|y1<<16)}
 //   rec_box  [F][N] float2        half-extents of the alpha_min support box around mu
 //   ntiles   [F][N] uint32        masked tiles touched (0 = culled or off-mask)
 //   cand     [F*N] uint32         (frame, Gaussian) pairs f * N + i that passed the coarse cull
 //   stage    [pairs] uint4        (tile, slot, key) of every pair, written by the projection
 //   keys     [pairs] uint64       (float bits of z_c) << 32 | Gaussian index, bucketed by tile
 //   sorted   [pairs] uint32       Gaussian index, each tile's bucket in front-to-back order
+//   px_list  [F*T][tile pixels] u8 masked pixels of each render tile (index in the tile),
+//                                 compacted in raster order
+//   items    [groups] uint32      (tile << 3 | 32-pixel group) work items, longest list first
 //   px_*     [F][H][W]            per-pixel state saved by the forward for the backward
 //   grad2d   [F][N][G2] float     per-(frame, unstable Gaussian) screen-space gradients
 #pragma once
@@ -24,8 +27,10 @@
 
 namespace rtg {
 
-constexpr int kTile = RTG_TILE;              // 16 x 16 pixel tiles
-constexpr int kTilePix = kTile * kTile;      // 256 pixels = 256 threads per tile CTA
+constexpr int kTile = RTG_TILE;              // 16 x 16 tiles of the unstable-mask rule
+constexpr int kTileShift = 4;                // log2(kTile)
+constexpr int kTilePix = kTile * kTile;      // 256 pixels = 256 threads per mask-tile CTA
+constexpr int kMaxTilePix = 256;             // largest render tile (pixel index fits a byte)
 constexpr int kMaxFrames = RTG_MAX_FRAMES;
 // q = t1^2 + t2^2 with t = U d and U scaled by sqrt(log2(e) / 2), so exp(-p/2) = 2^-q
 constexpr float kQScale = 0.84932180028801904272f;   // sqrt(0.5 * log2(e))
@@ -43,6 +48,9 @@ enum Counter {
   kSkip = 6,  // non-zero: pairs overflowed, downstream kernels skip
   kCand = 7,  // (frame, Gaussian) candidates that passed the coarse cull
   kStaged = 8,  // (Gaussian, tile) pairs staged by the projection for the scatter into buckets
+  kItems = 9,   // (tile, 32-pixel group) work items of the persistent schedule
+  kQFwd = 10,   // next item of the persistent forward (past the first one per warp)
+  kQBwd = 11,   // next item of the persistent backward
   kNumCounters = 16
 };
 
@@ -52,7 +60,9 @@ struct DevCam {
   float R[9];  // camera-to-world, row-major
   float t[3];
   float lim_x, lim_y;  // guard band on |X/Z| and |Y/Z|
-  int tiles_x, tiles_y;
+  int tiles_x, tiles_y;    // render tiles of 2^tws x 2^ths pixels
+  int tws, ths;
+  int mtiles_x, mtiles_y;  // 16 x 16 tiles of the unstable-mask rule
 };
 
 struct Prm {
@@ -93,13 +103,15 @@ struct Work {
   unsigned long long *keys;
   unsigned long long *keys_alt;
   uint4 *stage;         // [pairs] (global tile, slot in its bucket, key lo, key hi)
+  uint8_t *px_list;     // [F*T << (tws + ths)] masked pixels of each render tile
+  uint32_t *items;      // [groups] work items of the persistent schedule
   uint32_t *sorted;
   float *px_T;
   uint32_t *px_last;
   int32_t *px_hit;
   float *grad2d;
   float *loss_part;     // [kLossBlocks * 4]
-  float *tile_loss;     // [F*T*8*4] per-(tile, warp) fused L1 partials (colour sum, depth sum, depth count)
+  float *tile_loss;     // [groups][4] per-(tile, 32-pixel group) fused L1 partials (colour, depth, depth count)
   float *loss_scal;     // [4]: L, Lc, Ld, (unused); [4..5] gradient scales
   uint32_t *loss_done;
   uint32_t *status;     // host-mapped status word (device pointer)

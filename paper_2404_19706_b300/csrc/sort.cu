@@ -1,12 +1,15 @@
 // Per-tile depth ordering: the second level of a most-significant-digit radix sort on
 // the packed key (tile, IEEE bits of z_c, Gaussian index).  The tile digit was
 // resolved by bucketing (k_emit); here one CTA per tile sorts its bucket by the
-// remaining 64 bits with a stable least-significant-digit radix sort (8-bit digits),
-// skipping digit positions on which all keys of the bucket agree.  Buckets of up to
-// kSortCap keys stay in shared memory for every pass; longer buckets stream through
-// global memory in chunks, keeping running digit offsets so every pass stays stable.
-// The output is the list of Gaussian indices per tile in front-to-back order (the
-// "key that combines view space depth and tile ID", Supplement B).
+// remaining 64 bits with a stable least-significant-digit radix sort (digits of
+// kBits = 4 or 8 bits), skipping digit positions on which all keys of the bucket agree.
+// Buckets of up to kSortCap keys stay in shared memory for every pass; longer buckets
+// stream through global memory in chunks, keeping running digit offsets so every pass
+// stays stable.  A Gaussian enters a tile at most once, so the keys of a bucket are
+// distinct, and buckets up to a tuned length are ordered by ranking instead: each key's
+// position is the number of smaller keys.  The output is the list of Gaussian indices per
+// tile in front-to-back order (the "key that combines view space depth and tile ID",
+// Supplement B).
 #include "kernels.cuh"
 
 namespace rtg {
@@ -17,7 +20,7 @@ struct SortSmem {
   unsigned long long a[kSortCap];
   unsigned long long b[kSortCap];
   uint16_t lrank[kSortCap];
-  uint32_t cnt[kSortWarps * 256];
+  uint32_t cnt[kSortWarps * 256];  // [warp][digit], 2^kBits digits used
   uint32_t tot[256];
   uint32_t base[256];
   uint32_t run[256];
@@ -56,23 +59,26 @@ __device__ void varying_bits(const unsigned long long *src, uint32_t n, SortSmem
   __syncthreads();
 }
 
-// Stable ranking of m <= kSortCap shared-memory keys by the 8-bit digit at `shift`:
+// Stable ranking of m <= kSortCap shared-memory keys by the kBits-bit digit at `shift`:
 // warp w owns a contiguous chunk; within it, lanes with equal digits are grouped with
 // match.any and ranked by lane order, chunk by chunk.  Afterwards
 //   lrank[j]     rank of key j among equal digits of its warp chunk,
 //   cnt[w][d]    number of digit-d keys in the chunks of warps before w,
 //   tot[d]       number of digit-d keys.
+template <int kBits>
 __device__ void rank_digits(const unsigned long long *src, int m, int shift, SortSmem &s) {
+  constexpr int kRadix = 1 << kBits;
+  constexpr unsigned long long kMask = (unsigned long long)(kRadix - 1);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int k = threadIdx.x; k < kSortWarps * 256; k += kSortThreads) s.cnt[k] = 0u;
+  for (int k = threadIdx.x; k < kSortWarps * kRadix; k += kSortThreads) s.cnt[k] = 0u;
   __syncthreads();
   const int per = (((m + kSortWarps - 1) / kSortWarps) + 31) & ~31;
   const int beg = wid * per, end = min(m, beg + per);
-  uint32_t *mycnt = s.cnt + wid * 256;
+  uint32_t *mycnt = s.cnt + wid * kRadix;
   for (int b = beg; b < end; b += 32) {
     const int j = b + lane;
     const bool valid = j < end;
-    const unsigned digit = valid ? (unsigned)((src[j] >> shift) & 0xffull) : 256u + lane;
+    const unsigned digit = valid ? (unsigned)((src[j] >> shift) & kMask) : 256u + lane;
     const unsigned peers = __match_any_sync(0xffffffffu, digit);
     const int leader = __ffs(peers) - 1;
     uint32_t before = 0;
@@ -84,12 +90,12 @@ __device__ void rank_digits(const unsigned long long *src, int m, int shift, Sor
     if (valid) s.lrank[j] = (uint16_t)(before + __popc(peers & lanemask_lt()));
   }
   __syncthreads();
-  {
-    const int d = threadIdx.x;  // kSortThreads == 256 digits
+  if (threadIdx.x < kRadix) {
+    const int d = threadIdx.x;
     uint32_t run = 0;
     for (int k = 0; k < kSortWarps; ++k) {
-      const uint32_t c = s.cnt[k * 256 + d];
-      s.cnt[k * 256 + d] = run;
+      const uint32_t c = s.cnt[k * kRadix + d];
+      s.cnt[k * kRadix + d] = run;
       run += c;
     }
     s.tot[d] = run;
@@ -97,10 +103,11 @@ __device__ void rank_digits(const unsigned long long *src, int m, int shift, Sor
   __syncthreads();
 }
 
-// Exclusive scan of 256 values by 256 threads (value of thread d is in[d]).
-__device__ void scan256(const uint32_t *in, uint32_t *out, SortSmem &s) {
+// Exclusive scan of kRadix <= 256 values by 256 threads (value of thread d is in[d]).
+template <int kRadix>
+__device__ void scan_digits(const uint32_t *in, uint32_t *out, SortSmem &s) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const uint32_t v = in[threadIdx.x];
+  const uint32_t v = (int)threadIdx.x < kRadix ? in[threadIdx.x] : 0u;
   uint32_t inc = v;
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
@@ -111,26 +118,31 @@ __device__ void scan256(const uint32_t *in, uint32_t *out, SortSmem &s) {
   __syncthreads();
   uint32_t pre = 0;
   for (int k = 0; k < wid; ++k) pre += s_w[k];
-  out[threadIdx.x] = pre + inc - v;
+  if ((int)threadIdx.x < kRadix) out[threadIdx.x] = pre + inc - v;
   __syncthreads();
 }
 
+template <int kBits>
 __device__ __forceinline__ void scatter_chunk(const unsigned long long *src, int m, int shift, const uint32_t *base,
                                               unsigned long long *dst, SortSmem &s) {
+  constexpr int kRadix = 1 << kBits;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int per = (((m + kSortWarps - 1) / kSortWarps) + 31) & ~31;
   const int beg = wid * per, end = min(m, beg + per);
   for (int j = beg + lane; j < end; j += 32) {
     const unsigned long long k = src[j];
-    const unsigned d = (unsigned)((k >> shift) & 0xffull);
-    dst[base[d] + s.cnt[wid * 256 + d] + s.lrank[j]] = k;
+    const unsigned d = (unsigned)((k >> shift) & (unsigned long long)(kRadix - 1));
+    dst[base[d] + s.cnt[wid * kRadix + d] + s.lrank[j]] = k;
   }
 }
 
 }  // namespace
 
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_tiles(Work w) {
+template <int kBits>
+__global__ void __launch_bounds__(kSortThreads) k_sort_tiles(Work w, int rank_max) {
+  constexpr int kRadix = 1 << kBits;
+  constexpr unsigned long long kMask = (unsigned long long)(kRadix - 1);
   if (w.counters[kSkip] != 0ull) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SortSmem &s = *reinterpret_cast<SortSmem *>(smem_raw);
@@ -138,17 +150,28 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(Work w) {
   const uint32_t off = w.tile_offset[tile];
   const uint32_t n = w.tile_offset[tile + 1] - off;
   if (n == 0) return;
+  if (n <= (uint32_t)rank_max) {  // distinct keys: position = number of smaller keys
+    for (uint32_t j = threadIdx.x; j < n; j += kSortThreads) s.a[j] = w.keys[off + j];
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < n; j += kSortThreads) {
+      const unsigned long long k = s.a[j];
+      uint32_t pos = 0;
+      for (uint32_t i = 0; i < n; ++i) pos += s.a[i] < k ? 1u : 0u;
+      w.sorted[off + pos] = (uint32_t)k;
+    }
+    return;
+  }
   if (n <= (uint32_t)kSortCap) {
     for (uint32_t j = threadIdx.x; j < n; j += kSortThreads) s.a[j] = w.keys[off + j];
     __syncthreads();
     unsigned long long vary;
     varying_bits(s.a, n, s, vary);
     unsigned long long *cur = s.a, *oth = s.b;
-    for (int shift = 0; shift < 64; shift += 8) {
-      if (((vary >> shift) & 0xffull) == 0ull) continue;
-      rank_digits(cur, (int)n, shift, s);
-      scan256(s.tot, s.base, s);
-      scatter_chunk(cur, (int)n, shift, s.base, oth, s);
+    for (int shift = 0; shift < 64; shift += kBits) {
+      if (((vary >> shift) & kMask) == 0ull) continue;
+      rank_digits<kBits>(cur, (int)n, shift, s);
+      scan_digits<kRadix>(s.tot, s.base, s);
+      scatter_chunk<kBits>(cur, (int)n, shift, s.base, oth, s);
       __syncthreads();
       unsigned long long *t = cur;
       cur = oth;
@@ -161,22 +184,21 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(Work w) {
   unsigned long long *src = w.keys + off, *dst = w.keys_alt + off;
   unsigned long long vary;
   varying_bits(src, n, s, vary);
-  for (int shift = 0; shift < 64; shift += 8) {
-    if (((vary >> shift) & 0xffull) == 0ull) continue;
-    s.tot[threadIdx.x] = 0u;
+  for (int shift = 0; shift < 64; shift += kBits) {
+    if (((vary >> shift) & kMask) == 0ull) continue;
+    if ((int)threadIdx.x < kRadix) s.tot[threadIdx.x] = 0u;
     __syncthreads();
-    for (uint32_t j = threadIdx.x; j < n; j += kSortThreads)
-      atomicAdd(&s.tot[(unsigned)((src[j] >> shift) & 0xffull)], 1u);
+    for (uint32_t j = threadIdx.x; j < n; j += kSortThreads) atomicAdd(&s.tot[(unsigned)((src[j] >> shift) & kMask)], 1u);
     __syncthreads();
-    scan256(s.tot, s.run, s);
+    scan_digits<kRadix>(s.tot, s.run, s);
     for (uint32_t c0 = 0; c0 < n; c0 += kSortCap) {
       const int m = (int)min((uint32_t)kSortCap, n - c0);
       for (int j = threadIdx.x; j < m; j += kSortThreads) s.a[j] = src[c0 + j];
       __syncthreads();
-      rank_digits(s.a, m, shift, s);
-      scatter_chunk(s.a, m, shift, s.run, dst, s);
+      rank_digits<kBits>(s.a, m, shift, s);
+      scatter_chunk<kBits>(s.a, m, shift, s.run, dst, s);
       __syncthreads();
-      s.run[threadIdx.x] += s.tot[threadIdx.x];
+      if ((int)threadIdx.x < kRadix) s.run[threadIdx.x] += s.tot[threadIdx.x];
       __syncthreads();
     }
     unsigned long long *t = src;
@@ -188,11 +210,15 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(Work w) {
 }
 
 void init_sort_attributes() {
-  cudaFuncSetAttribute(k_sort_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SortSmem));
+  cudaFuncSetAttribute(k_sort_tiles<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SortSmem));
+  cudaFuncSetAttribute(k_sort_tiles<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SortSmem));
 }
 
-void launch_sort_tiles(const Work &w, int FT, cudaStream_t s) {
-  k_sort_tiles<<<FT, kSortThreads, sizeof(SortSmem), s>>>(w);
+void launch_sort_tiles(const Work &w, int FT, int bits, int rank_max, cudaStream_t s) {
+  if (bits == 4)
+    k_sort_tiles<4><<<FT, kSortThreads, sizeof(SortSmem), s>>>(w, rank_max);
+  else
+    k_sort_tiles<8><<<FT, kSortThreads, sizeof(SortSmem), s>>>(w, rank_max);
 }
 
 }  // namespace rtg

@@ -4,6 +4,9 @@ argument checks work without a GPU."""
 import ctypes
 import os
 import re
+import shutil
+import subprocess
+import tempfile
 
 import pytest
 
@@ -63,7 +66,8 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(_lib.rtg_render_params) == 9 * 4
     assert ctypes.sizeof(_lib.rtg_gaussians) == 8 + 8 + 13 * 8 + 8
     assert ctypes.sizeof(_lib.rtg_capacity) == 8 + 4 * 4 + 8
-    assert ctypes.sizeof(_lib.rtg_stats) == 5 * 8 + 2 * 4
+    assert ctypes.sizeof(_lib.rtg_stats) == 5 * 8 + 4 * 4
+    assert ctypes.sizeof(_lib.rtg_tuning) == 7 * 4
 
 
 @pytest.mark.gpu
@@ -73,3 +77,28 @@ def test_create_destroy_roundtrip():
     assert ctx.workspace_bytes() > 0
     assert rtg.get_status(ctx) == 0
     ctx.close()
+
+
+def test_struct_layouts_match_compiled_header():
+    """sizeof / offsetof of every ABI struct as gcc lays out include/rtg.h equal the ctypes
+    binding's (a field added to one side only fails here)."""
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    structs = [(n, getattr(_lib, n)) for n in ("rtg_camera", "rtg_render_params", "rtg_gaussians", "rtg_capacity",
+                                                 "rtg_stats", "rtg_tuning", "rtg_adam_params")]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rtg.h"', "int main(void) {"]
+    for name, cls in structs:
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{name}.{fname} %zu\\n", offsetof({name}, {fname}));')
+    lines += ["  return 0;", "}"]
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        open(src, "w").write("\n".join(lines) + "\n")
+        subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = dict(line.split() for line in out if line.strip())
+    for name, cls in structs:
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert int(got[f"{name}.{fname}"]) == getattr(cls, fname).offset, f"{name}.{fname}"

@@ -11,14 +11,14 @@ from gpu_util import gpu_forward, rtg
 pytestmark = pytest.mark.gpu
 
 
-def cpu_rebuild(rect, zbits, n, F, W, H, masks):
-    tx, ty = (W + 15) // 16, (H + 15) // 16
+def cpu_rebuild(rect, zbits, n, F, W, H, masks, tw=16, th=16):
+    tx, ty = (W + tw - 1) // tw, (H + th - 1) // th
     T = tx * ty
     active = np.ones((F, T), dtype=bool)
     if masks is not None:
-        m = np.zeros((F, ty * 16, tx * 16), dtype=bool)
+        m = np.zeros((F, ty * th, tx * tw), dtype=bool)
         m[:, :H, :W] = masks.reshape(F, H, W).astype(bool)
-        active = m.reshape(F, ty, 16, tx, 16).any(axis=(2, 4)).reshape(F, T)
+        active = m.reshape(F, ty, th, tx, tw).any(axis=(2, 4)).reshape(F, T)
     tiles, keys, ids = [], [], []
     for f in range(F):
         for i in range(n):
@@ -39,12 +39,18 @@ def cpu_rebuild(rect, zbits, n, F, W, H, masks):
     return offsets, ids[order].astype(np.uint32)
 
 
-def check(scene, cams, masks=None):
+def check(scene, cams, masks=None, tuning=None):
     cams = cams if isinstance(cams, list) else [cams]
     F, H, W = len(cams), cams[0].height, cams[0].width
-    got = gpu_forward(scene, cams, mask=masks)
+    ctx = None
+    if tuning is not None:
+        from gpu_util import ctx_for
+        ctx = ctx_for(scene.n, cams)
+        ctx.set_tuning(tuning)
+    got = gpu_forward(scene, cams, mask=masks, ctx=ctx)
     d = rtg().debug_binning(got["ctx"], F, W, H, scene.n)
-    offs, ids = cpu_rebuild(d["rect"], d["zbits"], scene.n, F, W, H, masks)
+    tw, th = got["stats"]["tile_w"], got["stats"]["tile_h"]
+    offs, ids = cpu_rebuild(d["rect"], d["zbits"], scene.n, F, W, H, masks, tw, th)
     np.testing.assert_array_equal(d["tile_offsets"], offs)
     np.testing.assert_array_equal(d["sorted_ids"], ids)
     assert d["pairs"] == len(ids) > 0
@@ -81,3 +87,23 @@ def test_binning_long_bucket_uses_global_sort_path():
     assert got["stats"]["max_tile_pairs"] > 2048
     zb = d["zbits"][d["sorted_ids"]]
     assert (np.diff(zb.astype(np.int64)) == 0).any()  # ties present
+
+
+@pytest.mark.parametrize("tile", [(8, 8), (8, 16), (16, 8), (32, 8)])
+def test_binning_bit_exact_every_render_tile(tile):
+    """Every render tile shape bins bit-exactly, and its tile rectangles are the 8 x 8
+    rectangles coarsened (the pixel rectangle behind them does not depend on the tile)."""
+    m = rtg()
+    scene, layout = synth.room_scene(2012, 8000)
+    cams = [c for _, c in zip(range(2), synth.room_camera_candidates(2013, layout, 92, 66, 70.0))]
+    masks = synth.random_masks(14, 2, 66, 92, 0.2, 0.6)
+    tw, th = tile
+    d, got = check(scene, cams, masks, m.Tuning(tw, th, schedule=1, sort_rank_max=512))
+    assert (got["stats"]["tile_w"], got["stats"]["tile_h"]) == tile
+    d8, _ = check(scene, cams, masks, m.Tuning(8, 8))
+    # which Gaussians reach a masked tile depends on the tile, the rectangle itself does not
+    both = (d8["rect"][:, 0] >= 0) & (d["rect"][:, 0] >= 0)
+    assert both.sum() > 100
+    ratio = np.array([tw // 8, th // 8, tw // 8, th // 8])
+    np.testing.assert_array_equal(d8["rect"][both] // ratio, d["rect"][both])
+    np.testing.assert_array_equal(d["zbits"][both], d8["zbits"][both])
