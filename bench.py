@@ -472,14 +472,18 @@ def run_ours(args):
 class PerFrameStep:
     """The masked iteration over F keyframes as F single-frame calls: for each frame the
     fused mask + forward + L1 and its backward (gradients accumulated over the frames),
-    then one Adam step and the scatter, exactly what MaskedStep does for all F at once."""
+    then one Adam step and the scatter, exactly what MaskedStep does for all F at once.
+    Frame f runs on its own context ctxs[f], which keeps that frame's optimisation window
+    open, as the batched step's context keeps the window of all F frames."""
 
-    def __init__(self, rtg, ctx1, g, cams, masks, tcol, tdep, settings):
+    def __init__(self, rtg, ctxs, g, cams, masks, tcol, tdep, settings):
         from paper_2404_19706_b300 import api
-        self.api, self.ctx, self.cams, self.settings = api, ctx1, cams, settings
+        self.api, self.ctxs, self.cams, self.settings = api, ctxs, cams, settings
         self.masks, self.tcol, self.tdep = masks, tcol, tdep
-        self.inner = rtg.MaskedStep(ctx1, g, [cams[0]], masks[0:1], tcol[0:1], tdep[0:1], settings,
+        self.inner = rtg.MaskedStep(ctxs[0], g, [cams[0]], masks[0:1], tcol[0:1], tdep[0:1], settings,
                                     recompute_mask=True)
+        for f in range(1, len(cams)):
+            api.window_begin(ctxs[f], [cams[f]], self.inner.g, settings)
         self.g, self.u, self.m, self.v, self.step_counter = (self.inner.g, self.inner.u, self.inner.m,
                                                              self.inner.v, self.inner.step_counter)
         F, Cc, H, W = tcol.shape
@@ -493,10 +497,10 @@ class PerFrameStep:
     def _body(self, stream=None):
         api, s = self.api, self.inner
         for f, cam in enumerate(self.cams):
-            api.render_forward_masked(self.ctx, [cam], s.g, self.settings, self.masks[f:f + 1], self.color,
+            api.render_forward_masked(self.ctxs[f], [cam], s.g, self.settings, self.masks[f:f + 1], self.color,
                                       self.depth, self.alpha, self.tcol[f:f + 1], self.tdep[f:f + 1], 1.0, 1.0,
                                       self.loss[f], None, stream)
-            api.render_backward_l1(self.ctx, *s.grads, accumulate=f > 0, stream=stream)
+            api.render_backward_l1(self.ctxs[f], *s.grads, accumulate=f > 0, stream=stream)
         api.adam_step_counted(s.u, s.grads, s.m, s.v, s.step_counter, s.adam, stream)
         api.scatter_unstable(s.ids, s.u, s.g, stream)
         return self.loss
@@ -602,20 +606,24 @@ def run_keyframes(args):
 
     tuned_b = run_tuner(ctx, batched._body, check_b, step_state(batched), args, "batched")
 
-    # per frame: the same iteration as F single-frame call sequences
-    ctx1 = rtg.Context(max_gaussians=scene.n, max_frames=1, max_width=W, max_height=H, max_pairs=kw["max_pairs"])
+    # per frame: the same iteration as F single-frame call sequences, one context per frame
+    ctxs = [rtg.Context(max_gaussians=scene.n, max_frames=1, max_width=W, max_height=H,
+                        max_pairs=kw["max_pairs"] // 4) for _ in range(F)]
+    ctx1 = ctxs[0]
     masks_p = torch.zeros(F, H, W, dtype=torch.uint8, device=dev)
     gp = rtg.Gaussians.from_scene(scene, device=dev)
-    perframe = PerFrameStep(rtg, ctx1, gp, kcams, masks_p, tcol, tdep, settings)
+    perframe = PerFrameStep(rtg, ctxs, gp, kcams, masks_p, tcol, tdep, settings)
     ckp = dict(mask=torch.zeros(1, H, W, dtype=torch.uint8, device=dev), color=torch.zeros(1, C, H, W, device=dev),
                depth=torch.zeros(1, H, W, device=dev), alpha=torch.zeros(1, H, W, device=dev))
 
     def check_p():
+        for t in ckp.values():
+            t.zero_()
         rtg.render_forward_masked(ctx1, [kcams[0]], perframe.g, settings, ckp["mask"], ckp["color"], ckp["depth"],
                                   ckp["alpha"])
         return [ckp["mask"], ckp["color"], ckp["depth"], ckp["alpha"]]
 
-    tuned_p = run_tuner(ctx1, perframe._body, check_p, step_state(perframe), args, "per_frame")
+    tuned_p = run_tuner(ctxs, perframe._body, check_p, step_state(perframe), args, "per_frame")
 
     # before any optimiser step the two arms render the same thing: the batched call gives
     # every frame bit for bit what a call with that frame alone gives (masks and images)
@@ -623,24 +631,25 @@ def run_keyframes(args):
     for f in range(F):
         for t in ckp.values():  # outputs are written on masked pixels only
             t.zero_()
-        rtg.render_forward_masked(ctx1, [kcams[f]], perframe.g, settings, ckp["mask"], ckp["color"], ckp["depth"],
-                                  ckp["alpha"])
+        rtg.render_forward_masked(ctxs[f], [kcams[f]], perframe.g, settings, ckp["mask"], ckp["color"],
+                                  ckp["depth"], ckp["alpha"])
         for k in ("mask", "color", "depth", "alpha"):
             assert torch.equal(ckp[k][0], ckb[k][f]), f"frame {f}: batched and per-frame {k} differ"
     torch.cuda.synchronize()
 
     results = {}
-    for name, st, c in (("batched", batched, ctx), ("per_frame", perframe, ctx1)):
+    for name, st, cs in (("batched", batched, [ctx]), ("per_frame", perframe, ctxs)):
         for _ in range(args.warmup):
             st.step()
         torch.cuda.synchronize()
-        assert rtg.get_status(c) == 0, name
+        assert all(rtg.get_status(c) == 0 for c in cs), name
+        assert all(rtg.window_is_open(c) for c in cs), f"{name}: a window closed"
         st.capture()
         st.step()
         torch.cuda.synchronize()
         ms, wall, clocks = timed_replays(st, args.steps, flush, stream, local)
-        assert rtg.get_status(c) == 0, name
-        results[name] = dict(ms=ms, wall=wall, clocks=clocks, stats=rtg.get_stats(c))
+        assert all(rtg.get_status(c) == 0 for c in cs), name
+        results[name] = dict(ms=ms, wall=wall, clocks=clocks, stats=rtg.get_stats(cs[0]))
 
     per_launch = kernel_profile(rtg, ctx, batched, args.steps, flush, stream)
     sb = results["batched"]["stats"]

@@ -225,6 +225,22 @@ rtg_status rtg_render_forward_masked(rtg_ctx *ctx, const rtg_camera *cams, int32
                                      const float *target_depth, float w_color, float w_depth, float *color,
                                      float *depth, float *alpha, int32_t *index_map, float *loss_out, void *stream);
 
+/* Optimisation window (Section 3.2): within a window only the unstable Gaussians are
+ * optimised; the stable ones keep their parameters.  rtg_window_begin projects every stable
+ * Gaussian into the window's F cameras once and keeps those records in the workspace.  A
+ * later forward (any of the three rtg_render_forward* calls) whose cameras, render
+ * parameters, Gaussian arrays (the same pointers) and precomputed unstable index
+ * (rank_map, unstable_ids, n_unstable; required here) are those of rtg_window_begin then
+ * projects only the unstable Gaussians and reuses the stable records: its results are
+ * identical to a forward without the window.  The caller promises that the stable
+ * Gaussians' parameters and the unstable flags do not change while the window is open.
+ * Any forward that does not match closes the window (it rewrites the records), as does
+ * rtg_window_end; rtg_window_is_open reports the state (1 open, 0 closed). */
+rtg_status rtg_window_begin(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, const rtg_gaussians *g,
+                            const rtg_render_params *prm, void *stream);
+rtg_status rtg_window_end(rtg_ctx *ctx);
+int32_t rtg_window_is_open(rtg_ctx *ctx);
+
 /* Adam (Kingma & Ba, Algorithm 1) on compact unstable parameters, in place, with the
  * per-group learning rates of Supplement C.  The scale is optimised in log space
  * (s <- s * exp(-step), gradient s * dL/ds).  m and v hold nu * (11 + C) float32 each,

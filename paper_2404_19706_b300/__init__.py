@@ -37,6 +37,9 @@ from .api import (  # noqa: E402,F401
     unstable_index,
     unstable_rank,
     unstable_mask,
+    window_begin,
+    window_end,
+    window_is_open,
     workspace_size,
 )
 from .optim import MaskedStep, RasterState, RTGRasterize, rasterize  # noqa: E402,F401

@@ -83,6 +83,10 @@ SIGNATURES = [
     ("rtg_render_backward_l1", c_int32, [c_void_p] + [c_void_p] * 5 + [c_int32, c_void_p]),
     ("rtg_render_backward", c_int32, [c_void_p] + [c_void_p] * 7 + [c_int32, c_void_p]),
     ("rtg_set_tuning", c_int32, [c_void_p, POINTER(rtg_tuning)]),
+    ("rtg_window_begin", c_int32, [c_void_p, POINTER(rtg_camera), c_int32, POINTER(rtg_gaussians),
+                                   POINTER(rtg_render_params), c_void_p]),
+    ("rtg_window_end", c_int32, [c_void_p]),
+    ("rtg_window_is_open", c_int32, [c_void_p]),
     ("rtg_get_tuning", c_int32, [c_void_p, POINTER(rtg_tuning)]),
     ("rtg_adam_step", c_int32, [c_int64, c_int32] + [c_void_p] * 12 + [c_int32, POINTER(rtg_adam_params),
                                                                        c_void_p]),

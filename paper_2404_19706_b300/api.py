@@ -244,6 +244,26 @@ def workspace_size(max_gaussians, max_frames=1, max_width=640, max_height=480, m
 
 # ----------------------------------------------------------------------------- entry points
 
+def window_begin(ctx: Context, cams, g: Gaussians, settings: RenderSettings, stream=None):
+    """Open an optimisation window: project the stable Gaussians into ``cams`` once; later
+    forwards with the same cameras, settings, arrays and unstable index reuse them."""
+    if g.rank_map is None:
+        raise ValueError("window_begin needs a Gaussians with the precomputed unstable index (rank_map)")
+    arr, F = _cams(cams)
+    gc = g.to_c()
+    prm = settings.to_c()
+    st = _lib.load().rtg_window_begin(ctx.ptr, arr, F, ctypes.byref(gc), ctypes.byref(prm), _stream(stream))
+    _check(st, "rtg_window_begin", ctx.ptr)
+
+
+def window_end(ctx: Context):
+    _check(_lib.load().rtg_window_end(ctx.ptr), "rtg_window_end", ctx.ptr)
+
+
+def window_is_open(ctx: Context) -> bool:
+    return bool(_lib.load().rtg_window_is_open(ctx.ptr))
+
+
 def unstable_mask(ctx: Context, cams, g: Gaussians, settings: RenderSettings, mask: torch.Tensor, stream=None):
     arr, F = _cams(cams)
     gc = g.to_c()

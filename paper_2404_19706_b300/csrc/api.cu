@@ -10,6 +10,15 @@
 
 using namespace rtg;
 
+// Open optimisation window: the call that projected the stable Gaussians (rtg_window_begin)
+struct Window {
+  bool open;
+  int F;
+  rtg_camera cams[RTG_MAX_FRAMES];
+  rtg_render_params prm;
+  rtg_gaussians g;
+};
+
 struct rtg_ctx {
   rtg_capacity cap;
   int device;
@@ -30,6 +39,7 @@ struct rtg_ctx {
   Tuning tune;      // launch configuration of the next forward
   Tuning tune_fwd;  // ... and of the last one, which its backward follows
   bool bwd_done;    // a backward of the last forward has run (its 2D gradient rows are used)
+  Window win;
   // tracing: (start, end) event pairs of the kernels launched while profiling is on
   bool prof;
   struct ProfRec *recs;
@@ -107,7 +117,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
   size_t cams, counters, rank, ids, block_cnt, cand, rec_hot, rec_cold, rec_box, ntiles, tile_npix, tile_count, tile_offset,
       tile_cursor, keys, keys_alt, stage, sorted, px_T, px_last, px_hit, grad2d, loss_part, loss_scal, loss_done, tile_loss,
-      px_list, items, total;
+      px_list, items, scand, total;
 };
 
 bool capacity_ok(const rtg_capacity *c) {
@@ -164,6 +174,7 @@ Layout layout_of(const rtg_capacity *c) {
   L.tile_loss = take(groups * 4 * 4);
   L.px_list = take(padded);
   L.items = take(groups * 4);
+  L.scand = take(Fm * N * 4);
   L.total = o;
   return L;
 }
@@ -203,6 +214,22 @@ int log2_exact(int v) {
   for (int k = 0; k < 31; ++k)
     if (v == (1 << k)) return k;
   return -1;
+}
+
+// True when a call renders exactly what the open window projected: the same cameras,
+// render parameters, Gaussian arrays and precomputed unstable index.
+bool window_matches(const rtg_ctx *ctx, const rtg_camera *cams, int F, const rtg_gaussians *g,
+                    const rtg_render_params *p) {
+  const Window &w = ctx->win;
+  if (!w.open || F != w.F || g == nullptr || p == nullptr || cams == nullptr) return false;
+  if (memcmp(cams, w.cams, sizeof(rtg_camera) * (size_t)F) != 0) return false;
+  if (memcmp(p, &w.prm, sizeof(rtg_render_params)) != 0) return false;
+  const rtg_gaussians &a = w.g;
+  return g->n == a.n && g->channels == a.channels && g->means == a.means && g->scales == a.scales &&
+         g->quats == a.quats && g->opacity == a.opacity && g->colors == a.colors && g->unstable == a.unstable &&
+         g->u_means == a.u_means && g->u_scales == a.u_scales && g->u_quats == a.u_quats &&
+         g->u_opacity == a.u_opacity && g->u_colors == a.u_colors && g->rank_map == a.rank_map &&
+         g->unstable_ids == a.unstable_ids && g->n_unstable == a.n_unstable;
 }
 
 // rtg_tuning -> Tuning, or false if the setting is not one this build implements
@@ -355,6 +382,7 @@ rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap) {
   w.tile_loss = (float *)(b + L.tile_loss);
   w.px_list = (uint8_t *)(b + L.px_list);
   w.items = (uint32_t *)(b + L.items);
+  w.scand = (uint32_t *)(b + L.scand);
   w.status = status_dev;
   {
     int sms = 148;
@@ -368,6 +396,7 @@ rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap) {
   }
   // zero the small bookkeeping region once (counters, loss ticket)
   cudaMemset(ctx->slab + L.counters, 0, kNumCounters * sizeof(unsigned long long));
+  ctx->win.open = false;
   cudaMemset(ctx->slab + L.loss_done, 0, 4);
   init_sort_attributes();
   if (cudaDeviceSynchronize() != cudaSuccess) {
@@ -492,6 +521,11 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
   const bool same_grid = tn.tws == kTileShift && tn.ths == kTileShift;
   const int64_t n = gp.n;
   const long long nu_preset = gp.rank_map ? (long long)gp.n_unstable : -1ll;
+  // with a matching open window only the unstable Gaussians are projected; any other
+  // forward rewrites the records the window keeps, so it closes the window
+  const bool win = window_matches(ctx, cams, F, g, prm);
+  if (!win) ctx->win.open = false;
+  const int cull = win ? kCullUnstable : kCullAll;
   Work w = ctx->w;
   if (gp.rank_map != nullptr) {
     w.rank = const_cast<int32_t *>(gp.rank_map);
@@ -508,7 +542,7 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
       if ((st = rank_pass(ctx, gp.unstable, n, w.rank, w.ids, w.counters, nullptr, s)) != RTG_OK) return st;
     {
       ProfScope ps(ctx, kPProject, s);
-      launch_project(gp, w, P, F, TM, kProjFused, ctx->cap.max_pairs, s);
+      launch_project(gp, w, P, F, TM, kProjFused, cull, ctx->cap.max_pairs, s);
     }
     {
       ProfScope ps(ctx, kPUnstableMask, s);  // coverage pass: scan, scatter, cover + tile rule
@@ -520,7 +554,7 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
     }
     {
       ProfScope ps(ctx, kPBin, s);
-      launch_bin(w, n, T, ctx->cap.max_pairs, s);
+      launch_bin(w, n, T, ctx->cap.max_pairs, true, win, s);
     }
     mask = mask_out;
   } else {
@@ -530,8 +564,14 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
     }
     if (gp.rank_map == nullptr)
       if ((st = rank_pass(ctx, gp.unstable, n, w.rank, w.ids, w.counters, nullptr, s)) != RTG_OK) return st;
-    ProfScope ps(ctx, kPProject, s);
-    launch_project(gp, w, P, F, T, kProjForward, ctx->cap.max_pairs, s);
+    {
+      ProfScope ps(ctx, kPProject, s);
+      launch_project(gp, w, P, F, T, kProjForward, cull, ctx->cap.max_pairs, s);
+    }
+    if (win) {
+      ProfScope ps(ctx, kPBin, s);
+      launch_bin(w, n, T, ctx->cap.max_pairs, false, true, s);
+    }
   }
   {
     ProfScope ps(ctx, kPScanTiles, s);
@@ -584,6 +624,50 @@ static rtg_status prepare_backward(rtg_ctx *ctx, cudaStream_t s) {
 }
 
 extern "C" {
+
+rtg_status rtg_window_begin(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, const rtg_gaussians *g,
+                            const rtg_render_params *prm, void *stream) {
+  if (ctx == nullptr) return RTG_ERR_ARG;
+  ctx->win.open = false;
+  Prm P;
+  rtg_status st = make_prm(ctx, prm, P);
+  if (st != RTG_OK) return st;
+  FrameSet fs;
+  if ((st = make_frames(ctx, cams, F, prm, fs)) != RTG_OK) return st;
+  GaussPtrs gp;
+  if ((st = make_gauss(ctx, g, gp)) != RTG_OK) return st;
+  if (gp.rank_map == nullptr) return fail(ctx, RTG_ERR_ARG, "window_begin needs the precomputed unstable index");
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->has_fwd = false;  // the window pass reuses the forward's workspace
+  Work w = ctx->w;
+  w.rank = const_cast<int32_t *>(gp.rank_map);
+  w.ids = const_cast<int32_t *>(gp.unstable_ids);
+  const DevCam &c0 = fs.cam[0];
+  {
+    ProfScope ps(ctx, kPProject, s);
+    launch_tile_mask(fs, w, nullptr, c0.mtiles_x * c0.mtiles_y, c0.mtiles_x, kTileShift, kTileShift, true, false,
+                     (long long)gp.n_unstable, s);
+    launch_window_reset(w, s);
+    launch_project(gp, w, P, F, c0.mtiles_x * c0.mtiles_y, kProjWindow, kCullStable, ctx->cap.max_pairs, s);
+  }
+  if ((st = check_launch(ctx, "window_begin")) != RTG_OK) return st;
+  Window &win = ctx->win;
+  win.F = F;
+  memcpy(win.cams, cams, sizeof(rtg_camera) * (size_t)F);
+  win.prm = *prm;
+  win.g = *g;
+  win.open = true;
+  ctx->last_stream = s;
+  return RTG_OK;
+}
+
+rtg_status rtg_window_end(rtg_ctx *ctx) {
+  if (ctx == nullptr) return RTG_ERR_ARG;
+  ctx->win.open = false;
+  return RTG_OK;
+}
+
+int32_t rtg_window_is_open(rtg_ctx *ctx) { return (ctx != nullptr && ctx->win.open) ? 1 : 0; }
 
 rtg_status rtg_render_forward(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, const rtg_gaussians *g,
                               const uint8_t *mask, const rtg_render_params *prm, float *color, float *depth,
@@ -791,7 +875,7 @@ rtg_status rtg_unstable_mask(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, co
                    gp.rank_map ? (long long)gp.n_unstable : -1ll, s);
   if (gp.u_means != nullptr && gp.rank_map == nullptr)
     if ((st = rank_pass(ctx, gp.unstable, gp.n, w.rank, w.ids, w.counters, nullptr, s)) != RTG_OK) return st;
-  launch_project(gp, w, P, F, T, kProjMask, ctx->cap.max_pairs, s);
+  launch_project(gp, w, P, F, T, kProjMask, kCullUnstable, ctx->cap.max_pairs, s);
   launch_scan_tiles(w, F * T, ctx->cap.max_pairs, -1, s);
   launch_emit(w, s);
   launch_mask_cover_tiles(w, P, gp.n, F, T, gp.C, mask, kCoverPlain, s);

@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(kMaxTilePix) k_tile_mask(FrameSet fs, Work w, 
   const DevCam &cam = fs.cam[f];
   if (setup && blockIdx.x == 0) {
     for (int i = threadIdx.x; i < fs.F; i += blockDim.x) w.cams[i] = fs.cam[i];
-    if (threadIdx.x < kNumCounters)
+    if (threadIdx.x < kNumReset)
       w.counters[threadIdx.x] = (threadIdx.x == kNumUnstable && nu_preset >= 0) ? (unsigned long long)nu_preset : 0ull;
   }
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -128,10 +128,10 @@ __global__ void __launch_bounds__(kRankThreads) k_rank_write(const uint8_t *__re
 // keeps, clears the tile count of the pairs it drops, and appends the rest to a dense
 // candidate list (one atomic per warp).  k_project then runs the exact double-float
 // projection over that list only, so its warps stay full.
-// With `ids` (unstable-mask pass only) the threads walk that list of unstable Gaussians
-// instead of all N; pairs of other Gaussians keep stale tile counts, which nothing reads
-// before the next forward projection rewrites them.
-template <bool kMask>
+// kSet selects the Gaussians considered (CullSet: all, unstable, stable).  With `ids` (the
+// precomputed unstable list) the threads walk that list instead of all N; entries of other
+// Gaussians keep their tile counts, which nothing reads before they are rewritten.
+template <int kSet>
 __global__ void __launch_bounds__(256) k_cull(GaussPtrs g, Work w, Prm prm, int F, const int32_t *__restrict__ ids,
                                               int64_t count) {
   __shared__ uint32_t s_w[8];
@@ -143,8 +143,10 @@ __global__ void __launch_bounds__(256) k_cull(GaussPtrs g, Work w, Prm prm, int 
   if (ids != nullptr) {
     live = t < count;
     i = live ? (int64_t)ids[t] : 0;
-  } else if (kMask && live) {
+  } else if (kSet == kCullUnstable && live) {
     live = g.unstable[i] != 0;
+  } else if (kSet == kCullStable && live) {
+    live = g.unstable[i] == 0;
   }
   float p[3] = {0.f, 0.f, 0.f};
   if (live) {
@@ -179,6 +181,8 @@ __global__ void __launch_bounds__(256) k_cull(GaussPtrs g, Work w, Prm prm, int 
 // kMode = kProjFused: first half of rtg_render_forward_masked: every projected candidate
 //   gets its records (its tile count is set later by k_bin, once the mask is known), and
 //   only the unstable ones are binned, into every tile, for the coverage test.
+// kMode = kProjWindow: rtg_window_begin: records only, and every projected candidate is
+//   appended to the window's list (stable Gaussians reach this kernel through the cull).
 // Every pair (candidate, masked tile) is staged as (tile, slot, key): the warp reserves its
 // staging range with one atomic, and each pair's slot in its tile bucket is the value the
 // tile counter returns, so the later scatter into buckets needs no atomics.
@@ -226,10 +230,14 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
         const int tiles_x = kMode == kProjForward ? cam.tiles_x : cam.mtiles_x;
         tx0 = o.x0 >> tws; tx1 = o.x1 >> tws; ty0 = o.y0 >> ths; ty1 = o.y1 >> ths;
         const uint32_t *npix = w.tile_npix + (int64_t)f * T;
-        if (kMode != kProjFused || g.unstable[i] != 0)
+        if (kMode != kProjWindow && (kMode != kProjFused || g.unstable[i] != 0))
           for (int ty = ty0; ty <= ty1; ++ty)
             for (int tx = tx0; tx <= tx1; ++tx) nt += npix[ty * tiles_x + tx] != 0u;
       }
+    }
+    if (kMode == kProjWindow) {  // one atomic per block appends the projected entries
+      const unsigned long long slot = block_reserve(w.counters + kWinStable, ok ? 1u : 0u, s_w, &s_base);
+      if (ok) w.scand[slot] = e;
     }
     // block-level reservation of the staging range (one atomic per block)
     const unsigned long long first = block_reserve(w.counters + kStaged, nt, s_w, &s_base);
@@ -237,7 +245,7 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
       const unsigned long long vbase = block_reserve(w.counters + kVisible, nt > 0 ? 1u : 0u, s_w, &s_base);
       (void)vbase;
     }
-    if (ok && (nt > 0 || kMode == kProjFused)) {
+    if (ok && (nt > 0 || kMode == kProjFused || kMode == kProjWindow)) {
       const DevCam &cam = w.cams[f];
       const int tiles_x = kMode == kProjForward ? cam.tiles_x : cam.mtiles_x;
       const uint32_t *npix = w.tile_npix + (int64_t)f * T;
@@ -271,32 +279,36 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
       cold[0] = make_float4(o.n[0], o.n[1], o.n[2], o.d0);
       cold[1] = make_float4(o.Z, __int_as_float(rk), __uint_as_float((uint32_t)o.x0 | ((uint32_t)o.y0 << 16)),
                             __uint_as_float((uint32_t)o.x1 | ((uint32_t)o.y1 << 16)));
-      if (kMode != kProjMask && rk >= 0) {
+      if (kMode != kProjMask && kMode != kProjWindow && rk >= 0) {
         float4 *g2 = reinterpret_cast<float4 *>(w.grad2d + ((int64_t)f * N + rk) * G2);
 #pragma unroll
         for (int q = 0; q < G2 / 4; ++q) g2[q] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
     // kProjFused: 1 marks "projected" for k_bin, which writes the final masked-tile count
-    if (k < ncand) w.ntiles[e] = (kMode == kProjFused) ? (ok ? 1u : 0u) : nt;
+    if (k < ncand) w.ntiles[e] = (kMode == kProjFused || kMode == kProjWindow) ? (ok ? 1u : 0u) : nt;
   }
 }
 
-// Second half of rtg_render_forward_masked: bins every projected candidate into the tiles
-// that survived the unstable mask (tile_npix now holds each tile's masked-pixel count).
-__global__ void __launch_bounds__(256) k_bin(Work w, int64_t N, int T, int64_t max_pairs) {
+// Bins projected (frame, Gaussian) entries into the render tiles that have masked pixels
+// (tile_npix holds each tile's masked-pixel count): the second half of
+// rtg_render_forward_masked (the cull's candidates that the fused projection marked
+// projected), and, with an open window, the cached stable entries, whose records the window
+// pass wrote.  Index k < ncand walks the candidates, the rest the window's list.
+__global__ void __launch_bounds__(256) k_bin(Work w, int64_t N, int T, int64_t max_pairs, int cands, int stable) {
   __shared__ uint32_t s_w[8];
   __shared__ unsigned long long s_base;
   if (w.counters[kSkip] != 0ull) return;
-  const int64_t ncand = (int64_t)w.counters[kCand];
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < ncand; base += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t ncand = cands ? (int64_t)w.counters[kCand] : 0;
+  const int64_t total = ncand + (stable ? (int64_t)w.counters[kWinStable] : 0);
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < total; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = base + threadIdx.x;
     uint32_t nt = 0, e = 0;
     int f = 0, tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1, tiles_x = 0;
     float4 c1 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (k < ncand) {
-      e = w.cand[k];
-      if (w.ntiles[e] != 0u) {
+    if (k < total) {
+      e = k < ncand ? w.cand[k] : w.scand[k - ncand];
+      if (k >= ncand || w.ntiles[e] != 0u) {
         f = (int)(e / (uint64_t)N);
         const DevCam &cam = w.cams[f];
         tiles_x = cam.tiles_x;
@@ -328,9 +340,11 @@ __global__ void __launch_bounds__(256) k_bin(Work w, int64_t N, int T, int64_t m
           }
         }
     }
-    if (k < ncand) w.ntiles[e] = nt;
+    if (k < total) w.ntiles[e] = nt;
   }
 }
+
+__global__ void k_window_reset(Work w) { w.counters[kWinStable] = 0ull; }
 
 // --------------------------------------------------------------------------- tile scan
 // Cost class of a tile list of n records for the persistent schedule's queue: 0 for an
@@ -466,38 +480,46 @@ void launch_rank(const uint8_t *unstable, int64_t n, int32_t *block_cnt, int32_t
   k_rank_write<<<nb, kRankThreads, 0, s>>>(unstable, n, block_cnt, rank, ids, nu_counter, nu_out);
 }
 
-void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, int T, int mode, int64_t max_pairs,
-                    cudaStream_t s) {
+void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, int T, int mode, int cull_set,
+                    int64_t max_pairs, cudaStream_t s) {
   if (g.n <= 0) return;
   const unsigned nb = (unsigned)((g.n + 255) / 256);
-  if (mode == kProjMask) {
+  if (cull_set == kCullUnstable) {
     if (g.rank_map != nullptr) {
       if (g.n_unstable > 0)
-        k_cull<true><<<(unsigned)((g.n_unstable + 255) / 256), 256, 0, s>>>(g, w, prm, F, g.unstable_ids,
-                                                                          g.n_unstable);
+        k_cull<kCullUnstable><<<(unsigned)((g.n_unstable + 255) / 256), 256, 0, s>>>(g, w, prm, F, g.unstable_ids,
+                                                                                   g.n_unstable);
     } else {
-      k_cull<true><<<nb, 256, 0, s>>>(g, w, prm, F, nullptr, 0);
+      k_cull<kCullUnstable><<<nb, 256, 0, s>>>(g, w, prm, F, nullptr, 0);
     }
+  } else if (cull_set == kCullStable) {
+    k_cull<kCullStable><<<nb, 256, 0, s>>>(g, w, prm, F, nullptr, 0);
   } else {
-    k_cull<false><<<nb, 256, 0, s>>>(g, w, prm, F, nullptr, 0);
+    k_cull<kCullAll><<<nb, 256, 0, s>>>(g, w, prm, F, nullptr, 0);
   }
 #define RTG_PROJ(CC, MM) k_project<CC, MM><<<kPersistBlocks, 256, 0, s>>>(g, w, prm, T, max_pairs)
-  if (g.C == 3) {
-    if (mode == kProjForward) RTG_PROJ(3, kProjForward);
-    else if (mode == kProjMask) RTG_PROJ(3, kProjMask);
-    else RTG_PROJ(3, kProjFused);
-  } else {
-    if (mode == kProjForward) RTG_PROJ(8, kProjForward);
-    else if (mode == kProjMask) RTG_PROJ(8, kProjMask);
-    else RTG_PROJ(8, kProjFused);
+#define RTG_PROJ_C(CC)                              \
+  switch (mode) {                                   \
+    case kProjForward: RTG_PROJ(CC, kProjForward); break; \
+    case kProjMask: RTG_PROJ(CC, kProjMask); break;       \
+    case kProjFused: RTG_PROJ(CC, kProjFused); break;     \
+    default: RTG_PROJ(CC, kProjWindow); break;            \
   }
+  if (g.C == 3) {
+    RTG_PROJ_C(3)
+  } else {
+    RTG_PROJ_C(8)
+  }
+#undef RTG_PROJ_C
 #undef RTG_PROJ
 }
 
-void launch_bin(const Work &w, int64_t N, int T, int64_t max_pairs, cudaStream_t s) {
+void launch_bin(const Work &w, int64_t N, int T, int64_t max_pairs, bool cands, bool stable, cudaStream_t s) {
   if (N <= 0) return;
-  k_bin<<<kPersistBlocks, 256, 0, s>>>(w, N, T, max_pairs);
+  k_bin<<<kPersistBlocks, 256, 0, s>>>(w, N, T, max_pairs, cands ? 1 : 0, stable ? 1 : 0);
 }
+
+void launch_window_reset(const Work &w, cudaStream_t s) { k_window_reset<<<1, 1, 0, s>>>(w); }
 
 void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, int gshift, cudaStream_t s) {
   k_scan_tiles<<<1, 1024, 0, s>>>(w, FT, max_pairs, gshift);

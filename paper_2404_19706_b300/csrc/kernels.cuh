@@ -87,10 +87,16 @@ void launch_tile_mask(const FrameSet &fs, const Work &w, const uint8_t *mask, in
                       bool setup, bool lists, long long nu_preset, cudaStream_t s);
 void launch_rank(const uint8_t *unstable, int64_t n, int32_t *block_cnt, int32_t *rank, int32_t *ids,
                  unsigned long long *nu_counter, int64_t *nu_out, cudaStream_t s);
-enum ProjMode { kProjForward = 0, kProjMask = 1, kProjFused = 2 };
-void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, int T, int mode, int64_t max_pairs,
-                    cudaStream_t s);
-void launch_bin(const Work &w, int64_t N, int T, int64_t max_pairs, cudaStream_t s);
+enum ProjMode { kProjForward = 0, kProjMask = 1, kProjFused = 2, kProjWindow = 3 };
+// Which (frame, Gaussian) pairs the coarse cull considers (kCullUnstable walks the
+// precomputed unstable list when there is one).
+enum CullSet { kCullAll = 0, kCullUnstable = 1, kCullStable = 2 };
+void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, int T, int mode, int cull_set,
+                    int64_t max_pairs, cudaStream_t s);
+// Bins projected entries into the masked render tiles: with `cands`, the cull's candidates
+// that the fused projection marked projected; with `stable`, the open window's list.
+void launch_bin(const Work &w, int64_t N, int T, int64_t max_pairs, bool cands, bool stable, cudaStream_t s);
+void launch_window_reset(const Work &w, cudaStream_t s);
 // gshift >= 0: also build the persistent schedule's item queue (2^gshift groups per tile)
 void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, int gshift, cudaStream_t s);
 void launch_emit(const Work &w, cudaStream_t s);

@@ -10,6 +10,8 @@
 //   rec_box  [F][N] float2        half-extents of the alpha_min support box around mu
 //   ntiles   [F][N] uint32        masked tiles touched (0 = culled or off-mask)
 //   cand     [F*N] uint32         (frame, Gaussian) pairs f * N + i that passed the coarse cull
+//   scand    [F*N] uint32         window cache: projected (frame, stable Gaussian) pairs, whose
+//                                 records stay valid while the window is open
 //   stage    [pairs] uint4        (tile, slot, key) of every pair, written by the projection
 //   keys     [pairs] uint64       (float bits of z_c) << 32 | Gaussian index, bucketed by tile
 //   sorted   [pairs] uint32       Gaussian index, each tile's bucket in front-to-back order
@@ -51,6 +53,8 @@ enum Counter {
   kItems = 9,   // (tile, 32-pixel group) work items of the persistent schedule
   kQFwd = 10,   // next item of the persistent forward (past the first one per warp)
   kQBwd = 11,   // next item of the persistent backward
+  kNumReset = 15,   // slots below this are cleared at the start of every call
+  kWinStable = 15,  // projected (frame, stable Gaussian) entries of the open window (kept)
   kNumCounters = 16
 };
 
@@ -92,6 +96,7 @@ struct Work {
   int32_t *ids;         // [N] compact -> original index
   int32_t *block_cnt;   // [ceil(N / kScanBlock)]
   uint32_t *cand;       // [F*N] candidates f * N + i of the coarse cull, dense, in no particular order
+  uint32_t *scand;      // [F*N] projected (frame, stable Gaussian) entries of the open window
   float4 *rec_hot;
   float4 *rec_cold;
   float2 *rec_box;      // [F][N] support half-extents (rx, ry) around mu

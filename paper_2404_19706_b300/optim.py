@@ -84,12 +84,17 @@ class MaskedStep:
     path: mask, forward, L1 loss, backward, Adam.  ``capture()`` records one iteration in a
     CUDA graph; later ``step()`` calls replay it (same cameras and buffers; the Adam step
     count lives on the device).
+
+    The step is one optimisation window (Section 3.2): its cameras and unstable set are
+    fixed and only the unstable Gaussians move.  With ``window`` (default) it opens the
+    context's window, so the stable Gaussians are projected once here and every iteration
+    projects only the unstable ones (results identical; rtg_window_begin).
     """
 
     def __init__(self, ctx: Context, g: Gaussians, cams, mask: Optional[torch.Tensor], target_color: torch.Tensor,
                  target_depth: torch.Tensor, settings: RenderSettings = RenderSettings(),
                  adam: AdamSettings = AdamSettings(), w_color: float = 1.0, w_depth: float = 1.0,
-                 recompute_mask: bool = False):
+                 recompute_mask: bool = False, window: bool = True):
         self.ctx, self.settings, self.adam = ctx, settings, adam
         self.cams = cams if isinstance(cams, (list, tuple)) else [cams]
         self.mask = mask
@@ -113,6 +118,9 @@ class MaskedStep:
         self.v = torch.zeros(self.nu * (11 + C), device=dev)
         self.step_counter = torch.zeros(1, dtype=torch.int32, device=dev)
         self.graph = None
+        self.window = window
+        if window:
+            api.window_begin(ctx, self.cams, self.g, settings)
 
     def _body(self, stream=None):
         s = self.state

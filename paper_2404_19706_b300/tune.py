@@ -24,7 +24,7 @@ from typing import Callable, Dict, List, Optional, Sequence
 import torch
 
 from . import api
-from .api import Context, Tuning
+from .api import Tuning
 
 TILES = [(16, 16), (16, 8), (8, 16), (8, 8), (32, 8)]
 BATCHES = [32, 64]
@@ -70,19 +70,28 @@ class Autotuner:
         the step's optimiser moved), so every candidate sees the same workload.
     """
 
-    def __init__(self, ctx: Context, step: Callable[[], object], check: Optional[Callable[[], Sequence]] = None,
+    def __init__(self, ctx, step: Callable[[], object], check: Optional[Callable[[], Sequence]] = None,
                  restore: Optional[Callable[[], None]] = None, warmup: int = 3, iters: int = 15, repeats: int = 3):
-        self.ctx, self.step, self.check, self.restore = ctx, step, check, restore
+        # ctx: a Context, or a sequence of Contexts that the step uses together (each gets
+        # every candidate tuning)
+        self.ctxs = list(ctx) if isinstance(ctx, (list, tuple)) else [ctx]
+        self.step, self.check, self.restore = step, check, restore
         self.warmup, self.iters, self.repeats = warmup, iters, repeats
         self._ref = None
 
+    def _status_ok(self) -> bool:
+        bad = [c for c in self.ctxs if api.get_status(c) != 0]
+        for c in bad:
+            api.reset_status(c)
+        return not bad
+
     def _verify(self, t: Tuning) -> Optional[str]:
-        api.reset_status(self.ctx)
+        for c in self.ctxs:
+            api.reset_status(c)
         if self.check is not None:  # before the step moves any parameter
             out = [x.clone() for x in self.check()]
             torch.cuda.synchronize()
-            if api.get_status(self.ctx) != 0:
-                api.reset_status(self.ctx)
+            if not self._status_ok():
                 return "pair capacity exceeded"
             if self._ref is None:
                 self._ref = out
@@ -92,14 +101,14 @@ class Autotuner:
                         raise AssertionError(f"tuning {t} changed a rendered value")
         self.step()  # eager once (also the first use of this configuration)
         torch.cuda.synchronize()
-        if api.get_status(self.ctx) != 0:
-            api.reset_status(self.ctx)
+        if not self._status_ok():
             return "pair capacity exceeded"
         return None
 
     def time(self, t: Tuning) -> Optional[float]:
         """Median ms per step of ``t`` over ``repeats`` timed runs of ``iters`` graph replays."""
-        self.ctx.set_tuning(t)
+        for c in self.ctxs:
+            c.set_tuning(t)
         note = self._verify(t)
         if note is not None:
             if self.restore is not None:
@@ -148,11 +157,12 @@ class Autotuner:
         b1 = measure(stage1(start))
         best = measure(stage2(b1))
         best_ms = min(r["ms"] for r in table if r["ms"] is not None and r["tuning"] == best.as_dict())
-        self.ctx.set_tuning(best)
+        for c in self.ctxs:
+            c.set_tuning(best)
         return TuneResult(best=best, best_ms=best_ms, default_ms=default_ms, table=table)
 
 
-def autotune(ctx: Context, step: Callable[[], object], check: Optional[Callable[[], Sequence]] = None,
+def autotune(ctx, step: Callable[[], object], check: Optional[Callable[[], Sequence]] = None,
              restore: Optional[Callable[[], None]] = None, **kw) -> TuneResult:
     """Runs the staged search and leaves ``ctx`` set to the fastest tuning."""
     return Autotuner(ctx, step, check, restore, **kw).run()
