@@ -44,7 +44,9 @@ C = 3
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=0,
+                    help="timed steps (0: 400 for the masked step, 60 for keyframes, so that the timed "
+                         "region spans several clock samples)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -54,6 +56,12 @@ def parse():
                          "keyframes vs per-frame launches")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--tune-table", default="", help="write the autotuner's candidate table (JSON) to this path")
+    ap.add_argument("--tuning", default="",
+                    help="fixed launch configuration instead of the autotuner's pick: "
+                         "TWxTH,batch,schedule,ctas_per_sm,sort_bits,sort_rank_max (e.g. 8x16,32,1,4,8,256)")
+    ap.add_argument("--max-pairs", type=int, default=0,
+                    help="pair capacity of the masked-step context (0: 24 per Gaussian); smaller keeps "
+                         "profiler captures light")
     return ap.parse_args()
 
 
@@ -201,8 +209,21 @@ def step_state(step):
     return [g.means, g.scales, g.quats, g.opacity, g.colors, *step.u, step.m, step.v, step.step_counter]
 
 
+def parse_tuning(text):
+    import paper_2404_19706_b300 as rtg
+    tile, batch, sched, ctas, bits, cut = text.split(",")
+    tw, th = tile.lower().split("x")
+    return rtg.Tuning(int(tw), int(th), int(batch), int(sched), int(ctas), int(bits), int(cut))
+
+
 def run_tuner(ctx, body, check, tensors, args, label):
-    """Autotunes the context's launch configuration on this workload (unless --no-tune)."""
+    """Autotunes the context's launch configuration on this workload (unless --no-tune, or a
+    fixed --tuning)."""
+    if args.tuning:
+        t = parse_tuning(args.tuning)
+        for c in (ctx if isinstance(ctx, (list, tuple)) else [ctx]):
+            c.set_tuning(t)
+        return None
     if args.no_tune:
         return None
     from paper_2404_19706_b300.tune import autotune
@@ -275,14 +296,24 @@ def alg_bytes(stats, N, F, H, W, Cc=C):
     }
 
 
-def roofline_of(per_launch, alg):
+# DRAM bytes (read + write) per launch of a kernel from one ncu capture of bench.py, keyed
+# by (kernel, render tile, record batch, schedule); the roofline's `traffic` is filled only
+# when the run's dominant kernel and tuning match a captured one.  Source and command:
+# profiles/masked_step_1M_640x480_kernels.md.
+NCU_TRAFFIC = {}
+
+
+def roofline_of(per_launch, alg, tuning=None):
     single = ["project", "emit", "sort_tiles", "forward", "backward", "project_backward", "adam", "scan_tiles",
               "tile_mask", "bin"]
     dom = max(single, key=lambda k: per_launch.get(k, 0.0))
     pk = peaks()
     achieved = alg[dom] / (per_launch[dom] * 1e-3) / 1e9
+    traffic = None
+    if tuning is not None:
+        traffic = NCU_TRAFFIC.get((dom, tuning.tile_w, tuning.tile_h, tuning.batch, tuning.schedule))
     return {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": pk["hbm_gbs"],
-            "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": None,
+            "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": traffic,
             "peak_source": "fallback" if pk.get("_fallback") else "measured (MEASURED_PEAKS.json hbm_gbs)",
             "alg_bytes_per_launch": int(alg[dom]), "ms_per_launch": round(per_launch[dom], 5)}, pk
 
@@ -290,9 +321,10 @@ def roofline_of(per_launch, alg):
 def kernels_per_step(stats, per_frame_calls=1):
     """Kernels one masked step launches: the fused masked forward (11, plus a render-grid
     tile-mask pass when the render tile is not 16 x 16) and loss finalize per forward call,
-    backward 2 per call, then Adam 2 and the scatter 1."""
+    backward 2 per call, then Adam 1 (the renderer reads the optimiser's compact arrays, so
+    nothing is scattered back during the window)."""
     extra = 0 if (stats["tile_w"], stats["tile_h"]) == (16, 16) else 1
-    return per_frame_calls * (11 + extra + 1 + 2) + 3
+    return per_frame_calls * (11 + extra + 1 + 2) + 1
 
 
 def timed_replays(step, steps, flush, stream, local, dist=None):
@@ -336,7 +368,7 @@ def run_ours(args):
     scene, cams = scene_and_candidates()
     settings = rtg.RenderSettings()
     ctx = rtg.Context(max_gaussians=scene.n, max_width=WORKLOAD["width"], max_height=WORKLOAD["height"],
-                      max_pairs=24 * scene.n)
+                      max_pairs=args.max_pairs or 24 * scene.n)
     H, W = WORKLOAD["height"], WORKLOAD["width"]
     mask = torch.zeros(1, H, W, dtype=torch.uint8, device=dev)
     chosen = None
@@ -403,7 +435,7 @@ def run_ours(args):
     per_launch = kernel_profile(rtg, ctx, step, args.steps, flush, stream)
     N, V, K, P, Nu = scene.n, stats["visible"], stats["pairs"], stats["masked_pixels"], stats["n_unstable"]
     alg = alg_bytes(stats, N, 1, H, W)
-    roofline, pk = roofline_of(per_launch, alg)
+    roofline, pk = roofline_of(per_launch, alg, ctx.get_tuning())
     b_step = sum(alg.values())
 
     # ---- end to end through the public API with host buffers (graph replay per step)
@@ -444,7 +476,7 @@ def run_ours(args):
                        "alg_bytes_per_step": int(b_step),
                        "step_hbm_roofline_frac": round(b_step / (ms_step * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
                        "tuning": ctx.get_tuning().as_dict(),
-                       "autotune": tuned.summary() if tuned is not None else "off (--no-tune)",
+                       "autotune": tuned.summary() if tuned is not None else ("fixed by --tuning" if args.tuning else "off (--no-tune)"),
                        "l2": "256 MB buffer written before every step, outside the timed spans",
                        "timing": "timed steps replay one CUDA graph of the whole step; kernel_ms_per_launch and "
                                  "the roofline come from a second live pass of the same number of eager steps "
@@ -472,7 +504,7 @@ def run_ours(args):
 class PerFrameStep:
     """The masked iteration over F keyframes as F single-frame calls: for each frame the
     fused mask + forward + L1 and its backward (gradients accumulated over the frames),
-    then one Adam step and the scatter, exactly what MaskedStep does for all F at once.
+    then one Adam step, exactly what MaskedStep does for all F at once.
     Frame f runs on its own context ctxs[f], which keeps that frame's optimisation window
     open, as the batched step's context keeps the window of all F frames."""
 
@@ -502,7 +534,6 @@ class PerFrameStep:
                                       self.loss[f], None, stream)
             api.render_backward_l1(self.ctxs[f], *s.grads, accumulate=f > 0, stream=stream)
         api.adam_step_counted(s.u, s.grads, s.m, s.v, s.step_counter, s.adam, stream)
-        api.scatter_unstable(s.ids, s.u, s.g, stream)
         return self.loss
 
     def step(self):
@@ -654,7 +685,7 @@ def run_keyframes(args):
     per_launch = kernel_profile(rtg, ctx, batched, args.steps, flush, stream)
     sb = results["batched"]["stats"]
     alg = alg_bytes(sb, scene.n, F, H, W)
-    roofline, pk = roofline_of(per_launch, alg)
+    roofline, pk = roofline_of(per_launch, alg, ctx.get_tuning())
     b_step = sum(alg.values())
 
     # end to end: targets uploaded from pinned host memory and the losses read back each step
@@ -691,10 +722,10 @@ def run_keyframes(args):
                    "alg_bytes_per_step": int(b_step),
                    "step_hbm_roofline_frac": round(b_step / (msb * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
                    "tuning": ctx.get_tuning().as_dict(),
-                   "autotune": tuned_b.summary() if tuned_b is not None else "off (--no-tune)",
+                   "autotune": tuned_b.summary() if tuned_b is not None else ("fixed by --tuning" if args.tuning else "off (--no-tune)"),
                    "per_frame": {"value": round(F * 1e3 / msp, 2), "unit": "frames/s", "ms_per_step": round(msp, 4),
                                  "tuning": ctx1.get_tuning().as_dict(),
-                                 "autotune": tuned_p.summary() if tuned_p is not None else "off (--no-tune)",
+                                 "autotune": tuned_p.summary() if tuned_p is not None else ("fixed by --tuning" if args.tuning else "off (--no-tune)"),
                                  "gpu_launches_per_step": kernels_per_step(results["per_frame"]["stats"], F)},
                    "batched_over_per_frame": round(msp / msb, 3),
                    "l2": "256 MB buffer written before every step, outside the timed spans",
@@ -778,6 +809,8 @@ DEFAULT_CANDIDATE = 7  # first pose of the seeded stream with 25-40% mask covera
 
 def main():
     args = parse()
+    if args.steps <= 0:
+        args.steps = 60 if args.workload == "keyframes" else 400
     if args.impl == "reference":
         out = run_reference(args)
     elif args.workload == "keyframes":

@@ -254,9 +254,11 @@ rtg_status rtg_adam_step(int64_t nu, int32_t C, float *means, float *scales, flo
                          const float *g_opacity, const float *g_colors, float *m, float *v, int32_t step,
                          const rtg_adam_params *hp, void *stream);
 
-/* The same Adam step with its count kept on the device: *step_counter (device int32,
- * start it at 0) is incremented first and the bias corrections use the new value, so the
- * call needs no host-side step number and can be replayed from a captured CUDA graph. */
+/* The same Adam step with its count kept on the device: step_counter is a device int32[2]
+ * (start both at 0).  [0] counts completed steps: the call uses t = [0] + 1 for the bias
+ * corrections and stores t when it finishes; [1] is scratch that returns to 0 after every
+ * call.  The call needs no host-side step number and can be replayed from a captured CUDA
+ * graph.  Two calls on one counter must not overlap on the GPU.  nu = 0 does nothing. */
 rtg_status rtg_adam_step_counted(int64_t nu, int32_t C, float *means, float *scales, float *quats, float *opacity,
                                  float *colors, const float *g_means, const float *g_scales, const float *g_quats,
                                  const float *g_opacity, const float *g_colors, float *m, float *v,

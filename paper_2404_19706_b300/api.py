@@ -376,7 +376,10 @@ def adam_step(params: Sequence[torch.Tensor], grads: Sequence[torch.Tensor], m: 
 
 def adam_step_counted(params: Sequence[torch.Tensor], grads: Sequence[torch.Tensor], m: torch.Tensor,
                       v: torch.Tensor, step_counter: torch.Tensor, hp: AdamSettings = AdamSettings(), stream=None):
-    """Adam with the step count in device memory (int32 [1], incremented by the call)."""
+    """Adam with the step count in device memory: step_counter is int32 [2] (completed steps,
+    and scratch that the call returns to 0); the call increments [0]."""
+    if step_counter.numel() < 2:
+        raise ValueError("step_counter must hold 2 int32 (completed steps, scratch)")
     means, scales, quats, opacity, colors = params
     nu, C = int(means.shape[0]), int(colors.shape[1])
     c = hp.to_c()

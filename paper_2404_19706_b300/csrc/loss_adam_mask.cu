@@ -86,14 +86,18 @@ __global__ void __launch_bounds__(256) k_loss_reduce(Work w, int F, int C, int H
 
 // Fused L1 (Eq. 7/8): sums the forward's per-(tile, 32-pixel group) partials in a fixed
 // order (only groups that held masked pixels wrote them), then the loss and its gradient
-// scales.  2^gshift groups per tile.
-// B300's FP64 rate is a small fraction of FP32 and this runs on one SM, so the sums are
-// FP32 with Kahan compensation per thread and a fixed-order tree across threads.
-__global__ void __launch_bounds__(1024) k_loss_finalize(Work w, int FT, int gshift, int C, float w_c, float w_d,
-                                                        float *__restrict__ loss_out) {
-  __shared__ float s_t[3][1024];
+// scales.  2^gshift groups per tile.  Block b sums a fixed range of tiles (Kahan per thread,
+// fixed-order tree across threads); the last block to finish sums the block partials in
+// block order, so the loss does not depend on scheduling.  The sums are FP32 (B300's FP64
+// rate is a small fraction of its FP32 rate).
+__global__ void __launch_bounds__(256) k_loss_finalize(Work w, int FT, int gshift, int C, float w_c, float w_d,
+                                                       float *__restrict__ loss_out) {
+  __shared__ float s_t[3][256];
+  __shared__ bool s_last;
+  const int per = (FT + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int t0 = (int)blockIdx.x * per, t1 = min(FT, t0 + per);
   float t[3] = {0.f, 0.f, 0.f}, comp[3] = {0.f, 0.f, 0.f};
-  for (int tile = threadIdx.x; tile < FT; tile += 1024) {
+  for (int tile = t0 + (int)threadIdx.x; tile < t1; tile += (int)blockDim.x) {
     const int nw = (int)((w.tile_npix[tile] + 31u) / 32u);
     for (int k = 0; k < nw; ++k) {
       const float *lp = w.tile_loss + (((int64_t)tile << gshift) + k) * 4;
@@ -109,7 +113,27 @@ __global__ void __launch_bounds__(1024) k_loss_finalize(Work w, int FT, int gshi
 #pragma unroll
   for (int q = 0; q < 3; ++q) s_t[q][threadIdx.x] = t[q];
   __syncthreads();
-  for (int stride = 512; stride > 0; stride >>= 1) {
+  for (int stride = 128; stride > 0; stride >>= 1) {
+    if ((int)threadIdx.x < stride)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) s_t[q][threadIdx.x] += s_t[q][threadIdx.x + stride];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) w.loss_part[blockIdx.x * 4 + threadIdx.x] = s_t[threadIdx.x][0];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(w.loss_done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  float a[3] = {0.f, 0.f, 0.f};
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) a[q] += __ldcg(w.loss_part + b * 4 + q);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) s_t[q][threadIdx.x] = a[q];
+  __syncthreads();
+  for (int stride = 128; stride > 0; stride >>= 1) {
     if ((int)threadIdx.x < stride)
 #pragma unroll
       for (int q = 0; q < 3; ++q) s_t[q][threadIdx.x] += s_t[q][threadIdx.x + stride];
@@ -124,12 +148,14 @@ __global__ void __launch_bounds__(1024) k_loss_finalize(Work w, int FT, int gshi
     loss_out[2] = Ld;
     w.loss_scal[4] = np > 0.f ? w_c / (np * (float)C) : 0.f;
     w.loss_scal[5] = nd > 0.f ? w_d / nd : 0.f;
+    *w.loss_done = 0u;
   }
 }
 
 void launch_loss_finalize(const Work &w, int FT, int gshift, int C, float w_c, float w_d, float *loss_out,
                           cudaStream_t s) {
-  k_loss_finalize<<<1, 1024, 0, s>>>(w, FT, gshift, C, w_c, w_d, loss_out);
+  const int blocks = std::max(1, std::min(kLossBlocks, (FT + 255) / 256));
+  k_loss_finalize<<<blocks, 256, 0, s>>>(w, FT, gshift, C, w_c, w_d, loss_out);
 }
 
 __device__ __forceinline__ float signf_(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
@@ -163,19 +189,30 @@ __device__ __forceinline__ float adam_delta(float g, float &m, float &v, float l
   return lr * (m * bc1) / (sqrtf(v) * bc2_sqrt + hp.eps);
 }
 
-// One thread per scalar parameter.  m and v are laid out group by group (means [nu,3],
-// scales [nu,3], quats [nu,4], opacity [nu], colours [nu,C]), so every stream is coalesced.
-__global__ void __launch_bounds__(256) k_adam(int64_t nu, int C, float *__restrict__ means, float *__restrict__ scales,
-                                              float *__restrict__ quats, float *__restrict__ opacity,
-                                              float *__restrict__ colors, const float *__restrict__ g_means,
-                                              const float *__restrict__ g_scales, const float *__restrict__ g_quats,
-                                              const float *__restrict__ g_opacity, const float *__restrict__ g_colors,
-                                              float *__restrict__ m, float *__restrict__ v, rtg_adam_params hp,
-                                              float bc1, float bc2_sqrt, const int32_t *__restrict__ step_dev) {
-  if (step_dev != nullptr) {  // bias corrections from the device step counter, once per block
+// Parameter groups of the compact unstable set (means, scales, quats, opacity, colours);
+// m and v hold the groups one after another in this order.
+struct AdamGroups {
+  float *param[5];
+  const float *grad[5];
+  float lr[5];
+  int64_t begin[6];  // element offsets of the groups in m / v; begin[5] = total
+};
+
+// Each thread updates four elements of a group per iteration, loading all four before
+// computing, so enough loads are in flight to cover HBM latency.  Every stream (param,
+// grad, m, v) is read and written coalesced.
+constexpr int kAdamUnroll = 4;
+
+__global__ void __launch_bounds__(256) k_adam(AdamGroups G, float *__restrict__ m, float *__restrict__ v,
+                                              rtg_adam_params hp, float bc1, float bc2_sqrt,
+                                              int32_t *__restrict__ step_dev) {
+  // Device step counter: step_dev[0] completed steps, step_dev[1] a ticket.  Every block
+  // takes t = step_dev[0] + 1 when it starts; the last block to finish stores t, after
+  // every block has read the old value.
+  if (step_dev != nullptr) {  // bias corrections of step t, once per block
     __shared__ float s_bc[2];
     if (threadIdx.x == 0) {
-      const float t = (float)*step_dev;
+      const float t = (float)(step_dev[0] + 1);
       s_bc[0] = 1.f / (1.f - powf(hp.beta1, t));
       s_bc[1] = rsqrtf(1.f - powf(hp.beta2, t));
     }
@@ -183,32 +220,50 @@ __global__ void __launch_bounds__(256) k_adam(int64_t nu, int C, float *__restri
     bc1 = s_bc[0];
     bc2_sqrt = s_bc[1];
   }
-  const int64_t total = nu * (11 + C);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    float *param;
-    const float *grad;
-    float lr;
-    int64_t j;
-    bool log_space = false;
-    if (i < 3 * nu) {
-      param = means; grad = g_means; lr = hp.lr_means; j = i;
-    } else if (i < 6 * nu) {
-      param = scales; grad = g_scales; lr = hp.lr_scales; j = i - 3 * nu; log_space = true;
-    } else if (i < 10 * nu) {
-      param = quats; grad = g_quats; lr = hp.lr_quats; j = i - 6 * nu;
-    } else if (i < 11 * nu) {
-      param = opacity; grad = g_opacity; lr = hp.lr_opacity; j = i - 10 * nu;
-    } else {
-      param = colors; grad = g_colors; lr = hp.lr_colors; j = i - 11 * nu;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+#pragma unroll 1
+  for (int grp = 0; grp < 5; ++grp) {
+    float *__restrict__ param = G.param[grp];
+    const float *__restrict__ grad = G.grad[grp];
+    const float lr = G.lr[grp];
+    const bool log_space = grp == 1;  // theta = log s, dL/dtheta = s dL/ds, s <- s exp(-step)
+    const int64_t off = G.begin[grp], n = G.begin[grp + 1] - off;
+    float *__restrict__ mg = m + off;
+    float *__restrict__ vg = v + off;
+    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j0 < n; j0 += kAdamUnroll * stride) {
+      float x[kAdamUnroll], g[kAdamUnroll], mm[kAdamUnroll], vv[kAdamUnroll];
+#pragma unroll
+      for (int u = 0; u < kAdamUnroll; ++u) {
+        const int64_t j = j0 + u * stride;
+        if (j < n) {
+          x[u] = param[j];
+          g[u] = grad[j];
+          mm[u] = mg[j];
+          vv[u] = vg[j];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kAdamUnroll; ++u) {
+        const int64_t j = j0 + u * stride;
+        if (j < n) {
+          const float gg = log_space ? g[u] * x[u] : g[u];
+          const float step = adam_delta(gg, mm[u], vv[u], lr, hp, bc1, bc2_sqrt);
+          param[j] = log_space ? x[u] * expf(-step) : x[u] - step;
+          mg[j] = mm[u];
+          vg[j] = vv[u];
+        }
+      }
     }
-    float mm = m[i], vv = v[i];
-    const float x = param[j];
-    // log-space scale: theta = log s, dL/dtheta = s dL/ds, s <- s exp(-step)
-    const float g = log_space ? grad[j] * x : grad[j];
-    const float step = adam_delta(g, mm, vv, lr, hp, bc1, bc2_sqrt);
-    param[j] = log_space ? x * expf(-step) : x - step;
-    m[i] = mm;
-    v[i] = vv;
+  }
+  if (step_dev != nullptr) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned ticket = atomicAdd(reinterpret_cast<unsigned *>(step_dev + 1), 1u);
+      if (ticket == gridDim.x - 1) {
+        step_dev[0] += 1;
+        step_dev[1] = 0;
+      }
+    }
   }
 }
 
@@ -247,12 +302,14 @@ __global__ void k_scatter(int64_t nu, int C, const int32_t *__restrict__ ids, co
 
 // --------------------------------------------------------------------------- unstable mask
 // One CTA per 16x16 tile (the tile grid of the rule).  The unstable Gaussians were
-// projected and bucketed into every tile their support box touches; each pixel scans its
-// tile's bucket until one footprint reaches alpha_min there (T_unstable < 1 in Eq. S2),
-// with the same projection and footprint expression as the forward, and the whole tile
-// stops as soon as all its pixels are covered.  The tile rule (Supplement B) is applied in
-// the same kernel: a tile with fewer than `discard` of its in-image pixels covered is
-// cleared.  Every in-image pixel of the mask is written.
+// projected and bucketed into every tile their support box touches; a pixel is covered
+// when one footprint reaches alpha_min there (T_unstable < 1 in Eq. S2), with the same
+// projection and footprint expression as the forward.  Each warp owns two pixel rows and
+// walks the tile's bucket alone, in batches of 32 records of which it keeps only those
+// whose support box reaches its pixel box (a conservative test), and stops as soon as all
+// its pixels are covered.  The tile rule (Supplement B) is applied in the same kernel: a
+// tile with fewer than `discard` of its in-image pixels covered is cleared.  Every
+// in-image pixel of the mask is written.
 // kMode = kCoverFusedSame (rtg_render_forward_masked, render tiles = 16 x 16): the tile's
 // masked-pixel count and pixel list replace the coverage pass's, and the pair counters are
 // cleared for the second binning.  kCoverFusedOther (other render tiles): only the staging
@@ -260,42 +317,62 @@ __global__ void k_scatter(int64_t nu, int C, const int32_t *__restrict__ ids, co
 template <int kMode>
 __global__ void __launch_bounds__(kTilePix) k_mask_cover_tiles(Work w, Prm prm, int64_t N, int T, int H4,
                                                                uint8_t *__restrict__ mask) {
-  __shared__ float4 s_rec[2][kTilePix];
-  __shared__ int s_wcnt[kTilePix / 32];
+  constexpr int NW = kTilePix / 32;
+  __shared__ float4 s_rec[NW][2][32];
+  __shared__ int s_wcnt[NW];
   if (w.counters[kSkip] != 0ull) return;
   const int tile = blockIdx.x;
   const int f = tile / T, lt = tile - f * T;
   const DevCam &cam = w.cams[f];
   const int tx = lt % cam.mtiles_x, ty = lt / cam.mtiles_x;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int px = tx * kTile + (tid & (kTile - 1)), py = ty * kTile + tid / kTile;
   const bool in = px < cam.W && py < cam.H;
   const float fpx = (float)px, fpy = (float)py;
   const uint32_t off = w.tile_offset[tile];
   const uint32_t n = w.tile_offset[tile + 1] - off;
   const float4 *__restrict__ rec = w.rec_hot + (int64_t)f * N * H4;
+  const float2 *__restrict__ box = w.rec_box + (int64_t)f * N;
+  // the warp's pixel box (two rows of 16; rows below the image are not in it)
+  const int bx0 = __reduce_min_sync(0xffffffffu, in ? px : 0x7fffffff);
+  const int bx1 = __reduce_max_sync(0xffffffffu, in ? px : -1);
+  const int by0 = __reduce_min_sync(0xffffffffu, in ? py : 0x7fffffff);
+  const int by1 = __reduce_max_sync(0xffffffffu, in ? py : -1);
+  const float wcx = 0.5f * (float)(bx0 + bx1), whx = 0.5f * (float)(bx1 - bx0);
+  const float wcy = 0.5f * (float)(by0 + by1), why = 0.5f * (float)(by1 - by0);
   bool cov = false;
-  for (uint32_t b0 = 0; b0 < n; b0 += kTilePix) {
-    if (__syncthreads_and(cov || !in)) break;
-    const uint32_t j = b0 + tid;
+  for (uint32_t b0 = 0; b0 < n; b0 += 32) {
+    if (__all_sync(0xffffffffu, cov || !in)) break;
+    const uint32_t j = b0 + lane;
+    bool keep = false;
+    float4 r0, r1;
     if (j < n) {
       const uint32_t gid = (uint32_t)w.keys[off + j];
-      s_rec[0][tid] = rec[(int64_t)gid * H4];
-      s_rec[1][tid] = rec[(int64_t)gid * H4 + 1];
+      const float2 bb = box[gid];
+      r0 = rec[(int64_t)gid * H4];
+      keep = fabsf(r0.x - wcx) <= whx + bb.x && fabsf(r0.y - wcy) <= why + bb.y;
+      if (keep) r1 = rec[(int64_t)gid * H4 + 1];
     }
-    __syncthreads();
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (keep) {
+      const int slot = __popc(bal & lanemask_lt());
+      s_rec[wid][0][slot] = r0;
+      s_rec[wid][1][slot] = r1;
+    }
+    __syncwarp();
     if (in && !cov) {
-      const int m = (int)min((uint32_t)kTilePix, n - b0);
+      const int m = __popc(bal);
       for (int k = 0; k < m; ++k) {
-        const float4 r0 = s_rec[0][k], r1 = s_rec[1][k];
+        const float4 a = s_rec[wid][0][k], c = s_rec[wid][1][k];
         float dx, dy, t1, t2, g;
-        if (footprint(fpx, fpy, r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, prm.f_max, dx, dy, t1, t2, g) >=
+        if (footprint(fpx, fpy, a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w, prm.f_max, dx, dy, t1, t2, g) >=
             prm.alpha_min) {
           cov = true;
           break;
         }
       }
     }
+    __syncwarp();
   }
   const int n_in = __syncthreads_count(in);
   const int n_cov = __syncthreads_count(cov);
@@ -303,7 +380,6 @@ __global__ void __launch_bounds__(kTilePix) k_mask_cover_tiles(Work w, Prm prm, 
   if (in) mask[((int64_t)f * cam.H + py) * cam.W + px] = (cov && keep) ? 1 : 0;
   if (kMode == kCoverFusedSame) {  // compacted pixel list of the render tile (raster order)
     const bool act = in && cov && keep;
-    const int lane = tid & 31, wid = tid >> 5;
     const unsigned bal = __ballot_sync(0xffffffffu, act);
     if (lane == 0) s_wcnt[wid] = __popc(bal);
     __syncthreads();
@@ -325,19 +401,29 @@ void launch_l1_loss(const Work &w, int F, int C, int H, int W, const float *colo
   k_loss_grad<<<kLossBlocks, 256, 0, s>>>(w, F, C, H, W, color, depth, tcolor, tdepth, mask, dL_dcolor, dL_ddepth);
 }
 
-__global__ void k_step_increment(int32_t *step) { *step += 1; }
-
 void launch_adam(int64_t nu, int C, float *means, float *scales, float *quats, float *opacity, float *colors,
                  const float *g_means, const float *g_scales, const float *g_quats, const float *g_opacity,
                  const float *g_colors, float *m, float *v, const rtg_adam_params &hp, float bc1, float bc2_sqrt,
                  int32_t *step_dev, cudaStream_t s) {
-  if (step_dev != nullptr) k_step_increment<<<1, 1, 0, s>>>(step_dev);
   if (nu <= 0) return;
-  const int64_t total = nu * (11 + C);
-  const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)kPersistBlocks * 4);
-  k_adam<<<blocks, 256, 0, s>>>(nu, C, means, scales, quats, opacity, colors, g_means, g_scales,
-                                                      g_quats, g_opacity, g_colors, m, v, hp, bc1, bc2_sqrt,
-                                    step_dev);
+  AdamGroups G;
+  float *params[5] = {means, scales, quats, opacity, colors};
+  const float *grads[5] = {g_means, g_scales, g_quats, g_opacity, g_colors};
+  const float lrs[5] = {hp.lr_means, hp.lr_scales, hp.lr_quats, hp.lr_opacity, hp.lr_colors};
+  const int64_t width[5] = {3, 3, 4, 1, C};
+  G.begin[0] = 0;
+  for (int k = 0; k < 5; ++k) {
+    G.param[k] = params[k];
+    G.grad[k] = grads[k];
+    G.lr[k] = lrs[k];
+    G.begin[k + 1] = G.begin[k] + nu * width[k];
+  }
+  const int64_t total = G.begin[5];
+  // a persistent grid (8 CTAs per SM): the element loop is a bandwidth-bound stream, and
+  // the counted step takes one same-address ticket per CTA
+  const unsigned blocks =
+      (unsigned)std::min<int64_t>((total + 256 * kAdamUnroll - 1) / (256 * kAdamUnroll), (int64_t)kPersistBlocks);
+  k_adam<<<blocks, 256, 0, s>>>(G, m, v, hp, bc1, bc2_sqrt, step_dev);
 }
 
 void launch_gather(int64_t nu, int C, const int32_t *ids, const float *means, const float *scales,

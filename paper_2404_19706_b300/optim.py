@@ -94,7 +94,7 @@ class MaskedStep:
     def __init__(self, ctx: Context, g: Gaussians, cams, mask: Optional[torch.Tensor], target_color: torch.Tensor,
                  target_depth: torch.Tensor, settings: RenderSettings = RenderSettings(),
                  adam: AdamSettings = AdamSettings(), w_color: float = 1.0, w_depth: float = 1.0,
-                 recompute_mask: bool = False, window: bool = True):
+                 recompute_mask: bool = False, window: bool = True, scatter_every_step: bool = False):
         self.ctx, self.settings, self.adam = ctx, settings, adam
         self.cams = cams if isinstance(cams, (list, tuple)) else [cams]
         self.mask = mask
@@ -104,10 +104,15 @@ class MaskedStep:
         self.w_color, self.w_depth = w_color, w_depth
         # the unstable index is fixed for the life of this step object (one window)
         self.rank, self.ids, self.nu = api.unstable_rank(ctx, g.unstable)
-        # the optimiser owns compact copies of the unstable parameters; after every Adam step
-        # they are scattered into the full arrays, which the renderer reads directly
+        # the optimiser owns compact copies of the unstable parameters, and the renderer reads
+        # the unstable Gaussians from them (the u_* overrides); the full arrays are brought up
+        # to date by write_back(), or after every step with scatter_every_step
         self.u = api.gather_unstable(self.ids, g)
-        self.g = dataclasses.replace(g, rank_map=self.rank, unstable_ids=self.ids, n_unstable=self.nu)
+        self.full = g
+        self.scatter_every_step = scatter_every_step
+        self.g = dataclasses.replace(g, rank_map=self.rank, unstable_ids=self.ids, n_unstable=self.nu,
+                                     u_means=self.u[0], u_scales=self.u[1], u_quats=self.u[2],
+                                     u_opacity=self.u[3], u_colors=self.u[4])
         self.state = RasterState(ctx, self.g, self.cams, mask, settings)
         dev = g.means.device
         C = g.channels
@@ -116,7 +121,7 @@ class MaskedStep:
         self.grads = [torch.zeros_like(t) for t in self.u]
         self.m = torch.zeros(self.nu * (11 + C), device=dev)
         self.v = torch.zeros(self.nu * (11 + C), device=dev)
-        self.step_counter = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.step_counter = torch.zeros(2, dtype=torch.int32, device=dev)  # completed steps, scratch
         self.graph = None
         self.window = window
         if window:
@@ -136,7 +141,8 @@ class MaskedStep:
                                   self.loss, None, stream)
         api.render_backward_l1(self.ctx, *self.grads, stream=stream)
         api.adam_step_counted(self.u, self.grads, self.m, self.v, self.step_counter, self.adam, stream)
-        api.scatter_unstable(self.ids, self.u, self.g, stream)
+        if self.scatter_every_step:
+            api.scatter_unstable(self.ids, self.u, self.full, stream)
         return self.loss
 
     def step(self, stream=None):
@@ -157,6 +163,5 @@ class MaskedStep:
         return graph
 
     def write_back(self, stream=None):
-        """Scatter the optimised compact parameters into the full arrays (every step already
-        does this; kept for callers that modify the compact copies themselves)."""
-        api.scatter_unstable(self.ids, self.u, self.g, stream)
+        """Scatter the optimised compact parameters into the full arrays."""
+        api.scatter_unstable(self.ids, self.u, self.full, stream)

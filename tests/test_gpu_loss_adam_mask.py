@@ -163,7 +163,36 @@ def test_masked_step_graph_replay_matches_eager():
     np.testing.assert_allclose(lb, la, rtol=1e-4)
     for a, b in zip(eager.u, graphed.u):
         np.testing.assert_allclose(b.cpu().numpy(), a.cpu().numpy(), rtol=1e-4, atol=1e-6)
-    assert int(graphed.step_counter.item()) == 6 and int(eager.step_counter.item()) == 6
+    assert graphed.step_counter.tolist() == [6, 0] and eager.step_counter.tolist() == [6, 0]
+
+
+def test_masked_step_scatter_every_step_keeps_full_arrays_current():
+    """The renderer reads the unstable Gaussians from the optimiser's compact arrays; with
+    scatter_every_step the full arrays follow them after every step, otherwise write_back()
+    brings them up to date, and the stable rows never change."""
+    m = rtg()
+    scene, layout = synth.room_scene(2045, 20000)
+    cam = next(synth.room_camera_candidates(2046, layout, 128, 96, 120.0))
+    scene.unstable = synth.flag_blobs(scene, [cam], 4000, 3, seed=10)
+    tref = gpu_forward(synth.jitter_scene(scene, 11), cam)
+    tc = torch.tensor(tref["color"]).cuda()
+    td = torch.tensor(np.where(tref["depth"] > 0, tref["depth"], 0)).cuda()
+    for every in (True, False):
+        ctx = ctx_for(scene.n, cam)
+        g = m.Gaussians.from_scene(scene)
+        before = g.means.clone()
+        mask = torch.zeros(1, 96, 128, dtype=torch.uint8, device="cuda")
+        step = m.MaskedStep(ctx, g, [cam], mask, tc, td, recompute_mask=True, scatter_every_step=every)
+        for _ in range(3):
+            step.step()
+        torch.cuda.synchronize()
+        u = g.unstable.bool()
+        if not every:
+            assert torch.equal(g.means, before)  # untouched until write_back
+            step.write_back()
+            torch.cuda.synchronize()
+        assert torch.equal(g.means[u], step.u[0]) and not torch.equal(g.means[u], before[u])
+        assert torch.equal(g.means[~u], before[~u])
 
 
 def test_precomputed_unstable_index_is_bitwise_identical():

@@ -145,6 +145,7 @@ def test_masked_step_with_and_without_window_agree():
         losses = [step.step().clone() for _ in range(3)]
         step.capture()
         losses += [step.step().clone() for _ in range(3)]
+        step.write_back()
         torch.cuda.synchronize()
         assert m.window_is_open(ctx) == window
         out.append((torch.stack(losses).cpu().numpy(), g.means.cpu().numpy(), mask.clone()))
