@@ -300,7 +300,10 @@ def alg_bytes(stats, N, F, H, W, Cc=C):
 # by (kernel, render tile, record batch, schedule); the roofline's `traffic` is filled only
 # when the run's dominant kernel and tuning match a captured one.  Source and command:
 # profiles/masked_step_1M_640x480_kernels.md.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    ("backward", 8, 16, 32, 1): 18_954_240 + 256,  # dram read + write, k_backward_queue<3, 32>
+    ("forward", 8, 16, 32, 1): 13_533_952,  # k_forward_queue<3, 32>
+}
 
 
 def roofline_of(per_launch, alg, tuning=None):
