@@ -227,12 +227,16 @@ rtg_status rtg_render_forward_masked(rtg_ctx *ctx, const rtg_camera *cams, int32
 
 /* Optimisation window (Section 3.2): within a window only the unstable Gaussians are
  * optimised; the stable ones keep their parameters.  rtg_window_begin projects every stable
- * Gaussian into the window's F cameras once and keeps those records in the workspace.  A
- * later forward (any of the three rtg_render_forward* calls) whose cameras, render
+ * Gaussian into the window's F cameras once and keeps those records in the workspace, and
+ * also the stable Gaussians' sorted per-tile lists over whole frames for the current render
+ * tile (it synchronises `stream` once; if those lists exceed max_pairs only the records are
+ * kept).  A later forward (any of the three rtg_render_forward* calls) whose cameras, render
  * parameters, Gaussian arrays (the same pointers) and precomputed unstable index
  * (rank_map, unstable_ids, n_unstable; required here) are those of rtg_window_begin then
- * projects only the unstable Gaussians and reuses the stable records: its results are
- * identical to a forward without the window.  The caller promises that the stable
+ * projects, bins and sorts only the unstable Gaussians and merges them with the cached
+ * lists: its results are identical to a forward without the window (rtg_stats.visible
+ * then counts the unstable projections only).  rtg_set_tuning with a new render tile
+ * rebuilds the lists (synchronising that stream).  The caller promises that the stable
  * Gaussians' parameters and the unstable flags do not change while the window is open.
  * Any forward that does not match closes the window (it rewrites the records), as does
  * rtg_window_end; rtg_window_is_open reports the state (1 open, 0 closed). */

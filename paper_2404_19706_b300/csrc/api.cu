@@ -17,6 +17,10 @@ struct Window {
   rtg_camera cams[RTG_MAX_FRAMES];
   rtg_render_params prm;
   rtg_gaussians g;
+  cudaStream_t stream;
+  // sorted per-tile lists of the stable Gaussians over whole frames, for one render grid
+  bool lists;
+  int lists_tws, lists_ths;
 };
 
 struct rtg_ctx {
@@ -26,6 +30,10 @@ struct rtg_ctx {
   size_t bytes;
   Work w;
   uint32_t *status_host;
+  uint32_t *winst_host;  // status word of the window's list build (host-mapped)
+  uint32_t *winst_dev;
+  uint32_t *win_scount, *win_soff;  // [F*T + 1] cached stable list length and offset per tile
+  unsigned long long *win_skeys;    // [pairs] cached stable keys, each tile's list sorted
   char err[512];
   // state of the last forward, consumed by the backward
   bool has_fwd;
@@ -117,7 +125,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
   size_t cams, counters, rank, ids, block_cnt, cand, rec_hot, rec_cold, rec_box, ntiles, tile_npix, tile_count, tile_offset,
       tile_cursor, keys, keys_alt, stage, sorted, px_T, px_last, px_hit, grad2d, loss_part, loss_scal, loss_done, tile_loss,
-      px_list, items, scand, total;
+      px_list, items, scand, win_scount, win_soff, win_skeys, total;
 };
 
 bool capacity_ok(const rtg_capacity *c) {
@@ -175,6 +183,9 @@ Layout layout_of(const rtg_capacity *c) {
   L.px_list = take(padded);
   L.items = take(groups * 4);
   L.scand = take(Fm * N * 4);
+  L.win_scount = take((FT + 1) * 4);
+  L.win_soff = take((FT + 1) * 4);
+  L.win_skeys = take(K * 8);
   L.total = o;
   return L;
 }
@@ -318,6 +329,51 @@ __global__ void k_debug_extract(Work w, int64_t N, int F, int32_t *rect, uint32_
   if (zbits != nullptr) zbits[i] = vis ? __float_as_uint(c1.x) : 0u;
 }
 
+// Sorted per-tile lists of the open window's stable Gaussians over whole frames, for the
+// render grid of ctx->tune: bins the cached stable projections into every tile, sorts each
+// tile, and keeps the sorted keys with each tile's count and offset.  A window forward then
+// bins and sorts only the unstable pairs and merges them with these lists per masked tile.
+// Synchronises the window's stream; if the lists do not fit in the pair capacity the window
+// keeps only its projections (and every forward bins the stable Gaussians itself).
+rtg_status build_window_lists(rtg_ctx *ctx) {
+  Window &win = ctx->win;
+  win.lists = false;
+  Prm P;
+  rtg_status st = make_prm(ctx, &win.prm, P);
+  if (st != RTG_OK) return st;
+  FrameSet fs;
+  if ((st = make_frames(ctx, win.cams, win.F, &win.prm, fs)) != RTG_OK) return st;
+  GaussPtrs gp;
+  if ((st = make_gauss(ctx, &win.g, gp)) != RTG_OK) return st;
+  const Tuning tn = ctx->tune;
+  const DevCam &c0 = fs.cam[0];
+  const int T = c0.tiles_x * c0.tiles_y, FT = win.F * T;
+  cudaStream_t s = win.stream;
+  Work w = ctx->w;
+  w.rank = const_cast<int32_t *>(gp.rank_map);
+  w.ids = const_cast<int32_t *>(gp.unstable_ids);
+  w.status = ctx->winst_dev;  // an overflow here must not mark the caller's status
+  *(volatile uint32_t *)ctx->winst_host = 0u;
+  launch_tile_mask(fs, w, nullptr, T, c0.tiles_x, tn.tws, tn.ths, true, false, (long long)gp.n_unstable, s);
+  launch_bin(w, gp.n, T, ctx->cap.max_pairs, false, true, s);
+  launch_scan_tiles(w, FT, ctx->cap.max_pairs, -1, nullptr, s);
+  launch_emit(w, s);
+  launch_sort_tiles(w, FT, tn.sort_bits, tn.sort_rank_max, StableLists{nullptr, nullptr, nullptr}, ctx->win_skeys,
+                    s);
+  cudaMemcpyAsync(ctx->win_scount, w.tile_count, (size_t)FT * 4, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(ctx->win_soff, w.tile_offset, (size_t)FT * 4, cudaMemcpyDeviceToDevice, s);
+  if ((st = check_launch(ctx, "window lists")) != RTG_OK) return st;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return check_launch(ctx, "window lists");
+  if (*(volatile uint32_t *)ctx->winst_host != 0u) {
+    *(volatile uint32_t *)ctx->winst_host = 0u;
+    return RTG_OK;  // did not fit: projections only
+  }
+  win.lists = true;
+  win.lists_tws = tn.tws;
+  win.lists_ths = tn.ths;
+  return RTG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -352,6 +408,15 @@ rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap) {
   *ctx->status_host = 0u;
   uint32_t *status_dev = nullptr;
   cudaHostGetDevicePointer((void **)&status_dev, ctx->status_host, 0);
+  if (cudaHostAlloc((void **)&ctx->winst_host, 4, cudaHostAllocMapped) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeHost(ctx->status_host);
+    cudaFree(ctx->slab);
+    free(ctx);
+    return RTG_ERR_CUDA;
+  }
+  *ctx->winst_host = 0u;
+  cudaHostGetDevicePointer((void **)&ctx->winst_dev, ctx->winst_host, 0);
   char *b = ctx->slab;
   Work &w = ctx->w;
   w.cams = (DevCam *)(b + L.cams);
@@ -383,6 +448,9 @@ rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap) {
   w.px_list = (uint8_t *)(b + L.px_list);
   w.items = (uint32_t *)(b + L.items);
   w.scand = (uint32_t *)(b + L.scand);
+  ctx->win_scount = (uint32_t *)(b + L.win_scount);
+  ctx->win_soff = (uint32_t *)(b + L.win_soff);
+  ctx->win_skeys = (unsigned long long *)(b + L.win_skeys);
   w.status = status_dev;
   {
     int sms = 148;
@@ -421,6 +489,7 @@ rtg_status rtg_destroy(rtg_ctx *ctx) {
   free(ctx->recs);
   cudaFree(ctx->slab);
   cudaFreeHost(ctx->status_host);
+  cudaFreeHost(ctx->winst_host);
   free(ctx);
   return RTG_OK;
 }
@@ -429,7 +498,10 @@ rtg_status rtg_set_tuning(rtg_ctx *ctx, const rtg_tuning *t) {
   if (ctx == nullptr) return RTG_ERR_ARG;
   Tuning o;
   if (!make_tuning(t, ctx->tune.num_sms, o)) return fail(ctx, RTG_ERR_ARG, "set_tuning: unsupported setting");
+  const bool grid_changed = o.tws != ctx->tune.tws || o.ths != ctx->tune.ths;
   ctx->tune = o;
+  // the window's cached stable lists belong to one render grid (and sort arrangement)
+  if (ctx->win.open && (grid_changed || !ctx->win.lists)) return build_window_lists(ctx);
   return RTG_OK;
 }
 
@@ -526,6 +598,10 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
   const bool win = window_matches(ctx, cams, F, g, prm);
   if (!win) ctx->win.open = false;
   const int cull = win ? kCullUnstable : kCullAll;
+  // with the window's sorted stable lists only the unstable pairs are binned and sorted
+  const bool lists = win && ctx->win.lists && ctx->win.lists_tws == tn.tws && ctx->win.lists_ths == tn.ths;
+  const StableLists sl = lists ? StableLists{ctx->win_skeys, ctx->win_soff, ctx->win_scount}
+                               : StableLists{nullptr, nullptr, nullptr};
   Work w = ctx->w;
   if (gp.rank_map != nullptr) {
     w.rank = const_cast<int32_t *>(gp.rank_map);
@@ -546,7 +622,7 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
     }
     {
       ProfScope ps(ctx, kPUnstableMask, s);  // coverage pass: scan, scatter, cover + tile rule
-      launch_scan_tiles(w, F * TM, ctx->cap.max_pairs, -1, s);
+      launch_scan_tiles(w, F * TM, ctx->cap.max_pairs, -1, nullptr, s);
       launch_emit(w, s);
       launch_mask_cover_tiles(w, P, n, F, TM, gp.C, mask_out, same_grid ? kCoverFusedSame : kCoverFusedOther, s);
       if (!same_grid)
@@ -554,7 +630,7 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
     }
     {
       ProfScope ps(ctx, kPBin, s);
-      launch_bin(w, n, T, ctx->cap.max_pairs, true, win, s);
+      launch_bin(w, n, T, ctx->cap.max_pairs, true, win && !lists, s);
     }
     mask = mask_out;
   } else {
@@ -568,14 +644,14 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
       ProfScope ps(ctx, kPProject, s);
       launch_project(gp, w, P, F, T, kProjForward, cull, ctx->cap.max_pairs, s);
     }
-    if (win) {
+    if (win && !lists) {
       ProfScope ps(ctx, kPBin, s);
       launch_bin(w, n, T, ctx->cap.max_pairs, false, true, s);
     }
   }
   {
     ProfScope ps(ctx, kPScanTiles, s);
-    launch_scan_tiles(w, FT, ctx->cap.max_pairs, tn.schedule == 1 ? tn.gshift() : -1, s);
+    launch_scan_tiles(w, FT, ctx->cap.max_pairs, tn.schedule == 1 ? tn.gshift() : -1, sl.count, s);
   }
   {
     ProfScope ps(ctx, kPEmit, s);
@@ -583,7 +659,7 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
   }
   {
     ProfScope ps(ctx, kPSortTiles, s);
-    launch_sort_tiles(w, FT, tn.sort_bits, tn.sort_rank_max, s);
+    launch_sort_tiles(w, FT, tn.sort_bits, tn.sort_rank_max, sl, nullptr, s);
   }
   {
     ProfScope ps(ctx, kPForward, s);
@@ -656,9 +732,12 @@ rtg_status rtg_window_begin(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, con
   memcpy(win.cams, cams, sizeof(rtg_camera) * (size_t)F);
   win.prm = *prm;
   win.g = *g;
+  win.stream = s;
   win.open = true;
   ctx->last_stream = s;
-  return RTG_OK;
+  st = build_window_lists(ctx);
+  if (st != RTG_OK) win.open = false;
+  return st;
 }
 
 rtg_status rtg_window_end(rtg_ctx *ctx) {
@@ -876,7 +955,7 @@ rtg_status rtg_unstable_mask(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, co
   if (gp.u_means != nullptr && gp.rank_map == nullptr)
     if ((st = rank_pass(ctx, gp.unstable, gp.n, w.rank, w.ids, w.counters, nullptr, s)) != RTG_OK) return st;
   launch_project(gp, w, P, F, T, kProjMask, kCullUnstable, ctx->cap.max_pairs, s);
-  launch_scan_tiles(w, F * T, ctx->cap.max_pairs, -1, s);
+  launch_scan_tiles(w, F * T, ctx->cap.max_pairs, -1, nullptr, s);
   launch_emit(w, s);
   launch_mask_cover_tiles(w, P, gp.n, F, T, gp.C, mask, kCoverPlain, s);
   ctx->last_stream = s;

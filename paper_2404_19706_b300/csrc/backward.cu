@@ -544,10 +544,12 @@ void launch_project_backward(const GaussPtrs &g, const Work &w, const Prm &prm, 
   if (g.n <= 0) return;
   const int acc = accumulate ? 1 : 0;
   if (g.C == 3)
-    k_project_backward<3><<<kPersistBlocks, 256, 0, s>>>(g, w, prm, F, g_means, g_scales, g_quats, g_opacity,
+    k_project_backward<3><<<resident_grid((const void *)k_project_backward<3>, 256), 256, 0, s>>>(
+        g, w, prm, F, g_means, g_scales, g_quats, g_opacity,
                                                          g_colors, acc);
   else
-    k_project_backward<8><<<kPersistBlocks, 256, 0, s>>>(g, w, prm, F, g_means, g_scales, g_quats, g_opacity,
+    k_project_backward<8><<<resident_grid((const void *)k_project_backward<8>, 256), 256, 0, s>>>(
+        g, w, prm, F, g_means, g_scales, g_quats, g_opacity,
                                                          g_colors, acc);
 }
 

@@ -4,6 +4,8 @@
 // of every Gaussian into every frame, the exclusive scan of per-tile pair counts (and
 // the work queue of the persistent schedule) and the emission of (depth, index) keys
 // into per-tile buckets.
+#include <mutex>
+
 #include "kernels.cuh"
 #include "project.cuh"
 
@@ -24,8 +26,9 @@ __global__ void __launch_bounds__(kMaxTilePix) k_tile_mask(FrameSet fs, Work w, 
   const DevCam &cam = fs.cam[f];
   if (setup && blockIdx.x == 0) {
     for (int i = threadIdx.x; i < fs.F; i += blockDim.x) w.cams[i] = fs.cam[i];
-    if (threadIdx.x < kNumReset)
-      w.counters[threadIdx.x] = (threadIdx.x == kNumUnstable && nu_preset >= 0) ? (unsigned long long)nu_preset : 0ull;
+    const int c = (int)threadIdx.x * kCounterStride;
+    if ((int)threadIdx.x < kNumCounterSlots && c != kWinStable)
+      w.counters[c] = (c == kNumUnstable && nu_preset >= 0) ? (unsigned long long)nu_preset : 0ull;
   }
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int tx = lt % tiles_x, ty = lt / tiles_x;
@@ -122,6 +125,146 @@ __global__ void __launch_bounds__(kRankThreads) k_rank_write(const uint8_t *__re
   }
 }
 
+// --------------------------------------------------------------------------- tile rects
+// A Gaussian's tile rectangle [tx0, tx1] x [ty0, ty1] is walked in row-major order,
+// kRectChunk tiles at a time: the loads of a chunk are issued together, so a rectangle is not
+// one long chain of dependent L2 round trips.
+constexpr int kRectChunk = 8;
+
+// Tiles of the rectangle that hold masked pixels.
+__device__ __forceinline__ uint32_t count_rect(const uint32_t *__restrict__ npix, int tiles_x, int tx0, int ty0,
+                                               int tx1, int ty1) {
+  const int area = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
+  uint32_t nt = 0;
+  int tx = tx0, ty = ty0;
+  for (int a0 = 0; a0 < area; a0 += kRectChunk) {
+    uint32_t v[kRectChunk];
+#pragma unroll
+    for (int u = 0; u < kRectChunk; ++u) {
+      v[u] = (a0 + u < area) ? npix[ty * tiles_x + tx] : 0u;
+      if (++tx > tx1) {
+        tx = tx0;
+        ++ty;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kRectChunk; ++u) nt += v[u] != 0u;
+  }
+  return nt;
+}
+
+// Warp-cooperative binning.  Each lane holds one (frame, Gaussian) entry with a tile
+// rectangle (empty when tx1 < tx0).  Rectangles of up to kRectChunk tiles are walked by
+// their own lane (one chunk); larger ones are walked by the whole warp together, 32 tiles
+// per round, so one Gaussian near the camera that spans hundreds of tiles does not hold its
+// warp (and, through the block's reservation barrier, its block) for hundreds of L2 round
+// trips.  All 32 lanes must call these functions together.  `fbase` is the lane's frame
+// offset f * T into the per-tile arrays; a lane without an entry passes an empty rectangle
+// (its tiles_x is not used: a big rectangle is walked with its own lane's tiles_x).
+
+// Masked tiles of each lane's rectangle.
+__device__ __forceinline__ uint32_t warp_count_rects(const uint32_t *__restrict__ npix, int tiles_x, int fbase,
+                                                     int tx0, int ty0, int tx1, int ty1) {
+  const int lane = threadIdx.x & 31;
+  const int rw = tx1 - tx0 + 1, area = tx1 < tx0 ? 0 : rw * (ty1 - ty0 + 1);
+  const bool big = area > kRectChunk;
+  uint32_t nt = (area > 0 && !big) ? count_rect(npix + fbase, tiles_x, tx0, ty0, tx1, ty1) : 0u;
+  unsigned bigs = __ballot_sync(0xffffffffu, big);
+  while (bigs) {
+    const int src = __ffs(bigs) - 1;
+    bigs &= bigs - 1;
+    const int s_area = __shfl_sync(0xffffffffu, area, src), s_rw = __shfl_sync(0xffffffffu, rw, src);
+    const int s_tx0 = __shfl_sync(0xffffffffu, tx0, src), s_ty0 = __shfl_sync(0xffffffffu, ty0, src);
+    const int s_fb = __shfl_sync(0xffffffffu, fbase, src), s_tx = __shfl_sync(0xffffffffu, tiles_x, src);
+    uint32_t cnt = 0;
+    for (int j0 = 0; j0 < s_area; j0 += 32) {
+      const int j = j0 + lane;
+      bool on = false;
+      if (j < s_area) {
+        const int yy = j / s_rw;
+        on = npix[s_fb + (s_ty0 + yy) * s_tx + s_tx0 + (j - yy * s_rw)] != 0u;
+      }
+      cnt += __popc(__ballot_sync(0xffffffffu, on));
+    }
+    if (lane == src) nt = cnt;
+  }
+  return nt;
+}
+
+// Stages one (global tile, slot, key lo, key hi) per masked tile of each lane's rectangle,
+// at positions first, first + 1, ... of that lane (from block_reserve of the counts above).
+__device__ __forceinline__ void warp_stage_rects(uint4 *__restrict__ stage, const uint32_t *__restrict__ npix,
+                                                 uint32_t *__restrict__ tcount, int tiles_x, int fbase, int tx0,
+                                                 int ty0, int tx1, int ty1, uint32_t nt, uint32_t klo, uint32_t khi,
+                                                 unsigned long long first, int64_t max_pairs) {
+  const int lane = threadIdx.x & 31;
+  const int rw = tx1 - tx0 + 1, area = tx1 < tx0 ? 0 : rw * (ty1 - ty0 + 1);
+  const bool big = area > kRectChunk;
+  // small rectangles: one chunk, all lanes together.  Lanes of a warp hold neighbouring
+  // Gaussians and often the same tiles, so the slot atomics are aggregated per tile across
+  // the warp (match.any): one atomic per distinct tile, its peers take consecutive slots.
+  {
+    const bool small = nt > 0 && !big;
+    int t[kRectChunk];
+    bool on[kRectChunk];
+    unsigned peers[kRectChunk];
+    uint32_t base[kRectChunk];
+    int tx = tx0, ty = ty0;
+#pragma unroll
+    for (int u = 0; u < kRectChunk; ++u) {
+      t[u] = fbase + ty * tiles_x + tx;
+      on[u] = small && u < area && npix[t[u]] != 0u;
+      if (++tx > tx1) {
+        tx = tx0;
+        ++ty;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kRectChunk; ++u) {
+      peers[u] = __match_any_sync(0xffffffffu, on[u] ? t[u] : -1 - lane);
+      base[u] = 0u;
+      if (on[u] && lane == __ffs(peers[u]) - 1) base[u] = atomicAdd(tcount + t[u], (uint32_t)__popc(peers[u]));
+    }
+    unsigned long long idx = first;
+#pragma unroll
+    for (int u = 0; u < kRectChunk; ++u) {
+      const uint32_t b = __shfl_sync(0xffffffffu, base[u], __ffs(peers[u]) - 1);
+      if (on[u]) {
+        if (idx < (unsigned long long)max_pairs)
+          stage[idx] = make_uint4((uint32_t)t[u], b + __popc(peers[u] & lanemask_lt()), klo, khi);
+        ++idx;
+      }
+    }
+  }
+  unsigned bigs = __ballot_sync(0xffffffffu, big && nt > 0);
+  while (bigs) {
+    const int src = __ffs(bigs) - 1;
+    bigs &= bigs - 1;
+    const int s_area = __shfl_sync(0xffffffffu, area, src), s_rw = __shfl_sync(0xffffffffu, rw, src);
+    const int s_tx0 = __shfl_sync(0xffffffffu, tx0, src), s_ty0 = __shfl_sync(0xffffffffu, ty0, src);
+    const int s_fb = __shfl_sync(0xffffffffu, fbase, src), s_tx = __shfl_sync(0xffffffffu, tiles_x, src);
+    const uint32_t s_klo = __shfl_sync(0xffffffffu, klo, src), s_khi = __shfl_sync(0xffffffffu, khi, src);
+    unsigned long long pos = __shfl_sync(0xffffffffu, first, src);
+    for (int j0 = 0; j0 < s_area; j0 += 32) {
+      const int j = j0 + lane;
+      int t = 0;
+      bool on = false;
+      if (j < s_area) {
+        const int yy = j / s_rw;
+        t = s_fb + (s_ty0 + yy) * s_tx + s_tx0 + (j - yy * s_rw);
+        on = npix[t] != 0u;
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, on);
+      if (on) {
+        const uint32_t slot = atomicAdd(tcount + t, 1u);
+        const unsigned long long idx = pos + __popc(bal & lanemask_lt());
+        if (idx < (unsigned long long)max_pairs) stage[idx] = make_uint4((uint32_t)t, slot, s_klo, s_khi);
+      }
+      pos += __popc(bal);
+    }
+  }
+}
+
 // --------------------------------------------------------------------------- projection
 // Two stages.  k_cull tests every (frame, Gaussian) with plain FP32 against the near plane
 // and the guard band, with a relative margin so that it never drops a pair the exact test
@@ -183,7 +326,7 @@ __global__ void __launch_bounds__(256) k_cull(GaussPtrs g, Work w, Prm prm, int 
 //   only the unstable ones are binned, into every tile, for the coverage test.
 // kMode = kProjWindow: rtg_window_begin: records only, and every projected candidate is
 //   appended to the window's list (stable Gaussians reach this kernel through the cull).
-// Every pair (candidate, masked tile) is staged as (tile, slot, key): the warp reserves its
+// Every pair (candidate, masked tile) is staged as (tile, slot, key): the block reserves its
 // staging range with one atomic, and each pair's slot in its tile bucket is the value the
 // tile counter returns, so the later scatter into buckets needs no atomics.
 template <int C, int kMode>
@@ -227,13 +370,13 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
         const DevCam &cam = w.cams[f];
         const int tws = kMode == kProjForward ? cam.tws : kTileShift;
         const int ths = kMode == kProjForward ? cam.ths : kTileShift;
-        const int tiles_x = kMode == kProjForward ? cam.tiles_x : cam.mtiles_x;
         tx0 = o.x0 >> tws; tx1 = o.x1 >> tws; ty0 = o.y0 >> ths; ty1 = o.y1 >> ths;
-        const uint32_t *npix = w.tile_npix + (int64_t)f * T;
-        if (kMode != kProjWindow && (kMode != kProjFused || g.unstable[i] != 0))
-          for (int ty = ty0; ty <= ty1; ++ty)
-            for (int tx = tx0; tx <= tx1; ++tx) nt += npix[ty * tiles_x + tx] != 0u;
+        if (kMode == kProjWindow || (kMode == kProjFused && g.unstable[i] == 0)) tx1 = tx0 - 1;  // no pairs
       }
+    }
+    {
+      const int tiles_x = (k < ncand) ? (kMode == kProjForward ? w.cams[f].tiles_x : w.cams[f].mtiles_x) : 0;
+      nt = warp_count_rects(w.tile_npix, tiles_x, f * T, tx0, ty0, tx1, ty1);
     }
     if (kMode == kProjWindow) {  // one atomic per block appends the projected entries
       const unsigned long long slot = block_reserve(w.counters + kWinStable, ok ? 1u : 0u, s_w, &s_base);
@@ -245,25 +388,12 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
       const unsigned long long vbase = block_reserve(w.counters + kVisible, nt > 0 ? 1u : 0u, s_w, &s_base);
       (void)vbase;
     }
+    {
+      const int tiles_x = (k < ncand) ? (kMode == kProjForward ? w.cams[f].tiles_x : w.cams[f].mtiles_x) : 0;
+      warp_stage_rects(w.stage, w.tile_npix, w.tile_count, tiles_x, f * T, tx0, ty0, tx1, ty1, nt, (uint32_t)i,
+                       ok ? __float_as_uint(o.Z) : 0u, first, max_pairs);
+    }
     if (ok && (nt > 0 || kMode == kProjFused || kMode == kProjWindow)) {
-      const DevCam &cam = w.cams[f];
-      const int tiles_x = kMode == kProjForward ? cam.tiles_x : cam.mtiles_x;
-      const uint32_t *npix = w.tile_npix + (int64_t)f * T;
-      uint32_t *tcount = w.tile_count + (int64_t)f * T;
-      const unsigned long long key = ((unsigned long long)__float_as_uint(o.Z) << 32) | (unsigned long long)(uint32_t)i;
-      unsigned long long idx = first;
-      if (nt > 0)  // kProjFused: stable Gaussians get records but no pairs here
-        for (int ty = ty0; ty <= ty1; ++ty)
-          for (int tx = tx0; tx <= tx1; ++tx) {
-            const int t = ty * tiles_x + tx;
-            if (npix[t] != 0u) {
-              const uint32_t slot = atomicAdd(tcount + t, 1u);
-              if (idx < (unsigned long long)max_pairs)
-                w.stage[idx] = make_uint4((uint32_t)((int64_t)f * T + t), slot, (uint32_t)(key & 0xffffffffull),
-                                          (uint32_t)(key >> 32));
-              ++idx;
-            }
-          }
       const int rk = w.rank[i];
       float4 *hot = w.rec_hot + ((int64_t)f * N + i) * H4;
       hot[0] = make_float4(o.mux.hi, o.muy.hi, o.mux.lo, o.muy.lo);
@@ -316,30 +446,14 @@ __global__ void __launch_bounds__(256) k_bin(Work w, int64_t N, int T, int64_t m
         const uint32_t lo = __float_as_uint(c1.z), hi = __float_as_uint(c1.w);
         tx0 = (int)(lo & 0xffffu) >> cam.tws; ty0 = (int)(lo >> 16) >> cam.ths;
         tx1 = (int)(hi & 0xffffu) >> cam.tws; ty1 = (int)(hi >> 16) >> cam.ths;
-        const uint32_t *npix = w.tile_npix + (int64_t)f * T;
-        for (int ty = ty0; ty <= ty1; ++ty)
-          for (int tx = tx0; tx <= tx1; ++tx) nt += npix[ty * tiles_x + tx] != 0u;
       }
     }
+    nt = warp_count_rects(w.tile_npix, tiles_x, f * T, tx0, ty0, tx1, ty1);
     const unsigned long long first = block_reserve(w.counters + kStaged, nt, s_w, &s_base);
     const unsigned long long vbase = block_reserve(w.counters + kVisible, nt > 0 ? 1u : 0u, s_w, &s_base);
     (void)vbase;
-    if (nt > 0) {
-      const int64_t i = (int64_t)e - (int64_t)f * N;
-      const uint32_t *npix = w.tile_npix + (int64_t)f * T;
-      uint32_t *tcount = w.tile_count + (int64_t)f * T;
-      const uint32_t klo = (uint32_t)i, khi = __float_as_uint(c1.x);
-      unsigned long long idx = first;
-      for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1; ++tx) {
-          const int t = ty * tiles_x + tx;
-          if (npix[t] != 0u) {
-            const uint32_t slot = atomicAdd(tcount + t, 1u);
-            if (idx < (unsigned long long)max_pairs) w.stage[idx] = make_uint4((uint32_t)((int64_t)f * T + t), slot, klo, khi);
-            ++idx;
-          }
-        }
-    }
+    warp_stage_rects(w.stage, w.tile_npix, w.tile_count, tiles_x, f * T, tx0, ty0, tx1, ty1, nt,
+                     (uint32_t)((int64_t)e - (int64_t)f * N), __float_as_uint(c1.x), first, max_pairs);
     if (k < total) w.ntiles[e] = nt;
   }
 }
@@ -362,7 +476,14 @@ __device__ __forceinline__ int queue_class(uint32_t n) {
 // masked pixels of each tile (2^gshift groups per tile at most), ordered by the tile's
 // list length, longest first (a counting sort on queue_class; the order within a class
 // is arbitrary and does not affect any result).
-__global__ void __launch_bounds__(1024) k_scan_tiles(Work w, int FT, int64_t max_pairs, int gshift) {
+// With `extra` (an open window's cached stable lists), a tile with masked pixels holds
+// tile_count[t] unstable pairs and extra[t] stable ones: its list length is their sum.
+__device__ __forceinline__ uint32_t list_len(const Work &w, const uint32_t *extra, int t) {
+  return w.tile_count[t] + ((extra != nullptr && w.tile_npix[t] != 0u) ? extra[t] : 0u);
+}
+
+__global__ void __launch_bounds__(1024) k_scan_tiles(Work w, int FT, int64_t max_pairs, int gshift,
+                                                     const uint32_t *__restrict__ extra) {
   __shared__ unsigned long long s_warp[32];
   __shared__ uint32_t s_wmax[32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -371,9 +492,10 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Work w, int FT, int64_t max
   unsigned long long local = 0, npix = 0;
   uint32_t mx = 0;
   for (int t = b; t < e; ++t) {
-    local += w.tile_count[t];
+    const uint32_t len = list_len(w, extra, t);
+    local += len;
     npix += w.tile_npix[t];
-    mx = max(mx, w.tile_count[t]);
+    mx = max(mx, len);
   }
   // inclusive warp scan of `local`
   unsigned long long inc = local;
@@ -400,7 +522,7 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Work w, int FT, int64_t max
   unsigned long long run = (wid > 0 ? s_warp[wid - 1] : 0ull) + inc - local;
   for (int t = b; t < e; ++t) {
     w.tile_offset[t] = (uint32_t)run;
-    run += w.tile_count[t];
+    run += list_len(w, extra, t);
   }
   // total masked pixels
   unsigned long long np = npix;
@@ -412,7 +534,7 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Work w, int FT, int64_t max
     unsigned long long total_pix = 0;
     for (int k = 0; k < 32; ++k) total_pix += s_warp[k];
     // s_warp was overwritten; recompute the pair total from the last offset
-    unsigned long long total = (unsigned long long)w.tile_offset[FT - 1] + w.tile_count[FT - 1];
+    unsigned long long total = (unsigned long long)w.tile_offset[FT - 1] + list_len(w, extra, FT - 1);
     w.tile_offset[FT] = (uint32_t)total;
     w.counters[kPairs] = total;
     w.counters[kMaskedPix] = total_pix;
@@ -429,7 +551,7 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Work w, int FT, int64_t max
   __syncthreads();
   for (int t = b; t < e; ++t) {
     const uint32_t np = w.tile_npix[t];
-    if (np != 0u) atomicAdd(&s_cls[queue_class(w.tile_count[t])], (np + 31u) >> 5);
+    if (np != 0u) atomicAdd(&s_cls[queue_class(list_len(w, extra, t))], (np + 31u) >> 5);
   }
   __syncthreads();
   if (tid == 0) {  // start of each class, classes in decreasing cost
@@ -448,7 +570,7 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Work w, int FT, int64_t max
     const uint32_t np = w.tile_npix[t];
     if (np == 0u) continue;
     const uint32_t ng = (np + 31u) >> 5;
-    const uint32_t pos = atomicAdd(&s_cls[queue_class(w.tile_count[t])], ng);
+    const uint32_t pos = atomicAdd(&s_cls[queue_class(list_len(w, extra, t))], ng);
     for (uint32_t g = 0; g < ng; ++g) w.items[pos + g] = ((uint32_t)t << 3) | g;
   }
 }
@@ -497,7 +619,9 @@ void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, in
   } else {
     k_cull<kCullAll><<<nb, 256, 0, s>>>(g, w, prm, F, nullptr, 0);
   }
-#define RTG_PROJ(CC, MM) k_project<CC, MM><<<kPersistBlocks, 256, 0, s>>>(g, w, prm, T, max_pairs)
+#define RTG_PROJ(CC, MM)                                                                  \
+  k_project<CC, MM><<<resident_grid((const void *)k_project<CC, MM>, 256), 256, 0, s>>>(g, w, prm, T, \
+                                                                                         max_pairs)
 #define RTG_PROJ_C(CC)                              \
   switch (mode) {                                   \
     case kProjForward: RTG_PROJ(CC, kProjForward); break; \
@@ -516,15 +640,41 @@ void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, in
 
 void launch_bin(const Work &w, int64_t N, int T, int64_t max_pairs, bool cands, bool stable, cudaStream_t s) {
   if (N <= 0) return;
-  k_bin<<<kPersistBlocks, 256, 0, s>>>(w, N, T, max_pairs, cands ? 1 : 0, stable ? 1 : 0);
+  k_bin<<<resident_grid((const void *)k_bin, 256), 256, 0, s>>>(w, N, T, max_pairs, cands ? 1 : 0,
+                                                                stable ? 1 : 0);
 }
 
 void launch_window_reset(const Work &w, cudaStream_t s) { k_window_reset<<<1, 1, 0, s>>>(w); }
 
-void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, int gshift, cudaStream_t s) {
-  k_scan_tiles<<<1, 1024, 0, s>>>(w, FT, max_pairs, gshift);
+void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, int gshift, const uint32_t *extra,
+                       cudaStream_t s) {
+  k_scan_tiles<<<1, 1024, 0, s>>>(w, FT, max_pairs, gshift, extra);
 }
 
-void launch_emit(const Work &w, cudaStream_t s) { k_emit<<<kPersistBlocks, 256, 0, s>>>(w); }
+void launch_emit(const Work &w, cudaStream_t s) {
+  k_emit<<<resident_grid((const void *)k_emit, 256), 256, 0, s>>>(w);
+}
+
+int resident_grid(const void *kernel, int block, size_t smem) {
+  struct Entry {
+    const void *kernel;
+    int device, block, grid;
+  };
+  static std::mutex mu;
+  static Entry cache[64];
+  static int n = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  for (int k = 0; k < n; ++k)
+    if (cache[k].kernel == kernel && cache[k].device == dev && cache[k].block == block) return cache[k].grid;
+  int sms = 0, per = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 148;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, block, smem) != cudaSuccess || per < 1) per = 1;
+  cudaGetLastError();
+  const int grid = sms * per;
+  if (n < 64) cache[n++] = Entry{kernel, dev, block, grid};
+  return grid;
+}
 
 }  // namespace rtg

@@ -12,6 +12,12 @@ constexpr int kSortCap = 2048;     // keys a tile-sort CTA sorts entirely in sha
 constexpr int kLossBlocks = 296;   // 2 x 148 SMs
 constexpr int kPersistBlocks = 148 * 8;
 
+// Blocks of `block` threads that one resident wave of `kernel` holds on the current
+// device (SMs x blocks per SM at this kernel's register and shared-memory use).  Grid-
+// stride kernels launched with this grid never queue a second wave of blocks that only
+// find the work already taken.  Cached per kernel.
+int resident_grid(const void *kernel, int block, size_t smem = 0);
+
 // Launch configuration of the render path (the C ABI's rtg_tuning, validated, with the
 // tile sides as shifts).
 struct Tuning {
@@ -97,11 +103,22 @@ void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, in
 // that the fused projection marked projected; with `stable`, the open window's list.
 void launch_bin(const Work &w, int64_t N, int T, int64_t max_pairs, bool cands, bool stable, cudaStream_t s);
 void launch_window_reset(const Work &w, cudaStream_t s);
-// gshift >= 0: also build the persistent schedule's item queue (2^gshift groups per tile)
-void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, int gshift, cudaStream_t s);
+// gshift >= 0: also build the persistent schedule's item queue (2^gshift groups per tile).
+// extra != nullptr: tiles with masked pixels also hold extra[t] cached stable pairs.
+void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, int gshift, const uint32_t *extra,
+                       cudaStream_t s);
 void launch_emit(const Work &w, cudaStream_t s);
 // sort.cu
-void launch_sort_tiles(const Work &w, int FT, int bits, int rank_max, cudaStream_t s);
+// Cached sorted stable lists of an open window (keys == nullptr: none): per tile its
+// count and offset into keys.
+struct StableLists {
+  const unsigned long long *keys;
+  const uint32_t *off;
+  const uint32_t *count;
+};
+// keys_out != nullptr: write each tile's sorted keys there instead of the index lists.
+void launch_sort_tiles(const Work &w, int FT, int bits, int rank_max, const StableLists &sl,
+                       unsigned long long *keys_out, cudaStream_t s);
 void init_sort_attributes();
 // forward.cu
 void launch_forward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn, float *color,

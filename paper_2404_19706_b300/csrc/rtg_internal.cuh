@@ -39,24 +39,27 @@ constexpr float kQScale = 0.84932180028801904272f;   // sqrt(0.5 * log2(e))
 constexpr float kLn2 = 0.69314718055994530942f;
 constexpr float kQScale2 = 0.72134752044448170368f;  // kQScale^2 = 0.5 * log2(e)
 
-// Counter slots in Work::counters (uint64).
+// Counter slots in Work::counters (uint64).  Each counter sits on its own 128-byte line:
+// thousands of blocks reserve staging ranges with atomics on them in the same kernels, and
+// atomics on one line serialise in one L2 slice even when their addresses differ.
+constexpr int kCounterStride = 16;  // uint64 per 128-byte line
 enum Counter {
-  kPairs = 0,
-  kFragments = 1,
-  kVisible = 2,
-  kMaskedPix = 3,
-  kNumUnstable = 4,
-  kMaxTilePairs = 5,
-  kSkip = 6,  // non-zero: pairs overflowed, downstream kernels skip
-  kCand = 7,  // (frame, Gaussian) candidates that passed the coarse cull
-  kStaged = 8,  // (Gaussian, tile) pairs staged by the projection for the scatter into buckets
-  kItems = 9,   // (tile, 32-pixel group) work items of the persistent schedule
-  kQFwd = 10,   // next item of the persistent forward (past the first one per warp)
-  kQBwd = 11,   // next item of the persistent backward
-  kNumReset = 15,   // slots below this are cleared at the start of every call
-  kWinStable = 15,  // projected (frame, stable Gaussian) entries of the open window (kept)
-  kNumCounters = 16
+  kPairs = 0 * kCounterStride,
+  kFragments = 1 * kCounterStride,
+  kVisible = 2 * kCounterStride,
+  kMaskedPix = 3 * kCounterStride,
+  kNumUnstable = 4 * kCounterStride,
+  kMaxTilePairs = 5 * kCounterStride,
+  kSkip = 6 * kCounterStride,         // non-zero: pairs overflowed, downstream kernels skip
+  kCand = 7 * kCounterStride,         // (frame, Gaussian) candidates that passed the coarse cull
+  kStaged = 8 * kCounterStride,       // (Gaussian, tile) pairs staged for the scatter into buckets
+  kItems = 9 * kCounterStride,        // (tile, 32-pixel group) work items of the persistent schedule
+  kQFwd = 10 * kCounterStride,        // next item of the persistent forward (past the first one per warp)
+  kQBwd = 11 * kCounterStride,        // next item of the persistent backward
+  kWinStable = 15 * kCounterStride,   // projected (frame, stable Gaussian) entries of the open window (kept)
 };
+constexpr int kNumCounterSlots = 16;  // slots; all but kWinStable are cleared at the start of every call
+constexpr int kNumCounters = kNumCounterSlots * kCounterStride;  // array length
 
 struct DevCam {
   float fx, fy, cx, cy;

@@ -139,8 +139,32 @@ __device__ __forceinline__ void scatter_chunk(const unsigned long long *src, int
 }  // namespace
 
 
+// Number of keys of the ascending array a[0..n) that are smaller than k.
+__device__ __forceinline__ uint32_t count_below(const unsigned long long *a, uint32_t n, unsigned long long k) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (a[mid] < k) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Writes list entry `pos` of the tile: the Gaussian index, or the whole key (keys_out).
+__device__ __forceinline__ void put(const Work &w, unsigned long long *keys_out, uint32_t off, uint32_t pos,
+                                    unsigned long long k) {
+  if (keys_out != nullptr) keys_out[off + pos] = k;
+  else w.sorted[off + pos] = (uint32_t)k;
+}
+
+// One CTA per tile.  The tile's bucket keys[off, off + n_b) is sorted (radix passes, or
+// ranking for short buckets).  With cached stable lists (an open optimisation window),
+// the bucket holds the unstable pairs only and the tile's list is the merge of the sorted
+// bucket with the cached, sorted stable keys of the tile: a key's position is its index in
+// its own list plus the number of smaller keys in the other (all keys are distinct).
 template <int kBits>
-__global__ void __launch_bounds__(kSortThreads) k_sort_tiles(Work w, int rank_max) {
+__global__ void __launch_bounds__(kSortThreads) k_sort_tiles(Work w, int rank_max, StableLists sl,
+                                                             unsigned long long *keys_out) {
   constexpr int kRadix = 1 << kBits;
   constexpr unsigned long long kMask = (unsigned long long)(kRadix - 1);
   if (w.counters[kSkip] != 0ull) return;
@@ -150,63 +174,89 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(Work w, int rank_ma
   const uint32_t off = w.tile_offset[tile];
   const uint32_t n = w.tile_offset[tile + 1] - off;
   if (n == 0) return;
-  if (n <= (uint32_t)rank_max) {  // distinct keys: position = number of smaller keys
-    for (uint32_t j = threadIdx.x; j < n; j += kSortThreads) s.a[j] = w.keys[off + j];
+  const uint32_t nb = sl.keys != nullptr ? w.tile_count[tile] : n;  // bucket (unstable) keys
+  const uint32_t ns = n - nb;                                        // cached stable keys
+  const unsigned long long *sorted_b = nullptr;                      // the sorted bucket
+  if (nb == 0) {
+    // nothing to sort
+  } else if (nb <= (uint32_t)rank_max) {  // distinct keys: position = number of smaller keys
+    for (uint32_t j = threadIdx.x; j < nb; j += kSortThreads) s.a[j] = w.keys[off + j];
     __syncthreads();
-    for (uint32_t j = threadIdx.x; j < n; j += kSortThreads) {
+    for (uint32_t j = threadIdx.x; j < nb; j += kSortThreads) {
       const unsigned long long k = s.a[j];
       uint32_t pos = 0;
-      for (uint32_t i = 0; i < n; ++i) pos += s.a[i] < k ? 1u : 0u;
-      w.sorted[off + pos] = (uint32_t)k;
+      for (uint32_t i = 0; i < nb; ++i) pos += s.a[i] < k ? 1u : 0u;
+      s.b[pos] = k;
     }
-    return;
-  }
-  if (n <= (uint32_t)kSortCap) {
-    for (uint32_t j = threadIdx.x; j < n; j += kSortThreads) s.a[j] = w.keys[off + j];
+    __syncthreads();
+    sorted_b = s.b;
+  } else if (nb <= (uint32_t)kSortCap) {
+    for (uint32_t j = threadIdx.x; j < nb; j += kSortThreads) s.a[j] = w.keys[off + j];
     __syncthreads();
     unsigned long long vary;
-    varying_bits(s.a, n, s, vary);
+    varying_bits(s.a, nb, s, vary);
     unsigned long long *cur = s.a, *oth = s.b;
     for (int shift = 0; shift < 64; shift += kBits) {
       if (((vary >> shift) & kMask) == 0ull) continue;
-      rank_digits<kBits>(cur, (int)n, shift, s);
+      rank_digits<kBits>(cur, (int)nb, shift, s);
       scan_digits<kRadix>(s.tot, s.base, s);
-      scatter_chunk<kBits>(cur, (int)n, shift, s.base, oth, s);
+      scatter_chunk<kBits>(cur, (int)nb, shift, s.base, oth, s);
       __syncthreads();
       unsigned long long *t = cur;
       cur = oth;
       oth = t;
     }
-    for (uint32_t j = threadIdx.x; j < n; j += kSortThreads) w.sorted[off + j] = (uint32_t)cur[j];
-    return;
-  }
-  // long bucket: chunked passes through global memory
-  unsigned long long *src = w.keys + off, *dst = w.keys_alt + off;
-  unsigned long long vary;
-  varying_bits(src, n, s, vary);
-  for (int shift = 0; shift < 64; shift += kBits) {
-    if (((vary >> shift) & kMask) == 0ull) continue;
-    if ((int)threadIdx.x < kRadix) s.tot[threadIdx.x] = 0u;
-    __syncthreads();
-    for (uint32_t j = threadIdx.x; j < n; j += kSortThreads) atomicAdd(&s.tot[(unsigned)((src[j] >> shift) & kMask)], 1u);
-    __syncthreads();
-    scan_digits<kRadix>(s.tot, s.run, s);
-    for (uint32_t c0 = 0; c0 < n; c0 += kSortCap) {
-      const int m = (int)min((uint32_t)kSortCap, n - c0);
-      for (int j = threadIdx.x; j < m; j += kSortThreads) s.a[j] = src[c0 + j];
+    sorted_b = cur;
+  } else {
+    // long bucket: chunked passes through global memory
+    unsigned long long *src = w.keys + off, *dst = w.keys_alt + off;
+    unsigned long long vary;
+    varying_bits(src, nb, s, vary);
+    for (int shift = 0; shift < 64; shift += kBits) {
+      if (((vary >> shift) & kMask) == 0ull) continue;
+      if ((int)threadIdx.x < kRadix) s.tot[threadIdx.x] = 0u;
       __syncthreads();
-      rank_digits<kBits>(s.a, m, shift, s);
-      scatter_chunk<kBits>(s.a, m, shift, s.run, dst, s);
+      for (uint32_t j = threadIdx.x; j < nb; j += kSortThreads)
+        atomicAdd(&s.tot[(unsigned)((src[j] >> shift) & kMask)], 1u);
       __syncthreads();
-      if ((int)threadIdx.x < kRadix) s.run[threadIdx.x] += s.tot[threadIdx.x];
+      scan_digits<kRadix>(s.tot, s.run, s);
+      for (uint32_t c0 = 0; c0 < nb; c0 += kSortCap) {
+        const int m = (int)min((uint32_t)kSortCap, nb - c0);
+        for (int j = threadIdx.x; j < m; j += kSortThreads) s.a[j] = src[c0 + j];
+        __syncthreads();
+        rank_digits<kBits>(s.a, m, shift, s);
+        scatter_chunk<kBits>(s.a, m, shift, s.run, dst, s);
+        __syncthreads();
+        if ((int)threadIdx.x < kRadix) s.run[threadIdx.x] += s.tot[threadIdx.x];
+        __syncthreads();
+      }
+      unsigned long long *t = src;
+      src = dst;
+      dst = t;
       __syncthreads();
     }
-    unsigned long long *t = src;
-    src = dst;
-    dst = t;
-    __syncthreads();
+    sorted_b = src;
   }
-  for (uint32_t j = threadIdx.x; j < n; j += kSortThreads) w.sorted[off + j] = (uint32_t)src[j];
+  if (ns == 0) {
+    for (uint32_t j = threadIdx.x; j < nb; j += kSortThreads) put(w, keys_out, off, j, sorted_b[j]);
+    return;
+  }
+  // merge with the tile's cached stable keys (staged in the free shared buffer if they fit)
+  const unsigned long long *sk = sl.keys + sl.off[tile];
+  unsigned long long *freebuf = sorted_b == s.a ? s.b : s.a;
+  if (ns <= (uint32_t)kSortCap) {
+    for (uint32_t j = threadIdx.x; j < ns; j += kSortThreads) freebuf[j] = sk[j];
+    __syncthreads();
+    sk = freebuf;
+  }
+  for (uint32_t j = threadIdx.x; j < nb; j += kSortThreads) {
+    const unsigned long long k = sorted_b[j];
+    put(w, keys_out, off, j + count_below(sk, ns, k), k);
+  }
+  for (uint32_t j = threadIdx.x; j < ns; j += kSortThreads) {
+    const unsigned long long k = sk[j];
+    put(w, keys_out, off, j + count_below(sorted_b, nb, k), k);
+  }
 }
 
 void init_sort_attributes() {
@@ -214,11 +264,12 @@ void init_sort_attributes() {
   cudaFuncSetAttribute(k_sort_tiles<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SortSmem));
 }
 
-void launch_sort_tiles(const Work &w, int FT, int bits, int rank_max, cudaStream_t s) {
+void launch_sort_tiles(const Work &w, int FT, int bits, int rank_max, const StableLists &sl,
+                       unsigned long long *keys_out, cudaStream_t s) {
   if (bits == 4)
-    k_sort_tiles<4><<<FT, kSortThreads, sizeof(SortSmem), s>>>(w, rank_max);
+    k_sort_tiles<4><<<FT, kSortThreads, sizeof(SortSmem), s>>>(w, rank_max, sl, keys_out);
   else
-    k_sort_tiles<8><<<FT, kSortThreads, sizeof(SortSmem), s>>>(w, rank_max);
+    k_sort_tiles<8><<<FT, kSortThreads, sizeof(SortSmem), s>>>(w, rank_max, sl, keys_out);
 }
 
 }  // namespace rtg

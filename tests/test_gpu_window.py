@@ -53,11 +53,14 @@ def render(ctx, g, cams, tc, td, masks, nu, fused, C=3):
 
 
 def same(a, b):
+    """b (a window forward) equals a (a full forward).  With the window's cached lists only
+    the unstable projections count as visible."""
     for k in ("mask", "color", "depth", "alpha", "index"):
         assert torch.equal(a[k], b[k]), k
     np.testing.assert_allclose(a["loss"].cpu().numpy(), b["loss"].cpu().numpy(), rtol=1e-6)
-    for k in ("pairs", "fragments", "visible", "masked_pixels"):
+    for k in ("pairs", "fragments", "masked_pixels", "max_tile_pairs"):
         assert a["stats"][k] == b["stats"][k], k
+    assert 0 < b["stats"]["visible"] <= a["stats"]["visible"]
     for x, y in zip(a["grads"], b["grads"]):
         x, y = x.cpu().numpy(), y.cpu().numpy()
         assert np.abs(x - y).max(initial=0) <= 2e-5 * max(np.abs(x).max(initial=0), 1e-30)
@@ -155,3 +158,40 @@ def test_masked_step_with_and_without_window_agree():
     d = np.abs(out[1][1] - out[0][1])
     assert np.mean(d > 1e-6) < 0.01 and d.max() <= 6 * 2 * 1e-3 + 1e-6
     assert out[0][0][-1, 0] < out[0][0][0, 0]  # the loss goes down
+
+
+def test_window_lists_follow_the_render_tile():
+    """Changing the render tile rebuilds the window's cached stable lists for the new grid."""
+    m = rtg()
+    ctx, g, cams, tc, td, masks, nu = setup(5600)
+    ref_ctx = ctx_for(g.n, cams)
+    m.window_begin(ctx, cams, g, m.RenderSettings())
+    for t in (m.Tuning(8, 16, schedule=1), m.Tuning(32, 8, 64), m.Tuning(16, 16, sort_rank_max=512)):
+        ctx.set_tuning(t)
+        ref_ctx.set_tuning(t)
+        assert m.window_is_open(ctx)
+        for fused in (False, True):
+            same(render(ref_ctx, g, cams, tc, td, masks, nu, fused), render(ctx, g, cams, tc, td, masks, nu, fused))
+
+
+def test_window_too_large_for_lists_keeps_projections_only():
+    """A pair capacity that holds a masked forward but not the stable Gaussians' whole-frame
+    lists: the window keeps its projections only, and forwards stay exact."""
+    m = rtg()
+    ctx0, g, cams, tc, td, _, nu = setup(5700)
+    small = torch.as_tensor(synth.random_masks(5710, F, H, W, 0.03, 0.08)).cuda()
+    full = render(ctx0, g, cams, tc, td, small, nu, fused=False)
+    probe = ctx_for(g.n, cams)
+    c = torch.zeros(F, 3, H, W, device="cuda")
+    d = torch.zeros(F, H, W, device="cuda")
+    a = torch.zeros(F, H, W, device="cuda")
+    m.render_forward(probe, cams, g, None, m.RenderSettings(), c, d, a)  # whole frames
+    ids = m.debug_binning(probe, F, W, H, g.n)["sorted_ids"]
+    stable_whole = int((g.unstable.cpu().numpy()[ids.astype(np.int64)] == 0).sum())
+    masked = full["stats"]["pairs"]
+    assert stable_whole > masked + 2, (stable_whole, masked)
+    ctx = ctx_for(g.n, cams, max_pairs=(stable_whole + masked) // 2)
+    m.window_begin(ctx, cams, g, m.RenderSettings())
+    assert m.window_is_open(ctx) and m.get_status(ctx) == 0
+    win = render(ctx, g, cams, tc, td, small, nu, fused=False)
+    same(full, win)
