@@ -37,7 +37,14 @@ KF_METRIC = "batched keyframe fwd+bwd frames/sec at 1200×680 (8 keyframes in on
 KEYFRAMES = dict(name="batched keyframes: 8 x 1200x680 (f 600), multi-room 12x10x3 m (2x2 rooms, 40 boxes), "
                       "2M Gaussians (10% unstable, 8 blobs), mask coverage 10-60%",
                  seed=4000, n=2_000_000, n_unstable=200_000, blobs=8, frames=8, width=1200, height=680, f=600.0,
-                 coverage=(0.10, 0.60), max_pairs=48 << 20)
+                 coverage=(0.10, 0.60), bands=4, max_pairs=48 << 20, channels=3, opaque=0.85,
+                 size=(12.0, 10.0, 3.0), grid=(2, 2), boxes=40, per_frame=True, metric=KF_METRIC)
+LARGE_METRIC = "large-scene batched fwd+bwd iterations/sec and fragments/sec (32 keyframes at 1200×680, 5M Gaussians)"
+LARGE = dict(name="large floor: 32 x 1200x680 (f 600), 30x20x3 m (5x4 rooms, 60 boxes), 5M Gaussians (90% opaque, "
+                  "8 channels, 10% unstable in 24 blobs), mask coverage 5-50%",
+             seed=5000, n=5_000_000, n_unstable=500_000, blobs=24, frames=32, width=1200, height=680, f=600.0,
+             coverage=(0.05, 0.50), bands=4, max_pairs=128 << 20, channels=8, opaque=0.9, size=(30.0, 20.0, 3.0),
+             grid=(5, 4), boxes=60, per_frame=False, metric=LARGE_METRIC)
 C = 3
 
 
@@ -51,9 +58,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--candidate", type=int, default=-1, help="camera candidate index (-1: search)")
-    ap.add_argument("--workload", default="masked-step", choices=["masked-step", "keyframes"],
+    ap.add_argument("--workload", default="masked-step", choices=["masked-step", "keyframes", "large"],
                     help="masked-step: the 640x480 masked iteration (default); keyframes: 8 batched 1200x680 "
-                         "keyframes vs per-frame launches")
+                         "keyframes vs per-frame launches; large: 32 batched 1200x680 keyframes, 5M Gaussians, "
+                         "8 channels")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--tune-table", default="", help="write the autotuner's candidate table (JSON) to this path")
     ap.add_argument("--tuning", default="",
@@ -560,21 +568,23 @@ def torch_zeros(shape, dev):
     return torch.zeros(shape, device=dev)
 
 
-def keyframes_workload(rtg, dev, settings):
+def keyframes_workload(rtg, dev, settings, kw):
     """Scene, unstable flags, the F keyframes (coverage spread over the range) and targets."""
     import torch
-    kw = KEYFRAMES
-    F, H, W = kw["frames"], kw["height"], kw["width"]
+    F, H, W, Cc = kw["frames"], kw["height"], kw["width"], kw["channels"]
     t0 = time.perf_counter()
-    scene, layout = synth.multiroom_scene(kw["seed"], kw["n"])
+    scene, layout = synth.room_scene(kw["seed"], kw["n"], channels=Cc, opaque_frac=kw["opaque"], size=kw["size"],
+                                     grid=kw["grid"], n_boxes=kw["boxes"])
     scene.unstable = synth.flag_blobs(scene, [], kw["n_unstable"], kw["blobs"], seed=kw["seed"] + 100, n_in_view=0)
     print(f"keyframes: scene {time.perf_counter() - t0:.1f} s", file=sys.stderr)
-    ctx = rtg.Context(max_gaussians=scene.n, max_frames=F, max_width=W, max_height=H, max_pairs=kw["max_pairs"])
+    ctx = rtg.Context(max_gaussians=scene.n, max_frames=F, max_width=W, max_height=H, max_channels=Cc,
+                      max_pairs=kw["max_pairs"])
     g = rtg.Gaussians.from_scene(scene, device=dev)
     cams = synth.room_camera_candidates(kw["seed"] + 1, layout, W, H, kw["f"])
     lo, hi = kw["coverage"]
-    edges = np.linspace(lo, hi, F // 2 + 1)  # two frames per coverage band, for uneven masks
-    per_band = {b: [] for b in range(F // 2)}
+    nb = kw["bands"]
+    edges = np.linspace(lo, hi, nb + 1)  # F / bands frames per coverage band, for uneven masks
+    per_band = {b: [] for b in range(nb)}
     masks = torch.zeros(F, H, W, dtype=torch.uint8, device=dev)
     drawn = 0
     while sum(len(v) for v in per_band.values()) < F and drawn < 64 * F:
@@ -584,17 +594,17 @@ def keyframes_workload(rtg, dev, settings):
         covs = masks.float().mean(dim=(1, 2)).tolist()
         for c, v in zip(batch, covs):
             if lo <= v <= hi:
-                bnd = min(int(np.searchsorted(edges, v, side="right")) - 1, F // 2 - 1)
-                if len(per_band[bnd]) < 2:
+                bnd = min(int(np.searchsorted(edges, v, side="right")) - 1, nb - 1)
+                if len(per_band[bnd]) < F // nb:
                     per_band[bnd].append((c, v))
-    chosen = [cv for b in range(F // 2) for cv in per_band[b]]
+    chosen = [cv for b in range(nb) for cv in per_band[b]]
     assert len(chosen) == F, f"only {len(chosen)} keyframes with coverage in [{lo}, {hi}] after {drawn} poses"
     kcams = [c for c, _ in chosen]
     rtg.unstable_mask(ctx, kcams, g, settings, masks)
     covs = masks.float().mean(dim=(1, 2)).tolist()
     target = synth.jitter_scene(scene, kw["seed"] + 7)
     gt = rtg.Gaussians.from_scene(target, device=dev)
-    tcol = torch.zeros(F, C, H, W, device=dev)
+    tcol = torch.zeros(F, Cc, H, W, device=dev)
     tdep = torch.full((F, H, W), -1.0, device=dev)
     talp = torch.zeros(F, H, W, device=dev)
     for f in range(F):  # full frames, one at a time (the largest pair count of the run)
@@ -608,8 +618,9 @@ def keyframes_workload(rtg, dev, settings):
     return scene, ctx, kcams, covs, tcol, tdep
 
 
-def run_keyframes(args):
-    """Batched keyframes: one graph over F frames vs F per-frame launch sequences."""
+def run_keyframes(args, kw):
+    """Batched keyframes: one graph over F frames, and (kw["per_frame"]) F per-frame launch
+    sequences of the same iteration for comparison."""
     import torch
     import paper_2404_19706_b300 as rtg
     rank = int(os.environ.get("RANK", "0"))
@@ -618,9 +629,9 @@ def run_keyframes(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     settings = rtg.RenderSettings()
-    kw = KEYFRAMES
-    F, H, W = kw["frames"], kw["height"], kw["width"]
-    scene, ctx, kcams, covs, tcol, tdep = keyframes_workload(rtg, dev, settings)
+    F, H, W, Cc = kw["frames"], kw["height"], kw["width"], kw["channels"]
+    torch.cuda.reset_peak_memory_stats(dev)
+    scene, ctx, kcams, covs, tcol, tdep = keyframes_workload(rtg, dev, settings, kw)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
@@ -639,40 +650,13 @@ def run_keyframes(args):
         return [ckb["mask"], ckb["color"], ckb["depth"], ckb["alpha"]]
 
     tuned_b = run_tuner(ctx, batched._body, check_b, step_state(batched), args, "batched")
-
-    # per frame: the same iteration as F single-frame call sequences, one context per frame
-    ctxs = [rtg.Context(max_gaussians=scene.n, max_frames=1, max_width=W, max_height=H,
-                        max_pairs=kw["max_pairs"] // 4) for _ in range(F)]
-    ctx1 = ctxs[0]
-    masks_p = torch.zeros(F, H, W, dtype=torch.uint8, device=dev)
-    gp = rtg.Gaussians.from_scene(scene, device=dev)
-    perframe = PerFrameStep(rtg, ctxs, gp, kcams, masks_p, tcol, tdep, settings)
-    ckp = dict(mask=torch.zeros(1, H, W, dtype=torch.uint8, device=dev), color=torch.zeros(1, C, H, W, device=dev),
-               depth=torch.zeros(1, H, W, device=dev), alpha=torch.zeros(1, H, W, device=dev))
-
-    def check_p():
-        for t in ckp.values():
-            t.zero_()
-        rtg.render_forward_masked(ctx1, [kcams[0]], perframe.g, settings, ckp["mask"], ckp["color"], ckp["depth"],
-                                  ckp["alpha"])
-        return [ckp["mask"], ckp["color"], ckp["depth"], ckp["alpha"]]
-
-    tuned_p = run_tuner(ctxs, perframe._body, check_p, step_state(perframe), args, "per_frame")
-
-    # before any optimiser step the two arms render the same thing: the batched call gives
-    # every frame bit for bit what a call with that frame alone gives (masks and images)
-    check_b()
-    for f in range(F):
-        for t in ckp.values():  # outputs are written on masked pixels only
-            t.zero_()
-        rtg.render_forward_masked(ctxs[f], [kcams[f]], perframe.g, settings, ckp["mask"], ckp["color"],
-                                  ckp["depth"], ckp["alpha"])
-        for k in ("mask", "color", "depth", "alpha"):
-            assert torch.equal(ckp[k][0], ckb[k][f]), f"frame {f}: batched and per-frame {k} differ"
-    torch.cuda.synchronize()
+    arms = [("batched", batched, [ctx])]
+    if kw["per_frame"]:
+        arms.append(per_frame_arm(rtg, args, kw, scene, kcams, tcol, tdep, settings, check_b, ckb))
+    tuned_p = arms[1][3] if len(arms) > 1 else None
 
     results = {}
-    for name, st, cs in (("batched", batched, [ctx]), ("per_frame", perframe, ctxs)):
+    for name, st, cs, *_ in arms:
         for _ in range(args.warmup):
             st.step()
         torch.cuda.synchronize()
@@ -684,10 +668,12 @@ def run_keyframes(args):
         ms, wall, clocks = timed_replays(st, args.steps, flush, stream, local)
         assert all(rtg.get_status(c) == 0 for c in cs), name
         results[name] = dict(ms=ms, wall=wall, clocks=clocks, stats=rtg.get_stats(cs[0]))
+    peak_torch = torch.cuda.max_memory_allocated(dev)
+    workspace = sum(c.workspace_bytes() for _, _, cs, *_ in arms for c in cs)
 
     per_launch = kernel_profile(rtg, ctx, batched, args.steps, flush, stream)
     sb = results["batched"]["stats"]
-    alg = alg_bytes(sb, scene.n, F, H, W)
+    alg = alg_bytes(sb, scene.n, F, H, W, Cc)
     roofline, pk = roofline_of(per_launch, alg, ctx.get_tuning())
     b_step = sum(alg.values())
 
@@ -712,36 +698,83 @@ def run_keyframes(args):
 
     if rank != 0:
         return None
-    msb, msp = results["batched"]["ms"], results["per_frame"]["ms"]
-    return {
-        "metric": KF_METRIC, "value": round(F * 1e3 / msb, 2), "unit": "frames/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(msb, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": kw["name"], "gaussians": scene.n, "unstable": sb["n_unstable"], "frames": F,
-                   "width": W, "height": H, "mask_coverage": [round(c, 4) for c in covs],
-                   "masked_pixels": sb["masked_pixels"], "pairs": sb["pairs"], "visible": sb["visible"],
-                   "fragments_per_step": sb["fragments"],
-                   "fragments_per_sec": round(sb["fragments"] * 1e3 / msb, 1),
-                   "alg_bytes_per_step": int(b_step),
-                   "step_hbm_roofline_frac": round(b_step / (msb * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
-                   "tuning": ctx.get_tuning().as_dict(),
-                   "autotune": tuned_b.summary() if tuned_b is not None else ("fixed by --tuning" if args.tuning else "off (--no-tune)"),
-                   "per_frame": {"value": round(F * 1e3 / msp, 2), "unit": "frames/s", "ms_per_step": round(msp, 4),
-                                 "tuning": ctx1.get_tuning().as_dict(),
-                                 "autotune": tuned_p.summary() if tuned_p is not None else ("fixed by --tuning" if args.tuning else "off (--no-tune)"),
-                                 "gpu_launches_per_step": kernels_per_step(results["per_frame"]["stats"], F)},
-                   "batched_over_per_frame": round(msp / msb, 3),
-                   "l2": "256 MB buffer written before every step, outside the timed spans",
+    msb = results["batched"]["ms"]
+    fixed = "fixed by --tuning" if args.tuning else "off (--no-tune)"
+    config = {"workload": kw["name"], "gaussians": scene.n, "unstable": sb["n_unstable"], "frames": F,
+              "channels": Cc, "width": W, "height": H, "mask_coverage": [round(c, 4) for c in covs],
+              "masked_pixels": sb["masked_pixels"], "pairs": sb["pairs"], "visible": sb["visible"],
+              "fragments_per_step": sb["fragments"], "fragments_per_sec": round(sb["fragments"] * 1e3 / msb, 1),
+              "alg_bytes_per_step": int(b_step),
+              "step_hbm_roofline_frac": round(b_step / (msb * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
+              "peak_hbm_gb": {"library_workspaces": round(workspace / 1e9, 2),
+                              "torch_tensors_peak": round(peak_torch / 1e9, 2)},
+              "tuning": ctx.get_tuning().as_dict(),
+              "autotune": tuned_b.summary() if tuned_b is not None else fixed}
+    if kw["per_frame"]:
+        msp = results["per_frame"]["ms"]
+        ctx1 = arms[1][2][0]
+        config["per_frame"] = {"value": round(F * 1e3 / msp, 2), "unit": "frames/s", "ms_per_step": round(msp, 4),
+                               "tuning": ctx1.get_tuning().as_dict(),
+                               "autotune": tuned_p.summary() if tuned_p is not None else fixed,
+                               "gpu_launches_per_step": kernels_per_step(results["per_frame"]["stats"], F)}
+        config["batched_over_per_frame"] = round(msp / msb, 3)
+    config.update({"l2": "256 MB buffer written before every step, outside the timed spans",
                    "timing": "each arm replays one CUDA graph of its whole step (F-frame calls, or F single-frame "
                              "call sequences); kernel_ms_per_launch from a live eager pass of the batched step",
                    "kernel_ms_per_launch": {k: round(v, 5) for k, v in per_launch.items()},
-                   "parallelism": "replicas x1"},
+                   "parallelism": "replicas x1"})
+    per_frame_metric = kw["per_frame"]
+    return {
+        "metric": kw["metric"],
+        "value": round(F * 1e3 / msb, 2) if per_frame_metric else round(1e3 / msb, 3),
+        "unit": "frames/s" if per_frame_metric else "iter/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(msb, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
         "roofline": roofline,
-        "e2e": {"value": round(F * 1e3 / e2e_step, 2), "unit": "frames/s",
+        "e2e": {"value": round(F * 1e3 / e2e_step, 2) if per_frame_metric else round(1e3 / e2e_step, 3),
+                "unit": "frames/s" if per_frame_metric else "iter/s",
                 "h2d_bytes_per_step": int(hc.numel() * 4 + hd.numel() * 4), "d2h_bytes_per_step": 12},
         "gpu_launches": kernels_per_step(sb) * args.steps,
         "clocks": results["batched"]["clocks"].summary(),
     }
+
+
+def per_frame_arm(rtg, args, kw, scene, kcams, tcol, tdep, settings, check_b, ckb):
+    """The same iteration as F single-frame call sequences, one context (and window) per
+    frame; checked against the batched arm before any optimiser step."""
+    import torch
+    F, H, W, Cc = kw["frames"], kw["height"], kw["width"], kw["channels"]
+    dev = tcol.device
+    ctxs = [rtg.Context(max_gaussians=scene.n, max_frames=1, max_width=W, max_height=H, max_channels=Cc,
+                        max_pairs=kw["max_pairs"] // 4) for _ in range(F)]
+    ctx1 = ctxs[0]
+    masks_p = torch.zeros(F, H, W, dtype=torch.uint8, device=dev)
+    gp = rtg.Gaussians.from_scene(scene, device=dev)
+    perframe = PerFrameStep(rtg, ctxs, gp, kcams, masks_p, tcol, tdep, settings)
+    ckp = dict(mask=torch.zeros(1, H, W, dtype=torch.uint8, device=dev), color=torch.zeros(1, Cc, H, W, device=dev),
+               depth=torch.zeros(1, H, W, device=dev), alpha=torch.zeros(1, H, W, device=dev))
+
+    def check_p():
+        for t in ckp.values():
+            t.zero_()
+        rtg.render_forward_masked(ctx1, [kcams[0]], perframe.g, settings, ckp["mask"], ckp["color"], ckp["depth"],
+                                  ckp["alpha"])
+        return [ckp["mask"], ckp["color"], ckp["depth"], ckp["alpha"]]
+
+    tuned_p = run_tuner(ctxs, perframe._body, check_p, step_state(perframe), args, "per_frame")
+
+    # before any optimiser step the two arms render the same thing: the batched call gives
+    # every frame bit for bit what a call with that frame alone gives (masks and images)
+    check_b()
+    for f in range(F):
+        for t in ckp.values():  # outputs are written on masked pixels only
+            t.zero_()
+        rtg.render_forward_masked(ctxs[f], [kcams[f]], perframe.g, settings, ckp["mask"], ckp["color"],
+                                  ckp["depth"], ckp["alpha"])
+        for k in ("mask", "color", "depth", "alpha"):
+            assert torch.equal(ckp[k][0], ckb[k][f]), f"frame {f}: batched and per-frame {k} differ"
+    torch.cuda.synchronize()
+    return ("per_frame", perframe, ctxs, tuned_p)
 
 
 def cpu_baseline_from_gpu(scene, cam, mask, tcol, tdep, n_masked):
@@ -813,11 +846,11 @@ DEFAULT_CANDIDATE = 7  # first pose of the seeded stream with 25-40% mask covera
 def main():
     args = parse()
     if args.steps <= 0:
-        args.steps = 60 if args.workload == "keyframes" else 400
+        args.steps = {"keyframes": 60, "large": 20}.get(args.workload, 400)
     if args.impl == "reference":
         out = run_reference(args)
-    elif args.workload == "keyframes":
-        out = run_keyframes(args)
+    elif args.workload in ("keyframes", "large"):
+        out = run_keyframes(args, KEYFRAMES if args.workload == "keyframes" else LARGE)
     else:
         out = run_ours(args)
     if out is not None:
