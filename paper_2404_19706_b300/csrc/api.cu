@@ -125,13 +125,15 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
   size_t cams, counters, rank, ids, block_cnt, cand, rec_hot, rec_cold, rec_box, ntiles, tile_npix, tile_count, tile_offset,
       tile_cursor, keys, keys_alt, stage, sorted, px_T, px_last, px_hit, grad2d, loss_part, loss_scal, loss_done, tile_loss,
-      px_list, items, scand, win_scount, win_soff, win_skeys, total;
+      px_list, items, scand, win_scount, win_soff, win_skeys, scan_part, scan_hist, total;
 };
 
 bool capacity_ok(const rtg_capacity *c) {
   return c != nullptr && c->max_gaussians >= 0 && c->max_frames >= 1 && c->max_frames <= RTG_MAX_FRAMES &&
          c->max_width >= 1 && c->max_height >= 1 && (c->max_channels == 3 || c->max_channels == 8) &&
          c->max_pairs >= 1 && c->max_pairs <= 0xffffffffLL && c->max_width <= 32768 && c->max_height <= 32768 &&
+         (int64_t)c->max_frames * ((c->max_width + 7) / 8) * ((c->max_height + 7) / 8) <=
+             (int64_t)1024 * kScanBlockTiles &&
          (int64_t)c->max_frames * c->max_gaussians < 0xffffffffLL;
 }
 
@@ -186,6 +188,9 @@ Layout layout_of(const rtg_capacity *c) {
   L.win_scount = take((FT + 1) * 4);
   L.win_soff = take((FT + 1) * 4);
   L.win_skeys = take(K * 8);
+  const size_t scan_blocks = (FT + kScanBlockTiles - 1) / kScanBlockTiles + 1;
+  L.scan_part = take(scan_blocks * 4 * 8);
+  L.scan_hist = take(scan_blocks * kQueueClasses * 4);
   L.total = o;
   return L;
 }
@@ -451,6 +456,8 @@ rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap) {
   ctx->win_scount = (uint32_t *)(b + L.win_scount);
   ctx->win_soff = (uint32_t *)(b + L.win_soff);
   ctx->win_skeys = (unsigned long long *)(b + L.win_skeys);
+  w.scan_part = (unsigned long long *)(b + L.scan_part);
+  w.scan_hist = (uint32_t *)(b + L.scan_hist);
   w.status = status_dev;
   {
     int sms = 148;

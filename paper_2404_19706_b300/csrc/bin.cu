@@ -463,7 +463,6 @@ __global__ void k_window_reset(Work w) { w.counters[kWinStable] = 0ull; }
 // --------------------------------------------------------------------------- tile scan
 // Cost class of a tile list of n records for the persistent schedule's queue: 0 for an
 // empty list, else four classes per octave of n (so the order is by n to within 19%).
-constexpr int kQueueClasses = 4 * 32 + 4;
 __device__ __forceinline__ int queue_class(uint32_t n) {
   if (n == 0u) return 0;
   const int lg = 31 - __clz(n);
@@ -646,9 +645,164 @@ void launch_bin(const Work &w, int64_t N, int T, int64_t max_pairs, bool cands, 
 
 void launch_window_reset(const Work &w, cudaStream_t s) { k_window_reset<<<1, 1, 0, s>>>(w); }
 
+// ---- multi-block tile scan (many tiles: batched keyframes at high resolution).  Three
+// kernels, none of which waits on another block: per-block partials, one CTA that turns
+// them into block bases and per-(block, class) queue starts and writes the totals, and a
+// per-block pass that writes the offsets and scatters the queue items.  Thread t of block b
+// owns tiles b * kScanBlockTiles + 4t .. + 3.
+
+__global__ void __launch_bounds__(1024) k_scan_part(Work w, int FT, int gshift, const uint32_t *__restrict__ extra) {
+  __shared__ unsigned long long s_a[32], s_b[32];
+  __shared__ uint32_t s_m[32];
+  __shared__ uint32_t s_cls[kQueueClasses];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int k = tid; k < kQueueClasses; k += 1024) s_cls[k] = 0u;
+  __syncthreads();
+  const int t0 = blockIdx.x * kScanBlockTiles + tid * 4;
+  unsigned long long len = 0, np = 0;
+  uint32_t mx = 0;
+  for (int t = t0; t < min(FT, t0 + 4); ++t) {
+    const uint32_t l = list_len(w, extra, t), p = w.tile_npix[t];
+    len += l;
+    np += p;
+    mx = max(mx, l);
+    if (gshift >= 0 && p != 0u) atomicAdd(&s_cls[queue_class(l)], (p + 31u) >> 5);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    len += __shfl_xor_sync(0xffffffffu, len, o);
+    np += __shfl_xor_sync(0xffffffffu, np, o);
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if (lane == 0) {
+    s_a[wid] = len;
+    s_b[wid] = np;
+    s_m[wid] = mx;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long a = 0, b = 0;
+    uint32_t m = 0;
+    for (int k = 0; k < 32; ++k) {
+      a += s_a[k];
+      b += s_b[k];
+      m = max(m, s_m[k]);
+    }
+    w.scan_part[blockIdx.x * 4 + 0] = a;
+    w.scan_part[blockIdx.x * 4 + 1] = b;
+    w.scan_part[blockIdx.x * 4 + 2] = m;
+  }
+  if (gshift >= 0)
+    for (int k = tid; k < kQueueClasses; k += 1024) w.scan_hist[blockIdx.x * kQueueClasses + k] = s_cls[k];
+}
+
+__global__ void __launch_bounds__(1024) k_scan_bases(Work w, int FT, int64_t max_pairs, int gshift, int B) {
+  __shared__ unsigned long long s_w[32];
+  __shared__ uint32_t s_start[kQueueClasses];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // exclusive prefix of the block pair totals (B <= 1024)
+  const unsigned long long v = tid < B ? w.scan_part[tid * 4] : 0ull;
+  unsigned long long inc = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
+  }
+  if (lane == 31) s_w[wid] = inc;
+  __syncthreads();
+  unsigned long long pre = 0;
+  for (int k = 0; k < wid; ++k) pre += s_w[k];
+  if (tid < B) w.scan_part[tid * 4 + 3] = pre + inc - v;
+  if (tid == 0) {
+    unsigned long long total = 0, total_pix = 0, mx = 0;
+    for (int b = 0; b < B; ++b) {
+      total += w.scan_part[b * 4 + 0];
+      total_pix += w.scan_part[b * 4 + 1];
+      mx = max(mx, w.scan_part[b * 4 + 2]);
+    }
+    w.tile_offset[FT] = (uint32_t)total;
+    w.counters[kPairs] = total;
+    w.counters[kMaskedPix] = total_pix;
+    w.counters[kMaxTilePairs] = mx;
+    if (total > (unsigned long long)max_pairs || total > 0xffffffffull) {
+      w.counters[kSkip] = 1ull;
+      atomicCAS(w.status, 0u, (uint32_t)(int32_t)RTG_ERR_WORKSPACE);
+    }
+  }
+  if (gshift < 0) return;
+  // queue: class totals, class starts in decreasing cost, then each block's start per class
+  if (tid < kQueueClasses) {
+    uint32_t c = 0;
+    for (int b = 0; b < B; ++b) c += w.scan_hist[b * kQueueClasses + tid];
+    s_start[tid] = c;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t run = 0;
+    for (int k = kQueueClasses - 1; k >= 0; --k) {
+      const uint32_t c = s_start[k];
+      s_start[k] = run;
+      run += c;
+    }
+    w.counters[kItems] = run;
+    w.counters[kQFwd] = 0ull;
+    w.counters[kQBwd] = 0ull;
+  }
+  __syncthreads();
+  if (tid < kQueueClasses) {
+    uint32_t run = s_start[tid];
+    for (int b = 0; b < B; ++b) {
+      const uint32_t c = w.scan_hist[b * kQueueClasses + tid];
+      w.scan_hist[b * kQueueClasses + tid] = run;
+      run += c;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_write(Work w, int FT, int gshift, const uint32_t *__restrict__ extra) {
+  __shared__ unsigned long long s_w[32];
+  __shared__ uint32_t s_cur[kQueueClasses];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (gshift >= 0)
+    for (int k = tid; k < kQueueClasses; k += 1024) s_cur[k] = w.scan_hist[blockIdx.x * kQueueClasses + k];
+  const int t0 = blockIdx.x * kScanBlockTiles + tid * 4, t1 = min(FT, t0 + 4);
+  uint32_t l[4] = {0u, 0u, 0u, 0u};
+  unsigned long long mine = 0;
+  for (int t = t0; t < t1; ++t) {
+    l[t - t0] = list_len(w, extra, t);
+    mine += l[t - t0];
+  }
+  unsigned long long inc = mine;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
+  }
+  if (lane == 31) s_w[wid] = inc;
+  __syncthreads();
+  unsigned long long run = w.scan_part[blockIdx.x * 4 + 3] + inc - mine;
+  for (int k = 0; k < wid; ++k) run += s_w[k];
+  for (int t = t0; t < t1; ++t) {
+    w.tile_offset[t] = (uint32_t)run;
+    run += l[t - t0];
+  }
+  if (gshift < 0) return;
+  for (int t = t0; t < t1; ++t) {
+    const uint32_t np = w.tile_npix[t];
+    if (np == 0u) continue;
+    const uint32_t ng = (np + 31u) >> 5;
+    const uint32_t pos = atomicAdd(&s_cur[queue_class(l[t - t0])], ng);
+    for (uint32_t g = 0; g < ng; ++g) w.items[pos + g] = ((uint32_t)t << 3) | g;
+  }
+}
+
 void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, int gshift, const uint32_t *extra,
                        cudaStream_t s) {
-  k_scan_tiles<<<1, 1024, 0, s>>>(w, FT, max_pairs, gshift, extra);
+  if (FT <= kScanSingleMax) {
+    k_scan_tiles<<<1, 1024, 0, s>>>(w, FT, max_pairs, gshift, extra);
+    return;
+  }
+  const int B = (FT + kScanBlockTiles - 1) / kScanBlockTiles;  // <= 1024 (capacity check)
+  k_scan_part<<<B, 1024, 0, s>>>(w, FT, gshift, extra);
+  k_scan_bases<<<1, 1024, 0, s>>>(w, FT, max_pairs, gshift, B);
+  k_scan_write<<<B, 1024, 0, s>>>(w, FT, gshift, extra);
 }
 
 void launch_emit(const Work &w, cudaStream_t s) {

@@ -113,6 +113,8 @@ struct Work {
   uint4 *stage;         // [pairs] (global tile, slot in its bucket, key lo, key hi)
   uint8_t *px_list;     // [F*T << (tws + ths)] masked pixels of each render tile
   uint32_t *items;      // [groups] work items of the persistent schedule
+  unsigned long long *scan_part;  // [scan blocks][4] partials of the multi-block tile scan
+  uint32_t *scan_hist;            // [scan blocks][queue classes] per-block class counts, then starts
   uint32_t *sorted;
   float *px_T;
   uint32_t *px_last;
