@@ -483,6 +483,8 @@ def run_ours(args):
             "config": {"workload": WORKLOAD["name"], "gaussians": N, "unstable": Nu, "width": W, "height": H,
                        "camera_candidate": k_cam, "mask_coverage": round(coverage, 4), "masked_pixels": P,
                        "pairs": K, "visible": V, "fragments_per_step": stats["fragments"],
+                       "warp_records_per_step": stats["warp_records"],
+                       "active_lanes_per_record": round(stats["fragments"] / max(stats["warp_records"], 1), 2),
                        "fragments_per_sec": round(world * stats["fragments"] * 1e3 / ms_step, 1),
                        "alg_bytes_per_step": int(b_step),
                        "step_hbm_roofline_frac": round(b_step / (ms_step * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
@@ -704,6 +706,8 @@ def run_keyframes(args, kw):
               "channels": Cc, "width": W, "height": H, "mask_coverage": [round(c, 4) for c in covs],
               "masked_pixels": sb["masked_pixels"], "pairs": sb["pairs"], "visible": sb["visible"],
               "fragments_per_step": sb["fragments"], "fragments_per_sec": round(sb["fragments"] * 1e3 / msb, 1),
+              "warp_records_per_step": sb["warp_records"],
+              "active_lanes_per_record": round(sb["fragments"] / max(sb["warp_records"], 1), 2),
               "alg_bytes_per_step": int(b_step),
               "step_hbm_roofline_frac": round(b_step / (msb * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
               "peak_hbm_gb": {"library_workspaces": round(workspace / 1e9, 2),

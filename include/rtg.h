@@ -105,6 +105,8 @@ typedef struct {
   int64_t visible;        /* (frame, Gaussian) projections that touch a masked tile */
   int64_t masked_pixels;  /* pixels rendered */
   int64_t n_unstable;     /* unstable Gaussians (rows of the compact gradients) */
+  int64_t warp_records;   /* records the forward's warps walked after culling (each warp
+                             composites 32 pixels against a record at once) */
   int32_t status;         /* device status word (rtg_status) */
   int32_t max_tile_pairs; /* longest per-tile list */
   int32_t tile_w, tile_h; /* render tile of that forward (rtg_tuning) */

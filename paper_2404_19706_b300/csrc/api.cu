@@ -985,6 +985,7 @@ rtg_status rtg_get_stats(rtg_ctx *ctx, rtg_stats *out) {
   out->visible = (int64_t)c[kVisible];
   out->masked_pixels = (int64_t)c[kMaskedPix];
   out->n_unstable = (int64_t)c[kNumUnstable];
+  out->warp_records = (int64_t)c[kWarpRecords];
   out->max_tile_pairs = (int32_t)c[kMaxTilePairs];
   out->status = (int32_t)*(volatile uint32_t *)ctx->status_host;
   out->tile_w = 1 << ctx->tune_fwd.tws;

@@ -10,7 +10,7 @@
 // The depth depends on f only through the choice of the hit fragment, so it adds no
 // gradient to f; its gradient goes to the hit Gaussian's plane record (d0, n_c) or to
 // its centre depth.  Each warp works alone on the forward's 32-pixel groups and skips the
-// records whose support box misses its pixel box (the forward's test); sums over the
+// records the forward's culling tests (support box, footprint ellipse) reject; sums over the
 // warp are formed by a halving reduce-scatter and added with vector atomics.  The two
 // schedules of the forward (CTA per tile, persistent warps over the item queue) apply.
 //
@@ -170,6 +170,7 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
   const int by1 = __reduce_max_sync(0xffffffffu, has ? py : -1);
   const float wcx = 0.5f * (float)(bx0 + bx1), whx = 0.5f * (float)(bx1 - bx0);
   const float wcy = 0.5f * (float)(by0 + by1), why = 0.5f * (float)(by1 - by0);
+  const float wbx0 = (float)bx0, wbx1 = (float)bx1, wby0 = (float)by0, wby1 = (float)by1;
   const uint32_t maxlast = __reduce_max_sync(0xffffffffu, last);
   const float4 *__restrict__ rec = w.rec_hot + (int64_t)f * N * H4;
   const float2 *__restrict__ box = w.rec_box + (int64_t)f * N;
@@ -212,8 +213,9 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
     int cnt = 0;
 #pragma unroll
     for (int u = 0; u < R; ++u) {
-      const bool keep =
-          valid[u] && fabsf(r[u][0].x - wcx) <= whx + bb[u].x && fabsf(r[u][0].y - wcy) <= why + bb[u].y;
+      const bool keep = valid[u] && fabsf(r[u][0].x - wcx) <= whx + bb[u].x &&
+                        fabsf(r[u][0].y - wcy) <= why + bb[u].y &&
+                        reaches_box(r[u][0], r[u][1], wbx0, wbx1, wby0, wby1, prm.alpha_min);
       const unsigned bal = __ballot_sync(0xffffffffu, keep);
       if (keep) {
         const int slot = cnt + __popc(bal & lanemask_lt());

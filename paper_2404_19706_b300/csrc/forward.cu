@@ -6,9 +6,9 @@
 // intersection of Eq. 4 and the cases of Eq. 5.  Only the masked pixels of a tile are
 // rendered (only pixels covered by unstable Gaussians, Supplement B): the tile-mask pass
 // compacted them into a list, and each warp works alone on 32 of them.  It walks the
-// tile's list in batches of B records and keeps only the records whose support box
-// reaches the warp's pixel box.  That test is conservative, so the result is that of the
-// per-pixel alpha_min test.  A warp stops as soon as all its pixels have stopped.
+// tile's list in batches of B records and keeps only the records whose support box, and
+// then whose footprint ellipse (reaches_box), reaches the warp's pixel box.  Both tests are
+// conservative, so the result is that of the per-pixel alpha_min test.  A warp stops as soon as all its pixels have stopped.
 // Two schedules share that per-warp body: one CTA per tile (one warp per 32 masked
 // pixels), or persistent warps that take (tile, group) items from the cost-ordered queue
 // spanning every frame of the call.
@@ -47,6 +47,7 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
   const int by1 = __reduce_max_sync(0xffffffffu, has ? py : -1);
   const float wcx = 0.5f * (float)(bx0 + bx1), whx = 0.5f * (float)(bx1 - bx0);
   const float wcy = 0.5f * (float)(by0 + by1), why = 0.5f * (float)(by1 - by0);
+  const float wbx0 = (float)bx0, wbx1 = (float)bx1, wby0 = (float)by0, wby1 = (float)by1;
   const uint32_t off = w.tile_offset[tile];
   const uint32_t n = w.tile_offset[tile + 1] - off;
   const float4 *__restrict__ rec = w.rec_hot + (int64_t)f * N * H4;
@@ -56,7 +57,7 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
   float acc[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) acc[c] = 0.f;
-  uint32_t last = 0, nfrag = 0;
+  uint32_t last = 0, nfrag = 0, nrec = 0;
   int hit_j = -1;
   bool done = !has;
   // the records of batch b0 + B are fetched while batch b0 is composited
@@ -96,8 +97,9 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
     int cnt = 0;
 #pragma unroll
     for (int u = 0; u < R; ++u) {
-      const bool keep =
-          valid[u] && fabsf(r[u][0].x - wcx) <= whx + bb[u].x && fabsf(r[u][0].y - wcy) <= why + bb[u].y;
+      const bool keep = valid[u] && fabsf(r[u][0].x - wcx) <= whx + bb[u].x &&
+                        fabsf(r[u][0].y - wcy) <= why + bb[u].y &&
+                        reaches_box(r[u][0], r[u][1], wbx0, wbx1, wby0, wby1, prm.alpha_min);
       const unsigned bal = __ballot_sync(0xffffffffu, keep);
       if (keep) {
         const int slot = cnt + __popc(bal & lanemask_lt());
@@ -107,6 +109,7 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
       }
       cnt += __popc(bal);
     }
+    nrec += (uint32_t)cnt;
     __syncwarp();
     if (!done) {
       for (int k = 0; k < cnt; ++k) {
@@ -192,9 +195,10 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
       lp[2] = nd;
     }
   }
-  // fragment counter: one atomic per warp
+  // fragment and walked-record counters: one atomic each per warp
   const unsigned fr = __reduce_add_sync(0xffffffffu, nfrag);
   if (lane == 0 && fr) atomicAdd(w.counters + kFragments, (unsigned long long)fr);
+  if (lane == 0 && nrec) atomicAdd(w.counters + kWarpRecords, (unsigned long long)nrec);
 }
 
 // Schedule 0: CTA `tile` with one warp per 32-pixel group of the tile's pixel list.

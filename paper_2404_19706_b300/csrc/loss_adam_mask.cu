@@ -351,7 +351,10 @@ __global__ void __launch_bounds__(kTilePix) k_mask_cover_tiles(Work w, Prm prm, 
       const float2 bb = box[gid];
       r0 = rec[(int64_t)gid * H4];
       keep = fabsf(r0.x - wcx) <= whx + bb.x && fabsf(r0.y - wcy) <= why + bb.y;
-      if (keep) r1 = rec[(int64_t)gid * H4 + 1];
+      if (keep) {
+        r1 = rec[(int64_t)gid * H4 + 1];
+        keep = reaches_box(r0, r1, (float)bx0, (float)bx1, (float)by0, (float)by1, prm.alpha_min);
+      }
     }
     const unsigned bal = __ballot_sync(0xffffffffu, keep);
     if (keep) {

@@ -117,4 +117,33 @@ __device__ __forceinline__ float footprint(float px, float py, float mxh, float 
   return fminf(f_max, alpha * g);
 }
 
+// Conservative test that a footprint reaches alpha_min at some point of the pixel box
+// [x0, x1] x [y0, y1] (pixel centres).  The support is q <= log2(alpha / alpha_min) with
+// q = |U d|^2 convex in d, so its minimum over the box is 0 when the centre is inside, and
+// otherwise lies on an edge, where it is a one-dimensional quadratic minimised at a clamped
+// stationary point.  Margins cover FP32 rounding, so a record this test rejects has no pixel
+// of the box with f >= alpha_min (per-pixel results do not change); it rejects the records
+// whose bounding box, but not their ellipse, meets the box.
+__device__ __forceinline__ bool reaches_box(const float4 &r0, const float4 &r1, float x0, float x1, float y0, float y1,
+                                            float alpha_min) {
+  const float dx0 = (x0 - r0.x) - r0.z, dx1 = (x1 - r0.x) - r0.z;
+  const float dy0 = (y0 - r0.y) - r0.w, dy1 = (y1 - r0.y) - r0.w;
+  if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return true;
+  const float u11 = r1.x, u12 = r1.y, u22 = r1.z;
+  const float a = u11 * u11, b = u11 * u12, c = fmaf(u12, u12, u22 * u22);
+  // approximate reciprocals: they only move the edge minimiser, and q changes quadratically
+  // there, far inside the margin below
+  const float ia = __fdividef(1.f, a), ic = __fdividef(1.f, c);
+  // q at (dx, dy) in the footprint's own form
+  auto qat = [&](float dx, float dy) {
+    const float t1 = fmaf(u11, dx, u12 * dy), t2 = u22 * dy;
+    return fmaf(t1, t1, t2 * t2);
+  };
+  const float ya = fminf(fmaxf(-b * dx0 * ic, dy0), dy1), yb = fminf(fmaxf(-b * dx1 * ic, dy0), dy1);
+  const float xa = fminf(fmaxf(-b * dy0 * ia, dx0), dx1), xb = fminf(fmaxf(-b * dy1 * ia, dx0), dx1);
+  const float qmin = fminf(fminf(qat(dx0, ya), qat(dx1, yb)), fminf(qat(xa, dy0), qat(xb, dy1)));
+  const float thr = __log2f(r1.w) - __log2f(alpha_min);
+  return qmin <= fmaf(fabsf(thr), 1e-4f, thr) + 1e-3f;
+}
+
 }  // namespace rtg

@@ -56,6 +56,7 @@ enum Counter {
   kItems = 9 * kCounterStride,        // (tile, 32-pixel group) work items of the persistent schedule
   kQFwd = 10 * kCounterStride,        // next item of the persistent forward (past the first one per warp)
   kQBwd = 11 * kCounterStride,        // next item of the persistent backward
+  kWarpRecords = 12 * kCounterStride, // records the forward's warps walked after culling
   kWinStable = 15 * kCounterStride,   // projected (frame, stable Gaussian) entries of the open window (kept)
 };
 constexpr int kNumCounterSlots = 16;  // slots; all but kWinStable are cleared at the start of every call
