@@ -404,6 +404,86 @@ void launch_l1_loss(const Work &w, int F, int C, int H, int W, const float *colo
   k_loss_grad<<<kLossBlocks, 256, 0, s>>>(w, F, C, H, W, color, depth, tcolor, tdepth, mask, dL_dcolor, dL_ddepth);
 }
 
+// Adam on groups [G0, G1) of row k: every parameter, gradient and moment of those groups is
+// loaded before any is used (one memory round trip), then updated.
+template <int C, int G0, int G1>
+__device__ __forceinline__ void adam_row_groups(const AdamGroups &G, int64_t k, float *__restrict__ m,
+                                                float *__restrict__ v, const rtg_adam_params &hp, float bc1,
+                                                float bc2_sqrt) {
+  constexpr int kW[5] = {3, 3, 4, 1, C};
+  constexpr int NP = (G0 <= 0 && G1 > 0 ? 3 : 0) + (G0 <= 1 && G1 > 1 ? 3 : 0) + (G0 <= 2 && G1 > 2 ? 4 : 0) +
+                     (G0 <= 3 && G1 > 3 ? 1 : 0) + (G0 <= 4 && G1 > 4 ? C : 0);
+  float x[NP], g[NP], mm[NP], vv[NP];
+  int q = 0;
+#pragma unroll
+  for (int grp = G0; grp < G1; ++grp) {
+#pragma unroll
+    for (int j = 0; j < kW[grp]; ++j, ++q) {
+      const int64_t e = k * kW[grp] + j;    // element within the group
+      const int64_t mi = G.begin[grp] + e;  // element within m / v
+      x[q] = G.param[grp][e];
+      g[q] = G.grad[grp][e];
+      mm[q] = m[mi];
+      vv[q] = v[mi];
+    }
+  }
+  q = 0;
+#pragma unroll
+  for (int grp = G0; grp < G1; ++grp) {
+#pragma unroll
+    for (int j = 0; j < kW[grp]; ++j, ++q) {
+      const int64_t e = k * kW[grp] + j;
+      const int64_t mi = G.begin[grp] + e;
+      const bool log_space = grp == 1;  // theta = log s, dL/dtheta = s dL/ds, s <- s exp(-step)
+      const float gg = log_space ? g[q] * x[q] : g[q];
+      const float step = adam_delta(gg, mm[q], vv[q], G.lr[grp], hp, bc1, bc2_sqrt);
+      G.param[grp][e] = log_space ? x[q] * expf(-step) : x[q] - step;
+      m[mi] = mm[q];
+      v[mi] = vv[q];
+    }
+  }
+}
+
+// One thread per unstable Gaussian (C = 3 or 8), so each thread has a whole row's loads in
+// flight at once and every stream stays coalesced (the groups are laid out one after
+// another).  C = 8 takes the geometry and the colours in two rounds to stay in registers.
+// The step ticket is taken when the block starts, so its latency overlaps the block's work;
+// the last block to take one stores t after finishing (every block read the old count first).
+template <int C>
+__global__ void __launch_bounds__(256) k_adam_rows(AdamGroups G, int64_t nu, float *__restrict__ m,
+                                                   float *__restrict__ v, rtg_adam_params hp, float bc1,
+                                                   float bc2_sqrt, int32_t *__restrict__ step_dev) {
+  __shared__ float s_bc[2];
+  __shared__ bool s_last;
+  if (step_dev != nullptr) {
+    if (threadIdx.x == 0) {
+      const float t = (float)(step_dev[0] + 1);
+      s_bc[0] = 1.f / (1.f - powf(hp.beta1, t));
+      s_bc[1] = rsqrtf(1.f - powf(hp.beta2, t));
+      s_last = atomicAdd(reinterpret_cast<unsigned *>(step_dev + 1), 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    bc1 = s_bc[0];
+    bc2_sqrt = s_bc[1];
+  }
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nu) {
+    if (C <= 4) {
+      adam_row_groups<C, 0, 5>(G, k, m, v, hp, bc1, bc2_sqrt);
+    } else {
+      adam_row_groups<C, 0, 4>(G, k, m, v, hp, bc1, bc2_sqrt);
+      adam_row_groups<C, 4, 5>(G, k, m, v, hp, bc1, bc2_sqrt);
+    }
+  }
+  if (step_dev != nullptr) {
+    __syncthreads();
+    if (threadIdx.x == 0 && s_last) {
+      step_dev[0] += 1;
+      step_dev[1] = 0;
+    }
+  }
+}
+
 void launch_adam(int64_t nu, int C, float *means, float *scales, float *quats, float *opacity, float *colors,
                  const float *g_means, const float *g_scales, const float *g_quats, const float *g_opacity,
                  const float *g_colors, float *m, float *v, const rtg_adam_params &hp, float bc1, float bc2_sqrt,
@@ -422,8 +502,13 @@ void launch_adam(int64_t nu, int C, float *means, float *scales, float *quats, f
     G.begin[k + 1] = G.begin[k] + nu * width[k];
   }
   const int64_t total = G.begin[5];
-  // a persistent grid (8 CTAs per SM): the element loop is a bandwidth-bound stream, and
-  // the counted step takes one same-address ticket per CTA
+  if (C == 3 || C == 8) {
+    const unsigned blocks = (unsigned)((nu + 255) / 256);
+    if (C == 3) k_adam_rows<3><<<blocks, 256, 0, s>>>(G, nu, m, v, hp, bc1, bc2_sqrt, step_dev);
+    else k_adam_rows<8><<<blocks, 256, 0, s>>>(G, nu, m, v, hp, bc1, bc2_sqrt, step_dev);
+    return;
+  }
+  // other channel counts: a persistent grid (8 CTAs per SM) over the elements
   const unsigned blocks =
       (unsigned)std::min<int64_t>((total + 256 * kAdamUnroll - 1) / (256 * kAdamUnroll), (int64_t)kPersistBlocks);
   k_adam<<<blocks, 256, 0, s>>>(G, m, v, hp, bc1, bc2_sqrt, step_dev);
