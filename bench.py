@@ -38,13 +38,13 @@ KEYFRAMES = dict(name="batched keyframes: 8 x 1200x680 (f 600), multi-room 12x10
                       "2M Gaussians (10% unstable, 8 blobs), mask coverage 10-60%",
                  seed=4000, n=2_000_000, n_unstable=200_000, blobs=8, frames=8, width=1200, height=680, f=600.0,
                  coverage=(0.10, 0.60), bands=4, max_pairs=48 << 20, channels=3, opaque=0.85,
-                 size=(12.0, 10.0, 3.0), grid=(2, 2), boxes=40, per_frame=True, metric=KF_METRIC)
+                 size=(12.0, 10.0, 3.0), grid=(2, 2), boxes=40, per_frame=True, metric=KF_METRIC, key="keyframes")
 LARGE_METRIC = "large-scene batched fwd+bwd iterations/sec and fragments/sec (32 keyframes at 1200×680, 5M Gaussians)"
 LARGE = dict(name="large floor: 32 x 1200x680 (f 600), 30x20x3 m (5x4 rooms, 60 boxes), 5M Gaussians (90% opaque, "
                   "8 channels, 10% unstable in 24 blobs), mask coverage 5-50%",
              seed=5000, n=5_000_000, n_unstable=500_000, blobs=24, frames=32, width=1200, height=680, f=600.0,
              coverage=(0.05, 0.50), bands=4, max_pairs=128 << 20, channels=8, opaque=0.9, size=(30.0, 20.0, 3.0),
-             grid=(5, 4), boxes=60, per_frame=False, metric=LARGE_METRIC)
+             grid=(5, 4), boxes=60, per_frame=False, metric=LARGE_METRIC, key="large")
 C = 3
 
 
@@ -328,26 +328,26 @@ def alg_bytes(stats, N, F, H, W, Cc=C):
 
 
 # DRAM bytes (read + write) per launch of a kernel from one ncu capture of bench.py, keyed
-# by (kernel, render tile, record batch, schedule); the roofline's `traffic` is filled only
-# when the run's dominant kernel and tuning match a captured one.  Source and command:
-# profiles/masked_step_1M_640x480_kernels.md.
+# by (workload, kernel, render tile, record batch, schedule); the roofline's `traffic` is
+# filled only when the run's workload, dominant kernel and tuning match a captured one.
+# Source and command: profiles/masked_step_1M_640x480_kernels.md.
 NCU_TRAFFIC = {
-    ("backward", 8, 16, 32, 1): 18_957_568,  # dram read + write, k_backward_queue<3, 32>
-    ("forward", 8, 16, 32, 1): 13_541_376 + 256,  # k_forward_queue<3, 32>
-    ("backward", 16, 16, 32, 1): 18_734_592,
-    ("forward", 16, 16, 32, 1): 13_311_744,
+    ("masked-step", "backward", 8, 16, 32, 1): 18_957_568,  # dram read + write, k_backward_queue<3, 32>
+    ("masked-step", "forward", 8, 16, 32, 1): 13_541_376 + 256,  # k_forward_queue<3, 32>
+    ("masked-step", "backward", 16, 16, 32, 1): 18_734_592,
+    ("masked-step", "forward", 16, 16, 32, 1): 13_311_744,
 }
 
 
-def roofline_of(per_launch, alg, tuning=None):
+def roofline_of(per_launch, alg, tuning=None, workload=None):
     single = ["project", "emit", "sort_tiles", "forward", "backward", "project_backward", "adam", "scan_tiles",
               "tile_mask", "bin"]
     dom = max(single, key=lambda k: per_launch.get(k, 0.0))
     pk = peaks()
     achieved = alg[dom] / (per_launch[dom] * 1e-3) / 1e9
     traffic = None
-    if tuning is not None:
-        traffic = NCU_TRAFFIC.get((dom, tuning.tile_w, tuning.tile_h, tuning.batch, tuning.schedule))
+    if tuning is not None and workload is not None:
+        traffic = NCU_TRAFFIC.get((workload, dom, tuning.tile_w, tuning.tile_h, tuning.batch, tuning.schedule))
     return {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": pk["hbm_gbs"],
             "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": traffic,
             "peak_source": "fallback" if pk.get("_fallback") else "measured (MEASURED_PEAKS.json hbm_gbs)",
@@ -471,7 +471,7 @@ def run_ours(args):
     per_launch = kernel_profile(rtg, ctx, step, args.steps, flush, stream)
     N, V, K, P, Nu = scene.n, stats["visible"], stats["pairs"], stats["masked_pixels"], stats["n_unstable"]
     alg = alg_bytes(stats, N, 1, H, W)
-    roofline, pk = roofline_of(per_launch, alg, ctx.get_tuning())
+    roofline, pk = roofline_of(per_launch, alg, ctx.get_tuning(), "masked-step")
     b_step = sum(alg.values())
 
     # ---- end to end through the public API with host buffers (graph replay per step)
@@ -701,7 +701,7 @@ def run_keyframes(args, kw):
     per_launch = kernel_profile(rtg, ctx, batched, args.steps, flush, stream)
     sb = results["batched"]["stats"]
     alg = alg_bytes(sb, scene.n, F, H, W, Cc)
-    roofline, pk = roofline_of(per_launch, alg, ctx.get_tuning())
+    roofline, pk = roofline_of(per_launch, alg, ctx.get_tuning(), kw["key"])
     b_step = sum(alg.values())
 
     # end to end: targets uploaded from pinned host memory and the losses read back each step
