@@ -41,7 +41,6 @@ struct rtg_ctx {
   GaussPtrs g;
   Prm prm;
   int F, W, H, T, C;
-  const uint8_t *mask;
   L1Fused l1;  // targets of the last rtg_render_forward_l1 (tcolor == nullptr otherwise)
   cudaStream_t last_stream;
   Tuning tune;      // launch configuration of the next forward
@@ -639,7 +638,6 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
       ProfScope ps(ctx, kPBin, s);
       launch_bin(w, n, T, ctx->cap.max_pairs, true, win && !lists, s);
     }
-    mask = mask_out;
   } else {
     {
       ProfScope ps(ctx, kPTileMask, s);
@@ -686,7 +684,6 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
   ctx->H = fs.cam[0].H;
   ctx->T = T;
   ctx->C = gp.C;
-  ctx->mask = mask;
   ctx->l1 = L1Fused{tcolor, tdepth, color, depth};
   ctx->tune_fwd = tn;
   ctx->bwd_done = false;

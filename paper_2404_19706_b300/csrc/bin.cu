@@ -331,7 +331,6 @@ __global__ void __launch_bounds__(256) k_cull(GaussPtrs g, Work w, Prm prm, int 
 // tile counter returns, so the later scatter into buckets needs no atomics.
 template <int C, int kMode>
 __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, int T, int64_t max_pairs) {
-  constexpr bool kMask = kMode == kProjMask;
   constexpr int H4 = (C <= 4) ? 3 : 4;
   constexpr int G2 = (C <= 5) ? 16 : 20;
   __shared__ uint32_t s_w[8];

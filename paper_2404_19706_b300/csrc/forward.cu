@@ -202,8 +202,14 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
 }
 
 // Schedule 0: CTA `tile` with one warp per 32-pixel group of the tile's pixel list.
+// Three CTAs per SM for the common C = 3, 32-record variant (it fits in 80 registers without
+// spilling); the others keep the registers they need.
 template <int C, int B>
-__global__ void __launch_bounds__(kMaxTilePix) k_forward(Work w, Prm prm, int64_t N, int T, FwdOut out) {
+constexpr int fwd_min_ctas() { return (C <= 4 && B == 32) ? 3 : 1; }
+
+template <int C, int B>
+__global__ void __launch_bounds__(kMaxTilePix, fwd_min_ctas<C, B>()) k_forward(Work w, Prm prm, int64_t N, int T,
+                                                                              FwdOut out) {
   constexpr int H4 = (C <= 4) ? 3 : 4;
   __shared__ float4 s_rec[kMaxTilePix / 32][H4][B];
   __shared__ uint32_t s_j[kMaxTilePix / 32][B];
@@ -217,7 +223,8 @@ __global__ void __launch_bounds__(kMaxTilePix) k_forward(Work w, Prm prm, int64_
 // from a shared counter, so warps that finish early take the remaining work.  The queue
 // holds the longest lists first.
 template <int C, int B>
-__global__ void __launch_bounds__(256) k_forward_queue(Work w, Prm prm, int64_t N, int T, FwdOut out) {
+__global__ void __launch_bounds__(256, fwd_min_ctas<C, B>()) k_forward_queue(Work w, Prm prm, int64_t N, int T,
+                                                                            FwdOut out) {
   constexpr int H4 = (C <= 4) ? 3 : 4;
   __shared__ float4 s_rec[8][H4][B];
   __shared__ uint32_t s_j[8][B];

@@ -10,7 +10,6 @@ constexpr int kSortThreads = 256;  // threads per tile-sort CTA
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortCap = 2048;     // keys a tile-sort CTA sorts entirely in shared memory
 constexpr int kLossBlocks = 296;   // 2 x 148 SMs
-constexpr int kPersistBlocks = 148 * 8;
 constexpr int kScanSingleMax = 8192;   // tiles up to which one CTA scans them all
 constexpr int kScanBlockTiles = 4096;  // tiles per CTA of the multi-block scan (4 per thread)
 constexpr int kQueueClasses = 4 * 32 + 4;  // cost classes of the persistent schedule's queue

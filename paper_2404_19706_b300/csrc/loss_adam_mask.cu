@@ -508,9 +508,9 @@ void launch_adam(int64_t nu, int C, float *means, float *scales, float *quats, f
     else k_adam_rows<8><<<blocks, 256, 0, s>>>(G, nu, m, v, hp, bc1, bc2_sqrt, step_dev);
     return;
   }
-  // other channel counts: a persistent grid (8 CTAs per SM) over the elements
-  const unsigned blocks =
-      (unsigned)std::min<int64_t>((total + 256 * kAdamUnroll - 1) / (256 * kAdamUnroll), (int64_t)kPersistBlocks);
+  // other channel counts: one resident wave of CTAs strides over the elements
+  const unsigned blocks = (unsigned)std::min<int64_t>((total + 256 * kAdamUnroll - 1) / (256 * kAdamUnroll),
+                                                      (int64_t)resident_grid((const void *)k_adam, 256));
   k_adam<<<blocks, 256, 0, s>>>(G, m, v, hp, bc1, bc2_sqrt, step_dev);
 }
 
