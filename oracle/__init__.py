@@ -19,6 +19,8 @@ Parity status per function (pins live in ``tests/test_oracle_pins.py``):
   unstable_mask      pinned (single-disc ellipse closed form; tile rule on a hand-made pattern)
   l1_loss            pinned (hand-computed values)
   adam_step          pinned (torch.optim.Adam on the same gradients)
+  global_opt.*       pinned (hand-made error patterns with ties and their masks, exact keep
+                     counts, closed-form rotation angles, the keyframe thresholds)
 """
 
 from .rasterizer import (  # noqa: F401
@@ -34,3 +36,4 @@ from .rasterizer import (  # noqa: F401
     decision_signature,
 )
 from .adam import adam_step, AdamHyper  # noqa: F401
+from . import global_opt  # noqa: F401
