@@ -45,6 +45,10 @@ LARGE = dict(name="large floor: 32 x 1200x680 (f 600), 30x20x3 m (5x4 rooms, 60 
              seed=5000, n=5_000_000, n_unstable=500_000, blobs=24, frames=32, width=1200, height=680, f=600.0,
              coverage=(0.05, 0.50), bands=4, max_pairs=128 << 20, channels=8, opaque=0.9, size=(30.0, 20.0, 3.0),
              grid=(5, 4), boxes=60, per_frame=False, metric=LARGE_METRIC, key="large")
+GLOBAL_METRIC = "global keyframe optimisation iterations/sec (4 x 640×480 keyframes, top-40% colour-error pixels)"
+GLOBAL = dict(name="global keyframe step: room 1M Gaussians, all optimised, 4 keyframes at 640x480 (f 600) taken "
+                   "by the 30 deg / 0.3 m rule, top 40% colour-error pixels, positions fixed, 0.1x rates",
+              seed=3000, n=1_000_000, frames=4, width=640, height=480, f=600.0, frac=0.4, max_pairs=40 << 20)
 C = 3
 
 
@@ -58,10 +62,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--candidate", type=int, default=-1, help="camera candidate index (-1: search)")
-    ap.add_argument("--workload", default="masked-step", choices=["masked-step", "keyframes", "large"],
+    ap.add_argument("--workload", default="masked-step", choices=["masked-step", "keyframes", "large", "global"],
                     help="masked-step: the 640x480 masked iteration (default); keyframes: 8 batched 1200x680 "
                          "keyframes vs per-frame launches; large: 32 batched 1200x680 keyframes, 5M Gaussians, "
-                         "8 channels")
+                         "8 channels; global: the global keyframe optimisation step (4 keyframes, top-40% "
+                         "pixels, every Gaussian)")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--tune-table", default="", help="write the autotuner's candidate table (JSON) to this path")
     ap.add_argument("--tuning", default="",
@@ -339,9 +344,9 @@ NCU_TRAFFIC = {
 }
 
 
-def roofline_of(per_launch, alg, tuning=None, workload=None):
+def roofline_of(per_launch, alg, tuning=None, workload=None, extra_kinds=()):
     single = ["project", "emit", "sort_tiles", "forward", "backward", "project_backward", "adam", "scan_tiles",
-              "tile_mask", "bin"]
+              "tile_mask", "bin", *extra_kinds]
     dom = max(single, key=lambda k: per_launch.get(k, 0.0))
     pk = peaks()
     achieved = alg[dom] / (per_launch[dom] * 1e-3) / 1e9
@@ -806,6 +811,213 @@ def per_frame_arm(rtg, args, kw, scene, kcams, tcol, tdep, settings, check_b, ck
     return ("per_frame", perframe, ctxs, tuned_p)
 
 
+# ----------------------------------------------------------------------------- GPU arm: global step
+
+class BoundGlobalStep:
+    """A GlobalStep with its keyframes and target buffers bound, for the bench's helpers
+    (which call step(), _body() and capture() without arguments)."""
+
+    def __init__(self, st, cams, tcol, tdep):
+        self.st, self.cams, self.tcol, self.tdep = st, cams, tcol, tdep
+
+    @property
+    def graph(self):
+        return self.st.graph
+
+    @graph.setter
+    def graph(self, g):
+        self.st.graph = g
+
+    def _body(self):
+        return self.st._body(self.cams, self.tcol, self.tdep)
+
+    def step(self):
+        return self.st.step(self.cams, self.tcol, self.tdep)
+
+    def capture(self):
+        return self.st.capture(self.cams, self.tcol, self.tdep)
+
+
+def global_kernels_per_step(F, H, W, tuning):
+    """Kernels of one global step: forward (tile mask, cull, project, scan (3 when the tiles
+    outnumber one scan block), emit, sort, composite), selection (4 histogram passes, tie
+    counts, mark), narrowing (1, plus the 3 queue kernels of the persistent schedule), L1
+    loss (2), backward (2) and Adam (1)."""
+    FT = F * ((W + tuning.tile_w - 1) // tuning.tile_w) * ((H + tuning.tile_h - 1) // tuning.tile_h)
+    scan = 1 if FT <= 8192 else 3
+    return (6 + scan) + 6 + (1 + (3 if tuning.schedule == 1 else 0)) + 2 + 2 + 1
+
+
+def oracle_global_rate(scene, cams, tcol, tdep, frac, budget_px=48):
+    """Iterations/s of the FP64 oracle on the global step, from bounded samples of frame 0:
+    per keyframe, a full-frame render (to rank the colour errors) and the loss gradient on
+    the selected pixels, each = fixed whole-scene cost (measured on one pixel) + pixels x
+    per-pixel cost (measured on `budget_px` random pixels with the Gaussians that can reach
+    them); plus the oracle's top-40% selection on all keyframes, timed directly."""
+    import torch
+    import oracle
+    from oracle import global_opt as go
+    st = oracle.Settings()
+    cam = cams[0]
+    H, W = cam.height, cam.width
+    allflag = all_optimised(scene)
+    rng = np.random.default_rng(2)
+    pix = np.stack([rng.integers(0, W, budget_px), rng.integers(0, H, budget_px)], 1)
+    tc = tcol[0].cpu().numpy()[:, pix[:, 1], pix[:, 0]].T.astype(np.float64)
+    td = tdep[0].cpu().numpy()[pix[:, 1], pix[:, 0]].astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.render(allflag, cam, st, pixels=pix[:1], need_borderline=False)
+    r_fix = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.loss_and_grads(allflag, cam, st, pix[:1], tc[:1], td[:1])
+    g_fix = time.perf_counter() - t0
+    sub = allflag.subset(reach_subset(scene, cam, pix))
+    t0 = time.perf_counter()
+    oracle.render(sub, cam, st, pixels=pix, need_borderline=False)
+    r_px = (time.perf_counter() - t0) / budget_px
+    t0 = time.perf_counter()
+    oracle.loss_and_grads(sub, cam, st, pix, tc, td)
+    g_px = (time.perf_counter() - t0) / budget_px
+    col = np.random.default_rng(3).uniform(0, 1, tcol.shape).astype(np.float32)
+    t0 = time.perf_counter()
+    go.top_error_mask(col, tcol.cpu().numpy(), frac)
+    sel_t = time.perf_counter() - t0
+    F, n = len(cams), H * W
+    k = go.keep_count(frac, n)
+    it_s = F * (r_fix + n * r_px + g_fix + k * g_px) + sel_t
+    spent = r_fix + g_fix + (r_px + g_px) * budget_px + sel_t
+    return dict(value=1.0 / it_s, unit="iter/s", cores=int(torch.get_num_threads()), kind="oracle",
+                sample=f"FP64 oracle on frame 0: render and loss+autograd fixed costs on 1 pixel ({r_fix:.1f} s, "
+                       f"{g_fix:.1f} s), per-pixel costs on {budget_px} random pixels with the Gaussians that reach "
+                       f"them; iteration = {F} x ({n} rendered + {k} selected px) + the selection "
+                       f"({sel_t:.2f} s), extrapolated ({spent:.1f} s CPU)")
+
+
+def all_optimised(scene):
+    """The scene with every Gaussian flagged for optimisation (a shallow copy)."""
+    import copy
+    s = copy.copy(scene)
+    s.unstable = np.ones(scene.n, np.uint8)
+    return s
+
+
+def run_global(args, kw=GLOBAL):
+    import torch
+    import paper_2404_19706_b300 as rtg
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    settings = rtg.RenderSettings()
+    F, H, W = kw["frames"], kw["height"], kw["width"]
+    scene, layout = synth.room_scene(kw["seed"], kw["n"])
+    cams = synth.room_camera_candidates(kw["seed"] + 1, layout, W, H, kw["f"])
+    # keyframes: the first poses of the seeded stream that the 30 deg / 0.3 m rule takes;
+    # a global step uses the latest and three earlier ones drawn at random
+    ks = rtg.KeyframeSet()
+    posed = []
+    while len(ks) < 2 * F:
+        cam = next(cams)
+        if ks.offer(len(posed), cam.R, cam.t):
+            posed.append(cam)
+    pick = ks.pick(np.random.default_rng(kw["seed"] + 5), n_random=F - 1)
+    kcams = [posed[i] for i in pick]
+    ctx = rtg.Context(max_gaussians=scene.n, max_frames=F, max_width=W, max_height=H, max_pairs=kw["max_pairs"])
+    target = synth.jitter_scene(scene, kw["seed"] + 7)
+    gt = rtg.Gaussians.from_scene(target, device=dev)
+    tcol = torch.zeros(F, C, H, W, device=dev)
+    tdep = torch.full((F, H, W), -1.0, device=dev)
+    rtg.render_forward(ctx, kcams, gt, None, settings, tcol, tdep, torch.zeros(F, H, W, device=dev))
+    tdep = torch.where(tdep > 0, tdep, torch.zeros_like(tdep))
+    del gt
+    g = rtg.Gaussians.from_scene(scene, device=dev)
+    gstep = rtg.GlobalStep(ctx, g, W, H, max_frames=F, settings=settings, frac=kw["frac"])
+    step = BoundGlobalStep(gstep, kcams, tcol, tdep)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ck = dict(color=torch.zeros_like(tcol), depth=torch.zeros_like(tdep), alpha=torch.zeros_like(tdep))
+
+    def check():
+        rtg.render_forward(ctx, kcams, gstep.g, None, settings, ck["color"], ck["depth"], ck["alpha"])
+        return [ck["color"], ck["depth"], ck["alpha"]]
+
+    state = [*gstep.params, gstep.m, gstep.v, gstep.step_counter]
+    tuned = run_tuner(ctx, step._body, check, state, args, "global")
+    for _ in range(args.warmup):
+        step.step()
+    torch.cuda.synchronize()
+    stats = rtg.get_stats(ctx)
+    assert stats["status"] == 0, stats
+    step.capture()
+    step.step()
+    torch.cuda.synchronize()
+    ms_step, wall, clocks = timed_replays(step, args.steps, flush, stream, local)
+    stats = rtg.get_stats(ctx)
+    assert stats["status"] == 0, stats
+    n_sel = int(gstep.selected[:F].sum().item())
+    per_launch = kernel_profile(rtg, ctx, step, args.steps, flush, stream)
+    alg = alg_bytes(stats, scene.n, F, H, W)
+    P, K, N = stats["masked_pixels"], stats["pairs"], scene.n
+    q_pix, r_rec, g2 = 4 * C + 16, 36 + 4 * C, 4 * (11 + C)
+    alg["backward"] = K * r_rec + n_sel * (q_pix + 2 * (4 * C + 4)) + N * g2
+    alg["l1_loss"] = P * (8 * C + 9) + P * (4 * C + 4)
+    alg["select_top_error"] = P * (8 * C + 1)
+    alg["narrow_pixels"] = P * 3
+    roofline, pk = roofline_of(per_launch, alg, ctx.get_tuning(), "global",
+                               extra_kinds=("select_top_error", "narrow_pixels", "l1_loss"))
+    b_step = sum(alg.values())
+
+    hc = torch.empty_like(tcol, device="cpu").pin_memory()
+    hd = torch.empty_like(tdep, device="cpu").pin_memory()
+    hc.copy_(tcol.cpu())
+    hd.copy_(tdep.cpu())
+    hloss = torch.empty(3, pin_memory=True)
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tcol.copy_(hc, non_blocking=True)
+        tdep.copy_(hd, non_blocking=True)
+        loss = step.step()
+        hloss.copy_(loss, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        if i >= args.warmup:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_step = float(np.mean(e2e_ms))
+    tuning = ctx.get_tuning()
+    if rank != 0:
+        return None
+    fixed = "fixed by --tuning" if args.tuning else "off (--no-tune)"
+    out = {
+        "metric": GLOBAL_METRIC, "value": round(1e3 / ms_step, 2), "unit": "iter/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": kw["name"], "gaussians": N, "frames": F, "width": W, "height": H,
+                   "keyframes_offered": len(posed), "keyframes_used": pick,
+                   "rendered_pixels": P, "selected_pixels": n_sel, "pairs": K, "visible": stats["visible"],
+                   "fragments_per_step": stats["fragments"],
+                   "alg_bytes_per_step": int(b_step),
+                   "step_hbm_roofline_frac": round(b_step / (ms_step * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
+                   "tuning": tuning.as_dict(), "autotune": tuned.summary() if tuned is not None else fixed,
+                   "l2": "256 MB buffer written before every step, outside the timed spans",
+                   "timing": "timed steps replay one CUDA graph of the whole global step; kernel_ms_per_launch "
+                             "from a live eager pass with per-kernel CUDA events",
+                   "wall_s_timed_region": round(wall, 3),
+                   "kernel_ms_per_launch": {k: round(v, 5) for k, v in per_launch.items()},
+                   "parallelism": "replicas x1"},
+        "roofline": roofline,
+        "e2e": {"value": round(1e3 / e2e_step, 2), "unit": "iter/s",
+                "h2d_bytes_per_step": int(hc.numel() * 4 + hd.numel() * 4), "d2h_bytes_per_step": 12},
+        "gpu_launches": global_kernels_per_step(F, H, W, tuning) * args.steps,
+        "clocks": clocks.summary(),
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_global_rate(scene, kcams, tcol, tdep, kw["frac"])
+    ctx.close()
+    return out
+
+
 def cpu_baseline_from_gpu(scene, cam, mask, tcol, tdep, n_masked):
     m = mask[0].cpu().numpy().astype(bool)
     ys, xs = np.nonzero(m)
@@ -880,11 +1092,13 @@ DEFAULT_CANDIDATE = 7  # first pose of the seeded stream with 25-40% mask covera
 def main():
     args = parse()
     if args.steps <= 0:
-        args.steps = {"keyframes": 60, "large": 20}.get(args.workload, 400)
+        args.steps = {"keyframes": 60, "large": 20, "global": 100}.get(args.workload, 400)
     if args.impl == "reference":
         out = run_reference(args)
     elif args.workload in ("keyframes", "large"):
         out = run_keyframes(args, KEYFRAMES if args.workload == "keyframes" else LARGE)
+    elif args.workload == "global":
+        out = run_global(args)
     else:
         out = run_ours(args)
     if out is not None:

@@ -247,6 +247,30 @@ rtg_status rtg_window_begin(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, con
 rtg_status rtg_window_end(rtg_ctx *ctx);
 int32_t rtg_window_is_open(rtg_ctx *ctx);
 
+/* Global keyframe optimisation (Section 3.2, "Keyframes and global optimization"): every
+ * Gaussian is optimised over a few keyframes, but only on the pixels of each keyframe with
+ * the largest colour errors (the top 40% in the paper).
+ *
+ * rtg_select_top_error writes mask_out [F,H,W] (uint8, device): per frame, 1 on the
+ * k = floor(frac * H * W) pixels of largest colour error e = |c_0 - t_0| + ... + |c_{C-1} -
+ * t_{C-1}| (summed in float32 in channel order) between color and target_color [F,C,H,W]
+ * (float32, device), 0 elsewhere; among equal errors the lower pixel index (row-major) is
+ * taken first.  The selection is exact: errors are ordered by their IEEE bit patterns (a NaN
+ * error ranks above every number).  frac in [0, 1]; k is computed in double precision.
+ * Needs no forward; uses only the context's workspace; the inputs are read, not kept.
+ *
+ * rtg_narrow_pixels restricts the pixel set of the last forward on this context to the
+ * pixels set in mask [F,H,W] (uint8, device; pixels the forward did not render are ignored),
+ * so that the next rtg_render_backward replays only those pixels.  The forward's per-pixel
+ * state and per-tile lists are reused as they are: no projection, binning or compositing
+ * runs again, and the gradients equal those of a forward rendered on the narrowed mask, up
+ * to float32 summation order.  The loss must then be formed on the same mask with
+ * rtg_l1_loss; rtg_render_backward_l1 returns RTG_ERR_STATE after narrowing (its fused loss
+ * covered the forward's pixels).  Narrowing again keeps the intersection. */
+rtg_status rtg_select_top_error(rtg_ctx *ctx, int32_t F, int32_t C, int32_t H, int32_t W, const float *color,
+                                const float *target_color, double frac, uint8_t *mask_out, void *stream);
+rtg_status rtg_narrow_pixels(rtg_ctx *ctx, const uint8_t *mask, void *stream);
+
 /* Adam (Kingma & Ba, Algorithm 1) on compact unstable parameters, in place, with the
  * per-group learning rates of Supplement C.  The scale is optimised in log space
  * (s <- s * exp(-step), gradient s * dL/ds).  m and v hold nu * (11 + C) float32 each,

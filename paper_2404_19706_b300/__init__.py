@@ -25,6 +25,7 @@ from .api import (  # noqa: E402,F401
     l1_loss,
     last_error,
     make_camera,
+    narrow_pixels,
     profile_enable,
     profile_read,
     render_backward,
@@ -34,6 +35,7 @@ from .api import (  # noqa: E402,F401
     render_forward,
     reset_status,
     scatter_unstable,
+    select_top_error,
     unstable_index,
     unstable_rank,
     unstable_mask,
@@ -43,5 +45,6 @@ from .api import (  # noqa: E402,F401
     workspace_size,
 )
 from .optim import MaskedStep, RasterState, RTGRasterize, rasterize  # noqa: E402,F401
+from .keyframes import GlobalStep, KeyframeSet, global_adam  # noqa: E402,F401
 
 LIBRARY_PATH = _lib.LIB_PATH

@@ -338,6 +338,26 @@ def l1_loss(ctx: Context, color, depth, target_color, target_depth, mask, w_colo
     _check(st, "rtg_l1_loss", ctx.ptr)
 
 
+def select_top_error(ctx: Context, color: torch.Tensor, target_color: torch.Tensor, frac: float,
+                     mask_out: torch.Tensor, stream=None):
+    """Per frame, 1 in mask_out [F,H,W] (uint8) on the floor(frac*H*W) pixels of largest
+    colour error |color - target| summed over channels; ties to the lower pixel index."""
+    F, C, H, W = color.shape
+    if tuple(target_color.shape) != (F, C, H, W) or tuple(mask_out.shape) != (F, H, W):
+        raise ValueError("select_top_error: color/target [F,C,H,W] and mask_out [F,H,W] must agree")
+    st = _lib.load().rtg_select_top_error(ctx.ptr, F, C, H, W, _ptr(color, torch.float32, "color"),
+                                          _ptr(target_color, torch.float32, "target_color"), float(frac),
+                                          _ptr(mask_out, torch.uint8, "mask_out"), _stream(stream))
+    _check(st, "rtg_select_top_error", ctx.ptr)
+
+
+def narrow_pixels(ctx: Context, mask: torch.Tensor, stream=None):
+    """Restrict the last forward's pixels to those set in mask [F,H,W] (uint8) for the next
+    render_backward (whose loss must be formed on the same mask with l1_loss)."""
+    st = _lib.load().rtg_narrow_pixels(ctx.ptr, _ptr(mask, torch.uint8, "mask"), _stream(stream))
+    _check(st, "rtg_narrow_pixels", ctx.ptr)
+
+
 _DUMMY = {}
 
 

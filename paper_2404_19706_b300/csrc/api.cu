@@ -46,6 +46,8 @@ struct rtg_ctx {
   Tuning tune;      // launch configuration of the next forward
   Tuning tune_fwd;  // ... and of the last one, which its backward follows
   bool bwd_done;    // a backward of the last forward has run (its 2D gradient rows are used)
+  bool narrowed;    // rtg_narrow_pixels reduced the last forward's pixel set
+  SelBufs sel;      // scratch of rtg_select_top_error (ticket set per call)
   Window win;
   // tracing: (start, end) event pairs of the kernels launched while profiling is on
   bool prof;
@@ -56,11 +58,12 @@ struct rtg_ctx {
 // Kernel kinds reported by the tracing interface (one launcher each).
 enum ProfKind {
   kPTileMask, kPUnstableIndex, kPProject, kPScanTiles, kPEmit, kPSortTiles, kPForward, kPL1Loss, kPBackward,
-  kPProjectBackward, kPUnstableMask, kPBin, kPNumKinds
+  kPProjectBackward, kPUnstableMask, kPBin, kPSelect, kPNarrow, kPNumKinds
 };
 static const char *kProfNames[kPNumKinds] = {"tile_mask", "unstable_index", "project", "scan_tiles",
                                              "emit", "sort_tiles", "forward", "l1_loss",
-                                             "backward", "project_backward", "unstable_mask", "bin"};
+                                             "backward", "project_backward", "unstable_mask", "bin",
+                                             "select_top_error", "narrow_pixels"};
 constexpr int kProfMaxRecords = 1 << 16;
 
 struct ProfRec {
@@ -124,7 +127,8 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
   size_t cams, counters, rank, ids, block_cnt, cand, rec_hot, rec_cold, rec_box, ntiles, tile_npix, tile_count, tile_offset,
       tile_cursor, keys, keys_alt, stage, sorted, px_T, px_last, px_hit, grad2d, loss_part, loss_scal, loss_done, tile_loss,
-      px_list, items, scand, win_scount, win_soff, win_skeys, scan_part, scan_hist, total;
+      px_list, items, scand, win_scount, win_soff, win_skeys, scan_part, scan_hist, sel_keys, sel_small, sel_state,
+      sel_tie, total;
 };
 
 bool capacity_ok(const rtg_capacity *c) {
@@ -190,6 +194,11 @@ Layout layout_of(const rtg_capacity *c) {
   const size_t scan_blocks = (FT + kScanBlockTiles - 1) / kScanBlockTiles + 1;
   L.scan_part = take(scan_blocks * 4 * 8);
   L.scan_hist = take(scan_blocks * kQueueClasses * 4);
+  const size_t sel_blocks = ((size_t)c->max_width * (size_t)c->max_height + kSelPerBlock - 1) / kSelPerBlock;
+  L.sel_keys = take(P * 4);
+  L.sel_small = take((4 * Fm * 256 + 5 * Fm) * 4);
+  L.sel_state = take(Fm * 2 * 4);
+  L.sel_tie = take(Fm * sel_blocks * 4);
   L.total = o;
   return L;
 }
@@ -458,6 +467,10 @@ rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap) {
   w.scan_part = (unsigned long long *)(b + L.scan_part);
   w.scan_hist = (uint32_t *)(b + L.scan_hist);
   w.status = status_dev;
+  ctx->sel.keys = (uint32_t *)(b + L.sel_keys);
+  ctx->sel.hist = (uint32_t *)(b + L.sel_small);
+  ctx->sel.state = (uint32_t *)(b + L.sel_state);
+  ctx->sel.tie = (uint32_t *)(b + L.sel_tie);
   {
     int sms = 148;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || sms < 1) {
@@ -687,6 +700,7 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
   ctx->l1 = L1Fused{tcolor, tdepth, color, depth};
   ctx->tune_fwd = tn;
   ctx->bwd_done = false;
+  ctx->narrowed = false;
   ctx->last_stream = s;
   return RTG_OK;
 }
@@ -786,7 +800,9 @@ rtg_status rtg_render_backward_l1(rtg_ctx *ctx, float *g_means, float *g_scales,
                                   float *g_colors, int32_t accumulate, void *stream) {
   if (ctx == nullptr) return RTG_ERR_ARG;
   if (!ctx->has_fwd || ctx->l1.tcolor == nullptr)
-    return fail(ctx, RTG_ERR_STATE, "render_backward_l1 without a preceding render_forward_l1");
+    return fail(ctx, RTG_ERR_STATE, ctx->has_fwd && ctx->narrowed
+                                        ? "render_backward_l1 after narrow_pixels (use l1_loss + render_backward)"
+                                        : "render_backward_l1 without a preceding render_forward_l1");
   if (!g_means || !g_scales || !g_quats || !g_opacity || !g_colors)
     return fail(ctx, RTG_ERR_ARG, "gradient output is NULL");
   cudaStream_t s = (cudaStream_t)stream;
@@ -846,6 +862,47 @@ rtg_status rtg_l1_loss(rtg_ctx *ctx, int32_t F, int32_t C, int32_t H, int32_t W,
                  dL_dcolor, dL_ddepth, s);
   ctx->last_stream = s;
   return check_launch(ctx, "l1_loss");
+}
+
+rtg_status rtg_select_top_error(rtg_ctx *ctx, int32_t F, int32_t C, int32_t H, int32_t W, const float *color,
+                                const float *target_color, double frac, uint8_t *mask_out, void *stream) {
+  if (ctx == nullptr) return RTG_ERR_ARG;
+  if (F < 1 || F > ctx->cap.max_frames || C < 1 || C > 64 || H < 1 || W < 1 || H > ctx->cap.max_height ||
+      W > ctx->cap.max_width)
+    return fail(ctx, RTG_ERR_ARG, "select_top_error: sizes outside the capacity");
+  if (!(frac >= 0.0 && frac <= 1.0)) return fail(ctx, RTG_ERR_ARG, "select_top_error: frac outside [0, 1]");
+  if (color == nullptr || target_color == nullptr || mask_out == nullptr)
+    return fail(ctx, RTG_ERR_ARG, "select_top_error: NULL pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = (int64_t)H * W;
+  const uint32_t k = (uint32_t)floor(frac * (double)n);
+  ProfScope ps(ctx, kPSelect, s);
+  if (k == 0u || (int64_t)k == n) {  // nothing or everything: no order needed
+    if (cudaMemsetAsync(mask_out, k == 0u ? 0 : 1, (size_t)F * (size_t)n, s) != cudaSuccess)
+      return check_launch(ctx, "select_top_error");
+  } else {
+    SelBufs b = ctx->sel;
+    b.ticket = b.hist + (size_t)4 * F * 256;
+    launch_select_top_error(b, F, C, n, k, color, target_color, mask_out, s);
+  }
+  ctx->last_stream = s;
+  return check_launch(ctx, "select_top_error");
+}
+
+rtg_status rtg_narrow_pixels(rtg_ctx *ctx, const uint8_t *mask, void *stream) {
+  if (ctx == nullptr) return RTG_ERR_ARG;
+  if (!ctx->has_fwd) return fail(ctx, RTG_ERR_STATE, "narrow_pixels without a preceding forward");
+  if (mask == nullptr) return fail(ctx, RTG_ERR_ARG, "narrow_pixels: mask is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const Tuning &tn = ctx->tune_fwd;
+  {
+    ProfScope ps(ctx, kPNarrow, s);
+    launch_narrow_pixels(ctx->w_fwd, ctx->F, ctx->T, tn.tws, tn.ths, mask, tn.schedule == 1 ? tn.gshift() : -1, s);
+  }
+  ctx->l1.tcolor = nullptr;  // the fused loss covered the forward's pixels, not these
+  ctx->narrowed = true;
+  ctx->last_stream = s;
+  return check_launch(ctx, "narrow_pixels");
 }
 
 rtg_status rtg_adam_step(int64_t nu, int32_t C, float *means, float *scales, float *quats, float *opacity,

@@ -649,8 +649,15 @@ void launch_window_reset(const Work &w, cudaStream_t s) { k_window_reset<<<1, 1,
 // them into block bases and per-(block, class) queue starts and writes the totals, and a
 // per-block pass that writes the offsets and scatters the queue items.  Thread t of block b
 // owns tiles b * kScanBlockTiles + 4t .. + 3.
+// With `requeue` they rebuild only the queue, for pixel lists narrowed after the forward:
+// the list lengths come from the forward's offsets, which stay as they are, as do the totals.
 
-__global__ void __launch_bounds__(1024) k_scan_part(Work w, int FT, int gshift, const uint32_t *__restrict__ extra) {
+__device__ __forceinline__ uint32_t scan_len(const Work &w, const uint32_t *extra, int t, int requeue) {
+  return requeue ? w.tile_offset[t + 1] - w.tile_offset[t] : list_len(w, extra, t);
+}
+
+__global__ void __launch_bounds__(1024) k_scan_part(Work w, int FT, int gshift, const uint32_t *__restrict__ extra,
+                                                    int requeue) {
   __shared__ unsigned long long s_a[32], s_b[32];
   __shared__ uint32_t s_m[32];
   __shared__ uint32_t s_cls[kQueueClasses];
@@ -661,7 +668,7 @@ __global__ void __launch_bounds__(1024) k_scan_part(Work w, int FT, int gshift, 
   unsigned long long len = 0, np = 0;
   uint32_t mx = 0;
   for (int t = t0; t < min(FT, t0 + 4); ++t) {
-    const uint32_t l = list_len(w, extra, t), p = w.tile_npix[t];
+    const uint32_t l = scan_len(w, extra, t, requeue), p = w.tile_npix[t];
     len += l;
     np += p;
     mx = max(mx, l);
@@ -694,36 +701,39 @@ __global__ void __launch_bounds__(1024) k_scan_part(Work w, int FT, int gshift, 
     for (int k = tid; k < kQueueClasses; k += 1024) w.scan_hist[blockIdx.x * kQueueClasses + k] = s_cls[k];
 }
 
-__global__ void __launch_bounds__(1024) k_scan_bases(Work w, int FT, int64_t max_pairs, int gshift, int B) {
+__global__ void __launch_bounds__(1024) k_scan_bases(Work w, int FT, int64_t max_pairs, int gshift, int B,
+                                                     int requeue) {
   __shared__ unsigned long long s_w[32];
   __shared__ uint32_t s_start[kQueueClasses];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  // exclusive prefix of the block pair totals (B <= 1024)
-  const unsigned long long v = tid < B ? w.scan_part[tid * 4] : 0ull;
-  unsigned long long inc = v;
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long u = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += u;
-  }
-  if (lane == 31) s_w[wid] = inc;
-  __syncthreads();
-  unsigned long long pre = 0;
-  for (int k = 0; k < wid; ++k) pre += s_w[k];
-  if (tid < B) w.scan_part[tid * 4 + 3] = pre + inc - v;
-  if (tid == 0) {
-    unsigned long long total = 0, total_pix = 0, mx = 0;
-    for (int b = 0; b < B; ++b) {
-      total += w.scan_part[b * 4 + 0];
-      total_pix += w.scan_part[b * 4 + 1];
-      mx = max(mx, w.scan_part[b * 4 + 2]);
+  if (!requeue) {  // block bases and totals
+    // exclusive prefix of the block pair totals (B <= 1024)
+    const unsigned long long v = tid < B ? w.scan_part[tid * 4] : 0ull;
+    unsigned long long inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long u = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += u;
     }
-    w.tile_offset[FT] = (uint32_t)total;
-    w.counters[kPairs] = total;
-    w.counters[kMaskedPix] = total_pix;
-    w.counters[kMaxTilePairs] = mx;
-    if (total > (unsigned long long)max_pairs || total > 0xffffffffull) {
-      w.counters[kSkip] = 1ull;
-      atomicCAS(w.status, 0u, (uint32_t)(int32_t)RTG_ERR_WORKSPACE);
+    if (lane == 31) s_w[wid] = inc;
+    __syncthreads();
+    unsigned long long pre = 0;
+    for (int k = 0; k < wid; ++k) pre += s_w[k];
+    if (tid < B) w.scan_part[tid * 4 + 3] = pre + inc - v;
+    if (tid == 0) {
+      unsigned long long total = 0, total_pix = 0, mx = 0;
+      for (int b = 0; b < B; ++b) {
+        total += w.scan_part[b * 4 + 0];
+        total_pix += w.scan_part[b * 4 + 1];
+        mx = max(mx, w.scan_part[b * 4 + 2]);
+      }
+      w.tile_offset[FT] = (uint32_t)total;
+      w.counters[kPairs] = total;
+      w.counters[kMaskedPix] = total_pix;
+      w.counters[kMaxTilePairs] = mx;
+      if (total > (unsigned long long)max_pairs || total > 0xffffffffull) {
+        w.counters[kSkip] = 1ull;
+        atomicCAS(w.status, 0u, (uint32_t)(int32_t)RTG_ERR_WORKSPACE);
+      }
     }
   }
   if (gshift < 0) return;
@@ -756,7 +766,8 @@ __global__ void __launch_bounds__(1024) k_scan_bases(Work w, int FT, int64_t max
   }
 }
 
-__global__ void __launch_bounds__(1024) k_scan_write(Work w, int FT, int gshift, const uint32_t *__restrict__ extra) {
+__global__ void __launch_bounds__(1024) k_scan_write(Work w, int FT, int gshift, const uint32_t *__restrict__ extra,
+                                                     int requeue) {
   __shared__ unsigned long long s_w[32];
   __shared__ uint32_t s_cur[kQueueClasses];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -766,7 +777,7 @@ __global__ void __launch_bounds__(1024) k_scan_write(Work w, int FT, int gshift,
   uint32_t l[4] = {0u, 0u, 0u, 0u};
   unsigned long long mine = 0;
   for (int t = t0; t < t1; ++t) {
-    l[t - t0] = list_len(w, extra, t);
+    l[t - t0] = scan_len(w, extra, t, requeue);
     mine += l[t - t0];
   }
   unsigned long long inc = mine;
@@ -776,11 +787,13 @@ __global__ void __launch_bounds__(1024) k_scan_write(Work w, int FT, int gshift,
   }
   if (lane == 31) s_w[wid] = inc;
   __syncthreads();
-  unsigned long long run = w.scan_part[blockIdx.x * 4 + 3] + inc - mine;
-  for (int k = 0; k < wid; ++k) run += s_w[k];
-  for (int t = t0; t < t1; ++t) {
-    w.tile_offset[t] = (uint32_t)run;
-    run += l[t - t0];
+  if (!requeue) {
+    unsigned long long run = w.scan_part[blockIdx.x * 4 + 3] + inc - mine;
+    for (int k = 0; k < wid; ++k) run += s_w[k];
+    for (int t = t0; t < t1; ++t) {
+      w.tile_offset[t] = (uint32_t)run;
+      run += l[t - t0];
+    }
   }
   if (gshift < 0) return;
   for (int t = t0; t < t1; ++t) {
@@ -799,9 +812,16 @@ void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, int gshift, con
     return;
   }
   const int B = (FT + kScanBlockTiles - 1) / kScanBlockTiles;  // <= 1024 (capacity check)
-  k_scan_part<<<B, 1024, 0, s>>>(w, FT, gshift, extra);
-  k_scan_bases<<<1, 1024, 0, s>>>(w, FT, max_pairs, gshift, B);
-  k_scan_write<<<B, 1024, 0, s>>>(w, FT, gshift, extra);
+  k_scan_part<<<B, 1024, 0, s>>>(w, FT, gshift, extra, 0);
+  k_scan_bases<<<1, 1024, 0, s>>>(w, FT, max_pairs, gshift, B, 0);
+  k_scan_write<<<B, 1024, 0, s>>>(w, FT, gshift, extra, 0);
+}
+
+void launch_requeue(const Work &w, int FT, int gshift, cudaStream_t s) {
+  const int B = (FT + kScanBlockTiles - 1) / kScanBlockTiles;
+  k_scan_part<<<B, 1024, 0, s>>>(w, FT, gshift, nullptr, 1);
+  k_scan_bases<<<1, 1024, 0, s>>>(w, FT, 0, gshift, B, 1);
+  k_scan_write<<<B, 1024, 0, s>>>(w, FT, gshift, nullptr, 1);
 }
 
 void launch_emit(const Work &w, cudaStream_t s) {

@@ -110,6 +110,9 @@ void launch_window_reset(const Work &w, cudaStream_t s);
 void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, int gshift, const uint32_t *extra,
                        cudaStream_t s);
 void launch_emit(const Work &w, cudaStream_t s);
+// Rebuilds the persistent schedule's queue from the current pixel counts, with each tile's
+// list length taken from the forward's offsets (which it leaves unchanged).
+void launch_requeue(const Work &w, int FT, int gshift, cudaStream_t s);
 // sort.cu
 // Cached sorted stable lists of an open window (keys == nullptr: none): per tile its
 // count and offset into keys.
@@ -153,5 +156,20 @@ void launch_scatter(int64_t nu, int C, const int32_t *ids, const float *um, cons
 enum CoverMode { kCoverPlain = 0, kCoverFusedSame = 1, kCoverFusedOther = 2 };
 void launch_mask_cover_tiles(const Work &w, const Prm &prm, int64_t N, int F, int T, int C, uint8_t *mask,
                              int mode, cudaStream_t s);
+// select.cu
+constexpr int kSelThreads = 256;   // threads per block of the top-error selection
+constexpr int kSelPerBlock = 4096; // pixels per block
+// Scratch of the top-error selection: keys [F][n] (error bits), hist [4][F][256] followed by
+// ticket [5][F] (cleared at the start of every call), state [F][2] (threshold key, equal
+// keys still to take), tie [F][blocks per frame].
+struct SelBufs {
+  uint32_t *keys, *hist, *ticket, *state, *tie;
+};
+void launch_select_top_error(const SelBufs &b, int F, int C, int64_t n, uint32_t k, const float *color,
+                             const float *target, uint8_t *mask, cudaStream_t s);
+// Keeps only the pixels set in mask [F,H,W] in the last forward's per-tile pixel lists;
+// gshift >= 0 also rebuilds the persistent schedule's queue.
+void launch_narrow_pixels(const Work &w, int F, int T, int tws, int ths, const uint8_t *mask, int gshift,
+                          cudaStream_t s);
 
 }  // namespace rtg

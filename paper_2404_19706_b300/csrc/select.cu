@@ -1,0 +1,211 @@
+// Global keyframe optimisation (Section 3.2, "Keyframes and global optimization"): each
+// keyframe of a global step is optimised only on its pixels with the largest colour errors.
+//
+// Top-error selection: per frame, the k = floor(frac * H * W) pixels of largest colour error
+// e = |c_0 - t_0| + |c_1 - t_1| + ... (float32, channel order), ties towards the lower
+// pixel index.  Errors are non-negative, so their IEEE bit patterns order like the values
+// and the k-th largest is found exactly by a radix select on the 32-bit pattern: four
+// passes over one byte each, most significant first.  A pass histograms, over every frame
+// at once, the byte of the keys that share the bytes fixed so far; the last block of each
+// frame to finish (a ticket counter) picks the byte that holds the k-th largest key.  Then
+// per-block counts of keys equal to the threshold T, their exclusive scan, and a mark pass:
+// key > T, or key == T among the first (k - #keys > T) of them in pixel order.
+//
+// Narrowing: the forward keeps its per-pixel state (final transmission, last fragment,
+// depth hit) in image layout, and its per-tile sorted lists cover every tile it rendered.
+// A backward over a subset of those pixels therefore needs only each tile's pixel list
+// compacted to the subset (and the persistent schedule's queue rebuilt); the lists and
+// records stay as they are.
+#include "kernels.cuh"
+
+namespace rtg {
+
+// ----------------------------------------------------------------------------- selection
+
+template <int P>
+__global__ void __launch_bounds__(kSelThreads) k_sel_pass(SelBufs b, int F, int C, int64_t n, int nb, uint32_t k,
+                                                          const float *__restrict__ color,
+                                                          const float *__restrict__ target) {
+  __shared__ uint32_t s_h[kSelThreads / 32][256];
+  __shared__ uint32_t s_w[kSelThreads / 32];
+  __shared__ int s_last;
+  constexpr int shift = 24 - 8 * P;
+  const int f = blockIdx.y, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int i = tid; i < (kSelThreads / 32) * 256; i += kSelThreads) (&s_h[0][0])[i] = 0u;
+  const uint32_t prefix = P > 0 ? b.state[2 * f] : 0u;
+  __syncthreads();
+  const int64_t i0 = (int64_t)blockIdx.x * kSelPerBlock, i1 = min(n, i0 + kSelPerBlock);
+  uint32_t *__restrict__ keys = b.keys + (int64_t)f * n;
+  for (int64_t i = i0 + tid; i < i1; i += kSelThreads) {
+    uint32_t key;
+    if (P == 0) {
+      float e = 0.f;
+      for (int c = 0; c < C; ++c) {
+        const int64_t o = ((int64_t)f * C + c) * n + i;
+        e = __fadd_rn(e, fabsf(__fsub_rn(color[o], target[o])));
+      }
+      key = __float_as_uint(e);
+      keys[i] = key;
+    } else {
+      key = keys[i];
+      if ((key >> (shift + 8)) != (prefix >> (shift + 8))) continue;
+    }
+    atomicAdd(&s_h[wid][(key >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  uint32_t *__restrict__ hist = b.hist + ((int64_t)P * F + f) * 256;
+  uint32_t sum = 0;
+#pragma unroll
+  for (int q = 0; q < kSelThreads / 32; ++q) sum += s_h[q][tid];
+  if (sum) atomicAdd(&hist[tid], sum);
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(&b.ticket[P * F + f], 1u) == (uint32_t)nb - 1u;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // last block of frame f: thread t looks at byte 255 - t; inclusive counts from the top
+  const uint32_t krem = P == 0 ? k : b.state[2 * f + 1];
+  const uint32_t h = __ldcg(&hist[255 - tid]);
+  uint32_t inc = h;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
+  }
+  if (lane == 31) s_w[wid] = inc;
+  __syncthreads();
+  for (int q = 0; q < wid; ++q) inc += s_w[q];
+  if (inc >= krem && inc - h < krem) {  // exactly one byte: the k-th largest key's
+    b.state[2 * f] = prefix | ((uint32_t)(255 - tid) << shift);
+    b.state[2 * f + 1] = krem - (inc - h);
+  }
+}
+
+// Per-block counts of keys equal to the threshold, then (last block of each frame) their
+// exclusive scan in place: the number of equal keys before each block.
+__global__ void __launch_bounds__(kSelThreads) k_sel_ties(SelBufs b, int F, int64_t n, int nb) {
+  __shared__ int s_w[kSelThreads / 32];
+  __shared__ uint32_t s_u[kSelThreads / 32];
+  __shared__ int s_last;
+  const int f = blockIdx.y, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t T = b.state[2 * f];
+  const int64_t i0 = (int64_t)blockIdx.x * kSelPerBlock, i1 = min(n, i0 + kSelPerBlock);
+  const uint32_t *__restrict__ keys = b.keys + (int64_t)f * n;
+  int cnt = 0;
+  for (int64_t i = i0 + tid; i < i1; i += kSelThreads) cnt += keys[i] == T;
+  cnt = block_sum_int(cnt, s_w);
+  uint32_t *__restrict__ tie = b.tie + (int64_t)f * nb;
+  if (tid == 0) tie[blockIdx.x] = (uint32_t)cnt;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(&b.ticket[4 * F + f], 1u) == (uint32_t)nb - 1u;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int per = (nb + kSelThreads - 1) / kSelThreads;
+  const int e0 = min(nb, tid * per), e1 = min(nb, e0 + per);
+  uint32_t mine = 0;
+  for (int e = e0; e < e1; ++e) mine += __ldcg(&tie[e]);
+  uint32_t inc = mine;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
+  }
+  if (lane == 31) s_u[wid] = inc;
+  __syncthreads();
+  uint32_t run = inc - mine;
+  for (int q = 0; q < wid; ++q) run += s_u[q];
+  for (int e = e0; e < e1; ++e) {
+    const uint32_t c = __ldcg(&tie[e]);
+    tie[e] = run;
+    run += c;
+  }
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_sel_mark(SelBufs b, int64_t n, int nb, uint8_t *__restrict__ mask) {
+  __shared__ uint32_t s_w[kSelThreads / 32];
+  const int f = blockIdx.y, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t T = b.state[2 * f], krem = b.state[2 * f + 1];
+  uint32_t base = b.tie[(int64_t)f * nb + blockIdx.x];  // equal keys in earlier blocks
+  const int64_t i0 = (int64_t)blockIdx.x * kSelPerBlock, i1 = min(n, i0 + kSelPerBlock);
+  const uint32_t *__restrict__ keys = b.keys + (int64_t)f * n;
+  uint8_t *__restrict__ out = mask + (int64_t)f * n;
+  for (int64_t r = i0; r < i1; r += kSelThreads) {  // rows of kSelThreads pixels, in order
+    const int64_t i = r + tid;
+    const bool in = i < i1;
+    const uint32_t key = in ? keys[i] : 0u;
+    bool sel = in && key > T;
+    if (base < krem) {  // block-uniform: some equal keys may still be taken
+      const bool eq = in && key == T;
+      const unsigned bal = __ballot_sync(0xffffffffu, eq);
+      if (lane == 0) s_w[wid] = __popc(bal);
+      __syncthreads();
+      uint32_t before = 0, total = 0;
+#pragma unroll
+      for (int q = 0; q < kSelThreads / 32; ++q) {
+        const uint32_t c = s_w[q];
+        before += q < wid ? c : 0u;
+        total += c;
+      }
+      __syncthreads();
+      if (eq && base + before + (uint32_t)__popc(bal & lanemask_lt()) < krem) sel = true;
+      base += total;
+    }
+    if (in) out[i] = sel ? 1 : 0;
+  }
+}
+
+void launch_select_top_error(const SelBufs &b, int F, int C, int64_t n, uint32_t k, const float *color,
+                             const float *target, uint8_t *mask, cudaStream_t s) {
+  const int nb = (int)((n + kSelPerBlock - 1) / kSelPerBlock);
+  const dim3 grid((unsigned)nb, (unsigned)F);
+  cudaMemsetAsync(b.hist, 0, ((size_t)4 * F * 256 + (size_t)5 * F) * sizeof(uint32_t), s);
+  k_sel_pass<0><<<grid, kSelThreads, 0, s>>>(b, F, C, n, nb, k, color, target);
+  k_sel_pass<1><<<grid, kSelThreads, 0, s>>>(b, F, C, n, nb, k, color, target);
+  k_sel_pass<2><<<grid, kSelThreads, 0, s>>>(b, F, C, n, nb, k, color, target);
+  k_sel_pass<3><<<grid, kSelThreads, 0, s>>>(b, F, C, n, nb, k, color, target);
+  k_sel_ties<<<grid, kSelThreads, 0, s>>>(b, F, n, nb);
+  k_sel_mark<<<grid, kSelThreads, 0, s>>>(b, n, nb, mask);
+}
+
+// ----------------------------------------------------------------------------- narrowing
+// One CTA of 2^(tws+ths) threads per render tile of the last forward: keeps the entries of
+// the tile's pixel list whose pixel is set in `mask`, in their order (raster order).
+__global__ void __launch_bounds__(kMaxTilePix) k_narrow_pixels(Work w, int T, const uint8_t *__restrict__ mask) {
+  __shared__ int s_wcnt[kMaxTilePix / 32];
+  const int tile = blockIdx.x;
+  const uint32_t np = w.tile_npix[tile];
+  if (np == 0u) return;
+  const int f = tile / T, lt = tile - f * T;
+  const DevCam &cam = w.cams[f];
+  const int tws = cam.tws, ths = cam.ths;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  uint8_t *__restrict__ list = w.px_list + ((int64_t)tile << (tws + ths));
+  const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
+  int my = 0;
+  bool keep = false;
+  if ((uint32_t)tid < np) {
+    my = list[tid];
+    const int px = (tx << tws) + (my & ((1 << tws) - 1)), py = (ty << ths) + (my >> tws);
+    keep = mask[((int64_t)f * cam.H + py) * cam.W + px] != 0;
+  }
+  const unsigned bal = __ballot_sync(0xffffffffu, keep);
+  if (lane == 0) s_wcnt[wid] = __popc(bal);
+  __syncthreads();  // every entry is read before any is rewritten
+  int before = 0, total = 0;
+  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+    const int c = s_wcnt[q];
+    before += q < wid ? c : 0;
+    total += c;
+  }
+  if (keep) list[before + __popc(bal & lanemask_lt())] = (uint8_t)my;
+  if (tid == 0) w.tile_npix[tile] = (uint32_t)total;
+}
+
+void launch_narrow_pixels(const Work &w, int F, int T, int tws, int ths, const uint8_t *mask, int gshift,
+                          cudaStream_t s) {
+  k_narrow_pixels<<<F * T, 1 << (tws + ths), 0, s>>>(w, T, mask);
+  if (gshift >= 0) launch_requeue(w, F * T, gshift, s);
+}
+
+}  // namespace rtg
