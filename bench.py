@@ -840,12 +840,12 @@ class BoundGlobalStep:
 
 def global_kernels_per_step(F, H, W, tuning):
     """Kernels of one global step: forward (tile mask, cull, project, scan (3 when the tiles
-    outnumber one scan block), emit, sort, composite), selection (4 histogram passes, tie
-    counts, mark), narrowing (1, plus the 3 queue kernels of the persistent schedule), L1
-    loss (2), backward (2) and Adam (1)."""
+    outnumber one scan block), emit, sort, composite), selection (3 histogram passes, tie
+    counts, mark), narrowing with the loss partials (1, plus the 3 queue kernels of the
+    persistent schedule) and the loss finalize (1), backward (2) and Adam (1)."""
     FT = F * ((W + tuning.tile_w - 1) // tuning.tile_w) * ((H + tuning.tile_h - 1) // tuning.tile_h)
     scan = 1 if FT <= 8192 else 3
-    return (6 + scan) + 6 + (1 + (3 if tuning.schedule == 1 else 0)) + 2 + 2 + 1
+    return (6 + scan) + 5 + (1 + (3 if tuning.schedule == 1 else 0)) + 1 + 2 + 1
 
 
 def oracle_global_rate(scene, cams, tcol, tdep, frac, budget_px=48):
@@ -957,13 +957,14 @@ def run_global(args, kw=GLOBAL):
     assert stats["status"] == 0, stats
     n_sel = int(gstep.selected[:F].sum().item())
     per_launch = kernel_profile(rtg, ctx, step, args.steps, flush, stream)
-    alg = alg_bytes(stats, scene.n, F, H, W)
-    P, K, N = stats["masked_pixels"], stats["pairs"], scene.n
+    # the stats count the narrowed pixels; the forward rendered every pixel of the keyframes
+    P, K, N = F * H * W, stats["pairs"], scene.n
+    alg = alg_bytes(dict(stats, masked_pixels=P), scene.n, F, H, W)
     q_pix, r_rec, g2 = 4 * C + 16, 36 + 4 * C, 4 * (11 + C)
     alg["backward"] = K * r_rec + n_sel * (q_pix + 2 * (4 * C + 4)) + N * g2
-    alg["l1_loss"] = P * (8 * C + 9) + P * (4 * C + 4)
+    alg["l1_loss"] = F * ((W + 15) // 16) * ((H + 15) // 16) * 8 * 12  # finalize of the narrowed partials
     alg["select_top_error"] = P * (8 * C + 1)
-    alg["narrow_pixels"] = P * 3
+    alg["narrow_pixels"] = P * 3 + n_sel * 2 * (4 * C + 4)  # lists and mask; colour, depth, targets
     roofline, pk = roofline_of(per_launch, alg, ctx.get_tuning(), "global",
                                extra_kinds=("select_top_error", "narrow_pixels", "l1_loss"))
     b_step = sum(alg.values())

@@ -261,15 +261,21 @@ int32_t rtg_window_is_open(rtg_ctx *ctx);
  *
  * rtg_narrow_pixels restricts the pixel set of the last forward on this context to the
  * pixels set in mask [F,H,W] (uint8, device; pixels the forward did not render are ignored),
- * so that the next rtg_render_backward replays only those pixels.  The forward's per-pixel
- * state and per-tile lists are reused as they are: no projection, binning or compositing
- * runs again, and the gradients equal those of a forward rendered on the narrowed mask, up
- * to float32 summation order.  The loss must then be formed on the same mask with
- * rtg_l1_loss; rtg_render_backward_l1 returns RTG_ERR_STATE after narrowing (its fused loss
- * covered the forward's pixels).  Narrowing again keeps the intersection. */
+ * so that the next backward replays only those pixels.  The forward's per-pixel state and
+ * per-tile lists are reused as they are: no projection, binning or compositing runs again,
+ * and the gradients equal those of a forward rendered on the narrowed mask, up to float32
+ * summation order.  rtg_stats.masked_pixels then counts the narrowed pixels.  Narrowing
+ * again keeps the intersection.
+ * With target_color [F,C,H,W] and target_depth [F,H,W] (device) and loss_out (device
+ * float[3]) it also forms the L1 losses of Eq. 7/8 on the narrowed pixels against those
+ * targets (weights w_color, w_depth), exactly as rtg_render_forward_l1 defines them, so that
+ * rtg_render_backward_l1 may follow (the targets must stay unchanged until it has run).
+ * Without targets (all three NULL) form the loss with rtg_l1_loss on the same mask and call
+ * rtg_render_backward; rtg_render_backward_l1 then returns RTG_ERR_STATE. */
 rtg_status rtg_select_top_error(rtg_ctx *ctx, int32_t F, int32_t C, int32_t H, int32_t W, const float *color,
                                 const float *target_color, double frac, uint8_t *mask_out, void *stream);
-rtg_status rtg_narrow_pixels(rtg_ctx *ctx, const uint8_t *mask, void *stream);
+rtg_status rtg_narrow_pixels(rtg_ctx *ctx, const uint8_t *mask, const float *target_color, const float *target_depth,
+                             float w_color, float w_depth, float *loss_out, void *stream);
 
 /* Adam (Kingma & Ba, Algorithm 1) on compact unstable parameters, in place, with the
  * per-group learning rates of Supplement C.  The scale is optimised in log space

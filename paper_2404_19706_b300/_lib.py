@@ -89,7 +89,8 @@ SIGNATURES = [
     ("rtg_window_is_open", c_int32, [c_void_p]),
     ("rtg_select_top_error", c_int32, [c_void_p, c_int32, c_int32, c_int32, c_int32, c_void_p, c_void_p,
                                        ctypes.c_double, c_void_p, c_void_p]),
-    ("rtg_narrow_pixels", c_int32, [c_void_p, c_void_p, c_void_p]),
+    ("rtg_narrow_pixels", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_float, c_void_p,
+                                    c_void_p]),
     ("rtg_get_tuning", c_int32, [c_void_p, POINTER(rtg_tuning)]),
     ("rtg_adam_step", c_int32, [c_int64, c_int32] + [c_void_p] * 12 + [c_int32, POINTER(rtg_adam_params),
                                                                        c_void_p]),

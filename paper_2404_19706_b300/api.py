@@ -351,10 +351,16 @@ def select_top_error(ctx: Context, color: torch.Tensor, target_color: torch.Tens
     _check(st, "rtg_select_top_error", ctx.ptr)
 
 
-def narrow_pixels(ctx: Context, mask: torch.Tensor, stream=None):
+def narrow_pixels(ctx: Context, mask: torch.Tensor, target_color: Optional[torch.Tensor] = None,
+                  target_depth: Optional[torch.Tensor] = None, w_color: float = 1.0, w_depth: float = 1.0,
+                  loss_out: Optional[torch.Tensor] = None, stream=None):
     """Restrict the last forward's pixels to those set in mask [F,H,W] (uint8) for the next
-    render_backward (whose loss must be formed on the same mask with l1_loss)."""
-    st = _lib.load().rtg_narrow_pixels(ctx.ptr, _ptr(mask, torch.uint8, "mask"), _stream(stream))
+    backward.  With the targets and loss_out it also forms the L1 loss on those pixels, for
+    render_backward_l1; without them use l1_loss on the same mask and render_backward."""
+    st = _lib.load().rtg_narrow_pixels(ctx.ptr, _ptr(mask, torch.uint8, "mask"),
+                                       _ptr(target_color, torch.float32, "target_color"),
+                                       _ptr(target_depth, torch.float32, "target_depth"), float(w_color),
+                                       float(w_depth), _ptr(loss_out, torch.float32, "loss_out"), _stream(stream))
     _check(st, "rtg_narrow_pixels", ctx.ptr)
 
 

@@ -196,7 +196,7 @@ Layout layout_of(const rtg_capacity *c) {
   L.scan_hist = take(scan_blocks * kQueueClasses * 4);
   const size_t sel_blocks = ((size_t)c->max_width * (size_t)c->max_height + kSelPerBlock - 1) / kSelPerBlock;
   L.sel_keys = take(P * 4);
-  L.sel_small = take((4 * Fm * 256 + 5 * Fm) * 4);
+  L.sel_small = take(sel_scratch_words((int)Fm) * 4);
   L.sel_state = take(Fm * 2 * 4);
   L.sel_tie = take(Fm * sel_blocks * 4);
   L.total = o;
@@ -801,7 +801,7 @@ rtg_status rtg_render_backward_l1(rtg_ctx *ctx, float *g_means, float *g_scales,
   if (ctx == nullptr) return RTG_ERR_ARG;
   if (!ctx->has_fwd || ctx->l1.tcolor == nullptr)
     return fail(ctx, RTG_ERR_STATE, ctx->has_fwd && ctx->narrowed
-                                        ? "render_backward_l1 after narrow_pixels (use l1_loss + render_backward)"
+                                        ? "render_backward_l1 after narrow_pixels without targets"
                                         : "render_backward_l1 without a preceding render_forward_l1");
   if (!g_means || !g_scales || !g_quats || !g_opacity || !g_colors)
     return fail(ctx, RTG_ERR_ARG, "gradient output is NULL");
@@ -882,24 +882,36 @@ rtg_status rtg_select_top_error(rtg_ctx *ctx, int32_t F, int32_t C, int32_t H, i
       return check_launch(ctx, "select_top_error");
   } else {
     SelBufs b = ctx->sel;
-    b.ticket = b.hist + (size_t)4 * F * 256;
+    b.ticket = b.hist + (size_t)kSelPasses * F * kSelHistStride;
     launch_select_top_error(b, F, C, n, k, color, target_color, mask_out, s);
   }
   ctx->last_stream = s;
   return check_launch(ctx, "select_top_error");
 }
 
-rtg_status rtg_narrow_pixels(rtg_ctx *ctx, const uint8_t *mask, void *stream) {
+rtg_status rtg_narrow_pixels(rtg_ctx *ctx, const uint8_t *mask, const float *target_color,
+                             const float *target_depth, float w_color, float w_depth, float *loss_out, void *stream) {
   if (ctx == nullptr) return RTG_ERR_ARG;
   if (!ctx->has_fwd) return fail(ctx, RTG_ERR_STATE, "narrow_pixels without a preceding forward");
   if (mask == nullptr) return fail(ctx, RTG_ERR_ARG, "narrow_pixels: mask is NULL");
+  const bool fused = target_color != nullptr;
+  if (fused != (target_depth != nullptr) || (fused && loss_out == nullptr))
+    return fail(ctx, RTG_ERR_ARG, "narrow_pixels: give both targets and loss_out, or none");
   cudaStream_t s = (cudaStream_t)stream;
   const Tuning &tn = ctx->tune_fwd;
+  const NarrowLoss nl{ctx->l1.color, ctx->l1.depth, target_color, target_depth, ctx->C};
   {
     ProfScope ps(ctx, kPNarrow, s);
-    launch_narrow_pixels(ctx->w_fwd, ctx->F, ctx->T, tn.tws, tn.ths, mask, tn.schedule == 1 ? tn.gshift() : -1, s);
+    launch_narrow_pixels(ctx->w_fwd, ctx->F, ctx->T, tn.tws, tn.ths, mask, tn.schedule == 1 ? tn.gshift() : -1,
+                         nl, s);
   }
-  ctx->l1.tcolor = nullptr;  // the fused loss covered the forward's pixels, not these
+  if (fused) {
+    ProfScope ps(ctx, kPL1Loss, s);
+    launch_loss_finalize(ctx->w_fwd, ctx->F * ctx->T, tn.gshift(), ctx->C, w_color, w_depth, loss_out, s);
+  }
+  // the backward_l1 of these pixels needs their loss; a fused loss of the forward covered others
+  ctx->l1.tcolor = fused ? target_color : nullptr;
+  ctx->l1.tdepth = fused ? target_depth : nullptr;
   ctx->narrowed = true;
   ctx->last_stream = s;
   return check_launch(ctx, "narrow_pixels");

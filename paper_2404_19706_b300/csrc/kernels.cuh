@@ -157,19 +157,29 @@ enum CoverMode { kCoverPlain = 0, kCoverFusedSame = 1, kCoverFusedOther = 2 };
 void launch_mask_cover_tiles(const Work &w, const Prm &prm, int64_t N, int F, int T, int C, uint8_t *mask,
                              int mode, cudaStream_t s);
 // select.cu
-constexpr int kSelThreads = 256;   // threads per block of the top-error selection
-constexpr int kSelPerBlock = 4096; // pixels per block
-// Scratch of the top-error selection: keys [F][n] (error bits), hist [4][F][256] followed by
-// ticket [5][F] (cleared at the start of every call), state [F][2] (threshold key, equal
+constexpr int kSelThreads = 256;    // threads per block of the top-error selection
+constexpr int kSelPerBlock = 1024;  // pixels per block (4 per thread)
+constexpr int kSelPasses = 3;       // radix passes of 11, 10 and 10 bits
+constexpr int kSelHistStride = 2048;
+// Scratch of the top-error selection: keys [F][n] (error bits), hist [3][F][2048] followed by
+// ticket [4][F] (cleared at the start of every call), state [F][2] (threshold key, equal
 // keys still to take), tie [F][blocks per frame].
 struct SelBufs {
   uint32_t *keys, *hist, *ticket, *state, *tie;
 };
+inline size_t sel_scratch_words(int F) { return (size_t)kSelPasses * F * kSelHistStride + (size_t)(kSelPasses + 1) * F; }
 void launch_select_top_error(const SelBufs &b, int F, int C, int64_t n, uint32_t k, const float *color,
                              const float *target, uint8_t *mask, cudaStream_t s);
-// Keeps only the pixels set in mask [F,H,W] in the last forward's per-tile pixel lists;
-// gshift >= 0 also rebuilds the persistent schedule's queue.
+// Inputs of the L1 partials formed while narrowing (tcolor == nullptr: none): the last
+// forward's colour and depth, the targets and the channel count.
+struct NarrowLoss {
+  const float *color, *depth, *tcolor, *tdepth;
+  int C;
+};
+// Keeps only the pixels set in mask [F,H,W] in the last forward's per-tile pixel lists and
+// sets the masked-pixel counter to their number; gshift >= 0 also rebuilds the persistent
+// schedule's queue.  With nl.tcolor, also writes the fused L1 partials of the new groups.
 void launch_narrow_pixels(const Work &w, int F, int T, int tws, int ths, const uint8_t *mask, int gshift,
-                          cudaStream_t s);
+                          const NarrowLoss &nl, cudaStream_t s);
 
 }  // namespace rtg

@@ -95,10 +95,10 @@ class GlobalStep:
     "unstable" set is the whole map) and owns Adam moments for all of them.  Per call:
       1. forward of all Gaussians on every pixel of the keyframes;
       2. per keyframe, the ``frac`` pixels of largest colour error (rtg_select_top_error);
-      3. the forward narrowed to those pixels (rtg_narrow_pixels: no second render);
-      4. the L1 colour + depth loss on them (Eq. 7/8) and its image gradients;
-      5. the backward to every Gaussian, and Adam with ``global_adam`` settings, in place on
-         the full arrays of ``g``.
+      3. the forward narrowed to those pixels, with the L1 colour + depth loss (Eq. 7/8)
+         formed on them in the same pass (rtg_narrow_pixels: no second render);
+      4. the fused backward to every Gaussian, and Adam with ``global_adam`` settings, in
+         place on the full arrays of ``g``.
     The calls allocate nothing and never synchronise; ``capture()`` records one iteration in
     a CUDA graph for a fixed set of cameras and target buffers.
     """
@@ -127,21 +127,16 @@ class GlobalStep:
         self.depth = torch.full((Fm, H, W), -1.0, device=dev)
         self.alpha = torch.zeros(Fm, H, W, device=dev)
         self.selected = torch.zeros(Fm, H, W, dtype=torch.uint8, device=dev)
-        self.dL_dcolor = torch.zeros(Fm, C, H, W, device=dev)
-        self.dL_ddepth = torch.zeros(Fm, H, W, device=dev)
         self.loss = torch.zeros(3, device=dev)
         self.graph = None
 
     def _body(self, cams: Sequence, target_color: torch.Tensor, target_depth: torch.Tensor, stream=None):
         F = len(cams)
-        color, depth, alpha = self.color[:F], self.depth[:F], self.alpha[:F]
-        sel, dc, dd = self.selected[:F], self.dL_dcolor[:F], self.dL_ddepth[:F]
+        color, depth, alpha, sel = self.color[:F], self.depth[:F], self.alpha[:F], self.selected[:F]
         api.render_forward(self.ctx, list(cams), self.g, None, self.settings, color, depth, alpha, None, stream)
         api.select_top_error(self.ctx, color, target_color, self.frac, sel, stream)
-        api.narrow_pixels(self.ctx, sel, stream)
-        api.l1_loss(self.ctx, color, depth, target_color, target_depth, sel, self.w_color, self.w_depth, self.loss,
-                    dc, dd, stream)
-        api.render_backward(self.ctx, dc, dd, *self.grads, stream=stream)
+        api.narrow_pixels(self.ctx, sel, target_color, target_depth, self.w_color, self.w_depth, self.loss, stream)
+        api.render_backward_l1(self.ctx, *self.grads, stream=stream)
         api.adam_step_counted(self.params, self.grads, self.m, self.v, self.step_counter, self.hyper, stream)
         return self.loss
 

@@ -107,4 +107,4 @@ def test_struct_layouts_match_compiled_header():
 def test_global_optimisation_entry_points_reject_bad_arguments_without_gpu():
     lib = _lib.load()
     assert lib.rtg_select_top_error(None, 1, 3, 8, 8, None, None, 0.4, None, None) == _lib.RTG_ERR_ARG
-    assert lib.rtg_narrow_pixels(None, None, None) == _lib.RTG_ERR_ARG
+    assert lib.rtg_narrow_pixels(None, None, None, None, 1.0, 1.0, None, None) == _lib.RTG_ERR_ARG

@@ -144,13 +144,42 @@ def test_narrowed_backward_equals_masked_forward(tuning):
     for k in GROUPS:
         a, b = grads_a[k], grads_b[k]
         assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b) + 1e-12, k
-    # the fused backward is refused after narrowing
-    loss = torch.zeros(3, device="cuda")
-    m.render_forward_l1(ctx, cams, g, None, m.RenderSettings(), tc, td, 1.0, 1.0, color, depth,
-                        torch.zeros(F, H, W, device="cuda"), loss)
+    # fused: narrowing with the targets forms the loss for render_backward_l1, and equals a
+    # forward_l1 rendered on the mask
+    grads_c, loss_c = _fused(m, ctx, cams, g, None, sel, tc, td, scene.n, C)
+    grads_d, loss_d = _fused(m, ctx, cams, g, sel, None, tc, td, scene.n, C)
+    np.testing.assert_allclose(loss_c, loss_d, rtol=1e-6)
+    np.testing.assert_allclose(loss_c, loss_b, rtol=1e-6)
+    assert m.get_stats(ctx)["masked_pixels"] == 2 * go.keep_count(0.4, H * W)
+    for k in GROUPS:
+        assert np.linalg.norm(grads_c[k] - grads_d[k]) <= 1e-5 * np.linalg.norm(grads_d[k]) + 1e-12, k
+        assert np.linalg.norm(grads_c[k] - grads_b[k]) <= 1e-5 * np.linalg.norm(grads_b[k]) + 1e-12, k
+    # narrowing without targets refuses the fused backward
+    _render(m, ctx, cams, g, None, C, H, W)
     m.narrow_pixels(ctx, sel)
     with pytest.raises(m.RTGError):
         m.render_backward_l1(ctx, *[torch.zeros(scene.n, k, device="cuda") for k in (3, 3, 4, 1, 3)])
+    with pytest.raises(m.RTGError):  # one target without the other
+        m.narrow_pixels(ctx, sel, tc, None, 1.0, 1.0, torch.zeros(3, device="cuda"))
+
+
+def _fused(m, ctx, cams, g, render_mask, narrow_mask, tc, td, n, C):
+    """forward_l1 on render_mask (None: every pixel), then (narrow_mask) narrowing with the
+    targets, then backward_l1; returns (gradients, loss)."""
+    F, _, H, W = tc.shape
+    loss = torch.zeros(3, device="cuda")
+    color = torch.zeros(F, C, H, W, device="cuda")
+    depth = torch.full((F, H, W), -1.0, device="cuda")
+    m.render_forward_l1(ctx, cams, g, render_mask, m.RenderSettings(), tc, td, 1.0, 1.0, color, depth,
+                        torch.zeros(F, H, W, device="cuda"), loss)
+    if narrow_mask is not None:
+        m.narrow_pixels(ctx, narrow_mask, tc, td, 1.0, 1.0, loss)
+    grads = [torch.zeros(n, 3, device="cuda"), torch.zeros(n, 3, device="cuda"), torch.zeros(n, 4, device="cuda"),
+             torch.zeros(n, device="cuda"), torch.zeros(n, C, device="cuda")]
+    m.render_backward_l1(ctx, *grads)
+    torch.cuda.synchronize()
+    assert m.get_status(ctx) == 0
+    return {k: t.cpu().numpy().astype(np.float64) for k, t in zip(GROUPS, grads)}, loss.cpu().numpy()
 
 
 @pytest.mark.parametrize("seed", [3000, 3100])
