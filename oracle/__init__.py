@@ -21,6 +21,9 @@ Parity status per function (pins live in ``tests/test_oracle_pins.py``):
   adam_step          pinned (torch.optim.Adam on the same gradients)
   global_opt.*       pinned (hand-made error patterns with ties and their masks, exact keep
                      counts, closed-form rotation angles, the keyframe thresholds)
+  adding.*           pinned (SplitMix64's published outputs, a hand-made frame with every
+                     case of Eq. 6 and the opaque/transparent decision, the draw rate,
+                     back-projection in closed form)
 """
 
 from .rasterizer import (  # noqa: F401
@@ -36,4 +39,4 @@ from .rasterizer import (  # noqa: F401
     decision_signature,
 )
 from .adam import adam_step, AdamHyper  # noqa: F401
-from . import global_opt  # noqa: F401
+from . import adding, global_opt  # noqa: F401
