@@ -15,6 +15,7 @@ pixel samples per step, extrapolated to the masked pixel count).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -49,6 +50,11 @@ GLOBAL_METRIC = "global keyframe optimisation iterations/sec (4 x 640×480 keyfr
 GLOBAL = dict(name="global keyframe step: room 1M Gaussians, all optimised, 4 keyframes at 640x480 (f 600) taken "
                    "by the 30 deg / 0.3 m rule, top 40% colour-error pixels, positions fixed, 0.1x rates",
               seed=3000, n=1_000_000, frames=4, width=640, height=480, f=600.0, frac=0.4, max_pairs=40 << 20)
+ADD_METRIC = "Gaussian-adding pass frames/sec (640×480 full-frame render of a 1M-Gaussian map + Eq. 6 masks, 5% draw)"
+ADDING = dict(name="adding pass: room 1M Gaussians minus one 50k-Gaussian blob (the newly seen region), 640x480 "
+                   "(f 600) full-frame render with index map, input frame = render of the whole room with a 25k-"
+                   "Gaussian stable patch recoloured by +0.3, 5% draw",
+              seed=3000, n=1_000_000, missing=50_000, width=640, height=480, f=600.0, capacity=1 << 16)
 C = 3
 
 
@@ -62,11 +68,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--candidate", type=int, default=-1, help="camera candidate index (-1: search)")
-    ap.add_argument("--workload", default="masked-step", choices=["masked-step", "keyframes", "large", "global"],
+    ap.add_argument("--workload", default="masked-step", choices=["masked-step", "keyframes", "large", "global", "adding"],
                     help="masked-step: the 640x480 masked iteration (default); keyframes: 8 batched 1200x680 "
                          "keyframes vs per-frame launches; large: 32 batched 1200x680 keyframes, 5M Gaussians, "
                          "8 channels; global: the global keyframe optimisation step (4 keyframes, top-40% "
-                         "pixels, every Gaussian)")
+                         "pixels, every Gaussian); adding: the Gaussian-adding pass (full-frame render, Eq. 6 "
+                         "masks, 5% draw)")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--tune-table", default="", help="write the autotuner's candidate table (JSON) to this path")
     ap.add_argument("--tuning", default="",
@@ -1019,6 +1026,206 @@ def run_global(args, kw=GLOBAL):
     return out
 
 
+# ----------------------------------------------------------------------------- GPU arm: adding pass
+
+class BoundAddingPass:
+    """An AddingPass with its frame bound, replayed from a CUDA graph (the seed is fixed in
+    the graph; each replay redoes the same draw)."""
+
+    def __init__(self, ap, cams, g, color, depth, seed):
+        self.ap, self.cams, self.g, self.color, self.depth, self.seed = ap, cams, g, color, depth, seed
+        self.graph = None
+
+    def _body(self):
+        return self.ap.run(self.cams, self.g, self.color, self.depth, self.seed)
+
+    def step(self):
+        if self.graph is not None:
+            self.graph.replay()
+            return self.ap.count
+        return self._body()
+
+    def capture(self):
+        import torch
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            self._body()
+        torch.cuda.synchronize()
+        self.graph = graph
+
+
+def oracle_adding_rate(scene, cam, maps, budget_px=48):
+    """Frames/s of the FP64 oracle on the adding pass, from bounded samples: the full-frame
+    render = fixed whole-scene cost (one pixel) + H*W x per-pixel cost (random pixels with the
+    Gaussians that reach them); plus the oracle's Eq. 6 masks and draw on the full maps,
+    timed directly."""
+    import torch
+    import oracle
+    from oracle import adding as ad
+    st = oracle.Settings()
+    H, W = cam.height, cam.width
+    rng = np.random.default_rng(4)
+    pix = np.stack([rng.integers(0, W, budget_px), rng.integers(0, H, budget_px)], 1)
+    t0 = time.perf_counter()
+    oracle.render(scene, cam, st, pixels=pix[:1], need_borderline=False)
+    fix = time.perf_counter() - t0
+    sub = scene.subset(reach_subset(scene, cam, pix))
+    t0 = time.perf_counter()
+    oracle.render(sub, cam, st, pixels=pix, need_borderline=False)
+    per = (time.perf_counter() - t0) / budget_px
+    t0 = time.perf_counter()
+    ad.add_candidates([cam], *maps, ad.AddParams(seed=1))
+    cand = time.perf_counter() - t0
+    it_s = fix + H * W * per + cand
+    return dict(value=1.0 / it_s, unit="frames/s", cores=int(torch.get_num_threads()), kind="oracle",
+                sample=f"FP64 oracle render: fixed cost on 1 pixel ({fix:.1f} s) + {H * W} px x per-pixel cost from "
+                       f"{budget_px} random pixels with the Gaussians that reach them; plus the oracle's masks, draw "
+                       f"and outputs on the full maps ({cand:.2f} s), extrapolated")
+
+
+def run_adding(args, kw=ADDING):
+    import torch
+    import paper_2404_19706_b300 as rtg
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    settings = rtg.RenderSettings()
+    H, W = kw["height"], kw["width"]
+    scene, layout = synth.room_scene(kw["seed"], kw["n"])
+    cams = synth.room_camera_candidates(kw["seed"] + 1, layout, W, H, kw["f"])
+    for _ in range(DEFAULT_CANDIDATE + 1):
+        cam = next(cams)
+    ctx = rtg.Context(max_gaussians=scene.n, max_frames=1, max_width=W, max_height=H, max_pairs=24 * scene.n)
+    # input frame: the whole room, with one patch recoloured (colour error on correct
+    # geometry); the map: the room without one blob of Gaussians in view (new geometry)
+    missing = synth.flag_blobs(scene, [cam], kw["missing"], 1, seed=kw["seed"] + 300, n_in_view=1).astype(bool)
+    keep = np.flatnonzero(~missing)
+    part = scene.subset(keep)
+    part.unstable = synth.flag_blobs(part, [cam], 200_000, 3, seed=kw["seed"] + 107, n_in_view=1)
+    stable = np.flatnonzero(part.unstable == 0)  # the recoloured patch lies on stable Gaussians
+    patch = synth.flag_blobs(part.subset(stable), [cam], kw["missing"] // 2, 1, seed=kw["seed"] + 301, n_in_view=1)
+    recol = np.zeros(scene.n, dtype=bool)
+    recol[keep[stable[patch.astype(bool)]]] = True
+    seen = scene.copy()
+    seen.colors = np.where(recol[:, None], np.clip(seen.colors + 0.3, -1.0, 2.0), seen.colors).astype(np.float32)
+    icol = torch.zeros(1, C, H, W, device=dev)
+    idep = torch.full((1, H, W), -1.0, device=dev)
+    rtg.render_forward(ctx, [cam], rtg.Gaussians.from_scene(seen, device=dev), None, settings, icol, idep,
+                       torch.zeros(1, H, W, device=dev))
+    idep = torch.where(idep > 0, idep, torch.zeros_like(idep))
+    g = rtg.Gaussians.from_scene(part, device=dev)
+    # the stability flags are fixed during the run: their index is computed once
+    rank_map, ids, nu = rtg.unstable_rank(ctx, g.unstable)
+    g = dataclasses.replace(g, rank_map=rank_map, unstable_ids=ids, n_unstable=nu)
+    ap = rtg.AddingPass(ctx, W, H, capacity=kw["capacity"])
+    step = BoundAddingPass(ap, [cam], g, icol, idep, seed=kw["seed"])
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ck = dict(color=torch.zeros_like(icol), depth=torch.zeros_like(idep), alpha=torch.zeros_like(idep))
+
+    def check():
+        rtg.render_forward(ctx, [cam], g, None, settings, ck["color"], ck["depth"], ck["alpha"])
+        return [ck["color"], ck["depth"], ck["alpha"]]
+
+    tuned = run_tuner(ctx, step._body, check, [], args, "adding")
+    for _ in range(args.warmup):
+        step.step()
+    torch.cuda.synchronize()
+    stats = rtg.get_stats(ctx)
+    assert stats["status"] == 0, stats
+    n_new = int(ap.count.item())
+    kinds = ap.kind[:min(n_new, kw["capacity"])].cpu().numpy()
+    step.capture()
+    step.step()
+    torch.cuda.synchronize()
+    ms_step, wall, clocks = timed_replays(step, args.steps, flush, stream, local)
+    per_launch = kernel_profile_adding(rtg, ctx, step, args.steps, flush)
+    P, K = H * W, stats["pairs"]
+    alg = alg_bytes(dict(stats, masked_pixels=P), part.n, 1, H, W)
+    for k in ("backward", "project_backward", "adam", "l1_loss", "unstable_mask", "bin", "unstable_index"):
+        alg.pop(k, None)
+    # the drawn pixels (sample rate) read depth, alpha, rendered depth, index, both colours and a
+    # flag; every new Gaussian writes pixel, kind, position, colour and opacity
+    rate = ap.add.sample_rate
+    alg["add_candidates"] = int(rate * P * (4 * 4 + 2 * 4 * C + 1)) + n_new * (4 + 1 + 12 + 4 * C + 4)
+    roofline, pk = roofline_of(per_launch, alg, ctx.get_tuning(), "adding", extra_kinds=("add_candidates",))
+    b_step = sum(alg.values())
+    # end to end: the input frame uploaded from pinned host memory, the count read back
+    hc = torch.empty_like(icol, device="cpu").pin_memory()
+    hd = torch.empty_like(idep, device="cpu").pin_memory()
+    hc.copy_(icol.cpu())
+    hd.copy_(idep.cpu())
+    hcount = torch.empty(1, dtype=torch.int64, pin_memory=True)
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        icol.copy_(hc, non_blocking=True)
+        idep.copy_(hd, non_blocking=True)
+        cnt = step.step()
+        hcount.copy_(cnt, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        if i >= args.warmup:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_step = float(np.mean(e2e_ms))
+    tuning = ctx.get_tuning()
+    if rank != 0:
+        return None
+    FT = ((W + tuning.tile_w - 1) // tuning.tile_w) * ((H + tuning.tile_h - 1) // tuning.tile_h)
+    launches = 6 + (1 if FT <= 8192 else 3) + 3  # forward (no index pass: precomputed) + adding
+    fixed = "fixed by --tuning" if args.tuning else "off (--no-tune)"
+    out = {
+        "metric": ADD_METRIC, "value": round(1e3 / ms_step, 2), "unit": "frames/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": kw["name"], "gaussians_in_map": part.n, "width": W, "height": H,
+                   "camera_candidate": DEFAULT_CANDIDATE, "new_gaussians": n_new,
+                   "new_opaque": int((kinds == 1).sum()), "new_transparent": int((kinds == 2).sum()),
+                   "pairs": K, "visible": stats["visible"], "fragments_per_step": stats["fragments"],
+                   "alg_bytes_per_step": int(b_step),
+                   "step_hbm_roofline_frac": round(b_step / (ms_step * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
+                   "tuning": tuning.as_dict(), "autotune": tuned.summary() if tuned is not None else fixed,
+                   "l2": "256 MB buffer written before every step, outside the timed spans",
+                   "timing": "timed steps replay one CUDA graph of the pass; kernel_ms_per_launch from a live eager "
+                             "pass with per-kernel CUDA events",
+                   "wall_s_timed_region": round(wall, 3),
+                   "kernel_ms_per_launch": {k: round(v, 5) for k, v in per_launch.items()},
+                   "parallelism": "replicas x1"},
+        "roofline": roofline,
+        "e2e": {"value": round(1e3 / e2e_step, 2), "unit": "frames/s",
+                "h2d_bytes_per_step": int(hc.numel() * 4 + hd.numel() * 4), "d2h_bytes_per_step": 8},
+        "gpu_launches": launches * args.steps,
+        "clocks": clocks.summary(),
+    }
+    if not args.no_cpu_baseline:
+        maps = (ap.color.cpu().numpy(), ap.alpha.cpu().numpy(), ap.depth.cpu().numpy(), ap.index.cpu().numpy(),
+                icol.cpu().numpy(), idep.cpu().numpy(), part.unstable)
+        out["cpu_baseline"] = oracle_adding_rate(part, cam, maps)
+    ctx.close()
+    return out
+
+
+def kernel_profile_adding(rtg, ctx, step, steps, flush):
+    """Per-kernel device ms per launch from eager passes with the library's tracing on."""
+    import torch
+    graph, step.graph = step.graph, None
+    try:
+        rtg.profile_enable(ctx, True)
+        rtg.profile_read(ctx)
+        for _ in range(steps):
+            flush.zero_()
+            step.step()
+        torch.cuda.synchronize()
+        prof = rtg.profile_read(ctx)
+        rtg.profile_enable(ctx, False)
+    finally:
+        step.graph = graph
+    return {k: (v[1] / v[0] if v[0] else 0.0) for k, v in prof.items()}
+
+
 def cpu_baseline_from_gpu(scene, cam, mask, tcol, tdep, n_masked):
     m = mask[0].cpu().numpy().astype(bool)
     ys, xs = np.nonzero(m)
@@ -1093,13 +1300,15 @@ DEFAULT_CANDIDATE = 7  # first pose of the seeded stream with 25-40% mask covera
 def main():
     args = parse()
     if args.steps <= 0:
-        args.steps = {"keyframes": 60, "large": 20, "global": 100}.get(args.workload, 400)
+        args.steps = {"keyframes": 60, "large": 20, "global": 100, "adding": 200}.get(args.workload, 400)
     if args.impl == "reference":
         out = run_reference(args)
     elif args.workload in ("keyframes", "large"):
         out = run_keyframes(args, KEYFRAMES if args.workload == "keyframes" else LARGE)
     elif args.workload == "global":
         out = run_global(args)
+    elif args.workload == "adding":
+        out = run_adding(args)
     else:
         out = run_ours(args)
     if out is not None:

@@ -277,6 +277,44 @@ rtg_status rtg_select_top_error(rtg_ctx *ctx, int32_t F, int32_t C, int32_t H, i
 rtg_status rtg_narrow_pixels(rtg_ctx *ctx, const uint8_t *mask, const float *target_color, const float *target_depth,
                              float w_color, float w_depth, float *loss_out, void *stream);
 
+/* Gaussian adding (Section 3.2, "Gaussians adding", Eq. 6).  From a full-frame render of
+ * the map (rtg_render_forward with mask NULL: render_color [F,C,H,W], render_alpha,
+ * render_depth [F,H,W] float32, index_map [F,H,W] int32) and the input frame (color
+ * [F,C,H,W], depth [F,H,W] float32, <= 0 = no measurement), the pixels that get a new
+ * Gaussian:
+ *   M_s: 1 - alpha > delta_T or |D_hat - D| > delta_d (D_hat = -1 without a hit): new
+ *        geometry, an opaque Gaussian (opacity_opaque);
+ *   M_c: not in M_s and the mean over channels of |C_hat - C| > delta_c, tested as the
+ *        float32 sum (channel order) > C * delta_c: a transparent Gaussian
+ *        (opacity_transparent), unless the Gaussian of the pixel's depth hit (index map)
+ *        is unstable (unstable[i] != 0) or there is none, when nothing is added.
+ * Pixels with depth <= 0 are in neither.  Every decision is taken in float32.  Of these, a
+ * uniform sample_rate is drawn: pixel p of frame f is drawn iff the top 24 bits of output
+ * number f*H*W + p of the SplitMix64 stream seeded with `seed` are below
+ * floor(sample_rate * 2^24) (computed in double precision).
+ * Outputs, in ascending (frame, pixel) order, for the first `capacity` new Gaussians:
+ * pixel_out [capacity] int32 (f*H*W + y*W + x), kind_out [capacity] uint8 (1 opaque,
+ * 2 transparent), position_out [capacity,3] float32 (R (D K^-1 (x, y, 1)) + t with the
+ * frame's camera-to-world pose), color_out [capacity,C] (the input colour), opacity_out
+ * [capacity].  count_out (device int64) receives the number of new Gaussians, which may
+ * exceed capacity (then only the first capacity are written).  Scales and rotations of the
+ * new Gaussians (Supplement A) are the caller's.  cams: HOST array of F cameras of one
+ * size; unstable [n_gaussians] uint8 (device).  Uses the context's workspace only; needs no
+ * forward on this context (the render may come from any). */
+typedef struct {
+  float delta_T, delta_d, delta_c; /* 0.5, 0.1 m, 0.1 */
+  float sample_rate;               /* 0.05 */
+  float opacity_opaque;            /* 0.99 */
+  float opacity_transparent;       /* 0.1 */
+  uint64_t seed;
+} rtg_add_params;
+rtg_status rtg_add_candidates(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, int32_t C, const float *render_color,
+                              const float *render_alpha, const float *render_depth, const int32_t *index_map,
+                              const float *color, const float *depth, const uint8_t *unstable, int64_t n_gaussians,
+                              const rtg_add_params *p, int64_t capacity, int64_t *count_out, int32_t *pixel_out,
+                              uint8_t *kind_out, float *position_out, float *color_out, float *opacity_out,
+                              void *stream);
+
 /* Adam (Kingma & Ba, Algorithm 1) on compact unstable parameters, in place, with the
  * per-group learning rates of Supplement C.  The scale is optimised in log space
  * (s <- s * exp(-step), gradient s * dL/ds).  m and v hold nu * (11 + C) float32 each,

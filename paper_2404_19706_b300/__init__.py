@@ -11,6 +11,8 @@ _lib.load()
 
 from .api import (  # noqa: E402,F401
     AdamSettings,
+    AddSettings,
+    add_candidates,
     Context,
     Gaussians,
     RenderSettings,
@@ -46,5 +48,6 @@ from .api import (  # noqa: E402,F401
 )
 from .optim import MaskedStep, RasterState, RTGRasterize, rasterize  # noqa: E402,F401
 from .keyframes import GlobalStep, KeyframeSet, global_adam  # noqa: E402,F401
+from .adding import AddingPass  # noqa: E402,F401
 
 LIBRARY_PATH = _lib.LIB_PATH

@@ -63,6 +63,11 @@ class rtg_adam_params(Structure):
                                        "beta2", "eps")]
 
 
+class rtg_add_params(Structure):
+    _fields_ = [("delta_T", c_float), ("delta_d", c_float), ("delta_c", c_float), ("sample_rate", c_float),
+                ("opacity_opaque", c_float), ("opacity_transparent", c_float), ("seed", ctypes.c_uint64)]
+
+
 # (name, restype, argtypes) of every entry point declared in include/rtg.h
 SIGNATURES = [
     ("rtg_workspace_size", c_int32, [POINTER(rtg_capacity), POINTER(c_size_t)]),
@@ -89,6 +94,8 @@ SIGNATURES = [
     ("rtg_window_is_open", c_int32, [c_void_p]),
     ("rtg_select_top_error", c_int32, [c_void_p, c_int32, c_int32, c_int32, c_int32, c_void_p, c_void_p,
                                        ctypes.c_double, c_void_p, c_void_p]),
+    ("rtg_add_candidates", c_int32, [c_void_p, POINTER(rtg_camera), c_int32, c_int32] + [c_void_p] * 7 +
+     [c_int64, POINTER(rtg_add_params), c_int64] + [c_void_p] * 6 + [c_void_p]),
     ("rtg_narrow_pixels", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_float, c_void_p,
                                     c_void_p]),
     ("rtg_get_tuning", c_int32, [c_void_p, POINTER(rtg_tuning)]),

@@ -89,6 +89,22 @@ class AdamSettings:
         return rtg_adam_params(*(float(getattr(self, f.name)) for f in dataclasses.fields(self)))
 
 
+@dataclasses.dataclass(frozen=True)
+class AddSettings:
+    """Thresholds of the Gaussian-adding masks (Section 3.2, Eq. 6), the sampled fraction and
+    the opacities of new opaque / transparent Gaussians (rtg_add_params, without the seed)."""
+    delta_T: float = 0.5
+    delta_d: float = 0.1
+    delta_c: float = 0.1
+    sample_rate: float = 0.05
+    opacity_opaque: float = 0.99
+    opacity_transparent: float = 0.1
+
+    def to_c(self, seed: int) -> "_lib.rtg_add_params":
+        return _lib.rtg_add_params(self.delta_T, self.delta_d, self.delta_c, self.sample_rate, self.opacity_opaque,
+                                   self.opacity_transparent, int(seed) & ((1 << 64) - 1))
+
+
 def make_camera(cam) -> rtg_camera:
     """Any object with fx, fy, cx, cy, width, height, R [3,3] (camera-to-world), t [3]."""
     c = rtg_camera()
@@ -362,6 +378,28 @@ def narrow_pixels(ctx: Context, mask: torch.Tensor, target_color: Optional[torch
                                        _ptr(target_depth, torch.float32, "target_depth"), float(w_color),
                                        float(w_depth), _ptr(loss_out, torch.float32, "loss_out"), _stream(stream))
     _check(st, "rtg_narrow_pixels", ctx.ptr)
+
+
+def add_candidates(ctx: Context, cams, render_color, render_alpha, render_depth, index_map, color, depth,
+                   unstable: torch.Tensor, settings: AddSettings, seed: int, count_out: torch.Tensor,
+                   pixel_out: torch.Tensor, kind_out: torch.Tensor, position_out: torch.Tensor,
+                   color_out: torch.Tensor, opacity_out: torch.Tensor, stream=None):
+    """The new Gaussians of the adding pass (rtg_add_candidates): up to pixel_out.numel() of
+    them written in (frame, pixel) order; count_out [1] int64 receives their number."""
+    arr, F = _cams(cams)
+    C = int(render_color.shape[1])
+    cap = int(pixel_out.numel())
+    prm = settings.to_c(seed)
+    st = _lib.load().rtg_add_candidates(
+        ctx.ptr, arr, F, C, _ptr(render_color, torch.float32, "render_color"),
+        _ptr(render_alpha, torch.float32, "render_alpha"), _ptr(render_depth, torch.float32, "render_depth"),
+        _ptr(index_map, torch.int32, "index_map"), _ptr(color, torch.float32, "color"),
+        _ptr(depth, torch.float32, "depth"), _ptr(unstable, torch.uint8, "unstable"), int(unstable.numel()),
+        ctypes.byref(prm), cap, _ptr(count_out, torch.int64, "count_out"), _ptr(pixel_out, torch.int32, "pixel_out"),
+        _ptr(kind_out, torch.uint8, "kind_out"), _ptr(position_out, torch.float32, "position_out"),
+        _ptr(color_out, torch.float32, "color_out"), _ptr(opacity_out, torch.float32, "opacity_out"),
+        _stream(stream))
+    _check(st, "rtg_add_candidates", ctx.ptr)
 
 
 _DUMMY = {}

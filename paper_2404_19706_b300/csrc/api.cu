@@ -58,12 +58,12 @@ struct rtg_ctx {
 // Kernel kinds reported by the tracing interface (one launcher each).
 enum ProfKind {
   kPTileMask, kPUnstableIndex, kPProject, kPScanTiles, kPEmit, kPSortTiles, kPForward, kPL1Loss, kPBackward,
-  kPProjectBackward, kPUnstableMask, kPBin, kPSelect, kPNarrow, kPNumKinds
+  kPProjectBackward, kPUnstableMask, kPBin, kPSelect, kPNarrow, kPAdd, kPNumKinds
 };
 static const char *kProfNames[kPNumKinds] = {"tile_mask", "unstable_index", "project", "scan_tiles",
                                              "emit", "sort_tiles", "forward", "l1_loss",
                                              "backward", "project_backward", "unstable_mask", "bin",
-                                             "select_top_error", "narrow_pixels"};
+                                             "select_top_error", "narrow_pixels", "add_candidates"};
 constexpr int kProfMaxRecords = 1 << 16;
 
 struct ProfRec {
@@ -915,6 +915,66 @@ rtg_status rtg_narrow_pixels(rtg_ctx *ctx, const uint8_t *mask, const float *tar
   ctx->narrowed = true;
   ctx->last_stream = s;
   return check_launch(ctx, "narrow_pixels");
+}
+
+rtg_status rtg_add_candidates(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, int32_t C, const float *render_color,
+                              const float *render_alpha, const float *render_depth, const int32_t *index_map,
+                              const float *color, const float *depth, const uint8_t *unstable, int64_t n_gaussians,
+                              const rtg_add_params *p, int64_t capacity, int64_t *count_out, int32_t *pixel_out,
+                              uint8_t *kind_out, float *position_out, float *color_out, float *opacity_out,
+                              void *stream) {
+  if (ctx == nullptr) return RTG_ERR_ARG;
+  if (cams == nullptr || p == nullptr || count_out == nullptr)
+    return fail(ctx, RTG_ERR_ARG, "add_candidates: NULL cameras, params or count_out");
+  if (F < 1 || F > ctx->cap.max_frames || C < 1 || C > 64)
+    return fail(ctx, RTG_ERR_ARG, "add_candidates: F or C out of range");
+  const int W = cams[0].width, H = cams[0].height;
+  for (int f = 0; f < F; ++f) {
+    if (cams[f].width != W || cams[f].height != H)
+      return fail(ctx, RTG_ERR_ARG, "add_candidates: all cameras must share width and height");
+    if (!(cams[f].fx > 0.f) || !(cams[f].fy > 0.f))
+      return fail(ctx, RTG_ERR_ARG, "add_candidates: focal lengths must be positive");
+  }
+  if (W < 1 || H < 1 || W > ctx->cap.max_width || H > ctx->cap.max_height)
+    return fail(ctx, RTG_ERR_ARG, "add_candidates: image outside the capacity");
+  if (!render_color || !render_alpha || !render_depth || !index_map || !color || !depth)
+    return fail(ctx, RTG_ERR_ARG, "add_candidates: NULL image");
+  if (n_gaussians < 0 || (n_gaussians > 0 && unstable == nullptr))
+    return fail(ctx, RTG_ERR_ARG, "add_candidates: bad Gaussian count or NULL flags");
+  if (capacity < 0 || (capacity > 0 && (!pixel_out || !kind_out || !position_out || !color_out || !opacity_out)))
+    return fail(ctx, RTG_ERR_ARG, "add_candidates: bad capacity or NULL output");
+  if (!(p->sample_rate >= 0.f && p->sample_rate <= 1.f))
+    return fail(ctx, RTG_ERR_ARG, "add_candidates: sample_rate outside [0, 1]");
+  AddArgs a;
+  a.C = C; a.H = H; a.W = W; a.n = n_gaussians;
+  a.rcolor = render_color; a.ralpha = render_alpha; a.rdepth = render_depth; a.index = index_map;
+  a.color = color; a.depth = depth; a.unstable = unstable;
+  a.dT = p->delta_T; a.dd = p->delta_d;
+  a.thr_c = (float)C * p->delta_c;  // float32 product, as the mean test's threshold
+  a.op_opaque = p->opacity_opaque; a.op_transparent = p->opacity_transparent;
+  a.seed = p->seed;
+  a.t24 = (uint32_t)floor((double)p->sample_rate * 16777216.0);
+  a.capacity = capacity;
+  a.count_out = (long long *)count_out;
+  a.pix_out = pixel_out; a.kind_out = kind_out; a.pos_out = position_out; a.col_out = color_out;
+  a.op_out = opacity_out;
+  a.cnt = ctx->sel.tie;
+  a.kinds = reinterpret_cast<uint8_t *>(ctx->sel.keys);  // F*H*W bytes of its F*H*W words
+  AddFrames fr;
+  memset(&fr, 0, sizeof(fr));
+  for (int f = 0; f < F; ++f) {
+    AddCam &c = fr.cam[f];
+    c.fx = cams[f].fx; c.fy = cams[f].fy; c.cx = cams[f].cx; c.cy = cams[f].cy;
+    for (int k = 0; k < 9; ++k) c.R[k] = cams[f].R[k];
+    for (int k = 0; k < 3; ++k) c.t[k] = cams[f].t[k];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  {
+    ProfScope ps(ctx, kPAdd, s);
+    launch_add_candidates(a, fr, F, s);
+  }
+  ctx->last_stream = s;
+  return check_launch(ctx, "add_candidates");
 }
 
 rtg_status rtg_adam_step(int64_t nu, int32_t C, float *means, float *scales, float *quats, float *opacity,

@@ -181,5 +181,35 @@ struct NarrowLoss {
 // schedule's queue.  With nl.tcolor, also writes the fused L1 partials of the new groups.
 void launch_narrow_pixels(const Work &w, int F, int T, int tws, int ths, const uint8_t *mask, int gshift,
                           const NarrowLoss &nl, cudaStream_t s);
+// adding.cu
+// Arguments of the Gaussian-adding pass: the render (colour [F,C,H,W], alpha, depth, index
+// map [F,H,W]), the input frame (colour, depth), the stability flags, the thresholds (the
+// colour one as C * delta_c), the draw (seed, floor(rate * 2^24)) and the outputs.
+struct AddArgs {
+  int C, H, W;
+  int64_t n;
+  const float *rcolor, *ralpha, *rdepth;
+  const int32_t *index;
+  const float *color, *depth;
+  const uint8_t *unstable;
+  float dT, dd, thr_c, op_opaque, op_transparent;
+  uint64_t seed;
+  uint32_t t24;
+  int64_t capacity;
+  long long *count_out;
+  int32_t *pix_out;
+  uint8_t *kind_out;
+  float *pos_out, *col_out, *op_out;
+  uint32_t *cnt;    // [F][blocks per frame] counts, then bases (the selection's tie scratch)
+  uint8_t *kinds;   // [F][H][W] kind of each pixel (the selection's key scratch)
+};
+struct AddCam {
+  float fx, fy, cx, cy;
+  float R[9], t[3];
+};
+struct AddFrames {
+  AddCam cam[kMaxFrames];
+};
+void launch_add_candidates(const AddArgs &a, const AddFrames &fr, int F, cudaStream_t s);
 
 }  // namespace rtg
