@@ -24,6 +24,8 @@ Parity status per function (pins live in ``tests/test_oracle_pins.py``):
   adding.*           pinned (SplitMix64's published outputs, a hand-made frame with every
                      case of Eq. 6 and the opaque/transparent decision, the draw rate,
                      back-projection in closed form)
+  state.*            pinned (hand-made confidence, fusion-weight, error-count, transition and
+                     compaction cases)
 """
 
 from .rasterizer import (  # noqa: F401
@@ -39,4 +41,4 @@ from .rasterizer import (  # noqa: F401
     decision_signature,
 )
 from .adam import adam_step, AdamHyper  # noqa: F401
-from . import adding, global_opt  # noqa: F401
+from . import adding, global_opt, state  # noqa: F401
