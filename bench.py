@@ -55,6 +55,12 @@ ADDING = dict(name="adding pass: room 1M Gaussians minus one 50k-Gaussian blob (
                    "(f 600) full-frame render with index map, input frame = render of the whole room with a 25k-"
                    "Gaussian stable patch recoloured by +0.3, 5% draw",
               seed=3000, n=1_000_000, missing=50_000, width=640, height=480, f=600.0, capacity=1 << 16)
+STATE_METRIC = ("state-management pass frames/sec (640×480 render of a 1M-Gaussian map, error counts, transitions, "
+                "pruning, Eq. 9 fusion of 200k Gaussians)")
+STATE = dict(name="state pass: room 1M Gaussians (200k unstable in 3 blobs), 640x480 (f 600) full-frame render with "
+                  "index map, error counts against a render of the jittered room, stable/unstable transitions at "
+                  "frame 1000, pruning of stale unstable Gaussians, Eq. 9 fusion of the 200k unstable Gaussians",
+             seed=3000, n=1_000_000, n_unstable=200_000, width=640, height=480, f=600.0, frame=1000)
 C = 3
 
 
@@ -68,12 +74,13 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--candidate", type=int, default=-1, help="camera candidate index (-1: search)")
-    ap.add_argument("--workload", default="masked-step", choices=["masked-step", "keyframes", "large", "global", "adding"],
+    ap.add_argument("--workload", default="masked-step", choices=["masked-step", "keyframes", "large", "global", "adding", "state"],
                     help="masked-step: the 640x480 masked iteration (default); keyframes: 8 batched 1200x680 "
                          "keyframes vs per-frame launches; large: 32 batched 1200x680 keyframes, 5M Gaussians, "
                          "8 channels; global: the global keyframe optimisation step (4 keyframes, top-40% "
                          "pixels, every Gaussian); adding: the Gaussian-adding pass (full-frame render, Eq. 6 "
-                         "masks, 5% draw)")
+                         "masks, 5% draw); state: fusion and state management (render, error counts, "
+                         "transitions, pruning, Eq. 9 fusion)")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--tune-table", default="", help="write the autotuner's candidate table (JSON) to this path")
     ap.add_argument("--tuning", default="",
@@ -1226,6 +1233,209 @@ def kernel_profile_adding(rtg, ctx, step, steps, flush):
     return {k: (v[1] / v[0] if v[0] else 0.0) for k, v in prof.items()}
 
 
+# ----------------------------------------------------------------------------- GPU arm: state management
+
+class StatePass:
+    """One state-management pass per frame, on preallocated buffers: full-frame render of the
+    map with its index map, error counts, transitions, pruning into a second set of arrays,
+    and the Eq. 9 fusion of the window's optimised Gaussians."""
+
+    def __init__(self, rtg, ctx, g, state, cam, icol, idep, ids, compact, frame, settings):
+        self.rtg, self.ctx, self.g, self.state, self.cam = rtg, ctx, g, state, cam
+        self.icol, self.idep, self.ids, self.compact, self.frame, self.settings = icol, idep, ids, compact, frame, settings
+        import torch
+        H, W = icol.shape[2], icol.shape[3]
+        dev = icol.device
+        self.rc = torch.zeros_like(icol)
+        self.rd = torch.zeros(1, H, W, device=dev)
+        self.ra = torch.zeros(1, H, W, device=dev)
+        self.ri = torch.zeros(1, H, W, dtype=torch.int32, device=dev)
+        self.src = state.arrays()
+        self.dst = rtg.MapArrays.empty_like(self.src)
+        self.count = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.graph = None
+
+    def _body(self):
+        r, st = self.rtg, self.state
+        r.render_forward(self.ctx, [self.cam], self.g, None, self.settings, self.rc, self.rd, self.ra, self.ri)
+        st.count_errors(self.rc, self.rd, self.ri, self.icol, self.idep)
+        st.update(self.frame)
+        r.compact_gaussians(self.ctx, st.remove, self.src, self.dst, self.count)
+        st.fuse(self.ids, self.compact)
+        return self.count
+
+    def step(self):
+        if self.graph is not None:
+            self.graph.replay()
+            return self.count
+        return self._body()
+
+    def capture(self):
+        import torch
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            self._body()
+        torch.cuda.synchronize()
+        self.graph = graph
+
+
+def oracle_state_rate(scene, cam, maps, arrays, budget_px=48):
+    """Frames/s of the oracle on the state pass: the full-frame render (fixed + per-pixel
+    costs from samples, as for the adding pass) plus its error counts, transitions, pruning
+    and fusion on the full arrays, timed directly."""
+    import torch
+    import oracle
+    from oracle import state as so
+    st = oracle.Settings()
+    H, W = cam.height, cam.width
+    rng = np.random.default_rng(6)
+    pix = np.stack([rng.integers(0, W, budget_px), rng.integers(0, H, budget_px)], 1)
+    t0 = time.perf_counter()
+    oracle.render(scene, cam, st, pixels=pix[:1], need_borderline=False)
+    fix = time.perf_counter() - t0
+    sub = scene.subset(reach_subset(scene, cam, pix))
+    t0 = time.perf_counter()
+    oracle.render(sub, cam, st, pixels=pix, need_borderline=False)
+    per = (time.perf_counter() - t0) / budget_px
+    rc, rd, ri, ic, idep = maps
+    full, comp, ids, eta0, eta, err, t0a, unstable = arrays
+    t1 = time.perf_counter()
+    counts = so.error_flags(rc, rd, ri, ic, idep, unstable)
+    u, e, r, rm = so.update_states(unstable, eta, err + counts, t0a, 1000)
+    so.compact(dict(full, unstable=u, eta=e, err=r, t0=t0a), rm)
+    so.fuse_window(full, comp, ids, eta0, e)
+    rest = time.perf_counter() - t1
+    it_s = fix + H * W * per + rest
+    return dict(value=1.0 / it_s, unit="frames/s", cores=int(torch.get_num_threads()), kind="oracle",
+                sample=f"FP64 oracle render: fixed cost on 1 pixel ({fix:.1f} s) + {H * W} px x per-pixel cost from "
+                       f"{budget_px} random pixels with the Gaussians that reach them; plus the oracle's error counts, "
+                       f"transitions, pruning and fusion on the full arrays ({rest:.2f} s), extrapolated")
+
+
+def run_state(args, kw=STATE):
+    import torch
+    import paper_2404_19706_b300 as rtg
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    settings = rtg.RenderSettings()
+    H, W = kw["height"], kw["width"]
+    scene, cams = scene_and_candidates()
+    for k in range(DEFAULT_CANDIDATE + 1):
+        cam = next(cams)
+    scene.unstable = flags_for(scene, cam, DEFAULT_CANDIDATE)
+    ctx = rtg.Context(max_gaussians=scene.n, max_frames=1, max_width=W, max_height=H, max_pairs=24 * scene.n)
+    # input frame: a render of the jittered room
+    gt = rtg.Gaussians.from_scene(synth.jitter_scene(scene, kw["seed"] + 7), device=dev)
+    icol = torch.zeros(1, C, H, W, device=dev)
+    idep = torch.full((1, H, W), -1.0, device=dev)
+    rtg.render_forward(ctx, [cam], gt, None, settings, icol, idep, torch.zeros(1, H, W, device=dev))
+    idep = torch.where(idep > 0, idep, torch.zeros_like(idep))
+    del gt
+    g = rtg.Gaussians.from_scene(scene, device=dev)
+    rank_map, ids, nu = rtg.unstable_rank(ctx, g.unstable)
+    g = dataclasses.replace(g, rank_map=rank_map, unstable_ids=ids, n_unstable=nu)
+    rng = np.random.default_rng(kw["seed"] + 9)
+    t0 = torch.as_tensor(rng.integers(0, kw["frame"], scene.n).astype(np.int32), device=dev)
+    state = rtg.MapState(ctx, g, t0=t0)
+    state.eta.copy_(torch.as_tensor(rng.integers(0, 150, scene.n).astype(np.int32), device=dev))
+    state.err.copy_(torch.as_tensor(rng.integers(0, 12, scene.n).astype(np.int32), device=dev))
+    state.window_start()
+    compact = rtg.gather_unstable(ids, g)  # the window's optimised Gaussians (a copy, moved a little)
+    for c in compact:
+        c.add_(0.001)
+    state.eta[ids.long()] += 3  # three colour updates in the window
+    sp = StatePass(rtg, ctx, g, state, cam, icol, idep, ids, compact, kw["frame"], settings)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ck = dict(color=torch.zeros_like(icol), depth=torch.zeros_like(idep), alpha=torch.zeros_like(idep))
+
+    def check():
+        rtg.render_forward(ctx, [cam], g, None, settings, ck["color"], ck["depth"], ck["alpha"])
+        return [ck["color"], ck["depth"], ck["alpha"]]
+
+    arrs = state.arrays()
+    tuned = run_tuner(ctx, sp._body, check, [arrs.means, arrs.scales, arrs.quats, arrs.opacity, arrs.colors,
+                                              arrs.unstable, arrs.eta, arrs.err], args, "state")
+    for _ in range(args.warmup):
+        sp.step()
+    torch.cuda.synchronize()
+    stats = rtg.get_stats(ctx)
+    assert stats["status"] == 0, stats
+    kept = int(sp.count.item())
+    sp.capture()
+    sp.step()
+    torch.cuda.synchronize()
+    ms_step, wall, clocks = timed_replays(sp, args.steps, flush, stream, local)
+    per_launch = kernel_profile_adding(rtg, ctx, sp, args.steps, flush)
+    P, K, N = H * W, stats["pairs"], scene.n
+    alg = alg_bytes(dict(stats, masked_pixels=P), N, 1, H, W)
+    for k in ("backward", "project_backward", "adam", "l1_loss", "unstable_mask", "bin", "unstable_index"):
+        alg.pop(k, None)
+    row = 4 * (11 + C) + 1 + 12  # parameters, flag, eta / err / t0 of one Gaussian
+    alg["error_count"] = P * (4 * C * 2 + 4 * 3) + N * 8
+    alg["compact_gaussians"] = N * 1 + 2 * kept * row + (N - kept) * 0
+    roofline, pk = roofline_of(per_launch, alg, ctx.get_tuning(), "state",
+                               extra_kinds=("error_count", "compact_gaussians"))
+    hc = torch.empty_like(icol, device="cpu").pin_memory()
+    hd = torch.empty_like(idep, device="cpu").pin_memory()
+    hc.copy_(icol.cpu())
+    hd.copy_(idep.cpu())
+    hcount = torch.empty(1, dtype=torch.int64, pin_memory=True)
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t_0 = time.perf_counter()
+        icol.copy_(hc, non_blocking=True)
+        idep.copy_(hd, non_blocking=True)
+        cnt = sp.step()
+        hcount.copy_(cnt, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        if i >= args.warmup:
+            e2e_ms.append((time.perf_counter() - t_0) * 1e3)
+    e2e_step = float(np.mean(e2e_ms))
+    tuning = ctx.get_tuning()
+    if rank != 0:
+        return None
+    FT = ((W + tuning.tile_w - 1) // tuning.tile_w) * ((H + tuning.tile_h - 1) // tuning.tile_h)
+    launches = 6 + (1 if FT <= 8192 else 3) + 2 + 1 + 3 + 1  # forward, error count, states, compaction, fusion
+    fixed = "fixed by --tuning" if args.tuning else "off (--no-tune)"
+    alg_step = sum(alg.values()) + int(nu) * (3 * 4 * (11 + C) + 12)  # + the fusion's reads and writes
+    out = {
+        "metric": STATE_METRIC, "value": round(1e3 / ms_step, 2), "unit": "frames/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": kw["name"], "gaussians": N, "unstable": int(nu), "kept_after_pruning": kept,
+                   "width": W, "height": H, "camera_candidate": DEFAULT_CANDIDATE, "pairs": K,
+                   "fragments_per_step": stats["fragments"], "alg_bytes_per_step": int(alg_step),
+                   "step_hbm_roofline_frac": round(alg_step / (ms_step * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
+                   "tuning": tuning.as_dict(), "autotune": tuned.summary() if tuned is not None else fixed,
+                   "l2": "256 MB buffer written before every step, outside the timed spans",
+                   "timing": "timed steps replay one CUDA graph of the pass; kernel_ms_per_launch from a live eager "
+                             "pass with per-kernel CUDA events (the fusion has no context and is not listed)",
+                   "wall_s_timed_region": round(wall, 3),
+                   "kernel_ms_per_launch": {k: round(v, 5) for k, v in per_launch.items()},
+                   "parallelism": "replicas x1"},
+        "roofline": roofline,
+        "e2e": {"value": round(1e3 / e2e_step, 2), "unit": "frames/s",
+                "h2d_bytes_per_step": int(hc.numel() * 4 + hd.numel() * 4), "d2h_bytes_per_step": 8},
+        "gpu_launches": launches * args.steps,
+        "clocks": clocks.summary(),
+    }
+    if not args.no_cpu_baseline:
+        full = {k: getattr(g, k).cpu().numpy() for k in ("means", "scales", "quats", "opacity", "colors")}
+        comp = {k: c.cpu().numpy() for k, c in zip(("means", "scales", "quats", "opacity", "colors"), compact)}
+        arrays = (full, comp, ids.cpu().numpy(), state.eta_start.cpu().numpy(), state.eta.cpu().numpy(),
+                  state.err.cpu().numpy(), state.t0.cpu().numpy(), g.unstable.cpu().numpy())
+        maps = (sp.rc.cpu().numpy(), sp.rd.cpu().numpy(), sp.ri.cpu().numpy(), icol.cpu().numpy(), idep.cpu().numpy())
+        out["cpu_baseline"] = oracle_state_rate(scene, cam, maps, arrays)
+    ctx.close()
+    return out
+
+
 def cpu_baseline_from_gpu(scene, cam, mask, tcol, tdep, n_masked):
     m = mask[0].cpu().numpy().astype(bool)
     ys, xs = np.nonzero(m)
@@ -1300,7 +1510,7 @@ DEFAULT_CANDIDATE = 7  # first pose of the seeded stream with 25-40% mask covera
 def main():
     args = parse()
     if args.steps <= 0:
-        args.steps = {"keyframes": 60, "large": 20, "global": 100, "adding": 200}.get(args.workload, 400)
+        args.steps = {"keyframes": 60, "large": 20, "global": 100, "adding": 200, "state": 200}.get(args.workload, 400)
     if args.impl == "reference":
         out = run_reference(args)
     elif args.workload in ("keyframes", "large"):
@@ -1309,6 +1519,8 @@ def main():
         out = run_global(args)
     elif args.workload == "adding":
         out = run_adding(args)
+    elif args.workload == "state":
+        out = run_state(args)
     else:
         out = run_ours(args)
     if out is not None:

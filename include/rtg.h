@@ -315,6 +315,62 @@ rtg_status rtg_add_candidates(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, i
                               uint8_t *kind_out, float *position_out, float *color_out, float *opacity_out,
                               void *stream);
 
+/* Fusion and state management (Section 3.2: "Gaussian optimization" with Eq. 9, and "State
+ * management").  Per-Gaussian state arrays are device arrays of the caller: eta [n] int32
+ * (confidence count), err [n] int32 (error count), t0 [n] int32 (frame of creation), and
+ * the unstable flags [n] uint8.
+ *
+ * rtg_confidence_update: after an optimisation iteration, eta[ids[k]] += 1 for each of the
+ * nu optimised Gaussians ids[k] (distinct) whose colour gradient row g_colors[k] [nu,C] has a
+ * non-zero entry (its colour was updated).
+ *
+ * rtg_fuse_window (Eq. 9): at the end of a window, for each optimised Gaussian i = ids[k]
+ * with eta_now[i] > 0: w = (eta_now[i] - eta_start[i]) / eta_now[i] and every stored
+ * parameter becomes (1 - w) * prev + w * optimised, in float32 rounded per operation; prev is
+ * the full array's row (the value before the window), optimised the compact row k of u_*
+ * [nu, .] (layouts as rtg_gaussians).  Gaussians with eta_now[i] == 0 keep their row.  This
+ * replaces rtg_scatter_unstable at the end of a window.
+ *
+ * rtg_error_count: from a full-frame render of the optimised map (render_color [F,C,H,W],
+ * render_depth [F,H,W], index_map [F,H,W]) and the input frames (color, depth; depth <= 0 =
+ * no measurement): a pixel errs if the float32 channel sum of |C_hat - C| > C * delta_c or,
+ * where the input has depth, |D_hat - D| > delta_d; every stable Gaussian (unstable[i] == 0)
+ * that is the depth hit of an erring pixel of frame f gets err[i] += 1, once per frame.
+ * Uses the context's workspace (n <= max_gaussians).
+ *
+ * rtg_update_states at frame `frame`: stable with err > delta_e -> unstable (eta = err = 0);
+ * unstable with eta > delta_eta -> stable (err = 0); otherwise unstable with
+ * frame - t0 > delta_t -> remove[i] = 1 (remove [n] uint8 output, 0 elsewhere).
+ *
+ * rtg_compact_gaussians: copies the rows of every array of `in` whose remove flag is 0, in
+ * order, to the same arrays of `out` (distinct buffers with room for n rows; C colour
+ * channels per Gaussian); *count_out (device int64) = rows kept.  Uses the context's
+ * workspace (n <= max_gaussians). */
+typedef struct {
+  int32_t delta_eta; /* 100 (synthetic scenes), 200 or 400 in the paper */
+  int32_t delta_e;   /* not given in the paper */
+  int32_t delta_t;   /* frames; not given in the paper */
+  float delta_c, delta_d; /* 0.1, 0.1 m */
+} rtg_state_params;
+typedef struct {
+  float *means, *scales, *quats, *opacity, *colors;
+  uint8_t *unstable;
+  int32_t *eta, *err, *t0;
+} rtg_map_arrays;
+rtg_status rtg_confidence_update(int64_t nu, int32_t C, const int32_t *ids, const float *g_colors, int32_t *eta,
+                                 void *stream);
+rtg_status rtg_fuse_window(int64_t nu, int32_t C, const int32_t *ids, const int32_t *eta_start,
+                           const int32_t *eta_now, const float *u_means, const float *u_scales, const float *u_quats,
+                           const float *u_opacity, const float *u_colors, float *means, float *scales, float *quats,
+                           float *opacity, float *colors, void *stream);
+rtg_status rtg_error_count(rtg_ctx *ctx, int32_t F, int32_t C, int32_t H, int32_t W, const float *render_color,
+                           const float *render_depth, const int32_t *index_map, const float *color, const float *depth,
+                           const uint8_t *unstable, int64_t n, const rtg_state_params *p, int32_t *err, void *stream);
+rtg_status rtg_update_states(int64_t n, int32_t frame, const int32_t *t0, const rtg_state_params *p,
+                             uint8_t *unstable, int32_t *eta, int32_t *err, uint8_t *remove, void *stream);
+rtg_status rtg_compact_gaussians(rtg_ctx *ctx, int64_t n, int32_t C, const uint8_t *remove, const rtg_map_arrays *in,
+                                 const rtg_map_arrays *out, int64_t *count_out, void *stream);
+
 /* Adam (Kingma & Ba, Algorithm 1) on compact unstable parameters, in place, with the
  * per-group learning rates of Supplement C.  The scale is optimised in log space
  * (s <- s * exp(-step), gradient s * dL/ds).  m and v hold nu * (11 + C) float32 each,

@@ -72,7 +72,7 @@ def fuse_window(full: dict, compact: dict, ids: np.ndarray, eta_start: np.ndarra
         b = np.asarray(compact[name], np.float32).reshape(len(ids), -1)
         prev = a2[ids]
         blended = ((one_w[:, None] * prev).astype(np.float32) + (w[:, None] * b).astype(np.float32)).astype(np.float32)
-        a2[ids] = blended
+        a2[ids] = np.where((e1 > 0)[:, None], blended, prev)
         out[name] = a2.reshape(shape)
     return out
 

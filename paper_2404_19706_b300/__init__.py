@@ -12,7 +12,14 @@ _lib.load()
 from .api import (  # noqa: E402,F401
     AdamSettings,
     AddSettings,
+    MapArrays,
+    StateSettings,
     add_candidates,
+    compact_gaussians,
+    confidence_update,
+    error_count,
+    fuse_window,
+    update_states,
     Context,
     Gaussians,
     RenderSettings,
@@ -49,5 +56,6 @@ from .api import (  # noqa: E402,F401
 from .optim import MaskedStep, RasterState, RTGRasterize, rasterize  # noqa: E402,F401
 from .keyframes import GlobalStep, KeyframeSet, global_adam  # noqa: E402,F401
 from .adding import AddingPass  # noqa: E402,F401
+from .state import MapState  # noqa: E402,F401
 
 LIBRARY_PATH = _lib.LIB_PATH

@@ -68,6 +68,16 @@ class rtg_add_params(Structure):
                 ("opacity_opaque", c_float), ("opacity_transparent", c_float), ("seed", ctypes.c_uint64)]
 
 
+class rtg_state_params(Structure):
+    _fields_ = [("delta_eta", c_int32), ("delta_e", c_int32), ("delta_t", c_int32), ("delta_c", c_float),
+                ("delta_d", c_float)]
+
+
+class rtg_map_arrays(Structure):
+    _fields_ = [(k, c_void_p) for k in ("means", "scales", "quats", "opacity", "colors", "unstable", "eta", "err",
+                                        "t0")]
+
+
 # (name, restype, argtypes) of every entry point declared in include/rtg.h
 SIGNATURES = [
     ("rtg_workspace_size", c_int32, [POINTER(rtg_capacity), POINTER(c_size_t)]),
@@ -96,6 +106,14 @@ SIGNATURES = [
                                        ctypes.c_double, c_void_p, c_void_p]),
     ("rtg_add_candidates", c_int32, [c_void_p, POINTER(rtg_camera), c_int32, c_int32] + [c_void_p] * 7 +
      [c_int64, POINTER(rtg_add_params), c_int64] + [c_void_p] * 6 + [c_void_p]),
+    ("rtg_confidence_update", c_int32, [c_int64, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("rtg_fuse_window", c_int32, [c_int64, c_int32] + [c_void_p] * 13 + [c_void_p]),
+    ("rtg_error_count", c_int32, [c_void_p, c_int32, c_int32, c_int32, c_int32] + [c_void_p] * 6 +
+     [c_int64, POINTER(rtg_state_params), c_void_p, c_void_p]),
+    ("rtg_update_states", c_int32, [c_int64, c_int32, c_void_p, POINTER(rtg_state_params)] + [c_void_p] * 4 +
+     [c_void_p]),
+    ("rtg_compact_gaussians", c_int32, [c_void_p, c_int64, c_int32, c_void_p, POINTER(rtg_map_arrays),
+                                        POINTER(rtg_map_arrays), c_void_p, c_void_p]),
     ("rtg_narrow_pixels", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_float, c_void_p,
                                     c_void_p]),
     ("rtg_get_tuning", c_int32, [c_void_p, POINTER(rtg_tuning)]),

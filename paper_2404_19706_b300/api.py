@@ -402,6 +402,107 @@ def add_candidates(ctx: Context, cams, render_color, render_alpha, render_depth,
     _check(st, "rtg_add_candidates", ctx.ptr)
 
 
+@dataclasses.dataclass(frozen=True)
+class StateSettings:
+    """Thresholds of the state management (Section 3.2): confidence count for stability, error
+    count for instability, age (frames) for removal, and the colour / depth error of a pixel.
+    delta_e and delta_t are not given in the paper."""
+    delta_eta: int = 100
+    delta_e: int = 10
+    delta_t: int = 200
+    delta_c: float = 0.1
+    delta_d: float = 0.1
+
+    def to_c(self) -> "_lib.rtg_state_params":
+        return _lib.rtg_state_params(int(self.delta_eta), int(self.delta_e), int(self.delta_t), float(self.delta_c),
+                                     float(self.delta_d))
+
+
+@dataclasses.dataclass
+class MapArrays:
+    """Every per-Gaussian array of the map (rtg_map_arrays)."""
+    means: torch.Tensor
+    scales: torch.Tensor
+    quats: torch.Tensor
+    opacity: torch.Tensor
+    colors: torch.Tensor
+    unstable: torch.Tensor  # u8
+    eta: torch.Tensor       # int32 confidence count
+    err: torch.Tensor       # int32 error count
+    t0: torch.Tensor        # int32 frame of creation
+
+    def to_c(self) -> "_lib.rtg_map_arrays":
+        f = lambda t, dt, k: _ptr(t, dt, k)  # noqa: E731
+        return _lib.rtg_map_arrays(*[f(getattr(self, k), torch.float32, k) for k in
+                                     ("means", "scales", "quats", "opacity", "colors")],
+                                   f(self.unstable, torch.uint8, "unstable"), f(self.eta, torch.int32, "eta"),
+                                   f(self.err, torch.int32, "err"), f(self.t0, torch.int32, "t0"))
+
+    @staticmethod
+    def empty_like(a: "MapArrays") -> "MapArrays":
+        return MapArrays(*[torch.empty_like(getattr(a, f.name)) for f in dataclasses.fields(MapArrays)])
+
+
+def confidence_update(ids: torch.Tensor, g_colors: torch.Tensor, eta: torch.Tensor, stream=None):
+    """eta[ids[k]] += 1 where the colour gradient row g_colors[k] is non-zero."""
+    nu, C = int(ids.numel()), int(g_colors.shape[1]) if g_colors.ndim > 1 else 1
+    if nu == 0:
+        return
+    st = _lib.load().rtg_confidence_update(nu, C, _ptr(ids, torch.int32, "ids"), _ptr(g_colors, torch.float32, "g_colors"),
+                                           _ptr(eta, torch.int32, "eta"), _stream(stream))
+    _check(st, "rtg_confidence_update")
+
+
+def fuse_window(ids: torch.Tensor, eta_start: torch.Tensor, eta_now: torch.Tensor, compact: Sequence[torch.Tensor],
+                g: Gaussians, stream=None):
+    """Eq. 9: blend the optimised compact rows into the full arrays of g with weights from
+    the confidence counts (in place)."""
+    nu, C = int(ids.numel()), g.channels
+    if nu == 0:
+        return
+    st = _lib.load().rtg_fuse_window(nu, C, _ptr(ids, torch.int32, "ids"), _ptr(eta_start, torch.int32, "eta_start"),
+                                     _ptr(eta_now, torch.int32, "eta_now"),
+                                     *[_ptr(t, torch.float32, "compact") for t in compact],
+                                     *[_ptr(getattr(g, k), torch.float32, k) for k in
+                                       ("means", "scales", "quats", "opacity", "colors")], _stream(stream))
+    _check(st, "rtg_fuse_window")
+
+
+def error_count(ctx: Context, render_color, render_depth, index_map, color, depth, unstable: torch.Tensor,
+                settings: StateSettings, err: torch.Tensor, stream=None):
+    """err[i] += the number of frames in which stable Gaussian i is the depth hit of an
+    erring pixel."""
+    F, C, H, W = render_color.shape
+    prm = settings.to_c()
+    st = _lib.load().rtg_error_count(ctx.ptr, F, C, H, W, _ptr(render_color, torch.float32, "render_color"),
+                                     _ptr(render_depth, torch.float32, "render_depth"),
+                                     _ptr(index_map, torch.int32, "index_map"), _ptr(color, torch.float32, "color"),
+                                     _ptr(depth, torch.float32, "depth"), _ptr(unstable, torch.uint8, "unstable"),
+                                     int(unstable.numel()), ctypes.byref(prm), _ptr(err, torch.int32, "err"),
+                                     _stream(stream))
+    _check(st, "rtg_error_count", ctx.ptr)
+
+
+def update_states(frame: int, t0, settings: StateSettings, unstable, eta, err, remove, stream=None):
+    prm = settings.to_c()
+    st = _lib.load().rtg_update_states(int(unstable.numel()), int(frame), _ptr(t0, torch.int32, "t0"),
+                                       ctypes.byref(prm), _ptr(unstable, torch.uint8, "unstable"),
+                                       _ptr(eta, torch.int32, "eta"), _ptr(err, torch.int32, "err"),
+                                       _ptr(remove, torch.uint8, "remove"), _stream(stream))
+    _check(st, "rtg_update_states")
+
+
+def compact_gaussians(ctx: Context, remove: torch.Tensor, src: MapArrays, dst: MapArrays, count_out: torch.Tensor,
+                      stream=None):
+    """Copy the rows of src not flagged in remove, in order, to dst; count_out [1] int64."""
+    n, C = int(remove.numel()), int(src.colors.shape[1])
+    a, b = src.to_c(), dst.to_c()
+    st = _lib.load().rtg_compact_gaussians(ctx.ptr, n, C, _ptr(remove, torch.uint8, "remove"), ctypes.byref(a),
+                                           ctypes.byref(b), _ptr(count_out, torch.int64, "count_out"),
+                                           _stream(stream))
+    _check(st, "rtg_compact_gaussians", ctx.ptr)
+
+
 _DUMMY = {}
 
 

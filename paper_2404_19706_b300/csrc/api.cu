@@ -48,6 +48,7 @@ struct rtg_ctx {
   bool bwd_done;    // a backward of the last forward has run (its 2D gradient rows are used)
   bool narrowed;    // rtg_narrow_pixels reduced the last forward's pixel set
   SelBufs sel;      // scratch of rtg_select_top_error (ticket set per call)
+  uint32_t *gauss_bits;  // [max_gaussians] per-frame error bits of rtg_error_count (kept zero)
   Window win;
   // tracing: (start, end) event pairs of the kernels launched while profiling is on
   bool prof;
@@ -58,12 +59,13 @@ struct rtg_ctx {
 // Kernel kinds reported by the tracing interface (one launcher each).
 enum ProfKind {
   kPTileMask, kPUnstableIndex, kPProject, kPScanTiles, kPEmit, kPSortTiles, kPForward, kPL1Loss, kPBackward,
-  kPProjectBackward, kPUnstableMask, kPBin, kPSelect, kPNarrow, kPAdd, kPNumKinds
+  kPProjectBackward, kPUnstableMask, kPBin, kPSelect, kPNarrow, kPAdd, kPErrorCount, kPCompact, kPNumKinds
 };
 static const char *kProfNames[kPNumKinds] = {"tile_mask", "unstable_index", "project", "scan_tiles",
                                              "emit", "sort_tiles", "forward", "l1_loss",
                                              "backward", "project_backward", "unstable_mask", "bin",
-                                             "select_top_error", "narrow_pixels", "add_candidates"};
+                                             "select_top_error", "narrow_pixels", "add_candidates",
+                                             "error_count", "compact_gaussians"};
 constexpr int kProfMaxRecords = 1 << 16;
 
 struct ProfRec {
@@ -128,7 +130,7 @@ struct Layout {
   size_t cams, counters, rank, ids, block_cnt, cand, rec_hot, rec_cold, rec_box, ntiles, tile_npix, tile_count, tile_offset,
       tile_cursor, keys, keys_alt, stage, sorted, px_T, px_last, px_hit, grad2d, loss_part, loss_scal, loss_done, tile_loss,
       px_list, items, scand, win_scount, win_soff, win_skeys, scan_part, scan_hist, sel_keys, sel_small, sel_state,
-      sel_tie, total;
+      sel_tie, gauss_bits, total;
 };
 
 bool capacity_ok(const rtg_capacity *c) {
@@ -199,6 +201,7 @@ Layout layout_of(const rtg_capacity *c) {
   L.sel_small = take(sel_scratch_words((int)Fm) * 4);
   L.sel_state = take(Fm * 2 * 4);
   L.sel_tie = take(Fm * sel_blocks * 4);
+  L.gauss_bits = take(N * 4);
   L.total = o;
   return L;
 }
@@ -471,6 +474,7 @@ rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap) {
   ctx->sel.hist = (uint32_t *)(b + L.sel_small);
   ctx->sel.state = (uint32_t *)(b + L.sel_state);
   ctx->sel.tie = (uint32_t *)(b + L.sel_tie);
+  ctx->gauss_bits = (uint32_t *)(b + L.gauss_bits);
   {
     int sms = 148;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || sms < 1) {
@@ -485,6 +489,7 @@ rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap) {
   cudaMemset(ctx->slab + L.counters, 0, kNumCounters * sizeof(unsigned long long));
   ctx->win.open = false;
   cudaMemset(ctx->slab + L.loss_done, 0, 4);
+  cudaMemset(ctx->slab + L.gauss_bits, 0, (size_t)(cap->max_gaussians > 0 ? cap->max_gaussians : 1) * 4);
   init_sort_attributes();
   if (cudaDeviceSynchronize() != cudaSuccess) {
     cudaGetLastError();
@@ -975,6 +980,81 @@ rtg_status rtg_add_candidates(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, i
   }
   ctx->last_stream = s;
   return check_launch(ctx, "add_candidates");
+}
+
+rtg_status rtg_confidence_update(int64_t nu, int32_t C, const int32_t *ids, const float *g_colors, int32_t *eta,
+                                 void *stream) {
+  if (nu < 0 || C < 1 || C > 64) return RTG_ERR_ARG;
+  if (nu == 0) return RTG_OK;
+  if (ids == nullptr || g_colors == nullptr || eta == nullptr) return RTG_ERR_ARG;
+  launch_confidence(nu, C, ids, g_colors, eta, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? RTG_OK : RTG_ERR_CUDA;
+}
+
+rtg_status rtg_fuse_window(int64_t nu, int32_t C, const int32_t *ids, const int32_t *eta_start,
+                           const int32_t *eta_now, const float *u_means, const float *u_scales, const float *u_quats,
+                           const float *u_opacity, const float *u_colors, float *means, float *scales, float *quats,
+                           float *opacity, float *colors, void *stream) {
+  if (nu < 0 || C < 1 || C > 64) return RTG_ERR_ARG;
+  if (nu == 0) return RTG_OK;
+  if (!ids || !eta_start || !eta_now || !u_means || !u_scales || !u_quats || !u_opacity || !u_colors || !means ||
+      !scales || !quats || !opacity || !colors)
+    return RTG_ERR_ARG;
+  const FuseArrays a{means, scales, quats, opacity, colors, u_means, u_scales, u_quats, u_opacity, u_colors};
+  launch_fuse(nu, C, ids, eta_start, eta_now, a, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? RTG_OK : RTG_ERR_CUDA;
+}
+
+rtg_status rtg_error_count(rtg_ctx *ctx, int32_t F, int32_t C, int32_t H, int32_t W, const float *render_color,
+                           const float *render_depth, const int32_t *index_map, const float *color, const float *depth,
+                           const uint8_t *unstable, int64_t n, const rtg_state_params *p, int32_t *err, void *stream) {
+  if (ctx == nullptr) return RTG_ERR_ARG;
+  if (F < 1 || F > 32 || C < 1 || C > 64 || H < 1 || W < 1 || p == nullptr)
+    return fail(ctx, RTG_ERR_ARG, "error_count: bad sizes or params");
+  if (n < 0 || n > ctx->cap.max_gaussians) return fail(ctx, RTG_ERR_ARG, "error_count: n outside the capacity");
+  if (!render_color || !render_depth || !index_map || !color || !depth || (n > 0 && (!unstable || !err)))
+    return fail(ctx, RTG_ERR_ARG, "error_count: NULL pointer");
+  if (n == 0) return RTG_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  {
+    ProfScope ps(ctx, kPErrorCount, s);
+    launch_error_count(F, C, (int64_t)H * W, render_color, render_depth, index_map, color, depth, unstable, n,
+                       (float)C * p->delta_c, p->delta_d, ctx->gauss_bits, err, s);
+  }
+  ctx->last_stream = s;
+  return check_launch(ctx, "error_count");
+}
+
+rtg_status rtg_update_states(int64_t n, int32_t frame, const int32_t *t0, const rtg_state_params *p,
+                             uint8_t *unstable, int32_t *eta, int32_t *err, uint8_t *remove, void *stream) {
+  if (n < 0 || p == nullptr) return RTG_ERR_ARG;
+  if (n == 0) return RTG_OK;
+  if (!t0 || !unstable || !eta || !err || !remove) return RTG_ERR_ARG;
+  launch_update_states(n, frame, t0, *p, unstable, eta, err, remove, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? RTG_OK : RTG_ERR_CUDA;
+}
+
+rtg_status rtg_compact_gaussians(rtg_ctx *ctx, int64_t n, int32_t C, const uint8_t *remove, const rtg_map_arrays *in,
+                                 const rtg_map_arrays *out, int64_t *count_out, void *stream) {
+  if (ctx == nullptr) return RTG_ERR_ARG;
+  if (n < 0 || n > ctx->cap.max_gaussians || C < 1 || C > 64 || !remove || !in || !out || !count_out)
+    return fail(ctx, RTG_ERR_ARG, "compact_gaussians: bad arguments");
+  const rtg_map_arrays *m[2] = {in, out};
+  for (const rtg_map_arrays *a : m)
+    if (!a->means || !a->scales || !a->quats || !a->opacity || !a->colors || !a->unstable || !a->eta || !a->err ||
+        !a->t0)
+      return fail(ctx, RTG_ERR_ARG, "compact_gaussians: NULL array");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n == 0) {
+    if (cudaMemsetAsync(count_out, 0, sizeof(int64_t), s) != cudaSuccess) return check_launch(ctx, "compact");
+    return RTG_OK;
+  }
+  {
+    ProfScope ps(ctx, kPCompact, s);
+    launch_compact(n, C, remove, ctx->w.block_cnt, *in, *out, (long long *)count_out, s);
+  }
+  ctx->last_stream = s;
+  return check_launch(ctx, "compact_gaussians");
 }
 
 rtg_status rtg_adam_step(int64_t nu, int32_t C, float *means, float *scales, float *quats, float *opacity,

@@ -211,5 +211,21 @@ struct AddFrames {
   AddCam cam[kMaxFrames];
 };
 void launch_add_candidates(const AddArgs &a, const AddFrames &fr, int F, cudaStream_t s);
+// state.cu
+struct FuseArrays {
+  float *means, *scales, *quats, *opacity, *colors;
+  const float *u_means, *u_scales, *u_quats, *u_opacity, *u_colors;
+};
+void launch_confidence(int64_t nu, int C, const int32_t *ids, const float *g_colors, int32_t *eta, cudaStream_t s);
+void launch_fuse(int64_t nu, int C, const int32_t *ids, const int32_t *eta_start, const int32_t *eta_now,
+                 const FuseArrays &a, cudaStream_t s);
+// bits: [n] uint32 scratch, zero on entry and left zero
+void launch_error_count(int F, int C, int64_t HW, const float *rcolor, const float *rdepth, const int32_t *index_map,
+                        const float *color, const float *depth, const uint8_t *unstable, int64_t n, float thr_c,
+                        float dd, uint32_t *bits, int32_t *err, cudaStream_t s);
+void launch_update_states(int64_t n, int32_t frame, const int32_t *t0, const rtg_state_params &p, uint8_t *unstable,
+                          int32_t *eta, int32_t *err, uint8_t *remove, cudaStream_t s);
+void launch_compact(int64_t n, int C, const uint8_t *remove, int32_t *block_cnt, const rtg_map_arrays &in,
+                    const rtg_map_arrays &out, long long *count_out, cudaStream_t s);
 
 }  // namespace rtg

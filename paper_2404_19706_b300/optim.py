@@ -94,7 +94,8 @@ class MaskedStep:
     def __init__(self, ctx: Context, g: Gaussians, cams, mask: Optional[torch.Tensor], target_color: torch.Tensor,
                  target_depth: torch.Tensor, settings: RenderSettings = RenderSettings(),
                  adam: AdamSettings = AdamSettings(), w_color: float = 1.0, w_depth: float = 1.0,
-                 recompute_mask: bool = False, window: bool = True, scatter_every_step: bool = False):
+                 recompute_mask: bool = False, window: bool = True, scatter_every_step: bool = False,
+                 map_state=None):
         self.ctx, self.settings, self.adam = ctx, settings, adam
         self.cams = cams if isinstance(cams, (list, tuple)) else [cams]
         self.mask = mask
@@ -126,6 +127,11 @@ class MaskedStep:
         self.window = window
         if window:
             api.window_begin(ctx, self.cams, self.g, settings)
+        # with a MapState, every iteration raises the confidence counts of the Gaussians
+        # whose colour it updated, and finish() fuses the window's result (Eq. 9)
+        self.map_state = map_state
+        if map_state is not None:
+            map_state.window_start()
 
     def _body(self, stream=None):
         s = self.state
@@ -140,6 +146,8 @@ class MaskedStep:
                                   self.target_depth, self.w_color, self.w_depth, s.color, s.depth, s.alpha,
                                   self.loss, None, stream)
         api.render_backward_l1(self.ctx, *self.grads, stream=stream)
+        if self.map_state is not None:
+            api.confidence_update(self.ids, self.grads[4], self.map_state.eta, stream)
         api.adam_step_counted(self.u, self.grads, self.m, self.v, self.step_counter, self.adam, stream)
         if self.scatter_every_step:
             api.scatter_unstable(self.ids, self.u, self.full, stream)
@@ -165,3 +173,11 @@ class MaskedStep:
     def write_back(self, stream=None):
         """Scatter the optimised compact parameters into the full arrays."""
         api.scatter_unstable(self.ids, self.u, self.full, stream)
+
+    def finish(self, stream=None):
+        """End of the window: with a MapState, fuse the optimised Gaussians into the map with
+        the weights of Eq. 9; without one, write them back as they are."""
+        if self.map_state is not None:
+            api.fuse_window(self.ids, self.map_state.eta_start, self.map_state.eta, self.u, self.full, stream)
+        else:
+            self.write_back(stream)

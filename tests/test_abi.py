@@ -69,6 +69,8 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(_lib.rtg_stats) == 6 * 8 + 4 * 4
     assert ctypes.sizeof(_lib.rtg_tuning) == 7 * 4
     assert ctypes.sizeof(_lib.rtg_add_params) == 6 * 4 + 8
+    assert ctypes.sizeof(_lib.rtg_state_params) == 5 * 4
+    assert ctypes.sizeof(_lib.rtg_map_arrays) == 9 * 8
 
 
 @pytest.mark.gpu
@@ -86,7 +88,8 @@ def test_struct_layouts_match_compiled_header():
     if shutil.which("gcc") is None:
         pytest.skip("gcc not available")
     structs = [(n, getattr(_lib, n)) for n in ("rtg_camera", "rtg_render_params", "rtg_gaussians", "rtg_capacity",
-                                                 "rtg_stats", "rtg_tuning", "rtg_adam_params", "rtg_add_params")]
+                                                 "rtg_stats", "rtg_tuning", "rtg_adam_params", "rtg_add_params",
+                                                 "rtg_state_params", "rtg_map_arrays")]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rtg.h"', "int main(void) {"]
     for name, cls in structs:
         lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
@@ -109,6 +112,13 @@ def test_global_optimisation_entry_points_reject_bad_arguments_without_gpu():
     lib = _lib.load()
     assert lib.rtg_select_top_error(None, 1, 3, 8, 8, None, None, 0.4, None, None) == _lib.RTG_ERR_ARG
     assert lib.rtg_narrow_pixels(None, None, None, None, 1.0, 1.0, None, None) == _lib.RTG_ERR_ARG
+    sp = _lib.rtg_state_params(100, 10, 200, 0.1, 0.1)
+    assert lib.rtg_confidence_update(-1, 3, None, None, None, None) == _lib.RTG_ERR_ARG
+    assert lib.rtg_confidence_update(0, 3, None, None, None, None) == _lib.RTG_OK
+    assert lib.rtg_fuse_window(5, 3, *([None] * 13), None) == _lib.RTG_ERR_ARG
+    assert lib.rtg_update_states(5, 0, None, ctypes.byref(sp), None, None, None, None, None) == _lib.RTG_ERR_ARG
+    assert lib.rtg_error_count(None, 1, 3, 8, 8, *([None] * 6), 0, ctypes.byref(sp), None, None) == _lib.RTG_ERR_ARG
+    assert lib.rtg_compact_gaussians(None, 0, 3, None, None, None, None, None) == _lib.RTG_ERR_ARG
     p = _lib.rtg_add_params(0.5, 0.1, 0.1, 0.05, 0.99, 0.1, 0)
     assert lib.rtg_add_candidates(None, None, 1, 3, *([None] * 7), 0, ctypes.byref(p), 0,
                                   *([None] * 6), None) == _lib.RTG_ERR_ARG
