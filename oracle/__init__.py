@@ -26,6 +26,11 @@ Parity status per function (pins live in ``tests/test_oracle_pins.py``):
                      back-projection in closed form)
   state.*            pinned (hand-made confidence, fusion-weight, error-count, transition and
                      compaction cases)
+  sh.*               pinned (the real SH basis against scipy's complex harmonics, the addition
+                     theorem, orthonormality by quadrature, a hand colour, the peak colour of
+                     one SH Gaussian, SH gradients against central differences, the
+                     regulariser's closed form, Adam with split colour rates against
+                     torch.optim.Adam)
 """
 
 from .rasterizer import (  # noqa: F401
@@ -41,4 +46,4 @@ from .rasterizer import (  # noqa: F401
     decision_signature,
 )
 from .adam import adam_step, AdamHyper  # noqa: F401
-from . import adding, global_opt, state  # noqa: F401
+from . import adding, global_opt, sh, state  # noqa: F401

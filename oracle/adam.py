@@ -30,6 +30,10 @@ class AdamHyper:
     beta1: float = 0.9
     beta2: float = 0.999
     eps: float = 1e-15
+    # with SH colour: the first colors_dc values of a colour row (the degree-0 coefficients)
+    # use lr_colors, the others lr_colors_rest (0.05 lr_SH0, Supplement C); 0 = all lr_colors
+    lr_colors_rest: float = 2.5e-5
+    colors_dc: int = 0
 
 
 def adam_step(params: Dict[str, np.ndarray], grads: Dict[str, np.ndarray], m: Dict[str, np.ndarray],
@@ -53,6 +57,10 @@ def adam_step(params: Dict[str, np.ndarray], grads: Dict[str, np.ndarray], m: Di
         vv = hp.beta2 * np.asarray(v[name], dtype=np.float64) + (1 - hp.beta2) * g * g
         m_hat = mm / (1 - hp.beta1 ** step)
         v_hat = vv / (1 - hp.beta2 ** step)
+        if name == "colors" and hp.colors_dc > 0:  # per-coefficient rate within each row
+            width = int(np.prod(x.shape[1:])) if x.ndim > 1 else 1
+            j = np.arange(width).reshape((1,) + tuple(x.shape[1:])) if x.ndim > 1 else np.zeros(1)
+            lr = np.where(j < hp.colors_dc, hp.lr_colors, hp.lr_colors_rest)
         theta = theta - lr * m_hat / (np.sqrt(v_hat) + hp.eps)
         newp[name] = np.exp(theta) if name == "scales" else theta
         newm[name], newv[name] = mm, vv

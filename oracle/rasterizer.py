@@ -104,6 +104,9 @@ def project(means: torch.Tensor, scales: torch.Tensor, quats: torch.Tensor, opac
     """
     Rg, tg = _cam_tensors(cam)
     fx, fy, cx, cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    if colors.ndim == 3:  # SH coefficients [n, K, 3]: the colour seen from this camera
+        from .sh import sh_colors
+        colors = sh_colors(colors, means, tg)
     with torch.no_grad():
         finite = (torch.isfinite(means).all(1) & torch.isfinite(scales).all(1) & torch.isfinite(quats).all(1)
                   & torch.isfinite(opacity) & torch.isfinite(colors).all(1)
@@ -301,7 +304,7 @@ def render(scene, cam, st: Settings = Settings(), pixels=None, mask=None, need_b
         for s in range(0, pix.shape[0], step):
             u = pix[s:s + step].to(DT)
             parts.append(_composite(u, pr, cam, st, need_borderline))
-    C = colors.shape[1]
+    C = 3 if colors.ndim == 3 else colors.shape[1]
     if not parts:
         z = torch.zeros(0, dtype=DT)
         zb = torch.zeros(0, dtype=torch.bool)
