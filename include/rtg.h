@@ -76,15 +76,25 @@ typedef struct {
  * Optional precomputed unstable index (from rtg_unstable_rank, valid while the flags do
  * not change, e.g. for a whole optimisation window): rank_map [n] int32 (compact index of
  * Gaussian i, -1 if stable), unstable_ids [n_unstable] int32 ascending, and their count.
- * When rank_map is non-NULL the calls skip recomputing the index. */
+ * When rank_map is non-NULL the calls skip recomputing the index.
+ * View-dependent colour (Section 3.1: c_i from the view direction r_i and the SH
+ * coefficients SH_i): with sh_degree d in 1..3, channels must be 3 and colors (and
+ * u_colors) hold (d+1)^2 x 3 SH coefficients per Gaussian, [n][(d+1)^2][3], index
+ * k = l^2 + l + m of the real orthonormal spherical harmonics without the Condon-Shortley
+ * phase.  The colour seen from a camera with centre t is sum_k SH[k] Y_k(r),
+ * r = (p - t) / |p - t|, with no offset and no clamping.  sh_degree 0: colors holds the
+ * channels directly.  The colour gradients of the backward then have the same layout as
+ * colors (one row of (d+1)^2 x 3 per Gaussian), and the position gradient includes the
+ * view-direction term. */
 typedef struct {
   int64_t n;
-  int32_t channels; /* 3 (RGB) or 8 (feature channels) */
+  int32_t channels; /* 3 (RGB) or 8 (feature channels); 3 with SH */
   const float *means, *scales, *quats, *opacity, *colors;
   const uint8_t *unstable;
   const float *u_means, *u_scales, *u_quats, *u_opacity, *u_colors;
   const int32_t *rank_map, *unstable_ids;
   int64_t n_unstable;
+  int32_t sh_degree; /* 0 (colours) or 1..3 (SH coefficients) */
 } rtg_gaussians;
 
 /* Workspace capacity; every later call must stay within it. */
@@ -315,6 +325,20 @@ rtg_status rtg_add_candidates(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, i
                               uint8_t *kind_out, float *position_out, float *color_out, float *opacity_out,
                               void *stream);
 
+/* Transparent-Gaussian regulariser (Section 3.2, the L_reg term of Eq. 8): over the nu
+ * optimised Gaussians in compact form (u_* [nu,.], layouts as rtg_gaussians) those with
+ * u_opacity < alpha_split (0.5: transparent Gaussians are added at 0.1, opaque ones at 0.99)
+ * are held to their values when added (means0 [nu,3], scales0 [nu,3], quats0 [nu,4]):
+ * L_reg = w_reg x the mean over their position, raw quaternion and scale components of the
+ * squared difference (w_reg = 1000 in the paper).  *loss_out (device float) receives
+ * w_reg L_reg; its gradient is ADDED to g_means, g_scales, g_quats [nu,.] (call it after the
+ * backward, before Adam).  No transparent Gaussian: loss 0, gradients unchanged.  Uses
+ * the context's loss scratch. */
+rtg_status rtg_transparent_reg(rtg_ctx *ctx, int64_t nu, const float *u_means, const float *u_scales,
+                               const float *u_quats, const float *u_opacity, const float *means0,
+                               const float *scales0, const float *quats0, float w_reg, float alpha_split,
+                               float *g_means, float *g_scales, float *g_quats, float *loss_out, void *stream);
+
 /* Fusion and state management (Section 3.2: "Gaussian optimization" with Eq. 9, and "State
  * management").  Per-Gaussian state arrays are device arrays of the caller: eta [n] int32
  * (confidence count), err [n] int32 (error count), t0 [n] int32 (frame of creation), and
@@ -375,9 +399,15 @@ rtg_status rtg_compact_gaussians(rtg_ctx *ctx, int64_t n, int32_t C, const uint8
  * per-group learning rates of Supplement C.  The scale is optimised in log space
  * (s <- s * exp(-step), gradient s * dL/ds).  m and v hold nu * (11 + C) float32 each,
  * laid out group by group like the parameters: means [nu,3], then scales [nu,3], quats
- * [nu,4], opacity [nu], colours [nu,C]; start them at zero.  `step` counts from 1. */
+ * [nu,4], opacity [nu], colours [nu,C]; start them at zero.  `step` counts from 1.
+ * C is the number of colour values per Gaussian ((d+1)^2 x 3 with SH colour).  With
+ * colors_dc > 0, the first colors_dc values of each colour row (the degree-0 SH
+ * coefficients: 3) use lr_colors and the others lr_colors_rest (Supplement C: 0.05 x
+ * lr_SH0); colors_dc = 0 gives every colour value lr_colors. */
 typedef struct {
   float lr_means, lr_scales, lr_quats, lr_opacity, lr_colors, beta1, beta2, eps;
+  float lr_colors_rest;
+  int32_t colors_dc;
 } rtg_adam_params;
 rtg_status rtg_adam_step(int64_t nu, int32_t C, float *means, float *scales, float *quats, float *opacity,
                          float *colors, const float *g_means, const float *g_scales, const float *g_quats,

@@ -61,7 +61,7 @@ def global_hyper(base: AdamHyper = AdamHyper(), lr_factor: float = 0.1) -> AdamH
     """Adam settings of the global optimisation: positions frozen, other rates x lr_factor."""
     return dataclasses.replace(base, lr_means=0.0, lr_scales=base.lr_scales * lr_factor,
                                lr_quats=base.lr_quats * lr_factor, lr_opacity=base.lr_opacity * lr_factor,
-                               lr_colors=base.lr_colors * lr_factor)
+                               lr_colors=base.lr_colors * lr_factor, lr_colors_rest=base.lr_colors_rest * lr_factor)
 
 
 def rotation_angle_deg(Ra: np.ndarray, Rb: np.ndarray) -> float:

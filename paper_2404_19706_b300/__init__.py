@@ -45,6 +45,7 @@ from .api import (  # noqa: E402,F401
     reset_status,
     scatter_unstable,
     select_top_error,
+    transparent_reg,
     unstable_index,
     unstable_rank,
     unstable_mask,

@@ -39,7 +39,7 @@ class rtg_gaussians(Structure):
     _fields_ = [("n", c_int64), ("channels", c_int32)] + [
         (k, c_void_p) for k in ("means", "scales", "quats", "opacity", "colors", "unstable",
                                 "u_means", "u_scales", "u_quats", "u_opacity", "u_colors",
-                                "rank_map", "unstable_ids")] + [("n_unstable", c_int64)]
+                                "rank_map", "unstable_ids")] + [("n_unstable", c_int64), ("sh_degree", c_int32)]
 
 
 class rtg_capacity(Structure):
@@ -60,7 +60,7 @@ class rtg_tuning(Structure):
 
 class rtg_adam_params(Structure):
     _fields_ = [(k, c_float) for k in ("lr_means", "lr_scales", "lr_quats", "lr_opacity", "lr_colors", "beta1",
-                                       "beta2", "eps")]
+                                       "beta2", "eps", "lr_colors_rest")] + [("colors_dc", c_int32)]
 
 
 class rtg_add_params(Structure):
@@ -106,6 +106,8 @@ SIGNATURES = [
                                        ctypes.c_double, c_void_p, c_void_p]),
     ("rtg_add_candidates", c_int32, [c_void_p, POINTER(rtg_camera), c_int32, c_int32] + [c_void_p] * 7 +
      [c_int64, POINTER(rtg_add_params), c_int64] + [c_void_p] * 6 + [c_void_p]),
+    ("rtg_transparent_reg", c_int32, [c_void_p, c_int64] + [c_void_p] * 7 + [c_float, c_float] + [c_void_p] * 4 +
+     [c_void_p]),
     ("rtg_confidence_update", c_int32, [c_int64, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("rtg_fuse_window", c_int32, [c_int64, c_int32] + [c_void_p] * 13 + [c_void_p]),
     ("rtg_error_count", c_int32, [c_void_p, c_int32, c_int32, c_int32, c_int32] + [c_void_p] * 6 +

@@ -84,9 +84,15 @@ class AdamSettings:
     beta1: float = 0.9
     beta2: float = 0.999
     eps: float = 1e-15
+    # SH colour: the first colors_dc values of a colour row (the degree-0 coefficients) use
+    # lr_colors, the others lr_colors_rest (0.05 lr_SH0); 0 = every value lr_colors
+    lr_colors_rest: float = 2.5e-5
+    colors_dc: int = 0
 
     def to_c(self) -> rtg_adam_params:
-        return rtg_adam_params(*(float(getattr(self, f.name)) for f in dataclasses.fields(self)))
+        names = ("lr_means", "lr_scales", "lr_quats", "lr_opacity", "lr_colors", "beta1", "beta2", "eps",
+                 "lr_colors_rest")
+        return rtg_adam_params(*(float(getattr(self, k)) for k in names), int(self.colors_dc))
 
 
 @dataclasses.dataclass(frozen=True)
@@ -143,6 +149,7 @@ class Gaussians:
     rank_map: Optional[torch.Tensor] = None      # optional precomputed unstable index (int32 [N])
     unstable_ids: Optional[torch.Tensor] = None  # int32 [Nu], ascending
     n_unstable: int = 0
+    sh_degree: int = 0  # 1..3: colors holds SH coefficients [N, (d+1)^2, 3]
 
     @property
     def n(self) -> int:
@@ -150,18 +157,26 @@ class Gaussians:
 
     @property
     def channels(self) -> int:
-        return int(self.colors.shape[1])
+        """Colour channels of a render (3 with SH colour)."""
+        return 3 if self.sh_degree > 0 else int(self.colors.shape[1])
+
+    @property
+    def color_width(self) -> int:
+        """Colour values per Gaussian: the channels, or 3 (d+1)^2 SH coefficients."""
+        return int(np.prod(self.colors.shape[1:]))
 
     @staticmethod
     def from_scene(scene, device="cuda") -> "Gaussians":
         def t(a, dt=torch.float32):
             return torch.as_tensor(np.ascontiguousarray(a)).to(device=device, dtype=dt).contiguous()
-        return Gaussians(t(scene.means), t(scene.scales), t(scene.quats), t(scene.opacity), t(scene.colors),
-                         t(scene.unstable, torch.uint8))
+        colors = np.asarray(scene.colors)
+        deg = int(round(np.sqrt(colors.shape[1]))) - 1 if colors.ndim == 3 else 0
+        return Gaussians(t(scene.means), t(scene.scales), t(scene.quats), t(scene.opacity), t(colors),
+                         t(scene.unstable, torch.uint8), sh_degree=deg)
 
     def to_c(self) -> rtg_gaussians:
         g = rtg_gaussians()
-        g.n, g.channels = self.n, self.channels
+        g.n, g.channels, g.sh_degree = self.n, self.channels, int(self.sh_degree)
         for name in ("means", "scales", "quats", "opacity", "colors"):
             setattr(g, name, _ptr(getattr(self, name), torch.float32, name))
         g.unstable = _ptr(self.unstable, torch.uint8, "unstable")
@@ -443,11 +458,25 @@ class MapArrays:
         return MapArrays(*[torch.empty_like(getattr(a, f.name)) for f in dataclasses.fields(MapArrays)])
 
 
+def transparent_reg(ctx: Context, compact: Sequence[torch.Tensor], initial: Sequence[torch.Tensor], grads,
+                    loss_out: torch.Tensor, w_reg: float = 1000.0, alpha_split: float = 0.5, stream=None):
+    """Adds the gradient of w_reg L_reg (transparent Gaussians held to their initial position,
+    rotation and scale) to grads (means, scales, quats); loss_out [1] receives w_reg L_reg.
+    compact: (means, scales, quats, opacity, ...) [nu, .]; initial: (means0, scales0, quats0)."""
+    nu = int(compact[0].shape[0])
+    st = _lib.load().rtg_transparent_reg(ctx.ptr, nu, *[_ptr(t, torch.float32, "compact") for t in compact[:4]],
+                                         *[_ptr(t, torch.float32, "initial") for t in initial[:3]], float(w_reg),
+                                         float(alpha_split), *[_ptr(t, torch.float32, "grad") for t in grads[:3]],
+                                         _ptr(loss_out, torch.float32, "loss_out"), _stream(stream))
+    _check(st, "rtg_transparent_reg", ctx.ptr)
+
+
 def confidence_update(ids: torch.Tensor, g_colors: torch.Tensor, eta: torch.Tensor, stream=None):
     """eta[ids[k]] += 1 where the colour gradient row g_colors[k] is non-zero."""
-    nu, C = int(ids.numel()), int(g_colors.shape[1]) if g_colors.ndim > 1 else 1
+    nu = int(ids.numel())
     if nu == 0:
         return
+    C = int(g_colors.numel()) // nu
     st = _lib.load().rtg_confidence_update(nu, C, _ptr(ids, torch.int32, "ids"), _ptr(g_colors, torch.float32, "g_colors"),
                                            _ptr(eta, torch.int32, "eta"), _stream(stream))
     _check(st, "rtg_confidence_update")
@@ -457,7 +486,7 @@ def fuse_window(ids: torch.Tensor, eta_start: torch.Tensor, eta_now: torch.Tenso
                 g: Gaussians, stream=None):
     """Eq. 9: blend the optimised compact rows into the full arrays of g with weights from
     the confidence counts (in place)."""
-    nu, C = int(ids.numel()), g.channels
+    nu, C = int(ids.numel()), g.color_width
     if nu == 0:
         return
     st = _lib.load().rtg_fuse_window(nu, C, _ptr(ids, torch.int32, "ids"), _ptr(eta_start, torch.int32, "eta_start"),
@@ -495,7 +524,8 @@ def update_states(frame: int, t0, settings: StateSettings, unstable, eta, err, r
 def compact_gaussians(ctx: Context, remove: torch.Tensor, src: MapArrays, dst: MapArrays, count_out: torch.Tensor,
                       stream=None):
     """Copy the rows of src not flagged in remove, in order, to dst; count_out [1] int64."""
-    n, C = int(remove.numel()), int(src.colors.shape[1])
+    n = int(remove.numel())
+    C = int(src.colors.numel()) // max(int(src.colors.shape[0]), 1)
     a, b = src.to_c(), dst.to_c()
     st = _lib.load().rtg_compact_gaussians(ctx.ptr, n, C, _ptr(remove, torch.uint8, "remove"), ctypes.byref(a),
                                            ctypes.byref(b), _ptr(count_out, torch.int64, "count_out"),
@@ -531,7 +561,8 @@ def adam_step(params: Sequence[torch.Tensor], grads: Sequence[torch.Tensor], m: 
     """params/grads: compact (means, scales, quats, opacity, colors); m, v: nu * (11 + C) floats
     each, zero at the start, laid out group by group like the parameters."""
     means, scales, quats, opacity, colors = params
-    nu, C = int(means.shape[0]), int(colors.shape[1])
+    nu = int(means.shape[0])
+    C = int(colors.numel()) // max(nu, 1)
     c = hp.to_c()
     ptrs = [_ptr(t, torch.float32, "param") for t in params] + [_ptr(t, torch.float32, "grad") for t in grads]
     st = _lib.load().rtg_adam_step(nu, C, *ptrs, _ptr(m, torch.float32, "m"), _ptr(v, torch.float32, "v"),
@@ -546,7 +577,8 @@ def adam_step_counted(params: Sequence[torch.Tensor], grads: Sequence[torch.Tens
     if step_counter.numel() < 2:
         raise ValueError("step_counter must hold 2 int32 (completed steps, scratch)")
     means, scales, quats, opacity, colors = params
-    nu, C = int(means.shape[0]), int(colors.shape[1])
+    nu = int(means.shape[0])
+    C = int(colors.numel()) // max(nu, 1)
     c = hp.to_c()
     ptrs = [_ptr(t, torch.float32, "param") for t in params] + [_ptr(t, torch.float32, "grad") for t in grads]
     st = _lib.load().rtg_adam_step_counted(nu, C, *ptrs, _ptr(m, torch.float32, "m"), _ptr(v, torch.float32, "v"),
@@ -593,10 +625,10 @@ def unstable_rank(ctx: Context, unstable: torch.Tensor, stream=None):
 
 
 def gather_unstable(ids: torch.Tensor, g: Gaussians, stream=None):
-    nu, C = int(ids.shape[0]), g.channels
+    nu, C = int(ids.shape[0]), g.color_width
     dev = g.means.device
     out = (torch.empty(nu, 3, device=dev), torch.empty(nu, 3, device=dev), torch.empty(nu, 4, device=dev),
-           torch.empty(nu, device=dev), torch.empty(nu, C, device=dev))
+           torch.empty(nu, device=dev), torch.empty((nu,) + tuple(g.colors.shape[1:]), device=dev))
     if nu:
         st = _lib.load().rtg_gather_unstable(nu, C, _ptr(ids, torch.int32, "ids"),
                                              *[_ptr(getattr(g, k), torch.float32, k) for k in
@@ -607,7 +639,7 @@ def gather_unstable(ids: torch.Tensor, g: Gaussians, stream=None):
 
 
 def scatter_unstable(ids: torch.Tensor, compact: Sequence[torch.Tensor], g: Gaussians, stream=None):
-    nu, C = int(ids.shape[0]), g.channels
+    nu, C = int(ids.shape[0]), g.color_width
     if nu == 0:
         return
     st = _lib.load().rtg_scatter_unstable(nu, C, _ptr(ids, torch.int32, "ids"),

@@ -287,6 +287,8 @@ rtg_status make_gauss(rtg_ctx *ctx, const rtg_gaussians *g, GaussPtrs &gp) {
   if (g->n > 0x7fffffffLL) return fail(ctx, RTG_ERR_UNSUPPORTED, "n above 2^31-1");
   if (g->channels != 3 && g->channels != 8) return fail(ctx, RTG_ERR_UNSUPPORTED, "channels must be 3 or 8");
   if (g->channels > ctx->cap.max_channels) return fail(ctx, RTG_ERR_ARG, "channels above capacity");
+  if (g->sh_degree < 0 || g->sh_degree > 3) return fail(ctx, RTG_ERR_UNSUPPORTED, "sh_degree must be 0..3");
+  if (g->sh_degree > 0 && g->channels != 3) return fail(ctx, RTG_ERR_ARG, "SH colour needs channels = 3");
   if (g->n > 0 && (!g->means || !g->scales || !g->quats || !g->opacity || !g->colors || !g->unstable))
     return fail(ctx, RTG_ERR_ARG, "a Gaussian array is NULL");
   const bool any_u = g->u_means || g->u_scales || g->u_quats || g->u_opacity || g->u_colors;
@@ -298,6 +300,8 @@ rtg_status make_gauss(rtg_ctx *ctx, const rtg_gaussians *g, GaussPtrs &gp) {
   gp.u_colors = g->u_colors;
   gp.n = g->n;
   gp.C = g->channels;
+  gp.sh_degree = g->sh_degree;
+  gp.col_stride = g->sh_degree > 0 ? 3 * (g->sh_degree + 1) * (g->sh_degree + 1) : g->channels;
   gp.rank_map = g->rank_map;
   gp.unstable_ids = g->unstable_ids;
   gp.n_unstable = g->rank_map ? g->n_unstable : 0;
@@ -980,6 +984,30 @@ rtg_status rtg_add_candidates(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, i
   }
   ctx->last_stream = s;
   return check_launch(ctx, "add_candidates");
+}
+
+rtg_status rtg_transparent_reg(rtg_ctx *ctx, int64_t nu, const float *u_means, const float *u_scales,
+                               const float *u_quats, const float *u_opacity, const float *means0,
+                               const float *scales0, const float *quats0, float w_reg, float alpha_split,
+                               float *g_means, float *g_scales, float *g_quats, float *loss_out, void *stream) {
+  if (ctx == nullptr) return RTG_ERR_ARG;
+  if (nu < 0 || !(w_reg >= 0.f) || loss_out == nullptr) return fail(ctx, RTG_ERR_ARG, "transparent_reg: bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (nu == 0) {
+    if (cudaMemsetAsync(loss_out, 0, sizeof(float), s) != cudaSuccess) return check_launch(ctx, "transparent_reg");
+    return RTG_OK;
+  }
+  if (!u_means || !u_scales || !u_quats || !u_opacity || !means0 || !scales0 || !quats0 || !g_means || !g_scales ||
+      !g_quats)
+    return fail(ctx, RTG_ERR_ARG, "transparent_reg: NULL array");
+  RegArgs a{nu, u_means, u_scales, u_quats, u_opacity, means0, scales0, quats0, w_reg, alpha_split, g_means,
+            g_scales, g_quats, ctx->w.loss_part, ctx->w.loss_done, ctx->w.loss_scal + 6};
+  {
+    ProfScope ps(ctx, kPL1Loss, s);
+    launch_transparent_reg(a, loss_out, s);
+  }
+  ctx->last_stream = s;
+  return check_launch(ctx, "transparent_reg");
 }
 
 rtg_status rtg_confidence_update(int64_t nu, int32_t C, const int32_t *ids, const float *g_colors, int32_t *eta,

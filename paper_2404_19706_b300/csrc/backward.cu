@@ -352,6 +352,12 @@ __global__ void __launch_bounds__(256) k_project_backward(GaussPtrs g, Work w, P
     float gp[3] = {0, 0, 0}, gs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, ga = 0.f, gc[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) gc[c] = 0.f;
+    // SH colour: the coefficient gradients are summed over the frames in the output row
+    const bool sh = C == 3 && g.sh_degree > 0;
+    float *__restrict__ g_row = g_colors + (int64_t)g.col_stride * k;
+    const float *__restrict__ coef = color_ptr(g, w.rank, i);
+    if (sh && !accumulate)
+      for (int j = 0; j < g.col_stride; ++j) g_row[j] = 0.f;
     if (ok) {
       const float qn = sqrtf(P.q[0] * P.q[0] + P.q[1] * P.q[1] + P.q[2] * P.q[2] + P.q[3] * P.q[3]);
       const float qw = P.q[0] / qn, qx = P.q[1] / qn, qy = P.q[2] / qn, qz = P.q[3] / qn;
@@ -368,6 +374,10 @@ __global__ void __launch_bounds__(256) k_project_backward(GaussPtrs g, Work w, P
         ga += row[kG2Alpha];
 #pragma unroll
         for (int c = 0; c < C; ++c) gc[c] += row[kG2Col + c];
+        if (sh) {
+          const float gcf[3] = {row[kG2Col], row[kG2Col + 1], row[kG2Col + 2]};
+          sh_color_backward(g.sh_degree, coef, P.p, cam.t, gcf, g_row, gp);
+        }
         const float gd0 = row[g2_d0(C)], gn[3] = {row[g2_nc(C)], row[g2_nc(C) + 1], row[g2_nc(C) + 2]};
         const float gz = row[g2_z(C)];
 
@@ -503,8 +513,9 @@ __global__ void __launch_bounds__(256) k_project_backward(GaussPtrs g, Work w, P
 #pragma unroll
       for (int m = 0; m < 4; ++m) gq[m] += g_quats[4 * k + m];
       ga += g_opacity[k];
+      if (!sh)
 #pragma unroll
-      for (int c = 0; c < C; ++c) gc[c] += g_colors[(int64_t)C * k + c];
+        for (int c = 0; c < C; ++c) gc[c] += g_colors[(int64_t)C * k + c];
     }
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
@@ -514,8 +525,9 @@ __global__ void __launch_bounds__(256) k_project_backward(GaussPtrs g, Work w, P
 #pragma unroll
     for (int m = 0; m < 4; ++m) g_quats[4 * k + m] = gq[m];
     g_opacity[k] = ga;
+    if (!sh)
 #pragma unroll
-    for (int c = 0; c < C; ++c) g_colors[(int64_t)C * k + c] = gc[c];
+      for (int c = 0; c < C; ++c) g_colors[(int64_t)C * k + c] = gc[c];
   }
 }
 

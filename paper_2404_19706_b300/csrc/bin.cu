@@ -352,11 +352,17 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
       i = (int64_t)e - (int64_t)f * N;
       ok = load_params(g, w.rank, i, P);
       const float *cp = color_ptr(g, w.rank, i);
+      if (C == 3 && g.sh_degree > 0) {  // the colour seen from this frame's camera
+        float c3[3];
+        sh_color(g.sh_degree, cp, P.p, w.cams[f].t, c3);
 #pragma unroll
-      for (int c = 0; c < C; ++c) {
-        col[c] = cp[c];
-        ok = ok && isfinite(col[c]);
+        for (int c = 0; c < C; ++c) col[c] = c3[c < 3 ? c : 0];
+      } else {
+#pragma unroll
+        for (int c = 0; c < C; ++c) col[c] = cp[c];
       }
+#pragma unroll
+      for (int c = 0; c < C; ++c) ok = ok && isfinite(col[c]);
       if (ok) {
         float R[9];
         const float rq = rsqrtf(P.q[0] * P.q[0] + P.q[1] * P.q[1] + P.q[2] * P.q[2] + P.q[3] * P.q[3]);

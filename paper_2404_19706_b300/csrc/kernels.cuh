@@ -141,6 +141,18 @@ void launch_project_backward(const GaussPtrs &g, const Work &w, const Prm &prm, 
 void launch_l1_loss(const Work &w, int F, int C, int H, int W, const float *color, const float *depth,
                     const float *tcolor, const float *tdepth, const uint8_t *mask, float w_c, float w_d,
                     float *loss_out, float *dL_dcolor, float *dL_ddepth, cudaStream_t s);
+// Transparent-Gaussian regulariser over the compact optimised set (nu rows).
+struct RegArgs {
+  int64_t nu;
+  const float *means, *scales, *quats, *opacity;  // current compact parameters
+  const float *means0, *scales0, *quats0;         // values when the Gaussians were added
+  float w_reg, alpha_split;
+  float *g_means, *g_scales, *g_quats;            // gradients, added to
+  float *part;                                    // [kLossBlocks * 2] scratch
+  uint32_t *done;                                 // ticket, zero between calls
+  float *scale;                                   // device scalar: 2 w_reg / (10 n_t)
+};
+void launch_transparent_reg(const RegArgs &a, float *loss_out, cudaStream_t s);
 void launch_adam(int64_t nu, int C, float *means, float *scales, float *quats, float *opacity, float *colors,
                  const float *g_means, const float *g_scales, const float *g_quats, const float *g_opacity,
                  const float *g_colors, float *m, float *v, const rtg_adam_params &hp, float bc1, float bc2_sqrt,

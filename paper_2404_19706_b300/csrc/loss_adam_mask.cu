@@ -152,6 +152,84 @@ __global__ void __launch_bounds__(256) k_loss_finalize(Work w, int FT, int gshif
   }
 }
 
+// --------------------------------------------------------------------------- L_reg
+// Transparent-Gaussian regulariser (Section 3.2, the L_reg term of Eq. 8): w_reg times the
+// mean squared difference of the position, raw quaternion and scale components of the
+// optimised Gaussians with opacity < alpha_split from their values when added.  Per-block
+// partial sums in a fixed grid, the last block (ticket) adds them in block order and
+// stores the loss and the gradient factor 2 w_reg / (10 n_t); the second kernel adds the
+// gradient.
+__global__ void __launch_bounds__(256) k_reg_reduce(RegArgs a, float *__restrict__ loss_out) {
+  __shared__ float s_t[2][256];
+  __shared__ int s_last;
+  float sum = 0.f, cnt = 0.f;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.nu; k += (int64_t)gridDim.x * blockDim.x) {
+    if (!(a.opacity[k] < a.alpha_split)) continue;
+    float d2 = 0.f;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float dm = a.means[3 * k + r] - a.means0[3 * k + r], ds = a.scales[3 * k + r] - a.scales0[3 * k + r];
+      d2 = fmaf(dm, dm, fmaf(ds, ds, d2));
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const float dq = a.quats[4 * k + r] - a.quats0[4 * k + r];
+      d2 = fmaf(dq, dq, d2);
+    }
+    sum += d2;
+    cnt += 1.f;
+  }
+  s_t[0][threadIdx.x] = sum;
+  s_t[1][threadIdx.x] = cnt;
+  __syncthreads();
+  for (int stride = 128; stride > 0; stride >>= 1) {
+    if ((int)threadIdx.x < stride) {
+      s_t[0][threadIdx.x] += s_t[0][threadIdx.x + stride];
+      s_t[1][threadIdx.x] += s_t[1][threadIdx.x + stride];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    a.part[2 * blockIdx.x] = s_t[0][0];
+    a.part[2 * blockIdx.x + 1] = s_t[1][0];
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(a.done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
+  float tot = 0.f, n = 0.f;
+  for (int b = 0; b < (int)gridDim.x; ++b) {
+    tot += __ldcg(a.part + 2 * b);
+    n += __ldcg(a.part + 2 * b + 1);
+  }
+  const float denom = 10.f * n;
+  *loss_out = n > 0.f ? a.w_reg * tot / denom : 0.f;
+  *a.scale = n > 0.f ? 2.f * a.w_reg / denom : 0.f;
+  *a.done = 0u;
+}
+
+__global__ void __launch_bounds__(256) k_reg_grad(RegArgs a) {
+  const float sc = *a.scale;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.nu; k += (int64_t)gridDim.x * blockDim.x) {
+    if (!(a.opacity[k] < a.alpha_split)) continue;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      a.g_means[3 * k + r] += sc * (a.means[3 * k + r] - a.means0[3 * k + r]);
+      a.g_scales[3 * k + r] += sc * (a.scales[3 * k + r] - a.scales0[3 * k + r]);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) a.g_quats[4 * k + r] += sc * (a.quats[4 * k + r] - a.quats0[4 * k + r]);
+  }
+}
+
+void launch_transparent_reg(const RegArgs &a, float *loss_out, cudaStream_t s) {
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(kLossBlocks, (a.nu + 255) / 256));
+  k_reg_reduce<<<blocks, 256, 0, s>>>(a, loss_out);
+  k_reg_grad<<<blocks, 256, 0, s>>>(a);
+}
+
 void launch_loss_finalize(const Work &w, int FT, int gshift, int C, float w_c, float w_d, float *loss_out,
                           cudaStream_t s) {
   const int blocks = std::max(1, std::min(kLossBlocks, (FT + 255) / 256));
@@ -196,6 +274,10 @@ struct AdamGroups {
   const float *grad[5];
   float lr[5];
   int64_t begin[6];  // element offsets of the groups in m / v; begin[5] = total
+  // colour group: values at row positions >= dc (dc > 0) use lr_rest (the SH coefficients
+  // of degree >= 1); width = values per row
+  float lr_rest;
+  int width, dc;
 };
 
 // Each thread updates four elements of a group per iteration, loading all four before
@@ -247,7 +329,8 @@ __global__ void __launch_bounds__(256) k_adam(AdamGroups G, float *__restrict__ 
         const int64_t j = j0 + u * stride;
         if (j < n) {
           const float gg = log_space ? g[u] * x[u] : g[u];
-          const float step = adam_delta(gg, mm[u], vv[u], lr, hp, bc1, bc2_sqrt);
+          const float lr_e = (grp == 4 && G.dc > 0 && (int)(j % G.width) >= G.dc) ? G.lr_rest : lr;
+          const float step = adam_delta(gg, mm[u], vv[u], lr_e, hp, bc1, bc2_sqrt);
           param[j] = log_space ? x[u] * expf(-step) : x[u] - step;
           mg[j] = mm[u];
           vg[j] = vv[u];
@@ -502,7 +585,10 @@ void launch_adam(int64_t nu, int C, float *means, float *scales, float *quats, f
     G.begin[k + 1] = G.begin[k] + nu * width[k];
   }
   const int64_t total = G.begin[5];
-  if (C == 3 || C == 8) {
+  G.lr_rest = hp.lr_colors_rest;
+  G.width = C;
+  G.dc = (hp.colors_dc > 0 && hp.colors_dc < C) ? hp.colors_dc : 0;
+  if ((C == 3 || C == 8) && G.dc == 0) {
     const unsigned blocks = (unsigned)((nu + 255) / 256);
     if (C == 3) k_adam_rows<3><<<blocks, 256, 0, s>>>(G, nu, m, v, hp, bc1, bc2_sqrt, step_dev);
     else k_adam_rows<8><<<blocks, 256, 0, s>>>(G, nu, m, v, hp, bc1, bc2_sqrt, step_dev);

@@ -7,6 +7,115 @@
 
 namespace rtg {
 
+// ----------------------------------------------------------------------------- SH colour
+// View-dependent colour (Section 3.1: c_i from the view direction r_i and the SH
+// coefficients): the real, orthonormal spherical harmonics up to degree 3 (no
+// Condon-Shortley phase), index k = l^2 + l + m, as polynomials of the unit direction
+// (x, y, z).  c = sum_k SH[k] Y_k(r) with r = (p - t) / |p - t| from the camera centre t;
+// no offset, no clamping.
+constexpr int kShMax = 16;  // (3 + 1)^2
+constexpr float kSh0 = 0.28209479177387814f;   // 1 / (2 sqrt(pi))
+constexpr float kSh1 = 0.48860251190291992f;   // sqrt(3 / (4 pi))
+constexpr float kSh2a = 1.0925484305920792f;   // sqrt(15 / pi) / 2
+constexpr float kSh2b = 0.31539156525252005f;  // sqrt(5 / pi) / 4
+constexpr float kSh2c = 0.54627421529603959f;  // sqrt(15 / pi) / 4
+constexpr float kSh3a = 0.59004358992664352f;  // sqrt(35 / (2 pi)) / 4
+constexpr float kSh3b = 2.8906114426405538f;   // sqrt(105 / pi) / 2
+constexpr float kSh3c = 0.45704579946446572f;  // sqrt(21 / (2 pi)) / 4
+constexpr float kSh3d = 0.37317633259011540f;  // sqrt(7 / pi) / 4
+constexpr float kSh3e = 1.4453057213202769f;   // sqrt(105 / pi) / 4
+
+__device__ __forceinline__ void sh_basis(int degree, float x, float y, float z, float (&Y)[kShMax]) {
+  Y[0] = kSh0;
+  if (degree < 1) return;
+  Y[1] = kSh1 * y;
+  Y[2] = kSh1 * z;
+  Y[3] = kSh1 * x;
+  if (degree < 2) return;
+  const float xx = x * x, yy = y * y, zz = z * z;
+  Y[4] = kSh2a * x * y;
+  Y[5] = kSh2a * y * z;
+  Y[6] = kSh2b * (3.f * zz - 1.f);
+  Y[7] = kSh2a * x * z;
+  Y[8] = kSh2c * (xx - yy);
+  if (degree < 3) return;
+  Y[9] = kSh3a * y * (3.f * xx - yy);
+  Y[10] = kSh3b * x * y * z;
+  Y[11] = kSh3c * y * (5.f * zz - 1.f);
+  Y[12] = kSh3d * z * (5.f * zz - 3.f);
+  Y[13] = kSh3c * x * (5.f * zz - 1.f);
+  Y[14] = kSh3e * z * (xx - yy);
+  Y[15] = kSh3a * x * (xx - 3.f * yy);
+}
+
+// sum_k s_k grad Y_k at (x, y, z) (the polynomials' partial derivatives)
+__device__ __forceinline__ void sh_dir_grad(int degree, float x, float y, float z, const float (&s)[kShMax],
+                                            float &gx, float &gy, float &gz) {
+  gx = 0.f; gy = 0.f; gz = 0.f;
+  if (degree < 1) return;
+  gy += kSh1 * s[1];
+  gz += kSh1 * s[2];
+  gx += kSh1 * s[3];
+  if (degree < 2) return;
+  const float xx = x * x, yy = y * y, zz = z * z;
+  gx += kSh2a * y * s[4];  gy += kSh2a * x * s[4];
+  gy += kSh2a * z * s[5];  gz += kSh2a * y * s[5];
+  gz += 6.f * kSh2b * z * s[6];
+  gx += kSh2a * z * s[7];  gz += kSh2a * x * s[7];
+  gx += 2.f * kSh2c * x * s[8];  gy -= 2.f * kSh2c * y * s[8];
+  if (degree < 3) return;
+  gx += 6.f * kSh3a * x * y * s[9];  gy += 3.f * kSh3a * (xx - yy) * s[9];
+  gx += kSh3b * y * z * s[10];  gy += kSh3b * x * z * s[10];  gz += kSh3b * x * y * s[10];
+  gy += kSh3c * (5.f * zz - 1.f) * s[11];  gz += 10.f * kSh3c * y * z * s[11];
+  gz += kSh3d * (15.f * zz - 3.f) * s[12];
+  gx += kSh3c * (5.f * zz - 1.f) * s[13];  gz += 10.f * kSh3c * x * z * s[13];
+  gx += 2.f * kSh3e * x * z * s[14];  gy -= 2.f * kSh3e * y * z * s[14];  gz += kSh3e * (xx - yy) * s[14];
+  gx += 3.f * kSh3a * (xx - yy) * s[15];  gy -= 6.f * kSh3a * x * y * s[15];
+}
+
+// Colour of a Gaussian at p with coefficients coef [K][3] seen from the camera centre t.
+__device__ __forceinline__ void sh_color(int degree, const float *__restrict__ coef, const float p[3],
+                                         const float t[3], float (&col)[3]) {
+  const float dx = p[0] - t[0], dy = p[1] - t[1], dz = p[2] - t[2];
+  const float il = 1.f / sqrtf(dx * dx + dy * dy + dz * dz);
+  float Y[kShMax];
+  sh_basis(degree, dx * il, dy * il, dz * il, Y);
+  const int K = (degree + 1) * (degree + 1);
+  col[0] = col[1] = col[2] = 0.f;
+  for (int k = 0; k < K; ++k) {
+    col[0] = fmaf(coef[3 * k], Y[k], col[0]);
+    col[1] = fmaf(coef[3 * k + 1], Y[k], col[1]);
+    col[2] = fmaf(coef[3 * k + 2], Y[k], col[2]);
+  }
+}
+
+// Backward of sh_color for one frame: g_coef [K][3] += gcol (x) Y, and the position gradient
+// through the view direction, gp += (I - r r^T) / |p - t| sum_k (gcol . coef_k) grad Y_k.
+__device__ __forceinline__ void sh_color_backward(int degree, const float *__restrict__ coef, const float p[3],
+                                                  const float t[3], const float gcol[3], float *__restrict__ g_coef,
+                                                  float gp[3]) {
+  const float dx = p[0] - t[0], dy = p[1] - t[1], dz = p[2] - t[2];
+  const float il = 1.f / sqrtf(dx * dx + dy * dy + dz * dz);
+  const float x = dx * il, y = dy * il, z = dz * il;
+  float Y[kShMax], sk[kShMax];
+  sh_basis(degree, x, y, z, Y);
+  const int K = (degree + 1) * (degree + 1);
+#pragma unroll
+  for (int k = 0; k < kShMax; ++k) sk[k] = 0.f;
+  for (int k = 0; k < K; ++k) {
+    g_coef[3 * k] += gcol[0] * Y[k];
+    g_coef[3 * k + 1] += gcol[1] * Y[k];
+    g_coef[3 * k + 2] += gcol[2] * Y[k];
+    sk[k] = gcol[0] * coef[3 * k] + gcol[1] * coef[3 * k + 1] + gcol[2] * coef[3 * k + 2];
+  }
+  float gx, gy, gz;
+  sh_dir_grad(degree, x, y, z, sk, gx, gy, gz);
+  const float dot = gx * x + gy * y + gz * z;
+  gp[0] += (gx - dot * x) * il;
+  gp[1] += (gy - dot * y) * il;
+  gp[2] += (gz - dot * z) * il;
+}
+
 struct Projected {
   df mux, muy;          // pixel-space centre (double-float)
   float u11, u12, u22;  // U with U^T U = Sigma_2D^-1 * kQScale^2 (upper triangular)

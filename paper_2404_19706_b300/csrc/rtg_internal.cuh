@@ -82,9 +82,11 @@ struct GaussPtrs {
   const uint8_t *unstable;
   const float *u_means, *u_scales, *u_quats, *u_opacity, *u_colors;
   int64_t n;
-  int C;
+  int C;                // colour channels of a render (3 with SH)
   const int32_t *rank_map, *unstable_ids;  // optional precomputed unstable index
   int64_t n_unstable;
+  int sh_degree;        // 0: colours are the channels; 1..3: SH coefficients [(d+1)^2][3]
+  int col_stride;       // colour values per Gaussian: C, or 3 (d+1)^2
 };
 
 // Inputs of the L1 loss fused into the forward / backward (tcolor == nullptr: not fused).
@@ -241,9 +243,9 @@ __device__ __forceinline__ bool load_params(const GaussPtrs &g, const int32_t *r
 __device__ __forceinline__ const float *color_ptr(const GaussPtrs &g, const int32_t *rank, int64_t i) {
   if (g.u_colors != nullptr) {
     int r = rank[i];
-    if (r >= 0) return g.u_colors + (int64_t)g.C * r;
+    if (r >= 0) return g.u_colors + (int64_t)g.col_stride * r;
   }
-  return g.colors + (int64_t)g.C * i;
+  return g.colors + (int64_t)g.col_stride * i;
 }
 
 }  // namespace rtg

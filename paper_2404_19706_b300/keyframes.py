@@ -85,7 +85,7 @@ def global_adam(base: AdamSettings = AdamSettings(), lr_factor: float = 0.1) -> 
     groups at lr_factor x their on-the-fly rates."""
     return dataclasses.replace(base, lr_means=0.0, lr_scales=base.lr_scales * lr_factor,
                                lr_quats=base.lr_quats * lr_factor, lr_opacity=base.lr_opacity * lr_factor,
-                               lr_colors=base.lr_colors * lr_factor)
+                               lr_colors=base.lr_colors * lr_factor, lr_colors_rest=base.lr_colors_rest * lr_factor)
 
 
 class GlobalStep:
@@ -112,15 +112,17 @@ class GlobalStep:
         self.hyper = global_adam(adam, lr_factor)
         self.w_color, self.w_depth = w_color, w_depth
         dev = g.means.device
-        n, C = g.n, g.channels
+        n, C, Cw = g.n, g.channels, g.color_width
+        if g.sh_degree > 0 and self.hyper.colors_dc == 0:  # SH0 rate for the degree-0 terms only
+            self.hyper = dataclasses.replace(self.hyper, colors_dc=3)
         self.flags = torch.ones(n, dtype=torch.uint8, device=dev)
         rank, ids, nu = api.unstable_rank(ctx, self.flags)
         self.g = dataclasses.replace(g, unstable=self.flags, rank_map=rank, unstable_ids=ids, n_unstable=nu,
                                      u_means=None, u_scales=None, u_quats=None, u_opacity=None, u_colors=None)
         self.params = (g.means, g.scales, g.quats, g.opacity, g.colors)
         self.grads = [torch.zeros_like(t) for t in self.params]
-        self.m = torch.zeros(n * (11 + C), device=dev)
-        self.v = torch.zeros(n * (11 + C), device=dev)
+        self.m = torch.zeros(n * (11 + Cw), device=dev)
+        self.v = torch.zeros(n * (11 + Cw), device=dev)
         self.step_counter = torch.zeros(2, dtype=torch.int32, device=dev)
         Fm, H, W = max_frames, height, width
         self.color = torch.zeros(Fm, C, H, W, device=dev)

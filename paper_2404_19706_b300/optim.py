@@ -95,7 +95,9 @@ class MaskedStep:
                  target_depth: torch.Tensor, settings: RenderSettings = RenderSettings(),
                  adam: AdamSettings = AdamSettings(), w_color: float = 1.0, w_depth: float = 1.0,
                  recompute_mask: bool = False, window: bool = True, scatter_every_step: bool = False,
-                 map_state=None):
+                 map_state=None, initial: Optional[Sequence[torch.Tensor]] = None, w_reg: float = 1000.0):
+        if g.sh_degree > 0 and adam.colors_dc == 0:  # Supplement C: SH0 rate for the degree-0 terms
+            adam = dataclasses.replace(adam, colors_dc=3)
         self.ctx, self.settings, self.adam = ctx, settings, adam
         self.cams = cams if isinstance(cams, (list, tuple)) else [cams]
         self.mask = mask
@@ -116,13 +118,22 @@ class MaskedStep:
                                      u_opacity=self.u[3], u_colors=self.u[4])
         self.state = RasterState(ctx, self.g, self.cams, mask, settings)
         dev = g.means.device
-        C = g.channels
+        C = g.color_width
         self.target_color, self.target_depth = target_color, target_depth
         self.loss = torch.zeros(3, device=dev)
         self.grads = [torch.zeros_like(t) for t in self.u]
         self.m = torch.zeros(self.nu * (11 + C), device=dev)
         self.v = torch.zeros(self.nu * (11 + C), device=dev)
         self.step_counter = torch.zeros(2, dtype=torch.int32, device=dev)  # completed steps, scratch
+        # transparent-Gaussian regulariser (L_reg of Eq. 8): the unstable Gaussians' values
+        # when they were added, given as full arrays (means0, scales0, quats0)
+        self.w_reg = w_reg
+        self.u0 = None
+        self.loss_reg = torch.zeros(1, device=dev)
+        if initial is not None:
+            m0, s0, q0 = initial
+            g0 = Gaussians(m0, s0, q0, g.opacity, g.colors, g.unstable, sh_degree=g.sh_degree)
+            self.u0 = api.gather_unstable(self.ids, g0)[:3]
         self.graph = None
         self.window = window
         if window:
@@ -148,6 +159,8 @@ class MaskedStep:
         api.render_backward_l1(self.ctx, *self.grads, stream=stream)
         if self.map_state is not None:
             api.confidence_update(self.ids, self.grads[4], self.map_state.eta, stream)
+        if self.u0 is not None:
+            api.transparent_reg(self.ctx, self.u, self.u0, self.grads, self.loss_reg, self.w_reg, stream=stream)
         api.adam_step_counted(self.u, self.grads, self.m, self.v, self.step_counter, self.adam, stream)
         if self.scatter_every_step:
             api.scatter_unstable(self.ids, self.u, self.full, stream)

@@ -22,4 +22,5 @@ from .scenes import (  # noqa: F401
     room_camera_candidates,
     room_scene,
     scatter_scene,
+    sh_coefficients,
 )

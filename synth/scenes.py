@@ -363,6 +363,16 @@ def flag_blobs(scene: Scene, cameras: Sequence[Camera], n_unstable: int, n_blobs
     return flags
 
 
+def sh_coefficients(seed: int, n: int, degree: int, dc_range=(1.0, 3.5), rest_sigma: float = 0.15) -> np.ndarray:
+    """Random SH colour coefficients [n, (degree+1)^2, 3] float32: the degree-0 term uniform in
+    dc_range (a colour of about 0.28 to 1 after the basis constant), the others N(0, rest_sigma)."""
+    rng = np.random.default_rng(seed)
+    K = (degree + 1) ** 2
+    c = rng.normal(0.0, rest_sigma, (n, K, 3))
+    c[:, 0, :] = rng.uniform(dc_range[0], dc_range[1], (n, 3))
+    return c.astype(F32)
+
+
 def jitter_scene(scene: Scene, seed: int, pos_sigma: float = 0.003, log_scale_sigma: float = 0.05,
                  rot_deg: float = 2.0, color_sigma: float = 0.03) -> Scene:
     """Perturbed copy used to render a fixed target image for the L1 losses."""

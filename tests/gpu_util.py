@@ -29,7 +29,8 @@ def gpu_forward(scene, cams, mask=None, settings=None, ctx=None, fill=True):
     """Renders through rtg_render_forward; returns numpy arrays (and the context)."""
     m = rtg()
     cams = cams if isinstance(cams, (list, tuple)) else [cams]
-    F, H, W, C = len(cams), cams[0].height, cams[0].width, scene.colors.shape[1]
+    F, H, W = len(cams), cams[0].height, cams[0].width
+    C = 3 if np.asarray(scene.colors).ndim == 3 else scene.colors.shape[1]  # SH coefficients render RGB
     g = m.Gaussians.from_scene(scene)
     own = ctx is None
     if own:

@@ -64,7 +64,7 @@ def test_struct_layouts_match_header():
     # rtg_camera: 4 floats, 2 ints, 9 + 3 floats
     assert ctypes.sizeof(_lib.rtg_camera) == 4 * 4 + 2 * 4 + 12 * 4
     assert ctypes.sizeof(_lib.rtg_render_params) == 9 * 4
-    assert ctypes.sizeof(_lib.rtg_gaussians) == 8 + 8 + 13 * 8 + 8
+    assert ctypes.sizeof(_lib.rtg_gaussians) == 8 + 8 + 13 * 8 + 8 + 8  # + sh_degree, padded
     assert ctypes.sizeof(_lib.rtg_capacity) == 8 + 4 * 4 + 8
     assert ctypes.sizeof(_lib.rtg_stats) == 6 * 8 + 4 * 4
     assert ctypes.sizeof(_lib.rtg_tuning) == 7 * 4
