@@ -61,6 +61,10 @@ STATE = dict(name="state pass: room 1M Gaussians (200k unstable in 3 blobs), 640
                   "index map, error counts against a render of the jittered room, stable/unstable transitions at "
                   "frame 1000, pruning of stale unstable Gaussians, Eq. 9 fusion of the 200k unstable Gaussians",
              seed=3000, n=1_000_000, n_unstable=200_000, width=640, height=480, f=600.0, frame=1000)
+SH_METRIC = ("masked fwd+bwd iterations/sec at 640×480 with SH degree-3 colour and the transparent regulariser; "
+             "% HBM roofline")
+SH_WORKLOAD = ("masked-step room 1M Gaussians (20% unstable, 3 blobs) 640x480, tile rule 0.5, SH degree-3 colour "
+               "(48 coefficients per Gaussian), L_reg on the transparent unstable Gaussians (w_reg 1000)")
 C = 3
 
 
@@ -74,13 +78,14 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--candidate", type=int, default=-1, help="camera candidate index (-1: search)")
-    ap.add_argument("--workload", default="masked-step", choices=["masked-step", "keyframes", "large", "global", "adding", "state"],
+    ap.add_argument("--workload", default="masked-step", choices=["masked-step", "keyframes", "large", "global", "adding", "state", "sh"],
                     help="masked-step: the 640x480 masked iteration (default); keyframes: 8 batched 1200x680 "
                          "keyframes vs per-frame launches; large: 32 batched 1200x680 keyframes, 5M Gaussians, "
                          "8 channels; global: the global keyframe optimisation step (4 keyframes, top-40% "
                          "pixels, every Gaussian); adding: the Gaussian-adding pass (full-frame render, Eq. 6 "
                          "masks, 5% draw); state: fusion and state management (render, error counts, "
-                         "transitions, pruning, Eq. 9 fusion)")
+                         "transitions, pruning, Eq. 9 fusion); sh: the masked step with SH degree-3 colour and "
+                         "the transparent regulariser")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--tune-table", default="", help="write the autotuner's candidate table (JSON) to this path")
     ap.add_argument("--tuning", default="",
@@ -323,9 +328,11 @@ def kernel_profile(rtg, ctx, step, steps, flush, stream):
     return {k: (v[1] / v[0] if v[0] else 0.0) for k, v in prof.items()}
 
 
-def alg_bytes(stats, N, F, H, W, Cc=C):
-    """Algorithmic bytes per launch of each kernel kind, from the step's own counters."""
-    p_in, r_rec, q_pix, g2 = 44 + 4 * Cc, 36 + 4 * Cc, 4 * Cc + 16, 4 * (11 + Cc)
+def alg_bytes(stats, N, F, H, W, Cc=C, Cw=None):
+    """Algorithmic bytes per launch of each kernel kind, from the step's own counters (Cc
+    colour channels of a render; Cw colour values stored per Gaussian, Cc without SH)."""
+    Cw = Cc if Cw is None else Cw
+    p_in, r_rec, q_pix, g2 = 44 + 4 * Cw, 36 + 4 * Cc, 4 * Cc + 16, 4 * (11 + Cc)
     V, K, P, Nu = stats["visible"], stats["pairs"], stats["masked_pixels"], stats["n_unstable"]
     tw, th = stats["tile_w"], stats["tile_h"]
     FT = F * ((W + tw - 1) // tw) * ((H + th - 1) // th)
@@ -420,7 +427,10 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
 
+    sh = args.workload == "sh"
     scene, cams = scene_and_candidates()
+    if sh:  # view-dependent colour: 16 SH coefficients per channel
+        scene.colors = synth.sh_coefficients(WORKLOAD["seed"] + 11, scene.n, 3)
     settings = rtg.RenderSettings()
     ctx = rtg.Context(max_gaussians=scene.n, max_width=WORKLOAD["width"], max_height=WORKLOAD["height"],
                       max_pairs=args.max_pairs or 24 * scene.n)
@@ -454,7 +464,8 @@ def run_ours(args):
     del gt
 
     g = rtg.Gaussians.from_scene(scene, device=dev)
-    step = rtg.MaskedStep(ctx, g, [cam], mask, tcol, tdep, settings, recompute_mask=True)
+    initial = (g.means.clone(), g.scales.clone(), g.quats.clone()) if sh else None  # L_reg reference
+    step = rtg.MaskedStep(ctx, g, [cam], mask, tcol, tdep, settings, recompute_mask=True, initial=initial)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 126 MB L2
 
@@ -489,8 +500,8 @@ def run_ours(args):
     # ---- per-kernel device time, live, and the roofline of the dominant kernel
     per_launch = kernel_profile(rtg, ctx, step, args.steps, flush, stream)
     N, V, K, P, Nu = scene.n, stats["visible"], stats["pairs"], stats["masked_pixels"], stats["n_unstable"]
-    alg = alg_bytes(stats, N, 1, H, W)
-    roofline, pk = roofline_of(per_launch, alg, ctx.get_tuning(), "masked-step")
+    alg = alg_bytes(stats, N, 1, H, W, Cw=g.color_width)
+    roofline, pk = roofline_of(per_launch, alg, ctx.get_tuning(), args.workload)
     b_step = sum(alg.values())
 
     # ---- end to end through the public API with host buffers (graph replay per step)
@@ -521,10 +532,12 @@ def run_ours(args):
         value = world * 1e3 / ms_step
         clk = clocks.summary()
         result = {
-            "metric": METRIC, "value": round(value, 2), "unit": "iter/s", "n_gpus": world, "steps": args.steps,
+            "metric": SH_METRIC if sh else METRIC, "value": round(value, 2), "unit": "iter/s", "n_gpus": world,
+            "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD["name"], "gaussians": N, "unstable": Nu, "width": W, "height": H,
+            "config": {"workload": SH_WORKLOAD if sh else WORKLOAD["name"], "gaussians": N, "unstable": Nu,
+                       "width": W, "height": H,
                        "camera_candidate": k_cam, "mask_coverage": round(coverage, 4), "masked_pixels": P,
                        "pairs": K, "visible": V, "fragments_per_step": stats["fragments"],
                        "warp_records_per_step": stats["warp_records"],
@@ -544,7 +557,7 @@ def run_ours(args):
             "roofline": roofline,
             "e2e": {"value": round(world * 1e3 / e2e_step, 2), "unit": "iter/s",
                     "h2d_bytes_per_step": int(hc.numel() * 4 + hd.numel() * 4), "d2h_bytes_per_step": 12},
-            "gpu_launches": kernels_per_step(stats) * args.steps,
+            "gpu_launches": (kernels_per_step(stats) + (2 if sh else 0)) * args.steps,
             "clocks": clk,
         }
         if world == 1 and not args.no_cpu_baseline:
@@ -1521,6 +1534,8 @@ def main():
         out = run_adding(args)
     elif args.workload == "state":
         out = run_state(args)
+    elif args.workload == "sh":
+        out = run_ours(args)
     else:
         out = run_ours(args)
     if out is not None:

@@ -352,12 +352,8 @@ __global__ void __launch_bounds__(256) k_project_backward(GaussPtrs g, Work w, P
     float gp[3] = {0, 0, 0}, gs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, ga = 0.f, gc[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) gc[c] = 0.f;
-    // SH colour: the coefficient gradients are summed over the frames in the output row
+    // SH colour: k_sh_backward writes the coefficient gradients and adds the position term
     const bool sh = C == 3 && g.sh_degree > 0;
-    float *__restrict__ g_row = g_colors + (int64_t)g.col_stride * k;
-    const float *__restrict__ coef = color_ptr(g, w.rank, i);
-    if (sh && !accumulate)
-      for (int j = 0; j < g.col_stride; ++j) g_row[j] = 0.f;
     if (ok) {
       const float qn = sqrtf(P.q[0] * P.q[0] + P.q[1] * P.q[1] + P.q[2] * P.q[2] + P.q[3] * P.q[3]);
       const float qw = P.q[0] / qn, qx = P.q[1] / qn, qy = P.q[2] / qn, qz = P.q[3] / qn;
@@ -374,10 +370,7 @@ __global__ void __launch_bounds__(256) k_project_backward(GaussPtrs g, Work w, P
         ga += row[kG2Alpha];
 #pragma unroll
         for (int c = 0; c < C; ++c) gc[c] += row[kG2Col + c];
-        if (sh) {
-          const float gcf[3] = {row[kG2Col], row[kG2Col + 1], row[kG2Col + 2]};
-          sh_color_backward(g.sh_degree, coef, P.p, cam.t, gcf, g_row, gp);
-        }
+
         const float gd0 = row[g2_d0(C)], gn[3] = {row[g2_nc(C)], row[g2_nc(C) + 1], row[g2_nc(C) + 2]};
         const float gz = row[g2_z(C)];
 
@@ -531,6 +524,85 @@ __global__ void __launch_bounds__(256) k_project_backward(GaussPtrs g, Work w, P
   }
 }
 
+// SH colour backward (Section 3.1 colour from the view direction): 4 lanes per optimised
+// Gaussian, lane t owning SH coefficients 4t .. 4t+3, so a group reads and writes its
+// coefficient row (3 (d+1)^2 floats) contiguously.  Per frame that sees the Gaussian, from
+// that frame's colour gradient g_c (the screen-space row): dL/dSH[k] += g_c Y_k(r), and the
+// position gets (I - r r^T) / |p - t| sum_k (g_c . SH[k]) grad Y_k, added to g_means.
+__global__ void __launch_bounds__(256) k_sh_backward(GaussPtrs g, Work w, int F, float *__restrict__ g_means,
+                                                     float *__restrict__ g_colors, int accumulate) {
+  constexpr int G2 = 16;  // C = 3
+  const int64_t nu = (int64_t)w.counters[kNumUnstable];
+  const int64_t N = g.n;
+  const int lane = threadIdx.x & 31, t = lane & 3, q0 = lane & ~3;
+  const unsigned gmask = 0xfu << q0;  // the 4 lanes of this Gaussian
+  const int deg = g.sh_degree, K = (deg + 1) * (deg + 1), width = 3 * K;
+  const int64_t ngroups = (int64_t)gridDim.x * (blockDim.x >> 2);
+  for (int64_t kk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2; kk < nu; kk += ngroups) {
+    const int64_t i = w.ids[kk];
+    const int r = (g.u_means != nullptr) ? w.rank[i] : -1;
+    const float *pm = r >= 0 ? g.u_means + 3 * (int64_t)r : g.means + 3 * i;
+    const float p[3] = {pm[0], pm[1], pm[2]};
+    const float *coef = color_ptr(g, w.rank, i);
+    float c[4][3], acc[4][3];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = 4 * t + j;
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        c[j][cc] = k < K ? coef[3 * k + cc] : 0.f;
+        acc[j][cc] = 0.f;
+      }
+    }
+    float gpos[3] = {0.f, 0.f, 0.f};
+    for (int f = 0; f < F; ++f) {
+      if (w.ntiles[(int64_t)f * N + i] == 0u) continue;  // the same for the whole group
+      const float *row = w.grad2d + ((int64_t)f * N + kk) * G2 + kG2Col;
+      const float gc0 = row[0], gc1 = row[1], gc2 = row[2];
+      const DevCam &cam = w.cams[f];
+      const float dx = p[0] - cam.t[0], dy = p[1] - cam.t[1], dz = p[2] - cam.t[2];
+      const float il = 1.f / sqrtf(dx * dx + dy * dy + dz * dz);
+      const float x = dx * il, y = dy * il, z = dz * il;
+      float Y[kShMax];
+      sh_basis(deg, x, y, z, Y);
+      float st[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float yk = 0.f;
+#pragma unroll
+        for (int q = 0; q < kShMax; ++q) yk = q == 4 * t + j ? Y[q] : yk;
+        acc[j][0] = fmaf(gc0, yk, acc[j][0]);
+        acc[j][1] = fmaf(gc1, yk, acc[j][1]);
+        acc[j][2] = fmaf(gc2, yk, acc[j][2]);
+        st[j] = gc0 * c[j][0] + gc1 * c[j][1] + gc2 * c[j][2];
+      }
+      float sk[kShMax];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sk[4 * q + j] = __shfl_sync(gmask, st[j], q0 + q);
+      float gx, gy, gz;
+      sh_dir_grad(deg, x, y, z, sk, gx, gy, gz);
+      const float dot = gx * x + gy * y + gz * z;
+      gpos[0] += (gx - dot * x) * il;
+      gpos[1] += (gy - dot * y) * il;
+      gpos[2] += (gz - dot * z) * il;
+    }
+    float *out = g_colors + (int64_t)width * kk;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = 4 * t + j;
+      if (k < K)
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) out[3 * k + cc] = accumulate ? out[3 * k + cc] + acc[j][cc] : acc[j][cc];
+    }
+    if (t == 0) {
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) g_means[3 * kk + cc] += gpos[cc];
+    }
+  }
+}
+
 template <int C, int B>
 static void launch_backward_cb(const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn,
                                const BwdIn &in, cudaStream_t s) {
@@ -557,10 +629,12 @@ void launch_project_backward(const GaussPtrs &g, const Work &w, const Prm &prm, 
                              cudaStream_t s) {
   if (g.n <= 0) return;
   const int acc = accumulate ? 1 : 0;
-  if (g.C == 3)
+  if (g.C == 3) {
     k_project_backward<3><<<resident_grid((const void *)k_project_backward<3>, 256), 256, 0, s>>>(
-        g, w, prm, F, g_means, g_scales, g_quats, g_opacity,
-                                                         g_colors, acc);
+        g, w, prm, F, g_means, g_scales, g_quats, g_opacity, g_colors, acc);
+    if (g.sh_degree > 0)
+      k_sh_backward<<<resident_grid((const void *)k_sh_backward, 256), 256, 0, s>>>(g, w, F, g_means, g_colors, acc);
+  }
   else
     k_project_backward<8><<<resident_grid((const void *)k_project_backward<8>, 256), 256, 0, s>>>(
         g, w, prm, F, g_means, g_scales, g_quats, g_opacity,

@@ -329,7 +329,11 @@ __global__ void __launch_bounds__(256) k_adam(AdamGroups G, float *__restrict__ 
         const int64_t j = j0 + u * stride;
         if (j < n) {
           const float gg = log_space ? g[u] * x[u] : g[u];
-          const float lr_e = (grp == 4 && G.dc > 0 && (int)(j % G.width) >= G.dc) ? G.lr_rest : lr;
+          float lr_e = lr;
+          if (grp == 4 && G.dc > 0) {  // position of the value in its colour row
+            const int pos = n < (1ll << 32) ? (int)((uint32_t)j % (uint32_t)G.width) : (int)(j % G.width);
+            if (pos >= G.dc) lr_e = G.lr_rest;
+          }
           const float step = adam_delta(gg, mm[u], vv[u], lr_e, hp, bc1, bc2_sqrt);
           param[j] = log_space ? x[u] * expf(-step) : x[u] - step;
           mg[j] = mm[u];

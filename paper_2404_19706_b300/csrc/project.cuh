@@ -89,33 +89,6 @@ __device__ __forceinline__ void sh_color(int degree, const float *__restrict__ c
   }
 }
 
-// Backward of sh_color for one frame: g_coef [K][3] += gcol (x) Y, and the position gradient
-// through the view direction, gp += (I - r r^T) / |p - t| sum_k (gcol . coef_k) grad Y_k.
-__device__ __forceinline__ void sh_color_backward(int degree, const float *__restrict__ coef, const float p[3],
-                                                  const float t[3], const float gcol[3], float *__restrict__ g_coef,
-                                                  float gp[3]) {
-  const float dx = p[0] - t[0], dy = p[1] - t[1], dz = p[2] - t[2];
-  const float il = 1.f / sqrtf(dx * dx + dy * dy + dz * dz);
-  const float x = dx * il, y = dy * il, z = dz * il;
-  float Y[kShMax], sk[kShMax];
-  sh_basis(degree, x, y, z, Y);
-  const int K = (degree + 1) * (degree + 1);
-#pragma unroll
-  for (int k = 0; k < kShMax; ++k) sk[k] = 0.f;
-  for (int k = 0; k < K; ++k) {
-    g_coef[3 * k] += gcol[0] * Y[k];
-    g_coef[3 * k + 1] += gcol[1] * Y[k];
-    g_coef[3 * k + 2] += gcol[2] * Y[k];
-    sk[k] = gcol[0] * coef[3 * k] + gcol[1] * coef[3 * k + 1] + gcol[2] * coef[3 * k + 2];
-  }
-  float gx, gy, gz;
-  sh_dir_grad(degree, x, y, z, sk, gx, gy, gz);
-  const float dot = gx * x + gy * y + gz * z;
-  gp[0] += (gx - dot * x) * il;
-  gp[1] += (gy - dot * y) * il;
-  gp[2] += (gz - dot * z) * il;
-}
-
 struct Projected {
   df mux, muy;          // pixel-space centre (double-float)
   float u11, u12, u22;  // U with U^T U = Sigma_2D^-1 * kQScale^2 (upper triangular)
