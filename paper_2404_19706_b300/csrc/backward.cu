@@ -227,58 +227,91 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
       cnt += __popc(bal);
     }
     __syncwarp();
-    for (int k = cnt - 1; k >= 0; --k) {
-      const uint32_t jj = s_j[k];
-      bool act = has && jj < last;
-      const float4 r0 = s_rec[0][k], r1 = s_rec[1][k];
-      float dx = 0.f, dy = 0.f, t1 = 0.f, t2 = 0.f, g = 0.f, fa = 0.f;
-      if (act) {
-        fa = footprint(fpx, fpy, r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, prm.f_max, dx, dy, t1, t2, g);
-        act = fa >= prm.alpha_min;
-      }
-      const int rkk = s_rank[k];
-      float v[NV];
+    // Records run back to front in pairs: the two footprints are independent and are
+    // evaluated together, the transmission and colour sums then take the two fragments in
+    // order, and the two gradient rows are reduced together, so their shuffles overlap.
+    auto frag = [&](bool act, float fa, float g, float dx, float dy, float t1, float t2, const float4 &r1, int k,
+                    int rkk, float (&v)[NV]) {
 #pragma unroll
       for (int qq = 0; qq < NV; ++qq) v[qq] = 0.f;
-      if (act) {
-        const float om = 1.f - fa;
-        const float iom = __frcp_rn(om);
-        T_ = T_ * iom;  // transmission in front of fragment jj
-        const float wgt = fa * T_;
-        const float4 c0 = s_rec[2][k];
-        float cw[8] = {c0.x, c0.y, c0.z, c0.w, 0.f, 0.f, 0.f, 0.f};
-        if (H4 == 4) {
-          const float4 c1 = s_rec[3 % H4][k];
-          cw[4] = c1.x; cw[5] = c1.y; cw[6] = c1.z; cw[7] = c1.w;
-        }
-        float dLdf = 0.f;
+      if (!act) return;
+      const float om = 1.f - fa;
+      const float iom = __frcp_rn(om);
+      T_ = T_ * iom;  // transmission in front of this fragment
+      const float wgt = fa * T_;
+      const float4 c0 = s_rec[2][k];
+      float cw[8] = {c0.x, c0.y, c0.z, c0.w, 0.f, 0.f, 0.f, 0.f};
+      if (H4 == 4) {
+        const float4 c1 = s_rec[3 % H4][k];
+        cw[4] = c1.x; cw[5] = c1.y; cw[6] = c1.z; cw[7] = c1.w;
+      }
+      float dLdf = 0.f;
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-          v[6 + c] = wgt * dC[c];
-          dLdf = fmaf(dC[c], fmaf(cw[c], T_, -S[c] * iom), dLdf);
-          S[c] = fmaf(cw[c], wgt, S[c]);
-        }
-        if (rkk >= 0 && r1.w * g < prm.f_max) {  // unclamped branch of min(f_max, alpha g)
-          v[5] = dLdf * g;
-          const float dLdq = -dLdf * r1.w * g * kLn2;  // g = 2^-q
-          v[0] = -2.f * dLdq * (r1.x * t1);
-          v[1] = -2.f * dLdq * fmaf(r1.y, t1, r1.z * t2);
-          const float dLdp = dLdq * kQScale2;  // q = kQScale2 * d^T conic d
-          v[2] = dLdp * dx * dx;
-          v[3] = dLdp * 2.f * dx * dy;
-          v[4] = dLdp * dy * dy;
-        }
+      for (int c = 0; c < C; ++c) {
+        v[6 + c] = wgt * dC[c];
+        dLdf = fmaf(dC[c], fmaf(cw[c], T_, -S[c] * iom), dLdf);
+        S[c] = fmaf(cw[c], wgt, S[c]);
       }
-      if (rkk >= 0 && __any_sync(0xffffffffu, act)) {
-        const float tot = warp_transpose_sum<NV>(v);  // lane L: total of value L >> 1
-        const float t1v = __shfl_down_sync(0xffffffffu, tot, 2);
-        const float t2v = __shfl_down_sync(0xffffffffu, tot, 4);
-        const float t3v = __shfl_down_sync(0xffffffffu, tot, 6);
-        if ((lane & 7) == 0 && (lane >> 3) < NG) {
-          float4 *row = reinterpret_cast<float4 *>(g2base + (int64_t)rkk * G2);
-          atomicAdd(row + (lane >> 3), make_float4(tot, t1v, t2v, t3v));
-        }
+      if (rkk >= 0 && r1.w * g < prm.f_max) {  // unclamped branch of min(f_max, alpha g)
+        v[5] = dLdf * g;
+        const float dLdq = -dLdf * r1.w * g * kLn2;  // g = 2^-q
+        v[0] = -2.f * dLdq * (r1.x * t1);
+        v[1] = -2.f * dLdq * fmaf(r1.y, t1, r1.z * t2);
+        const float dLdp = dLdq * kQScale2;  // q = kQScale2 * d^T conic d
+        v[2] = dLdp * dx * dx;
+        v[3] = dLdp * 2.f * dx * dy;
+        v[4] = dLdp * dy * dy;
       }
+    };
+    // lane L holds the total of value L >> 1; lanes 8q add the float4 group q of the row
+    auto emit_row = [&](float tot, int rkk) {
+      const float t1v = __shfl_down_sync(0xffffffffu, tot, 2);
+      const float t2v = __shfl_down_sync(0xffffffffu, tot, 4);
+      const float t3v = __shfl_down_sync(0xffffffffu, tot, 6);
+      if ((lane & 7) == 0 && (lane >> 3) < NG) {
+        float4 *row = reinterpret_cast<float4 *>(g2base + (int64_t)rkk * G2);
+        atomicAdd(row + (lane >> 3), make_float4(tot, t1v, t2v, t3v));
+      }
+    };
+    int k = cnt - 1;
+    for (; k >= 1; k -= 2) {
+      const uint32_t jA = s_j[k], jB = s_j[k - 1];
+      const float4 a0 = s_rec[0][k], a1 = s_rec[1][k], b0 = s_rec[0][k - 1], b1 = s_rec[1][k - 1];
+      float dxA, dyA, t1A, t2A, gA, dxB, dyB, t1B, t2B, gB;
+      const float faA = footprint(fpx, fpy, a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, prm.f_max, dxA, dyA, t1A,
+                                  t2A, gA);
+      const float faB = footprint(fpx, fpy, b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w, prm.f_max, dxB, dyB, t1B,
+                                  t2B, gB);
+      const bool actA = has && jA < last && faA >= prm.alpha_min;
+      const bool actB = has && jB < last && faB >= prm.alpha_min;
+      const int rA = s_rank[k], rB = s_rank[k - 1];
+      float vA[NV], vB[NV];
+      frag(actA, faA, gA, dxA, dyA, t1A, t2A, a1, k, rA, vA);
+      frag(actB, faB, gB, dxB, dyB, t1B, t2B, b1, k - 1, rB, vB);
+      const bool fA = rA >= 0 && __any_sync(0xffffffffu, actA);
+      const bool fB = rB >= 0 && __any_sync(0xffffffffu, actB);
+      if (fA && fB) {
+        const float totA = warp_transpose_sum<NV>(vA);
+        const float totB = warp_transpose_sum<NV>(vB);
+        emit_row(totA, rA);
+        emit_row(totB, rB);
+      } else if (fA) {
+        emit_row(warp_transpose_sum<NV>(vA), rA);
+      } else if (fB) {
+        emit_row(warp_transpose_sum<NV>(vB), rB);
+      }
+    }
+    if (k == 0) {
+      const uint32_t jA = s_j[0];
+      const float4 a0 = s_rec[0][0], a1 = s_rec[1][0];
+      float dxA, dyA, t1A, t2A, gA;
+      const float faA = footprint(fpx, fpy, a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, prm.f_max, dxA, dyA, t1A,
+                                  t2A, gA);
+      const bool actA = has && jA < last && faA >= prm.alpha_min;
+      const int rA = s_rank[0];
+      float vA[NV];
+      frag(actA, faA, gA, dxA, dyA, t1A, t2A, a1, 0, rA, vA);
+      if (rA >= 0 && __any_sync(0xffffffffu, actA)) emit_row(warp_transpose_sum<NV>(vA), rA);
     }
     __syncwarp();
 #pragma unroll
