@@ -332,7 +332,8 @@ struct BwdIn {
 
 // Schedule 0: CTA `tile` with one warp per 32-pixel group of the tile's pixel list.
 template <int C, int B>
-__global__ void __launch_bounds__(kMaxTilePix) k_backward(Work w, Prm prm, int64_t N, int T, BwdIn in) {
+__global__ void __launch_bounds__(kMaxTilePix) k_backward(Work w, Prm prm, int64_t N, int T,
+                                                                               BwdIn in) {
   constexpr int H4 = (C <= 4) ? 3 : 4;
   __shared__ float4 s_rec[kMaxTilePix / 32][H4][B];
   __shared__ uint32_t s_j[kMaxTilePix / 32][B];
@@ -346,7 +347,8 @@ __global__ void __launch_bounds__(kMaxTilePix) k_backward(Work w, Prm prm, int64
 
 // Schedule 1: persistent warps over the forward's item queue (its own counter).
 template <int C, int B>
-__global__ void __launch_bounds__(256) k_backward_queue(Work w, Prm prm, int64_t N, int T, BwdIn in) {
+__global__ void __launch_bounds__(256) k_backward_queue(Work w, Prm prm, int64_t N, int T,
+                                                                              BwdIn in) {
   constexpr int H4 = (C <= 4) ? 3 : 4;
   __shared__ float4 s_rec[8][H4][B];
   __shared__ uint32_t s_j[8][B];

@@ -8,11 +8,14 @@ stops with an error.
 
 Search, in stages (each stage keeps the previous stages' best values):
   1. render tile x record batch x schedule (CTA per tile, or persistent warps at 2, 4 or
-     8 CTAs per SM), with the default sort;
+     8 CTAs per SM), with 8-bit digits and ranking for buckets of at most 256 keys;
   2. sort digit width x ranking cutoff.
 Each candidate is captured in a CUDA graph and timed by replaying it between CUDA events
-on the capture stream.  A candidate whose forward overflows the pair capacity
-(RTG_ERR_WORKSPACE) is skipped.
+on the capture stream.  With a flush buffer (larger than L2), the buffer is written before
+every replay and each replay is timed alone, so candidates are ranked under the same
+cold-L2 conditions as a benchmark that flushes between steps; the score is the median over
+the replays.  A candidate whose forward overflows the pair capacity (RTG_ERR_WORKSPACE) is
+skipped.
 """
 
 from __future__ import annotations
@@ -32,8 +35,15 @@ SCHEDULES = [(0, 4), (1, 2), (1, 4), (1, 8)]  # (schedule, persistent CTAs per S
 SORTS = [(8, 0), (8, 256), (8, 512), (4, 0), (4, 256)]  # (digit bits, ranking cutoff)
 
 
+STAGE1_SORT = (8, 256)  # sort used while the tile shape and schedule are searched
+
+
 def stage1(base: Tuning = Tuning()) -> List[Tuning]:
+    """Tile x batch x schedule, with the ranking sort for short buckets: smaller tiles make
+    shorter buckets, and ranking them is what makes those tiles pay, so searching the tile
+    shapes under the plain radix sort would rank them too low."""
     out = []
+    base = dataclasses.replace(base, sort_digit_bits=STAGE1_SORT[0], sort_rank_max=STAGE1_SORT[1])
     for (tw, th) in TILES:
         for b in BATCHES:
             for (sch, ctas) in SCHEDULES:
@@ -71,12 +81,14 @@ class Autotuner:
     """
 
     def __init__(self, ctx, step: Callable[[], object], check: Optional[Callable[[], Sequence]] = None,
-                 restore: Optional[Callable[[], None]] = None, warmup: int = 3, iters: int = 15, repeats: int = 3):
+                 restore: Optional[Callable[[], None]] = None, warmup: int = 3, iters: int = 15, repeats: int = 3,
+                 flush: Optional[torch.Tensor] = None):
         # ctx: a Context, or a sequence of Contexts that the step uses together (each gets
         # every candidate tuning)
         self.ctxs = list(ctx) if isinstance(ctx, (list, tuple)) else [ctx]
         self.step, self.check, self.restore = step, check, restore
         self.warmup, self.iters, self.repeats = warmup, iters, repeats
+        self.flush = flush
         self._ref = None
 
     def _status_ok(self) -> bool:
@@ -106,7 +118,8 @@ class Autotuner:
         return None
 
     def time(self, t: Tuning) -> Optional[float]:
-        """Median ms per step of ``t`` over ``repeats`` timed runs of ``iters`` graph replays."""
+        """Median ms per step of ``t``: over iters x repeats single replays with the flush buffer
+        written before each, else over ``repeats`` timed runs of ``iters`` back-to-back replays."""
         for c in self.ctxs:
             c.set_tuning(t)
         note = self._verify(t)
@@ -121,7 +134,18 @@ class Autotuner:
         for _ in range(self.warmup):
             graph.replay()
         samples = []
-        for _ in range(self.repeats):
+        if self.flush is not None:  # cold L2 before every replay, each replay timed alone
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(self.iters * self.repeats)]
+            torch.cuda.synchronize()
+            for a, b in ev:
+                self.flush.zero_()
+                a.record(stream)
+                graph.replay()
+                b.record(stream)
+            torch.cuda.synchronize()
+            samples = [a.elapsed_time(b) for a, b in ev]
+        for _ in range(self.repeats if self.flush is None else 0):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             a.record(stream)

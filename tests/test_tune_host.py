@@ -16,7 +16,7 @@ def test_stage1_covers_tile_batch_schedule_grid():
     assert all(valid(t) for t in c)
     assert {(t.tile_w, t.tile_h) for t in c} == {(8, 8), (8, 16), (16, 8), (16, 16), (32, 8)}
     assert {t.batch for t in c} == {32, 64} and {t.schedule for t in c} == {0, 1}
-    assert all(t.sort_digit_bits == 8 and t.sort_rank_max == 0 for t in c)  # default sort in stage 1
+    assert all(t.sort_digit_bits == 8 and t.sort_rank_max == 256 for t in c)  # ranking sort in stage 1
 
 
 def test_stage2_varies_only_the_sort():
