@@ -542,22 +542,65 @@ __global__ void __launch_bounds__(256) k_adam_rows(AdamGroups G, int64_t nu, flo
                                                    float bc2_sqrt, int32_t *__restrict__ step_dev) {
   __shared__ float s_bc[2];
   __shared__ bool s_last;
-  if (step_dev != nullptr) {
-    if (threadIdx.x == 0) {
-      const float t = (float)(step_dev[0] + 1);
-      s_bc[0] = 1.f / (1.f - powf(hp.beta1, t));
-      s_bc[1] = rsqrtf(1.f - powf(hp.beta2, t));
-      s_last = atomicAdd(reinterpret_cast<unsigned *>(step_dev + 1), 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    bc1 = s_bc[0];
-    bc2_sqrt = s_bc[1];
-  }
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < nu) {
-    if (C <= 4) {
-      adam_row_groups<C, 0, 5>(G, k, m, v, hp, bc1, bc2_sqrt);
-    } else {
+  if (C <= 4) {
+    // the row's loads are issued before the block waits for its step ticket and bias
+    // corrections, so their latencies overlap
+    constexpr int NP = 11 + C;
+    constexpr int kW[5] = {3, 3, 4, 1, C};
+    float x[NP], g[NP], mm[NP], vv[NP];
+    if (k < nu) {
+      int q = 0;
+#pragma unroll
+      for (int grp = 0; grp < 5; ++grp)
+#pragma unroll
+        for (int j = 0; j < kW[grp]; ++j, ++q) {
+          const int64_t e = k * kW[grp] + j, mi = G.begin[grp] + e;
+          x[q] = G.param[grp][e];
+          g[q] = G.grad[grp][e];
+          mm[q] = m[mi];
+          vv[q] = v[mi];
+        }
+    }
+    if (step_dev != nullptr) {
+      if (threadIdx.x == 0) {
+        const float t = (float)(step_dev[0] + 1);
+        s_bc[0] = 1.f / (1.f - powf(hp.beta1, t));
+        s_bc[1] = rsqrtf(1.f - powf(hp.beta2, t));
+        s_last = atomicAdd(reinterpret_cast<unsigned *>(step_dev + 1), 1u) == gridDim.x - 1;
+      }
+      __syncthreads();
+      bc1 = s_bc[0];
+      bc2_sqrt = s_bc[1];
+    }
+    if (k < nu) {
+      int q = 0;
+#pragma unroll
+      for (int grp = 0; grp < 5; ++grp)
+#pragma unroll
+        for (int j = 0; j < kW[grp]; ++j, ++q) {
+          const int64_t e = k * kW[grp] + j, mi = G.begin[grp] + e;
+          const bool log_space = grp == 1;  // theta = log s, dL/dtheta = s dL/ds, s <- s exp(-step)
+          const float gg = log_space ? g[q] * x[q] : g[q];
+          const float step = adam_delta(gg, mm[q], vv[q], G.lr[grp], hp, bc1, bc2_sqrt);
+          G.param[grp][e] = log_space ? x[q] * expf(-step) : x[q] - step;
+          m[mi] = mm[q];
+          v[mi] = vv[q];
+        }
+    }
+  } else {
+    if (step_dev != nullptr) {
+      if (threadIdx.x == 0) {
+        const float t = (float)(step_dev[0] + 1);
+        s_bc[0] = 1.f / (1.f - powf(hp.beta1, t));
+        s_bc[1] = rsqrtf(1.f - powf(hp.beta2, t));
+        s_last = atomicAdd(reinterpret_cast<unsigned *>(step_dev + 1), 1u) == gridDim.x - 1;
+      }
+      __syncthreads();
+      bc1 = s_bc[0];
+      bc2_sqrt = s_bc[1];
+    }
+    if (k < nu) {
       adam_row_groups<C, 0, 4>(G, k, m, v, hp, bc1, bc2_sqrt);
       adam_row_groups<C, 4, 5>(G, k, m, v, hp, bc1, bc2_sqrt);
     }
