@@ -358,13 +358,10 @@ def alg_bytes(stats, N, F, H, W, Cc=C, Cw=None):
 
 # DRAM bytes (read + write) per launch of a kernel from one ncu capture of bench.py, keyed
 # by (workload, kernel, render tile, record batch, schedule); the roofline's `traffic` is
-# filled only when the run's workload, dominant kernel and tuning match a captured one.
-# Source and command: profiles/masked_step_1M_640x480_kernels.md.
+# filled only when the run's workload, dominant kernel and tuning match a captured one of
+# the kernel as it is now.  Source and command: profiles/masked_step_1M_640x480_kernels.md.
 NCU_TRAFFIC = {
-    ("masked-step", "backward", 8, 16, 32, 1): 18_957_568,  # dram read + write, k_backward_queue<3, 32>
-    ("masked-step", "forward", 8, 16, 32, 1): 13_541_376 + 256,  # k_forward_queue<3, 32>
-    ("masked-step", "backward", 16, 16, 32, 1): 18_734_592,
-    ("masked-step", "forward", 16, 16, 32, 1): 13_311_744,
+    ("masked-step", "backward", 8, 8, 64, 1): 19_168_768 + 0,  # k_backward_queue<3, 64>, paired records
 }
 
 
@@ -1468,8 +1465,20 @@ def run_reference(args):
     t0 = time.perf_counter()
     oracle.loss_and_grads(scene, cam, st, pix[:1], tc[:1], td[:1])
     fixed = time.perf_counter() - t0
-    # each step: the per-pixel work of S random masked pixels, on the Gaussians that can reach
-    # them (the oracle renders those pixels exactly as on the whole scene), extrapolated
+    # calibration, once: the oracle's per-pixel cost on the whole scene (as it stands) and
+    # on the Gaussians that can reach the same pixels (which render them identically)
+    S_cal = min(48, len(pix))
+    cal = rng.choice(len(pix), size=S_cal, replace=False)
+    t0 = time.perf_counter()
+    oracle.loss_and_grads(scene, cam, st, pix[cal], tc[cal], td[cal])
+    per_full = max((time.perf_counter() - t0 - fixed) / S_cal, 1e-9)
+    sub = scene.subset(reach_subset(scene, cam, pix[cal]))
+    t0 = time.perf_counter()
+    oracle.loss_and_grads(sub, cam, st, pix[cal], tc[cal], td[cal])
+    per_sub_cal = max((time.perf_counter() - t0) / S_cal, 1e-9)
+    scale = per_full / per_sub_cal
+    # each step: the per-pixel work of S random masked pixels, run on the Gaussians that can
+    # reach them and scaled to the whole scene by the calibration, extrapolated to n_masked
     S = 16
     times = []
     for i in range(args.warmup + args.steps):
@@ -1479,7 +1488,7 @@ def run_reference(args):
         oracle.loss_and_grads(sub, cam, st, pix[sel], tc[sel], td[sel])
         dt = time.perf_counter() - t0
         if i >= args.warmup:
-            times.append(fixed + dt * n_masked / len(sel))
+            times.append(fixed + dt * scale * n_masked / len(sel))
     ms = float(np.mean(times)) * 1e3
     value = 1e3 / ms
     cores = int(torch.get_num_threads())
@@ -1489,9 +1498,10 @@ def run_reference(args):
             "config": {"workload": WORKLOAD["name"], "camera_candidate": k_cam, "masked_pixels_est": n_masked},
             "cpu_baseline": {"value": value, "unit": "iter/s", "cores": cores, "kind": "oracle",
                              "sample": f"each step: FP64 oracle forward+L1+autograd on {S} random masked pixels "
-                                       f"(with the Gaussians that can reach them), extrapolated to {n_masked} "
-                                       f"masked pixels, plus the {fixed:.2f} s whole-scene projection and its "
-                                       f"backward measured once"},
+                                       f"(run with the Gaussians that can reach them, scaled to the whole scene by "
+                                       f"a once-measured whole-scene / subset per-pixel ratio of {scale:.1f} on "
+                                       f"{S_cal} pixels), extrapolated to {n_masked} masked pixels, plus the "
+                                       f"{fixed:.2f} s whole-scene projection and its backward measured once"},
             "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
