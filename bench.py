@@ -921,13 +921,13 @@ def oracle_global_rate(scene, cams, tcol, tdep, frac, budget_px=48):
     t0 = time.perf_counter()
     oracle.loss_and_grads(allflag, cam, st, pix[:1], tc[:1], td[:1])
     g_fix = time.perf_counter() - t0
-    sub = allflag.subset(reach_subset(scene, cam, pix))
+    # per-pixel costs of the oracle as it stands: the whole scene, budget_px pixels
     t0 = time.perf_counter()
-    oracle.render(sub, cam, st, pixels=pix, need_borderline=False)
-    r_px = (time.perf_counter() - t0) / budget_px
+    oracle.render(allflag, cam, st, pixels=pix, need_borderline=False)
+    r_px = max((time.perf_counter() - t0 - r_fix) / (budget_px - 1), 1e-9)
     t0 = time.perf_counter()
-    oracle.loss_and_grads(sub, cam, st, pix, tc, td)
-    g_px = (time.perf_counter() - t0) / budget_px
+    oracle.loss_and_grads(allflag, cam, st, pix, tc, td)
+    g_px = max((time.perf_counter() - t0 - g_fix) / (budget_px - 1), 1e-9)
     col = np.random.default_rng(3).uniform(0, 1, tcol.shape).astype(np.float32)
     t0 = time.perf_counter()
     go.top_error_mask(col, tcol.cpu().numpy(), frac)
@@ -935,12 +935,12 @@ def oracle_global_rate(scene, cams, tcol, tdep, frac, budget_px=48):
     F, n = len(cams), H * W
     k = go.keep_count(frac, n)
     it_s = F * (r_fix + n * r_px + g_fix + k * g_px) + sel_t
-    spent = r_fix + g_fix + (r_px + g_px) * budget_px + sel_t
+    spent = 2 * (r_fix + g_fix) + (r_px + g_px) * budget_px + sel_t
     return dict(value=1.0 / it_s, unit="iter/s", cores=int(torch.get_num_threads()), kind="oracle",
-                sample=f"FP64 oracle on frame 0: render and loss+autograd fixed costs on 1 pixel ({r_fix:.1f} s, "
-                       f"{g_fix:.1f} s), per-pixel costs on {budget_px} random pixels with the Gaussians that reach "
-                       f"them; iteration = {F} x ({n} rendered + {k} selected px) + the selection "
-                       f"({sel_t:.2f} s), extrapolated ({spent:.1f} s CPU)")
+                sample=f"FP64 oracle on frame 0, whole scene: render and loss+autograd on 1 pixel ({r_fix:.1f} s, "
+                       f"{g_fix:.1f} s) and on {budget_px} random pixels (per-pixel costs from the difference); "
+                       f"iteration = {F} x ({n} rendered + {k} selected px) + the selection ({sel_t:.2f} s), "
+                       f"extrapolated ({spent:.1f} s CPU)")
 
 
 def all_optimised(scene):
@@ -1097,18 +1097,17 @@ def oracle_adding_rate(scene, cam, maps, budget_px=48):
     t0 = time.perf_counter()
     oracle.render(scene, cam, st, pixels=pix[:1], need_borderline=False)
     fix = time.perf_counter() - t0
-    sub = scene.subset(reach_subset(scene, cam, pix))
     t0 = time.perf_counter()
-    oracle.render(sub, cam, st, pixels=pix, need_borderline=False)
-    per = (time.perf_counter() - t0) / budget_px
+    oracle.render(scene, cam, st, pixels=pix, need_borderline=False)  # the whole scene, as it stands
+    per = max((time.perf_counter() - t0 - fix) / (budget_px - 1), 1e-9)
     t0 = time.perf_counter()
     ad.add_candidates([cam], *maps, ad.AddParams(seed=1))
     cand = time.perf_counter() - t0
     it_s = fix + H * W * per + cand
     return dict(value=1.0 / it_s, unit="frames/s", cores=int(torch.get_num_threads()), kind="oracle",
-                sample=f"FP64 oracle render: fixed cost on 1 pixel ({fix:.1f} s) + {H * W} px x per-pixel cost from "
-                       f"{budget_px} random pixels with the Gaussians that reach them; plus the oracle's masks, draw "
-                       f"and outputs on the full maps ({cand:.2f} s), extrapolated")
+                sample=f"FP64 oracle render of the whole scene: 1 pixel ({fix:.1f} s) and {budget_px} random pixels "
+                       f"(per-pixel cost from the difference), extrapolated to {H * W} px; plus the oracle's masks, "
+                       f"draw and outputs on the full maps ({cand:.2f} s)")
 
 
 def run_adding(args, kw=ADDING):
@@ -1298,10 +1297,9 @@ def oracle_state_rate(scene, cam, maps, arrays, budget_px=48):
     t0 = time.perf_counter()
     oracle.render(scene, cam, st, pixels=pix[:1], need_borderline=False)
     fix = time.perf_counter() - t0
-    sub = scene.subset(reach_subset(scene, cam, pix))
     t0 = time.perf_counter()
-    oracle.render(sub, cam, st, pixels=pix, need_borderline=False)
-    per = (time.perf_counter() - t0) / budget_px
+    oracle.render(scene, cam, st, pixels=pix, need_borderline=False)  # the whole scene, as it stands
+    per = max((time.perf_counter() - t0 - fix) / (budget_px - 1), 1e-9)
     rc, rd, ri, ic, idep = maps
     full, comp, ids, eta0, eta, err, t0a, unstable = arrays
     t1 = time.perf_counter()
@@ -1312,9 +1310,9 @@ def oracle_state_rate(scene, cam, maps, arrays, budget_px=48):
     rest = time.perf_counter() - t1
     it_s = fix + H * W * per + rest
     return dict(value=1.0 / it_s, unit="frames/s", cores=int(torch.get_num_threads()), kind="oracle",
-                sample=f"FP64 oracle render: fixed cost on 1 pixel ({fix:.1f} s) + {H * W} px x per-pixel cost from "
-                       f"{budget_px} random pixels with the Gaussians that reach them; plus the oracle's error counts, "
-                       f"transitions, pruning and fusion on the full arrays ({rest:.2f} s), extrapolated")
+                sample=f"FP64 oracle render of the whole scene: 1 pixel ({fix:.1f} s) and {budget_px} random pixels "
+                       f"(per-pixel cost from the difference), extrapolated to {H * W} px; plus the oracle's error "
+                       f"counts, transitions, pruning and fusion on the full arrays ({rest:.2f} s)")
 
 
 def run_state(args, kw=STATE):
