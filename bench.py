@@ -90,7 +90,7 @@ def parse():
     ap.add_argument("--tune-table", default="", help="write the autotuner's candidate table (JSON) to this path")
     ap.add_argument("--tuning", default="",
                     help="fixed launch configuration instead of the autotuner's pick: "
-                         "TWxTH,batch,schedule,ctas_per_sm,sort_bits,sort_rank_max (e.g. 8x16,32,1,4,8,256)")
+                         "TWxTH,batch,schedule,ctas_per_sm,sort_bits,sort_rank_max[,overlap] (e.g. 8x16,32,1,4,8,256)")
     ap.add_argument("--max-pairs", type=int, default=0,
                     help="pair capacity of the masked-step context (0: 24 per Gaussian); smaller keeps "
                          "profiler captures light")
@@ -266,9 +266,11 @@ def step_state(step):
 
 def parse_tuning(text):
     import paper_2404_19706_b300 as rtg
-    tile, batch, sched, ctas, bits, cut = text.split(",")
+    parts = text.split(",")
+    tile, batch, sched, ctas, bits, cut = parts[:6]
+    overlap = int(parts[6]) if len(parts) > 6 else 1
     tw, th = tile.lower().split("x")
-    return rtg.Tuning(int(tw), int(th), int(batch), int(sched), int(ctas), int(bits), int(cut))
+    return rtg.Tuning(int(tw), int(th), int(batch), int(sched), int(ctas), int(bits), int(cut), overlap)
 
 
 def run_tuner(ctx, body, check, tensors, args, label):

@@ -140,7 +140,14 @@ typedef struct {
  *   sort_rank_max     buckets of at most this many keys are ordered by ranking (a key's
  *                     position is the number of smaller keys) instead of radix passes;
  *                     0..2048, 0 = never.
- * Defaults: 16x16, 32, schedule 0, 4, 8, 0.  A setting takes effect at the next forward;
+ *   overlap           1: each call's kernels are launched with programmatic dependent
+ *                     launch, so a kernel's CTAs are scheduled while its predecessor in
+ *                     the stream drains; each waits for the predecessor's completion
+ *                     before it touches memory.  0: plain stream order.  Kernels launched
+ *                     while tracing is on (rtg_profile_enable) use plain order; the calls
+ *                     that take no context (Adam, gather / scatter, state updates) always
+ *                     launch with overlap.
+ * Defaults: 16x16, 32, schedule 0, 4, 8, 0, 1.  A setting takes effect at the next forward;
  * the backward always uses the setting of the forward it follows. */
 typedef struct {
   int32_t tile_w, tile_h;
@@ -149,6 +156,7 @@ typedef struct {
   int32_t persist_ctas_per_sm;
   int32_t sort_digit_bits;
   int32_t sort_rank_max;
+  int32_t overlap;
 } rtg_tuning;
 
 /* Bytes of device workspace rtg_create allocates for `cap`. */

@@ -55,7 +55,8 @@ class rtg_stats(Structure):
 
 class rtg_tuning(Structure):
     _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("batch", c_int32), ("schedule", c_int32),
-                ("persist_ctas_per_sm", c_int32), ("sort_digit_bits", c_int32), ("sort_rank_max", c_int32)]
+                ("persist_ctas_per_sm", c_int32), ("sort_digit_bits", c_int32), ("sort_rank_max", c_int32),
+                ("overlap", c_int32)]
 
 
 class rtg_adam_params(Structure):

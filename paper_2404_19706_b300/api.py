@@ -241,7 +241,7 @@ class Context:
         c = _lib.rtg_tuning()
         _check(_lib.load().rtg_get_tuning(self.ptr, ctypes.byref(c)), "rtg_get_tuning", self.ptr)
         return Tuning(c.tile_w, c.tile_h, c.batch, c.schedule, c.persist_ctas_per_sm, c.sort_digit_bits,
-                      c.sort_rank_max)
+                      c.sort_rank_max, c.overlap)
 
 
 @dataclasses.dataclass(frozen=True)
@@ -254,15 +254,16 @@ class Tuning:
     persist_ctas_per_sm: int = 4
     sort_digit_bits: int = 8
     sort_rank_max: int = 0
+    overlap: int = 1           # programmatic dependent launch between the kernels of a call
 
     def to_c(self):
         return _lib.rtg_tuning(self.tile_w, self.tile_h, self.batch, self.schedule, self.persist_ctas_per_sm,
-                               self.sort_digit_bits, self.sort_rank_max)
+                               self.sort_digit_bits, self.sort_rank_max, self.overlap)
 
     def as_dict(self) -> dict:
         return {"tile": f"{self.tile_w}x{self.tile_h}", "batch": self.batch, "schedule": self.schedule,
                 "persist_ctas_per_sm": self.persist_ctas_per_sm, "sort_digit_bits": self.sort_digit_bits,
-                "sort_rank_max": self.sort_rank_max}
+                "sort_rank_max": self.sort_rank_max, "overlap": self.overlap}
 
 
 def workspace_size(max_gaussians, max_frames=1, max_width=640, max_height=480, max_channels=3, max_pairs=1 << 20):

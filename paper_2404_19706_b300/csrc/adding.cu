@@ -60,6 +60,7 @@ __device__ __forceinline__ int add_kind(const AddArgs &a, int f, int64_t p) {
 // Per pixel its kind (a byte, kept for the write pass), per block the number of new
 // Gaussians.  Thread t of block b owns pixels b * kSelPerBlock + 4t .. + 3.
 __global__ void __launch_bounds__(kSelThreads) k_add_count(AddArgs a, int nb) {
+  grid_dep_wait();
   __shared__ int s_w[kSelThreads / 32];
   const int f = blockIdx.y;
   const int64_t HW = (int64_t)a.H * a.W, p0 = (int64_t)blockIdx.x * kSelPerBlock + 4 * threadIdx.x;
@@ -80,6 +81,7 @@ __global__ void __launch_bounds__(kSelThreads) k_add_count(AddArgs a, int nb) {
 
 // One CTA: exclusive scan of the per-block counts over all frames (frame-major), total out.
 __global__ void __launch_bounds__(1024) k_add_scan(AddArgs a, int total_blocks) {
+  grid_dep_wait();
   __shared__ unsigned long long s_w[32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int per = (total_blocks + 1023) / 1024;
@@ -106,6 +108,7 @@ __global__ void __launch_bounds__(1024) k_add_scan(AddArgs a, int total_blocks) 
 // Each thread reads the kinds of its 4 pixels, takes its slots from a block scan, and writes
 // the new Gaussians of those pixels (those below the capacity).
 __global__ void __launch_bounds__(kSelThreads) k_add_write(AddArgs a, AddFrames fr, int nb) {
+  grid_dep_wait();
   __shared__ uint32_t s_w[kSelThreads / 32];
   const int f = blockIdx.y, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int64_t HW = (int64_t)a.H * a.W, p0 = (int64_t)blockIdx.x * kSelPerBlock + 4 * tid;
@@ -153,9 +156,9 @@ void launch_add_candidates(const AddArgs &a, const AddFrames &fr, int F, cudaStr
   const int64_t HW = (int64_t)a.H * a.W;
   const int nb = (int)((HW + kSelPerBlock - 1) / kSelPerBlock);
   const dim3 grid((unsigned)nb, (unsigned)F);
-  k_add_count<<<grid, kSelThreads, 0, s>>>(a, nb);
-  k_add_scan<<<1, 1024, 0, s>>>(a, nb * F);
-  k_add_write<<<grid, kSelThreads, 0, s>>>(a, fr, nb);
+  launch(k_add_count, grid, kSelThreads, 0, s, a, nb);
+  launch(k_add_scan, 1, 1024, 0, s, a, nb * F);
+  launch(k_add_write, grid, kSelThreads, 0, s, a, fr, nb);
 }
 
 }  // namespace rtg

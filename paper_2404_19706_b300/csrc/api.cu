@@ -74,13 +74,17 @@ struct ProfRec {
 };
 
 namespace {
-// Records the launches between construction and destruction under `kind` when the
-// context's tracing is on; no-op otherwise.
+// Brackets the launches of one kernel kind.  Sets the calling thread's launch-overlap flag
+// from the context's tuning (off while tracing, so that each kind's events time its own
+// kernels) and restores it afterwards; with tracing on, records the launches between
+// construction and destruction under `kind`.
 struct ProfScope {
   rtg_ctx *c;
   int idx;
   cudaStream_t s;
-  ProfScope(rtg_ctx *ctx, int kind, cudaStream_t st) : c(ctx), idx(-1), s(st) {
+  bool prev_overlap;
+  ProfScope(rtg_ctx *ctx, int kind, cudaStream_t st) : c(ctx), idx(-1), s(st), prev_overlap(launch_overlap()) {
+    set_launch_overlap(c != nullptr && c->tune.overlap != 0 && !c->prof);
     if (c == nullptr || !c->prof) return;
     if (c->nrec == c->caprec) {
       if (c->caprec >= kProfMaxRecords) return;
@@ -100,6 +104,7 @@ struct ProfScope {
   }
   ~ProfScope() {
     if (idx >= 0) cudaEventRecord(c->recs[idx].b, s);
+    set_launch_overlap(prev_overlap);
   }
 };
 }  // namespace
@@ -269,6 +274,7 @@ bool make_tuning(const rtg_tuning *t, int num_sms, Tuning &o) {
   if (t->persist_ctas_per_sm < 1 || t->persist_ctas_per_sm > 8) return false;
   if (t->sort_digit_bits != 4 && t->sort_digit_bits != 8) return false;
   if (t->sort_rank_max < 0 || t->sort_rank_max > kSortCap) return false;
+  if (t->overlap != 0 && t->overlap != 1) return false;
   o.tws = tws;
   o.ths = ths;
   o.batch = t->batch;
@@ -276,6 +282,7 @@ bool make_tuning(const rtg_tuning *t, int num_sms, Tuning &o) {
   o.ctas_per_sm = t->persist_ctas_per_sm;
   o.sort_bits = t->sort_digit_bits;
   o.sort_rank_max = t->sort_rank_max;
+  o.overlap = t->overlap;
   o.num_sms = num_sms;
   return true;
 }
@@ -334,6 +341,7 @@ rtg_status rank_pass(rtg_ctx *ctx, const uint8_t *unstable, int64_t n, int32_t *
 }
 
 __global__ void k_debug_extract(Work w, int64_t N, int F, int32_t *rect, uint32_t *zbits) {
+  grid_dep_wait();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N * F) return;
   const float4 c1 = w.rec_cold[i * 2 + 1];
@@ -485,7 +493,7 @@ rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap) {
       cudaGetLastError();
       sms = 148;
     }
-    const rtg_tuning def = {16, 16, 32, 0, 4, 8, 0};
+    const rtg_tuning def = {16, 16, 32, 0, 4, 8, 0, 1};
     make_tuning(&def, sms, ctx->tune);
     ctx->tune_fwd = ctx->tune;
   }
@@ -543,6 +551,7 @@ rtg_status rtg_get_tuning(rtg_ctx *ctx, rtg_tuning *out) {
   out->persist_ctas_per_sm = t.ctas_per_sm;
   out->sort_digit_bits = t.sort_bits;
   out->sort_rank_max = t.sort_rank_max;
+  out->overlap = t.overlap;
   return RTG_OK;
 }
 
@@ -1240,7 +1249,7 @@ rtg_status rtg_debug_binning(rtg_ctx *ctx, uint32_t *tile_offsets, uint32_t *sor
   if (sorted_ids && pairs) cudaMemcpyAsync(sorted_ids, ctx->w.sorted, pairs * 4, cudaMemcpyDeviceToDevice, s);
   const int64_t NF = ctx->g.n * ctx->F;
   if ((rect || zbits) && NF > 0)
-    k_debug_extract<<<(unsigned)((NF + 255) / 256), 256, 0, s>>>(ctx->w, ctx->g.n, ctx->F, rect, zbits);
+    launch(k_debug_extract, (unsigned)((NF + 255) / 256), 256, 0, s, ctx->w, ctx->g.n, ctx->F, rect, zbits);
   return check_launch(ctx, "debug_binning");
 }
 

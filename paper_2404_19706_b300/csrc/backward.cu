@@ -334,6 +334,7 @@ struct BwdIn {
 template <int C, int B>
 __global__ void __launch_bounds__(kMaxTilePix) k_backward(Work w, Prm prm, int64_t N, int T,
                                                                                BwdIn in) {
+  grid_dep_wait();
   constexpr int H4 = (C <= 4) ? 3 : 4;
   __shared__ float4 s_rec[kMaxTilePix / 32][H4][B];
   __shared__ uint32_t s_j[kMaxTilePix / 32][B];
@@ -349,6 +350,7 @@ __global__ void __launch_bounds__(kMaxTilePix) k_backward(Work w, Prm prm, int64
 template <int C, int B>
 __global__ void __launch_bounds__(256) k_backward_queue(Work w, Prm prm, int64_t N, int T,
                                                                               BwdIn in) {
+  grid_dep_wait();
   constexpr int H4 = (C <= 4) ? 3 : 4;
   __shared__ float4 s_rec[8][H4][B];
   __shared__ uint32_t s_j[8][B];
@@ -376,6 +378,7 @@ __global__ void __launch_bounds__(256) k_project_backward(GaussPtrs g, Work w, P
                                                           float *__restrict__ g_means, float *__restrict__ g_scales,
                                                           float *__restrict__ g_quats, float *__restrict__ g_opacity,
                                                           float *__restrict__ g_colors, int accumulate) {
+  grid_dep_wait();
   constexpr int G2 = (C <= 5) ? 16 : 20;
   const int64_t nu = (int64_t)w.counters[kNumUnstable];
   const int64_t N = g.n;
@@ -566,6 +569,7 @@ __global__ void __launch_bounds__(256) k_project_backward(GaussPtrs g, Work w, P
 // position gets (I - r r^T) / |p - t| sum_k (g_c . SH[k]) grad Y_k, added to g_means.
 __global__ void __launch_bounds__(256) k_sh_backward(GaussPtrs g, Work w, int F, float *__restrict__ g_means,
                                                      float *__restrict__ g_colors, int accumulate) {
+  grid_dep_wait();
   constexpr int G2 = 16;  // C = 3
   const int64_t nu = (int64_t)w.counters[kNumUnstable];
   const int64_t N = g.n;
@@ -642,9 +646,9 @@ template <int C, int B>
 static void launch_backward_cb(const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn,
                                const BwdIn &in, cudaStream_t s) {
   if (tn.schedule == 1)
-    k_backward_queue<C, B><<<tn.num_sms * tn.ctas_per_sm, 256, 0, s>>>(w, prm, N, T, in);
+    launch(k_backward_queue<C, B>, tn.num_sms * tn.ctas_per_sm, 256, 0, s, w, prm, N, T, in);
   else
-    k_backward<C, B><<<F * T, 1 << (tn.tws + tn.ths), 0, s>>>(w, prm, N, T, in);
+    launch(k_backward<C, B>, F * T, 1 << (tn.tws + tn.ths), 0, s, w, prm, N, T, in);
 }
 
 void launch_backward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn,
@@ -665,13 +669,13 @@ void launch_project_backward(const GaussPtrs &g, const Work &w, const Prm &prm, 
   if (g.n <= 0) return;
   const int acc = accumulate ? 1 : 0;
   if (g.C == 3) {
-    k_project_backward<3><<<resident_grid((const void *)k_project_backward<3>, 256), 256, 0, s>>>(
+    launch(k_project_backward<3>, resident_grid((const void *)k_project_backward<3>, 256), 256, 0, s,
         g, w, prm, F, g_means, g_scales, g_quats, g_opacity, g_colors, acc);
     if (g.sh_degree > 0)
-      k_sh_backward<<<resident_grid((const void *)k_sh_backward, 256), 256, 0, s>>>(g, w, F, g_means, g_colors, acc);
+      launch(k_sh_backward, resident_grid((const void *)k_sh_backward, 256), 256, 0, s, g, w, F, g_means, g_colors, acc);
   }
   else
-    k_project_backward<8><<<resident_grid((const void *)k_project_backward<8>, 256), 256, 0, s>>>(
+    launch(k_project_backward<8>, resident_grid((const void *)k_project_backward<8>, 256), 256, 0, s,
         g, w, prm, F, g_means, g_scales, g_quats, g_opacity,
                                                          g_colors, acc);
 }

@@ -20,6 +20,7 @@ namespace rtg {
 __global__ void __launch_bounds__(kMaxTilePix) k_tile_mask(FrameSet fs, Work w, const uint8_t *__restrict__ mask,
                                                            int T, int tiles_x, int tws, int ths, int setup,
                                                            int lists, long long nu_preset) {
+  grid_dep_wait();
   __shared__ int s_wcnt[kMaxTilePix / 32];
   const int tile = blockIdx.x;
   const int f = tile / T, lt = tile - f * T;
@@ -76,6 +77,7 @@ __device__ __forceinline__ uint32_t load_flags(const uint8_t *__restrict__ unsta
 
 __global__ void __launch_bounds__(kRankThreads) k_rank_count(const uint8_t *__restrict__ unstable, int64_t n,
                                                              int32_t *__restrict__ block_cnt) {
+  grid_dep_wait();
   __shared__ int s_warp[kRankThreads / 32];
   uint8_t fl[kRankPer];
   const int64_t i0 = ((int64_t)blockIdx.x * kRankThreads + threadIdx.x) * kRankPer;
@@ -87,6 +89,7 @@ __global__ void __launch_bounds__(kRankThreads) k_rank_write(const uint8_t *__re
                                                              const int32_t *__restrict__ block_cnt,
                                                              int32_t *__restrict__ rank, int32_t *__restrict__ ids,
                                                              unsigned long long *nu_counter, int64_t *nu_out) {
+  grid_dep_wait();
   __shared__ int s_warp[kRankThreads / 32];
   __shared__ int s_base;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -277,6 +280,7 @@ __device__ __forceinline__ void warp_stage_rects(uint4 *__restrict__ stage, cons
 template <int kSet>
 __global__ void __launch_bounds__(256) k_cull(GaussPtrs g, Work w, Prm prm, int F, const int32_t *__restrict__ ids,
                                               int64_t count) {
+  grid_dep_wait();
   __shared__ uint32_t s_w[8];
   __shared__ unsigned long long s_base;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -331,6 +335,7 @@ __global__ void __launch_bounds__(256) k_cull(GaussPtrs g, Work w, Prm prm, int 
 // tile counter returns, so the later scatter into buckets needs no atomics.
 template <int C, int kMode>
 __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, int T, int64_t max_pairs) {
+  grid_dep_wait();
   constexpr int H4 = (C <= 4) ? 3 : 4;
   constexpr int G2 = (C <= 5) ? 16 : 20;
   __shared__ uint32_t s_w[8];
@@ -431,6 +436,7 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
 // projected), and, with an open window, the cached stable entries, whose records the window
 // pass wrote.  Index k < ncand walks the candidates, the rest the window's list.
 __global__ void __launch_bounds__(256) k_bin(Work w, int64_t N, int T, int64_t max_pairs, int cands, int stable) {
+  grid_dep_wait();
   __shared__ uint32_t s_w[8];
   __shared__ unsigned long long s_base;
   if (w.counters[kSkip] != 0ull) return;
@@ -463,7 +469,7 @@ __global__ void __launch_bounds__(256) k_bin(Work w, int64_t N, int T, int64_t m
   }
 }
 
-__global__ void k_window_reset(Work w) { w.counters[kWinStable] = 0ull; }
+__global__ void k_window_reset(Work w) { grid_dep_wait(); w.counters[kWinStable] = 0ull; }
 
 // --------------------------------------------------------------------------- tile scan
 // Cost class of a tile list of n records for the persistent schedule's queue: 0 for an
@@ -488,6 +494,7 @@ __device__ __forceinline__ uint32_t list_len(const Work &w, const uint32_t *extr
 
 __global__ void __launch_bounds__(1024) k_scan_tiles(Work w, int FT, int64_t max_pairs, int gshift,
                                                      const uint32_t *__restrict__ extra) {
+  grid_dep_wait();
   __shared__ unsigned long long s_warp[32];
   __shared__ uint32_t s_wmax[32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -584,6 +591,7 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Work w, int FT, int64_t max
 // Positive floats order like their bit patterns, so sorting a bucket by key orders it by
 // depth, then by index.
 __global__ void __launch_bounds__(256) k_emit(Work w) {
+  grid_dep_wait();
   if (w.counters[kSkip] != 0ull) return;
   const int64_t npairs = (int64_t)w.counters[kStaged];
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < npairs; k += (int64_t)gridDim.x * blockDim.x) {
@@ -594,7 +602,7 @@ __global__ void __launch_bounds__(256) k_emit(Work w) {
 
 void launch_tile_mask(const FrameSet &fs, const Work &w, const uint8_t *mask, int T, int tiles_x, int tws, int ths,
                       bool setup, bool lists, long long nu_preset, cudaStream_t s) {
-  k_tile_mask<<<fs.F * T, 1 << (tws + ths), 0, s>>>(fs, w, mask, T, tiles_x, tws, ths, setup ? 1 : 0, lists ? 1 : 0,
+  launch(k_tile_mask, fs.F * T, 1 << (tws + ths), 0, s, fs, w, mask, T, tiles_x, tws, ths, setup ? 1 : 0, lists ? 1 : 0,
                                                     nu_preset);
 }
 
@@ -602,8 +610,8 @@ void launch_rank(const uint8_t *unstable, int64_t n, int32_t *block_cnt, int32_t
                  unsigned long long *nu_counter, int64_t *nu_out, cudaStream_t s) {
   if (n <= 0) return;
   const int nb = (int)((n + kRankPerBlock - 1) / kRankPerBlock);  // <= ceil(n / kScanBlock) entries of block_cnt
-  k_rank_count<<<nb, kRankThreads, 0, s>>>(unstable, n, block_cnt);
-  k_rank_write<<<nb, kRankThreads, 0, s>>>(unstable, n, block_cnt, rank, ids, nu_counter, nu_out);
+  launch(k_rank_count, nb, kRankThreads, 0, s, unstable, n, block_cnt);
+  launch(k_rank_write, nb, kRankThreads, 0, s, unstable, n, block_cnt, rank, ids, nu_counter, nu_out);
 }
 
 void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, int T, int mode, int cull_set,
@@ -613,18 +621,18 @@ void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, in
   if (cull_set == kCullUnstable) {
     if (g.rank_map != nullptr) {
       if (g.n_unstable > 0)
-        k_cull<kCullUnstable><<<(unsigned)((g.n_unstable + 255) / 256), 256, 0, s>>>(g, w, prm, F, g.unstable_ids,
+        launch(k_cull<kCullUnstable>, (unsigned)((g.n_unstable + 255) / 256), 256, 0, s, g, w, prm, F, g.unstable_ids,
                                                                                    g.n_unstable);
     } else {
-      k_cull<kCullUnstable><<<nb, 256, 0, s>>>(g, w, prm, F, nullptr, 0);
+      launch(k_cull<kCullUnstable>, nb, 256, 0, s, g, w, prm, F, nullptr, 0);
     }
   } else if (cull_set == kCullStable) {
-    k_cull<kCullStable><<<nb, 256, 0, s>>>(g, w, prm, F, nullptr, 0);
+    launch(k_cull<kCullStable>, nb, 256, 0, s, g, w, prm, F, nullptr, 0);
   } else {
-    k_cull<kCullAll><<<nb, 256, 0, s>>>(g, w, prm, F, nullptr, 0);
+    launch(k_cull<kCullAll>, nb, 256, 0, s, g, w, prm, F, nullptr, 0);
   }
 #define RTG_PROJ(CC, MM)                                                                  \
-  k_project<CC, MM><<<resident_grid((const void *)k_project<CC, MM>, 256), 256, 0, s>>>(g, w, prm, T, \
+  launch(k_project<CC, MM>, resident_grid((const void *)k_project<CC, MM>, 256), 256, 0, s, g, w, prm, T, \
                                                                                          max_pairs)
 #define RTG_PROJ_C(CC)                              \
   switch (mode) {                                   \
@@ -644,11 +652,11 @@ void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, in
 
 void launch_bin(const Work &w, int64_t N, int T, int64_t max_pairs, bool cands, bool stable, cudaStream_t s) {
   if (N <= 0) return;
-  k_bin<<<resident_grid((const void *)k_bin, 256), 256, 0, s>>>(w, N, T, max_pairs, cands ? 1 : 0,
+  launch(k_bin, resident_grid((const void *)k_bin, 256), 256, 0, s, w, N, T, max_pairs, cands ? 1 : 0,
                                                                 stable ? 1 : 0);
 }
 
-void launch_window_reset(const Work &w, cudaStream_t s) { k_window_reset<<<1, 1, 0, s>>>(w); }
+void launch_window_reset(const Work &w, cudaStream_t s) { launch(k_window_reset, 1, 1, 0, s, w); }
 
 // ---- multi-block tile scan (many tiles: batched keyframes at high resolution).  Three
 // kernels, none of which waits on another block: per-block partials, one CTA that turns
@@ -664,6 +672,7 @@ __device__ __forceinline__ uint32_t scan_len(const Work &w, const uint32_t *extr
 
 __global__ void __launch_bounds__(1024) k_scan_part(Work w, int FT, int gshift, const uint32_t *__restrict__ extra,
                                                     int requeue) {
+  grid_dep_wait();
   __shared__ unsigned long long s_a[32], s_b[32];
   __shared__ uint32_t s_m[32];
   __shared__ uint32_t s_cls[kQueueClasses];
@@ -709,6 +718,7 @@ __global__ void __launch_bounds__(1024) k_scan_part(Work w, int FT, int gshift, 
 
 __global__ void __launch_bounds__(1024) k_scan_bases(Work w, int FT, int64_t max_pairs, int gshift, int B,
                                                      int requeue) {
+  grid_dep_wait();
   __shared__ unsigned long long s_w[32];
   __shared__ uint32_t s_start[kQueueClasses];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -774,6 +784,7 @@ __global__ void __launch_bounds__(1024) k_scan_bases(Work w, int FT, int64_t max
 
 __global__ void __launch_bounds__(1024) k_scan_write(Work w, int FT, int gshift, const uint32_t *__restrict__ extra,
                                                      int requeue) {
+  grid_dep_wait();
   __shared__ unsigned long long s_w[32];
   __shared__ uint32_t s_cur[kQueueClasses];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -814,24 +825,24 @@ __global__ void __launch_bounds__(1024) k_scan_write(Work w, int FT, int gshift,
 void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, int gshift, const uint32_t *extra,
                        cudaStream_t s) {
   if (FT <= kScanSingleMax) {
-    k_scan_tiles<<<1, 1024, 0, s>>>(w, FT, max_pairs, gshift, extra);
+    launch(k_scan_tiles, 1, 1024, 0, s, w, FT, max_pairs, gshift, extra);
     return;
   }
   const int B = (FT + kScanBlockTiles - 1) / kScanBlockTiles;  // <= 1024 (capacity check)
-  k_scan_part<<<B, 1024, 0, s>>>(w, FT, gshift, extra, 0);
-  k_scan_bases<<<1, 1024, 0, s>>>(w, FT, max_pairs, gshift, B, 0);
-  k_scan_write<<<B, 1024, 0, s>>>(w, FT, gshift, extra, 0);
+  launch(k_scan_part, B, 1024, 0, s, w, FT, gshift, extra, 0);
+  launch(k_scan_bases, 1, 1024, 0, s, w, FT, max_pairs, gshift, B, 0);
+  launch(k_scan_write, B, 1024, 0, s, w, FT, gshift, extra, 0);
 }
 
 void launch_requeue(const Work &w, int FT, int gshift, cudaStream_t s) {
   const int B = (FT + kScanBlockTiles - 1) / kScanBlockTiles;
-  k_scan_part<<<B, 1024, 0, s>>>(w, FT, gshift, nullptr, 1);
-  k_scan_bases<<<1, 1024, 0, s>>>(w, FT, 0, gshift, B, 1);
-  k_scan_write<<<B, 1024, 0, s>>>(w, FT, gshift, nullptr, 1);
+  launch(k_scan_part, B, 1024, 0, s, w, FT, gshift, nullptr, 1);
+  launch(k_scan_bases, 1, 1024, 0, s, w, FT, 0, gshift, B, 1);
+  launch(k_scan_write, B, 1024, 0, s, w, FT, gshift, nullptr, 1);
 }
 
 void launch_emit(const Work &w, cudaStream_t s) {
-  k_emit<<<resident_grid((const void *)k_emit, 256), 256, 0, s>>>(w);
+  launch(k_emit, resident_grid((const void *)k_emit, 256), 256, 0, s, w);
 }
 
 int resident_grid(const void *kernel, int block, size_t smem) {
@@ -855,5 +866,11 @@ int resident_grid(const void *kernel, int block, size_t smem) {
   if (n < 64) cache[n++] = Entry{kernel, dev, block, grid};
   return grid;
 }
+
+namespace {
+thread_local bool tl_overlap = true;  // calls without a context launch with overlap
+}
+bool launch_overlap() { return tl_overlap; }
+void set_launch_overlap(bool on) { tl_overlap = on; }
 
 }  // namespace rtg

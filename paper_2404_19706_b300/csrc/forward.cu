@@ -210,6 +210,7 @@ constexpr int fwd_min_ctas() { return (C <= 4 && B == 32) ? 3 : 1; }
 template <int C, int B>
 __global__ void __launch_bounds__(kMaxTilePix, fwd_min_ctas<C, B>()) k_forward(Work w, Prm prm, int64_t N, int T,
                                                                               FwdOut out) {
+  grid_dep_wait();
   constexpr int H4 = (C <= 4) ? 3 : 4;
   __shared__ float4 s_rec[kMaxTilePix / 32][H4][B];
   __shared__ uint32_t s_j[kMaxTilePix / 32][B];
@@ -225,6 +226,7 @@ __global__ void __launch_bounds__(kMaxTilePix, fwd_min_ctas<C, B>()) k_forward(W
 template <int C, int B>
 __global__ void __launch_bounds__(256, fwd_min_ctas<C, B>()) k_forward_queue(Work w, Prm prm, int64_t N, int T,
                                                                             FwdOut out) {
+  grid_dep_wait();
   constexpr int H4 = (C <= 4) ? 3 : 4;
   __shared__ float4 s_rec[8][H4][B];
   __shared__ uint32_t s_j[8][B];
@@ -246,9 +248,9 @@ template <int C, int B>
 static void launch_forward_cb(const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn,
                               const FwdOut &out, cudaStream_t s) {
   if (tn.schedule == 1)
-    k_forward_queue<C, B><<<tn.num_sms * tn.ctas_per_sm, 256, 0, s>>>(w, prm, N, T, out);
+    launch(k_forward_queue<C, B>, tn.num_sms * tn.ctas_per_sm, 256, 0, s, w, prm, N, T, out);
   else
-    k_forward<C, B><<<F * T, 1 << (tn.tws + tn.ths), 0, s>>>(w, prm, N, T, out);
+    launch(k_forward<C, B>, F * T, 1 << (tn.tws + tn.ths), 0, s, w, prm, N, T, out);
 }
 
 void launch_forward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn, float *color,

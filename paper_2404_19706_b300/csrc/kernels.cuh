@@ -20,6 +20,36 @@ constexpr int kQueueClasses = 4 * 32 + 4;  // cost classes of the persistent sch
 // find the work already taken.  Cached per kernel.
 int resident_grid(const void *kernel, int block, size_t smem = 0);
 
+// Programmatic dependent launch (sm_90 and later).  While the calling thread's overlap flag
+// is set, launch() marks each kernel as a programmatic dependent of the previous kernel in
+// its stream: its CTAs may be scheduled as soon as every CTA of the predecessor has begun,
+// and they wait in grid_dep_wait() until the predecessor has completed and its writes are
+// visible.  Every kernel opens with grid_dep_wait() (it returns at once after a plain
+// launch), so no kernel reads or writes memory its predecessor still uses; the wait is
+// transitive, since a kernel completes only after its own wait returned.  The wait then
+// lets the kernel's own successor be scheduled.
+__device__ __forceinline__ void grid_dep_wait() {
+  asm volatile("griddepcontrol.wait;\n\tgriddepcontrol.launch_dependents;" ::: "memory");
+}
+
+bool launch_overlap();
+void set_launch_overlap(bool on);
+
+template <typename... P, typename... A>
+void launch(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A... args) {
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr.val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = launch_overlap() ? &attr : nullptr;
+  cfg.numAttrs = launch_overlap() ? 1 : 0;
+  (void)cudaLaunchKernelEx(&cfg, kernel, args...);  // errors surface in the caller's check
+}
+
 // Launch configuration of the render path (the C ABI's rtg_tuning, validated, with the
 // tile sides as shifts).
 struct Tuning {
@@ -29,6 +59,7 @@ struct Tuning {
   int ctas_per_sm;    // schedule 1
   int sort_bits;      // 4 or 8
   int sort_rank_max;  // 0..kSortCap
+  int overlap;        // programmatic dependent launch between the kernels of a call
   int num_sms;        // of the context's device
   int gshift() const { return tws + ths - 5; }  // log2(32-pixel groups per tile)
 };

@@ -19,6 +19,7 @@ __global__ void __launch_bounds__(256) k_loss_reduce(Work w, int F, int C, int H
                                                      const float *__restrict__ tdepth,
                                                      const uint8_t *__restrict__ mask, float w_c, float w_d,
                                                      float *__restrict__ loss_out) {
+  grid_dep_wait();
   __shared__ float s_red[4][8];
   __shared__ bool s_last;
   const int64_t HW = (int64_t)H * W, NP = (int64_t)F * HW;
@@ -92,6 +93,7 @@ __global__ void __launch_bounds__(256) k_loss_reduce(Work w, int F, int C, int H
 // rate is a small fraction of its FP32 rate).
 __global__ void __launch_bounds__(256) k_loss_finalize(Work w, int FT, int gshift, int C, float w_c, float w_d,
                                                        float *__restrict__ loss_out) {
+  grid_dep_wait();
   __shared__ float s_t[3][256];
   __shared__ bool s_last;
   const int per = (FT + (int)gridDim.x - 1) / (int)gridDim.x;
@@ -160,6 +162,7 @@ __global__ void __launch_bounds__(256) k_loss_finalize(Work w, int FT, int gshif
 // stores the loss and the gradient factor 2 w_reg / (10 n_t); the second kernel adds the
 // gradient.
 __global__ void __launch_bounds__(256) k_reg_reduce(RegArgs a, float *__restrict__ loss_out) {
+  grid_dep_wait();
   __shared__ float s_t[2][256];
   __shared__ int s_last;
   float sum = 0.f, cnt = 0.f;
@@ -211,6 +214,7 @@ __global__ void __launch_bounds__(256) k_reg_reduce(RegArgs a, float *__restrict
 }
 
 __global__ void __launch_bounds__(256) k_reg_grad(RegArgs a) {
+  grid_dep_wait();
   const float sc = *a.scale;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.nu; k += (int64_t)gridDim.x * blockDim.x) {
     if (!(a.opacity[k] < a.alpha_split)) continue;
@@ -226,14 +230,14 @@ __global__ void __launch_bounds__(256) k_reg_grad(RegArgs a) {
 
 void launch_transparent_reg(const RegArgs &a, float *loss_out, cudaStream_t s) {
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(kLossBlocks, (a.nu + 255) / 256));
-  k_reg_reduce<<<blocks, 256, 0, s>>>(a, loss_out);
-  k_reg_grad<<<blocks, 256, 0, s>>>(a);
+  launch(k_reg_reduce, blocks, 256, 0, s, a, loss_out);
+  launch(k_reg_grad, blocks, 256, 0, s, a);
 }
 
 void launch_loss_finalize(const Work &w, int FT, int gshift, int C, float w_c, float w_d, float *loss_out,
                           cudaStream_t s) {
   const int blocks = std::max(1, std::min(kLossBlocks, (FT + 255) / 256));
-  k_loss_finalize<<<blocks, 256, 0, s>>>(w, FT, gshift, C, w_c, w_d, loss_out);
+  launch(k_loss_finalize, blocks, 256, 0, s, w, FT, gshift, C, w_c, w_d, loss_out);
 }
 
 __device__ __forceinline__ float signf_(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
@@ -244,6 +248,7 @@ __global__ void __launch_bounds__(256) k_loss_grad(Work w, int F, int C, int H, 
                                                    const float *__restrict__ tdepth,
                                                    const uint8_t *__restrict__ mask, float *__restrict__ dL_dcolor,
                                                    float *__restrict__ dL_ddepth) {
+  grid_dep_wait();
   const int64_t HW = (int64_t)H * W, NP = (int64_t)F * HW;
   const float s_c = w.loss_scal[4], s_d = w.loss_scal[5];
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < NP; p += (int64_t)gridDim.x * blockDim.x) {
@@ -288,6 +293,7 @@ constexpr int kAdamUnroll = 4;
 __global__ void __launch_bounds__(256) k_adam(AdamGroups G, float *__restrict__ m, float *__restrict__ v,
                                               rtg_adam_params hp, float bc1, float bc2_sqrt,
                                               int32_t *__restrict__ step_dev) {
+  grid_dep_wait();
   // Device step counter: step_dev[0] completed steps, step_dev[1] a ticket.  Every block
   // takes t = step_dev[0] + 1 when it starts; the last block to finish stores t, after
   // every block has read the old value.
@@ -359,6 +365,7 @@ __global__ void k_gather(int64_t nu, int C, const int32_t *__restrict__ ids, con
                          const float *__restrict__ opacity, const float *__restrict__ colors, float *__restrict__ um,
                          float *__restrict__ us, float *__restrict__ uq, float *__restrict__ uo,
                          float *__restrict__ uc) {
+  grid_dep_wait();
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nu) return;
   const int64_t i = ids[k];
@@ -375,6 +382,7 @@ __global__ void k_scatter(int64_t nu, int C, const int32_t *__restrict__ ids, co
                           const float *__restrict__ us, const float *__restrict__ uq, const float *__restrict__ uo,
                           const float *__restrict__ uc, float *__restrict__ means, float *__restrict__ scales,
                           float *__restrict__ quats, float *__restrict__ opacity, float *__restrict__ colors) {
+  grid_dep_wait();
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nu) return;
   const int64_t i = ids[k];
@@ -404,6 +412,7 @@ __global__ void k_scatter(int64_t nu, int C, const int32_t *__restrict__ ids, co
 template <int kMode>
 __global__ void __launch_bounds__(kTilePix) k_mask_cover_tiles(Work w, Prm prm, int64_t N, int T, int H4,
                                                                uint8_t *__restrict__ mask) {
+  grid_dep_wait();
   constexpr int NW = kTilePix / 32;
   __shared__ float4 s_rec[NW][2][32];
   __shared__ int s_wcnt[NW];
@@ -487,8 +496,8 @@ __global__ void __launch_bounds__(kTilePix) k_mask_cover_tiles(Work w, Prm prm, 
 void launch_l1_loss(const Work &w, int F, int C, int H, int W, const float *color, const float *depth,
                     const float *tcolor, const float *tdepth, const uint8_t *mask, float w_c, float w_d,
                     float *loss_out, float *dL_dcolor, float *dL_ddepth, cudaStream_t s) {
-  k_loss_reduce<<<kLossBlocks, 256, 0, s>>>(w, F, C, H, W, color, depth, tcolor, tdepth, mask, w_c, w_d, loss_out);
-  k_loss_grad<<<kLossBlocks, 256, 0, s>>>(w, F, C, H, W, color, depth, tcolor, tdepth, mask, dL_dcolor, dL_ddepth);
+  launch(k_loss_reduce, kLossBlocks, 256, 0, s, w, F, C, H, W, color, depth, tcolor, tdepth, mask, w_c, w_d, loss_out);
+  launch(k_loss_grad, kLossBlocks, 256, 0, s, w, F, C, H, W, color, depth, tcolor, tdepth, mask, dL_dcolor, dL_ddepth);
 }
 
 // Adam on groups [G0, G1) of row k: every parameter, gradient and moment of those groups is
@@ -540,6 +549,7 @@ template <int C>
 __global__ void __launch_bounds__(256) k_adam_rows(AdamGroups G, int64_t nu, float *__restrict__ m,
                                                    float *__restrict__ v, rtg_adam_params hp, float bc1,
                                                    float bc2_sqrt, int32_t *__restrict__ step_dev) {
+  grid_dep_wait();
   __shared__ float s_bc[2];
   __shared__ bool s_last;
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -637,21 +647,21 @@ void launch_adam(int64_t nu, int C, float *means, float *scales, float *quats, f
   G.dc = (hp.colors_dc > 0 && hp.colors_dc < C) ? hp.colors_dc : 0;
   if ((C == 3 || C == 8) && G.dc == 0) {
     const unsigned blocks = (unsigned)((nu + 255) / 256);
-    if (C == 3) k_adam_rows<3><<<blocks, 256, 0, s>>>(G, nu, m, v, hp, bc1, bc2_sqrt, step_dev);
-    else k_adam_rows<8><<<blocks, 256, 0, s>>>(G, nu, m, v, hp, bc1, bc2_sqrt, step_dev);
+    if (C == 3) launch(k_adam_rows<3>, blocks, 256, 0, s, G, nu, m, v, hp, bc1, bc2_sqrt, step_dev);
+    else launch(k_adam_rows<8>, blocks, 256, 0, s, G, nu, m, v, hp, bc1, bc2_sqrt, step_dev);
     return;
   }
   // other channel counts: one resident wave of CTAs strides over the elements
   const unsigned blocks = (unsigned)std::min<int64_t>((total + 256 * kAdamUnroll - 1) / (256 * kAdamUnroll),
                                                       (int64_t)resident_grid((const void *)k_adam, 256));
-  k_adam<<<blocks, 256, 0, s>>>(G, m, v, hp, bc1, bc2_sqrt, step_dev);
+  launch(k_adam, blocks, 256, 0, s, G, m, v, hp, bc1, bc2_sqrt, step_dev);
 }
 
 void launch_gather(int64_t nu, int C, const int32_t *ids, const float *means, const float *scales,
                    const float *quats, const float *opacity, const float *colors, float *um, float *us, float *uq,
                    float *uo, float *uc, cudaStream_t s) {
   if (nu <= 0) return;
-  k_gather<<<(unsigned)((nu + 255) / 256), 256, 0, s>>>(nu, C, ids, means, scales, quats, opacity, colors, um, us, uq,
+  launch(k_gather, (unsigned)((nu + 255) / 256), 256, 0, s, nu, C, ids, means, scales, quats, opacity, colors, um, us, uq,
                                                         uo, uc);
 }
 
@@ -659,18 +669,18 @@ void launch_scatter(int64_t nu, int C, const int32_t *ids, const float *um, cons
                     const float *uo, const float *uc, float *means, float *scales, float *quats, float *opacity,
                     float *colors, cudaStream_t s) {
   if (nu <= 0) return;
-  k_scatter<<<(unsigned)((nu + 255) / 256), 256, 0, s>>>(nu, C, ids, um, us, uq, uo, uc, means, scales, quats,
+  launch(k_scatter, (unsigned)((nu + 255) / 256), 256, 0, s, nu, C, ids, um, us, uq, uo, uc, means, scales, quats,
                                                          opacity, colors);
 }
 
 void launch_mask_cover_tiles(const Work &w, const Prm &prm, int64_t N, int F, int T, int C, uint8_t *mask,
                              int mode, cudaStream_t s) {
   if (mode == kCoverFusedSame)
-    k_mask_cover_tiles<kCoverFusedSame><<<F * T, kTilePix, 0, s>>>(w, prm, N, T, hot4_of(C), mask);
+    launch(k_mask_cover_tiles<kCoverFusedSame>, F * T, kTilePix, 0, s, w, prm, N, T, hot4_of(C), mask);
   else if (mode == kCoverFusedOther)
-    k_mask_cover_tiles<kCoverFusedOther><<<F * T, kTilePix, 0, s>>>(w, prm, N, T, hot4_of(C), mask);
+    launch(k_mask_cover_tiles<kCoverFusedOther>, F * T, kTilePix, 0, s, w, prm, N, T, hot4_of(C), mask);
   else
-    k_mask_cover_tiles<kCoverPlain><<<F * T, kTilePix, 0, s>>>(w, prm, N, T, hot4_of(C), mask);
+    launch(k_mask_cover_tiles<kCoverPlain>, F * T, kTilePix, 0, s, w, prm, N, T, hot4_of(C), mask);
 }
 
 }  // namespace rtg

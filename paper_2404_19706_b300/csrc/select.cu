@@ -36,6 +36,7 @@ template <int P>
 __global__ void __launch_bounds__(kSelThreads) k_sel_pass(SelBufs b, int F, int C, int64_t n, int nb, uint32_t k,
                                                           const float *__restrict__ color,
                                                           const float *__restrict__ target) {
+  grid_dep_wait();
   using D = SelDigit<P>;
   constexpr int kPer = kSelPerBlock / kSelThreads;  // pixels per thread
   constexpr int kChunk = D::bins / kSelThreads;     // histogram bins per thread
@@ -133,6 +134,7 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_pass(SelBufs b, int F, int 
 // Per-block counts of keys equal to the threshold, then (last block of each frame) their
 // exclusive scan in place: the number of equal keys before each block.
 __global__ void __launch_bounds__(kSelThreads) k_sel_ties(SelBufs b, int F, int64_t n, int nb) {
+  grid_dep_wait();
   __shared__ int s_w[kSelThreads / 32];
   __shared__ uint32_t s_u[kSelThreads / 32];
   __shared__ int s_last;
@@ -172,6 +174,7 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_ties(SelBufs b, int F, int6
 }
 
 __global__ void __launch_bounds__(kSelThreads) k_sel_mark(SelBufs b, int64_t n, int nb, uint8_t *__restrict__ mask) {
+  grid_dep_wait();
   __shared__ uint32_t s_w[kSelThreads / 32];
   const int f = blockIdx.y, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t T = b.state[2 * f], krem = b.state[2 * f + 1];
@@ -209,11 +212,11 @@ void launch_select_top_error(const SelBufs &b, int F, int C, int64_t n, uint32_t
   const int nb = (int)((n + kSelPerBlock - 1) / kSelPerBlock);
   const dim3 grid((unsigned)nb, (unsigned)F);
   cudaMemsetAsync(b.hist, 0, sel_scratch_words(F) * sizeof(uint32_t), s);
-  k_sel_pass<0><<<grid, kSelThreads, 0, s>>>(b, F, C, n, nb, k, color, target);
-  k_sel_pass<1><<<grid, kSelThreads, 0, s>>>(b, F, C, n, nb, k, color, target);
-  k_sel_pass<2><<<grid, kSelThreads, 0, s>>>(b, F, C, n, nb, k, color, target);
-  k_sel_ties<<<grid, kSelThreads, 0, s>>>(b, F, n, nb);
-  k_sel_mark<<<grid, kSelThreads, 0, s>>>(b, n, nb, mask);
+  launch(k_sel_pass<0>, grid, kSelThreads, 0, s, b, F, C, n, nb, k, color, target);
+  launch(k_sel_pass<1>, grid, kSelThreads, 0, s, b, F, C, n, nb, k, color, target);
+  launch(k_sel_pass<2>, grid, kSelThreads, 0, s, b, F, C, n, nb, k, color, target);
+  launch(k_sel_ties, grid, kSelThreads, 0, s, b, F, n, nb);
+  launch(k_sel_mark, grid, kSelThreads, 0, s, b, n, nb, mask);
 }
 
 // ----------------------------------------------------------------------------- narrowing
@@ -224,6 +227,7 @@ void launch_select_top_error(const SelBufs &b, int F, int C, int64_t n, uint32_t
 // forward does for its groups.
 __global__ void __launch_bounds__(kMaxTilePix) k_narrow_pixels(Work w, int T, const uint8_t *__restrict__ mask,
                                                                NarrowLoss nl) {
+  grid_dep_wait();
   __shared__ int s_wcnt[kMaxTilePix / 32];
   __shared__ uint8_t s_list[kMaxTilePix];
   const int tile = blockIdx.x;
@@ -295,7 +299,7 @@ __global__ void __launch_bounds__(kMaxTilePix) k_narrow_pixels(Work w, int T, co
 void launch_narrow_pixels(const Work &w, int F, int T, int tws, int ths, const uint8_t *mask, int gshift,
                           const NarrowLoss &nl, cudaStream_t s) {
   cudaMemsetAsync(w.counters + kMaskedPix, 0, sizeof(unsigned long long), s);
-  k_narrow_pixels<<<F * T, 1 << (tws + ths), 0, s>>>(w, T, mask, nl);
+  launch(k_narrow_pixels, F * T, 1 << (tws + ths), 0, s, w, T, mask, nl);
   if (gshift >= 0) launch_requeue(w, F * T, gshift, s);
 }
 

@@ -165,6 +165,7 @@ __device__ __forceinline__ void put(const Work &w, unsigned long long *keys_out,
 template <int kBits>
 __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(Work w, int rank_max, StableLists sl,
                                                              unsigned long long *keys_out) {
+  grid_dep_wait();
   constexpr int kRadix = 1 << kBits;
   constexpr unsigned long long kMask = (unsigned long long)(kRadix - 1);
   if (w.counters[kSkip] != 0ull) return;
@@ -267,9 +268,9 @@ void init_sort_attributes() {
 void launch_sort_tiles(const Work &w, int FT, int bits, int rank_max, const StableLists &sl,
                        unsigned long long *keys_out, cudaStream_t s) {
   if (bits == 4)
-    k_sort_tiles<4><<<FT, kSortThreads, sizeof(SortSmem), s>>>(w, rank_max, sl, keys_out);
+    launch(k_sort_tiles<4>, FT, kSortThreads, sizeof(SortSmem), s, w, rank_max, sl, keys_out);
   else
-    k_sort_tiles<8><<<FT, kSortThreads, sizeof(SortSmem), s>>>(w, rank_max, sl, keys_out);
+    launch(k_sort_tiles<8>, FT, kSortThreads, sizeof(SortSmem), s, w, rank_max, sl, keys_out);
 }
 
 }  // namespace rtg

@@ -14,6 +14,7 @@ namespace rtg {
 
 __global__ void __launch_bounds__(256) k_confidence(int64_t nu, int C, const int32_t *__restrict__ ids,
                                                     const float *__restrict__ g_colors, int32_t *__restrict__ eta) {
+  grid_dep_wait();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nu; k += (int64_t)gridDim.x * blockDim.x) {
     bool upd = false;
     for (int c = 0; c < C; ++c) upd |= g_colors[k * C + c] != 0.f;
@@ -28,6 +29,7 @@ __device__ __forceinline__ float blend(float a, float b, float one_w, float w) {
 __global__ void __launch_bounds__(256) k_fuse(int64_t nu, int C, const int32_t *__restrict__ ids,
                                               const int32_t *__restrict__ eta_start,
                                               const int32_t *__restrict__ eta_now, FuseArrays a) {
+  grid_dep_wait();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nu; k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = ids[k];
     const int32_t e1 = eta_now[i], e0 = eta_start[i];
@@ -52,6 +54,7 @@ __global__ void __launch_bounds__(256) k_error_mark(int F, int C, int64_t HW, co
                                                     const float *__restrict__ color, const float *__restrict__ depth,
                                                     const uint8_t *__restrict__ unstable, int64_t n, float thr_c,
                                                     float dd, uint32_t *__restrict__ bits) {
+  grid_dep_wait();
   const int64_t NP = (int64_t)F * HW;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < NP; q += (int64_t)gridDim.x * blockDim.x) {
     const int32_t idx = index_map[q];
@@ -75,6 +78,7 @@ __global__ void __launch_bounds__(256) k_error_mark(int F, int C, int64_t HW, co
 }
 
 __global__ void __launch_bounds__(256) k_error_accum(int64_t n, uint32_t *__restrict__ bits, int32_t *__restrict__ err) {
+  grid_dep_wait();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t b = bits[i];
     if (b) {
@@ -88,6 +92,7 @@ __global__ void __launch_bounds__(256) k_update_states(int64_t n, int32_t frame,
                                                        rtg_state_params p, uint8_t *__restrict__ unstable,
                                                        int32_t *__restrict__ eta, int32_t *__restrict__ err,
                                                        uint8_t *__restrict__ remove) {
+  grid_dep_wait();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     uint8_t rm = 0;
     if (unstable[i] == 0) {
@@ -113,6 +118,7 @@ constexpr int kCompactPer = 1024;
 
 __global__ void __launch_bounds__(256) k_compact_count(int64_t n, const uint8_t *__restrict__ remove,
                                                        int32_t *__restrict__ cnt) {
+  grid_dep_wait();
   __shared__ int s_w[8];
   const int64_t i0 = (int64_t)blockIdx.x * kCompactPer + threadIdx.x;
   int c = 0;
@@ -126,6 +132,7 @@ __global__ void __launch_bounds__(256) k_compact_count(int64_t n, const uint8_t 
 }
 
 __global__ void __launch_bounds__(1024) k_compact_scan(int nb, int32_t *__restrict__ cnt, long long *count_out) {
+  grid_dep_wait();
   __shared__ long long s_w[32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int per = (nb + 1023) / 1024;
@@ -152,6 +159,7 @@ __global__ void __launch_bounds__(1024) k_compact_scan(int nb, int32_t *__restri
 __global__ void __launch_bounds__(256) k_compact_write(int64_t n, int C, const uint8_t *__restrict__ remove,
                                                        const int32_t *__restrict__ base, rtg_map_arrays in,
                                                        rtg_map_arrays out) {
+  grid_dep_wait();
   __shared__ int s_w[8];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   int64_t run = base[blockIdx.x];  // kept rows of earlier blocks and chunks
@@ -197,34 +205,34 @@ static int elementwise_grid(const void *kernel, int64_t work) {
 }
 
 void launch_confidence(int64_t nu, int C, const int32_t *ids, const float *g_colors, int32_t *eta, cudaStream_t s) {
-  k_confidence<<<elementwise_grid((const void *)k_confidence, nu), 256, 0, s>>>(nu, C, ids, g_colors, eta);
+  launch(k_confidence, elementwise_grid((const void *)k_confidence, nu), 256, 0, s, nu, C, ids, g_colors, eta);
 }
 
 void launch_fuse(int64_t nu, int C, const int32_t *ids, const int32_t *eta_start, const int32_t *eta_now,
                  const FuseArrays &a, cudaStream_t s) {
-  k_fuse<<<elementwise_grid((const void *)k_fuse, nu), 256, 0, s>>>(nu, C, ids, eta_start, eta_now, a);
+  launch(k_fuse, elementwise_grid((const void *)k_fuse, nu), 256, 0, s, nu, C, ids, eta_start, eta_now, a);
 }
 
 void launch_error_count(int F, int C, int64_t HW, const float *rcolor, const float *rdepth, const int32_t *index_map,
                         const float *color, const float *depth, const uint8_t *unstable, int64_t n, float thr_c,
                         float dd, uint32_t *bits, int32_t *err, cudaStream_t s) {
-  k_error_mark<<<elementwise_grid((const void *)k_error_mark, (int64_t)F * HW), 256, 0, s>>>(
+  launch(k_error_mark, elementwise_grid((const void *)k_error_mark, (int64_t)F * HW), 256, 0, s,
       F, C, HW, rcolor, rdepth, index_map, color, depth, unstable, n, thr_c, dd, bits);
-  k_error_accum<<<elementwise_grid((const void *)k_error_accum, n), 256, 0, s>>>(n, bits, err);
+  launch(k_error_accum, elementwise_grid((const void *)k_error_accum, n), 256, 0, s, n, bits, err);
 }
 
 void launch_update_states(int64_t n, int32_t frame, const int32_t *t0, const rtg_state_params &p, uint8_t *unstable,
                           int32_t *eta, int32_t *err, uint8_t *remove, cudaStream_t s) {
-  k_update_states<<<elementwise_grid((const void *)k_update_states, n), 256, 0, s>>>(n, frame, t0, p, unstable, eta,
+  launch(k_update_states, elementwise_grid((const void *)k_update_states, n), 256, 0, s, n, frame, t0, p, unstable, eta,
                                                                                      err, remove);
 }
 
 void launch_compact(int64_t n, int C, const uint8_t *remove, int32_t *block_cnt, const rtg_map_arrays &in,
                     const rtg_map_arrays &out, long long *count_out, cudaStream_t s) {
   const int nb = (int)((n + kCompactPer - 1) / kCompactPer);
-  k_compact_count<<<nb, 256, 0, s>>>(n, remove, block_cnt);
-  k_compact_scan<<<1, 1024, 0, s>>>(nb, block_cnt, count_out);
-  k_compact_write<<<nb, 256, 0, s>>>(n, C, remove, block_cnt, in, out);
+  launch(k_compact_count, nb, 256, 0, s, n, remove, block_cnt);
+  launch(k_compact_scan, 1, 1024, 0, s, nb, block_cnt, count_out);
+  launch(k_compact_write, nb, 256, 0, s, n, C, remove, block_cnt, in, out);
 }
 
 }  // namespace rtg

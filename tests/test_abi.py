@@ -67,7 +67,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(_lib.rtg_gaussians) == 8 + 8 + 13 * 8 + 8 + 8  # + sh_degree, padded
     assert ctypes.sizeof(_lib.rtg_capacity) == 8 + 4 * 4 + 8
     assert ctypes.sizeof(_lib.rtg_stats) == 6 * 8 + 4 * 4
-    assert ctypes.sizeof(_lib.rtg_tuning) == 7 * 4
+    assert ctypes.sizeof(_lib.rtg_tuning) == 8 * 4
     assert ctypes.sizeof(_lib.rtg_add_params) == 6 * 4 + 8
     assert ctypes.sizeof(_lib.rtg_state_params) == 5 * 4
     assert ctypes.sizeof(_lib.rtg_map_arrays) == 9 * 8
