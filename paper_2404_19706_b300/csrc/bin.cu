@@ -129,141 +129,118 @@ __global__ void __launch_bounds__(kRankThreads) k_rank_write(const uint8_t *__re
 }
 
 // --------------------------------------------------------------------------- tile rects
-// A Gaussian's tile rectangle [tx0, tx1] x [ty0, ty1] is walked in row-major order,
-// kRectChunk tiles at a time: the loads of a chunk are issued together, so a rectangle is not
-// one long chain of dependent L2 round trips.
-constexpr int kRectChunk = 8;
+// Flattened warp walk.  Each lane of a warp holds one (frame, Gaussian) entry with a tile
+// rectangle [tx0, tx1] x [ty0, ty1] (empty when tx1 < tx0) in the frame whose per-tile
+// arrays start at fbase, rows of tiles_x tiles.  The rectangles are concatenated in lane
+// order into one sequence of A tiles, which the warp takes 32 x kWalkRounds tiles per pass:
+// a lane finds the rectangle that holds each of its tiles by a binary search over the
+// warp's prefix of areas, then issues the loads (and later the slot atomics) of all its
+// tiles of the pass before it waits for any.  A pass costs one L2 round trip per stage
+// however the tiles are spread over the lanes, so a Gaussian near the camera that spans
+// hundreds of tiles is walked by the whole warp in a few passes instead of holding it (and,
+// through the block's reservation barrier, its block) for a chain of round trips.  All 32
+// lanes call these functions together.
+constexpr int kWalkRounds = 4;
 
-// Tiles of the rectangle that hold masked pixels.
-__device__ __forceinline__ uint32_t count_rect(const uint32_t *__restrict__ npix, int tiles_x, int tx0, int ty0,
-                                               int tx1, int ty1) {
-  const int area = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
-  uint32_t nt = 0;
-  int tx = tx0, ty = ty0;
-  for (int a0 = 0; a0 < area; a0 += kRectChunk) {
-    uint32_t v[kRectChunk];
-#pragma unroll
-    for (int u = 0; u < kRectChunk; ++u) {
-      v[u] = (a0 + u < area) ? npix[ty * tiles_x + tx] : 0u;
-      if (++tx > tx1) {
-        tx = tx0;
-        ++ty;
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kRectChunk; ++u) nt += v[u] != 0u;
-  }
-  return nt;
-}
+struct WarpRects {
+  int P;                          // exclusive prefix of the lanes' areas: this lane's first item
+  int A;                          // the warp's total area (the same in every lane)
+  int tx0, ty0, rw, fbase, tiles_x;  // this lane's rectangle
+};
 
-// Warp-cooperative binning.  Each lane holds one (frame, Gaussian) entry with a tile
-// rectangle (empty when tx1 < tx0).  Rectangles of up to kRectChunk tiles are walked by
-// their own lane (one chunk); larger ones are walked by the whole warp together, 32 tiles
-// per round, so one Gaussian near the camera that spans hundreds of tiles does not hold its
-// warp (and, through the block's reservation barrier, its block) for hundreds of L2 round
-// trips.  All 32 lanes must call these functions together.  `fbase` is the lane's frame
-// offset f * T into the per-tile arrays; a lane without an entry passes an empty rectangle
-// (its tiles_x is not used: a big rectangle is walked with its own lane's tiles_x).
-
-// Masked tiles of each lane's rectangle.
-__device__ __forceinline__ uint32_t warp_count_rects(const uint32_t *__restrict__ npix, int tiles_x, int fbase,
-                                                     int tx0, int ty0, int tx1, int ty1) {
+__device__ __forceinline__ WarpRects warp_rects(int tiles_x, int fbase, int tx0, int ty0, int tx1, int ty1) {
   const int lane = threadIdx.x & 31;
-  const int rw = tx1 - tx0 + 1, area = tx1 < tx0 ? 0 : rw * (ty1 - ty0 + 1);
-  const bool big = area > kRectChunk;
-  uint32_t nt = (area > 0 && !big) ? count_rect(npix + fbase, tiles_x, tx0, ty0, tx1, ty1) : 0u;
-  unsigned bigs = __ballot_sync(0xffffffffu, big);
-  while (bigs) {
-    const int src = __ffs(bigs) - 1;
-    bigs &= bigs - 1;
-    const int s_area = __shfl_sync(0xffffffffu, area, src), s_rw = __shfl_sync(0xffffffffu, rw, src);
-    const int s_tx0 = __shfl_sync(0xffffffffu, tx0, src), s_ty0 = __shfl_sync(0xffffffffu, ty0, src);
-    const int s_fb = __shfl_sync(0xffffffffu, fbase, src), s_tx = __shfl_sync(0xffffffffu, tiles_x, src);
-    uint32_t cnt = 0;
-    for (int j0 = 0; j0 < s_area; j0 += 32) {
-      const int j = j0 + lane;
-      bool on = false;
-      if (j < s_area) {
-        const int yy = j / s_rw;
-        on = npix[s_fb + (s_ty0 + yy) * s_tx + s_tx0 + (j - yy * s_rw)] != 0u;
-      }
-      cnt += __popc(__ballot_sync(0xffffffffu, on));
-    }
-    if (lane == src) nt = cnt;
+  const int rw = tx1 - tx0 + 1, area = (tx1 < tx0 || ty1 < ty0) ? 0 : rw * (ty1 - ty0 + 1);
+  int incl = area;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
   }
-  return nt;
+  return WarpRects{incl - area, __shfl_sync(0xffffffffu, incl, 31), tx0, ty0, rw, fbase, tiles_x};
 }
 
-// Stages one (global tile, slot, key lo, key hi) per masked tile of each lane's rectangle,
-// at positions first, first + 1, ... of that lane (from block_reserve of the counts above).
+// Item `it` (0 <= it < A) of the warp's sequence: the lane whose rectangle holds it (the
+// last lane whose first item is at most `it`; lanes with empty rectangles share their
+// successor's first item and are passed over) and the item's index into the per-tile arrays.
+__device__ __forceinline__ int warp_rect_item(const WarpRects &r, int it, int &owner) {
+  int lo = 0;
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1)
+    if (__shfl_sync(0xffffffffu, r.P, lo + s) <= it) lo += s;
+  owner = lo;
+  const int j = it - __shfl_sync(0xffffffffu, r.P, lo);
+  const int rw = __shfl_sync(0xffffffffu, r.rw, lo);
+  const int tx0 = __shfl_sync(0xffffffffu, r.tx0, lo), ty0 = __shfl_sync(0xffffffffu, r.ty0, lo);
+  const int fb = __shfl_sync(0xffffffffu, r.fbase, lo), tw = __shfl_sync(0xffffffffu, r.tiles_x, lo);
+  const int yy = j / rw;
+  return fb + (ty0 + yy) * tw + tx0 + (j - yy * rw);
+}
+
+// Tiles with masked pixels over the warp's rectangles: the warp total (in every lane); `vis`
+// gets a bit per lane whose rectangle holds at least one.
+__device__ __forceinline__ uint32_t warp_count_rects(const uint32_t *__restrict__ npix, const WarpRects &r,
+                                                     unsigned &vis) {
+  const int lane = threadIdx.x & 31;
+  uint32_t total = 0;
+  vis = 0u;
+  for (int b0 = 0; b0 < r.A; b0 += 32 * kWalkRounds) {
+    uint32_t v[kWalkRounds];
+    int own[kWalkRounds];
+#pragma unroll
+    for (int u = 0; u < kWalkRounds; ++u) {
+      const int it = b0 + u * 32 + lane;
+      const int t = warp_rect_item(r, min(it, r.A - 1), own[u]);
+      v[u] = it < r.A ? npix[t] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kWalkRounds; ++u) {
+      const bool on = v[u] != 0u;
+      total += (uint32_t)__popc(__ballot_sync(0xffffffffu, on));
+      vis |= __reduce_or_sync(0xffffffffu, on ? 1u << own[u] : 0u);
+    }
+  }
+  return total;
+}
+
+// Stages one (global tile, slot, key lo, key hi) per masked tile over the warp's rectangles
+// at positions first, first + 1, ... (`first`: the warp's reservation, the same in every
+// lane; the keys are each owner lane's).  A tile's slots come from one atomic per distinct
+// tile of a round (match.any): lanes of a warp hold neighbouring Gaussians and often share
+// tiles, and the peers take consecutive slots.
 __device__ __forceinline__ void warp_stage_rects(uint4 *__restrict__ stage, const uint32_t *__restrict__ npix,
-                                                 uint32_t *__restrict__ tcount, int tiles_x, int fbase, int tx0,
-                                                 int ty0, int tx1, int ty1, uint32_t nt, uint32_t klo, uint32_t khi,
-                                                 unsigned long long first, int64_t max_pairs) {
+                                                 uint32_t *__restrict__ tcount, const WarpRects &r, uint32_t klo,
+                                                 uint32_t khi, unsigned long long first, int64_t max_pairs) {
   const int lane = threadIdx.x & 31;
-  const int rw = tx1 - tx0 + 1, area = tx1 < tx0 ? 0 : rw * (ty1 - ty0 + 1);
-  const bool big = area > kRectChunk;
-  // small rectangles: one chunk, all lanes together.  Lanes of a warp hold neighbouring
-  // Gaussians and often the same tiles, so the slot atomics are aggregated per tile across
-  // the warp (match.any): one atomic per distinct tile, its peers take consecutive slots.
-  {
-    const bool small = nt > 0 && !big;
-    int t[kRectChunk];
-    bool on[kRectChunk];
-    unsigned peers[kRectChunk];
-    uint32_t base[kRectChunk];
-    int tx = tx0, ty = ty0;
+  unsigned long long pos = first;
+  for (int b0 = 0; b0 < r.A; b0 += 32 * kWalkRounds) {
+    int t[kWalkRounds], own[kWalkRounds];
+    bool on[kWalkRounds];
 #pragma unroll
-    for (int u = 0; u < kRectChunk; ++u) {
-      t[u] = fbase + ty * tiles_x + tx;
-      on[u] = small && u < area && npix[t[u]] != 0u;
-      if (++tx > tx1) {
-        tx = tx0;
-        ++ty;
-      }
+    for (int u = 0; u < kWalkRounds; ++u) {
+      const int it = b0 + u * 32 + lane;
+      t[u] = warp_rect_item(r, min(it, r.A - 1), own[u]);
+      on[u] = it < r.A && npix[t[u]] != 0u;
     }
+    unsigned peers[kWalkRounds];
+    uint32_t base[kWalkRounds];
 #pragma unroll
-    for (int u = 0; u < kRectChunk; ++u) {
+    for (int u = 0; u < kWalkRounds; ++u) {
       peers[u] = __match_any_sync(0xffffffffu, on[u] ? t[u] : -1 - lane);
       base[u] = 0u;
       if (on[u] && lane == __ffs(peers[u]) - 1) base[u] = atomicAdd(tcount + t[u], (uint32_t)__popc(peers[u]));
     }
-    unsigned long long idx = first;
 #pragma unroll
-    for (int u = 0; u < kRectChunk; ++u) {
+    for (int u = 0; u < kWalkRounds; ++u) {
       const uint32_t b = __shfl_sync(0xffffffffu, base[u], __ffs(peers[u]) - 1);
+      const uint32_t lo = __shfl_sync(0xffffffffu, klo, own[u]), hi = __shfl_sync(0xffffffffu, khi, own[u]);
+      const unsigned bal = __ballot_sync(0xffffffffu, on[u]);
       if (on[u]) {
+        const unsigned long long idx = pos + (unsigned long long)__popc(bal & lanemask_lt());
         if (idx < (unsigned long long)max_pairs)
-          stage[idx] = make_uint4((uint32_t)t[u], b + __popc(peers[u] & lanemask_lt()), klo, khi);
-        ++idx;
+          stage[idx] = make_uint4((uint32_t)t[u], b + (uint32_t)__popc(peers[u] & lanemask_lt()), lo, hi);
       }
-    }
-  }
-  unsigned bigs = __ballot_sync(0xffffffffu, big && nt > 0);
-  while (bigs) {
-    const int src = __ffs(bigs) - 1;
-    bigs &= bigs - 1;
-    const int s_area = __shfl_sync(0xffffffffu, area, src), s_rw = __shfl_sync(0xffffffffu, rw, src);
-    const int s_tx0 = __shfl_sync(0xffffffffu, tx0, src), s_ty0 = __shfl_sync(0xffffffffu, ty0, src);
-    const int s_fb = __shfl_sync(0xffffffffu, fbase, src), s_tx = __shfl_sync(0xffffffffu, tiles_x, src);
-    const uint32_t s_klo = __shfl_sync(0xffffffffu, klo, src), s_khi = __shfl_sync(0xffffffffu, khi, src);
-    unsigned long long pos = __shfl_sync(0xffffffffu, first, src);
-    for (int j0 = 0; j0 < s_area; j0 += 32) {
-      const int j = j0 + lane;
-      int t = 0;
-      bool on = false;
-      if (j < s_area) {
-        const int yy = j / s_rw;
-        t = s_fb + (s_ty0 + yy) * s_tx + s_tx0 + (j - yy * s_rw);
-        on = npix[t] != 0u;
-      }
-      const unsigned bal = __ballot_sync(0xffffffffu, on);
-      if (on) {
-        const uint32_t slot = atomicAdd(tcount + t, 1u);
-        const unsigned long long idx = pos + __popc(bal & lanemask_lt());
-        if (idx < (unsigned long long)max_pairs) stage[idx] = make_uint4((uint32_t)t, slot, s_klo, s_khi);
-      }
-      pos += __popc(bal);
+      pos += (unsigned long long)__popc(bal);
     }
   }
 }
@@ -338,13 +315,13 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
   grid_dep_wait();
   constexpr int H4 = (C <= 4) ? 3 : 4;
   constexpr int G2 = (C <= 5) ? 16 : 20;
-  __shared__ uint32_t s_w[8];
+  __shared__ uint32_t s_w[16];
   __shared__ unsigned long long s_base;
   const int64_t N = g.n;
   const int64_t ncand = (int64_t)w.counters[kCand];
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < ncand; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = base + threadIdx.x;
-    uint32_t nt = 0, e = 0;
+    uint32_t e = 0;
     int f = 0, tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
     int64_t i = 0;
     bool ok = false;
@@ -384,26 +361,22 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
         if (kMode == kProjWindow || (kMode == kProjFused && g.unstable[i] == 0)) tx1 = tx0 - 1;  // no pairs
       }
     }
-    {
-      const int tiles_x = (k < ncand) ? (kMode == kProjForward ? w.cams[f].tiles_x : w.cams[f].mtiles_x) : 0;
-      nt = warp_count_rects(w.tile_npix, tiles_x, f * T, tx0, ty0, tx1, ty1);
-    }
+    const int tiles_x = (k < ncand) ? (kMode == kProjForward ? w.cams[f].tiles_x : w.cams[f].mtiles_x) : 0;
+    const WarpRects wr = warp_rects(tiles_x, f * T, tx0, ty0, tx1, ty1);
+    unsigned vis = 0u;
+    const uint32_t wtotal = warp_count_rects(w.tile_npix, wr, vis);
+    const bool visible = (vis >> (threadIdx.x & 31)) & 1u;
     if (kMode == kProjWindow) {  // one atomic per block appends the projected entries
       const unsigned long long slot = block_reserve(w.counters + kWinStable, ok ? 1u : 0u, s_w, &s_base);
       if (ok) w.scand[slot] = e;
     }
-    // block-level reservation of the staging range (one atomic per block)
-    const unsigned long long first = block_reserve(w.counters + kStaged, nt, s_w, &s_base);
-    if (kMode == kProjForward) {
-      const unsigned long long vbase = block_reserve(w.counters + kVisible, nt > 0 ? 1u : 0u, s_w, &s_base);
-      (void)vbase;
-    }
-    {
-      const int tiles_x = (k < ncand) ? (kMode == kProjForward ? w.cams[f].tiles_x : w.cams[f].mtiles_x) : 0;
-      warp_stage_rects(w.stage, w.tile_npix, w.tile_count, tiles_x, f * T, tx0, ty0, tx1, ty1, nt, (uint32_t)i,
-                       ok ? __float_as_uint(o.Z) : 0u, first, max_pairs);
-    }
-    if (ok && (nt > 0 || kMode == kProjFused || kMode == kProjWindow)) {
+    // block-level reservation of the warps' staging ranges (one atomic per block)
+    const unsigned long long first = __shfl_sync(
+        0xffffffffu,
+        block_reserve(w.counters + kStaged, (threadIdx.x & 31) == 0 ? wtotal : 0u, s_w, &s_base,
+                      kMode == kProjForward ? w.counters + kVisible : nullptr, visible ? 1u : 0u),
+        0);
+    if (ok && (visible || kMode == kProjFused || kMode == kProjWindow)) {
       const int rk = w.rank[i];
       float4 *hot = w.rec_hot + ((int64_t)f * N + i) * H4;
       hot[0] = make_float4(o.mux.hi, o.muy.hi, o.mux.lo, o.muy.lo);
@@ -425,8 +398,11 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
         for (int q = 0; q < G2 / 4; ++q) g2[q] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
-    // kProjFused: 1 marks "projected" for k_bin, which writes the final masked-tile count
-    if (k < ncand) w.ntiles[e] = (kMode == kProjFused || kMode == kProjWindow) ? (ok ? 1u : 0u) : nt;
+    // kProjFused: 1 marks "projected" for k_bin, which writes the final visibility
+    if (k < ncand) w.ntiles[e] = (kMode == kProjFused || kMode == kProjWindow) ? (ok ? 1u : 0u) : (visible ? 1u : 0u);
+    // the records are written; now the pairs
+    warp_stage_rects(w.stage, w.tile_npix, w.tile_count, wr, (uint32_t)i, ok ? __float_as_uint(o.Z) : 0u, first,
+                     max_pairs);
   }
 }
 
@@ -437,14 +413,14 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
 // pass wrote.  Index k < ncand walks the candidates, the rest the window's list.
 __global__ void __launch_bounds__(256) k_bin(Work w, int64_t N, int T, int64_t max_pairs, int cands, int stable) {
   grid_dep_wait();
-  __shared__ uint32_t s_w[8];
+  __shared__ uint32_t s_w[16];
   __shared__ unsigned long long s_base;
   if (w.counters[kSkip] != 0ull) return;
   const int64_t ncand = cands ? (int64_t)w.counters[kCand] : 0;
   const int64_t total = ncand + (stable ? (int64_t)w.counters[kWinStable] : 0);
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < total; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = base + threadIdx.x;
-    uint32_t nt = 0, e = 0;
+    uint32_t e = 0;
     int f = 0, tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1, tiles_x = 0;
     float4 c1 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (k < total) {
@@ -459,13 +435,18 @@ __global__ void __launch_bounds__(256) k_bin(Work w, int64_t N, int T, int64_t m
         tx1 = (int)(hi & 0xffffu) >> cam.tws; ty1 = (int)(hi >> 16) >> cam.ths;
       }
     }
-    nt = warp_count_rects(w.tile_npix, tiles_x, f * T, tx0, ty0, tx1, ty1);
-    const unsigned long long first = block_reserve(w.counters + kStaged, nt, s_w, &s_base);
-    const unsigned long long vbase = block_reserve(w.counters + kVisible, nt > 0 ? 1u : 0u, s_w, &s_base);
-    (void)vbase;
-    warp_stage_rects(w.stage, w.tile_npix, w.tile_count, tiles_x, f * T, tx0, ty0, tx1, ty1, nt,
-                     (uint32_t)((int64_t)e - (int64_t)f * N), __float_as_uint(c1.x), first, max_pairs);
-    if (k < total) w.ntiles[e] = nt;
+    const WarpRects wr = warp_rects(tiles_x, f * T, tx0, ty0, tx1, ty1);
+    unsigned vis = 0u;
+    const uint32_t wtotal = warp_count_rects(w.tile_npix, wr, vis);
+    const bool visible = (vis >> (threadIdx.x & 31)) & 1u;
+    const unsigned long long first = __shfl_sync(
+        0xffffffffu,
+        block_reserve(w.counters + kStaged, (threadIdx.x & 31) == 0 ? wtotal : 0u, s_w, &s_base,
+                      w.counters + kVisible, visible ? 1u : 0u),
+        0);
+    if (k < total) w.ntiles[e] = visible ? 1u : 0u;
+    warp_stage_rects(w.stage, w.tile_npix, w.tile_count, wr, (uint32_t)((int64_t)e - (int64_t)f * N),
+                     __float_as_uint(c1.x), first, max_pairs);
   }
 }
 

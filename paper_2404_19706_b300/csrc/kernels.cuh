@@ -84,10 +84,14 @@ __device__ __forceinline__ int block_sum_int(int v, int *s_warp) {
 
 // Reserves `cnt` consecutive slots of a global counter for every thread of the block with a
 // single atomic per block (same-address atomics serialise in one L2 slice, so one per warp
-// over a million threads is slow).  Returns this thread's first slot.  All threads of the
-// block must call it; s_w must hold blockDim.x / 32 entries.
+// over a million threads is slow).  Returns this thread's first slot.  With `counter2`, the
+// block's sum of `cnt2` is added to it in the same barrier round (a count: no slot is
+// returned).  All threads of the block must call it; s_w must hold 2 * blockDim.x / 32
+// entries.
 __device__ __forceinline__ unsigned long long block_reserve(unsigned long long *counter, uint32_t cnt, uint32_t *s_w,
-                                                            unsigned long long *s_base) {
+                                                            unsigned long long *s_base,
+                                                            unsigned long long *counter2 = nullptr,
+                                                            uint32_t cnt2 = 0u) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   uint32_t incl = cnt;
   for (int o = 1; o < 32; o <<= 1) {
@@ -95,14 +99,20 @@ __device__ __forceinline__ unsigned long long block_reserve(unsigned long long *
     if (lane >= o) incl += v;
   }
   if (lane == 31) s_w[wid] = incl;
+  if (counter2 != nullptr) {
+    const uint32_t c2 = __reduce_add_sync(0xffffffffu, cnt2);
+    if (lane == 0) s_w[nw + wid] = c2;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    uint32_t run = 0;
+    uint32_t run = 0, run2 = 0;
     for (int k = 0; k < nw; ++k) {
       const uint32_t c = s_w[k];
       s_w[k] = run;
       run += c;
+      if (counter2 != nullptr) run2 += s_w[nw + k];
     }
+    if (counter2 != nullptr && run2) atomicAdd(counter2, (unsigned long long)run2);
     *s_base = run ? atomicAdd(counter, (unsigned long long)run) : 0ull;
   }
   __syncthreads();
