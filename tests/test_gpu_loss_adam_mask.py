@@ -265,8 +265,12 @@ def test_fused_l1_forward_backward_match_separate_calls():
     torch.cuda.synchronize()
     assert torch.equal(c1, c2) and torch.equal(d1, d2)
     np.testing.assert_allclose(l2.cpu().numpy(), l1.cpu().numpy(), rtol=1e-5)
+    # the gradient rows are float32 sums formed by atomics whose order varies between runs:
+    # an element with cancellation differs by a few ulp of its largest terms, so the
+    # absolute tolerance scales with the array's magnitude
     for a, b in zip(g1, g2):
-        np.testing.assert_allclose(b.cpu().numpy(), a.cpu().numpy(), rtol=1e-5, atol=1e-9)
+        a, b = a.cpu().numpy(), b.cpu().numpy()
+        np.testing.assert_allclose(b, a, rtol=1e-5, atol=1e-6 * float(np.abs(a).max()))
     assert float(l1[0]) > 0
 
 
