@@ -279,16 +279,42 @@ struct AdamGroups {
   const float *grad[5];
   float lr[5];
   int64_t begin[6];  // element offsets of the groups in m / v; begin[5] = total
+  int64_t quad[6];   // the groups' first quads (runs of 4 elements) in one sequence; quad[5] = total
+  int vec[5];        // the group's four streams are 16-byte aligned: quads move as float4
   // colour group: values at row positions >= dc (dc > 0) use lr_rest (the SH coefficients
   // of degree >= 1); width = values per row
   float lr_rest;
   int width, dc;
 };
 
-// Each thread updates four elements of a group per iteration, loading all four before
-// computing, so enough loads are in flight to cover HBM latency.  Every stream (param,
-// grad, m, v) is read and written coalesced.
-constexpr int kAdamUnroll = 4;
+// Adam is element-wise, so the kernel walks the parameter groups as one sequence of quads
+// (4 consecutive elements of one group; a group's last quad may be short).  A thread takes
+// kAdamRounds quads per round, a grid's width apart, and issues every load of the round
+// (float4 per stream where the group is aligned) before it computes, so each thread has up
+// to 8 vector loads in flight and every stream (param, grad, m, v) moves in coalesced
+// 16-byte accesses.
+constexpr int kAdamRounds = 2;
+
+__device__ __forceinline__ float4 ld4(const float *p, int64_t e, int cnt, bool vec) {
+  if (vec && cnt == 4) return *reinterpret_cast<const float4 *>(p + e);
+  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (cnt > 0) r.x = p[e];
+  if (cnt > 1) r.y = p[e + 1];
+  if (cnt > 2) r.z = p[e + 2];
+  if (cnt > 3) r.w = p[e + 3];
+  return r;
+}
+
+__device__ __forceinline__ void st4(float *p, int64_t e, int cnt, bool vec, const float4 &r) {
+  if (vec && cnt == 4) {
+    *reinterpret_cast<float4 *>(p + e) = r;
+    return;
+  }
+  if (cnt > 0) p[e] = r.x;
+  if (cnt > 1) p[e + 1] = r.y;
+  if (cnt > 2) p[e + 2] = r.z;
+  if (cnt > 3) p[e + 3] = r.w;
+}
 
 __global__ void __launch_bounds__(256) k_adam(AdamGroups G, float *__restrict__ m, float *__restrict__ v,
                                               rtg_adam_params hp, float bc1, float bc2_sqrt,
@@ -308,44 +334,56 @@ __global__ void __launch_bounds__(256) k_adam(AdamGroups G, float *__restrict__ 
     bc1 = s_bc[0];
     bc2_sqrt = s_bc[1];
   }
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-#pragma unroll 1
-  for (int grp = 0; grp < 5; ++grp) {
-    float *__restrict__ param = G.param[grp];
-    const float *__restrict__ grad = G.grad[grp];
-    const float lr = G.lr[grp];
-    const bool log_space = grp == 1;  // theta = log s, dL/dtheta = s dL/ds, s <- s exp(-step)
-    const int64_t off = G.begin[grp], n = G.begin[grp + 1] - off;
-    float *__restrict__ mg = m + off;
-    float *__restrict__ vg = v + off;
-    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j0 < n; j0 += kAdamUnroll * stride) {
-      float x[kAdamUnroll], g[kAdamUnroll], mm[kAdamUnroll], vv[kAdamUnroll];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x, nq = G.quad[5];
+  for (int64_t q0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q0 < nq; q0 += kAdamRounds * stride) {
+    float4 x[kAdamRounds], g[kAdamRounds], mm[kAdamRounds], vv[kAdamRounds];
+    int grp[kAdamRounds], cnt[kAdamRounds];
+    int64_t e[kAdamRounds];
 #pragma unroll
-      for (int u = 0; u < kAdamUnroll; ++u) {
-        const int64_t j = j0 + u * stride;
-        if (j < n) {
-          x[u] = param[j];
-          g[u] = grad[j];
-          mm[u] = mg[j];
-          vv[u] = vg[j];
-        }
-      }
+    for (int r = 0; r < kAdamRounds; ++r) {
+      const int64_t q = q0 + r * stride;
+      grp[r] = 0;
+      cnt[r] = 0;
+      e[r] = 0;
+      if (q < nq) {
+        int k = 0;
 #pragma unroll
-      for (int u = 0; u < kAdamUnroll; ++u) {
-        const int64_t j = j0 + u * stride;
-        if (j < n) {
-          const float gg = log_space ? g[u] * x[u] : g[u];
-          float lr_e = lr;
-          if (grp == 4 && G.dc > 0) {  // position of the value in its colour row
-            const int pos = n < (1ll << 32) ? (int)((uint32_t)j % (uint32_t)G.width) : (int)(j % G.width);
-            if (pos >= G.dc) lr_e = G.lr_rest;
-          }
-          const float step = adam_delta(gg, mm[u], vv[u], lr_e, hp, bc1, bc2_sqrt);
-          param[j] = log_space ? x[u] * expf(-step) : x[u] - step;
-          mg[j] = mm[u];
-          vg[j] = vv[u];
-        }
+        for (int j = 1; j < 5; ++j) k += q >= G.quad[j] ? 1 : 0;
+        grp[r] = k;
+        e[r] = 4 * (q - G.quad[k]);
+        const int64_t n = G.begin[k + 1] - G.begin[k];
+        cnt[r] = (int)min((int64_t)4, n - e[r]);
       }
+      const int k = grp[r];
+      const bool vec = G.vec[k] != 0;
+      x[r] = ld4(G.param[k], e[r], cnt[r], vec);
+      g[r] = ld4(G.grad[k], e[r], cnt[r], vec);
+      mm[r] = ld4(m + G.begin[k], e[r], cnt[r], vec);
+      vv[r] = ld4(v + G.begin[k], e[r], cnt[r], vec);
+    }
+#pragma unroll
+    for (int r = 0; r < kAdamRounds; ++r) {
+      if (cnt[r] == 0) continue;
+      const int k = grp[r];
+      const bool log_space = k == 1;  // theta = log s, dL/dtheta = s dL/ds, s <- s exp(-step)
+      float xs[4] = {x[r].x, x[r].y, x[r].z, x[r].w}, gs[4] = {g[r].x, g[r].y, g[r].z, g[r].w};
+      float ms[4] = {mm[r].x, mm[r].y, mm[r].z, mm[r].w}, vs[4] = {vv[r].x, vv[r].y, vv[r].z, vv[r].w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float gg = log_space ? gs[u] * xs[u] : gs[u];
+        float lr_e = G.lr[k];
+        if (k == 4 && G.dc > 0) {  // position of the value in its colour row
+          const int64_t j = e[r] + u;
+          const int pos = j < (1ll << 32) ? (int)((uint32_t)j % (uint32_t)G.width) : (int)(j % G.width);
+          if (pos >= G.dc) lr_e = G.lr_rest;
+        }
+        const float step = adam_delta(gg, ms[u], vs[u], lr_e, hp, bc1, bc2_sqrt);
+        xs[u] = log_space ? xs[u] * expf(-step) : xs[u] - step;
+      }
+      const bool vec = G.vec[k] != 0;
+      st4(G.param[k], e[r], cnt[r], vec, make_float4(xs[0], xs[1], xs[2], xs[3]));
+      st4(m + G.begin[k], e[r], cnt[r], vec, make_float4(ms[0], ms[1], ms[2], ms[3]));
+      st4(v + G.begin[k], e[r], cnt[r], vec, make_float4(vs[0], vs[1], vs[2], vs[3]));
     }
   }
   if (step_dev != nullptr) {
@@ -437,21 +475,33 @@ __global__ void __launch_bounds__(kTilePix) k_mask_cover_tiles(Work w, Prm prm, 
   const float wcx = 0.5f * (float)(bx0 + bx1), whx = 0.5f * (float)(bx1 - bx0);
   const float wcy = 0.5f * (float)(by0 + by1), why = 0.5f * (float)(by1 - by0);
   bool cov = false;
+  // Software pipeline over the batches of 32 records: while batch b is tested, the records
+  // of batch b + 1 and the Gaussian indices of batch b + 2 are in flight, so a batch costs
+  // about one L2 round trip instead of the chain index -> record -> record.
+  auto gid_of = [&](uint32_t b0_) -> uint32_t {
+    const uint32_t j = b0_ + lane;
+    return j < n ? (uint32_t)w.keys[off + j] : 0xffffffffu;
+  };
+  auto fetch = [&](uint32_t gid, float4 &a0, float4 &a1, float2 &bb) {
+    if (gid != 0xffffffffu) {
+      bb = box[gid];
+      a0 = rec[(int64_t)gid * H4];
+      a1 = rec[(int64_t)gid * H4 + 1];
+    }
+  };
+  float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
+  float2 bb = make_float2(0.f, 0.f);
+  uint32_t gcur = gid_of(0);
+  uint32_t gnext = n > 32 ? gid_of(32) : 0xffffffffu;
+  fetch(gcur, r0, r1, bb);
   for (uint32_t b0 = 0; b0 < n; b0 += 32) {
     if (__all_sync(0xffffffffu, cov || !in)) break;
-    const uint32_t j = b0 + lane;
-    bool keep = false;
-    float4 r0, r1;
-    if (j < n) {
-      const uint32_t gid = (uint32_t)w.keys[off + j];
-      const float2 bb = box[gid];
-      r0 = rec[(int64_t)gid * H4];
-      keep = fabsf(r0.x - wcx) <= whx + bb.x && fabsf(r0.y - wcy) <= why + bb.y;
-      if (keep) {
-        r1 = rec[(int64_t)gid * H4 + 1];
-        keep = reaches_box(r0, r1, (float)bx0, (float)bx1, (float)by0, (float)by1, prm.alpha_min);
-      }
-    }
+    float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0;
+    float2 nbb = make_float2(0.f, 0.f);
+    fetch(gnext, n0, n1, nbb);
+    const uint32_t gafter = b0 + 64 < n ? gid_of(b0 + 64) : 0xffffffffu;
+    bool keep = gcur != 0xffffffffu && fabsf(r0.x - wcx) <= whx + bb.x && fabsf(r0.y - wcy) <= why + bb.y;
+    if (keep) keep = reaches_box(r0, r1, (float)bx0, (float)bx1, (float)by0, (float)by1, prm.alpha_min);
     const unsigned bal = __ballot_sync(0xffffffffu, keep);
     if (keep) {
       const int slot = __popc(bal & lanemask_lt());
@@ -472,6 +522,11 @@ __global__ void __launch_bounds__(kTilePix) k_mask_cover_tiles(Work w, Prm prm, 
       }
     }
     __syncwarp();
+    r0 = n0;
+    r1 = n1;
+    bb = nbb;
+    gcur = gnext;
+    gnext = gafter;
   }
   const int n_in = __syncthreads_count(in);
   const int n_cov = __syncthreads_count(cov);
@@ -500,130 +555,6 @@ void launch_l1_loss(const Work &w, int F, int C, int H, int W, const float *colo
   launch(k_loss_grad, kLossBlocks, 256, 0, s, w, F, C, H, W, color, depth, tcolor, tdepth, mask, dL_dcolor, dL_ddepth);
 }
 
-// Adam on groups [G0, G1) of row k: every parameter, gradient and moment of those groups is
-// loaded before any is used (one memory round trip), then updated.
-template <int C, int G0, int G1>
-__device__ __forceinline__ void adam_row_groups(const AdamGroups &G, int64_t k, float *__restrict__ m,
-                                                float *__restrict__ v, const rtg_adam_params &hp, float bc1,
-                                                float bc2_sqrt) {
-  constexpr int kW[5] = {3, 3, 4, 1, C};
-  constexpr int NP = (G0 <= 0 && G1 > 0 ? 3 : 0) + (G0 <= 1 && G1 > 1 ? 3 : 0) + (G0 <= 2 && G1 > 2 ? 4 : 0) +
-                     (G0 <= 3 && G1 > 3 ? 1 : 0) + (G0 <= 4 && G1 > 4 ? C : 0);
-  float x[NP], g[NP], mm[NP], vv[NP];
-  int q = 0;
-#pragma unroll
-  for (int grp = G0; grp < G1; ++grp) {
-#pragma unroll
-    for (int j = 0; j < kW[grp]; ++j, ++q) {
-      const int64_t e = k * kW[grp] + j;    // element within the group
-      const int64_t mi = G.begin[grp] + e;  // element within m / v
-      x[q] = G.param[grp][e];
-      g[q] = G.grad[grp][e];
-      mm[q] = m[mi];
-      vv[q] = v[mi];
-    }
-  }
-  q = 0;
-#pragma unroll
-  for (int grp = G0; grp < G1; ++grp) {
-#pragma unroll
-    for (int j = 0; j < kW[grp]; ++j, ++q) {
-      const int64_t e = k * kW[grp] + j;
-      const int64_t mi = G.begin[grp] + e;
-      const bool log_space = grp == 1;  // theta = log s, dL/dtheta = s dL/ds, s <- s exp(-step)
-      const float gg = log_space ? g[q] * x[q] : g[q];
-      const float step = adam_delta(gg, mm[q], vv[q], G.lr[grp], hp, bc1, bc2_sqrt);
-      G.param[grp][e] = log_space ? x[q] * expf(-step) : x[q] - step;
-      m[mi] = mm[q];
-      v[mi] = vv[q];
-    }
-  }
-}
-
-// One thread per unstable Gaussian (C = 3 or 8), so each thread has a whole row's loads in
-// flight at once and every stream stays coalesced (the groups are laid out one after
-// another).  C = 8 takes the geometry and the colours in two rounds to stay in registers.
-// The step ticket is taken when the block starts, so its latency overlaps the block's work;
-// the last block to take one stores t after finishing (every block read the old count first).
-template <int C>
-__global__ void __launch_bounds__(256) k_adam_rows(AdamGroups G, int64_t nu, float *__restrict__ m,
-                                                   float *__restrict__ v, rtg_adam_params hp, float bc1,
-                                                   float bc2_sqrt, int32_t *__restrict__ step_dev) {
-  grid_dep_wait();
-  __shared__ float s_bc[2];
-  __shared__ bool s_last;
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (C <= 4) {
-    // the row's loads are issued before the block waits for its step ticket and bias
-    // corrections, so their latencies overlap
-    constexpr int NP = 11 + C;
-    constexpr int kW[5] = {3, 3, 4, 1, C};
-    float x[NP], g[NP], mm[NP], vv[NP];
-    if (k < nu) {
-      int q = 0;
-#pragma unroll
-      for (int grp = 0; grp < 5; ++grp)
-#pragma unroll
-        for (int j = 0; j < kW[grp]; ++j, ++q) {
-          const int64_t e = k * kW[grp] + j, mi = G.begin[grp] + e;
-          x[q] = G.param[grp][e];
-          g[q] = G.grad[grp][e];
-          mm[q] = m[mi];
-          vv[q] = v[mi];
-        }
-    }
-    if (step_dev != nullptr) {
-      if (threadIdx.x == 0) {
-        const float t = (float)(step_dev[0] + 1);
-        s_bc[0] = 1.f / (1.f - powf(hp.beta1, t));
-        s_bc[1] = rsqrtf(1.f - powf(hp.beta2, t));
-        s_last = atomicAdd(reinterpret_cast<unsigned *>(step_dev + 1), 1u) == gridDim.x - 1;
-      }
-      __syncthreads();
-      bc1 = s_bc[0];
-      bc2_sqrt = s_bc[1];
-    }
-    if (k < nu) {
-      int q = 0;
-#pragma unroll
-      for (int grp = 0; grp < 5; ++grp)
-#pragma unroll
-        for (int j = 0; j < kW[grp]; ++j, ++q) {
-          const int64_t e = k * kW[grp] + j, mi = G.begin[grp] + e;
-          const bool log_space = grp == 1;  // theta = log s, dL/dtheta = s dL/ds, s <- s exp(-step)
-          const float gg = log_space ? g[q] * x[q] : g[q];
-          const float step = adam_delta(gg, mm[q], vv[q], G.lr[grp], hp, bc1, bc2_sqrt);
-          G.param[grp][e] = log_space ? x[q] * expf(-step) : x[q] - step;
-          m[mi] = mm[q];
-          v[mi] = vv[q];
-        }
-    }
-  } else {
-    if (step_dev != nullptr) {
-      if (threadIdx.x == 0) {
-        const float t = (float)(step_dev[0] + 1);
-        s_bc[0] = 1.f / (1.f - powf(hp.beta1, t));
-        s_bc[1] = rsqrtf(1.f - powf(hp.beta2, t));
-        s_last = atomicAdd(reinterpret_cast<unsigned *>(step_dev + 1), 1u) == gridDim.x - 1;
-      }
-      __syncthreads();
-      bc1 = s_bc[0];
-      bc2_sqrt = s_bc[1];
-    }
-    if (k < nu) {
-      adam_row_groups<C, 0, 4>(G, k, m, v, hp, bc1, bc2_sqrt);
-      adam_row_groups<C, 4, 5>(G, k, m, v, hp, bc1, bc2_sqrt);
-    }
-  }
-  if (step_dev != nullptr) {
-    __syncthreads();
-    if (threadIdx.x == 0 && s_last) {
-      step_dev[0] += 1;
-      step_dev[1] = 0;
-    }
-  }
-}
-
 void launch_adam(int64_t nu, int C, float *means, float *scales, float *quats, float *opacity, float *colors,
                  const float *g_means, const float *g_scales, const float *g_quats, const float *g_opacity,
                  const float *g_colors, float *m, float *v, const rtg_adam_params &hp, float bc1, float bc2_sqrt,
@@ -641,19 +572,18 @@ void launch_adam(int64_t nu, int C, float *means, float *scales, float *quats, f
     G.lr[k] = lrs[k];
     G.begin[k + 1] = G.begin[k] + nu * width[k];
   }
-  const int64_t total = G.begin[5];
   G.lr_rest = hp.lr_colors_rest;
   G.width = C;
   G.dc = (hp.colors_dc > 0 && hp.colors_dc < C) ? hp.colors_dc : 0;
-  if ((C == 3 || C == 8) && G.dc == 0) {
-    const unsigned blocks = (unsigned)((nu + 255) / 256);
-    if (C == 3) launch(k_adam_rows<3>, blocks, 256, 0, s, G, nu, m, v, hp, bc1, bc2_sqrt, step_dev);
-    else launch(k_adam_rows<8>, blocks, 256, 0, s, G, nu, m, v, hp, bc1, bc2_sqrt, step_dev);
-    return;
+  G.quad[0] = 0;
+  for (int k = 0; k < 5; ++k) {
+    G.quad[k + 1] = G.quad[k] + (nu * width[k] + 3) / 4;
+    const uintptr_t a = (uintptr_t)G.param[k] | (uintptr_t)G.grad[k] | (uintptr_t)(m + G.begin[k]) |
+                        (uintptr_t)(v + G.begin[k]);
+    G.vec[k] = (a & 15u) == 0u ? 1 : 0;
   }
-  // other channel counts: one resident wave of CTAs strides over the elements
-  const unsigned blocks = (unsigned)std::min<int64_t>((total + 256 * kAdamUnroll - 1) / (256 * kAdamUnroll),
-                                                      (int64_t)resident_grid((const void *)k_adam, 256));
+  const int64_t rounds = (G.quad[5] + 256 * kAdamRounds - 1) / (256 * kAdamRounds);
+  const unsigned blocks = (unsigned)std::min<int64_t>(rounds, (int64_t)resident_grid((const void *)k_adam, 256));
   launch(k_adam, blocks, 256, 0, s, G, m, v, hp, bc1, bc2_sqrt, step_dev);
 }
 
