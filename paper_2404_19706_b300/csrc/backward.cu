@@ -28,38 +28,74 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// Sums up to 16 per-lane values over the warp by halving exchanges (a reduce-scatter:
-// 8 + 4 + 2 + 1 + 1 shuffles instead of 5 per value).  Lane L returns the warp total of
-// value L >> 1; values at or beyond NV count as zero.
-template <int NV>
-__device__ __forceinline__ float warp_transpose_sum(const float (&in)[NV]) {
-  const int lane = threadIdx.x & 31;
-  float v8[8];
-  {
-    const bool up = lane & 16;
+// Warp sums of a gradient row by halving exchanges (a reduce-scatter).  At each level the
+// lanes whose level bit is clear keep the first half of their array of partial sums and the
+// others the second half, each adding its partner's copy: n values cost ceil(n / 2)
+// shuffles per level instead of one per value, and the last lane of the chain holds one
+// warp total.  Arrays of odd length are padded with a zero at the end of the level.
+__host__ __device__ constexpr int rs_half(int n) { return (n + 1) / 2; }
+
+template <int N, int H>
+__device__ __forceinline__ void rs_level(const float (&in)[N], float (&out)[H], bool up, int mask) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const float lo = i < NV ? in[i] : 0.f, hi = (8 + i) < NV ? in[8 + i] : 0.f;
-      v8[i] = (up ? hi : lo) + __shfl_xor_sync(0xffffffffu, up ? lo : hi, 16);
+  for (int i = 0; i < H; ++i) {
+    const float lo = in[i], hi = (H + i) < N ? in[H + i] : 0.f;
+    out[i] = (up ? hi : lo) + __shfl_xor_sync(0xffffffffu, up ? lo : hi, mask);
+  }
+}
+
+// The value a lane holds after the levels with the given half sizes (the level bits taken
+// from `bits`, most significant first), and whether it is a real value rather than padding.
+template <int N, int S1, int S2, int S3, int S4>
+__device__ __forceinline__ int rs_index(int bits, bool &valid) {
+  const int sz[4] = {S1, S2, S3, S4};
+  int idx = 0, n = N;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if ((bits >> (3 - k)) & 1) {
+      idx += sz[k];
+      n = n > sz[k] ? n - sz[k] : 0;
+    } else {
+      n = n < sz[k] ? n : sz[k];
     }
   }
-  float v4[4];
-  {
-    const bool up = lane & 8;
+  valid = n == 1;
+  return idx;
+}
+
+// One record: NV <= 16 values over the whole warp (levels 16, 8, 4, 2, then a plain sum over
+// lane pairs).  Lane L returns the total of value rs_index(L >> 1); lanes 2k and 2k + 1 agree.
+template <int NV>
+__device__ __forceinline__ float warp_rs_one(const float (&in)[NV]) {
+  constexpr int S1 = rs_half(NV), S2 = rs_half(S1), S3 = rs_half(S2), S4 = rs_half(S3);
+  static_assert(S4 == 1, "at most 16 values");
+  const int lane = threadIdx.x & 31;
+  float a1[S1], a2[S2], a3[S3], a4[S4];
+  rs_level<NV, S1>(in, a1, lane & 16, 16);
+  rs_level<S1, S2>(a1, a2, lane & 8, 8);
+  rs_level<S2, S3>(a2, a3, lane & 4, 4);
+  rs_level<S3, S4>(a3, a4, lane & 2, 2);
+  return a4[0] + __shfl_xor_sync(0xffffffffu, a4[0], 1);
+}
+
+// Two records: the first level sends record A to the lanes with bit 16 clear and record B
+// to the others (NV shuffles), then levels 8, 4, 2, 1 split each record's NV values.  Lane L
+// returns the total of value rs_index(L & 15) of record L >> 4; every real value is held by
+// exactly one lane.
+template <int NV>
+__device__ __forceinline__ float warp_rs_two(const float (&A)[NV], const float (&B)[NV]) {
+  constexpr int T1 = rs_half(NV), T2 = rs_half(T1), T3 = rs_half(T2), T4 = rs_half(T3);
+  static_assert(T4 == 1, "at most 16 values");
+  const int lane = threadIdx.x & 31;
+  const bool up = lane & 16;
+  float a0[NV], a1[T1], a2[T2], a3[T3], a4[T4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-      v4[i] = (up ? v8[4 + i] : v8[i]) + __shfl_xor_sync(0xffffffffu, up ? v8[i] : v8[4 + i], 8);
-  }
-  float v2[2];
-  {
-    const bool up = lane & 4;
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-      v2[i] = (up ? v4[2 + i] : v4[i]) + __shfl_xor_sync(0xffffffffu, up ? v4[i] : v4[2 + i], 4);
-  }
-  const bool up = lane & 2;
-  float v = (up ? v2[1] : v2[0]) + __shfl_xor_sync(0xffffffffu, up ? v2[0] : v2[1], 2);
-  return v + __shfl_xor_sync(0xffffffffu, v, 1);
+  for (int i = 0; i < NV; ++i) a0[i] = (up ? B[i] : A[i]) + __shfl_xor_sync(0xffffffffu, up ? A[i] : B[i], 16);
+  rs_level<NV, T1>(a0, a1, lane & 8, 8);
+  rs_level<T1, T2>(a1, a2, lane & 4, 4);
+  rs_level<T2, T3>(a2, a3, lane & 2, 2);
+  rs_level<T3, T4>(a3, a4, lane & 1, 1);
+  return a4[0];
 }
 
 // Replays the pixels of group `grp` of render tile `tile` (the forward's pixel grouping)
@@ -72,9 +108,15 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
   constexpr int H4 = (C <= 4) ? 3 : 4;
   constexpr int G2 = (C <= 5) ? 16 : 20;
   constexpr int NV = 6 + C;            // d mu (2), d conic (3), d alpha, d colour (C)
-  constexpr int NG = (NV + 3) / 4;     // float4 groups of a grad2d row they occupy
   constexpr int R = B / 32;
   const int lane = threadIdx.x & 31;
+  // the row value each lane holds after the reduce-scatters (one record, two records)
+  bool one_valid, two_valid;
+  const int one_idx = rs_index<NV, rs_half(NV), rs_half(rs_half(NV)), rs_half(rs_half(rs_half(NV))), 1>(
+      (lane >> 1) & 15, one_valid);
+  one_valid = one_valid && (lane & 1) == 0;
+  const int two_idx = rs_index<NV, rs_half(NV), rs_half(rs_half(NV)), rs_half(rs_half(rs_half(NV))), 1>(
+      lane & 15, two_valid);
   const int f = tile / T, lt = tile - f * T;
   const DevCam &cam = w.cams[f];
   const int tws = cam.tws, ths = cam.ths;
@@ -263,15 +305,14 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
         v[4] = dLdp * dy * dy;
       }
     };
-    // lane L holds the total of value L >> 1; lanes 8q add the float4 group q of the row
-    auto emit_row = [&](float tot, int rkk) {
-      const float t1v = __shfl_down_sync(0xffffffffu, tot, 2);
-      const float t2v = __shfl_down_sync(0xffffffffu, tot, 4);
-      const float t3v = __shfl_down_sync(0xffffffffu, tot, 6);
-      if ((lane & 7) == 0 && (lane >> 3) < NG) {
-        float4 *row = reinterpret_cast<float4 *>(g2base + (int64_t)rkk * G2);
-        atomicAdd(row + (lane >> 3), make_float4(tot, t1v, t2v, t3v));
-      }
+    // each lane adds the one warp total it holds to its slot of the record's row (the
+    // values are the row's first NV slots): one reduction instruction per record or pair
+    auto emit_one = [&](float tot, int rkk) {
+      if (one_valid) atomicAdd(g2base + (int64_t)rkk * G2 + one_idx, tot);
+    };
+    auto emit_two = [&](float tot, int rkA, int rkB, bool fA, bool fB) {
+      const bool mine = (lane & 16) ? fB : fA;
+      if (two_valid && mine) atomicAdd(g2base + (int64_t)((lane & 16) ? rkB : rkA) * G2 + two_idx, tot);
     };
     int k = cnt - 1;
     for (; k >= 1; k -= 2) {
@@ -291,14 +332,11 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
       const bool fA = rA >= 0 && __any_sync(0xffffffffu, actA);
       const bool fB = rB >= 0 && __any_sync(0xffffffffu, actB);
       if (fA && fB) {
-        const float totA = warp_transpose_sum<NV>(vA);
-        const float totB = warp_transpose_sum<NV>(vB);
-        emit_row(totA, rA);
-        emit_row(totB, rB);
+        emit_two(warp_rs_two<NV>(vA, vB), rA, rB, true, true);
       } else if (fA) {
-        emit_row(warp_transpose_sum<NV>(vA), rA);
+        emit_one(warp_rs_one<NV>(vA), rA);
       } else if (fB) {
-        emit_row(warp_transpose_sum<NV>(vB), rB);
+        emit_one(warp_rs_one<NV>(vB), rB);
       }
     }
     if (k == 0) {
@@ -311,7 +349,7 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
       const int rA = s_rank[0];
       float vA[NV];
       frag(actA, faA, gA, dxA, dyA, t1A, t2A, a1, 0, rA, vA);
-      if (rA >= 0 && __any_sync(0xffffffffu, actA)) emit_row(warp_transpose_sum<NV>(vA), rA);
+      if (rA >= 0 && __any_sync(0xffffffffu, actA)) emit_one(warp_rs_one<NV>(vA), rA);
     }
     __syncwarp();
 #pragma unroll
