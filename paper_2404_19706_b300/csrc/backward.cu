@@ -412,191 +412,266 @@ __global__ void __launch_bounds__(256) k_backward_queue(Work w, Prm prm, int64_t
 // The persistent backward's queue counter is cleared here (this kernel always follows the
 // backward), so a second backward of the same forward finds the queue full again.
 template <int C>
+__device__ __forceinline__ void project_backward_one(const GaussPtrs &g, const Work &w, const Prm &prm, int F,
+                                                     int64_t N, int64_t k, int64_t i, float *__restrict__ g_means,
+                                                     float *__restrict__ g_scales, float *__restrict__ g_quats,
+                                                     float *__restrict__ g_opacity, float *__restrict__ g_colors,
+                                                     int accumulate) {
+  constexpr int G2 = (C <= 5) ? 16 : 20;
+  GParams P;
+  const bool ok = load_params(g, w.rank, i, P);
+  float gp[3] = {0, 0, 0}, gs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, ga = 0.f, gc[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) gc[c] = 0.f;
+  // SH colour: k_sh_backward writes the coefficient gradients and adds the position term
+  const bool sh = C == 3 && g.sh_degree > 0;
+  if (ok) {
+    const float qn = sqrtf(P.q[0] * P.q[0] + P.q[1] * P.q[1] + P.q[2] * P.q[2] + P.q[3] * P.q[3]);
+    const float qw = P.q[0] / qn, qx = P.q[1] / qn, qy = P.q[2] / qn, qz = P.q[3] / qn;
+    float R[9];
+    quat_to_rot(qw, qx, qy, qz, R);
+    const int kmin = argmin3(P.s[0], P.s[1], P.s[2]);
+    float gR[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int f = 0; f < F; ++f) {
+      if (w.ntiles[(int64_t)f * N + i] == 0u) continue;
+      const DevCam &cam = w.cams[f];
+      const float *row = w.grad2d + ((int64_t)f * N + k) * G2;
+      const float gmx = row[kG2Mu], gmy = row[kG2Mu + 1];
+      const float gA = row[kG2Conic], gB = row[kG2Conic + 1], gCc = row[kG2Conic + 2];
+      ga += row[kG2Alpha];
+#pragma unroll
+      for (int c = 0; c < C; ++c) gc[c] += row[kG2Col + c];
+
+      const float gd0 = row[g2_d0(C)], gn[3] = {row[g2_nc(C)], row[g2_nc(C) + 1], row[g2_nc(C) + 2]};
+      const float gz = row[g2_z(C)];
+
+      // forward quantities (FP32 recomputation)
+      const float d[3] = {P.p[0] - cam.t[0], P.p[1] - cam.t[1], P.p[2] - cam.t[2]};
+      float pc[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) pc[r] = cam.R[r] * d[0] + cam.R[3 + r] * d[1] + cam.R[6 + r] * d[2];
+      float A[9];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) A[3 * r + c] = cam.R[r] * R[c] + cam.R[3 + r] * R[3 + c] + cam.R[6 + r] * R[6 + c];
+      const float X = pc[0], Y = pc[1], Z = pc[2], iz = 1.f / Z;
+      const float j00 = cam.fx * iz, j02 = -cam.fx * X * iz * iz, j11 = cam.fy * iz, j12 = -cam.fy * Y * iz * iz;
+      // Sigma_c = A S^2 A^T (camera-frame covariance); cov = J Sigma_c J^T + lowpass I
+      float Sc[9];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          float acc = 0.f;
+#pragma unroll
+          for (int m = 0; m < 3; ++m) acc += A[3 * r + m] * P.s[m] * P.s[m] * A[3 * c + m];
+          Sc[3 * r + c] = acc;
+        }
+      const float J[6] = {j00, 0.f, j02, 0.f, j11, j12};
+      float JS[6];  // J Sigma_c (2x3)
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) JS[3 * r + c] = J[3 * r] * Sc[c] + J[3 * r + 1] * Sc[3 + c] + J[3 * r + 2] * Sc[6 + c];
+      const float a = JS[0] * J[0] + JS[1] * J[1] + JS[2] * J[2] + prm.lowpass;
+      const float b = JS[0] * J[3] + JS[1] * J[4] + JS[2] * J[5];
+      const float cc = JS[3] * J[3] + JS[4] * J[4] + JS[5] * J[5] + prm.lowpass;
+      const float det = a * cc - b * b;
+      const float id2 = 1.f / (det * det);
+      // conic (a', b', c') = (c, -b, a) / det  ->  gradient w.r.t. (a, b, c) of Sigma_2D
+      const float ga_ = (-cc * cc * gA + b * cc * gB - b * b * gCc) * id2;
+      const float gb_ = (2.f * b * cc * gA - (a * cc + b * b) * gB + 2.f * a * b * gCc) * id2;
+      const float gc_ = (-b * b * gA + a * b * gB - a * a * gCc) * id2;
+      // symmetric matrix gradient G = [[ga, gb/2], [gb/2, gc]]
+      const float G[4] = {ga_, 0.5f * gb_, 0.5f * gb_, gc_};
+      // dL/dSigma_c = J^T G J ; dL/dJ = 2 G J Sigma_c
+      float GJ[6];
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) GJ[3 * r + c] = G[2 * r] * J[c] + G[2 * r + 1] * J[3 + c];
+      float gSc[9];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) gSc[3 * r + c] = J[r] * GJ[c] + J[3 + r] * GJ[3 + c];
+      float gJ[6];
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          gJ[3 * r + c] = 2.f * (GJ[3 * r] * Sc[c] + GJ[3 * r + 1] * Sc[3 + c] + GJ[3 * r + 2] * Sc[6 + c]);
+      // camera-frame centre: J entries, mu, depth terms
+      float gpc[3];
+      gpc[0] = gJ[2] * (-cam.fx * iz * iz) + gmx * cam.fx * iz;
+      gpc[1] = gJ[5] * (-cam.fy * iz * iz) + gmy * cam.fy * iz;
+      gpc[2] = gJ[0] * (-cam.fx * iz * iz) + gJ[2] * (2.f * cam.fx * X * iz * iz * iz) +
+               gJ[4] * (-cam.fy * iz * iz) + gJ[5] * (2.f * cam.fy * Y * iz * iz * iz) -
+               (gmx * cam.fx * X + gmy * cam.fy * Y) * iz * iz + gz;
+      const float nc[3] = {A[kmin], A[3 + kmin], A[6 + kmin]};
+#pragma unroll
+      for (int r = 0; r < 3; ++r) gpc[r] += gd0 * nc[r];
+      float gnc[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) gnc[r] = gd0 * pc[r] + gn[r];
+      // p_c = W (p - t)  ->  dL/dp = W^T dL/dp_c = R_g dL/dp_c
+#pragma unroll
+      for (int r = 0; r < 3; ++r) gp[r] += cam.R[3 * r] * gpc[0] + cam.R[3 * r + 1] * gpc[1] + cam.R[3 * r + 2] * gpc[2];
+      // Sigma_c = W Sigma W^T -> dL/dSigma = W^T gSc W ; Sigma = R S^2 R^T
+      float gS[9];  // dL/dSigma (world), = R_g gSc R_g^T
+      {
+        float tmp[9];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            tmp[3 * r + c] = cam.R[3 * r] * gSc[c] + cam.R[3 * r + 1] * gSc[3 + c] + cam.R[3 * r + 2] * gSc[6 + c];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            gS[3 * r + c] = tmp[3 * r] * cam.R[3 * c] + tmp[3 * r + 1] * cam.R[3 * c + 1] + tmp[3 * r + 2] * cam.R[3 * c + 2];
+      }
+      // dL/dR += 2 gS R D (D = diag s^2), dL/ds_m += 2 s_m (R^T gS R)_mm
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float gSR = gS[3 * r] * R[c] + gS[3 * r + 1] * R[3 + c] + gS[3 * r + 2] * R[6 + c];
+          gR[3 * r + c] += 2.f * gSR * P.s[c] * P.s[c];
+        }
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        float acc = 0.f;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) acc += R[3 * r + m] * gS[3 * r + c] * R[3 * c + m];
+        gs[m] += 2.f * P.s[m] * acc;
+      }
+      // n_c = W R e_k -> dL/dR[:, k] += W^T dL/dn_c = R_g dL/dn_c
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+        gR[3 * r + kmin] += cam.R[3 * r] * gnc[0] + cam.R[3 * r + 1] * gnc[1] + cam.R[3 * r + 2] * gnc[2];
+    }
+    // R(q) -> unit quaternion -> raw quaternion
+    const float G01 = gR[1], G02 = gR[2], G10 = gR[3], G12 = gR[5], G20 = gR[6], G21 = gR[7];
+    const float G00 = gR[0], G11 = gR[4], G22 = gR[8];
+    float gqn[4];
+    gqn[0] = 2.f * (-qz * G01 + qy * G02 + qz * G10 - qx * G12 - qy * G20 + qx * G21);
+    gqn[1] = 2.f * (qy * G01 + qz * G02 + qy * G10 - 2.f * qx * G11 - qw * G12 + qz * G20 + qw * G21 - 2.f * qx * G22);
+    gqn[2] = 2.f * (-2.f * qy * G00 + qx * G01 + qw * G02 + qx * G10 + qz * G12 - qw * G20 + qz * G21 - 2.f * qy * G22);
+    gqn[3] = 2.f * (-2.f * qz * G00 - qw * G01 + qx * G02 + qw * G10 - 2.f * qz * G11 + qy * G12 + qx * G20 + qy * G21);
+    const float qh[4] = {qw, qx, qy, qz};
+    const float dotq = qh[0] * gqn[0] + qh[1] * gqn[1] + qh[2] * gqn[2] + qh[3] * gqn[3];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) gq[m] = (gqn[m] - qh[m] * dotq) / qn;
+  }
+  if (accumulate) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      gp[r] += g_means[3 * k + r];
+      gs[r] += g_scales[3 * k + r];
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) gq[m] += g_quats[4 * k + m];
+    ga += g_opacity[k];
+    if (!sh)
+#pragma unroll
+      for (int c = 0; c < C; ++c) gc[c] += g_colors[(int64_t)C * k + c];
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    g_means[3 * k + r] = gp[r];
+    g_scales[3 * k + r] = gs[r];
+  }
+#pragma unroll
+  for (int m = 0; m < 4; ++m) g_quats[4 * k + m] = gq[m];
+  g_opacity[k] = ga;
+  if (!sh)
+#pragma unroll
+    for (int c = 0; c < C; ++c) g_colors[(int64_t)C * k + c] = gc[c];
+}
+
+// Most unstable Gaussians of a masked step have no row in any frame (outside every frame's
+// masked tiles).  So each CTA takes kPbRounds rounds of the grid-stride walk over the compact
+// indices at once: a light pass checks them with all their loads in flight, writes the zero
+// gradients of those without a row (unless accumulating) and lists the others in shared
+// memory; then the CTA's threads run the chain rule over that list only.  The rounds stay
+// interleaved over the grid as in a plain grid-stride loop, and when most entries have rows
+// (every Gaussian seen in several keyframes) each thread keeps its own, as that loop would.
+constexpr int kPbRounds = 4;
+
+template <int C>
 __global__ void __launch_bounds__(256) k_project_backward(GaussPtrs g, Work w, Prm prm, int F,
                                                           float *__restrict__ g_means, float *__restrict__ g_scales,
                                                           float *__restrict__ g_quats, float *__restrict__ g_opacity,
                                                           float *__restrict__ g_colors, int accumulate) {
   grid_dep_wait();
-  constexpr int G2 = (C <= 5) ? 16 : 20;
+  __shared__ int s_k[256 * kPbRounds], s_i[256 * kPbRounds];
+  __shared__ int s_n;
   const int64_t nu = (int64_t)w.counters[kNumUnstable];
   const int64_t N = g.n;
+  const bool sh = C == 3 && g.sh_degree > 0;  // k_sh_backward writes the colour rows
   if (blockIdx.x == 0 && threadIdx.x == 0) w.counters[kQBwd] = 0ull;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nu; k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = w.ids[k];
-    GParams P;
-    const bool ok = load_params(g, w.rank, i, P);
-    float gp[3] = {0, 0, 0}, gs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, ga = 0.f, gc[C];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // the grid-stride rounds, grouped evenly: no CTA ends with a short group while others still
+  // run a full one
+  const int64_t rounds = (nu + stride - 1) / stride;
+  const int64_t groups = (rounds + kPbRounds - 1) / kPbRounds;
+  const int64_t per = groups > 0 ? (rounds + groups - 1) / groups : 0;
+  for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x; r0 < nu; r0 += per * stride) {
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    int64_t ii[kPbRounds];
+    unsigned mine = 0u;  // bit u: round u's entry has a row
 #pragma unroll
-    for (int c = 0; c < C; ++c) gc[c] = 0.f;
-    // SH colour: k_sh_backward writes the coefficient gradients and adds the position term
-    const bool sh = C == 3 && g.sh_degree > 0;
-    if (ok) {
-      const float qn = sqrtf(P.q[0] * P.q[0] + P.q[1] * P.q[1] + P.q[2] * P.q[2] + P.q[3] * P.q[3]);
-      const float qw = P.q[0] / qn, qx = P.q[1] / qn, qy = P.q[2] / qn, qz = P.q[3] / qn;
-      float R[9];
-      quat_to_rot(qw, qx, qy, qz, R);
-      const int kmin = argmin3(P.s[0], P.s[1], P.s[2]);
-      float gR[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-      for (int f = 0; f < F; ++f) {
-        if (w.ntiles[(int64_t)f * N + i] == 0u) continue;
-        const DevCam &cam = w.cams[f];
-        const float *row = w.grad2d + ((int64_t)f * N + k) * G2;
-        const float gmx = row[kG2Mu], gmy = row[kG2Mu + 1];
-        const float gA = row[kG2Conic], gB = row[kG2Conic + 1], gCc = row[kG2Conic + 2];
-        ga += row[kG2Alpha];
+    for (int u = 0; u < kPbRounds; ++u) {
+      const int64_t k = r0 + u * stride + threadIdx.x;
+      ii[u] = (u < per && k < nu) ? (int64_t)w.ids[k] : -1;
+    }
 #pragma unroll
-        for (int c = 0; c < C; ++c) gc[c] += row[kG2Col + c];
-
-        const float gd0 = row[g2_d0(C)], gn[3] = {row[g2_nc(C)], row[g2_nc(C) + 1], row[g2_nc(C) + 2]};
-        const float gz = row[g2_z(C)];
-
-        // forward quantities (FP32 recomputation)
-        const float d[3] = {P.p[0] - cam.t[0], P.p[1] - cam.t[1], P.p[2] - cam.t[2]};
-        float pc[3];
+    for (int u = 0; u < kPbRounds; ++u) {
+      const int64_t k = r0 + u * stride + threadIdx.x;
+      if (ii[u] < 0) continue;
+      uint32_t any = 0u;  // every frame's flag is loaded (no early exit), so the loads overlap
+      for (int f = 0; f < F; ++f) any |= w.ntiles[(int64_t)f * N + ii[u]];
+      if (any != 0u) {
+        mine |= 1u << u;
+        const int slot = atomicAdd(&s_n, 1);
+        s_k[slot] = (int)k;
+        s_i[slot] = (int)ii[u];
+      } else if (!accumulate) {
 #pragma unroll
-        for (int r = 0; r < 3; ++r) pc[r] = cam.R[r] * d[0] + cam.R[3 + r] * d[1] + cam.R[6 + r] * d[2];
-        float A[9];
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) A[3 * r + c] = cam.R[r] * R[c] + cam.R[3 + r] * R[3 + c] + cam.R[6 + r] * R[6 + c];
-        const float X = pc[0], Y = pc[1], Z = pc[2], iz = 1.f / Z;
-        const float j00 = cam.fx * iz, j02 = -cam.fx * X * iz * iz, j11 = cam.fy * iz, j12 = -cam.fy * Y * iz * iz;
-        // Sigma_c = A S^2 A^T (camera-frame covariance); cov = J Sigma_c J^T + lowpass I
-        float Sc[9];
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            float acc = 0.f;
-#pragma unroll
-            for (int m = 0; m < 3; ++m) acc += A[3 * r + m] * P.s[m] * P.s[m] * A[3 * c + m];
-            Sc[3 * r + c] = acc;
-          }
-        const float J[6] = {j00, 0.f, j02, 0.f, j11, j12};
-        float JS[6];  // J Sigma_c (2x3)
-#pragma unroll
-        for (int r = 0; r < 2; ++r)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) JS[3 * r + c] = J[3 * r] * Sc[c] + J[3 * r + 1] * Sc[3 + c] + J[3 * r + 2] * Sc[6 + c];
-        const float a = JS[0] * J[0] + JS[1] * J[1] + JS[2] * J[2] + prm.lowpass;
-        const float b = JS[0] * J[3] + JS[1] * J[4] + JS[2] * J[5];
-        const float cc = JS[3] * J[3] + JS[4] * J[4] + JS[5] * J[5] + prm.lowpass;
-        const float det = a * cc - b * b;
-        const float id2 = 1.f / (det * det);
-        // conic (a', b', c') = (c, -b, a) / det  ->  gradient w.r.t. (a, b, c) of Sigma_2D
-        const float ga_ = (-cc * cc * gA + b * cc * gB - b * b * gCc) * id2;
-        const float gb_ = (2.f * b * cc * gA - (a * cc + b * b) * gB + 2.f * a * b * gCc) * id2;
-        const float gc_ = (-b * b * gA + a * b * gB - a * a * gCc) * id2;
-        // symmetric matrix gradient G = [[ga, gb/2], [gb/2, gc]]
-        const float G[4] = {ga_, 0.5f * gb_, 0.5f * gb_, gc_};
-        // dL/dSigma_c = J^T G J ; dL/dJ = 2 G J Sigma_c
-        float GJ[6];
-#pragma unroll
-        for (int r = 0; r < 2; ++r)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) GJ[3 * r + c] = G[2 * r] * J[c] + G[2 * r + 1] * J[3 + c];
-        float gSc[9];
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) gSc[3 * r + c] = J[r] * GJ[c] + J[3 + r] * GJ[3 + c];
-        float gJ[6];
-#pragma unroll
-        for (int r = 0; r < 2; ++r)
-#pragma unroll
-          for (int c = 0; c < 3; ++c)
-            gJ[3 * r + c] = 2.f * (GJ[3 * r] * Sc[c] + GJ[3 * r + 1] * Sc[3 + c] + GJ[3 * r + 2] * Sc[6 + c]);
-        // camera-frame centre: J entries, mu, depth terms
-        float gpc[3];
-        gpc[0] = gJ[2] * (-cam.fx * iz * iz) + gmx * cam.fx * iz;
-        gpc[1] = gJ[5] * (-cam.fy * iz * iz) + gmy * cam.fy * iz;
-        gpc[2] = gJ[0] * (-cam.fx * iz * iz) + gJ[2] * (2.f * cam.fx * X * iz * iz * iz) +
-                 gJ[4] * (-cam.fy * iz * iz) + gJ[5] * (2.f * cam.fy * Y * iz * iz * iz) -
-                 (gmx * cam.fx * X + gmy * cam.fy * Y) * iz * iz + gz;
-        const float nc[3] = {A[kmin], A[3 + kmin], A[6 + kmin]};
-#pragma unroll
-        for (int r = 0; r < 3; ++r) gpc[r] += gd0 * nc[r];
-        float gnc[3];
-#pragma unroll
-        for (int r = 0; r < 3; ++r) gnc[r] = gd0 * pc[r] + gn[r];
-        // p_c = W (p - t)  ->  dL/dp = W^T dL/dp_c = R_g dL/dp_c
-#pragma unroll
-        for (int r = 0; r < 3; ++r) gp[r] += cam.R[3 * r] * gpc[0] + cam.R[3 * r + 1] * gpc[1] + cam.R[3 * r + 2] * gpc[2];
-        // Sigma_c = W Sigma W^T -> dL/dSigma = W^T gSc W ; Sigma = R S^2 R^T
-        float gS[9];  // dL/dSigma (world), = R_g gSc R_g^T
-        {
-          float tmp[9];
-#pragma unroll
-          for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-              tmp[3 * r + c] = cam.R[3 * r] * gSc[c] + cam.R[3 * r + 1] * gSc[3 + c] + cam.R[3 * r + 2] * gSc[6 + c];
-#pragma unroll
-          for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-              gS[3 * r + c] = tmp[3 * r] * cam.R[3 * c] + tmp[3 * r + 1] * cam.R[3 * c + 1] + tmp[3 * r + 2] * cam.R[3 * c + 2];
+        for (int r = 0; r < 3; ++r) {
+          g_means[3 * k + r] = 0.f;
+          g_scales[3 * k + r] = 0.f;
         }
-        // dL/dR += 2 gS R D (D = diag s^2), dL/ds_m += 2 s_m (R^T gS R)_mm
 #pragma unroll
-        for (int r = 0; r < 3; ++r)
+        for (int m = 0; m < 4; ++m) g_quats[4 * k + m] = 0.f;
+        g_opacity[k] = 0.f;
+        if (!sh)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const float gSR = gS[3 * r] * R[c] + gS[3 * r + 1] * R[3 + c] + gS[3 * r + 2] * R[6 + c];
-            gR[3 * r + c] += 2.f * gSR * P.s[c] * P.s[c];
-          }
-#pragma unroll
-        for (int m = 0; m < 3; ++m) {
-          float acc = 0.f;
-#pragma unroll
-          for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) acc += R[3 * r + m] * gS[3 * r + c] * R[3 * c + m];
-          gs[m] += 2.f * P.s[m] * acc;
-        }
-        // n_c = W R e_k -> dL/dR[:, k] += W^T dL/dn_c = R_g dL/dn_c
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-          gR[3 * r + kmin] += cam.R[3 * r] * gnc[0] + cam.R[3 * r + 1] * gnc[1] + cam.R[3 * r + 2] * gnc[2];
+          for (int c = 0; c < C; ++c) g_colors[(int64_t)C * k + c] = 0.f;
       }
-      // R(q) -> unit quaternion -> raw quaternion
-      const float G01 = gR[1], G02 = gR[2], G10 = gR[3], G12 = gR[5], G20 = gR[6], G21 = gR[7];
-      const float G00 = gR[0], G11 = gR[4], G22 = gR[8];
-      float gqn[4];
-      gqn[0] = 2.f * (-qz * G01 + qy * G02 + qz * G10 - qx * G12 - qy * G20 + qx * G21);
-      gqn[1] = 2.f * (qy * G01 + qz * G02 + qy * G10 - 2.f * qx * G11 - qw * G12 + qz * G20 + qw * G21 - 2.f * qx * G22);
-      gqn[2] = 2.f * (-2.f * qy * G00 + qx * G01 + qw * G02 + qx * G10 + qz * G12 - qw * G20 + qz * G21 - 2.f * qy * G22);
-      gqn[3] = 2.f * (-2.f * qz * G00 - qw * G01 + qx * G02 + qw * G10 - 2.f * qz * G11 + qy * G12 + qx * G20 + qy * G21);
-      const float qh[4] = {qw, qx, qy, qz};
-      const float dotq = qh[0] * gqn[0] + qh[1] * gqn[1] + qh[2] * gqn[2] + qh[3] * gqn[3];
-#pragma unroll
-      for (int m = 0; m < 4; ++m) gq[m] = (gqn[m] - qh[m] * dotq) / qn;
     }
-    if (accumulate) {
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        gp[r] += g_means[3 * k + r];
-        gs[r] += g_scales[3 * k + r];
-      }
-#pragma unroll
-      for (int m = 0; m < 4; ++m) gq[m] += g_quats[4 * k + m];
-      ga += g_opacity[k];
-      if (!sh)
-#pragma unroll
-        for (int c = 0; c < C; ++c) gc[c] += g_colors[(int64_t)C * k + c];
+    __syncthreads();
+    const int nv = s_n;
+    if (2 * nv > (int)per * (int)blockDim.x) {
+      // dense (most Gaussians seen): each thread keeps its own entries, as a plain
+      // grid-stride loop would, instead of a list whose last pass leaves most lanes idle
+#pragma unroll 1
+      for (int u = 0; u < kPbRounds; ++u)
+        if ((mine >> u) & 1u)
+          project_backward_one<C>(g, w, prm, F, N, r0 + u * stride + threadIdx.x, ii[u], g_means, g_scales,
+                                  g_quats, g_opacity, g_colors, accumulate);
+    } else {
+      for (int j = threadIdx.x; j < nv; j += blockDim.x)
+        project_backward_one<C>(g, w, prm, F, N, s_k[j], s_i[j], g_means, g_scales, g_quats, g_opacity, g_colors,
+                                accumulate);
     }
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      g_means[3 * k + r] = gp[r];
-      g_scales[3 * k + r] = gs[r];
-    }
-#pragma unroll
-    for (int m = 0; m < 4; ++m) g_quats[4 * k + m] = gq[m];
-    g_opacity[k] = ga;
-    if (!sh)
-#pragma unroll
-      for (int c = 0; c < C; ++c) g_colors[(int64_t)C * k + c] = gc[c];
+    __syncthreads();
   }
 }
 

@@ -106,7 +106,7 @@ struct Work {
   float4 *rec_hot;
   float4 *rec_cold;
   float2 *rec_box;      // [F][N] support half-extents (rx, ry) around mu
-  uint32_t *ntiles;
+  uint32_t *ntiles;     // [F*N] non-zero iff the (frame, Gaussian) entry has a pair in a masked tile
   uint32_t *tile_npix;  // [F*T] masked pixels per tile
   uint32_t *tile_count; // [F*T + 1]
   uint32_t *tile_offset;// [F*T + 1]
