@@ -12,41 +12,49 @@
 namespace rtg {
 
 // --------------------------------------------------------------------------- setup + tile mask
-// One CTA of 2^(tws+ths) threads per (frame, tile) of a grid of 2^tws x 2^ths pixel tiles.
-// Counts the masked in-image pixels of the tile, clears its pair counter and, with
-// `lists`, writes the tile's masked pixels (index within the tile) compacted in raster
-// order: the forward and backward give each 32 of them to one warp.  With `setup`, block 0
-// also publishes the cameras and clears the per-call counters.
+// CTAs of kMaxTilePix threads over the (frame, tile)s of a grid of 2^tws x 2^ths pixel
+// tiles, one thread per pixel: a CTA takes kMaxTilePix / 2^(tws+ths) consecutive tiles (so
+// small tiles do not make thousands of tiny CTAs).  Counts the masked in-image pixels of
+// each tile, clears its pair counter and, with `lists`, writes the tile's masked pixels
+// (index within the tile) compacted in raster order: the forward and backward give each 32
+// of them to one warp.  With `setup`, block 0 also publishes the cameras and clears the
+// per-call counters.
 __global__ void __launch_bounds__(kMaxTilePix) k_tile_mask(FrameSet fs, Work w, const uint8_t *__restrict__ mask,
                                                            int T, int tiles_x, int tws, int ths, int setup,
                                                            int lists, long long nu_preset) {
   grid_dep_wait();
   __shared__ int s_wcnt[kMaxTilePix / 32];
-  const int tile = blockIdx.x;
-  const int f = tile / T, lt = tile - f * T;
-  const DevCam &cam = fs.cam[f];
   if (setup && blockIdx.x == 0) {
     for (int i = threadIdx.x; i < fs.F; i += blockDim.x) w.cams[i] = fs.cam[i];
     const int c = (int)threadIdx.x * kCounterStride;
     if ((int)threadIdx.x < kNumCounterSlots && c != kWinStable)
       w.counters[c] = (c == kNumUnstable && nu_preset >= 0) ? (unsigned long long)nu_preset : 0ull;
   }
+  const int sh = tws + ths;  // log2 pixels per tile
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tile = (int)blockIdx.x * (kMaxTilePix >> sh) + (tid >> sh);
+  const int pix = tid & ((1 << sh) - 1);
+  const int FT = fs.F * T;
+  const bool live = tile < FT;
+  const int f = live ? tile / T : 0, lt = tile - f * T;
+  const DevCam &cam = fs.cam[f];
   const int tx = lt % tiles_x, ty = lt / tiles_x;
-  const int px = (tx << tws) + (tid & ((1 << tws) - 1)), py = (ty << ths) + (tid >> tws);
-  bool in = px < cam.W && py < cam.H;
+  const int px = (tx << tws) + (pix & ((1 << tws) - 1)), py = (ty << ths) + (pix >> tws);
+  bool in = live && px < cam.W && py < cam.H;
   if (in && mask != nullptr) in = mask[((int64_t)f * cam.H + py) * cam.W + px] != 0;
   const unsigned bal = __ballot_sync(0xffffffffu, in);
   if (lane == 0) s_wcnt[wid] = __popc(bal);
   __syncthreads();
+  // warps of this tile: [w0, w0 + wpt) (a tile has at least 8 x 8 pixels, two warps)
+  const int wpt = 1 << (sh - 5), w0 = wid & ~(wpt - 1);
   int before = 0, total = 0;
-  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+  for (int k = w0; k < w0 + wpt; ++k) {
     const int c = s_wcnt[k];
     before += k < wid ? c : 0;
     total += c;
   }
-  if (lists && in) w.px_list[((int64_t)tile << (tws + ths)) + before + __popc(bal & lanemask_lt())] = (uint8_t)tid;
-  if (tid == 0) {
+  if (lists && in) w.px_list[((int64_t)tile << sh) + before + __popc(bal & lanemask_lt())] = (uint8_t)pix;
+  if (live && pix == 0) {
     w.tile_npix[tile] = (uint32_t)total;
     w.tile_count[tile] = 0u;
   }
@@ -473,6 +481,10 @@ __device__ __forceinline__ uint32_t list_len(const Work &w, const uint32_t *extr
   return w.tile_count[t] + ((extra != nullptr && w.tile_npix[t] != 0u) ? extra[t] : 0u);
 }
 
+// Thread t owns tiles [t * per, t * per + per) (per <= kScanSingleMax / 1024): their counts
+// are loaded once, all at once, and kept in registers for the offsets and the queue.
+constexpr int kScanPer = kScanSingleMax / 1024;
+
 __global__ void __launch_bounds__(1024) k_scan_tiles(Work w, int FT, int64_t max_pairs, int gshift,
                                                      const uint32_t *__restrict__ extra) {
   grid_dep_wait();
@@ -481,13 +493,23 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Work w, int FT, int64_t max
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int per = (FT + 1023) / 1024;
   const int b = tid * per, e = min(FT, b + per);
+  uint32_t len[kScanPer], npx[kScanPer];
+#pragma unroll
+  for (int u = 0; u < kScanPer; ++u) {
+    const int t = b + u;
+    const bool in = u < per && t < e;
+    const uint32_t cnt = in ? w.tile_count[t] : 0u;
+    npx[u] = in ? w.tile_npix[t] : 0u;
+    const uint32_t ex = (in && extra != nullptr) ? extra[t] : 0u;
+    len[u] = cnt + (npx[u] != 0u ? ex : 0u);
+  }
   unsigned long long local = 0, npix = 0;
   uint32_t mx = 0;
-  for (int t = b; t < e; ++t) {
-    const uint32_t len = list_len(w, extra, t);
-    local += len;
-    npix += w.tile_npix[t];
-    mx = max(mx, len);
+#pragma unroll
+  for (int u = 0; u < kScanPer; ++u) {
+    local += len[u];
+    npix += npx[u];
+    mx = max(mx, len[u]);
   }
   // inclusive warp scan of `local`
   unsigned long long inc = local;
@@ -496,8 +518,14 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Work w, int FT, int64_t max
     if (lane >= o) inc += v;
   }
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  unsigned long long np = npix;
+  for (int o = 16; o > 0; o >>= 1) np += __shfl_xor_sync(0xffffffffu, np, o);
+  __shared__ unsigned long long s_pix[32];
   if (lane == 31) s_warp[wid] = inc;
-  if (lane == 0) s_wmax[wid] = mx;
+  if (lane == 0) {
+    s_wmax[wid] = mx;
+    s_pix[wid] = np;
+  }
   __syncthreads();
   if (wid == 0) {
     unsigned long long v = s_warp[lane];
@@ -509,27 +537,22 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Work w, int FT, int64_t max
     uint32_t m = s_wmax[lane];
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     s_wmax[lane] = m;
+    unsigned long long pz = s_pix[lane];
+    for (int o = 16; o > 0; o >>= 1) pz += __shfl_xor_sync(0xffffffffu, pz, o);
+    s_pix[lane] = pz;
   }
   __syncthreads();
   unsigned long long run = (wid > 0 ? s_warp[wid - 1] : 0ull) + inc - local;
-  for (int t = b; t < e; ++t) {
-    w.tile_offset[t] = (uint32_t)run;
-    run += list_len(w, extra, t);
+#pragma unroll
+  for (int u = 0; u < kScanPer; ++u) {
+    if (b + u < e) w.tile_offset[b + u] = (uint32_t)run;
+    run += len[u];
   }
-  // total masked pixels
-  unsigned long long np = npix;
-  for (int o = 16; o > 0; o >>= 1) np += __shfl_xor_sync(0xffffffffu, np, o);
-  __syncthreads();
-  if (lane == 0) s_warp[wid] = np;
-  __syncthreads();
-  if (tid == 0) {
-    unsigned long long total_pix = 0;
-    for (int k = 0; k < 32; ++k) total_pix += s_warp[k];
-    // s_warp was overwritten; recompute the pair total from the last offset
-    unsigned long long total = (unsigned long long)w.tile_offset[FT - 1] + list_len(w, extra, FT - 1);
+  if (tid == 1023) {  // the last thread's running offset is the pair total
+    const unsigned long long total = run;
     w.tile_offset[FT] = (uint32_t)total;
     w.counters[kPairs] = total;
-    w.counters[kMaskedPix] = total_pix;
+    w.counters[kMaskedPix] = s_pix[0];
     w.counters[kMaxTilePairs] = s_wmax[0];
     if (total > (unsigned long long)max_pairs || total > 0xffffffffull) {
       w.counters[kSkip] = 1ull;
@@ -541,29 +564,28 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Work w, int FT, int64_t max
   __shared__ uint32_t s_cls[kQueueClasses];
   for (int k = tid; k < kQueueClasses; k += 1024) s_cls[k] = 0u;
   __syncthreads();
-  for (int t = b; t < e; ++t) {
-    const uint32_t np = w.tile_npix[t];
-    if (np != 0u) atomicAdd(&s_cls[queue_class(list_len(w, extra, t))], (np + 31u) >> 5);
-  }
+#pragma unroll
+  for (int u = 0; u < kScanPer; ++u)
+    if (npx[u] != 0u) atomicAdd(&s_cls[queue_class(len[u])], (npx[u] + 31u) >> 5);
   __syncthreads();
   if (tid == 0) {  // start of each class, classes in decreasing cost
-    uint32_t run = 0;
+    uint32_t r = 0;
     for (int k = kQueueClasses - 1; k >= 0; --k) {
       const uint32_t c = s_cls[k];
-      s_cls[k] = run;
-      run += c;
+      s_cls[k] = r;
+      r += c;
     }
-    w.counters[kItems] = run;
+    w.counters[kItems] = r;
     w.counters[kQFwd] = 0ull;
     w.counters[kQBwd] = 0ull;
   }
   __syncthreads();
-  for (int t = b; t < e; ++t) {
-    const uint32_t np = w.tile_npix[t];
-    if (np == 0u) continue;
-    const uint32_t ng = (np + 31u) >> 5;
-    const uint32_t pos = atomicAdd(&s_cls[queue_class(list_len(w, extra, t))], ng);
-    for (uint32_t g = 0; g < ng; ++g) w.items[pos + g] = ((uint32_t)t << 3) | g;
+#pragma unroll
+  for (int u = 0; u < kScanPer; ++u) {
+    if (npx[u] == 0u) continue;
+    const uint32_t ng = (npx[u] + 31u) >> 5;
+    const uint32_t pos = atomicAdd(&s_cls[queue_class(len[u])], ng);
+    for (uint32_t g = 0; g < ng; ++g) w.items[pos + g] = ((uint32_t)(b + u) << 3) | g;
   }
 }
 
@@ -583,8 +605,9 @@ __global__ void __launch_bounds__(256) k_emit(Work w) {
 
 void launch_tile_mask(const FrameSet &fs, const Work &w, const uint8_t *mask, int T, int tiles_x, int tws, int ths,
                       bool setup, bool lists, long long nu_preset, cudaStream_t s) {
-  launch(k_tile_mask, fs.F * T, 1 << (tws + ths), 0, s, fs, w, mask, T, tiles_x, tws, ths, setup ? 1 : 0, lists ? 1 : 0,
-                                                    nu_preset);
+  const int per = kMaxTilePix >> (tws + ths);  // tiles per CTA
+  launch(k_tile_mask, (fs.F * T + per - 1) / per, kMaxTilePix, 0, s, fs, w, mask, T, tiles_x, tws, ths, setup ? 1 : 0,
+         lists ? 1 : 0, nu_preset);
 }
 
 void launch_rank(const uint8_t *unstable, int64_t n, int32_t *block_cnt, int32_t *rank, int32_t *ids,

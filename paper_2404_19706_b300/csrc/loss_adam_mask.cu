@@ -269,7 +269,7 @@ __device__ __forceinline__ float adam_delta(float g, float &m, float &v, float l
                                             float bc1, float bc2_sqrt) {
   m = fmaf(hp.beta1, m, (1.f - hp.beta1) * g);
   v = fmaf(hp.beta2, v, (1.f - hp.beta2) * g * g);
-  return lr * (m * bc1) / (sqrtf(v) * bc2_sqrt + hp.eps);
+  return lr * (m * bc1) * __frcp_rn(fmaf(sqrtf(v), bc2_sqrt, hp.eps));
 }
 
 // Parameter groups of the compact unstable set (means, scales, quats, opacity, colours);
@@ -365,20 +365,23 @@ __global__ void __launch_bounds__(256) k_adam(AdamGroups G, float *__restrict__ 
     for (int r = 0; r < kAdamRounds; ++r) {
       if (cnt[r] == 0) continue;
       const int k = grp[r];
-      const bool log_space = k == 1;  // theta = log s, dL/dtheta = s dL/ds, s <- s exp(-step)
+      const float lr = G.lr[k];
       float xs[4] = {x[r].x, x[r].y, x[r].z, x[r].w}, gs[4] = {g[r].x, g[r].y, g[r].z, g[r].w};
       float ms[4] = {mm[r].x, mm[r].y, mm[r].z, mm[r].w}, vs[4] = {vv[r].x, vv[r].y, vv[r].z, vv[r].w};
+      // the group is the same for (nearly) a whole warp, so these branches do not diverge
+      if (k == 1) {  // theta = log s, dL/dtheta = s dL/ds, s <- s exp(-step)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float gg = log_space ? gs[u] * xs[u] : gs[u];
-        float lr_e = G.lr[k];
-        if (k == 4 && G.dc > 0) {  // position of the value in its colour row
+        for (int u = 0; u < 4; ++u) xs[u] *= expf(-adam_delta(gs[u] * xs[u], ms[u], vs[u], lr, hp, bc1, bc2_sqrt));
+      } else if (k == 4 && G.dc > 0) {  // lr_rest past the first dc values of a colour row
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
           const int64_t j = e[r] + u;
           const int pos = j < (1ll << 32) ? (int)((uint32_t)j % (uint32_t)G.width) : (int)(j % G.width);
-          if (pos >= G.dc) lr_e = G.lr_rest;
+          xs[u] -= adam_delta(gs[u], ms[u], vs[u], pos >= G.dc ? G.lr_rest : lr, hp, bc1, bc2_sqrt);
         }
-        const float step = adam_delta(gg, ms[u], vs[u], lr_e, hp, bc1, bc2_sqrt);
-        xs[u] = log_space ? xs[u] * expf(-step) : xs[u] - step;
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xs[u] -= adam_delta(gs[u], ms[u], vs[u], lr, hp, bc1, bc2_sqrt);
       }
       const bool vec = G.vec[k] != 0;
       st4(G.param[k], e[r], cnt[r], vec, make_float4(xs[0], xs[1], xs[2], xs[3]));
