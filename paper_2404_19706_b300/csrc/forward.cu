@@ -60,10 +60,12 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
   uint32_t last = 0, nfrag = 0, nrec = 0;
   int hit_j = -1;
   bool done = !has;
-  // the records of batch b0 + B are fetched while batch b0 is composited
+  // the records of batch b0 + B, and the indices of batch b0 + 2B, are fetched while batch
+  // b0 is composited, so a batch waits on one L2 round trip rather than index -> record
   float4 r[R][H4];
   float2 bb[R];
   bool valid[R];
+  uint32_t gnext[R];
 #pragma unroll
   for (int u = 0; u < R; ++u) {
     const uint32_t j = (uint32_t)(u * 32 + lane);
@@ -75,6 +77,8 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
       for (int k = 0; k < H4; ++k) r[u][k] = rec[(int64_t)gid * H4 + k];
       bb[u] = box[gid];
     }
+    const uint32_t jn = (uint32_t)(B + u * 32 + lane);
+    gnext[u] = jn < n ? w.sorted[off + jn] : 0u;
   }
   for (uint32_t b0 = 0; b0 < n; b0 += B) {
     if (__all_sync(0xffffffffu, done)) break;
@@ -87,11 +91,13 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
       vn[u] = jn < n;
       bn[u] = make_float2(0.f, 0.f);
       if (vn[u]) {
-        const uint32_t gid = w.sorted[off + jn];
+        const uint32_t gid = gnext[u];
 #pragma unroll
         for (int k = 0; k < H4; ++k) rn[u][k] = rec[(int64_t)gid * H4 + k];
         bn[u] = box[gid];
       }
+      const uint32_t ja = b0 + 2 * B + (uint32_t)(u * 32 + lane);
+      gnext[u] = ja < n ? w.sorted[off + ja] : 0u;
     }
     // keep the records whose support box reaches the warp's pixel box, in list order
     int cnt = 0;
@@ -112,17 +118,11 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
     nrec += (uint32_t)cnt;
     __syncwarp();
     if (!done) {
-      for (int k = 0; k < cnt; ++k) {
-        const float4 r0 = s_rec[0][k], r1 = s_rec[1][k];
-        float dx, dy, t1, t2, g;
-        const float fa = footprint(fpx, fpy, r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, prm.f_max, dx, dy, t1,
-                                   t2, g);
-        if (fa < prm.alpha_min) continue;
+      // composites fragment k (footprint fa) in list order; false once the pixel stops
+      auto blend = [&](int k, float fa) -> bool {
+        if (fa < prm.alpha_min) return true;
         const float Tn = T_ * (1.f - fa);
-        if (Tn < prm.t_eps) {
-          done = true;
-          break;
-        }
+        if (Tn < prm.t_eps) return false;
         const float wgt = fa * T_;
         const float4 c0 = s_rec[2][k];
         float cw[8] = {c0.x, c0.y, c0.z, c0.w, 0.f, 0.f, 0.f, 0.f};
@@ -137,7 +137,23 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
         T_ = Tn;
         last = jj + 1;
         ++nfrag;
+        return true;
+      };
+      auto alpha_of = [&](int k) {
+        const float4 r0 = s_rec[0][k], r1 = s_rec[1][k];
+        float dx, dy, t1, t2, g;
+        return footprint(fpx, fpy, r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, prm.f_max, dx, dy, t1, t2, g);
+      };
+      // two footprints at a time: they are independent, only the blending is in order
+      int k = 0;
+      for (; k + 1 < cnt; k += 2) {
+        const float fa0 = alpha_of(k), fa1 = alpha_of(k + 1);
+        if (!blend(k, fa0) || !blend(k + 1, fa1)) {
+          done = true;
+          break;
+        }
       }
+      if (!done && k < cnt && !blend(k, alpha_of(k))) done = true;
     }
     __syncwarp();
 #pragma unroll
@@ -202,10 +218,11 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
 }
 
 // Schedule 0: CTA `tile` with one warp per 32-pixel group of the tile's pixel list.
-// Three CTAs per SM for the common C = 3, 32-record variant (it fits in 80 registers without
-// spilling); the others keep the registers they need.
+// Registers for the occupancy the tuned schedules use: three CTAs per SM for C <= 4 with
+// 32-record batches (80 registers), two with 64-record batches (128); C = 8 keeps the
+// registers it needs.
 template <int C, int B>
-constexpr int fwd_min_ctas() { return (C <= 4 && B == 32) ? 3 : 1; }
+constexpr int fwd_min_ctas() { return C <= 4 ? (B == 32 ? 3 : 2) : 1; }
 
 template <int C, int B>
 __global__ void __launch_bounds__(kMaxTilePix, fwd_min_ctas<C, B>()) k_forward(Work w, Prm prm, int64_t N, int T,

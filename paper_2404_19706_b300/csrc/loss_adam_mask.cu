@@ -514,15 +514,14 @@ __global__ void __launch_bounds__(kTilePix) k_mask_cover_tiles(Work w, Prm prm, 
     __syncwarp();
     if (in && !cov) {
       const int m = __popc(bal);
-      for (int k = 0; k < m; ++k) {
+      auto alpha_of = [&](int k) {
         const float4 a = s_rec[wid][0][k], c = s_rec[wid][1][k];
         float dx, dy, t1, t2, g;
-        if (footprint(fpx, fpy, a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w, prm.f_max, dx, dy, t1, t2, g) >=
-            prm.alpha_min) {
-          cov = true;
-          break;
-        }
-      }
+        return footprint(fpx, fpy, a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w, prm.f_max, dx, dy, t1, t2, g);
+      };
+      // two independent footprints per step
+      for (int k = 0; k < m && !cov; k += 2)
+        cov = alpha_of(k) >= prm.alpha_min || (k + 1 < m && alpha_of(k + 1) >= prm.alpha_min);
     }
     __syncwarp();
     r0 = n0;
