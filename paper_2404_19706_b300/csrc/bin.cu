@@ -186,12 +186,18 @@ __device__ __forceinline__ int warp_rect_item(const WarpRects &r, int it, int &o
 }
 
 // Tiles with masked pixels over the warp's rectangles: the warp total (in every lane); `vis`
-// gets a bit per lane whose rectangle holds at least one.
+// gets a bit per lane whose rectangle holds at least one.  all_on: every tile of every
+// rectangle has pixels (a grid without a mask, rectangles clamped to the image), so the
+// total is the area and nothing is loaded.
 __device__ __forceinline__ uint32_t warp_count_rects(const uint32_t *__restrict__ npix, const WarpRects &r,
-                                                     unsigned &vis) {
+                                                     unsigned &vis, bool all_on = false) {
   const int lane = threadIdx.x & 31;
   uint32_t total = 0;
   vis = 0u;
+  if (all_on) {
+    vis = __ballot_sync(0xffffffffu, __shfl_down_sync(0xffffffffu, r.P, 1) > r.P || (lane == 31 && r.A > r.P));
+    return (uint32_t)r.A;
+  }
   for (int b0 = 0; b0 < r.A; b0 += 32 * kWalkRounds) {
     uint32_t v[kWalkRounds];
     int own[kWalkRounds];
@@ -218,7 +224,8 @@ __device__ __forceinline__ uint32_t warp_count_rects(const uint32_t *__restrict_
 // tiles, and the peers take consecutive slots.
 __device__ __forceinline__ void warp_stage_rects(uint4 *__restrict__ stage, const uint32_t *__restrict__ npix,
                                                  uint32_t *__restrict__ tcount, const WarpRects &r, uint32_t klo,
-                                                 uint32_t khi, unsigned long long first, int64_t max_pairs) {
+                                                 uint32_t khi, unsigned long long first, int64_t max_pairs,
+                                                 bool all_on = false) {
   const int lane = threadIdx.x & 31;
   unsigned long long pos = first;
   for (int b0 = 0; b0 < r.A; b0 += 32 * kWalkRounds) {
@@ -228,7 +235,7 @@ __device__ __forceinline__ void warp_stage_rects(uint4 *__restrict__ stage, cons
     for (int u = 0; u < kWalkRounds; ++u) {
       const int it = b0 + u * 32 + lane;
       t[u] = warp_rect_item(r, min(it, r.A - 1), own[u]);
-      on[u] = it < r.A && npix[t[u]] != 0u;
+      on[u] = it < r.A && (all_on || npix[t[u]] != 0u);
     }
     unsigned peers[kWalkRounds];
     uint32_t base[kWalkRounds];
@@ -371,8 +378,11 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
     }
     const int tiles_x = (k < ncand) ? (kMode == kProjForward ? w.cams[f].tiles_x : w.cams[f].mtiles_x) : 0;
     const WarpRects wr = warp_rects(tiles_x, f * T, tx0, ty0, tx1, ty1);
+    // the mask passes bin into the 16 x 16 grid of a call without a mask: every tile of a
+    // (clamped) rectangle has pixels
+    constexpr bool all_on = kMode == kProjFused || kMode == kProjMask;
     unsigned vis = 0u;
-    const uint32_t wtotal = warp_count_rects(w.tile_npix, wr, vis);
+    const uint32_t wtotal = warp_count_rects(w.tile_npix, wr, vis, all_on);
     const bool visible = (vis >> (threadIdx.x & 31)) & 1u;
     if (kMode == kProjWindow) {  // one atomic per block appends the projected entries
       const unsigned long long slot = block_reserve(w.counters + kWinStable, ok ? 1u : 0u, s_w, &s_base);
@@ -410,7 +420,7 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
     if (k < ncand) w.ntiles[e] = (kMode == kProjFused || kMode == kProjWindow) ? (ok ? 1u : 0u) : (visible ? 1u : 0u);
     // the records are written; now the pairs
     warp_stage_rects(w.stage, w.tile_npix, w.tile_count, wr, (uint32_t)i, ok ? __float_as_uint(o.Z) : 0u, first,
-                     max_pairs);
+                     max_pairs, all_on);
   }
 }
 
