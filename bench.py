@@ -382,13 +382,20 @@ def roofline_of(per_launch, alg, tuning=None, workload=None, extra_kinds=()):
             "alg_bytes_per_launch": int(alg[dom]), "ms_per_launch": round(per_launch[dom], 5)}, pk
 
 
-def kernels_per_step(stats, per_frame_calls=1):
-    """Kernels one masked step launches: the fused masked forward (11, plus a render-grid
-    tile-mask pass when the render tile is not 16 x 16) and loss finalize per forward call,
-    backward 2 per call, then Adam 1 (the renderer reads the optimiser's compact arrays, so
-    nothing is scattered back during the window)."""
-    extra = 0 if (stats["tile_w"], stats["tile_h"]) == (16, 16) else 1
-    return per_frame_calls * (11 + extra + 1 + 2) + 1
+def kernels_per_step(stats, F, H, W, schedule, per_frame_calls=1):
+    """Kernels one masked step launches.  Per forward call of F frames: tile mask, cull,
+    project, the mask grid's scan (1 kernel, 3 when its tiles outnumber one scan block), emit,
+    cover, a render-grid tile-mask pass when the render tile is not 16 x 16, bin, the render
+    grid's scan, emit, sort and composite, plus the loss finalize unless the persistent
+    schedule's forward does it; backward 2 per call; then Adam 1 (the renderer reads the
+    optimiser's compact arrays, so nothing is scattered back during the window)."""
+    tw, th = stats["tile_w"], stats["tile_h"]
+    scan = lambda ft: 1 if ft <= 8192 else 3
+    ft_mask = F * ((W + 15) // 16) * ((H + 15) // 16)
+    ft_render = F * ((W + tw - 1) // tw) * ((H + th - 1) // th)
+    extra = 0 if (tw, th) == (16, 16) else 1
+    fwd = 3 + scan(ft_mask) + 2 + extra + 1 + scan(ft_render) + 3 + (0 if schedule == 1 else 1)
+    return per_frame_calls * (fwd + 2) + 1
 
 
 def pipelined_e2e(step_fn, dev_inputs, result, warmup, steps):
@@ -597,7 +604,9 @@ def run_ours(args):
             "roofline": roofline,
             "e2e": {"value": round(world * 1e3 / e2e_step, 2), "unit": "iter/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "pipelined": "next step's upload overlaps this step's compute"},
-            "gpu_launches": (kernels_per_step(stats) + (2 if sh else 0)) * args.steps,
+            # SH: the coefficient backward, and the regulariser's reduce and gradient kernels
+            "gpu_launches": (kernels_per_step(stats, 1, H, W, ctx.get_tuning().schedule) + (3 if sh else 0)) *
+                            args.steps,
             "clocks": clk,
         }
         if world == 1 and not args.no_cpu_baseline:
@@ -802,7 +811,8 @@ def run_keyframes(args, kw):
         config["per_frame"] = {"value": round(F * 1e3 / msp, 2), "unit": "frames/s", "ms_per_step": round(msp, 4),
                                "tuning": ctx1.get_tuning().as_dict(),
                                "autotune": tuned_p.summary() if tuned_p is not None else fixed,
-                               "gpu_launches_per_step": kernels_per_step(results["per_frame"]["stats"], F)}
+                               "gpu_launches_per_step": kernels_per_step(results["per_frame"]["stats"], 1, H, W,
+                                                                         ctx1.get_tuning().schedule, F)}
         config["batched_over_per_frame"] = round(msp / msb, 3)
     config.update({"l2": "256 MB buffer written before every step, outside the timed spans",
                    "timing": "each arm replays one CUDA graph of its whole step (F-frame calls, or F single-frame "
@@ -820,7 +830,7 @@ def run_keyframes(args, kw):
         "e2e": {"value": round(F * 1e3 / e2e_step, 2) if per_frame_metric else round(1e3 / e2e_step, 3),
                 "unit": "frames/s" if per_frame_metric else "iter/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "pipelined": "next step's upload overlaps this step's compute"},
-        "gpu_launches": kernels_per_step(sb) * args.steps,
+        "gpu_launches": kernels_per_step(sb, F, H, W, ctx.get_tuning().schedule) * args.steps,
         "clocks": results["batched"]["clocks"].summary(),
     }
 

@@ -135,7 +135,7 @@ struct Layout {
   size_t cams, counters, rank, ids, block_cnt, cand, rec_hot, rec_cold, rec_box, ntiles, tile_npix, tile_count, tile_offset,
       tile_cursor, keys, keys_alt, stage, sorted, px_T, px_last, px_hit, grad2d, loss_part, loss_scal, loss_done, tile_loss,
       px_list, items, scand, win_scount, win_soff, win_skeys, scan_part, scan_hist, sel_keys, sel_small, sel_state,
-      sel_tie, gauss_bits, total;
+      sel_tie, gauss_bits, loss_acc, total;
 };
 
 bool capacity_ok(const rtg_capacity *c) {
@@ -207,6 +207,7 @@ Layout layout_of(const rtg_capacity *c) {
   L.sel_state = take(Fm * 2 * 4);
   L.sel_tie = take(Fm * sel_blocks * 4);
   L.gauss_bits = take(N * 4);
+  L.loss_acc = take(4 * 8);
   L.total = o;
   return L;
 }
@@ -472,6 +473,7 @@ rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap) {
   w.loss_part = (float *)(b + L.loss_part);
   w.loss_scal = (float *)(b + L.loss_scal);
   w.loss_done = (uint32_t *)(b + L.loss_done);
+  w.loss_acc = (double *)(b + L.loss_acc);
   w.tile_loss = (float *)(b + L.tile_loss);
   w.px_list = (uint8_t *)(b + L.px_list);
   w.items = (uint32_t *)(b + L.items);
@@ -501,6 +503,7 @@ rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap) {
   cudaMemset(ctx->slab + L.counters, 0, kNumCounters * sizeof(unsigned long long));
   ctx->win.open = false;
   cudaMemset(ctx->slab + L.loss_done, 0, 4);
+  cudaMemset(ctx->slab + L.loss_acc, 0, 4 * 8);
   cudaMemset(ctx->slab + L.gauss_bits, 0, (size_t)(cap->max_gaussians > 0 ? cap->max_gaussians : 1) * 4);
   init_sort_attributes();
   if (cudaDeviceSynchronize() != cudaSuccess) {
@@ -699,9 +702,12 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
   }
   {
     ProfScope ps(ctx, kPForward, s);
-    launch_forward(gp.C, w, P, n, F, T, tn, color, depth, alpha, index_map, tcolor, tdepth, s);
+    // the persistent schedule finalizes the fused L1 in its last CTA
+    const bool fused_loss = tcolor != nullptr && tn.schedule == 1;
+    launch_forward(gp.C, w, P, n, F, T, tn, color, depth, alpha, index_map, tcolor, tdepth,
+                   fused_loss ? loss_out : nullptr, w_c, w_d, s);
   }
-  if (tcolor != nullptr) {
+  if (tcolor != nullptr && tn.schedule != 1) {
     ProfScope ps(ctx, kPL1Loss, s);
     launch_loss_finalize(w, FT, tn.gshift(), gp.C, w_c, w_d, loss_out, s);
   }

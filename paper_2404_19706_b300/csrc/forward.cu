@@ -21,13 +21,16 @@ struct FwdOut {
   float *color, *depth, *alpha;
   int32_t *index_map;
   const float *tcolor, *tdepth;  // fused L1 targets (nullptr: not fused)
+  float *loss_out;               // non-null: the persistent forward finalizes the L1 loss
+  float w_c, w_d;
 };
 
 // Renders the pixels of group `grp` (32 consecutive entries of the tile's pixel list) of
 // render tile `tile`.  Called by a whole warp; s_rec / s_j are the warp's own staging.
 template <int C, int B>
 __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int64_t N, int T, int tile, int grp,
-                                              float4 (*s_rec)[B], uint32_t *s_j, const FwdOut &out) {
+                                              float4 (*s_rec)[B], uint32_t *s_j, const FwdOut &out,
+                                              double *s_loss = nullptr) {
   constexpr int H4 = (C <= 4) ? 3 : 4;
   constexpr int R = B / 32;  // records per lane per batch
   const int lane = threadIdx.x & 31;
@@ -209,6 +212,11 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
       lp[0] = lc;
       lp[1] = ld;
       lp[2] = nd;
+      if (s_loss != nullptr) {  // the CTA's FP64 sums: their order (the queue's) does not show
+        atomicAdd(s_loss + 0, (double)lc);
+        atomicAdd(s_loss + 1, (double)ld);
+        atomicAdd(s_loss + 2, (double)nd);
+      }
     }
   }
   // fragment and walked-record counters: one atomic each per warp
@@ -247,17 +255,46 @@ __global__ void __launch_bounds__(256, fwd_min_ctas<C, B>()) k_forward_queue(Wor
   constexpr int H4 = (C <= 4) ? 3 : 4;
   __shared__ float4 s_rec[8][H4][B];
   __shared__ uint32_t s_j[8][B];
+  __shared__ double s_loss[3];
   if (w.counters[kSkip] != 0ull) return;
+  if (threadIdx.x < 3) s_loss[threadIdx.x] = 0.0;
+  __syncthreads();
   const uint32_t nitems = (uint32_t)w.counters[kItems];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t nwarps = gridDim.x * 8u;
   uint32_t it = blockIdx.x * 8u + (uint32_t)wid;
   while (it < nitems) {
     const uint32_t item = w.items[it];
-    forward_group<C, B>(w, prm, N, T, (int)(item >> 3), (int)(item & 7u), s_rec[wid], s_j[wid], out);
+    forward_group<C, B>(w, prm, N, T, (int)(item >> 3), (int)(item & 7u), s_rec[wid], s_j[wid], out,
+                        out.loss_out != nullptr ? s_loss : nullptr);
     uint32_t nx = 0;
     if (lane == 0) nx = nwarps + (uint32_t)atomicAdd(w.counters + kQFwd, 1ull);
     it = __shfl_sync(0xffffffffu, nx, 0);
+  }
+  if (out.loss_out != nullptr) {  // the last CTA to finish finalizes the L1 loss (Eq. 7)
+    __shared__ bool s_last;
+    __syncthreads();
+    if (threadIdx.x < 3) atomicAdd(w.loss_acc + threadIdx.x, s_loss[threadIdx.x]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(w.loss_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+      __threadfence();
+      const double sc = __ldcg(w.loss_acc + 0), sd = __ldcg(w.loss_acc + 1), nd = __ldcg(w.loss_acc + 2);
+      const float np = (float)w.counters[kMaskedPix];
+      const float Lc = np > 0.f ? (float)sc / (np * (float)C) : 0.f;
+      const float Ld = nd > 0.0 ? (float)(sd / nd) : 0.f;
+      out.loss_out[0] = out.w_c * Lc + out.w_d * Ld;
+      out.loss_out[1] = Lc;
+      out.loss_out[2] = Ld;
+      w.loss_scal[4] = np > 0.f ? out.w_c / (np * (float)C) : 0.f;
+      w.loss_scal[5] = nd > 0.0 ? out.w_d / (float)nd : 0.f;
+      w.loss_acc[0] = 0.0;
+      w.loss_acc[1] = 0.0;
+      w.loss_acc[2] = 0.0;
+      *w.loss_done = 0u;
+    }
   }
 }
 
@@ -272,8 +309,9 @@ static void launch_forward_cb(const Work &w, const Prm &prm, int64_t N, int F, i
 
 void launch_forward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn, float *color,
                     float *depth, float *alpha, int32_t *index_map, const float *tcolor, const float *tdepth,
-                    cudaStream_t s) {
-  const FwdOut out{color, depth, alpha, index_map, tcolor, tdepth};
+                    float *loss_out, float w_c, float w_d, cudaStream_t s) {
+  const FwdOut out{color, depth, alpha, index_map, tcolor, tdepth,
+                   (tn.schedule == 1 && tcolor != nullptr) ? loss_out : nullptr, w_c, w_d};
   if (C == 3) {
     if (tn.batch == 64) launch_forward_cb<3, 64>(w, prm, N, F, T, tn, out, s);
     else launch_forward_cb<3, 32>(w, prm, N, F, T, tn, out, s);

@@ -167,9 +167,11 @@ void launch_sort_tiles(const Work &w, int FT, int bits, int rank_max, const Stab
                        unsigned long long *keys_out, cudaStream_t s);
 void init_sort_attributes();
 // forward.cu
+// loss_out != nullptr (persistent schedule with fused targets): the forward also finalizes
+// the L1 loss (loss_out[0..2] and the gradient scales), as launch_loss_finalize would.
 void launch_forward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn, float *color,
                     float *depth, float *alpha, int32_t *index_map, const float *tcolor, const float *tdepth,
-                    cudaStream_t s);
+                    float *loss_out, float w_c, float w_d, cudaStream_t s);
 // backward.cu
 void launch_backward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn,
                      const float *dL_dcolor, const float *dL_ddepth, const L1Fused &l1, cudaStream_t s);

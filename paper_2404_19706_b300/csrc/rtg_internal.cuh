@@ -127,6 +127,8 @@ struct Work {
   float *tile_loss;     // [groups][4] per-(tile, 32-pixel group) fused L1 partials (colour, depth, depth count)
   float *loss_scal;     // [4]: L, Lc, Ld, (unused); [4..5] gradient scales
   uint32_t *loss_done;
+  double *loss_acc;     // [4] FP64 sums of the persistent forward's fused L1 (colour, depth, depth
+                        // count); the CTA that finalizes the loss returns them to zero
   uint32_t *status;     // host-mapped status word (device pointer)
 };
 
