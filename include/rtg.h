@@ -65,8 +65,8 @@ typedef struct {
       tile_discard_frac;
 } rtg_render_params;
 
-/* Gaussian arrays (Section 3.1: "all parameters are stored in a flat array indexed
- * by the Gaussian index i").  Structure-of-arrays, float32, device pointers:
+/* Gaussian arrays (Section 3.1 keeps every parameter in flat arrays addressed by the
+ * Gaussian's index).  Structure-of-arrays, float32, device pointers:
  * means [n,3], scales [n,3], quats [n,4], opacity [n], colors [n,channels],
  * unstable [n] (uint8, non-zero = unstable, Section 3.2 state).
  * Optional compact overrides u_*: when u_means is non-NULL, the parameters of the

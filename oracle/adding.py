@@ -19,7 +19,7 @@ Readings (the paragraph leaves them open):
     position for a new Gaussian);
   - |C_hat - C| is the mean absolute difference over the C channels (as in the colour
     loss), tested as sum_c |C_hat_c - C_c| > C * delta_c, the sum in channel order;
-  - "uniformly sample 5%": every pixel of M_s or M_c is kept independently with
+  - the 5% uniform sample: every pixel of M_s or M_c is kept independently with
     probability 5%, from a counter-based draw: SplitMix64 (Steele, Lea and Flood, 2014)
     seeded with `seed`, output number f * H * W + p for pixel p of frame f; the top 24
     bits u are compared with floor(rate * 2^24): kept iff u is below it;

@@ -21,11 +21,13 @@ Readings of points the paper leaves open (all carried by ``Settings``):
   * f_i(u) = min(f_max, alpha_i * exp(-0.5 d^T Sigma_2D^-1 d)), d = u - mu, with a
     low-pass dilation Sigma_2D = J W Sigma W^T J^T + lowpass * I (the 3DGS convention
     Eq. 2 cites); a fragment contributes iff f >= alpha_min; no background colour.
-  * "alpha along the ray > delta_alpha" (Section 3.1) uses that same f value.
-  * "<n, r> < 60 degrees" is the angle between lines: the plane branch is taken iff
-    |n.r| / |r| >= cos(60 deg) = 0.5 (equality included).
+  * the hit test of Section 3.1 (the opacity met along the ray above delta_alpha) uses
+    that same f value.
+  * the 60-degree limit on the angle of normal and ray (Section 3.1) is an angle between
+    lines: the plane branch is taken iff |n.r| / |r| >= cos(60 deg) = 0.5 (equality
+    included).
   * the disc normal is the axis of the smallest scale, lowest index on ties
-    (Section 3.1: "the direction of the smallest eigenvector").
+    (Section 3.1 takes the eigenvector of the smallest eigenvalue as the normal).
   * a Gaussian is culled if any parameter is not finite, if its camera depth is
     <= near_z, or if |X/Z| > guard_band * (W/2)/fx or |Y/Z| > guard_band * (H/2)/fy.
   * only processed fragments are depth candidates (colour and depth stop together).

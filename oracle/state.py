@@ -12,7 +12,7 @@
     stable; unstable with k - t_i > delta_t -> removed.
 
 Readings (the paragraphs leave them open):
-  - "the colour is updated": in an optimisation iteration, the Gaussian's colour gradient
+  - an update of the colour (the count's trigger): in an optimisation iteration, the Gaussian's colour gradient
     is non-zero in some channel (it was rendered on the iteration's pixels);
   - fusion uses float32 arithmetic: w = float(eta' - eta) / float(eta'), then
     (1 - w) * a + w * b rounded per operation, applied to every stored parameter

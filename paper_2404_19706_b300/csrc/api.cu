@@ -388,7 +388,7 @@ rtg_status build_window_lists(rtg_ctx *ctx) {
   launch_scan_tiles(w, FT, ctx->cap.max_pairs, -1, nullptr, s);
   launch_emit(w, s);
   launch_sort_tiles(w, FT, tn.sort_bits, tn.sort_rank_max, StableLists{nullptr, nullptr, nullptr}, ctx->win_skeys,
-                    s);
+                    tn.tws + tn.ths <= 6, s);
   cudaMemcpyAsync(ctx->win_scount, w.tile_count, (size_t)FT * 4, cudaMemcpyDeviceToDevice, s);
   cudaMemcpyAsync(ctx->win_soff, w.tile_offset, (size_t)FT * 4, cudaMemcpyDeviceToDevice, s);
   if ((st = check_launch(ctx, "window lists")) != RTG_OK) return st;
@@ -698,7 +698,7 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
   }
   {
     ProfScope ps(ctx, kPSortTiles, s);
-    launch_sort_tiles(w, FT, tn.sort_bits, tn.sort_rank_max, sl, nullptr, s);
+    launch_sort_tiles(w, FT, tn.sort_bits, tn.sort_rank_max, sl, nullptr, tn.tws + tn.ths <= 6, s);
   }
   {
     ProfScope ps(ctx, kPForward, s);

@@ -1,5 +1,5 @@
-// Backward pass of the masked render (Section 3.1: "the depth ... is linearly computed
-// from the position and rotation of the Gaussian ... fully differentiable"; Section 3.2:
+// Backward pass of the masked render (Section 3.1: the depth is a linear function of the
+// Gaussian's position and rotation, so the whole render is differentiable; Section 3.2:
 // only the unstable Gaussians are optimised).
 //
 // k_backward replays each masked pixel's composited fragments back to front, recovering

@@ -9,6 +9,7 @@ constexpr int kScanBlock = 1024;   // threads per block of the unstable-index sc
 constexpr int kSortThreads = 256;  // threads per tile-sort CTA
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortCap = 2048;     // keys a tile-sort CTA sorts entirely in shared memory
+constexpr int kSortCapSmall = 512; // ... in the variant for tiles of at most 64 pixels
 constexpr int kLossBlocks = 296;   // 2 x 148 SMs
 constexpr int kScanSingleMax = 8192;   // tiles up to which one CTA scans them all
 constexpr int kScanBlockTiles = 4096;  // tiles per CTA of the multi-block scan (4 per thread)
@@ -163,8 +164,9 @@ struct StableLists {
   const uint32_t *count;
 };
 // keys_out != nullptr: write each tile's sorted keys there instead of the index lists.
+// small: the tiles have at most 64 pixels (short lists; a variant with smaller buffers).
 void launch_sort_tiles(const Work &w, int FT, int bits, int rank_max, const StableLists &sl,
-                       unsigned long long *keys_out, cudaStream_t s);
+                       unsigned long long *keys_out, bool small, cudaStream_t s);
 void init_sort_attributes();
 // forward.cu
 // loss_out != nullptr (persistent schedule with fused targets): the forward also finalizes

@@ -8,18 +8,19 @@
 // stays stable.  A Gaussian enters a tile at most once, so the keys of a bucket are
 // distinct, and buckets up to a tuned length are ordered by ranking instead: each key's
 // position is the number of smaller keys.  The output is the list of Gaussian indices per
-// tile in front-to-back order (the "key that combines view space depth and tile ID",
-// Supplement B).
+// tile in front-to-back order (Supplement B sorts by a key made of the tile and the
+// view-space depth).
 #include "kernels.cuh"
 
 namespace rtg {
 
 namespace {
 
+template <int kCap>
 struct SortSmem {
-  unsigned long long a[kSortCap];
-  unsigned long long b[kSortCap];
-  uint16_t lrank[kSortCap];
+  unsigned long long a[kCap];
+  unsigned long long b[kCap];
+  uint16_t lrank[kCap];
   uint32_t cnt[kSortWarps * 256];  // [warp][digit], 2^kBits digits used
   uint32_t tot[256];
   uint32_t base[256];
@@ -32,7 +33,8 @@ __device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned long long v,
 }
 
 // OR and AND over the keys src[0..n) (global or shared), block-wide.
-__device__ void varying_bits(const unsigned long long *src, uint32_t n, SortSmem &s, unsigned long long &vary) {
+template <class S>
+__device__ void varying_bits(const unsigned long long *src, uint32_t n, S &s, unsigned long long &vary) {
   unsigned long long o = 0ull, a = ~0ull;
   for (uint32_t j = threadIdx.x; j < n; j += kSortThreads) {
     const unsigned long long k = src[j];
@@ -59,14 +61,14 @@ __device__ void varying_bits(const unsigned long long *src, uint32_t n, SortSmem
   __syncthreads();
 }
 
-// Stable ranking of m <= kSortCap shared-memory keys by the kBits-bit digit at `shift`:
+// Stable ranking of m <= kCap shared-memory keys by the kBits-bit digit at `shift`:
 // warp w owns a contiguous chunk; within it, lanes with equal digits are grouped with
 // match.any and ranked by lane order, chunk by chunk.  Afterwards
 //   lrank[j]     rank of key j among equal digits of its warp chunk,
 //   cnt[w][d]    number of digit-d keys in the chunks of warps before w,
 //   tot[d]       number of digit-d keys.
-template <int kBits>
-__device__ void rank_digits(const unsigned long long *src, int m, int shift, SortSmem &s) {
+template <int kBits, class S>
+__device__ void rank_digits(const unsigned long long *src, int m, int shift, S &s) {
   constexpr int kRadix = 1 << kBits;
   constexpr unsigned long long kMask = (unsigned long long)(kRadix - 1);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -104,8 +106,8 @@ __device__ void rank_digits(const unsigned long long *src, int m, int shift, Sor
 }
 
 // Exclusive scan of kRadix <= 256 values by 256 threads (value of thread d is in[d]).
-template <int kRadix>
-__device__ void scan_digits(const uint32_t *in, uint32_t *out, SortSmem &s) {
+template <int kRadix, class S>
+__device__ void scan_digits(const uint32_t *in, uint32_t *out, S &s) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t v = (int)threadIdx.x < kRadix ? in[threadIdx.x] : 0u;
   uint32_t inc = v;
@@ -122,9 +124,9 @@ __device__ void scan_digits(const uint32_t *in, uint32_t *out, SortSmem &s) {
   __syncthreads();
 }
 
-template <int kBits>
+template <int kBits, class S>
 __device__ __forceinline__ void scatter_chunk(const unsigned long long *src, int m, int shift, const uint32_t *base,
-                                              unsigned long long *dst, SortSmem &s) {
+                                              unsigned long long *dst, S &s) {
   constexpr int kRadix = 1 << kBits;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int per = (((m + kSortWarps - 1) / kSortWarps) + 31) & ~31;
@@ -162,7 +164,7 @@ __device__ __forceinline__ void put(const Work &w, unsigned long long *keys_out,
 // the bucket holds the unstable pairs only and the tile's list is the merge of the sorted
 // bucket with the cached, sorted stable keys of the tile: a key's position is its index in
 // its own list plus the number of smaller keys in the other (all keys are distinct).
-template <int kBits>
+template <int kBits, int kCap>
 __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(Work w, int rank_max, StableLists sl,
                                                              unsigned long long *keys_out) {
   grid_dep_wait();
@@ -170,7 +172,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(Work w, int rank_ma
   constexpr unsigned long long kMask = (unsigned long long)(kRadix - 1);
   if (w.counters[kSkip] != 0ull) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  SortSmem &s = *reinterpret_cast<SortSmem *>(smem_raw);
+  SortSmem<kCap> &s = *reinterpret_cast<SortSmem<kCap> *>(smem_raw);
   const int tile = blockIdx.x;
   const uint32_t off = w.tile_offset[tile];
   const uint32_t n = w.tile_offset[tile + 1] - off;
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(Work w, int rank_ma
   const unsigned long long *sorted_b = nullptr;                      // the sorted bucket
   if (nb == 0) {
     // nothing to sort
-  } else if (nb <= (uint32_t)rank_max) {  // distinct keys: position = number of smaller keys
+  } else if (nb <= (uint32_t)(rank_max < kCap ? rank_max : kCap)) {  // distinct keys: position = number of smaller keys
     for (uint32_t j = threadIdx.x; j < nb; j += kSortThreads) s.a[j] = w.keys[off + j];
     __syncthreads();
     for (uint32_t j = threadIdx.x; j < nb; j += kSortThreads) {
@@ -191,7 +193,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(Work w, int rank_ma
     }
     __syncthreads();
     sorted_b = s.b;
-  } else if (nb <= (uint32_t)kSortCap) {
+  } else if (nb <= (uint32_t)kCap) {
     for (uint32_t j = threadIdx.x; j < nb; j += kSortThreads) s.a[j] = w.keys[off + j];
     __syncthreads();
     unsigned long long vary;
@@ -221,8 +223,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(Work w, int rank_ma
         atomicAdd(&s.tot[(unsigned)((src[j] >> shift) & kMask)], 1u);
       __syncthreads();
       scan_digits<kRadix>(s.tot, s.run, s);
-      for (uint32_t c0 = 0; c0 < nb; c0 += kSortCap) {
-        const int m = (int)min((uint32_t)kSortCap, nb - c0);
+      for (uint32_t c0 = 0; c0 < nb; c0 += kCap) {
+        const int m = (int)min((uint32_t)kCap, nb - c0);
         for (int j = threadIdx.x; j < m; j += kSortThreads) s.a[j] = src[c0 + j];
         __syncthreads();
         rank_digits<kBits>(s.a, m, shift, s);
@@ -245,7 +247,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(Work w, int rank_ma
   // merge with the tile's cached stable keys (staged in the free shared buffer if they fit)
   const unsigned long long *sk = sl.keys + sl.off[tile];
   unsigned long long *freebuf = sorted_b == s.a ? s.b : s.a;
-  if (ns <= (uint32_t)kSortCap) {
+  if (ns <= (uint32_t)kCap) {
     for (uint32_t j = threadIdx.x; j < ns; j += kSortThreads) freebuf[j] = sk[j];
     __syncthreads();
     sk = freebuf;
@@ -261,16 +263,29 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(Work w, int rank_ma
 }
 
 void init_sort_attributes() {
-  cudaFuncSetAttribute(k_sort_tiles<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SortSmem));
-  cudaFuncSetAttribute(k_sort_tiles<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SortSmem));
+  cudaFuncSetAttribute(k_sort_tiles<8, kSortCap>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(SortSmem<kSortCap>));
+  cudaFuncSetAttribute(k_sort_tiles<4, kSortCap>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(SortSmem<kSortCap>));
 }
 
 void launch_sort_tiles(const Work &w, int FT, int bits, int rank_max, const StableLists &sl,
-                       unsigned long long *keys_out, cudaStream_t s) {
-  if (bits == 4)
-    launch(k_sort_tiles<4>, FT, kSortThreads, sizeof(SortSmem), s, w, rank_max, sl, keys_out);
-  else
-    launch(k_sort_tiles<8>, FT, kSortThreads, sizeof(SortSmem), s, w, rank_max, sl, keys_out);
+                       unsigned long long *keys_out, bool small, cudaStream_t s) {
+  // Tiles of at most 64 pixels have short lists: the variant whose buffers hold kSortCapSmall
+  // keys fits twice as many CTAs on an SM (longer buckets take the chunked global-memory
+  // path, longer stable lists are searched in place).
+  if (small) {
+    if (bits == 4)
+      launch(k_sort_tiles<4, kSortCapSmall>, FT, kSortThreads, sizeof(SortSmem<kSortCapSmall>), s, w, rank_max, sl,
+             keys_out);
+    else
+      launch(k_sort_tiles<8, kSortCapSmall>, FT, kSortThreads, sizeof(SortSmem<kSortCapSmall>), s, w, rank_max, sl,
+             keys_out);
+  } else if (bits == 4) {
+    launch(k_sort_tiles<4, kSortCap>, FT, kSortThreads, sizeof(SortSmem<kSortCap>), s, w, rank_max, sl, keys_out);
+  } else {
+    launch(k_sort_tiles<8, kSortCap>, FT, kSortThreads, sizeof(SortSmem<kSortCap>), s, w, rank_max, sl, keys_out);
+  }
 }
 
 }  // namespace rtg
