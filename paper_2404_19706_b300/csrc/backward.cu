@@ -99,10 +99,11 @@ __device__ __forceinline__ float warp_rs_two(const float (&A)[NV], const float (
 }
 
 // Replays the pixels of group `grp` of render tile `tile` (the forward's pixel grouping)
-// back to front.  Called by a whole warp; s_rec / s_j / s_rank are the warp's staging.
+// back to front.  Called by a whole warp; s_rec / s_jr (list position, unstable rank) are
+// the warp's staging.
 template <int C, int B>
 __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, int64_t N, int T, int tile, int grp,
-                                               float4 (*s_rec)[B], uint32_t *s_j, int *s_rank,
+                                               float4 (*s_rec)[B], int2 *s_jr,
                                                const float *__restrict__ dL_dcolor,
                                                const float *__restrict__ dL_ddepth, const L1Fused &l1) {
   constexpr int H4 = (C <= 4) ? 3 : 4;
@@ -263,8 +264,7 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
         const int slot = cnt + __popc(bal & lanemask_lt());
 #pragma unroll
         for (int k = 0; k < H4; ++k) s_rec[k][slot] = r[u][k];
-        s_j[slot] = (uint32_t)(b_beg + u * 32 + lane);
-        s_rank[slot] = rk[u];
+        s_jr[slot] = make_int2(b_beg + u * 32 + lane, rk[u]);
       }
       cnt += __popc(bal);
     }
@@ -278,7 +278,7 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
       for (int qq = 0; qq < NV; ++qq) v[qq] = 0.f;
       if (!act) return;
       const float om = 1.f - fa;
-      const float iom = __frcp_rn(om);
+      const float iom = __fdividef(1.f, om);  // 1 - f >= 1 - f_max: a normal divisor
       T_ = T_ * iom;  // transmission in front of this fragment
       const float wgt = fa * T_;
       const float4 c0 = s_rec[2][k];
@@ -316,7 +316,8 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
     };
     int k = cnt - 1;
     for (; k >= 1; k -= 2) {
-      const uint32_t jA = s_j[k], jB = s_j[k - 1];
+      const int2 jrA = s_jr[k], jrB = s_jr[k - 1];
+      const uint32_t jA = (uint32_t)jrA.x, jB = (uint32_t)jrB.x;
       const float4 a0 = s_rec[0][k], a1 = s_rec[1][k], b0 = s_rec[0][k - 1], b1 = s_rec[1][k - 1];
       float dxA, dyA, t1A, t2A, gA, dxB, dyB, t1B, t2B, gB;
       const float faA = footprint(fpx, fpy, a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, prm.f_max, dxA, dyA, t1A,
@@ -325,7 +326,7 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
                                   t2B, gB);
       const bool actA = has && jA < last && faA >= prm.alpha_min;
       const bool actB = has && jB < last && faB >= prm.alpha_min;
-      const int rA = s_rank[k], rB = s_rank[k - 1];
+      const int rA = jrA.y, rB = jrB.y;
       float vA[NV], vB[NV];
       frag(actA, faA, gA, dxA, dyA, t1A, t2A, a1, k, rA, vA);
       frag(actB, faB, gB, dxB, dyB, t1B, t2B, b1, k - 1, rB, vB);
@@ -340,13 +341,14 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
       }
     }
     if (k == 0) {
-      const uint32_t jA = s_j[0];
+      const int2 jrA = s_jr[0];
+      const uint32_t jA = (uint32_t)jrA.x;
       const float4 a0 = s_rec[0][0], a1 = s_rec[1][0];
       float dxA, dyA, t1A, t2A, gA;
       const float faA = footprint(fpx, fpy, a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, prm.f_max, dxA, dyA, t1A,
                                   t2A, gA);
       const bool actA = has && jA < last && faA >= prm.alpha_min;
-      const int rA = s_rank[0];
+      const int rA = jrA.y;
       float vA[NV];
       frag(actA, faA, gA, dxA, dyA, t1A, t2A, a1, 0, rA, vA);
       if (rA >= 0 && __any_sync(0xffffffffu, actA)) emit_one(warp_rs_one<NV>(vA), rA);
@@ -375,12 +377,11 @@ __global__ void __launch_bounds__(kMaxTilePix) k_backward(Work w, Prm prm, int64
   grid_dep_wait();
   constexpr int H4 = (C <= 4) ? 3 : 4;
   __shared__ float4 s_rec[kMaxTilePix / 32][H4][B];
-  __shared__ uint32_t s_j[kMaxTilePix / 32][B];
-  __shared__ int s_rank[kMaxTilePix / 32][B];
+  __shared__ int2 s_jr[kMaxTilePix / 32][B];
   if (w.counters[kSkip] != 0ull) return;
   const int tile = blockIdx.x, wid = threadIdx.x >> 5;
   if (wid * 32 >= (int)w.tile_npix[tile]) return;
-  backward_group<C, B>(w, prm, N, T, tile, wid, s_rec[wid], s_j[wid], s_rank[wid], in.dL_dcolor, in.dL_ddepth,
+  backward_group<C, B>(w, prm, N, T, tile, wid, s_rec[wid], s_jr[wid], in.dL_dcolor, in.dL_ddepth,
                        in.l1);
 }
 
@@ -391,8 +392,7 @@ __global__ void __launch_bounds__(256) k_backward_queue(Work w, Prm prm, int64_t
   grid_dep_wait();
   constexpr int H4 = (C <= 4) ? 3 : 4;
   __shared__ float4 s_rec[8][H4][B];
-  __shared__ uint32_t s_j[8][B];
-  __shared__ int s_rank[8][B];
+  __shared__ int2 s_jr[8][B];
   if (w.counters[kSkip] != 0ull) return;
   const uint32_t nitems = (uint32_t)w.counters[kItems];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(256) k_backward_queue(Work w, Prm prm, int64_t
   uint32_t it = blockIdx.x * 8u + (uint32_t)wid;
   while (it < nitems) {
     const uint32_t item = w.items[it];
-    backward_group<C, B>(w, prm, N, T, (int)(item >> 3), (int)(item & 7u), s_rec[wid], s_j[wid], s_rank[wid],
+    backward_group<C, B>(w, prm, N, T, (int)(item >> 3), (int)(item & 7u), s_rec[wid], s_jr[wid],
                          in.dL_dcolor, in.dL_ddepth, in.l1);
     uint32_t nx = 0;
     if (lane == 0) nx = nwarps + (uint32_t)atomicAdd(w.counters + kQBwd, 1ull);
