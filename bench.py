@@ -382,20 +382,40 @@ def roofline_of(per_launch, alg, tuning=None, workload=None, extra_kinds=()):
             "alg_bytes_per_launch": int(alg[dom]), "ms_per_launch": round(per_launch[dom], 5)}, pk
 
 
-def kernels_per_step(stats, F, H, W, schedule, per_frame_calls=1):
+DEPTH_SCALE = 5000.0  # 16-bit sensor depth in 1/5000 m (the unit common RGB-D datasets store)
+
+
+def sensor_frames(rtg, tcol, tdep):
+    """The targets as an RGB-D sensor delivers them: 8-bit interleaved colour and 16-bit depth
+    in 1/DEPTH_SCALE m (0: no measurement).  The float targets are replaced by their device
+    decode, so every arm optimises against the same values.  Returns the device (rgb, depth)."""
+    import torch
+    rgb = (tcol.clamp(0, 1) * 255).round().to(torch.uint8).permute(0, 2, 3, 1).contiguous()
+    dep = torch.where(tdep > 0, (tdep * DEPTH_SCALE).round(), torch.zeros_like(tdep)).clamp(0, 65535)
+    dep = dep.to(torch.int32).to(torch.uint16)
+    rtg.decode_rgbd(rgb, dep, DEPTH_SCALE, tcol, tdep)
+    return rgb, dep
+
+
+FRAME_NOTE = ("RGB-D frame: 8-bit RGB + 16-bit depth (1/5000 m), decoded on the device at the start of every step "
+              "(rtg_decode_rgbd); the e2e arm uploads it in that form")
+
+
+def kernels_per_step(stats, F, H, W, schedule, per_frame_calls=1, decode=False):
     """Kernels one masked step launches.  Per forward call of F frames: tile mask, cull,
     project, the mask grid's scan (1 kernel, 3 when its tiles outnumber one scan block), emit,
     cover, a render-grid tile-mask pass when the render tile is not 16 x 16, bin, the render
     grid's scan, emit, sort and composite, plus the loss finalize unless the persistent
-    schedule's forward does it; backward 2 per call; then Adam 1 (the renderer reads the
-    optimiser's compact arrays, so nothing is scattered back during the window)."""
+    schedule's forward does it; backward 2 per call; the frame decode per call when the step
+    reads a sensor frame; then Adam 1 (the renderer reads the optimiser's compact arrays, so
+    nothing is scattered back during the window)."""
     tw, th = stats["tile_w"], stats["tile_h"]
     scan = lambda ft: 1 if ft <= 8192 else 3
     ft_mask = F * ((W + 15) // 16) * ((H + 15) // 16)
     ft_render = F * ((W + tw - 1) // tw) * ((H + th - 1) // th)
     extra = 0 if (tw, th) == (16, 16) else 1
     fwd = 3 + scan(ft_mask) + 2 + extra + 1 + scan(ft_render) + 3 + (0 if schedule == 1 else 1)
-    return per_frame_calls * (fwd + 2) + 1
+    return per_frame_calls * (fwd + 2 + (1 if decode else 0)) + 1
 
 
 def pipelined_e2e(step_fn, dev_inputs, result, warmup, steps):
@@ -524,10 +544,12 @@ def run_ours(args):
     rtg.render_forward(ctx, cam, gt, None, settings, tcol, tdep, talp)
     tdep = torch.where(tdep > 0, tdep, torch.zeros_like(tdep))
     del gt
+    frame_rgb, frame_dep = sensor_frames(rtg, tcol, tdep)  # the step's input: the sensor frame
 
     g = rtg.Gaussians.from_scene(scene, device=dev)
     initial = (g.means.clone(), g.scales.clone(), g.quats.clone()) if sh else None  # L_reg reference
-    step = rtg.MaskedStep(ctx, g, [cam], mask, tcol, tdep, settings, recompute_mask=True, initial=initial)
+    step = rtg.MaskedStep(ctx, g, [cam], mask, tcol, tdep, settings, recompute_mask=True, initial=initial,
+                          frame=(frame_rgb, frame_dep, DEPTH_SCALE))
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 126 MB L2
 
@@ -567,7 +589,7 @@ def run_ours(args):
     b_step = sum(alg.values())
 
     # ---- end to end through the public API with host buffers (graph replay per step)
-    e2e_step, h2d, d2h = pipelined_e2e(step.step, [step.target_color, step.target_depth], step.loss, args.warmup,
+    e2e_step, h2d, d2h = pipelined_e2e(step.step, [frame_rgb, frame_dep], step.loss, args.warmup,
                                        args.steps)
     if dist is not None:
         t = torch.tensor([e2e_step], device=dev)
@@ -600,13 +622,14 @@ def run_ours(args):
                                  "with per-kernel CUDA events",
                        "wall_s_timed_region": round(wall, 3),
                        "kernel_ms_per_launch": {k: round(v, 5) for k, v in per_launch.items()},
+                       "input": FRAME_NOTE,
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline,
             "e2e": {"value": round(world * 1e3 / e2e_step, 2), "unit": "iter/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "pipelined": "next step's upload overlaps this step's compute"},
             # SH: the coefficient backward, and the regulariser's reduce and gradient kernels
-            "gpu_launches": (kernels_per_step(stats, 1, H, W, ctx.get_tuning().schedule) + (3 if sh else 0)) *
-                            args.steps,
+            "gpu_launches": (kernels_per_step(stats, 1, H, W, ctx.get_tuning().schedule, decode=True) +
+                             (3 if sh else 0)) * args.steps,
             "clocks": clk,
         }
         if world == 1 and not args.no_cpu_baseline:
@@ -627,9 +650,10 @@ class PerFrameStep:
     Frame f runs on its own context ctxs[f], which keeps that frame's optimisation window
     open, as the batched step's context keeps the window of all F frames."""
 
-    def __init__(self, rtg, ctxs, g, cams, masks, tcol, tdep, settings):
+    def __init__(self, rtg, ctxs, g, cams, masks, tcol, tdep, settings, frames=None):
         from paper_2404_19706_b300 import api
         self.api, self.ctxs, self.cams, self.settings = api, ctxs, cams, settings
+        self.frames = frames  # sensor frames (rgb, depth): each call decodes its own frame first
         self.masks, self.tcol, self.tdep = masks, tcol, tdep
         self.inner = rtg.MaskedStep(ctxs[0], g, [cams[0]], masks[0:1], tcol[0:1], tdep[0:1], settings,
                                     recompute_mask=True)
@@ -648,6 +672,9 @@ class PerFrameStep:
     def _body(self, stream=None):
         api, s = self.api, self.inner
         for f, cam in enumerate(self.cams):
+            if self.frames is not None:
+                api.decode_rgbd(self.frames[0][f:f + 1], self.frames[1][f:f + 1], DEPTH_SCALE, self.tcol[f:f + 1],
+                                self.tdep[f:f + 1], stream)
             api.render_forward_masked(self.ctxs[f], [cam], s.g, self.settings, self.masks[f:f + 1], self.color,
                                       self.depth, self.alpha, self.tcol[f:f + 1], self.tdep[f:f + 1], 1.0, 1.0,
                                       self.loss[f], None, stream)
@@ -746,7 +773,9 @@ def run_keyframes(args, kw):
     # batched: every frame in one call per kernel, one graph
     masks_b = torch.zeros(F, H, W, dtype=torch.uint8, device=dev)
     gb = rtg.Gaussians.from_scene(scene, device=dev)
-    batched = rtg.MaskedStep(ctx, gb, kcams, masks_b, tcol, tdep, settings, recompute_mask=True)
+    frames = sensor_frames(rtg, tcol, tdep) if Cc == 3 else None  # 8-channel images stay float planes
+    batched = rtg.MaskedStep(ctx, gb, kcams, masks_b, tcol, tdep, settings, recompute_mask=True,
+                             frame=(frames[0], frames[1], DEPTH_SCALE) if frames is not None else None)
     ckb = dict(mask=torch.zeros_like(masks_b), color=torch.zeros_like(tcol), depth=torch.zeros_like(tdep),
                alpha=torch.zeros_like(tdep))
 
@@ -760,7 +789,7 @@ def run_keyframes(args, kw):
     tuned_b = run_tuner(ctx, batched._body, check_b, step_state(batched), args, "batched")
     arms = [("batched", batched, [ctx])]
     if kw["per_frame"]:
-        arms.append(per_frame_arm(rtg, args, kw, scene, kcams, tcol, tdep, settings, check_b, ckb))
+        arms.append(per_frame_arm(rtg, args, kw, scene, kcams, tcol, tdep, settings, check_b, ckb, frames))
     tuned_p = arms[1][3] if len(arms) > 1 else None
 
     results = {}
@@ -786,7 +815,8 @@ def run_keyframes(args, kw):
     b_step = sum(alg.values())
 
     # end to end: targets uploaded from pinned host memory and the losses read back each step
-    e2e_step, h2d, d2h = pipelined_e2e(batched.step, [batched.target_color, batched.target_depth], batched.loss,
+    e2e_inputs = list(frames) if frames is not None else [batched.target_color, batched.target_depth]
+    e2e_step, h2d, d2h = pipelined_e2e(batched.step, e2e_inputs, batched.loss,
                                        args.warmup, args.steps)
 
     if rank != 0:
@@ -812,12 +842,14 @@ def run_keyframes(args, kw):
                                "tuning": ctx1.get_tuning().as_dict(),
                                "autotune": tuned_p.summary() if tuned_p is not None else fixed,
                                "gpu_launches_per_step": kernels_per_step(results["per_frame"]["stats"], 1, H, W,
-                                                                         ctx1.get_tuning().schedule, F)}
+                                                                         ctx1.get_tuning().schedule, F,
+                                                                         decode=frames is not None)}
         config["batched_over_per_frame"] = round(msp / msb, 3)
     config.update({"l2": "256 MB buffer written before every step, outside the timed spans",
                    "timing": "each arm replays one CUDA graph of its whole step (F-frame calls, or F single-frame "
                              "call sequences); kernel_ms_per_launch from a live eager pass of the batched step",
                    "kernel_ms_per_launch": {k: round(v, 5) for k, v in per_launch.items()},
+                   "input": FRAME_NOTE if frames is not None else "float target planes (8 channels)",
                    "parallelism": "replicas x1"})
     per_frame_metric = kw["per_frame"]
     return {
@@ -830,12 +862,13 @@ def run_keyframes(args, kw):
         "e2e": {"value": round(F * 1e3 / e2e_step, 2) if per_frame_metric else round(1e3 / e2e_step, 3),
                 "unit": "frames/s" if per_frame_metric else "iter/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "pipelined": "next step's upload overlaps this step's compute"},
-        "gpu_launches": kernels_per_step(sb, F, H, W, ctx.get_tuning().schedule) * args.steps,
+        "gpu_launches": kernels_per_step(sb, F, H, W, ctx.get_tuning().schedule, decode=frames is not None) *
+                        args.steps,
         "clocks": results["batched"]["clocks"].summary(),
     }
 
 
-def per_frame_arm(rtg, args, kw, scene, kcams, tcol, tdep, settings, check_b, ckb):
+def per_frame_arm(rtg, args, kw, scene, kcams, tcol, tdep, settings, check_b, ckb, frames=None):
     """The same iteration as F single-frame call sequences, one context (and window) per
     frame; checked against the batched arm before any optimiser step."""
     import torch
@@ -846,7 +879,7 @@ def per_frame_arm(rtg, args, kw, scene, kcams, tcol, tdep, settings, check_b, ck
     ctx1 = ctxs[0]
     masks_p = torch.zeros(F, H, W, dtype=torch.uint8, device=dev)
     gp = rtg.Gaussians.from_scene(scene, device=dev)
-    perframe = PerFrameStep(rtg, ctxs, gp, kcams, masks_p, tcol, tdep, settings)
+    perframe = PerFrameStep(rtg, ctxs, gp, kcams, masks_p, tcol, tdep, settings, frames)
     ckp = dict(mask=torch.zeros(1, H, W, dtype=torch.uint8, device=dev), color=torch.zeros(1, Cc, H, W, device=dev),
                depth=torch.zeros(1, H, W, device=dev), alpha=torch.zeros(1, H, W, device=dev))
 

@@ -403,6 +403,16 @@ rtg_status rtg_update_states(int64_t n, int32_t frame, const int32_t *t0, const 
 rtg_status rtg_compact_gaussians(rtg_ctx *ctx, int64_t n, int32_t C, const uint8_t *remove, const rtg_map_arrays *in,
                                  const rtg_map_arrays *out, int64_t *count_out, void *stream);
 
+/* Decode F RGB-D sensor frames (Section 3: each input frame is a colour image and a depth
+ * map) into the float planes the loss reads.  DEVICE arrays:
+ *   rgb   [F,H,W,3] uint8, interleaved;      color     [F,3,H,W] float32 = value / 255
+ *   depth [F,H,W] uint16, depth_scale units; depth_out [F,H,W] float32 = value / depth_scale
+ * (metres; a 0, no measurement, stays 0).  Both quotients are IEEE float32 divisions, equal
+ * bit for bit to the same conversion on the host.  F, H, W >= 1, depth_scale > 0 and finite,
+ * no NULL pointer, else RTG_ERR_ARG.  Asynchronous on `stream`; needs no context. */
+rtg_status rtg_decode_rgbd(int32_t F, int32_t H, int32_t W, const uint8_t *rgb, const uint16_t *depth,
+                           float depth_scale, float *color, float *depth_out, void *stream);
+
 /* Adam (Kingma & Ba, Algorithm 1) on compact unstable parameters, in place, with the
  * per-group learning rates of Supplement C.  The scale is optimised in log space
  * (s <- s * exp(-step), gradient s * dL/ds).  m and v hold nu * (11 + C) float32 each,

@@ -27,6 +27,7 @@ from .api import (  # noqa: E402,F401
     RTGError,
     adam_step,
     adam_step_counted,
+    decode_rgbd,
     debug_binning,
     gather_unstable,
     get_stats,

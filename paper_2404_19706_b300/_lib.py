@@ -120,6 +120,8 @@ SIGNATURES = [
     ("rtg_narrow_pixels", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_float, c_void_p,
                                     c_void_p]),
     ("rtg_get_tuning", c_int32, [c_void_p, POINTER(rtg_tuning)]),
+    ("rtg_decode_rgbd", c_int32, [c_int32, c_int32, c_int32, c_void_p, c_void_p, c_float, c_void_p, c_void_p,
+                                  c_void_p]),
     ("rtg_adam_step", c_int32, [c_int64, c_int32] + [c_void_p] * 12 + [c_int32, POINTER(rtg_adam_params),
                                                                        c_void_p]),
     ("rtg_adam_step_counted", c_int32, [c_int64, c_int32] + [c_void_p] * 13 + [POINTER(rtg_adam_params),

@@ -557,6 +557,26 @@ def render_backward(ctx: Context, dL_dcolor, dL_ddepth, g_means, g_scales, g_qua
     _check(st, "rtg_render_backward", ctx.ptr)
 
 
+def decode_rgbd(rgb: torch.Tensor, depth: torch.Tensor, depth_scale: float, color: torch.Tensor,
+                depth_out: torch.Tensor, stream=None):
+    """RGB-D sensor frames to the float planes the loss reads (rtg_decode_rgbd): rgb uint8
+    [F,H,W,3] (or [H,W,3]), depth uint16 [F,H,W] (or [H,W]) in 1/depth_scale metres; writes
+    color [F,3,H,W] = rgb / 255 and depth_out [F,H,W] = depth / depth_scale (0 stays 0)."""
+    if rgb.dim() == 3:
+        rgb = rgb.unsqueeze(0)
+    if depth.dim() == 2:
+        depth = depth.unsqueeze(0)
+    F, H, W, three = rgb.shape
+    if three != 3 or tuple(depth.shape) != (F, H, W):
+        raise ValueError("rgb must be [F,H,W,3] and depth [F,H,W]")
+    if color.numel() != F * 3 * H * W or depth_out.numel() != F * H * W:
+        raise ValueError("color must hold F*3*H*W values and depth_out F*H*W")
+    st = _lib.load().rtg_decode_rgbd(F, H, W, _ptr(rgb, torch.uint8, "rgb"), _ptr(depth, torch.uint16, "depth"),
+                                     float(depth_scale), _ptr(color, torch.float32, "color"),
+                                     _ptr(depth_out, torch.float32, "depth_out"), _stream(stream))
+    _check(st, "rtg_decode_rgbd")
+
+
 def adam_step(params: Sequence[torch.Tensor], grads: Sequence[torch.Tensor], m: torch.Tensor, v: torch.Tensor,
               step: int, hp: AdamSettings = AdamSettings(), stream=None):
     """params/grads: compact (means, scales, quats, opacity, colors); m, v: nu * (11 + C) floats

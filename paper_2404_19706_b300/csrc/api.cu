@@ -1100,6 +1100,15 @@ rtg_status rtg_compact_gaussians(rtg_ctx *ctx, int64_t n, int32_t C, const uint8
   return check_launch(ctx, "compact_gaussians");
 }
 
+rtg_status rtg_decode_rgbd(int32_t F, int32_t H, int32_t W, const uint8_t *rgb, const uint16_t *depth,
+                           float depth_scale, float *color, float *depth_out, void *stream) {
+  if (F < 1 || H < 1 || W < 1 || !(depth_scale > 0.f) || !isfinite(depth_scale) || rgb == nullptr ||
+      depth == nullptr || color == nullptr || depth_out == nullptr)
+    return RTG_ERR_ARG;
+  launch_decode_rgbd(F, H, W, rgb, depth, depth_scale, color, depth_out, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? RTG_OK : RTG_ERR_CUDA;
+}
+
 rtg_status rtg_adam_step(int64_t nu, int32_t C, float *means, float *scales, float *quats, float *opacity,
                          float *colors, const float *g_means, const float *g_scales, const float *g_quats,
                          const float *g_opacity, const float *g_colors, float *m, float *v, int32_t step,

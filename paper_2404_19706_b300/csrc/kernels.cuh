@@ -168,6 +168,9 @@ struct StableLists {
 void launch_sort_tiles(const Work &w, int FT, int bits, int rank_max, const StableLists &sl,
                        unsigned long long *keys_out, bool small, cudaStream_t s);
 void init_sort_attributes();
+// frame.cu
+void launch_decode_rgbd(int F, int H, int W, const uint8_t *rgb, const uint16_t *depth, float depth_scale,
+                        float *color, float *depth_out, cudaStream_t s);
 // forward.cu
 // loss_out != nullptr (persistent schedule with fused targets): the forward also finalizes
 // the L1 loss (loss_out[0..2] and the gradient scales), as launch_loss_finalize would.

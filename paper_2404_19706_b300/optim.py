@@ -89,13 +89,19 @@ class MaskedStep:
     fixed and only the unstable Gaussians move.  With ``window`` (default) it opens the
     context's window, so the stable Gaussians are projected once here and every iteration
     projects only the unstable ones (results identical; rtg_window_begin).
+
+    With ``frame = (rgb, depth, depth_scale)`` (uint8 [F,H,W,3], uint16 [F,H,W], device) the
+    step's input is the sensor frame itself: every iteration first decodes it into
+    ``target_color`` / ``target_depth`` (rtg_decode_rgbd), so a frame loop uploads 5 bytes a
+    pixel instead of the 16 of the float planes.
     """
 
     def __init__(self, ctx: Context, g: Gaussians, cams, mask: Optional[torch.Tensor], target_color: torch.Tensor,
                  target_depth: torch.Tensor, settings: RenderSettings = RenderSettings(),
                  adam: AdamSettings = AdamSettings(), w_color: float = 1.0, w_depth: float = 1.0,
                  recompute_mask: bool = False, window: bool = True, scatter_every_step: bool = False,
-                 map_state=None, initial: Optional[Sequence[torch.Tensor]] = None, w_reg: float = 1000.0):
+                 map_state=None, initial: Optional[Sequence[torch.Tensor]] = None, w_reg: float = 1000.0,
+                 frame=None):
         if g.sh_degree > 0 and adam.colors_dc == 0:  # Supplement C: SH0 rate for the degree-0 terms
             adam = dataclasses.replace(adam, colors_dc=3)
         self.ctx, self.settings, self.adam = ctx, settings, adam
@@ -120,6 +126,7 @@ class MaskedStep:
         dev = g.means.device
         C = g.color_width
         self.target_color, self.target_depth = target_color, target_depth
+        self.frame = frame
         self.loss = torch.zeros(3, device=dev)
         self.grads = [torch.zeros_like(t) for t in self.u]
         self.m = torch.zeros(self.nu * (11 + C), device=dev)
@@ -146,6 +153,8 @@ class MaskedStep:
 
     def _body(self, stream=None):
         s = self.state
+        if self.frame is not None:
+            api.decode_rgbd(self.frame[0], self.frame[1], self.frame[2], self.target_color, self.target_depth, stream)
         if self.recompute_mask:
             # mask, forward and L1 loss in one pass sharing a single projection
             api.render_forward_masked(self.ctx, self.cams, self.g, self.settings, self.mask, s.color, s.depth,

@@ -119,6 +119,11 @@ def test_global_optimisation_entry_points_reject_bad_arguments_without_gpu():
     assert lib.rtg_update_states(5, 0, None, ctypes.byref(sp), None, None, None, None, None) == _lib.RTG_ERR_ARG
     assert lib.rtg_error_count(None, 1, 3, 8, 8, *([None] * 6), 0, ctypes.byref(sp), None, None) == _lib.RTG_ERR_ARG
     assert lib.rtg_compact_gaussians(None, 0, 3, None, None, None, None, None) == _lib.RTG_ERR_ARG
+    # frame decode: sizes, scale and pointers are checked before any device work
+    assert lib.rtg_decode_rgbd(0, 4, 4, 1, 1, 5000.0, 1, 1, None) == _lib.RTG_ERR_ARG
+    assert lib.rtg_decode_rgbd(1, 4, 4, 1, 1, 0.0, 1, 1, None) == _lib.RTG_ERR_ARG
+    assert lib.rtg_decode_rgbd(1, 4, 4, 1, 1, float("inf"), 1, 1, None) == _lib.RTG_ERR_ARG
+    assert lib.rtg_decode_rgbd(1, 4, 4, None, 1, 5000.0, 1, 1, None) == _lib.RTG_ERR_ARG
     p = _lib.rtg_add_params(0.5, 0.1, 0.1, 0.05, 0.99, 0.1, 0)
     assert lib.rtg_add_candidates(None, None, 1, 3, *([None] * 7), 0, ctypes.byref(p), 0,
                                   *([None] * 6), None) == _lib.RTG_ERR_ARG

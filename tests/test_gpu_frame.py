@@ -1,0 +1,87 @@
+"""RGB-D frame decode (rtg_decode_rgbd) against the same conversion on the host, and a
+masked step fed the sensor frame against one fed the decoded float planes."""
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import rtg
+
+pytestmark = pytest.mark.gpu
+
+
+def host_decode(rgb, depth, scale):
+    color = (rgb.astype(np.float32) / np.float32(255)).transpose(0, 3, 1, 2)
+    return np.ascontiguousarray(color), depth.astype(np.float32) / np.float32(scale)
+
+
+@pytest.mark.parametrize("F,H,W,scale", [(1, 7, 5, 5000.0), (3, 33, 65, 1000.0), (2, 480, 640, 6553.5)])
+def test_decode_matches_host_bit_for_bit(F, H, W, scale):
+    m = rtg()
+    rng = np.random.default_rng(F * H + W)
+    rgb = rng.integers(0, 256, (F, H, W, 3), dtype=np.uint8)
+    depth = rng.integers(0, 65536, (F, H, W), dtype=np.uint16)
+    rgb[0, 0, 0] = (0, 255, 128)
+    depth[0, 0, :2] = (0, 65535)
+    color = torch.full((F, 3, H, W), -1.0, device="cuda")
+    dout = torch.full((F, H, W), -1.0, device="cuda")
+    m.decode_rgbd(torch.from_numpy(rgb).cuda(), torch.from_numpy(depth).cuda(), scale, color, dout)
+    torch.cuda.synchronize()
+    ref_c, ref_d = host_decode(rgb, depth, scale)
+    assert np.array_equal(color.cpu().numpy(), ref_c)
+    assert np.array_equal(dout.cpu().numpy(), ref_d)
+    assert float(dout[0, 0, 0]) == 0.0
+
+
+def test_decode_rejects_bad_shapes_and_types():
+    m = rtg()
+    rgb = torch.zeros(1, 4, 4, 3, dtype=torch.uint8, device="cuda")
+    depth = torch.zeros(1, 4, 4, dtype=torch.uint16, device="cuda")
+    color, dout = torch.zeros(1, 3, 4, 4, device="cuda"), torch.zeros(1, 4, 4, device="cuda")
+    with pytest.raises(ValueError):
+        m.decode_rgbd(rgb, torch.zeros(1, 4, 5, dtype=torch.uint16, device="cuda"), 1000.0, color, dout)
+    with pytest.raises(TypeError):
+        m.decode_rgbd(rgb, depth.to(torch.int32), 1000.0, color, dout)
+    with pytest.raises(RuntimeError):
+        m.decode_rgbd(rgb, depth, 0.0, color, dout)
+
+
+def test_masked_step_from_sensor_frame_equals_decoded_targets():
+    import synth
+    m = rtg()
+    scene, layout = synth.room_scene(515, 20000)
+    cam = next(synth.room_camera_candidates(516, layout, 96, 72, 90.0))
+    scene.unstable = synth.flag_blobs(scene, [cam], 3000, 2, seed=3)
+    H, W = cam.height, cam.width
+    ref = m.Gaussians.from_scene(synth.jitter_scene(scene, 9))
+    ctx0 = m.Context(max_gaussians=scene.n, max_width=W, max_height=H)
+    c = torch.zeros(1, 3, H, W, device="cuda")
+    d = torch.full((1, H, W), -1.0, device="cuda")
+    a = torch.zeros(1, H, W, device="cuda")
+    m.render_forward(ctx0, cam, ref, None, m.RenderSettings(), c, d, a)
+    rgb = (c[0].clamp(0, 1) * 255).round().to(torch.uint8).permute(1, 2, 0).contiguous().unsqueeze(0)
+    dep = torch.where(d > 0, (d * 5000).round(), torch.zeros_like(d)).clamp(0, 65535).to(torch.int32)
+    dep = dep.to(torch.uint16)
+    out = []
+    for use_frame in (False, True):
+        ctx = m.Context(max_gaussians=scene.n, max_width=W, max_height=H)
+        g = m.Gaussians.from_scene(scene)
+        tc, td = torch.zeros(1, 3, H, W, device="cuda"), torch.zeros(1, H, W, device="cuda")
+        if not use_frame:
+            m.decode_rgbd(rgb, dep, 5000.0, tc, td)
+        mask = torch.zeros(1, H, W, dtype=torch.uint8, device="cuda")
+        step = m.MaskedStep(ctx, g, [cam], mask, tc, td, recompute_mask=True,
+                            frame=(rgb, dep, 5000.0) if use_frame else None)
+        loss = step.step().cpu().numpy().copy()  # the first loss: the forward of identical targets
+        for _ in range(2):
+            step.step()
+        torch.cuda.synchronize()
+        out.append((loss, tc.cpu().numpy(), td.cpu().numpy(), [t.cpu().numpy().copy() for t in step.u]))
+    assert out[0][0][0] > 0
+    np.testing.assert_array_equal(out[0][1], out[1][1])  # the step decoded the same planes
+    np.testing.assert_array_equal(out[0][2], out[1][2])
+    np.testing.assert_allclose(out[1][0], out[0][0], rtol=1e-6)
+    # the parameters after three steps: the gradient rows are float32 atomics whose order
+    # varies between runs
+    for a_, b_ in zip(out[0][3], out[1][3]):
+        np.testing.assert_allclose(b_, a_, rtol=1e-5, atol=1e-6)
