@@ -908,29 +908,45 @@ def per_frame_arm(rtg, args, kw, scene, kcams, tcol, tdep, settings, check_b, ck
 
 # ----------------------------------------------------------------------------- GPU arm: global step
 
-class BoundGlobalStep:
-    """A GlobalStep with its keyframes and target buffers bound, for the bench's helpers
-    (which call step(), _body() and capture() without arguments)."""
-
-    def __init__(self, st, cams, tcol, tdep):
-        self.st, self.cams, self.tcol, self.tdep = st, cams, tcol, tdep
-
-    @property
-    def graph(self):
-        return self.st.graph
-
-    @graph.setter
-    def graph(self, g):
-        self.st.graph = g
-
-    def _body(self):
-        return self.st._body(self.cams, self.tcol, self.tdep)
+class Replayable:
+    """step() replays the CUDA graph of _body() once capture() has recorded it."""
+    graph = None
 
     def step(self):
-        return self.st.step(self.cams, self.tcol, self.tdep)
+        if self.graph is not None:
+            self.graph.replay()
+            return self.result
+        return self._body()
 
     def capture(self):
-        return self.st.capture(self.cams, self.tcol, self.tdep)
+        import torch
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            self._body()
+        torch.cuda.synchronize()
+        self.graph = graph
+
+
+def decode_frames(frames, tcol, tdep):
+    """The step's first kernel when its input is a sensor frame (rgb, depth)."""
+    if frames is not None:
+        from paper_2404_19706_b300 import api
+        api.decode_rgbd(frames[0], frames[1], DEPTH_SCALE, tcol, tdep)
+
+
+class BoundGlobalStep(Replayable):
+    """A GlobalStep with its keyframes and target buffers bound, for the bench's helpers
+    (which call step(), _body() and capture() without arguments); with `frames`, every step
+    first decodes the keyframes' sensor frames into the targets."""
+
+    def __init__(self, st, cams, tcol, tdep, frames=None):
+        self.st, self.cams, self.tcol, self.tdep, self.frames = st, cams, tcol, tdep, frames
+        self.result = st.loss
+
+    def _body(self):
+        decode_frames(self.frames, self.tcol, self.tdep)
+        return self.st._body(self.cams, self.tcol, self.tdep)
 
 
 def global_kernels_per_step(F, H, W, tuning):
@@ -1028,7 +1044,8 @@ def run_global(args, kw=GLOBAL):
     del gt
     g = rtg.Gaussians.from_scene(scene, device=dev)
     gstep = rtg.GlobalStep(ctx, g, W, H, max_frames=F, settings=settings, frac=kw["frac"])
-    step = BoundGlobalStep(gstep, kcams, tcol, tdep)
+    frames = sensor_frames(rtg, tcol, tdep)  # the keyframes as sensor frames
+    step = BoundGlobalStep(gstep, kcams, tcol, tdep, frames)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     ck = dict(color=torch.zeros_like(tcol), depth=torch.zeros_like(tdep), alpha=torch.zeros_like(tdep))
@@ -1064,7 +1081,7 @@ def run_global(args, kw=GLOBAL):
                                extra_kinds=("select_top_error", "narrow_pixels", "l1_loss"))
     b_step = sum(alg.values())
 
-    e2e_step, h2d, d2h = pipelined_e2e(step.step, [tcol, tdep], gstep.loss, args.warmup, args.steps)
+    e2e_step, h2d, d2h = pipelined_e2e(step.step, list(frames), gstep.loss, args.warmup, args.steps)
     tuning = ctx.get_tuning()
     if rank != 0:
         return None
@@ -1085,11 +1102,12 @@ def run_global(args, kw=GLOBAL):
                              "from a live eager pass with per-kernel CUDA events",
                    "wall_s_timed_region": round(wall, 3),
                    "kernel_ms_per_launch": {k: round(v, 5) for k, v in per_launch.items()},
+                   "input": FRAME_NOTE,
                    "parallelism": "replicas x1"},
         "roofline": roofline,
         "e2e": {"value": round(1e3 / e2e_step, 2), "unit": "iter/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "pipelined": "next step's upload overlaps this step's compute"},
-        "gpu_launches": global_kernels_per_step(F, H, W, tuning) * args.steps,
+        "gpu_launches": (global_kernels_per_step(F, H, W, tuning) + 1) * args.steps,  # + the frame decode
         "clocks": clocks.summary(),
     }
     if not args.no_cpu_baseline:
@@ -1100,31 +1118,19 @@ def run_global(args, kw=GLOBAL):
 
 # ----------------------------------------------------------------------------- GPU arm: adding pass
 
-class BoundAddingPass:
+class BoundAddingPass(Replayable):
     """An AddingPass with its frame bound, replayed from a CUDA graph (the seed is fixed in
-    the graph; each replay redoes the same draw)."""
+    the graph; each replay redoes the same draw); with `frames`, the pass first decodes the
+    sensor frame into color / depth."""
 
-    def __init__(self, ap, cams, g, color, depth, seed):
+    def __init__(self, ap, cams, g, color, depth, seed, frames=None):
         self.ap, self.cams, self.g, self.color, self.depth, self.seed = ap, cams, g, color, depth, seed
-        self.graph = None
+        self.frames = frames
+        self.result = ap.count
 
     def _body(self):
+        decode_frames(self.frames, self.color, self.depth)
         return self.ap.run(self.cams, self.g, self.color, self.depth, self.seed)
-
-    def step(self):
-        if self.graph is not None:
-            self.graph.replay()
-            return self.ap.count
-        return self._body()
-
-    def capture(self):
-        import torch
-        torch.cuda.synchronize()
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph):
-            self._body()
-        torch.cuda.synchronize()
-        self.graph = graph
 
 
 def oracle_adding_rate(scene, cam, maps, budget_px=48):
@@ -1192,7 +1198,8 @@ def run_adding(args, kw=ADDING):
     rank_map, ids, nu = rtg.unstable_rank(ctx, g.unstable)
     g = dataclasses.replace(g, rank_map=rank_map, unstable_ids=ids, n_unstable=nu)
     ap = rtg.AddingPass(ctx, W, H, capacity=kw["capacity"])
-    step = BoundAddingPass(ap, [cam], g, icol, idep, seed=kw["seed"])
+    frames = sensor_frames(rtg, icol, idep)  # the input frame as the sensor delivers it
+    step = BoundAddingPass(ap, [cam], g, icol, idep, seed=kw["seed"], frames=frames)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     ck = dict(color=torch.zeros_like(icol), depth=torch.zeros_like(idep), alpha=torch.zeros_like(idep))
@@ -1225,12 +1232,12 @@ def run_adding(args, kw=ADDING):
     roofline, pk = roofline_of(per_launch, alg, ctx.get_tuning(), "adding", extra_kinds=("add_candidates",))
     b_step = sum(alg.values())
     # end to end: the input frame uploaded from pinned host memory, the count read back
-    e2e_step, h2d, d2h = pipelined_e2e(step.step, [icol, idep], ap.count, args.warmup, args.steps)
+    e2e_step, h2d, d2h = pipelined_e2e(step.step, list(frames), ap.count, args.warmup, args.steps)
     tuning = ctx.get_tuning()
     if rank != 0:
         return None
     FT = ((W + tuning.tile_w - 1) // tuning.tile_w) * ((H + tuning.tile_h - 1) // tuning.tile_h)
-    launches = 6 + (1 if FT <= 8192 else 3) + 3  # forward (no index pass: precomputed) + adding
+    launches = 1 + 6 + (1 if FT <= 8192 else 3) + 3  # decode, forward (no index pass: precomputed), adding
     fixed = "fixed by --tuning" if args.tuning else "off (--no-tune)"
     out = {
         "metric": ADD_METRIC, "value": round(1e3 / ms_step, 2), "unit": "frames/s", "n_gpus": world,
@@ -1248,6 +1255,7 @@ def run_adding(args, kw=ADDING):
                              "pass with per-kernel CUDA events",
                    "wall_s_timed_region": round(wall, 3),
                    "kernel_ms_per_launch": {k: round(v, 5) for k, v in per_launch.items()},
+                   "input": FRAME_NOTE,
                    "parallelism": "replicas x1"},
         "roofline": roofline,
         "e2e": {"value": round(1e3 / e2e_step, 2), "unit": "frames/s", "h2d_bytes_per_step": h2d,
@@ -1283,12 +1291,13 @@ def kernel_profile_adding(rtg, ctx, step, steps, flush):
 
 # ----------------------------------------------------------------------------- GPU arm: state management
 
-class StatePass:
+class StatePass(Replayable):
     """One state-management pass per frame, on preallocated buffers: full-frame render of the
     map with its index map, error counts, transitions, pruning into a second set of arrays,
-    and the Eq. 9 fusion of the window's optimised Gaussians."""
+    and the Eq. 9 fusion of the window's optimised Gaussians; with `frames`, the pass first
+    decodes the sensor frame into icol / idep."""
 
-    def __init__(self, rtg, ctx, g, state, cam, icol, idep, ids, compact, frame, settings):
+    def __init__(self, rtg, ctx, g, state, cam, icol, idep, ids, compact, frame, settings, frames=None):
         self.rtg, self.ctx, self.g, self.state, self.cam = rtg, ctx, g, state, cam
         self.icol, self.idep, self.ids, self.compact, self.frame, self.settings = icol, idep, ids, compact, frame, settings
         import torch
@@ -1301,31 +1310,18 @@ class StatePass:
         self.src = state.arrays()
         self.dst = rtg.MapArrays.empty_like(self.src)
         self.count = torch.zeros(1, dtype=torch.int64, device=dev)
-        self.graph = None
+        self.result = self.count
+        self.frames = frames
 
     def _body(self):
         r, st = self.rtg, self.state
+        decode_frames(self.frames, self.icol, self.idep)
         r.render_forward(self.ctx, [self.cam], self.g, None, self.settings, self.rc, self.rd, self.ra, self.ri)
         st.count_errors(self.rc, self.rd, self.ri, self.icol, self.idep)
         st.update(self.frame)
         r.compact_gaussians(self.ctx, st.remove, self.src, self.dst, self.count)
         st.fuse(self.ids, self.compact)
         return self.count
-
-    def step(self):
-        if self.graph is not None:
-            self.graph.replay()
-            return self.count
-        return self._body()
-
-    def capture(self):
-        import torch
-        torch.cuda.synchronize()
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph):
-            self._body()
-        torch.cuda.synchronize()
-        self.graph = graph
 
 
 def oracle_state_rate(scene, cam, maps, arrays, budget_px=48):
@@ -1395,7 +1391,8 @@ def run_state(args, kw=STATE):
     for c in compact:
         c.add_(0.001)
     state.eta[ids.long()] += 3  # three colour updates in the window
-    sp = StatePass(rtg, ctx, g, state, cam, icol, idep, ids, compact, kw["frame"], settings)
+    frames = sensor_frames(rtg, icol, idep)  # the input frame as the sensor delivers it
+    sp = StatePass(rtg, ctx, g, state, cam, icol, idep, ids, compact, kw["frame"], settings, frames)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     ck = dict(color=torch.zeros_like(icol), depth=torch.zeros_like(idep), alpha=torch.zeros_like(idep))
@@ -1427,12 +1424,12 @@ def run_state(args, kw=STATE):
     alg["compact_gaussians"] = N * 1 + 2 * kept * row + (N - kept) * 0
     roofline, pk = roofline_of(per_launch, alg, ctx.get_tuning(), "state",
                                extra_kinds=("error_count", "compact_gaussians"))
-    e2e_step, h2d, d2h = pipelined_e2e(sp.step, [icol, idep], sp.count, args.warmup, args.steps)
+    e2e_step, h2d, d2h = pipelined_e2e(sp.step, list(frames), sp.count, args.warmup, args.steps)
     tuning = ctx.get_tuning()
     if rank != 0:
         return None
     FT = ((W + tuning.tile_w - 1) // tuning.tile_w) * ((H + tuning.tile_h - 1) // tuning.tile_h)
-    launches = 6 + (1 if FT <= 8192 else 3) + 2 + 1 + 3 + 1  # forward, error count, states, compaction, fusion
+    launches = 1 + 6 + (1 if FT <= 8192 else 3) + 2 + 1 + 3 + 1  # decode, forward, errors, states, compaction, fusion
     fixed = "fixed by --tuning" if args.tuning else "off (--no-tune)"
     alg_step = sum(alg.values()) + int(nu) * (3 * 4 * (11 + C) + 12)  # + the fusion's reads and writes
     out = {
@@ -1449,6 +1446,7 @@ def run_state(args, kw=STATE):
                              "pass with per-kernel CUDA events (the fusion has no context and is not listed)",
                    "wall_s_timed_region": round(wall, 3),
                    "kernel_ms_per_launch": {k: round(v, 5) for k, v in per_launch.items()},
+                   "input": FRAME_NOTE,
                    "parallelism": "replicas x1"},
         "roofline": roofline,
         "e2e": {"value": round(1e3 / e2e_step, 2), "unit": "frames/s", "h2d_bytes_per_step": h2d,
