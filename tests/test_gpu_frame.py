@@ -15,7 +15,8 @@ def host_decode(rgb, depth, scale):
     return np.ascontiguousarray(color), depth.astype(np.float32) / np.float32(scale)
 
 
-@pytest.mark.parametrize("F,H,W,scale", [(1, 7, 5, 5000.0), (3, 33, 65, 1000.0), (2, 480, 640, 6553.5)])
+@pytest.mark.parametrize("F,H,W,scale", [(1, 7, 5, 5000.0), (1, 4, 6, 5000.0), (3, 33, 65, 1000.0),
+                                         (2, 480, 640, 6553.5)])
 def test_decode_matches_host_bit_for_bit(F, H, W, scale):
     m = rtg()
     rng = np.random.default_rng(F * H + W)
