@@ -471,6 +471,23 @@ def pipelined_e2e(step_fn, dev_inputs, result, warmup, steps):
     return ms, int(sum(t.numel() * t.element_size() for t in dev_inputs)), int(result.numel() * result.element_size())
 
 
+def max_over_ranks(value, dist, device):
+    """The largest of the ranks' values, on every rank (the slowest replica's time); the value
+    itself without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, ms_per_step, units_per_step=1.0):
+    """Whole-job throughput of `world` replicas that each run one step (of units_per_step
+    units) per ms_per_step, the max over ranks."""
+    return world * units_per_step * 1e3 / ms_per_step
+
+
 def timed_replays(step, steps, flush, stream, local, dist=None):
     """K graph replays, each between CUDA events on the launching stream, L2 flushed before each."""
     import torch
@@ -576,10 +593,7 @@ def run_ours(args):
     ms_step, wall, clocks = timed_replays(step, args.steps, flush, stream, local, dist)
     stats = rtg.get_stats(ctx)
     assert stats["status"] == 0, stats
-    if dist is not None:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(ms_step, dist, dev)
 
     # ---- per-kernel device time, live, and the roofline of the dominant kernel
     per_launch = kernel_profile(rtg, ctx, step, args.steps, flush, stream)
@@ -591,14 +605,11 @@ def run_ours(args):
     # ---- end to end through the public API with host buffers (graph replay per step)
     e2e_step, h2d, d2h = pipelined_e2e(step.step, [frame_rgb, frame_dep], step.loss, args.warmup,
                                        args.steps)
-    if dist is not None:
-        t = torch.tensor([e2e_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_step = float(t.item())
+    e2e_step = max_over_ranks(e2e_step, dist, dev)
 
     result = None
     if rank == 0:
-        value = world * 1e3 / ms_step
+        value = job_rate(world, ms_step)
         clk = clocks.summary()
         result = {
             "metric": SH_METRIC if sh else METRIC, "value": round(value, 2), "unit": "iter/s", "n_gpus": world,
@@ -611,7 +622,7 @@ def run_ours(args):
                        "pairs": K, "visible": V, "fragments_per_step": stats["fragments"],
                        "warp_records_per_step": stats["warp_records"],
                        "active_lanes_per_record": round(stats["fragments"] / max(stats["warp_records"], 1), 2),
-                       "fragments_per_sec": round(world * stats["fragments"] * 1e3 / ms_step, 1),
+                       "fragments_per_sec": round(job_rate(world, ms_step, stats["fragments"]), 1),
                        "alg_bytes_per_step": int(b_step),
                        "step_hbm_roofline_frac": round(b_step / (ms_step * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
                        "tuning": ctx.get_tuning().as_dict(),
@@ -625,7 +636,7 @@ def run_ours(args):
                        "input": FRAME_NOTE,
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline,
-            "e2e": {"value": round(world * 1e3 / e2e_step, 2), "unit": "iter/s", "h2d_bytes_per_step": h2d,
+            "e2e": {"value": round(job_rate(world, e2e_step), 2), "unit": "iter/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "pipelined": "next step's upload overlaps this step's compute"},
             # SH: the coefficient backward, and the regulariser's reduce and gradient kernels
             "gpu_launches": (kernels_per_step(stats, 1, H, W, ctx.get_tuning().schedule, decode=True) +
