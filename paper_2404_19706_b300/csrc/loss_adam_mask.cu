@@ -161,77 +161,123 @@ __global__ void __launch_bounds__(256) k_loss_finalize(Work w, int FT, int gshif
 // partial sums in a fixed grid, the last block (ticket) adds them in block order and
 // stores the loss and the gradient factor 2 w_reg / (10 n_t); the second kernel adds the
 // gradient.
+// The transparent-Gaussian regulariser: every row's values are loaded with its opacity (no
+// load waits on the opacity test), the block sums go through warp shuffles, and the last
+// block sums the per-block partials with all its threads.
+__device__ __forceinline__ float reg_d2(const RegArgs &a, int64_t k) {
+  float d2 = 0.f;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const float dm = a.means[3 * k + r] - a.means0[3 * k + r], ds = a.scales[3 * k + r] - a.scales0[3 * k + r];
+    d2 = fmaf(dm, dm, fmaf(ds, ds, d2));
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const float dq = a.quats[4 * k + r] - a.quats0[4 * k + r];
+    d2 = fmaf(dq, dq, d2);
+  }
+  return d2;
+}
+
+// Sums of two values over the block (result in every thread); s holds 2 x 8 floats.
+__device__ __forceinline__ float2 block_sum2(float x, float y, float *s) {
+  for (int o = 16; o > 0; o >>= 1) {
+    x += __shfl_xor_sync(0xffffffffu, x, o);
+    y += __shfl_xor_sync(0xffffffffu, y, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    s[wid] = x;
+    s[8 + wid] = y;
+  }
+  __syncthreads();
+  float2 r = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    r.x += s[k];
+    r.y += s[8 + k];
+  }
+  return r;
+}
+
 __global__ void __launch_bounds__(256) k_reg_reduce(RegArgs a, float *__restrict__ loss_out) {
   grid_dep_wait();
-  __shared__ float s_t[2][256];
+  __shared__ float s_w[16];
   __shared__ int s_last;
   float sum = 0.f, cnt = 0.f;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.nu; k += (int64_t)gridDim.x * blockDim.x) {
-    if (!(a.opacity[k] < a.alpha_split)) continue;
-    float d2 = 0.f;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  constexpr int U = 4;  // rows a thread has in flight
+  for (int64_t k0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k0 < a.nu; k0 += U * stride) {
+    bool t[U];
+    float d2[U];
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      const float dm = a.means[3 * k + r] - a.means0[3 * k + r], ds = a.scales[3 * k + r] - a.scales0[3 * k + r];
-      d2 = fmaf(dm, dm, fmaf(ds, ds, d2));
+    for (int u = 0; u < U; ++u) {
+      const int64_t k = k0 + u * stride;
+      t[u] = k < a.nu && a.opacity[k] < a.alpha_split;
+      d2[u] = k < a.nu ? reg_d2(a, k) : 0.f;
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const float dq = a.quats[4 * k + r] - a.quats0[4 * k + r];
-      d2 = fmaf(dq, dq, d2);
+    for (int u = 0; u < U; ++u) {
+      sum += t[u] ? d2[u] : 0.f;
+      cnt += t[u] ? 1.f : 0.f;
     }
-    sum += d2;
-    cnt += 1.f;
   }
-  s_t[0][threadIdx.x] = sum;
-  s_t[1][threadIdx.x] = cnt;
-  __syncthreads();
-  for (int stride = 128; stride > 0; stride >>= 1) {
-    if ((int)threadIdx.x < stride) {
-      s_t[0][threadIdx.x] += s_t[0][threadIdx.x + stride];
-      s_t[1][threadIdx.x] += s_t[1][threadIdx.x + stride];
-    }
-    __syncthreads();
-  }
+  const float2 blk = block_sum2(sum, cnt, s_w);
   if (threadIdx.x == 0) {
-    a.part[2 * blockIdx.x] = s_t[0][0];
-    a.part[2 * blockIdx.x + 1] = s_t[1][0];
+    a.part[2 * blockIdx.x] = blk.x;
+    a.part[2 * blockIdx.x + 1] = blk.y;
   }
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) s_last = atomicAdd(a.done, 1u) == gridDim.x - 1;
   __syncthreads();
-  if (!s_last || threadIdx.x != 0) return;
+  if (!s_last) return;
   __threadfence();
   float tot = 0.f, n = 0.f;
-  for (int b = 0; b < (int)gridDim.x; ++b) {
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
     tot += __ldcg(a.part + 2 * b);
     n += __ldcg(a.part + 2 * b + 1);
   }
-  const float denom = 10.f * n;
-  *loss_out = n > 0.f ? a.w_reg * tot / denom : 0.f;
-  *a.scale = n > 0.f ? 2.f * a.w_reg / denom : 0.f;
-  *a.done = 0u;
+  const float2 all = block_sum2(tot, n, s_w);
+  if (threadIdx.x == 0) {
+    const float denom = 10.f * all.y;
+    *loss_out = all.y > 0.f ? a.w_reg * all.x / denom : 0.f;
+    *a.scale = all.y > 0.f ? 2.f * a.w_reg / denom : 0.f;
+    *a.done = 0u;
+  }
 }
 
 __global__ void __launch_bounds__(256) k_reg_grad(RegArgs a) {
   grid_dep_wait();
   const float sc = *a.scale;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.nu; k += (int64_t)gridDim.x * blockDim.x) {
-    if (!(a.opacity[k] < a.alpha_split)) continue;
+    const bool t = a.opacity[k] < a.alpha_split;
+    float dm[3], ds[3], dq[4];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-      a.g_means[3 * k + r] += sc * (a.means[3 * k + r] - a.means0[3 * k + r]);
-      a.g_scales[3 * k + r] += sc * (a.scales[3 * k + r] - a.scales0[3 * k + r]);
+      dm[r] = a.means[3 * k + r] - a.means0[3 * k + r];
+      ds[r] = a.scales[3 * k + r] - a.scales0[3 * k + r];
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) a.g_quats[4 * k + r] += sc * (a.quats[4 * k + r] - a.quats0[4 * k + r]);
+    for (int r = 0; r < 4; ++r) dq[r] = a.quats[4 * k + r] - a.quats0[4 * k + r];
+    if (!t) continue;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      a.g_means[3 * k + r] += sc * dm[r];
+      a.g_scales[3 * k + r] += sc * ds[r];
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) a.g_quats[4 * k + r] += sc * dq[r];
   }
 }
 
 void launch_transparent_reg(const RegArgs &a, float *loss_out, cudaStream_t s) {
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(kLossBlocks, (a.nu + 255) / 256));
   launch(k_reg_reduce, blocks, 256, 0, s, a, loss_out);
-  launch(k_reg_grad, blocks, 256, 0, s, a);
+  // one row a thread: the rows' loads all start at once
+  const int64_t rows = (a.nu + 255) / 256;
+  launch(k_reg_grad, (unsigned)std::max<int64_t>(1, rows), 256, 0, s, a);
 }
 
 void launch_loss_finalize(const Work &w, int FT, int gshift, int C, float w_c, float w_d, float *loss_out,
