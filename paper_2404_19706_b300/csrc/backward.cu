@@ -684,74 +684,105 @@ __global__ void __launch_bounds__(256) k_sh_backward(GaussPtrs g, Work w, int F,
                                                      float *__restrict__ g_colors, int accumulate) {
   grid_dep_wait();
   constexpr int G2 = 16;  // C = 3
+  constexpr int kChunk = 1024;  // unstable Gaussians a CTA sorts out at once
+  __shared__ int s_k[kChunk], s_i[kChunk];
+  __shared__ int s_n;
   const int64_t nu = (int64_t)w.counters[kNumUnstable];
   const int64_t N = g.n;
   const int lane = threadIdx.x & 31, t = lane & 3, q0 = lane & ~3;
-  const unsigned gmask = 0xfu << q0;  // the 4 lanes of this Gaussian
+  const unsigned gmask = 0xfu << q0;  // the 4 lanes of a Gaussian
   const int deg = g.sh_degree, K = (deg + 1) * (deg + 1), width = 3 * K;
-  const int64_t ngroups = (int64_t)gridDim.x * (blockDim.x >> 2);
-  for (int64_t kk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2; kk < nu; kk += ngroups) {
-    const int64_t i = w.ids[kk];
-    const int r = (g.u_means != nullptr) ? w.rank[i] : -1;
-    const float *pm = r >= 0 ? g.u_means + 3 * (int64_t)r : g.means + 3 * i;
-    const float p[3] = {pm[0], pm[1], pm[2]};
-    const float *coef = color_ptr(g, w.rank, i);
-    float c[4][3], acc[4][3];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int k = 4 * t + j;
-#pragma unroll
-      for (int cc = 0; cc < 3; ++cc) {
-        c[j][cc] = k < K ? coef[3 * k + cc] : 0.f;
-        acc[j][cc] = 0.f;
+  // Most unstable Gaussians have no row in any frame.  A CTA takes a contiguous chunk of
+  // compact indices: it zeroes the chunk's coefficient rows with coalesced stores (unless
+  // accumulating) and lists the Gaussians with a row, then 4 lanes per listed Gaussian run
+  // the chain rule, so the heavy code runs on full warps.
+  for (int64_t c0 = (int64_t)blockIdx.x * kChunk; c0 < nu; c0 += (int64_t)gridDim.x * kChunk) {
+    const int64_t c1 = c0 + kChunk < nu ? c0 + kChunk : nu;
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    for (int64_t kk = c0 + threadIdx.x; kk < c1; kk += blockDim.x) {
+      const int64_t i = w.ids[kk];
+      uint32_t any = 0u;  // all frames' flags are loaded (no early exit), so the loads overlap
+      for (int f = 0; f < F; ++f) any |= w.ntiles[(int64_t)f * N + i];
+      if (any != 0u) {
+        const int slot = atomicAdd(&s_n, 1);
+        s_k[slot] = (int)kk;
+        s_i[slot] = (int)i;
       }
     }
-    float gpos[3] = {0.f, 0.f, 0.f};
-    for (int f = 0; f < F; ++f) {
-      if (w.ntiles[(int64_t)f * N + i] == 0u) continue;  // the same for the whole group
-      const float *row = w.grad2d + ((int64_t)f * N + kk) * G2 + kG2Col;
-      const float gc0 = row[0], gc1 = row[1], gc2 = row[2];
-      const DevCam &cam = w.cams[f];
-      const float dx = p[0] - cam.t[0], dy = p[1] - cam.t[1], dz = p[2] - cam.t[2];
-      const float il = 1.f / sqrtf(dx * dx + dy * dy + dz * dz);
-      const float x = dx * il, y = dy * il, z = dz * il;
-      float Y[kShMax];
-      sh_basis(deg, x, y, z, Y);
-      float st[4];
+    if (!accumulate) {
+      float *z = g_colors + (int64_t)width * c0;
+      const int64_t nz = (int64_t)width * (c1 - c0);
+      for (int64_t e = threadIdx.x; e < nz; e += blockDim.x) z[e] = 0.f;
+    }
+    __syncthreads();
+    const int nv = s_n;
+    for (int j0 = 0; j0 < nv; j0 += (int)blockDim.x / 4) {
+      const int jv = j0 + ((int)threadIdx.x >> 2);
+      if (jv >= nv) continue;  // whole groups of 4 lanes skip together
+      const int64_t kk = s_k[jv], i = s_i[jv];
+      float *out = g_colors + (int64_t)width * kk;
+      const int r = (g.u_means != nullptr) ? w.rank[i] : -1;
+      const float *pm = r >= 0 ? g.u_means + 3 * (int64_t)r : g.means + 3 * i;
+      const float p[3] = {pm[0], pm[1], pm[2]};
+      const float *coef = color_ptr(g, w.rank, i);
+      float c[4][3], acc[4][3];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        float yk = 0.f;
+        const int k = 4 * t + j;
 #pragma unroll
-        for (int q = 0; q < kShMax; ++q) yk = q == 4 * t + j ? Y[q] : yk;
-        acc[j][0] = fmaf(gc0, yk, acc[j][0]);
-        acc[j][1] = fmaf(gc1, yk, acc[j][1]);
-        acc[j][2] = fmaf(gc2, yk, acc[j][2]);
-        st[j] = gc0 * c[j][0] + gc1 * c[j][1] + gc2 * c[j][2];
+        for (int cc = 0; cc < 3; ++cc) {
+          c[j][cc] = k < K ? coef[3 * k + cc] : 0.f;
+          acc[j][cc] = 0.f;
+        }
       }
-      float sk[kShMax];
+      float gpos[3] = {0.f, 0.f, 0.f};
+      for (int f = 0; f < F; ++f) {
+        if (w.ntiles[(int64_t)f * N + i] == 0u) continue;  // the same for the 4 lanes
+        const float *row = w.grad2d + ((int64_t)f * N + kk) * G2 + kG2Col;
+        const float gc0 = row[0], gc1 = row[1], gc2 = row[2];
+        const DevCam &cam = w.cams[f];
+        const float dx = p[0] - cam.t[0], dy = p[1] - cam.t[1], dz = p[2] - cam.t[2];
+        const float il = 1.f / sqrtf(dx * dx + dy * dy + dz * dz);
+        const float x = dx * il, y = dy * il, z = dz * il;
+        float Y[kShMax];
+        sh_basis(deg, x, y, z, Y);
+        float st[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+        for (int j = 0; j < 4; ++j) {
+          float yk = 0.f;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) sk[4 * q + j] = __shfl_sync(gmask, st[j], q0 + q);
-      float gx, gy, gz;
-      sh_dir_grad(deg, x, y, z, sk, gx, gy, gz);
-      const float dot = gx * x + gy * y + gz * z;
-      gpos[0] += (gx - dot * x) * il;
-      gpos[1] += (gy - dot * y) * il;
-      gpos[2] += (gz - dot * z) * il;
+          for (int q = 0; q < kShMax; ++q) yk = q == 4 * t + j ? Y[q] : yk;
+          acc[j][0] = fmaf(gc0, yk, acc[j][0]);
+          acc[j][1] = fmaf(gc1, yk, acc[j][1]);
+          acc[j][2] = fmaf(gc2, yk, acc[j][2]);
+          st[j] = gc0 * c[j][0] + gc1 * c[j][1] + gc2 * c[j][2];
+        }
+        float sk[kShMax];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) sk[4 * q + j] = __shfl_sync(gmask, st[j], q0 + q);
+        float gx, gy, gz;
+        sh_dir_grad(deg, x, y, z, sk, gx, gy, gz);
+        const float dot = gx * x + gy * y + gz * z;
+        gpos[0] += (gx - dot * x) * il;
+        gpos[1] += (gy - dot * y) * il;
+        gpos[2] += (gz - dot * z) * il;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int k = 4 * t + j;
+        if (k < K)
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc) out[3 * k + cc] = accumulate ? out[3 * k + cc] + acc[j][cc] : acc[j][cc];
+      }
+      if (t == 0) {
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) g_means[3 * kk + cc] += gpos[cc];
+      }
     }
-    float *out = g_colors + (int64_t)width * kk;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int k = 4 * t + j;
-      if (k < K)
-#pragma unroll
-        for (int cc = 0; cc < 3; ++cc) out[3 * k + cc] = accumulate ? out[3 * k + cc] + acc[j][cc] : acc[j][cc];
-    }
-    if (t == 0) {
-#pragma unroll
-      for (int cc = 0; cc < 3; ++cc) g_means[3 * kk + cc] += gpos[cc];
-    }
+    __syncthreads();
   }
 }
 
