@@ -382,6 +382,12 @@ def roofline_of(per_launch, alg, tuning=None, workload=None, extra_kinds=()):
             "alg_bytes_per_launch": int(alg[dom]), "ms_per_launch": round(per_launch[dom], 5)}, pk
 
 
+def scan_emit_launches(ft):
+    """The tile scan with the scatter into the buckets: one kernel up to 8,192 tiles, else the
+    three-kernel scan and a scatter."""
+    return 1 if ft <= 8192 else 4
+
+
 DEPTH_SCALE = 5000.0  # 16-bit sensor depth in 1/5000 m (the unit common RGB-D datasets store)
 
 
@@ -403,18 +409,19 @@ FRAME_NOTE = ("RGB-D frame: 8-bit RGB + 16-bit depth (1/5000 m), decoded on the 
 
 def kernels_per_step(stats, F, H, W, schedule, per_frame_calls=1, decode=False):
     """Kernels one masked step launches.  Per forward call of F frames: tile mask, cull,
-    project, the mask grid's scan (1 kernel, 3 when its tiles outnumber one scan block), emit,
-    cover, a render-grid tile-mask pass when the render tile is not 16 x 16, bin, the render
-    grid's scan, emit, sort and composite, plus the loss finalize unless the persistent
-    schedule's forward does it; backward 2 per call; the frame decode per call when the step
-    reads a sensor frame; then Adam 1 (the renderer reads the optimiser's compact arrays, so
-    nothing is scattered back during the window)."""
+    project, the mask grid's scan with the scatter into its buckets (1 kernel; 3 + a scatter
+    when its tiles outnumber one scan block), cover, a render-grid tile-mask pass when the
+    render tile is not 16 x 16, bin, the render grid's scan and scatter, sort and composite,
+    plus the loss finalize unless the persistent schedule's forward does it; backward 2 per
+    call; the frame decode per call when the step reads a sensor frame; then Adam 1 (the
+    renderer reads the optimiser's compact arrays, so nothing is scattered back during the
+    window)."""
     tw, th = stats["tile_w"], stats["tile_h"]
-    scan = lambda ft: 1 if ft <= 8192 else 3
     ft_mask = F * ((W + 15) // 16) * ((H + 15) // 16)
     ft_render = F * ((W + tw - 1) // tw) * ((H + th - 1) // th)
     extra = 0 if (tw, th) == (16, 16) else 1
-    fwd = 3 + scan(ft_mask) + 2 + extra + 1 + scan(ft_render) + 3 + (0 if schedule == 1 else 1)
+    fwd = 3 + scan_emit_launches(ft_mask) + 1 + extra + 1 + scan_emit_launches(ft_render) + 2 + \
+        (0 if schedule == 1 else 1)
     return per_frame_calls * (fwd + 2 + (1 if decode else 0)) + 1
 
 
@@ -961,13 +968,12 @@ class BoundGlobalStep(Replayable):
 
 
 def global_kernels_per_step(F, H, W, tuning):
-    """Kernels of one global step: forward (tile mask, cull, project, scan (3 when the tiles
-    outnumber one scan block), emit, sort, composite), selection (3 histogram passes, tie
-    counts, mark), narrowing with the loss partials (1, plus the 3 queue kernels of the
-    persistent schedule) and the loss finalize (1), backward (2) and Adam (1)."""
+    """Kernels of one global step: forward (tile mask, cull, project, scan with the scatter into
+    the buckets, sort, composite), selection (3 histogram passes, tie counts, mark),
+    narrowing with the loss partials (1, plus the 3 queue kernels of the persistent schedule)
+    and the loss finalize (1), backward (2) and Adam (1)."""
     FT = F * ((W + tuning.tile_w - 1) // tuning.tile_w) * ((H + tuning.tile_h - 1) // tuning.tile_h)
-    scan = 1 if FT <= 8192 else 3
-    return (6 + scan) + 5 + (1 + (3 if tuning.schedule == 1 else 0)) + 1 + 2 + 1
+    return (5 + scan_emit_launches(FT)) + 5 + (1 + (3 if tuning.schedule == 1 else 0)) + 1 + 2 + 1
 
 
 def oracle_global_rate(scene, cams, tcol, tdep, frac, budget_px=48):
@@ -1248,7 +1254,7 @@ def run_adding(args, kw=ADDING):
     if rank != 0:
         return None
     FT = ((W + tuning.tile_w - 1) // tuning.tile_w) * ((H + tuning.tile_h - 1) // tuning.tile_h)
-    launches = 1 + 6 + (1 if FT <= 8192 else 3) + 3  # decode, forward (no index pass: precomputed), adding
+    launches = 1 + 5 + scan_emit_launches(FT) + 3  # decode, forward (no index pass: precomputed), adding
     fixed = "fixed by --tuning" if args.tuning else "off (--no-tune)"
     out = {
         "metric": ADD_METRIC, "value": round(1e3 / ms_step, 2), "unit": "frames/s", "n_gpus": world,
@@ -1440,7 +1446,7 @@ def run_state(args, kw=STATE):
     if rank != 0:
         return None
     FT = ((W + tuning.tile_w - 1) // tuning.tile_w) * ((H + tuning.tile_h - 1) // tuning.tile_h)
-    launches = 1 + 6 + (1 if FT <= 8192 else 3) + 2 + 1 + 3 + 1  # decode, forward, errors, states, compaction, fusion
+    launches = 1 + 5 + scan_emit_launches(FT) + 2 + 1 + 3 + 1  # decode, forward, errors, states, compaction, fusion
     fixed = "fixed by --tuning" if args.tuning else "off (--no-tune)"
     alg_step = sum(alg.values()) + int(nu) * (3 * 4 * (11 + C) + 12)  # + the fusion's reads and writes
     out = {

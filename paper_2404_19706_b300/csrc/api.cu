@@ -385,8 +385,7 @@ rtg_status build_window_lists(rtg_ctx *ctx) {
   *(volatile uint32_t *)ctx->winst_host = 0u;
   launch_tile_mask(fs, w, nullptr, T, c0.tiles_x, tn.tws, tn.ths, true, false, (long long)gp.n_unstable, s);
   launch_bin(w, gp.n, T, ctx->cap.max_pairs, false, true, s);
-  launch_scan_tiles(w, FT, ctx->cap.max_pairs, -1, nullptr, s);
-  launch_emit(w, s);
+  launch_scan_tiles(w, FT, ctx->cap.max_pairs, -1, nullptr, s, true);
   launch_sort_tiles(w, FT, tn.sort_bits, tn.sort_rank_max, StableLists{nullptr, nullptr, nullptr}, ctx->win_skeys,
                     tn.tws + tn.ths <= 6, s);
   cudaMemcpyAsync(ctx->win_scount, w.tile_count, (size_t)FT * 4, cudaMemcpyDeviceToDevice, s);
@@ -662,8 +661,7 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
     }
     {
       ProfScope ps(ctx, kPUnstableMask, s);  // coverage pass: scan, scatter, cover + tile rule
-      launch_scan_tiles(w, F * TM, ctx->cap.max_pairs, -1, nullptr, s);
-      launch_emit(w, s);
+      launch_scan_tiles(w, F * TM, ctx->cap.max_pairs, -1, nullptr, s, true);
       launch_mask_cover_tiles(w, P, n, F, TM, gp.C, mask_out, same_grid ? kCoverFusedSame : kCoverFusedOther, s);
       if (!same_grid)
         launch_tile_mask(fs, w, mask_out, T, c0.tiles_x, tn.tws, tn.ths, false, true, -1ll, s);
@@ -689,12 +687,8 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
     }
   }
   {
-    ProfScope ps(ctx, kPScanTiles, s);
-    launch_scan_tiles(w, FT, ctx->cap.max_pairs, tn.schedule == 1 ? tn.gshift() : -1, sl.count, s);
-  }
-  {
-    ProfScope ps(ctx, kPEmit, s);
-    launch_emit(w, s);
+    ProfScope ps(ctx, kPScanTiles, s);  // with the scatter into the buckets (k_emit above 8,192 tiles)
+    launch_scan_tiles(w, FT, ctx->cap.max_pairs, tn.schedule == 1 ? tn.gshift() : -1, sl.count, s, true);
   }
   {
     ProfScope ps(ctx, kPSortTiles, s);
@@ -1220,8 +1214,7 @@ rtg_status rtg_unstable_mask(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, co
   if (gp.u_means != nullptr && gp.rank_map == nullptr)
     if ((st = rank_pass(ctx, gp.unstable, gp.n, w.rank, w.ids, w.counters, nullptr, s)) != RTG_OK) return st;
   launch_project(gp, w, P, F, T, kProjMask, kCullUnstable, ctx->cap.max_pairs, s);
-  launch_scan_tiles(w, F * T, ctx->cap.max_pairs, -1, nullptr, s);
-  launch_emit(w, s);
+  launch_scan_tiles(w, F * T, ctx->cap.max_pairs, -1, nullptr, s, true);
   launch_mask_cover_tiles(w, P, gp.n, F, T, gp.C, mask, kCoverPlain, s);
   ctx->last_stream = s;
   return check_launch(ctx, "unstable_mask");

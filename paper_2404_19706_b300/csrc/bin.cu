@@ -493,11 +493,19 @@ __device__ __forceinline__ uint32_t list_len(const Work &w, const uint32_t *extr
 
 // Thread t owns tiles [t * per, t * per + per) (per <= kScanSingleMax / 1024): their counts
 // are loaded once, all at once, and kept in registers for the offsets and the queue.
+// kEmit: the scatter of the staged pairs into their buckets is fused in.  Every CTA scans
+// the tiles itself into shared memory (the scan is small and deterministic, so all CTAs
+// agree) and scatters its share of the pairs from there; CTA 0 alone writes the offsets,
+// counters and item queue.  No CTA waits on another.
 constexpr int kScanPer = kScanSingleMax / 1024;
 
+template <bool kEmit>
 __global__ void __launch_bounds__(1024) k_scan_tiles(Work w, int FT, int64_t max_pairs, int gshift,
                                                      const uint32_t *__restrict__ extra) {
   grid_dep_wait();
+  extern __shared__ uint32_t s_off[];  // kEmit: the FT + 1 bucket offsets
+  __shared__ unsigned long long s_total;
+  const bool lead = blockIdx.x == 0;
   __shared__ unsigned long long s_warp[32];
   __shared__ uint32_t s_wmax[32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -555,21 +563,37 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Work w, int FT, int64_t max
   unsigned long long run = (wid > 0 ? s_warp[wid - 1] : 0ull) + inc - local;
 #pragma unroll
   for (int u = 0; u < kScanPer; ++u) {
-    if (b + u < e) w.tile_offset[b + u] = (uint32_t)run;
+    if (b + u < e) {
+      if (lead) w.tile_offset[b + u] = (uint32_t)run;
+      if (kEmit) s_off[b + u] = (uint32_t)run;
+    }
     run += len[u];
   }
   if (tid == 1023) {  // the last thread's running offset is the pair total
     const unsigned long long total = run;
-    w.tile_offset[FT] = (uint32_t)total;
-    w.counters[kPairs] = total;
-    w.counters[kMaskedPix] = s_pix[0];
-    w.counters[kMaxTilePairs] = s_wmax[0];
-    if (total > (unsigned long long)max_pairs || total > 0xffffffffull) {
-      w.counters[kSkip] = 1ull;
-      atomicCAS(w.status, 0u, (uint32_t)(int32_t)RTG_ERR_WORKSPACE);
+    s_total = total;
+    if (lead) {
+      w.tile_offset[FT] = (uint32_t)total;
+      w.counters[kPairs] = total;
+      w.counters[kMaskedPix] = s_pix[0];
+      w.counters[kMaxTilePairs] = s_wmax[0];
+      if (total > (unsigned long long)max_pairs || total > 0xffffffffull) {
+        w.counters[kSkip] = 1ull;
+        atomicCAS(w.status, 0u, (uint32_t)(int32_t)RTG_ERR_WORKSPACE);
+      }
     }
   }
-  if (gshift < 0) return;
+  if (kEmit) {
+    __syncthreads();
+    if (s_total <= (unsigned long long)max_pairs && s_total <= 0xffffffffull) {
+      const int64_t npairs = (int64_t)w.counters[kStaged];
+      for (int64_t k = (int64_t)blockIdx.x * blockDim.x + tid; k < npairs; k += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 st = w.stage[k];
+        w.keys[(int64_t)s_off[st.x] + st.y] = ((unsigned long long)st.w << 32) | (unsigned long long)st.z;
+      }
+    }
+  }
+  if (gshift < 0 || !lead) return;
   // ---- item queue
   __shared__ uint32_t s_cls[kQueueClasses];
   for (int k = tid; k < kQueueClasses; k += 1024) s_cls[k] = 0u;
@@ -836,16 +860,22 @@ __global__ void __launch_bounds__(1024) k_scan_write(Work w, int FT, int gshift,
   }
 }
 
-void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, int gshift, const uint32_t *extra,
-                       cudaStream_t s) {
+void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, int gshift, const uint32_t *extra, cudaStream_t s,
+                       bool emit) {
   if (FT <= kScanSingleMax) {
-    launch(k_scan_tiles, 1, 1024, 0, s, w, FT, max_pairs, gshift, extra);
+    if (emit)  // one CTA per SM, each scattering its share of the pairs
+      launch(k_scan_tiles<true>, (unsigned)resident_grid((const void *)k_scan_tiles<true>, 1024,
+                                                         (size_t)(FT + 1) * 4),
+             1024, (size_t)(FT + 1) * 4, s, w, FT, max_pairs, gshift, extra);
+    else
+      launch(k_scan_tiles<false>, 1, 1024, 0, s, w, FT, max_pairs, gshift, extra);
     return;
   }
   const int B = (FT + kScanBlockTiles - 1) / kScanBlockTiles;  // <= 1024 (capacity check)
   launch(k_scan_part, B, 1024, 0, s, w, FT, gshift, extra, 0);
   launch(k_scan_bases, 1, 1024, 0, s, w, FT, max_pairs, gshift, B, 0);
   launch(k_scan_write, B, 1024, 0, s, w, FT, gshift, extra, 0);
+  if (emit) launch_emit(w, s);
 }
 
 void launch_requeue(const Work &w, int FT, int gshift, cudaStream_t s) {

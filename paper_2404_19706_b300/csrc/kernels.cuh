@@ -149,8 +149,10 @@ void launch_bin(const Work &w, int64_t N, int T, int64_t max_pairs, bool cands, 
 void launch_window_reset(const Work &w, cudaStream_t s);
 // gshift >= 0: also build the persistent schedule's item queue (2^gshift groups per tile).
 // extra != nullptr: tiles with masked pixels also hold extra[t] cached stable pairs.
-void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, int gshift, const uint32_t *extra,
-                       cudaStream_t s);
+// emit: also scatter the staged pairs into their buckets (fused into the scan when one CTA
+// scans all the tiles, else a k_emit launch after it).
+void launch_scan_tiles(const Work &w, int FT, int64_t max_pairs, int gshift, const uint32_t *extra, cudaStream_t s,
+                       bool emit = false);
 void launch_emit(const Work &w, cudaStream_t s);
 // Rebuilds the persistent schedule's queue from the current pixel counts, with each tile's
 // list length taken from the forward's offsets (which it leaves unchanged).
