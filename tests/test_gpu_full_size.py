@@ -99,14 +99,15 @@ def sample_masked(mask, k, rng):
 
 def test_config3_masked_step_1M_sampled():
     """1M Gaussians, 20% unstable in 3 blobs, 640x480, mask with the tile rule (the bench's
-    camera candidate), tuning 8x16 / batch 32 / persistent / ranking sort <= 256."""
+    camera candidate), the bench's tuning: 8x8 / batch 64 / persistent at 2 CTAs per SM /
+    ranking sort <= 512."""
     m = rtg()
     scene, layout = synth.room_scene(3000, 1_000_000)
     cams = synth.room_camera_candidates(3001, layout, 640, 480, 600.0)
     for _ in range(8):
         cam = next(cams)  # candidate 7
     scene.unstable = synth.flag_blobs(scene, [cam], 200_000, 3, seed=3000 + 100 + 7, n_in_view=1)
-    out = masked_forward(scene, [cam], m.Tuning(8, 16, 32, 1, 4, 8, 256), 24_000_000, 3)
+    out = masked_forward(scene, [cam], m.Tuning(8, 8, 64, 1, 2, 8, 512), 24_000_000, 3)
     cov = out["mask"][0].mean()
     assert 0.25 <= cov <= 0.40, cov
     pix = sample_masked(out["mask"][0], 48, np.random.default_rng(31))
@@ -116,12 +117,13 @@ def test_config3_masked_step_1M_sampled():
 
 def test_config4_keyframes_2M_sampled():
     """2M Gaussians on a 2x2 grid of rooms, 10% unstable in 8 blobs, 8 keyframes at
-    1200x680 in one call, tuning 16x16 / CTA per tile / ranking sort <= 512."""
+    1200x680 in one call, the bench's tuning: 8x16 / batch 32 / CTA per tile / ranking sort
+    <= 512."""
     m = rtg()
     scene, layout = synth.multiroom_scene(4000, 2_000_000)
     scene.unstable = synth.flag_blobs(scene, [], 200_000, 8, seed=4100, n_in_view=0)
     cams = [c for _, c in zip(range(8), synth.room_camera_candidates(4001, layout, 1200, 680, 600.0))]
-    out = masked_forward(scene, cams, m.Tuning(16, 16, 32, 0, 4, 8, 512), 48 << 20, 4)
+    out = masked_forward(scene, cams, m.Tuning(8, 16, 32, 0, 4, 8, 512), 48 << 20, 4)
     rng = np.random.default_rng(41)
     frames = [f for f in range(8) if out["mask"][f].sum() >= 16]
     assert len(frames) >= 3
@@ -133,13 +135,14 @@ def test_config4_keyframes_2M_sampled():
 
 def test_config5_large_floor_5M_32_keyframes_8_channels_sampled():
     """5M Gaussians on a 30x20x3 m floor (5x4 rooms), 90% opaque, 8 colour channels, 10%
-    unstable, 32 keyframes at 1200x680 in one call (default tuning)."""
+    unstable, 32 keyframes at 1200x680 in one call, the bench's tuning: 8x8 / batch 32 /
+    persistent at 2 CTAs per SM / ranking sort <= 512."""
     m = rtg()
     scene, layout = synth.room_scene(5000, 5_000_000, channels=8, opaque_frac=0.9, size=(30.0, 20.0, 3.0),
                                      grid=(5, 4), n_boxes=60)
     scene.unstable = synth.flag_blobs(scene, [], 500_000, 24, seed=5100, n_in_view=0)
     cams = [c for _, c in zip(range(32), synth.room_camera_candidates(5001, layout, 1200, 680, 600.0))]
-    out = masked_forward(scene, cams, m.Tuning(), 128 << 20, 5)
+    out = masked_forward(scene, cams, m.Tuning(8, 8, 32, 1, 2, 8, 512), 128 << 20, 5)
     assert out["stats"]["masked_pixels"] > 0
     rng = np.random.default_rng(51)
     frames = [f for f in range(32) if out["mask"][f].sum() >= 8]
@@ -148,3 +151,74 @@ def test_config5_large_floor_5M_32_keyframes_8_channels_sampled():
         pix = sample_masked(out["mask"][f], 8, rng)
         n = check_pixels(scene, cams[f], out["color"][f], out["depth"][f], out["alpha"][f], out["index"][f], pix)
         assert n >= 7
+
+
+GROUPS = ("means", "scales", "quats", "opacity", "colors")
+
+
+def test_config3_gradients_sampled_pixels():
+    """The backward at full size, in the bench's tuning: the 1M-Gaussian config-3 scene with
+    the loss restricted to sampled masked pixels, against the FP64 oracle's analytic
+    gradient on the Gaussians that can reach those pixels; every other unstable Gaussian
+    must get exactly zero."""
+    m = rtg()
+    scene, layout = synth.room_scene(3000, 1_000_000)
+    cams = synth.room_camera_candidates(3001, layout, 640, 480, 600.0)
+    for _ in range(8):
+        cam = next(cams)  # candidate 7
+    scene.unstable = synth.flag_blobs(scene, [cam], 200_000, 3, seed=3000 + 100 + 7, n_in_view=1)
+    H, W = cam.height, cam.width
+    ctx = m.Context(max_gaussians=scene.n, max_width=W, max_height=H, max_pairs=24_000_000)
+    ctx.set_tuning(m.Tuning(8, 8, 64, 1, 2, 8, 512))
+    g = m.Gaussians.from_scene(scene)
+    mask = torch.zeros(1, H, W, dtype=torch.uint8, device="cuda")
+    m.unstable_mask(ctx, cam, g, m.RenderSettings(), mask)
+    rng = np.random.default_rng(77)
+    pix = sample_masked(mask[0].cpu().numpy(), 64, rng)
+    sub_idx = reach_subset(scene, cam, pix)
+    sub = scene.subset(sub_idx)
+    tc = rng.uniform(0.0, 1.0, (len(pix), 3))
+    td = rng.uniform(1.0, 5.0, len(pix))
+    # pixels whose gradient sits on a threshold (alpha_min, f_max, the hit test) are left out
+    pre = oracle.loss_and_grads(sub, cam, ST, pix, tc, td)
+    keep = ~pre["grad_borderline"]
+    assert keep.sum() >= 56
+    pix, tc, td = pix[keep], tc[keep], td[keep]
+    ref = oracle.loss_and_grads(sub, cam, ST, pix, tc, td)
+    # the GPU step on exactly those pixels
+    ms = torch.zeros(1, H, W, dtype=torch.uint8, device="cuda")
+    tcol = torch.zeros(1, 3, H, W, device="cuda")
+    tdep = torch.zeros(1, H, W, device="cuda")
+    xs, ys = torch.as_tensor(pix[:, 0]).cuda(), torch.as_tensor(pix[:, 1]).cuda()
+    ms[0, ys, xs] = 1
+    tcol[0, :, ys, xs] = torch.as_tensor(tc.T, dtype=torch.float32).cuda()
+    tdep[0, ys, xs] = torch.as_tensor(td, dtype=torch.float32).cuda()
+    color = torch.zeros(1, 3, H, W, device="cuda")
+    depth = torch.full((1, H, W), -1.0, device="cuda")
+    alpha = torch.zeros(1, H, W, device="cuda")
+    m.render_forward(ctx, cam, g, ms, m.RenderSettings(), color, depth, alpha)
+    loss = torch.zeros(3, device="cuda")
+    dc, dd = torch.zeros_like(color), torch.zeros_like(depth)
+    m.l1_loss(ctx, color, depth, tcol, tdep, ms, 1.0, 1.0, loss, dc, dd)
+    nu = int(scene.unstable.sum())
+    grads = [torch.zeros(nu, 3, device="cuda"), torch.zeros(nu, 3, device="cuda"), torch.zeros(nu, 4, device="cuda"),
+             torch.zeros(nu, device="cuda"), torch.zeros(nu, 3, device="cuda")]
+    m.render_backward(ctx, dc, dd, *grads)
+    torch.cuda.synchronize()
+    assert m.get_status(ctx) == 0
+    assert float(loss[0]) == pytest.approx(ref["loss"], rel=1e-4)
+    got = {k: t.cpu().numpy().astype(np.float64) for k, t in zip(GROUPS, grads)}
+    # compact rank of every unstable Gaussian of the full scene; the subset's, in its order
+    rank = np.cumsum(scene.unstable.astype(np.int64)) - 1
+    sub_unstable = sub_idx[scene.unstable[sub_idx] != 0]
+    rows = rank[sub_unstable]
+    others = np.ones(nu, dtype=bool)
+    others[rows] = False
+    for k in GROUPS:
+        r = ref["grads"][k].reshape(len(rows), -1)
+        gg = got[k].reshape(nu, -1)[rows]
+        scale = np.abs(r).max()
+        assert scale > 0, k
+        assert np.linalg.norm(gg - r) <= 1e-3 * np.linalg.norm(r), (k, np.linalg.norm(gg - r) / np.linalg.norm(r))
+        assert (np.abs(gg - r) <= 1e-3 * np.abs(r) + 1e-3 * scale).all(), (k, np.abs(gg - r).max(), scale)
+        assert not got[k].reshape(nu, -1)[others].any(), k  # no influence on these pixels
