@@ -397,7 +397,9 @@ __global__ void __launch_bounds__(256) k_backward_queue(Work w, Prm prm, int64_t
   const uint32_t nitems = (uint32_t)w.counters[kItems];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t nwarps = gridDim.x * 8u;
-  uint32_t it = blockIdx.x * 8u + (uint32_t)wid;
+  // the first items (the longest lists) go one to a CTA, round robin, so that they do not
+  // share the issue slots of a few SMs
+  uint32_t it = (uint32_t)wid * gridDim.x + blockIdx.x;
   while (it < nitems) {
     const uint32_t item = w.items[it];
     backward_group<C, B>(w, prm, N, T, (int)(item >> 3), (int)(item & 7u), s_rec[wid], s_jr[wid],

@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kMaxTilePix, fwd_min_ctas<C, B>()) k_forward(W
   forward_group<C, B>(w, prm, N, T, tile, wid, s_rec[wid], s_j[wid], out);
 }
 
-// Schedule 1: persistent warps.  Warp k of the grid starts with item k; later items come
+// Schedule 1: persistent warps.  Each warp starts with one of the first items; later items come
 // from a shared counter, so warps that finish early take the remaining work.  The queue
 // holds the longest lists first.
 template <int C, int B>
@@ -262,7 +262,9 @@ __global__ void __launch_bounds__(256, fwd_min_ctas<C, B>()) k_forward_queue(Wor
   const uint32_t nitems = (uint32_t)w.counters[kItems];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t nwarps = gridDim.x * 8u;
-  uint32_t it = blockIdx.x * 8u + (uint32_t)wid;
+  // the first items (the longest lists) go one to a CTA, round robin, so that they do not
+  // share the issue slots of a few SMs
+  uint32_t it = (uint32_t)wid * gridDim.x + blockIdx.x;
   while (it < nitems) {
     const uint32_t item = w.items[it];
     forward_group<C, B>(w, prm, N, T, (int)(item >> 3), (int)(item & 7u), s_rec[wid], s_j[wid], out,
