@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(kMaxTilePix) k_backward(Work w, Prm prm, int64
 // Schedule 1: persistent warps over the forward's item queue (its own counter).
 template <int C, int B>
 __global__ void __launch_bounds__(256) k_backward_queue(Work w, Prm prm, int64_t N, int T,
-                                                                              BwdIn in) {
+                                                                              BwdIn in, int spread) {
   grid_dep_wait();
   constexpr int H4 = (C <= 4) ? 3 : 4;
   __shared__ float4 s_rec[8][H4][B];
@@ -397,9 +397,7 @@ __global__ void __launch_bounds__(256) k_backward_queue(Work w, Prm prm, int64_t
   const uint32_t nitems = (uint32_t)w.counters[kItems];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t nwarps = gridDim.x * 8u;
-  // the first items (the longest lists) go one to a CTA, round robin, so that they do not
-  // share the issue slots of a few SMs
-  uint32_t it = (uint32_t)wid * gridDim.x + blockIdx.x;
+  uint32_t it = first_item(w, wid, spread);
   while (it < nitems) {
     const uint32_t item = w.items[it];
     backward_group<C, B>(w, prm, N, T, (int)(item >> 3), (int)(item & 7u), s_rec[wid], s_jr[wid],
@@ -792,7 +790,8 @@ template <int C, int B>
 static void launch_backward_cb(const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn,
                                const BwdIn &in, cudaStream_t s) {
   if (tn.schedule == 1)
-    launch(k_backward_queue<C, B>, tn.num_sms * tn.ctas_per_sm, 256, 0, s, w, prm, N, T, in);
+    launch(k_backward_queue<C, B>, tn.num_sms * tn.ctas_per_sm, 256, 0, s, w, prm, N, T, in,
+           tn.ctas_per_sm <= 2 ? 1 : 0);
   else
     launch(k_backward<C, B>, F * T, 1 << (tn.tws + tn.ths), 0, s, w, prm, N, T, in);
 }

@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kMaxTilePix, fwd_min_ctas<C, B>()) k_forward(W
 // holds the longest lists first.
 template <int C, int B>
 __global__ void __launch_bounds__(256, fwd_min_ctas<C, B>()) k_forward_queue(Work w, Prm prm, int64_t N, int T,
-                                                                            FwdOut out) {
+                                                                            FwdOut out, int spread) {
   grid_dep_wait();
   constexpr int H4 = (C <= 4) ? 3 : 4;
   __shared__ float4 s_rec[8][H4][B];
@@ -262,9 +262,7 @@ __global__ void __launch_bounds__(256, fwd_min_ctas<C, B>()) k_forward_queue(Wor
   const uint32_t nitems = (uint32_t)w.counters[kItems];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t nwarps = gridDim.x * 8u;
-  // the first items (the longest lists) go one to a CTA, round robin, so that they do not
-  // share the issue slots of a few SMs
-  uint32_t it = (uint32_t)wid * gridDim.x + blockIdx.x;
+  uint32_t it = first_item(w, wid, spread);
   while (it < nitems) {
     const uint32_t item = w.items[it];
     forward_group<C, B>(w, prm, N, T, (int)(item >> 3), (int)(item & 7u), s_rec[wid], s_j[wid], out,
@@ -304,7 +302,8 @@ template <int C, int B>
 static void launch_forward_cb(const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn,
                               const FwdOut &out, cudaStream_t s) {
   if (tn.schedule == 1)
-    launch(k_forward_queue<C, B>, tn.num_sms * tn.ctas_per_sm, 256, 0, s, w, prm, N, T, out);
+    launch(k_forward_queue<C, B>, tn.num_sms * tn.ctas_per_sm, 256, 0, s, w, prm, N, T, out,
+           tn.ctas_per_sm <= 2 ? 1 : 0);
   else
     launch(k_forward<C, B>, F * T, 1 << (tn.tws + tn.ths), 0, s, w, prm, N, T, out);
 }

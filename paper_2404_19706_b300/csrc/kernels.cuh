@@ -122,6 +122,22 @@ __device__ __forceinline__ unsigned long long block_reserve(unsigned long long *
   return r;
 }
 
+// First item of warp `wid` of a persistent 8-warp CTA.  The queue holds the longest lists
+// first and a tile's groups next to each other.  With `spread` (grids of at most two CTAs
+// an SM, where a CTA's warps are a quarter of the SM's or more) the first items go out a
+// tile at a time (P = a full tile's groups, up to 8), round robin over the CTAs, so that
+// the longest lists do not share the issue slots of a few SMs while the groups of a tile,
+// which read the same records, share a CTA: warp k of CTA b takes item
+// (k / P) * P * grid + P * b + k % P.  Otherwise (four or more CTAs an SM) CTA b takes
+// items 8b .. 8b + 7, neighbouring tiles of the queue, whose records overlap in L1.
+__device__ __forceinline__ uint32_t first_item(const Work &w, int wid, int spread) {
+  if (!spread) return blockIdx.x * 8u + (uint32_t)wid;
+  const int gs = w.cams[0].tws + w.cams[0].ths - 5;
+  const uint32_t P = 1u << (gs < 0 ? 0 : (gs > 3 ? 3 : gs));
+  const uint32_t k = (uint32_t)wid;
+  return (k / P) * P * gridDim.x + P * blockIdx.x + k % P;
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
