@@ -361,9 +361,9 @@ def alg_bytes(stats, N, F, H, W, Cc=C, Cw=None):
 # DRAM bytes (read + write) per launch of a kernel from one ncu capture of bench.py, keyed
 # by (workload, kernel, render tile, record batch, schedule); the roofline's `traffic` is
 # filled only when the run's workload, dominant kernel and tuning match a captured one of
-# the kernel as it is now.  Source and command: profiles/masked_step_1M_640x480_kernels.md.
+# the kernel as it is now.  Source and command: profiles/masked_step_1M_640x480_launches.md.
 NCU_TRAFFIC = {
-    ("masked-step", "backward", 8, 8, 64, 1): 19_194_112 + 0,  # k_backward_queue<3, 64> (current capture)
+    ("masked-step", "backward", 8, 8, 64, 1): 19_233_280,  # k_backward_queue<3, 64> (current capture)
 }
 
 
