@@ -120,6 +120,10 @@ typedef struct {
   int32_t status;         /* device status word (rtg_status) */
   int32_t max_tile_pairs; /* longest per-tile list */
   int32_t tile_w, tile_h; /* render tile of that forward (rtg_tuning) */
+  int64_t window_stable;  /* (frame, stable Gaussian) projections of the open window, made once
+                             by rtg_window_begin (0 without a window) */
+  int64_t window_pairs;   /* stable (Gaussian, tile) pairs in the window's cached sorted lists
+                             (0 without cached lists) */
 } rtg_stats;
 
 /* Launch configuration of the render path.  Section 3.1 rasterises by screen tiles but
@@ -470,7 +474,9 @@ rtg_status rtg_scatter_unstable(int64_t nu, int32_t C, const int32_t *ids, const
  * exits).  Larger n returns RTG_ERR_WORKSPACE without launching anything.  Outputs are as
  * for rtg_unstable_index: ids [nu] (device int32, ascending) and *nu_out (device int64).
  * The first call on each device looks up the scratch array's device address, so make it
- * before any stream capture.  Calls share that one array, so two calls that overlap on
+ * before any stream capture.  The address is kept per device ordinal for the life of the
+ * process: after cudaDeviceReset, or under a second driver context on the same device, it
+ * would be stale, so neither is supported.  Calls share that one array, so two calls that overlap on
  * the GPU (different streams, no ordering between them) race; order them on one stream.
  * Every scratch entry a call reads is written earlier in the same call, so nothing needs
  * clearing between calls. */
@@ -498,6 +504,19 @@ rtg_status rtg_profile_enable(rtg_ctx *ctx, int32_t on);
 int32_t rtg_profile_kinds(void);
 const char *rtg_profile_kind_name(int32_t kind);
 rtg_status rtg_profile_read(rtg_ctx *ctx, int64_t *launches, double *total_ms, int32_t n_kinds);
+
+/* Arithmetic-pipe throughput probe (no counterpart in the paper: it measures the device, so
+ * that the compositing kernels, which are bound by instruction issue rather than by HBM,
+ * can be set against a measured roof).  Launches one kernel that fills every SM of the
+ * current device (2,048 threads an SM, 8 independent dependency chains a thread) with
+ * `iters` x 32 instructions a thread of one kind: kind 0 FP32 fused multiply-add
+ * (counted as 2 flops), kind 1 the SFU base-2 exponential (ex2.approx, 1 op).  `out` is a
+ * device float array of at least 2,048 x (number of SMs) entries; the kernel never writes
+ * it in practice, but it must be valid.  *ops_out (HOST) receives the operations the
+ * launch performs; the caller times the launch with CUDA events on `stream`.  Errors:
+ * RTG_ERR_ARG for a bad kind, iters <= 0 or NULL pointers; RTG_ERR_CUDA if the launch
+ * fails. */
+rtg_status rtg_alu_probe(int32_t kind, int32_t iters, float *out, int64_t *ops_out, void *stream);
 
 /* Binning introspection of the last forward (for exactness tests): tile_offsets
  * [F*T+1] (uint32, T = ceil(W/tile_w)*ceil(H/tile_h) render tiles per frame under the

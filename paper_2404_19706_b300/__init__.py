@@ -38,6 +38,7 @@ from .api import (  # noqa: E402,F401
     narrow_pixels,
     profile_enable,
     profile_read,
+    alu_probe,
     render_backward,
     render_backward_l1,
     render_forward_l1,

@@ -50,7 +50,7 @@ class rtg_capacity(Structure):
 class rtg_stats(Structure):
     _fields_ = [("pairs", c_int64), ("fragments", c_int64), ("visible", c_int64), ("masked_pixels", c_int64),
                 ("n_unstable", c_int64), ("warp_records", c_int64), ("status", c_int32), ("max_tile_pairs", c_int32), ("tile_w", c_int32),
-                ("tile_h", c_int32)]
+                ("tile_h", c_int32), ("window_stable", c_int64), ("window_pairs", c_int64)]
 
 
 class rtg_tuning(Structure):
@@ -139,6 +139,7 @@ SIGNATURES = [
     ("rtg_profile_kinds", c_int32, []),
     ("rtg_profile_kind_name", c_char_p, [c_int32]),
     ("rtg_profile_read", c_int32, [c_void_p, POINTER(c_int64), POINTER(ctypes.c_double), c_int32]),
+    ("rtg_alu_probe", c_int32, [c_int32, c_int32, c_void_p, POINTER(c_int64), c_void_p]),
     ("rtg_debug_binning", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
 ]
 

@@ -721,3 +721,13 @@ def profile_read(ctx: Context) -> dict:
     ms = (ctypes.c_double * k)()
     _check(lib.rtg_profile_read(ctx.ptr, launches, ms, k), "rtg_profile_read", ctx.ptr)
     return {lib.rtg_profile_kind_name(i).decode(): (int(launches[i]), float(ms[i])) for i in range(k)}
+
+
+def alu_probe(kind: int, iters: int, out: torch.Tensor, stream=None) -> int:
+    """Launches the arithmetic-pipe probe (kind 0: FP32 FMA, kind 1: SFU ex2) on the current
+    device and returns the operations it performs; `out` is a float32 device scratch of at
+    least 2048 x SM-count entries.  The caller times the launch."""
+    ops = ctypes.c_int64()
+    _check(_lib.load().rtg_alu_probe(int(kind), int(iters), _ptr(out), ctypes.byref(ops), _stream(stream)),
+           "rtg_alu_probe")
+    return int(ops.value)

@@ -505,6 +505,7 @@ rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap) {
   cudaMemset(ctx->slab + L.loss_acc, 0, 4 * 8);
   cudaMemset(ctx->slab + L.gauss_bits, 0, (size_t)(cap->max_gaussians > 0 ? cap->max_gaussians : 1) * 4);
   init_sort_attributes();
+
   if (cudaDeviceSynchronize() != cudaSuccess) {
     cudaGetLastError();
     cudaFreeHost(ctx->status_host);
@@ -1241,6 +1242,20 @@ rtg_status rtg_get_stats(rtg_ctx *ctx, rtg_stats *out) {
   out->status = (int32_t)*(volatile uint32_t *)ctx->status_host;
   out->tile_w = 1 << ctx->tune_fwd.tws;
   out->tile_h = 1 << ctx->tune_fwd.ths;
+  out->window_stable = ctx->win.open ? (int64_t)c[kWinStable] : 0;
+  out->window_pairs = 0;
+  if (ctx->win.open && ctx->win.lists) {
+    const int Wd = ctx->win.cams[0].width, Hd = ctx->win.cams[0].height;
+    const int T = ((Wd + (1 << ctx->win.lists_tws) - 1) >> ctx->win.lists_tws) *
+                  ((Hd + (1 << ctx->win.lists_ths) - 1) >> ctx->win.lists_ths);
+    const size_t FT = (size_t)ctx->win.F * T;
+    uint32_t last[2] = {0u, 0u};
+    if (FT > 0 && cudaMemcpy(&last[0], ctx->win_soff + FT - 1, 4, cudaMemcpyDeviceToHost) == cudaSuccess &&
+        cudaMemcpy(&last[1], ctx->win_scount + FT - 1, 4, cudaMemcpyDeviceToHost) == cudaSuccess)
+      out->window_pairs = (int64_t)last[0] + last[1];
+    else
+      cudaGetLastError();
+  }
   return RTG_OK;
 }
 

@@ -58,6 +58,11 @@ def test_host_side_argument_errors_without_gpu():
     assert lib.rtg_create(ctypes.byref(out), None) == _lib.RTG_ERR_ARG and not out.value
     assert lib.rtg_render_forward(None, None, 1, None, None, None, None, None, None, None, None) == _lib.RTG_ERR_ARG
     assert lib.rtg_gather_unstable(-1, 3, *([None] * 11), None) == _lib.RTG_ERR_ARG
+    ops = ctypes.c_int64(-7)
+    assert lib.rtg_alu_probe(2, 10, 1, ctypes.byref(ops), None) == _lib.RTG_ERR_ARG  # unknown kind
+    assert lib.rtg_alu_probe(0, 0, 1, ctypes.byref(ops), None) == _lib.RTG_ERR_ARG   # no iterations
+    assert lib.rtg_alu_probe(1, 10, None, ctypes.byref(ops), None) == _lib.RTG_ERR_ARG
+    assert ops.value == -7
 
 
 def test_struct_layouts_match_header():
@@ -66,7 +71,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(_lib.rtg_render_params) == 9 * 4
     assert ctypes.sizeof(_lib.rtg_gaussians) == 8 + 8 + 13 * 8 + 8 + 8  # + sh_degree, padded
     assert ctypes.sizeof(_lib.rtg_capacity) == 8 + 4 * 4 + 8
-    assert ctypes.sizeof(_lib.rtg_stats) == 6 * 8 + 4 * 4
+    assert ctypes.sizeof(_lib.rtg_stats) == 6 * 8 + 4 * 4 + 2 * 8  # + the window counters
     assert ctypes.sizeof(_lib.rtg_tuning) == 8 * 4
     assert ctypes.sizeof(_lib.rtg_add_params) == 6 * 4 + 8
     assert ctypes.sizeof(_lib.rtg_state_params) == 5 * 4
