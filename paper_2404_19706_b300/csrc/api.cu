@@ -505,7 +505,7 @@ rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap) {
   cudaMemset(ctx->slab + L.loss_acc, 0, 4 * 8);
   cudaMemset(ctx->slab + L.gauss_bits, 0, (size_t)(cap->max_gaussians > 0 ? cap->max_gaussians : 1) * 4);
   init_sort_attributes();
-
+  init_backward_attributes();
   if (cudaDeviceSynchronize() != cudaSuccess) {
     cudaGetLastError();
     cudaFreeHost(ctx->status_host);

@@ -28,102 +28,119 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// Warp sums of a gradient row by halving exchanges (a reduce-scatter).  At each level the
-// lanes whose level bit is clear keep the first half of their array of partial sums and the
-// others the second half, each adding its partner's copy: n values cost ceil(n / 2)
-// shuffles per level instead of one per value, and the last lane of the chain holds one
-// warp total.  Arrays of odd length are padded with a zero at the end of the level.
-__host__ __device__ constexpr int rs_half(int n) { return (n + 1) / 2; }
+// Per-warp shared memory of the backward compositing.  The replay runs with one pixel a lane
+// (the transmission and the colour behind a fragment are per-pixel recurrences), but the
+// gradient rows are sums over pixels for one record: so the replay leaves, for each unstable
+// record it meets with at least one active pixel, the pixel's blend weight f T and
+// dL/dalpha in a pending slot, and once kBwdSlots records are pending the warp sums their
+// rows with the records spread over the lanes (flush_rows).
+constexpr int kBwdSlots = 16;
 
-template <int N, int H>
-__device__ __forceinline__ void rs_level(const float (&in)[N], float (&out)[H], bool up, int mask) {
-#pragma unroll
-  for (int i = 0; i < H; ++i) {
-    const float lo = in[i], hi = (H + i) < N ? in[H + i] : 0.f;
-    out[i] = (up ? hi : lo) + __shfl_xor_sync(0xffffffffu, up ? lo : hi, mask);
-  }
-}
+template <int C, int B>
+struct BwdWarpSmem {
+  static constexpr int H4 = (C <= 4) ? 3 : 4;
+  float4 rec[H4][B];          // the batch's kept records, in list order
+  int2 jr[B];                 // their list position and unstable rank
+  float2 wg[kBwdSlots][33];   // pending record x pixel: (f T, dL/dalpha); rows padded by one
+  float4 prec[kBwdSlots][2];  // pending record: centre (hi, lo); conic factor and alpha
+  int prank[kBwdSlots];       // pending record's unstable rank (its grad2d row)
+  float2 px[32];              // the group's pixel centres
+  float dc[C][32];            // the group's dL/dcolour, per channel
+};
 
-// The value a lane holds after the levels with the given half sizes (the level bits taken
-// from `bits`, most significant first), and whether it is a real value rather than padding.
-template <int N, int S1, int S2, int S3, int S4>
-__device__ __forceinline__ int rs_index(int bits, bool &valid) {
-  const int sz[4] = {S1, S2, S3, S4};
-  int idx = 0, n = N;
+template <int C, int B>
+constexpr size_t bwd_smem_bytes() { return 8 * sizeof(BwdWarpSmem<C, B>); }
+
+// Adds the gradient rows of pending records [0, n) to grad2d.  L lanes take a record (S =
+// 32 / L records a pass, each lane 32 / L of the group's pixels); the L partial sums are
+// joined by shuffles.  With G = dL/dalpha of a fragment (zero where the footprint is clamped
+// at f_max, f = alpha 2^-q) and t = U d, q = |t|^2:
+//   dL/dmu    = 2 alpha ln2 (u11 sum G t1,  u12 sum G t1 + u22 sum G t2)
+//   dL/dconic = -alpha ln2 kQScale2 (sum G dx^2, 2 sum G dx dy, sum G dy^2)
+//   dL/dalpha = sum G,   dL/dc = sum f T dL/dC.
+// Each record's row takes ceil((6 + C) / 4) vector atomics (the depth slots get zeros).
+template <int C, int B, int L>
+__device__ __forceinline__ void flush_rows(const BwdWarpSmem<C, B> &sm, int n, int npix, float *__restrict__ g2base) {
+  constexpr int NV = 6 + C, S = 32 / L, PX = 32 / L, G2 = (C <= 5) ? 16 : 20;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / S;
+  for (int base = 0; base < n; base += S) {
+    const int slot = base + (lane % S);
+    const float4 a0 = sm.prec[slot][0], a1 = sm.prec[slot][1];
+    float acc[NV];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    if ((bits >> (3 - k)) & 1) {
-      idx += sz[k];
-      n = n > sz[k] ? n - sz[k] : 0;
-    } else {
-      n = n < sz[k] ? n : sz[k];
+    for (int v = 0; v < NV; ++v) acc[v] = 0.f;
+#pragma unroll 4
+    for (int i = 0; i < PX; ++i) {
+      const int p = sub * PX + i;
+      if (p < npix) {
+        const float2 w_ = sm.wg[slot][p];
+        const float2 pp = sm.px[p];
+        const float dx = (pp.x - a0.x) - a0.z, dy = (pp.y - a0.y) - a0.w;
+        const float t1 = fmaf(a1.x, dx, a1.y * dy), t2 = a1.z * dy;
+        const float G = w_.y, Gx = G * dx;
+        acc[0] = fmaf(G, t1, acc[0]);
+        acc[1] = fmaf(G, t2, acc[1]);
+        acc[2] = fmaf(Gx, dx, acc[2]);
+        acc[3] = fmaf(Gx, dy, acc[3]);
+        acc[4] = fmaf(G * dy, dy, acc[4]);
+        acc[5] += G;
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[6 + c] = fmaf(w_.x, sm.dc[c][p], acc[6 + c]);
+      }
+    }
+#pragma unroll
+    for (int o = S; o < 32; o <<= 1)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+    if (sub == 0 && slot < n) {
+      const float al = a1.w * kLn2, c2 = 2.f * al, kc = -al * kQScale2;
+      float v[4 * ((NV + 3) / 4)];
+      v[0] = c2 * a1.x * acc[0];
+      v[1] = c2 * fmaf(a1.y, acc[0], a1.z * acc[1]);
+      v[2] = kc * acc[2];
+      v[3] = 2.f * kc * acc[3];
+      v[4] = kc * acc[4];
+#pragma unroll
+      for (int q = 5; q < NV; ++q) v[q] = acc[q];
+#pragma unroll
+      for (int q = NV; q < 4 * ((NV + 3) / 4); ++q) v[q] = 0.f;
+      float4 *row = reinterpret_cast<float4 *>(g2base + (int64_t)sm.prank[slot] * G2);
+#pragma unroll
+      for (int q = 0; q < (NV + 3) / 4; ++q)
+        atomicAdd(row + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
     }
   }
-  valid = n == 1;
-  return idx;
 }
 
-// One record: NV <= 16 values over the whole warp (levels 16, 8, 4, 2, then a plain sum over
-// lane pairs).  Lane L returns the total of value rs_index(L >> 1); lanes 2k and 2k + 1 agree.
-template <int NV>
-__device__ __forceinline__ float warp_rs_one(const float (&in)[NV]) {
-  constexpr int S1 = rs_half(NV), S2 = rs_half(S1), S3 = rs_half(S2), S4 = rs_half(S3);
-  static_assert(S4 == 1, "at most 16 values");
-  const int lane = threadIdx.x & 31;
-  float a1[S1], a2[S2], a3[S3], a4[S4];
-  rs_level<NV, S1>(in, a1, lane & 16, 16);
-  rs_level<S1, S2>(a1, a2, lane & 8, 8);
-  rs_level<S2, S3>(a2, a3, lane & 4, 4);
-  rs_level<S3, S4>(a3, a4, lane & 2, 2);
-  return a4[0] + __shfl_xor_sync(0xffffffffu, a4[0], 1);
-}
-
-// Two records: the first level sends record A to the lanes with bit 16 clear and record B
-// to the others (NV shuffles), then levels 8, 4, 2, 1 split each record's NV values.  Lane L
-// returns the total of value rs_index(L & 15) of record L >> 4; every real value is held by
-// exactly one lane.
-template <int NV>
-__device__ __forceinline__ float warp_rs_two(const float (&A)[NV], const float (&B)[NV]) {
-  constexpr int T1 = rs_half(NV), T2 = rs_half(T1), T3 = rs_half(T2), T4 = rs_half(T3);
-  static_assert(T4 == 1, "at most 16 values");
-  const int lane = threadIdx.x & 31;
-  const bool up = lane & 16;
-  float a0[NV], a1[T1], a2[T2], a3[T3], a4[T4];
-#pragma unroll
-  for (int i = 0; i < NV; ++i) a0[i] = (up ? B[i] : A[i]) + __shfl_xor_sync(0xffffffffu, up ? A[i] : B[i], 16);
-  rs_level<NV, T1>(a0, a1, lane & 8, 8);
-  rs_level<T1, T2>(a1, a2, lane & 4, 4);
-  rs_level<T2, T3>(a2, a3, lane & 2, 2);
-  rs_level<T3, T4>(a3, a4, lane & 1, 1);
-  return a4[0];
+// The rows of the last n < kBwdSlots pending records: more lanes per record when few are left.
+template <int C, int B>
+__device__ __forceinline__ void flush_rows_tail(const BwdWarpSmem<C, B> &sm, int n, int npix, float *g2base) {
+  if (n <= 0) return;
+  if (n <= 2) flush_rows<C, B, 16>(sm, n, npix, g2base);
+  else if (n <= 4) flush_rows<C, B, 8>(sm, n, npix, g2base);
+  else if (n <= 8) flush_rows<C, B, 4>(sm, n, npix, g2base);
+  else flush_rows<C, B, 2>(sm, n, npix, g2base);
 }
 
 // Replays the pixels of group `grp` of render tile `tile` (the forward's pixel grouping)
-// back to front.  Called by a whole warp; s_rec / s_jr (list position, unstable rank) are
-// the warp's staging.
+// back to front.  Called by a whole warp; sm is the warp's own shared memory.
 template <int C, int B>
 __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, int64_t N, int T, int tile, int grp,
-                                               float4 (*s_rec)[B], int2 *s_jr,
-                                               const float *__restrict__ dL_dcolor,
+                                               BwdWarpSmem<C, B> &sm, const float *__restrict__ dL_dcolor,
                                                const float *__restrict__ dL_ddepth, const L1Fused &l1) {
   constexpr int H4 = (C <= 4) ? 3 : 4;
   constexpr int G2 = (C <= 5) ? 16 : 20;
-  constexpr int NV = 6 + C;            // d mu (2), d conic (3), d alpha, d colour (C)
   constexpr int R = B / 32;
   const int lane = threadIdx.x & 31;
-  // the row value each lane holds after the reduce-scatters (one record, two records)
-  bool one_valid, two_valid;
-  const int one_idx = rs_index<NV, rs_half(NV), rs_half(rs_half(NV)), rs_half(rs_half(rs_half(NV))), 1>(
-      (lane >> 1) & 15, one_valid);
-  one_valid = one_valid && (lane & 1) == 0;
-  const int two_idx = rs_index<NV, rs_half(NV), rs_half(rs_half(NV)), rs_half(rs_half(rs_half(NV))), 1>(
-      lane & 15, two_valid);
   const int f = tile / T, lt = tile - f * T;
   const DevCam &cam = w.cams[f];
   const int tws = cam.tws, ths = cam.ths;
   const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
+  const int npix_tile = (int)w.tile_npix[tile];
   const int q = grp * 32 + lane;
-  const bool has = q < (int)w.tile_npix[tile];
+  const bool has = q < npix_tile;
+  const int npix = min(32, npix_tile - grp * 32);
   const int my = has ? (int)w.px_list[((int64_t)tile << (tws + ths)) + q] : 0;
   const int px = (tx << tws) + (my & ((1 << tws) - 1)), py = (ty << ths) + (my >> tws);
   const float fpx = (float)px, fpy = (float)py;
@@ -158,6 +175,10 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
     }
   }
   float *__restrict__ g2base = w.grad2d + (int64_t)f * N * G2;
+  // the group's pixels and colour gradients, read by every lane when the rows are summed
+  sm.px[lane] = make_float2(fpx, fpy);
+#pragma unroll
+  for (int c = 0; c < C; ++c) sm.dc[c][lane] = dC[c];
 
   // ---- depth: gradient to the hit Gaussian's plane record or centre depth (Eq. 4/5)
   {
@@ -220,6 +241,7 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
   float S[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) S[c] = 0.f;
+  int nslot = 0;  // pending records (warp-uniform)
 
   // batches of B records run back to front; the records of the next (earlier) batch are
   // fetched while the current one is replayed
@@ -241,6 +263,48 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
       }
     }
   };
+  // One fragment, back to front: its transmission by division, dL/df from the colour behind
+  // it, and for an unstable record a pending slot with (f T, dL/dalpha) per pixel.  A record
+  // no pixel of the group composited (outside its support, or past the early stop) is
+  // skipped as a whole.
+  auto replay = [&](int k, float fa, float g) {
+    const int2 jr = sm.jr[k];
+    const bool act = has && (uint32_t)jr.x < last && fa >= prm.alpha_min;
+    if (!__any_sync(0xffffffffu, act)) return;
+    float wgt = 0.f, G = 0.f;
+    if (act) {
+      const float iom = __fdividef(1.f, 1.f - fa);  // 1 - f >= 1 - f_max: a normal divisor
+      T_ = T_ * iom;  // transmission in front of this fragment
+      wgt = fa * T_;
+      const float4 c0 = sm.rec[2][k];
+      float cw[8] = {c0.x, c0.y, c0.z, c0.w, 0.f, 0.f, 0.f, 0.f};
+      if (H4 == 4) {
+        const float4 c1 = sm.rec[3 % H4][k];
+        cw[4] = c1.x; cw[5] = c1.y; cw[6] = c1.z; cw[7] = c1.w;
+      }
+      float dLdf = 0.f;
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        dLdf = fmaf(dC[c], fmaf(cw[c], T_, -S[c] * iom), dLdf);
+        S[c] = fmaf(cw[c], wgt, S[c]);
+      }
+      if (sm.rec[1][k].w * g < prm.f_max) G = dLdf * g;  // unclamped branch of min(f_max, alpha g)
+    }
+    if (jr.y >= 0) {  // warp-uniform: the record is unstable
+      sm.wg[nslot][lane] = make_float2(wgt, G);
+      if (lane == 0) {
+        sm.prec[nslot][0] = sm.rec[0][k];
+        sm.prec[nslot][1] = sm.rec[1][k];
+        sm.prank[nslot] = jr.y;
+      }
+      if (++nslot == kBwdSlots) {
+        __syncwarp();
+        flush_rows<C, B, 2>(sm, kBwdSlots, npix, g2base);
+        __syncwarp();
+        nslot = 0;
+      }
+    }
+  };
   float4 r[R][H4];
   float2 bb[R];
   int rk[R];
@@ -254,6 +318,7 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
     bool vnext[R];
     fetch(b_beg, rn, bn, rkn, vnext);
     int cnt = 0;
+    __syncwarp();  // the previous batch's staged records are no longer read
 #pragma unroll
     for (int u = 0; u < R; ++u) {
       const bool keep = valid[u] && fabsf(r[u][0].x - wcx) <= whx + bb[u].x &&
@@ -263,106 +328,44 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
       if (keep) {
         const int slot = cnt + __popc(bal & lanemask_lt());
 #pragma unroll
-        for (int k = 0; k < H4; ++k) s_rec[k][slot] = r[u][k];
-        s_jr[slot] = make_int2(b_beg + u * 32 + lane, rk[u]);
+        for (int k = 0; k < H4; ++k) sm.rec[k][slot] = r[u][k];
+        sm.jr[slot] = make_int2(b_beg + u * 32 + lane, rk[u]);
       }
       cnt += __popc(bal);
     }
     __syncwarp();
-    // Records run back to front in pairs: the two footprints are independent and are
-    // evaluated together, the transmission and colour sums then take the two fragments in
-    // order, and the two gradient rows are reduced together, so their shuffles overlap.
-    auto frag = [&](bool act, float fa, float g, float dx, float dy, float t1, float t2, const float4 &r1, int k,
-                    int rkk, float (&v)[NV]) {
-#pragma unroll
-      for (int qq = 0; qq < NV; ++qq) v[qq] = 0.f;
-      if (!act) return;
-      const float om = 1.f - fa;
-      const float iom = __fdividef(1.f, om);  // 1 - f >= 1 - f_max: a normal divisor
-      T_ = T_ * iom;  // transmission in front of this fragment
-      const float wgt = fa * T_;
-      const float4 c0 = s_rec[2][k];
-      float cw[8] = {c0.x, c0.y, c0.z, c0.w, 0.f, 0.f, 0.f, 0.f};
-      if (H4 == 4) {
-        const float4 c1 = s_rec[3 % H4][k];
-        cw[4] = c1.x; cw[5] = c1.y; cw[6] = c1.z; cw[7] = c1.w;
-      }
-      float dLdf = 0.f;
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        v[6 + c] = wgt * dC[c];
-        dLdf = fmaf(dC[c], fmaf(cw[c], T_, -S[c] * iom), dLdf);
-        S[c] = fmaf(cw[c], wgt, S[c]);
-      }
-      if (rkk >= 0 && r1.w * g < prm.f_max) {  // unclamped branch of min(f_max, alpha g)
-        v[5] = dLdf * g;
-        const float dLdq = -dLdf * r1.w * g * kLn2;  // g = 2^-q
-        v[0] = -2.f * dLdq * (r1.x * t1);
-        v[1] = -2.f * dLdq * fmaf(r1.y, t1, r1.z * t2);
-        const float dLdp = dLdq * kQScale2;  // q = kQScale2 * d^T conic d
-        v[2] = dLdp * dx * dx;
-        v[3] = dLdp * 2.f * dx * dy;
-        v[4] = dLdp * dy * dy;
-      }
-    };
-    // each lane adds the one warp total it holds to its slot of the record's row (the
-    // values are the row's first NV slots): one reduction instruction per record or pair
-    auto emit_one = [&](float tot, int rkk) {
-      if (one_valid) atomicAdd(g2base + (int64_t)rkk * G2 + one_idx, tot);
-    };
-    auto emit_two = [&](float tot, int rkA, int rkB, bool fA, bool fB) {
-      const bool mine = (lane & 16) ? fB : fA;
-      if (two_valid && mine) atomicAdd(g2base + (int64_t)((lane & 16) ? rkB : rkA) * G2 + two_idx, tot);
-    };
+    // records back to front, footprints two at a time (they are independent; the
+    // recurrences then take the two fragments in order)
     int k = cnt - 1;
     for (; k >= 1; k -= 2) {
-      const int2 jrA = s_jr[k], jrB = s_jr[k - 1];
-      const uint32_t jA = (uint32_t)jrA.x, jB = (uint32_t)jrB.x;
-      const float4 a0 = s_rec[0][k], a1 = s_rec[1][k], b0 = s_rec[0][k - 1], b1 = s_rec[1][k - 1];
+      const float4 a0 = sm.rec[0][k], a1 = sm.rec[1][k], b0 = sm.rec[0][k - 1], b1 = sm.rec[1][k - 1];
       float dxA, dyA, t1A, t2A, gA, dxB, dyB, t1B, t2B, gB;
       const float faA = footprint(fpx, fpy, a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, prm.f_max, dxA, dyA, t1A,
                                   t2A, gA);
       const float faB = footprint(fpx, fpy, b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w, prm.f_max, dxB, dyB, t1B,
                                   t2B, gB);
-      const bool actA = has && jA < last && faA >= prm.alpha_min;
-      const bool actB = has && jB < last && faB >= prm.alpha_min;
-      const int rA = jrA.y, rB = jrB.y;
-      float vA[NV], vB[NV];
-      frag(actA, faA, gA, dxA, dyA, t1A, t2A, a1, k, rA, vA);
-      frag(actB, faB, gB, dxB, dyB, t1B, t2B, b1, k - 1, rB, vB);
-      const bool fA = rA >= 0 && __any_sync(0xffffffffu, actA);
-      const bool fB = rB >= 0 && __any_sync(0xffffffffu, actB);
-      if (fA && fB) {
-        emit_two(warp_rs_two<NV>(vA, vB), rA, rB, true, true);
-      } else if (fA) {
-        emit_one(warp_rs_one<NV>(vA), rA);
-      } else if (fB) {
-        emit_one(warp_rs_one<NV>(vB), rB);
-      }
+      replay(k, faA, gA);
+      replay(k - 1, faB, gB);
     }
     if (k == 0) {
-      const int2 jrA = s_jr[0];
-      const uint32_t jA = (uint32_t)jrA.x;
-      const float4 a0 = s_rec[0][0], a1 = s_rec[1][0];
+      const float4 a0 = sm.rec[0][0], a1 = sm.rec[1][0];
       float dxA, dyA, t1A, t2A, gA;
       const float faA = footprint(fpx, fpy, a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, prm.f_max, dxA, dyA, t1A,
                                   t2A, gA);
-      const bool actA = has && jA < last && faA >= prm.alpha_min;
-      const int rA = jrA.y;
-      float vA[NV];
-      frag(actA, faA, gA, dxA, dyA, t1A, t2A, a1, 0, rA, vA);
-      if (rA >= 0 && __any_sync(0xffffffffu, actA)) emit_one(warp_rs_one<NV>(vA), rA);
+      replay(0, faA, gA);
     }
-    __syncwarp();
 #pragma unroll
     for (int u = 0; u < R; ++u) {
 #pragma unroll
-      for (int k = 0; k < H4; ++k) r[u][k] = rn[u][k];
+      for (int k2 = 0; k2 < H4; ++k2) r[u][k2] = rn[u][k2];
       bb[u] = bn[u];
       rk[u] = rkn[u];
       valid[u] = vnext[u];
     }
   }
+  __syncwarp();
+  flush_rows_tail<C, B>(sm, nslot, npix, g2base);
+  __syncwarp();  // the next group rewrites the warp's pixel arrays
 }
 
 struct BwdIn {
@@ -372,36 +375,30 @@ struct BwdIn {
 
 // Schedule 0: CTA `tile` with one warp per 32-pixel group of the tile's pixel list.
 template <int C, int B>
-__global__ void __launch_bounds__(kMaxTilePix) k_backward(Work w, Prm prm, int64_t N, int T,
-                                                                               BwdIn in) {
+__global__ void __launch_bounds__(kMaxTilePix, 2) k_backward(Work w, Prm prm, int64_t N, int T, BwdIn in) {
   grid_dep_wait();
-  constexpr int H4 = (C <= 4) ? 3 : 4;
-  __shared__ float4 s_rec[kMaxTilePix / 32][H4][B];
-  __shared__ int2 s_jr[kMaxTilePix / 32][B];
+  extern __shared__ float4 bwd_dyn_smem[];
   if (w.counters[kSkip] != 0ull) return;
   const int tile = blockIdx.x, wid = threadIdx.x >> 5;
   if (wid * 32 >= (int)w.tile_npix[tile]) return;
-  backward_group<C, B>(w, prm, N, T, tile, wid, s_rec[wid], s_jr[wid], in.dL_dcolor, in.dL_ddepth,
-                       in.l1);
+  BwdWarpSmem<C, B> *sm = reinterpret_cast<BwdWarpSmem<C, B> *>(bwd_dyn_smem) + wid;
+  backward_group<C, B>(w, prm, N, T, tile, wid, *sm, in.dL_dcolor, in.dL_ddepth, in.l1);
 }
 
 // Schedule 1: persistent warps over the forward's item queue (its own counter).
 template <int C, int B>
-__global__ void __launch_bounds__(256) k_backward_queue(Work w, Prm prm, int64_t N, int T,
-                                                                              BwdIn in, int spread) {
+__global__ void __launch_bounds__(256, 2) k_backward_queue(Work w, Prm prm, int64_t N, int T, BwdIn in, int spread) {
   grid_dep_wait();
-  constexpr int H4 = (C <= 4) ? 3 : 4;
-  __shared__ float4 s_rec[8][H4][B];
-  __shared__ int2 s_jr[8][B];
+  extern __shared__ float4 bwd_dyn_smem[];
   if (w.counters[kSkip] != 0ull) return;
   const uint32_t nitems = (uint32_t)w.counters[kItems];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  BwdWarpSmem<C, B> *sm = reinterpret_cast<BwdWarpSmem<C, B> *>(bwd_dyn_smem) + wid;
   const uint32_t nwarps = gridDim.x * 8u;
   uint32_t it = first_item(w, wid, spread);
   while (it < nitems) {
     const uint32_t item = w.items[it];
-    backward_group<C, B>(w, prm, N, T, (int)(item >> 3), (int)(item & 7u), s_rec[wid], s_jr[wid],
-                         in.dL_dcolor, in.dL_ddepth, in.l1);
+    backward_group<C, B>(w, prm, N, T, (int)(item >> 3), (int)(item & 7u), *sm, in.dL_dcolor, in.dL_ddepth, in.l1);
     uint32_t nx = 0;
     if (lane == 0) nx = nwarps + (uint32_t)atomicAdd(w.counters + kQBwd, 1ull);
     it = __shfl_sync(0xffffffffu, nx, 0);
@@ -790,10 +787,25 @@ template <int C, int B>
 static void launch_backward_cb(const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn,
                                const BwdIn &in, cudaStream_t s) {
   if (tn.schedule == 1)
-    launch(k_backward_queue<C, B>, tn.num_sms * tn.ctas_per_sm, 256, 0, s, w, prm, N, T, in,
+    launch(k_backward_queue<C, B>, tn.num_sms * tn.ctas_per_sm, 256, bwd_smem_bytes<C, B>(), s, w, prm, N, T, in,
            tn.ctas_per_sm <= 2 ? 1 : 0);
   else
-    launch(k_backward<C, B>, F * T, 1 << (tn.tws + tn.ths), 0, s, w, prm, N, T, in);
+    launch(k_backward<C, B>, F * T, 1 << (tn.tws + tn.ths),
+           (size_t)((1 << (tn.tws + tn.ths)) / 32) * sizeof(BwdWarpSmem<C, B>), s, w, prm, N, T, in);
+}
+
+template <int C, int B>
+static void set_backward_attributes() {
+  cudaFuncSetAttribute(k_backward_queue<C, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)bwd_smem_bytes<C, B>());
+  cudaFuncSetAttribute(k_backward<C, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem_bytes<C, B>());
+}
+
+void init_backward_attributes() {
+  set_backward_attributes<3, 32>();
+  set_backward_attributes<3, 64>();
+  set_backward_attributes<8, 32>();
+  set_backward_attributes<8, 64>();
 }
 
 void launch_backward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn,

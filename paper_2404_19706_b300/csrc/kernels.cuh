@@ -198,6 +198,7 @@ void launch_forward(int C, const Work &w, const Prm &prm, int64_t N, int F, int 
 // backward.cu
 void launch_backward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn,
                      const float *dL_dcolor, const float *dL_ddepth, const L1Fused &l1, cudaStream_t s);
+void init_backward_attributes();
 void launch_loss_finalize(const Work &w, int FT, int gshift, int C, float w_c, float w_d, float *loss_out,
                           cudaStream_t s);
 void launch_project_backward(const GaussPtrs &g, const Work &w, const Prm &prm, int F, float *g_means,
