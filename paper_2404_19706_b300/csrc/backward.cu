@@ -31,96 +31,78 @@ __device__ __forceinline__ float warp_sum(float v) {
 // Per-warp shared memory of the backward compositing.  The replay runs with one pixel a lane
 // (the transmission and the colour behind a fragment are per-pixel recurrences), but the
 // gradient rows are sums over pixels for one record: so the replay leaves, for each unstable
-// record it meets with at least one active pixel, the pixel's blend weight f T and
-// dL/dalpha in a pending slot, and once kBwdSlots records are pending the warp sums their
-// rows with the records spread over the lanes (flush_rows).
-constexpr int kBwdSlots = 16;
+// record of the batch it meets with at least one active pixel, the pixel's blend weight f T
+// and dL/dalpha in a pending slot, and at the end of the batch (or when the slots are full)
+// the warp sums the pending rows with one record a lane, over that record's active pixels
+// only (flush_rows).
+__host__ __device__ constexpr int bwd_slots(int C, int B) { return (C > 4 && B > 32) ? 16 : 32; }
 
 template <int C, int B>
 struct BwdWarpSmem {
   static constexpr int H4 = (C <= 4) ? 3 : 4;
-  float4 rec[H4][B];          // the batch's kept records, in list order
-  int2 jr[B];                 // their list position and unstable rank
-  float2 wg[kBwdSlots][33];   // pending record x pixel: (f T, dL/dalpha); rows padded by one
-  float4 prec[kBwdSlots][2];  // pending record: centre (hi, lo); conic factor and alpha
-  int prank[kBwdSlots];       // pending record's unstable rank (its grad2d row)
-  float2 px[32];              // the group's pixel centres
-  float dc[C][32];            // the group's dL/dcolour, per channel
+  static constexpr int kSlots = bwd_slots(C, B);
+  float4 rec[H4][B];        // the batch's kept records, in list order
+  int2 jr[B];               // their list position and unstable rank
+  float2 wg[kSlots][33];    // pending record x pixel: (f T, dL/dalpha); rows padded by one
+  float2 px[32];            // the group's pixel centres
+  float dc[C][32];          // the group's dL/dcolour, per channel
 };
 
 template <int C, int B>
 constexpr size_t bwd_smem_bytes() { return 8 * sizeof(BwdWarpSmem<C, B>); }
 
-// Adds the gradient rows of pending records [0, n) to grad2d.  L lanes take a record (S =
-// 32 / L records a pass, each lane 32 / L of the group's pixels); the L partial sums are
-// joined by shuffles.  With G = dL/dalpha of a fragment (zero where the footprint is clamped
-// at f_max, f = alpha 2^-q) and t = U d, q = |t|^2:
+// Adds the gradient rows of pending records [0, n) to grad2d, lane s taking slot s: staged
+// record slot_k (a slot of sm.rec) whose active pixels are the bits of slot_m.  With
+// G = dL/dalpha of a fragment (zero where the footprint is clamped at f_max, f = alpha 2^-q)
+// and t = U d, q = |t|^2:
 //   dL/dmu    = 2 alpha ln2 (u11 sum G t1,  u12 sum G t1 + u22 sum G t2)
 //   dL/dconic = -alpha ln2 kQScale2 (sum G dx^2, 2 sum G dx dy, sum G dy^2)
-//   dL/dalpha = sum G,   dL/dc = sum f T dL/dC.
-// Each record's row takes ceil((6 + C) / 4) vector atomics (the depth slots get zeros).
-template <int C, int B, int L>
-__device__ __forceinline__ void flush_rows(const BwdWarpSmem<C, B> &sm, int n, int npix, float *__restrict__ g2base) {
-  constexpr int NV = 6 + C, S = 32 / L, PX = 32 / L, G2 = (C <= 5) ? 16 : 20;
-  const int lane = threadIdx.x & 31;
-  const int sub = lane / S;
-  for (int base = 0; base < n; base += S) {
-    const int slot = base + (lane % S);
-    const float4 a0 = sm.prec[slot][0], a1 = sm.prec[slot][1];
-    float acc[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] = 0.f;
-#pragma unroll 4
-    for (int i = 0; i < PX; ++i) {
-      const int p = sub * PX + i;
-      if (p < npix) {
-        const float2 w_ = sm.wg[slot][p];
-        const float2 pp = sm.px[p];
-        const float dx = (pp.x - a0.x) - a0.z, dy = (pp.y - a0.y) - a0.w;
-        const float t1 = fmaf(a1.x, dx, a1.y * dy), t2 = a1.z * dy;
-        const float G = w_.y, Gx = G * dx;
-        acc[0] = fmaf(G, t1, acc[0]);
-        acc[1] = fmaf(G, t2, acc[1]);
-        acc[2] = fmaf(Gx, dx, acc[2]);
-        acc[3] = fmaf(Gx, dy, acc[3]);
-        acc[4] = fmaf(G * dy, dy, acc[4]);
-        acc[5] += G;
-#pragma unroll
-        for (int c = 0; c < C; ++c) acc[6 + c] = fmaf(w_.x, sm.dc[c][p], acc[6 + c]);
-      }
-    }
-#pragma unroll
-    for (int o = S; o < 32; o <<= 1)
-#pragma unroll
-      for (int v = 0; v < NV; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
-    if (sub == 0 && slot < n) {
-      const float al = a1.w * kLn2, c2 = 2.f * al, kc = -al * kQScale2;
-      float v[4 * ((NV + 3) / 4)];
-      v[0] = c2 * a1.x * acc[0];
-      v[1] = c2 * fmaf(a1.y, acc[0], a1.z * acc[1]);
-      v[2] = kc * acc[2];
-      v[3] = 2.f * kc * acc[3];
-      v[4] = kc * acc[4];
-#pragma unroll
-      for (int q = 5; q < NV; ++q) v[q] = acc[q];
-#pragma unroll
-      for (int q = NV; q < 4 * ((NV + 3) / 4); ++q) v[q] = 0.f;
-      float4 *row = reinterpret_cast<float4 *>(g2base + (int64_t)sm.prank[slot] * G2);
-#pragma unroll
-      for (int q = 0; q < (NV + 3) / 4; ++q)
-        atomicAdd(row + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
-    }
-  }
-}
-
-// The rows of the last n < kBwdSlots pending records: more lanes per record when few are left.
+//   dL/dalpha = sum G,   dL/dc = sum f T dL/dC,
+// each sum over the record's active pixels.  A row takes ceil((6 + C) / 4) vector atomics
+// (the depth slots get zeros).
 template <int C, int B>
-__device__ __forceinline__ void flush_rows_tail(const BwdWarpSmem<C, B> &sm, int n, int npix, float *g2base) {
-  if (n <= 0) return;
-  if (n <= 2) flush_rows<C, B, 16>(sm, n, npix, g2base);
-  else if (n <= 4) flush_rows<C, B, 8>(sm, n, npix, g2base);
-  else if (n <= 8) flush_rows<C, B, 4>(sm, n, npix, g2base);
-  else flush_rows<C, B, 2>(sm, n, npix, g2base);
+__device__ __forceinline__ void flush_rows(const BwdWarpSmem<C, B> &sm, int n, int slot_k, unsigned slot_m,
+                                           float *__restrict__ g2base) {
+  constexpr int NV = 6 + C, G2 = (C <= 5) ? 16 : 20;
+  const int lane = threadIdx.x & 31;
+  if (lane >= n) return;
+  const float4 a0 = sm.rec[0][slot_k], a1 = sm.rec[1][slot_k];
+  const int rank = sm.jr[slot_k].y;
+  float acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0.f;
+  unsigned m = slot_m;
+  while (m) {
+    const int p = __ffs(m) - 1;
+    m &= m - 1u;
+    const float2 w_ = sm.wg[lane][p];
+    const float2 pp = sm.px[p];
+    const float dx = (pp.x - a0.x) - a0.z, dy = (pp.y - a0.y) - a0.w;
+    const float t1 = fmaf(a1.x, dx, a1.y * dy), t2 = a1.z * dy;
+    const float G = w_.y, Gx = G * dx;
+    acc[0] = fmaf(G, t1, acc[0]);
+    acc[1] = fmaf(G, t2, acc[1]);
+    acc[2] = fmaf(Gx, dx, acc[2]);
+    acc[3] = fmaf(Gx, dy, acc[3]);
+    acc[4] = fmaf(G * dy, dy, acc[4]);
+    acc[5] += G;
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[6 + c] = fmaf(w_.x, sm.dc[c][p], acc[6 + c]);
+  }
+  const float al = a1.w * kLn2, c2 = 2.f * al, kc = -al * kQScale2;
+  float v[4 * ((NV + 3) / 4)];
+  v[0] = c2 * a1.x * acc[0];
+  v[1] = c2 * fmaf(a1.y, acc[0], a1.z * acc[1]);
+  v[2] = kc * acc[2];
+  v[3] = 2.f * kc * acc[3];
+  v[4] = kc * acc[4];
+#pragma unroll
+  for (int q = 5; q < NV; ++q) v[q] = acc[q];
+#pragma unroll
+  for (int q = NV; q < 4 * ((NV + 3) / 4); ++q) v[q] = 0.f;
+  float4 *row = reinterpret_cast<float4 *>(g2base + (int64_t)rank * G2);
+#pragma unroll
+  for (int q = 0; q < (NV + 3) / 4; ++q) atomicAdd(row + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
 }
 
 // Replays the pixels of group `grp` of render tile `tile` (the forward's pixel grouping)
@@ -140,7 +122,6 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
   const int npix_tile = (int)w.tile_npix[tile];
   const int q = grp * 32 + lane;
   const bool has = q < npix_tile;
-  const int npix = min(32, npix_tile - grp * 32);
   const int my = has ? (int)w.px_list[((int64_t)tile << (tws + ths)) + q] : 0;
   const int px = (tx << tws) + (my & ((1 << tws) - 1)), py = (ty << ths) + (my >> tws);
   const float fpx = (float)px, fpy = (float)py;
@@ -241,7 +222,10 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
   float S[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) S[c] = 0.f;
-  int nslot = 0;  // pending records (warp-uniform)
+  constexpr int kSlots = bwd_slots(C, B);
+  int nslot = 0;          // pending records of the batch (warp-uniform)
+  int slot_k = 0;         // lane s: the staged record of pending slot s
+  unsigned slot_m = 0u;   // lane s: its active pixels
 
   // batches of B records run back to front; the records of the next (earlier) batch are
   // fetched while the current one is replayed
@@ -292,14 +276,12 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
     }
     if (jr.y >= 0) {  // warp-uniform: the record is unstable
       sm.wg[nslot][lane] = make_float2(wgt, G);
-      if (lane == 0) {
-        sm.prec[nslot][0] = sm.rec[0][k];
-        sm.prec[nslot][1] = sm.rec[1][k];
-        sm.prank[nslot] = jr.y;
-      }
-      if (++nslot == kBwdSlots) {
+      const unsigned am = __ballot_sync(0xffffffffu, act);
+      slot_k = lane == nslot ? k : slot_k;
+      slot_m = lane == nslot ? am : slot_m;
+      if (++nslot == kSlots) {
         __syncwarp();
-        flush_rows<C, B, 2>(sm, kBwdSlots, npix, g2base);
+        flush_rows<C, B>(sm, nslot, slot_k, slot_m, g2base);
         __syncwarp();
         nslot = 0;
       }
@@ -354,6 +336,11 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
                                   t2A, gA);
       replay(0, faA, gA);
     }
+    if (nslot > 0) {  // the batch's staging is rewritten next: its pending rows go now
+      __syncwarp();
+      flush_rows<C, B>(sm, nslot, slot_k, slot_m, g2base);
+      nslot = 0;
+    }
 #pragma unroll
     for (int u = 0; u < R; ++u) {
 #pragma unroll
@@ -363,8 +350,6 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
       valid[u] = vnext[u];
     }
   }
-  __syncwarp();
-  flush_rows_tail<C, B>(sm, nslot, npix, g2base);
   __syncwarp();  // the next group rewrites the warp's pixel arrays
 }
 

@@ -16,9 +16,9 @@ namespace rtg {
 // tiles, one thread per pixel: a CTA takes kMaxTilePix / 2^(tws+ths) consecutive tiles (so
 // small tiles do not make thousands of tiny CTAs).  Counts the masked in-image pixels of
 // each tile, clears its pair counter and, with `lists`, writes the tile's masked pixels
-// (index within the tile) compacted in raster order: the forward and backward give each 32
-// of them to one warp.  With `setup`, block 0 also publishes the cameras and clears the
-// per-call counters.
+// (raster index within the tile) compacted in the tile's Z order (tile_order_pixel): the
+// forward and backward give each 32 of them to one warp.  With `setup`, block 0 also
+// publishes the cameras and clears the per-call counters.
 __global__ void __launch_bounds__(kMaxTilePix) k_tile_mask(FrameSet fs, Work w, const uint8_t *__restrict__ mask,
                                                            int T, int tiles_x, int tws, int ths, int setup,
                                                            int lists, long long nu_preset) {
@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(kMaxTilePix) k_tile_mask(FrameSet fs, Work w, 
   const int sh = tws + ths;  // log2 pixels per tile
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int tile = (int)blockIdx.x * (kMaxTilePix >> sh) + (tid >> sh);
-  const int pix = tid & ((1 << sh) - 1);
+  const int pix = tile_order_pixel(tid & ((1 << sh) - 1), tws, ths);  // threads take the tile in Z order
   const int FT = fs.F * T;
   const bool live = tile < FT;
   const int f = live ? tile / T : 0, lt = tile - f * T;

@@ -144,6 +144,28 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
+// Pixel order inside a render tile of 2^tws x 2^ths pixels (returns the raster index
+// y << tws | x of position t): Z order, the low bits of x and y interleaved (x first), the
+// remaining bits of the longer side on top.  Every aligned run of 32 positions is then an
+// 8 x 4 block, so the 32 pixels a warp composites form a compact box (a 16-pixel-wide tile
+// in raster order would give a warp two rows).  The tile passes list masked pixels in this
+// order.
+__device__ __forceinline__ int tile_order_pixel(int t, int tws, int ths) {
+  const int m = tws < ths ? tws : ths;
+  int x = 0, y = 0;
+#pragma unroll
+  for (int b = 0; b < 5; ++b) {
+    if (b < m) {
+      x |= ((t >> (2 * b)) & 1) << b;
+      y |= ((t >> (2 * b + 1)) & 1) << b;
+    }
+  }
+  const int hi = t >> (2 * m);
+  if (tws > ths) x |= hi << m;
+  else y |= hi << m;
+  return (y << tws) | x;
+}
+
 // ---- host launchers (each defined in the translation unit of its kernels)
 // bin.cu
 // Per-tile masked-pixel counts over a grid of 2^tws x 2^ths tiles (tiles_x per row), and,

@@ -486,8 +486,8 @@ __global__ void k_scatter(int64_t nu, int C, const int32_t *__restrict__ ids, co
 // One CTA per 16x16 tile (the tile grid of the rule).  The unstable Gaussians were
 // projected and bucketed into every tile their support box touches; a pixel is covered
 // when one footprint reaches alpha_min there (T_unstable < 1 in Eq. S2), with the same
-// projection and footprint expression as the forward.  Each warp owns two pixel rows and
-// walks the tile's bucket alone, in batches of 32 records of which it keeps only those
+// projection and footprint expression as the forward.  Each warp owns an 8 x 4 pixel block
+// (the tile taken in Z order) and walks the tile's bucket alone, in batches of 32 records of which it keeps only those
 // whose support box reaches its pixel box (a conservative test), and stops as soon as all
 // its pixels are covered.  The tile rule (Supplement B) is applied in the same kernel: a
 // tile with fewer than `discard` of its in-image pixels covered is cleared.  Every
@@ -509,14 +509,15 @@ __global__ void __launch_bounds__(kTilePix) k_mask_cover_tiles(Work w, Prm prm, 
   const DevCam &cam = w.cams[f];
   const int tx = lt % cam.mtiles_x, ty = lt / cam.mtiles_x;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int px = tx * kTile + (tid & (kTile - 1)), py = ty * kTile + tid / kTile;
+  const int rpix = tile_order_pixel(tid, kTileShift, kTileShift);  // Z order: a warp owns an 8 x 4 block
+  const int px = tx * kTile + (rpix & (kTile - 1)), py = ty * kTile + (rpix >> kTileShift);
   const bool in = px < cam.W && py < cam.H;
   const float fpx = (float)px, fpy = (float)py;
   const uint32_t off = w.tile_offset[tile];
   const uint32_t n = w.tile_offset[tile + 1] - off;
   const float4 *__restrict__ rec = w.rec_hot + (int64_t)f * N * H4;
   const float2 *__restrict__ box = w.rec_box + (int64_t)f * N;
-  // the warp's pixel box (two rows of 16; rows below the image are not in it)
+  // the warp's pixel box (an 8 x 4 block; pixels outside the image are not in it)
   const int bx0 = __reduce_min_sync(0xffffffffu, in ? px : 0x7fffffff);
   const int bx1 = __reduce_max_sync(0xffffffffu, in ? px : -1);
   const int by0 = __reduce_min_sync(0xffffffffu, in ? py : 0x7fffffff);
@@ -580,14 +581,14 @@ __global__ void __launch_bounds__(kTilePix) k_mask_cover_tiles(Work w, Prm prm, 
   const int n_cov = __syncthreads_count(cov);
   const bool keep = !(prm.discard > 0.f) || (float)n_cov >= prm.discard * (float)n_in;
   if (in) mask[((int64_t)f * cam.H + py) * cam.W + px] = (cov && keep) ? 1 : 0;
-  if (kMode == kCoverFusedSame) {  // compacted pixel list of the render tile (raster order)
+  if (kMode == kCoverFusedSame) {  // compacted pixel list of the render tile (Z order)
     const bool act = in && cov && keep;
     const unsigned bal = __ballot_sync(0xffffffffu, act);
     if (lane == 0) s_wcnt[wid] = __popc(bal);
     __syncthreads();
     int before = 0;
     for (int k = 0; k < wid; ++k) before += s_wcnt[k];
-    if (act) w.px_list[((int64_t)tile << (2 * kTileShift)) + before + __popc(bal & lanemask_lt())] = (uint8_t)tid;
+    if (act) w.px_list[((int64_t)tile << (2 * kTileShift)) + before + __popc(bal & lanemask_lt())] = (uint8_t)rpix;
     if (tid == 0) {
       w.tile_npix[tile] = keep ? (uint32_t)n_cov : 0u;
       w.tile_count[tile] = 0u;

@@ -16,7 +16,7 @@
 //   keys     [pairs] uint64       (float bits of z_c) << 32 | Gaussian index, bucketed by tile
 //   sorted   [pairs] uint32       Gaussian index, each tile's bucket in front-to-back order
 //   px_list  [F*T][tile pixels] u8 masked pixels of each render tile (index in the tile),
-//                                 compacted in raster order
+//                                 compacted in the tile's Z order
 //   items    [groups] uint32      (tile << 3 | 32-pixel group) work items, longest list first
 //   px_*     [F][H][W]            per-pixel state saved by the forward for the backward
 //   grad2d   [F][N][G2] float     per-(frame, unstable Gaussian) screen-space gradients

@@ -221,7 +221,7 @@ void launch_select_top_error(const SelBufs &b, int F, int C, int64_t n, uint32_t
 
 // ----------------------------------------------------------------------------- narrowing
 // One CTA of 2^(tws+ths) threads per render tile of the last forward: keeps the entries of
-// the tile's pixel list whose pixel is set in `mask`, in their order (raster order), and adds
+// the tile's pixel list whose pixel is set in `mask`, in their order (the tile's Z order), and adds
 // the tile's new pixel count to the masked-pixel counter.  With targets, warp g then forms
 // the fused L1 partials (colour, depth, depth count) of the tile's new group g, as the
 // forward does for its groups.
