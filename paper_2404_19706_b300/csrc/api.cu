@@ -46,6 +46,7 @@ struct rtg_ctx {
   Tuning tune;      // launch configuration of the next forward
   Tuning tune_fwd;  // ... and of the last one, which its backward follows
   bool bwd_done;    // a backward of the last forward has run (its 2D gradient rows are used)
+  bool fmask_ok;    // the last forward's composited-lane masks are intact (no binning since)
   bool narrowed;    // rtg_narrow_pixels reduced the last forward's pixel set
   SelBufs sel;      // scratch of rtg_select_top_error (ticket set per call)
   uint32_t *gauss_bits;  // [max_gaussians] per-frame error bits of rtg_error_count (kept zero)
@@ -367,6 +368,7 @@ __global__ void k_debug_extract(Work w, int64_t N, int F, int32_t *rect, uint32_
 rtg_status build_window_lists(rtg_ctx *ctx) {
   Window &win = ctx->win;
   win.lists = false;
+  ctx->fmask_ok = false;  // the list build bins over the last forward's composited-lane masks
   Prm P;
   rtg_status st = make_prm(ctx, &win.prm, P);
   if (st != RTG_OK) return st;
@@ -699,8 +701,9 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
     ProfScope ps(ctx, kPForward, s);
     // the persistent schedule finalizes the fused L1 in its last CTA
     const bool fused_loss = tcolor != nullptr && tn.schedule == 1;
+    // the composited-lane masks go over the call's bucket keys and staging, free after the sort
     launch_forward(gp.C, w, P, n, F, T, tn, color, depth, alpha, index_map, tcolor, tdepth,
-                   fused_loss ? loss_out : nullptr, w_c, w_d, s);
+                   fused_loss ? loss_out : nullptr, w_c, w_d, reinterpret_cast<uint32_t *>(w.keys), s);
   }
   if (tcolor != nullptr && tn.schedule != 1) {
     ProfScope ps(ctx, kPL1Loss, s);
@@ -708,6 +711,7 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
   }
   if ((st = check_launch(ctx, "render_forward")) != RTG_OK) return st;
   ctx->has_fwd = true;
+  ctx->fmask_ok = true;
   ctx->w_fwd = w;
   ctx->g = gp;
   ctx->prm = P;
@@ -722,6 +726,13 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
   ctx->narrowed = false;
   ctx->last_stream = s;
   return RTG_OK;
+}
+
+// The last forward's composited-lane masks, when its backward can use them: not after the
+// forward was narrowed to a pixel subset (its pixel groups changed), nor after a call that
+// binned again (the masks share the bucket keys' memory).
+static const uint32_t *fwd_masks(const rtg_ctx *ctx) {
+  return (ctx->fmask_ok && !ctx->narrowed) ? reinterpret_cast<const uint32_t *>(ctx->w_fwd.keys) : nullptr;
 }
 
 // The forward's projection zeroes the 2D gradient rows its backward accumulates into; a
@@ -830,7 +841,8 @@ rtg_status rtg_render_backward_l1(rtg_ctx *ctx, float *g_means, float *g_scales,
   if (st != RTG_OK) return st;
   {
     ProfScope ps(ctx, kPBackward, s);
-    launch_backward(ctx->C, ctx->w_fwd, ctx->prm, n, ctx->F, ctx->T, ctx->tune_fwd, nullptr, nullptr, ctx->l1, s);
+    launch_backward(ctx->C, ctx->w_fwd, ctx->prm, n, ctx->F, ctx->T, ctx->tune_fwd, nullptr, nullptr, ctx->l1,
+                    fwd_masks(ctx), s);
   }
   {
     ProfScope ps(ctx, kPProjectBackward, s);
@@ -856,7 +868,7 @@ rtg_status rtg_render_backward(rtg_ctx *ctx, const float *dL_dcolor, const float
   {
     ProfScope ps(ctx, kPBackward, s);
     launch_backward(ctx->C, ctx->w_fwd, ctx->prm, n, ctx->F, ctx->T, ctx->tune_fwd, dL_dcolor, dL_ddepth,
-                    L1Fused{nullptr, nullptr, nullptr, nullptr}, s);
+                    L1Fused{nullptr, nullptr, nullptr, nullptr}, fwd_masks(ctx), s);
   }
   {
     ProfScope ps(ctx, kPProjectBackward, s);

@@ -105,35 +105,44 @@ __device__ __forceinline__ void flush_rows(const BwdWarpSmem<C, B> &sm, int n, i
   for (int q = 0; q < (NV + 3) / 4; ++q) atomicAdd(row + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
 }
 
-// Replays the pixels of group `grp` of render tile `tile` (the forward's pixel grouping)
-// back to front.  Called by a whole warp; sm is the warp's own shared memory.
-template <int C, int B>
-__device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, int64_t N, int T, int tile, int grp,
-                                               BwdWarpSmem<C, B> &sm, const float *__restrict__ dL_dcolor,
-                                               const float *__restrict__ dL_ddepth, const L1Fused &l1) {
-  constexpr int H4 = (C <= 4) ? 3 : 4;
+// A lane's pixel of group `grp` of render tile `tile` (the forward's pixel grouping) and its
+// loss gradients, with the group's pixel centres and colour gradients stored in s_px / s_dc
+// for the row sums; also adds the depth gradient of the pixels' hit Gaussians (Eq. 4/5),
+// the depth depending on f only through the choice of the hit.
+template <int C>
+struct BwdPixel {
+  bool has;
+  int f, px, py;
+  float fpx, fpy;
+  uint32_t off, last;
+  float T_;
+  float dC[C];
+  float *g2base;
+};
+
+template <int C>
+__device__ __forceinline__ void bwd_pixel_prologue(const Work &w, const Prm &prm, int64_t N, int T, int tile, int grp,
+                                                   const float *__restrict__ dL_dcolor,
+                                                   const float *__restrict__ dL_ddepth, const L1Fused &l1,
+                                                   float2 *s_px, float (*s_dc)[32], BwdPixel<C> &o) {
   constexpr int G2 = (C <= 5) ? 16 : 20;
-  constexpr int R = B / 32;
   const int lane = threadIdx.x & 31;
   const int f = tile / T, lt = tile - f * T;
   const DevCam &cam = w.cams[f];
   const int tws = cam.tws, ths = cam.ths;
   const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-  const int npix_tile = (int)w.tile_npix[tile];
   const int q = grp * 32 + lane;
-  const bool has = q < npix_tile;
+  const bool has = q < (int)w.tile_npix[tile];
   const int my = has ? (int)w.px_list[((int64_t)tile << (tws + ths)) + q] : 0;
   const int px = (tx << tws) + (my & ((1 << tws) - 1)), py = (ty << ths) + (my >> tws);
   const float fpx = (float)px, fpy = (float)py;
   const int64_t HW = (int64_t)cam.H * cam.W;
   const int64_t pix = (int64_t)f * HW + (int64_t)py * cam.W + px;
-  const uint32_t off = w.tile_offset[tile];
   float T_ = 1.f, dLdD = 0.f;
   uint32_t last = 0;
   int hit = -1;
-  float dC[C];
 #pragma unroll
-  for (int c = 0; c < C; ++c) dC[c] = 0.f;
+  for (int c = 0; c < C; ++c) o.dC[c] = 0.f;
   if (has) {
     T_ = w.px_T[pix];
     last = w.px_last[pix];
@@ -142,24 +151,23 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
       const float sc = w.loss_scal[4], sd = w.loss_scal[5];
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        const int64_t o = ((int64_t)f * C + c) * HW + (int64_t)py * cam.W + px;
-        const float d = l1.color[o] - l1.tcolor[o];
-        dC[c] = d > 0.f ? sc : (d < 0.f ? -sc : 0.f);
+        const int64_t oc = ((int64_t)f * C + c) * HW + (int64_t)py * cam.W + px;
+        const float d = l1.color[oc] - l1.tcolor[oc];
+        o.dC[c] = d > 0.f ? sc : (d < 0.f ? -sc : 0.f);
       }
       const float Dh = l1.depth[pix], td = l1.tdepth[pix];
       const float d = Dh - td;
       dLdD = (Dh != -1.f && td > 0.f) ? (d > 0.f ? sd : (d < 0.f ? -sd : 0.f)) : 0.f;
     } else {
 #pragma unroll
-      for (int c = 0; c < C; ++c) dC[c] = dL_dcolor[((int64_t)f * C + c) * HW + (int64_t)py * cam.W + px];
+      for (int c = 0; c < C; ++c) o.dC[c] = dL_dcolor[((int64_t)f * C + c) * HW + (int64_t)py * cam.W + px];
       dLdD = dL_ddepth[pix];
     }
   }
   float *__restrict__ g2base = w.grad2d + (int64_t)f * N * G2;
-  // the group's pixels and colour gradients, read by every lane when the rows are summed
-  sm.px[lane] = make_float2(fpx, fpy);
+  s_px[lane] = make_float2(fpx, fpy);
 #pragma unroll
-  for (int c = 0; c < C; ++c) sm.dc[c][lane] = dC[c];
+  for (int c = 0; c < C; ++c) s_dc[c][lane] = o.dC[c];
 
   // ---- depth: gradient to the hit Gaussian's plane record or centre depth (Eq. 4/5)
   {
@@ -206,6 +214,40 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
       pending &= ~__ballot_sync(0xffffffffu, in);
     }
   }
+  o.has = has;
+  o.f = f;
+  o.px = px;
+  o.py = py;
+  o.fpx = fpx;
+  o.fpy = fpy;
+  o.off = w.tile_offset[tile];
+  o.last = last;
+  o.T_ = T_;
+  o.g2base = g2base;
+}
+
+// Replays the pixels of group `grp` of render tile `tile` (the forward's pixel grouping)
+// back to front, walking the tile's list with the forward's culling (no composited-lane
+// masks: a forward narrowed to a pixel subset).  Called by a whole warp; sm is the warp's
+// own shared memory.
+template <int C, int B>
+__device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, int64_t N, int T, int tile, int grp,
+                                               BwdWarpSmem<C, B> &sm, const float *__restrict__ dL_dcolor,
+                                               const float *__restrict__ dL_ddepth, const L1Fused &l1) {
+  constexpr int H4 = (C <= 4) ? 3 : 4;
+  constexpr int R = B / 32;
+  const int lane = threadIdx.x & 31;
+  BwdPixel<C> pxs;
+  bwd_pixel_prologue<C>(w, prm, N, T, tile, grp, dL_dcolor, dL_ddepth, l1, sm.px, sm.dc, pxs);
+  const bool has = pxs.has;
+  const int f = pxs.f, px = pxs.px, py = pxs.py;
+  const float fpx = pxs.fpx, fpy = pxs.fpy;
+  const uint32_t off = pxs.off, last = pxs.last;
+  float T_ = pxs.T_;
+  float dC[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) dC[c] = pxs.dC[c];
+  float *__restrict__ g2base = pxs.g2base;
 
   // bounding box of the warp's pixels (records whose support misses it were skipped by the
   // forward's identical test and contribute nothing here)
@@ -353,9 +395,185 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
   __syncwarp();  // the next group rewrites the warp's pixel arrays
 }
 
+// ---- backward with the forward's composited-lane masks
+// The forward left, for each entry j of a tile's list and each 32-pixel group g, the mask of
+// the lanes that composited entry j, at fmask[(off + j) * groups + g].  The backward then
+// walks the list in batches of 32 entries back to front, stages only the entries some lane
+// composited, and each lane replays its own fragments only (its bit of each staged mask),
+// so no lane steps through fragments it did not composite.  The unstable records' rows are
+// then summed one record a lane, as in flush_rows.
+template <int C>
+struct BwdFlSmem {
+  static constexpr int H4 = (C <= 4) ? 3 : 4;
+  float4 rec[H4][32];    // the batch's composited entries' records, in list order
+  int2 jr[32];           // their list position and unstable rank
+  uint32_t am[32];       // their composited lanes
+  uint8_t us[32];        // staged slot -> row slot of an unstable record
+  uint8_t uk[32];        // row slot -> staged slot
+  float2 wg[32][33];     // row slot x pixel: (f T, dL/dalpha); zero where not composited
+  float2 px[32];
+  float dc[C][32];
+};
+
+template <int C>
+constexpr size_t bwd_fl_smem_bytes() { return 8 * sizeof(BwdFlSmem<C>); }
+
+template <int C>
+__device__ __forceinline__ void backward_group_fl(const Work &w, const Prm &prm, int64_t N, int T, int tile, int grp,
+                                                  BwdFlSmem<C> &sm, const uint32_t *__restrict__ fmask,
+                                                  const float *__restrict__ dL_dcolor,
+                                                  const float *__restrict__ dL_ddepth, const L1Fused &l1) {
+  constexpr int H4 = (C <= 4) ? 3 : 4;
+  constexpr int NV = 6 + C, G2 = (C <= 5) ? 16 : 20;
+  const int lane = threadIdx.x & 31;
+  BwdPixel<C> pxs;
+  bwd_pixel_prologue<C>(w, prm, N, T, tile, grp, dL_dcolor, dL_ddepth, l1, sm.px, sm.dc, pxs);
+  const float fpx = pxs.fpx, fpy = pxs.fpy;
+  const uint32_t off = pxs.off;
+  const int f = pxs.f;
+  float T_ = pxs.T_;
+  float dC[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) dC[c] = pxs.dC[c];
+  float *__restrict__ g2base = pxs.g2base;
+  const DevCam &cam = w.cams[f];
+  const int ngrp = 1 << (cam.tws + cam.ths - 5);
+  const uint32_t maxlast = __reduce_max_sync(0xffffffffu, pxs.last);
+  const float4 *__restrict__ rec = w.rec_hot + (int64_t)f * N * H4;
+  float S[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) S[c] = 0.f;
+
+  // entry b_end - 32 + lane of the list: its mask and, when some lane composited it, its
+  // record and unstable rank (fetched one batch ahead)
+  auto fetch = [&](int b_end_, uint32_t &am_, float4 (&rr)[H4], int &rank_) {
+    const int jq = b_end_ - 32 + lane;
+    am_ = jq >= 0 ? fmask[(int64_t)(off + (uint32_t)jq) * ngrp + grp] : 0u;
+    rank_ = -1;
+    if (am_ != 0u) {
+      const uint32_t gid = w.sorted[off + jq];
+#pragma unroll
+      for (int k = 0; k < H4; ++k) rr[k] = rec[(int64_t)gid * H4 + k];
+      rank_ = (H4 == 3) ? __float_as_int(rr[2].w) : __float_as_int(w.rec_cold[((int64_t)f * N + gid) * 2 + 1].y);
+    }
+  };
+  uint32_t am = 0u;
+  float4 r[H4];
+  int rk = -1;
+  fetch((int)maxlast, am, r, rk);
+  for (int b_end = (int)maxlast; b_end > 0; b_end -= 32) {
+    uint32_t amn = 0u;
+    float4 rn[H4];
+    int rkn = -1;
+    if (b_end > 32) fetch(b_end - 32, amn, rn, rkn);
+    // stage the composited entries in list order; number the unstable ones
+    const unsigned bal = __ballot_sync(0xffffffffu, am != 0u);
+    const int slot = __popc(bal & lanemask_lt());
+    const unsigned ubal = __ballot_sync(0xffffffffu, am != 0u && rk >= 0);
+    const int nu = __popc(ubal);
+    if (am != 0u) {
+#pragma unroll
+      for (int k = 0; k < H4; ++k) sm.rec[k][slot] = r[k];
+      sm.jr[slot] = make_int2(b_end - 32 + lane, rk);
+      sm.am[slot] = am;
+      if (rk >= 0) {
+        const int u = __popc(ubal & lanemask_lt());
+        sm.us[slot] = (uint8_t)u;
+        sm.uk[u] = (uint8_t)slot;
+      }
+    }
+    // the rows of this batch's unstable records start at zero for every pixel
+    for (int u = 0; u < nu; ++u) sm.wg[u][lane] = make_float2(0.f, 0.f);
+    __syncwarp();
+    // this lane's fragments among the staged entries: bit k = lane's bit of mask k
+    const int cnt = __popc(bal);
+    uint32_t mine = 0u;
+    for (int k = 0; k < cnt; ++k) mine |= ((sm.am[k] >> lane) & 1u) << k;
+    // back to front over this lane's own fragments: the transmission in front of each by
+    // division, dL/df from the colour behind it, and for an unstable record (f T, dL/dalpha)
+    while (mine) {
+      const int k = 31 - __clz(mine);
+      mine ^= 1u << k;
+      const float4 a0 = sm.rec[0][k], a1 = sm.rec[1][k];
+      float dx, dy, t1, t2, g;
+      const float fa = footprint(fpx, fpy, a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, prm.f_max, dx, dy, t1, t2,
+                                 g);
+      const float iom = __fdividef(1.f, 1.f - fa);  // 1 - f >= 1 - f_max: a normal divisor
+      T_ = T_ * iom;
+      const float wgt = fa * T_;
+      const float4 c0 = sm.rec[2][k];
+      float cw[8] = {c0.x, c0.y, c0.z, c0.w, 0.f, 0.f, 0.f, 0.f};
+      if (H4 == 4) {
+        const float4 c1 = sm.rec[3 % H4][k];
+        cw[4] = c1.x; cw[5] = c1.y; cw[6] = c1.z; cw[7] = c1.w;
+      }
+      float dLdf = 0.f;
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        dLdf = fmaf(dC[c], fmaf(cw[c], T_, -S[c] * iom), dLdf);
+        S[c] = fmaf(cw[c], wgt, S[c]);
+      }
+      if (sm.jr[k].y >= 0) {
+        const float G = a1.w * g < prm.f_max ? dLdf * g : 0.f;  // unclamped branch of min(f_max, alpha g)
+        sm.wg[sm.us[k]][lane] = make_float2(wgt, G);
+      }
+    }
+    __syncwarp();
+    // the rows of the unstable records, one a lane, over each record's composited pixels
+    if (lane < nu) {
+      const int k = sm.uk[lane];
+      const float4 a0 = sm.rec[0][k], a1 = sm.rec[1][k];
+      const int rank = sm.jr[k].y;
+      float acc[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] = 0.f;
+      unsigned m = sm.am[k];
+      while (m) {
+        const int p = __ffs(m) - 1;
+        m &= m - 1u;
+        const float2 w_ = sm.wg[lane][p];
+        const float2 pp = sm.px[p];
+        const float dx = (pp.x - a0.x) - a0.z, dy = (pp.y - a0.y) - a0.w;
+        const float t1 = fmaf(a1.x, dx, a1.y * dy), t2 = a1.z * dy;
+        const float G = w_.y, Gx = G * dx;
+        acc[0] = fmaf(G, t1, acc[0]);
+        acc[1] = fmaf(G, t2, acc[1]);
+        acc[2] = fmaf(Gx, dx, acc[2]);
+        acc[3] = fmaf(Gx, dy, acc[3]);
+        acc[4] = fmaf(G * dy, dy, acc[4]);
+        acc[5] += G;
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[6 + c] = fmaf(w_.x, sm.dc[c][p], acc[6 + c]);
+      }
+      const float al = a1.w * kLn2, c2 = 2.f * al, kc = -al * kQScale2;
+      float v[4 * ((NV + 3) / 4)];
+      v[0] = c2 * a1.x * acc[0];
+      v[1] = c2 * fmaf(a1.y, acc[0], a1.z * acc[1]);
+      v[2] = kc * acc[2];
+      v[3] = 2.f * kc * acc[3];
+      v[4] = kc * acc[4];
+#pragma unroll
+      for (int qv = 5; qv < NV; ++qv) v[qv] = acc[qv];
+#pragma unroll
+      for (int qv = NV; qv < 4 * ((NV + 3) / 4); ++qv) v[qv] = 0.f;
+      float4 *row = reinterpret_cast<float4 *>(g2base + (int64_t)rank * G2);
+#pragma unroll
+      for (int qv = 0; qv < (NV + 3) / 4; ++qv)
+        atomicAdd(row + qv, make_float4(v[4 * qv], v[4 * qv + 1], v[4 * qv + 2], v[4 * qv + 3]));
+    }
+    __syncwarp();  // the next batch rewrites the staging
+    am = amn;
+    rk = rkn;
+#pragma unroll
+    for (int k = 0; k < H4; ++k) r[k] = rn[k];
+  }
+  __syncwarp();  // the next group rewrites the warp's pixel arrays
+}
+
 struct BwdIn {
   const float *dL_dcolor, *dL_ddepth;
   L1Fused l1;
+  const uint32_t *fmask;  // the forward's composited-lane masks (nullptr: walk with the culling)
 };
 
 // Schedule 0: CTA `tile` with one warp per 32-pixel group of the tile's pixel list.
@@ -384,6 +602,39 @@ __global__ void __launch_bounds__(256, 2) k_backward_queue(Work w, Prm prm, int6
   while (it < nitems) {
     const uint32_t item = w.items[it];
     backward_group<C, B>(w, prm, N, T, (int)(item >> 3), (int)(item & 7u), *sm, in.dL_dcolor, in.dL_ddepth, in.l1);
+    uint32_t nx = 0;
+    if (lane == 0) nx = nwarps + (uint32_t)atomicAdd(w.counters + kQBwd, 1ull);
+    it = __shfl_sync(0xffffffffu, nx, 0);
+  }
+}
+
+// Schedule 0 and 1 with the forward's composited-lane masks.
+template <int C>
+__global__ void __launch_bounds__(kMaxTilePix, 2) k_backward_fl(Work w, Prm prm, int64_t N, int T, BwdIn in) {
+  grid_dep_wait();
+  extern __shared__ float4 bwd_dyn_smem[];
+  if (w.counters[kSkip] != 0ull) return;
+  const int tile = blockIdx.x, wid = threadIdx.x >> 5;
+  if (wid * 32 >= (int)w.tile_npix[tile]) return;
+  BwdFlSmem<C> *sm = reinterpret_cast<BwdFlSmem<C> *>(bwd_dyn_smem) + wid;
+  backward_group_fl<C>(w, prm, N, T, tile, wid, *sm, in.fmask, in.dL_dcolor, in.dL_ddepth, in.l1);
+}
+
+template <int C>
+__global__ void __launch_bounds__(256, 2) k_backward_fl_queue(Work w, Prm prm, int64_t N, int T, BwdIn in,
+                                                              int spread) {
+  grid_dep_wait();
+  extern __shared__ float4 bwd_dyn_smem[];
+  if (w.counters[kSkip] != 0ull) return;
+  const uint32_t nitems = (uint32_t)w.counters[kItems];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  BwdFlSmem<C> *sm = reinterpret_cast<BwdFlSmem<C> *>(bwd_dyn_smem) + wid;
+  const uint32_t nwarps = gridDim.x * 8u;
+  uint32_t it = first_item(w, wid, spread);
+  while (it < nitems) {
+    const uint32_t item = w.items[it];
+    backward_group_fl<C>(w, prm, N, T, (int)(item >> 3), (int)(item & 7u), *sm, in.fmask, in.dL_dcolor,
+                         in.dL_ddepth, in.l1);
     uint32_t nx = 0;
     if (lane == 0) nx = nwarps + (uint32_t)atomicAdd(w.counters + kQBwd, 1ull);
     it = __shfl_sync(0xffffffffu, nx, 0);
@@ -768,6 +1019,17 @@ __global__ void __launch_bounds__(256) k_sh_backward(GaussPtrs g, Work w, int F,
   }
 }
 
+template <int C>
+static void launch_backward_fl(const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn,
+                               const BwdIn &in, cudaStream_t s) {
+  if (tn.schedule == 1)
+    launch(k_backward_fl_queue<C>, tn.num_sms * tn.ctas_per_sm, 256, bwd_fl_smem_bytes<C>(), s, w, prm, N, T, in,
+           tn.ctas_per_sm <= 2 ? 1 : 0);
+  else
+    launch(k_backward_fl<C>, F * T, 1 << (tn.tws + tn.ths),
+           (size_t)((1 << (tn.tws + tn.ths)) / 32) * sizeof(BwdFlSmem<C>), s, w, prm, N, T, in);
+}
+
 template <int C, int B>
 static void launch_backward_cb(const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn,
                                const BwdIn &in, cudaStream_t s) {
@@ -787,6 +1049,12 @@ static void set_backward_attributes() {
 }
 
 void init_backward_attributes() {
+  cudaFuncSetAttribute(k_backward_fl_queue<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)bwd_fl_smem_bytes<3>());
+  cudaFuncSetAttribute(k_backward_fl<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_fl_smem_bytes<3>());
+  cudaFuncSetAttribute(k_backward_fl_queue<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)bwd_fl_smem_bytes<8>());
+  cudaFuncSetAttribute(k_backward_fl<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_fl_smem_bytes<8>());
   set_backward_attributes<3, 32>();
   set_backward_attributes<3, 64>();
   set_backward_attributes<8, 32>();
@@ -794,8 +1062,14 @@ void init_backward_attributes() {
 }
 
 void launch_backward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn,
-                     const float *dL_dcolor, const float *dL_ddepth, const L1Fused &l1, cudaStream_t s) {
-  const BwdIn in{dL_dcolor, dL_ddepth, l1};
+                     const float *dL_dcolor, const float *dL_ddepth, const L1Fused &l1, const uint32_t *fmask,
+                     cudaStream_t s) {
+  const BwdIn in{dL_dcolor, dL_ddepth, l1, fmask};
+  if (fmask != nullptr) {
+    if (C == 3) launch_backward_fl<3>(w, prm, N, F, T, tn, in, s);
+    else launch_backward_fl<8>(w, prm, N, F, T, tn, in, s);
+    return;
+  }
   if (C == 3) {
     if (tn.batch == 64) launch_backward_cb<3, 64>(w, prm, N, F, T, tn, in, s);
     else launch_backward_cb<3, 32>(w, prm, N, F, T, tn, in, s);

@@ -12,6 +12,8 @@
 // Two schedules share that per-warp body: one CTA per tile (one warp per 32 masked
 // pixels), or persistent warps that take (tile, group) items from the cost-ordered queue
 // spanning every frame of the call.
+#include <type_traits>
+
 #include "kernels.cuh"
 #include "project.cuh"
 
@@ -23,6 +25,7 @@ struct FwdOut {
   const float *tcolor, *tdepth;  // fused L1 targets (nullptr: not fused)
   float *loss_out;               // non-null: the persistent forward finalizes the L1 loss
   float w_c, w_d;
+  uint32_t *fmask;               // non-null: the composited-lane masks for the backward
 };
 
 // Renders the pixels of group `grp` (32 consecutive entries of the tile's pixel list) of
@@ -63,6 +66,13 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
   uint32_t last = 0, nfrag = 0, nrec = 0;
   int hit_j = -1;
   bool done = !has;
+  // With out.fmask, entry j of the tile's list gets, for this group, the mask of the lanes
+  // that composited it (0 where culled or composited by none), at (off + j) * groups + grp:
+  // the backward then replays each lane's own fragments only.  Every entry of a batch the
+  // warp walks is written, and the backward walks no further than the last composited one.
+  const int ngrp = 1 << (tws + ths - 5);
+  using Bits = typename std::conditional<(B > 32), unsigned long long, uint32_t>::type;
+  Bits ebits = 0;  // the batch's entries (list position - b0) this lane composited
   // the records of batch b0 + B, and the indices of batch b0 + 2B, are fetched while batch
   // b0 is composited, so a batch waits on one L2 round trip rather than index -> record
   float4 r[R][H4];
@@ -140,6 +150,7 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
         T_ = Tn;
         last = jj + 1;
         ++nfrag;
+        ebits |= (Bits)1 << (jj - b0);
         return true;
       };
       auto alpha_of = [&](int k) {
@@ -159,6 +170,24 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
       if (!done && k < cnt && !blend(k, alpha_of(k))) done = true;
     }
     __syncwarp();
+    if (out.fmask != nullptr) {
+      // lane L gets the composited lanes of entry b0 + 32u + L (a bit transpose by ballots;
+      // culled entries get none) and stores them, one coalesced store per 32 entries
+#pragma unroll
+      for (int u = 0; u < R; ++u) {
+        const uint32_t wv = (uint32_t)(ebits >> (32 * u));
+        uint32_t am = 0u;
+        if (__any_sync(0xffffffffu, wv != 0u)) {
+#pragma unroll
+          for (int e = 0; e < 32; ++e) {
+            const unsigned m = __ballot_sync(0xffffffffu, (wv >> e) & 1u);
+            am = lane == e ? m : am;
+          }
+        }
+        if (valid[u]) out.fmask[(int64_t)(off + b0 + (uint32_t)(u * 32 + lane)) * ngrp + grp] = am;
+      }
+      ebits = 0;
+    }
 #pragma unroll
     for (int u = 0; u < R; ++u) {
 #pragma unroll
@@ -310,9 +339,9 @@ static void launch_forward_cb(const Work &w, const Prm &prm, int64_t N, int F, i
 
 void launch_forward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn, float *color,
                     float *depth, float *alpha, int32_t *index_map, const float *tcolor, const float *tdepth,
-                    float *loss_out, float w_c, float w_d, cudaStream_t s) {
+                    float *loss_out, float w_c, float w_d, uint32_t *fmask, cudaStream_t s) {
   const FwdOut out{color, depth, alpha, index_map, tcolor, tdepth,
-                   (tn.schedule == 1 && tcolor != nullptr) ? loss_out : nullptr, w_c, w_d};
+                   (tn.schedule == 1 && tcolor != nullptr) ? loss_out : nullptr, w_c, w_d, fmask};
   if (C == 3) {
     if (tn.batch == 64) launch_forward_cb<3, 64>(w, prm, N, F, T, tn, out, s);
     else launch_forward_cb<3, 32>(w, prm, N, F, T, tn, out, s);

@@ -214,12 +214,18 @@ void launch_decode_rgbd(int F, int H, int W, const uint8_t *rgb, const uint16_t 
 // forward.cu
 // loss_out != nullptr (persistent schedule with fused targets): the forward also finalizes
 // the L1 loss (loss_out[0..2] and the gradient scales), as launch_loss_finalize would.
+// fmask != nullptr: also write, per (tile list entry, 32-pixel group), the lanes that
+// composited the entry (8 x max_pairs words; the bucket keys and staging of the call are
+// free by then), for launch_backward.
 void launch_forward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn, float *color,
                     float *depth, float *alpha, int32_t *index_map, const float *tcolor, const float *tdepth,
-                    float *loss_out, float w_c, float w_d, cudaStream_t s);
+                    float *loss_out, float w_c, float w_d, uint32_t *fmask, cudaStream_t s);
 // backward.cu
+// fmask: the last forward's composited-lane masks (nullptr after the forward was narrowed to
+// a pixel subset: the groups changed, so the backward walks the lists with the culling).
 void launch_backward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn,
-                     const float *dL_dcolor, const float *dL_ddepth, const L1Fused &l1, cudaStream_t s);
+                     const float *dL_dcolor, const float *dL_ddepth, const L1Fused &l1, const uint32_t *fmask,
+                     cudaStream_t s);
 void init_backward_attributes();
 void launch_loss_finalize(const Work &w, int FT, int gshift, int C, float w_c, float w_d, float *loss_out,
                           cudaStream_t s);
