@@ -442,9 +442,9 @@ def step_sum(alg, per_launch, extra=()):
 # DRAM bytes (read + write) per launch of a kernel from one ncu capture of bench.py, keyed
 # by (workload, kernel, render tile, record batch, schedule); the roofline's `traffic` is
 # filled only when the run's workload, dominant kernel and tuning match a captured one of
-# the kernel as it is now.  Source and command: profiles/masked_step_1M_640x480_launches.md.
+# the kernel as it is now.  Source and command: the profiles/ summary named beside each.
 NCU_TRAFFIC = {
-    ("masked-step", "backward", 8, 8, 64, 1): 19_233_280,  # k_backward_queue<3, 64> (current capture)
+    ("masked-step", "backward", 8, 8, 64, 1): 17_403_904,  # k_backward_fl_queue<3> (compositing_fwd_bwd_1M_640x480_ncu.md)
 }
 
 
@@ -772,6 +772,8 @@ def run_ours(args, kw=TARGET, lite=False):
                        "mask": "built once before the optimisation", "mask_build_ms": round(mask_ms, 4),
                        "mask_coverage": round(coverage, 4), "pairs": K, "fragments_per_step": stats["fragments"],
                        "active_lanes_per_record": round(stats["fragments"] / max(stats["warp_records"], 1), 2),
+                       "backward_active_lanes_per_step": round(stats["fragments"] / max(stats["backward_steps"], 1),
+                                                               2),
                        "alg_bytes_per_step": b_step, "step_hbm_roofline_frac": round(step_frac, 4),
                        "roofline": roofline, "tuning": ctx.get_tuning().as_dict(),
                        "kernel_ms_per_launch": {k: round(v, 5) for k, v in per_launch.items() if v > 0}}
@@ -820,6 +822,9 @@ def run_ours(args, kw=TARGET, lite=False):
                        "pairs": K, "visible": V, "fragments_per_step": stats["fragments"],
                        "warp_records_per_step": stats["warp_records"],
                        "active_lanes_per_record": round(stats["fragments"] / max(stats["warp_records"], 1), 2),
+                       "backward_steps_per_step": stats["backward_steps"],
+                       "backward_active_lanes_per_step": round(stats["fragments"] / max(stats["backward_steps"], 1),
+                                                               2),
                        "fragments_per_sec": round(job_rate(world, ms_step, stats["fragments"]), 1),
                        "alg_bytes_per_step": b_step, "alg_bytes_terms": b_terms, "alg_bytes_rule": b_rule,
                        "step_hbm_roofline_frac": round(step_frac, 4),

@@ -124,6 +124,9 @@ typedef struct {
                              by rtg_window_begin (0 without a window) */
   int64_t window_pairs;   /* stable (Gaussian, tile) pairs in the window's cached sorted lists
                              (0 without cached lists) */
+  int64_t backward_steps; /* steps of the last backward's fragment replay: each step a warp
+                             takes one fragment on every lane that still has one (so
+                             fragments / backward_steps = active lanes of 32) */
 } rtg_stats;
 
 /* Launch configuration of the render path.  Section 3.1 rasterises by screen tiles but

@@ -50,7 +50,8 @@ class rtg_capacity(Structure):
 class rtg_stats(Structure):
     _fields_ = [("pairs", c_int64), ("fragments", c_int64), ("visible", c_int64), ("masked_pixels", c_int64),
                 ("n_unstable", c_int64), ("warp_records", c_int64), ("status", c_int32), ("max_tile_pairs", c_int32), ("tile_w", c_int32),
-                ("tile_h", c_int32), ("window_stable", c_int64), ("window_pairs", c_int64)]
+                ("tile_h", c_int32), ("window_stable", c_int64), ("window_pairs", c_int64),
+                ("backward_steps", c_int64)]
 
 
 class rtg_tuning(Structure):

@@ -1250,6 +1250,7 @@ rtg_status rtg_get_stats(rtg_ctx *ctx, rtg_stats *out) {
   out->masked_pixels = (int64_t)c[kMaskedPix];
   out->n_unstable = (int64_t)c[kNumUnstable];
   out->warp_records = (int64_t)c[kWarpRecords];
+  out->backward_steps = (int64_t)c[kBwdSteps];
   out->max_tile_pairs = (int32_t)c[kMaxTilePairs];
   out->status = (int32_t)*(volatile uint32_t *)ctx->status_host;
   out->tile_w = 1 << ctx->tune_fwd.tws;

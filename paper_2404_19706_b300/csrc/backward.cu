@@ -457,7 +457,7 @@ __device__ __forceinline__ void backward_group_fl(const Work &w, const Prm &prm,
       rank_ = (H4 == 3) ? __float_as_int(rr[2].w) : __float_as_int(w.rec_cold[((int64_t)f * N + gid) * 2 + 1].y);
     }
   };
-  uint32_t am = 0u;
+  uint32_t am = 0u, nsteps = 0u;
   float4 r[H4];
   int rk = -1;
   fetch((int)maxlast, am, r, rk);
@@ -489,6 +489,7 @@ __device__ __forceinline__ void backward_group_fl(const Work &w, const Prm &prm,
     const int cnt = __popc(bal);
     uint32_t mine = 0u;
     for (int k = 0; k < cnt; ++k) mine |= ((sm.am[k] >> lane) & 1u) << k;
+    nsteps += __reduce_max_sync(0xffffffffu, (unsigned)__popc(mine));
     // back to front over this lane's own fragments: the transmission in front of each by
     // division, dL/df from the colour behind it, and for an unstable record (f T, dL/dalpha)
     while (mine) {
@@ -567,6 +568,7 @@ __device__ __forceinline__ void backward_group_fl(const Work &w, const Prm &prm,
 #pragma unroll
     for (int k = 0; k < H4; ++k) r[k] = rn[k];
   }
+  if (lane == 0 && nsteps) atomicAdd(w.counters + kBwdSteps, (unsigned long long)nsteps);
   __syncwarp();  // the next group rewrites the warp's pixel arrays
 }
 

@@ -57,6 +57,7 @@ enum Counter {
   kQFwd = 10 * kCounterStride,        // next item of the persistent forward (past the first one per warp)
   kQBwd = 11 * kCounterStride,        // next item of the persistent backward
   kWarpRecords = 12 * kCounterStride, // records the forward's warps walked after culling
+  kBwdSteps = 13 * kCounterStride,    // steps of the backward's per-lane fragment replay (warp-wide)
   kWinStable = 15 * kCounterStride,   // projected (frame, stable Gaussian) entries of the open window (kept)
 };
 constexpr int kNumCounterSlots = 16;  // slots; all but kWinStable are cleared at the start of every call

@@ -71,7 +71,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(_lib.rtg_render_params) == 9 * 4
     assert ctypes.sizeof(_lib.rtg_gaussians) == 8 + 8 + 13 * 8 + 8 + 8  # + sh_degree, padded
     assert ctypes.sizeof(_lib.rtg_capacity) == 8 + 4 * 4 + 8
-    assert ctypes.sizeof(_lib.rtg_stats) == 6 * 8 + 4 * 4 + 2 * 8  # + the window counters
+    assert ctypes.sizeof(_lib.rtg_stats) == 6 * 8 + 4 * 4 + 3 * 8  # + window counters, backward steps
     assert ctypes.sizeof(_lib.rtg_tuning) == 8 * 4
     assert ctypes.sizeof(_lib.rtg_add_params) == 6 * 4 + 8
     assert ctypes.sizeof(_lib.rtg_state_params) == 5 * 4
