@@ -241,6 +241,24 @@ rtg_status rtg_render_forward_l1(rtg_ctx *ctx, const rtg_camera *cams, int32_t F
 rtg_status rtg_render_backward_l1(rtg_ctx *ctx, float *g_means, float *g_scales, float *g_quats, float *g_opacity,
                                   float *g_colors, int32_t accumulate, void *stream);
 
+/* One keyframe batch split by frame over several GPUs (each rank renders its own frames of
+ * the batch on its own context).  The means of Eq. 7 run over the pixels of the whole batch,
+ * so a rank's backward needs the batch's pixel counts, not its own:
+ *   rtg_loss_counts writes, after an rtg_render_forward_l1 (or a fused masked forward with
+ *   targets), counts_out (device double[4]) = (P, P_d, sum |C_hat - C|, sum |D_hat - D|)
+ *   of that forward: its masked pixels, its pixels in the depth term, and its two L1 sums;
+ *   the caller sums these over the ranks (one all-reduce);
+ *   rtg_set_loss_scales then sets the next rtg_render_backward_l1's gradient scales from the
+ *   summed counts totals (device double[4]): w_color / (P C) and w_depth / P_d, and, when
+ *   loss_out (device float[3]) is not NULL, writes the batch's loss (L, L_color, L_depth).
+ * Each rank's gradients are then its share of the batch gradient, and their sum (a second
+ * all-reduce of the compact gradient arrays) is the gradient of the whole batch; every rank
+ * applies the same Adam step.  Asynchronous on `stream`; RTG_ERR_STATE without a forward
+ * with targets, RTG_ERR_ARG for NULL counts. */
+rtg_status rtg_loss_counts(rtg_ctx *ctx, double *counts_out, void *stream);
+rtg_status rtg_set_loss_scales(rtg_ctx *ctx, const double *totals, float w_color, float w_depth, float *loss_out,
+                               void *stream);
+
 /* The unstable-pixel mask and the forward in one pass (Supplement B with Section 3.1):
  * builds the mask exactly as rtg_unstable_mask does and writes it to mask_out [F,H,W]
  * (every in-image pixel), then renders exactly those pixels as rtg_render_forward does,

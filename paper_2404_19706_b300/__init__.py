@@ -39,6 +39,8 @@ from .api import (  # noqa: E402,F401
     profile_enable,
     profile_read,
     alu_probe,
+    loss_counts,
+    set_loss_scales,
     render_backward,
     render_backward_l1,
     render_forward_l1,

@@ -141,6 +141,8 @@ SIGNATURES = [
     ("rtg_profile_kind_name", c_char_p, [c_int32]),
     ("rtg_profile_read", c_int32, [c_void_p, POINTER(c_int64), POINTER(ctypes.c_double), c_int32]),
     ("rtg_alu_probe", c_int32, [c_int32, c_int32, c_void_p, POINTER(c_int64), c_void_p]),
+    ("rtg_loss_counts", c_int32, [c_void_p, c_void_p, c_void_p]),
+    ("rtg_set_loss_scales", c_int32, [c_void_p, c_void_p, c_float, c_float, c_void_p, c_void_p]),
     ("rtg_debug_binning", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
 ]
 

@@ -358,6 +358,24 @@ def render_backward_l1(ctx: Context, g_means, g_scales, g_quats, g_opacity, g_co
     _check(st, "rtg_render_backward_l1", ctx.ptr)
 
 
+def loss_counts(ctx: Context, counts_out: torch.Tensor, stream=None):
+    """rtg_loss_counts: (P, P_d, L1 colour sum, L1 depth sum) of the last forward with targets
+    into a float64 device tensor of 4."""
+    _check(_lib.load().rtg_loss_counts(ctx.ptr, _ptr(counts_out, torch.float64, "counts_out"), _stream(stream)),
+           "rtg_loss_counts", ctx.ptr)
+
+
+def set_loss_scales(ctx: Context, totals: torch.Tensor, w_color: float, w_depth: float, loss_out=None,
+                    stream=None):
+    """rtg_set_loss_scales: the next backward_l1's gradient scales from batch totals (float64
+    device tensor of 4, summed rtg_loss_counts outputs); loss_out (float32 device [3]) gets the
+    batch's loss."""
+    st = _lib.load().rtg_set_loss_scales(ctx.ptr, _ptr(totals, torch.float64, "totals"), float(w_color),
+                                         float(w_depth), _ptr(loss_out, torch.float32, "loss_out"),
+                                         _stream(stream))
+    _check(st, "rtg_set_loss_scales", ctx.ptr)
+
+
 def l1_loss(ctx: Context, color, depth, target_color, target_depth, mask, w_color: float, w_depth: float,
             loss_out, dL_dcolor, dL_ddepth, stream=None):
     F, C, H, W = color.shape

@@ -853,6 +853,28 @@ rtg_status rtg_render_backward_l1(rtg_ctx *ctx, float *g_means, float *g_scales,
   return check_launch(ctx, "render_backward_l1");
 }
 
+rtg_status rtg_loss_counts(rtg_ctx *ctx, double *counts_out, void *stream) {
+  if (ctx == nullptr || counts_out == nullptr) return RTG_ERR_ARG;
+  if (!ctx->has_fwd || ctx->l1.tcolor == nullptr)
+    return fail(ctx, RTG_ERR_STATE, "loss_counts without a preceding forward with targets");
+  cudaStream_t s = (cudaStream_t)stream;
+  launch_loss_counts(ctx->w_fwd, ctx->C, counts_out, s);
+  ctx->last_stream = s;
+  return check_launch(ctx, "loss_counts");
+}
+
+rtg_status rtg_set_loss_scales(rtg_ctx *ctx, const double *totals, float w_color, float w_depth, float *loss_out,
+                               void *stream) {
+  if (ctx == nullptr || totals == nullptr) return RTG_ERR_ARG;
+  if (!ctx->has_fwd || ctx->l1.tcolor == nullptr)
+    return fail(ctx, RTG_ERR_STATE, "set_loss_scales without a preceding forward with targets");
+  if (!(w_color >= 0.f) || !(w_depth >= 0.f)) return fail(ctx, RTG_ERR_ARG, "loss weights must be >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  launch_set_loss_scales(ctx->w_fwd, ctx->C, totals, w_color, w_depth, loss_out, s);
+  ctx->last_stream = s;
+  return check_launch(ctx, "set_loss_scales");
+}
+
 rtg_status rtg_render_backward(rtg_ctx *ctx, const float *dL_dcolor, const float *dL_ddepth, float *g_means,
                                float *g_scales, float *g_quats, float *g_opacity, float *g_colors,
                                int32_t accumulate, void *stream) {

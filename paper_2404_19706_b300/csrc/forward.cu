@@ -319,6 +319,9 @@ __global__ void __launch_bounds__(256, fwd_min_ctas<C, B>()) k_forward_queue(Wor
       out.loss_out[2] = Ld;
       w.loss_scal[4] = np > 0.f ? out.w_c / (np * (float)C) : 0.f;
       w.loss_scal[5] = nd > 0.0 ? out.w_d / (float)nd : 0.f;
+      w.loss_scal[1] = Lc;
+      w.loss_scal[2] = Ld;
+      w.counters[kDepthPix] = (unsigned long long)nd;
       w.loss_acc[0] = 0.0;
       w.loss_acc[1] = 0.0;
       w.loss_acc[2] = 0.0;

@@ -233,6 +233,9 @@ void launch_project_backward(const GaussPtrs &g, const Work &w, const Prm &prm, 
                              float *g_scales, float *g_quats, float *g_opacity, float *g_colors, bool accumulate,
                              cudaStream_t s);
 // loss_adam_mask.cu
+void launch_loss_counts(const Work &w, int C, double *out, cudaStream_t s);
+void launch_set_loss_scales(const Work &w, int C, const double *tot, float w_c, float w_d, float *loss_out,
+                            cudaStream_t s);
 void launch_l1_loss(const Work &w, int F, int C, int H, int W, const float *color, const float *depth,
                     const float *tcolor, const float *tdepth, const uint8_t *mask, float w_c, float w_d,
                     float *loss_out, float *dL_dcolor, float *dL_ddepth, cudaStream_t s);

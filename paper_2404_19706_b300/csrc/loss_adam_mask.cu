@@ -81,8 +81,52 @@ __global__ void __launch_bounds__(256) k_loss_reduce(Work w, int F, int C, int H
     loss_out[2] = Ld;
     w.loss_scal[4] = np > 0.f ? w_c / (np * (float)C) : 0.f;
     w.loss_scal[5] = nd > 0.f ? w_d / nd : 0.f;
+    w.loss_scal[1] = Lc;
+    w.loss_scal[2] = Ld;
+    w.counters[kDepthPix] = (unsigned long long)nd;
     *w.loss_done = 0u;
   }
+}
+
+// The last fused L1 loss's pixel counts and sums, for a caller that splits one batch of
+// keyframes over several GPUs: out = (P, P_d, sum |C_hat - C| over the P x C values,
+// sum |D_hat - D| over the P_d depth pixels), as doubles (summed over ranks by the caller).
+__global__ void k_loss_counts(Work w, int C, double *__restrict__ out) {
+  grid_dep_wait();
+  if (threadIdx.x != 0) return;
+  const double np = (double)w.counters[kMaskedPix], nd = (double)w.counters[kDepthPix];
+  out[0] = np;
+  out[1] = nd;
+  out[2] = (double)w.loss_scal[1] * np * (double)C;
+  out[3] = (double)w.loss_scal[2] * nd;
+}
+
+// The backward's L1 gradient scales for the loss of the whole batch (Eq. 7 means over every
+// rank's pixels): w_c / (P_total C) and w_d / P_d,total from the summed counts, and, with
+// loss_out, that loss (L, L_color, L_depth) from the summed sums.
+__global__ void k_set_loss_scales(Work w, int C, const double *__restrict__ tot, float w_c, float w_d,
+                                  float *__restrict__ loss_out) {
+  grid_dep_wait();
+  if (threadIdx.x != 0) return;
+  const double np = tot[0], nd = tot[1];
+  w.loss_scal[4] = np > 0.0 ? (float)((double)w_c / (np * (double)C)) : 0.f;
+  w.loss_scal[5] = nd > 0.0 ? (float)((double)w_d / nd) : 0.f;
+  if (loss_out != nullptr) {
+    const float Lc = np > 0.0 ? (float)(tot[2] / (np * (double)C)) : 0.f;
+    const float Ld = nd > 0.0 ? (float)(tot[3] / nd) : 0.f;
+    loss_out[0] = w_c * Lc + w_d * Ld;
+    loss_out[1] = Lc;
+    loss_out[2] = Ld;
+  }
+}
+
+void launch_loss_counts(const Work &w, int C, double *out, cudaStream_t s) {
+  launch(k_loss_counts, 1, 32, 0, s, w, C, out);
+}
+
+void launch_set_loss_scales(const Work &w, int C, const double *tot, float w_c, float w_d, float *loss_out,
+                            cudaStream_t s) {
+  launch(k_set_loss_scales, 1, 32, 0, s, w, C, tot, w_c, w_d, loss_out);
 }
 
 // Fused L1 (Eq. 7/8): sums the forward's per-(tile, 32-pixel group) partials in a fixed
@@ -150,6 +194,9 @@ __global__ void __launch_bounds__(256) k_loss_finalize(Work w, int FT, int gshif
     loss_out[2] = Ld;
     w.loss_scal[4] = np > 0.f ? w_c / (np * (float)C) : 0.f;
     w.loss_scal[5] = nd > 0.f ? w_d / nd : 0.f;
+    w.loss_scal[1] = Lc;
+    w.loss_scal[2] = Ld;
+    w.counters[kDepthPix] = (unsigned long long)nd;
     *w.loss_done = 0u;
   }
 }

@@ -58,6 +58,7 @@ enum Counter {
   kQBwd = 11 * kCounterStride,        // next item of the persistent backward
   kWarpRecords = 12 * kCounterStride, // records the forward's warps walked after culling
   kBwdSteps = 13 * kCounterStride,    // steps of the backward's per-lane fragment replay (warp-wide)
+  kDepthPix = 14 * kCounterStride,    // pixels in the last fused L1 loss's depth term (D_hat != -1, D > 0)
   kWinStable = 15 * kCounterStride,   // projected (frame, stable Gaussian) entries of the open window (kept)
 };
 constexpr int kNumCounterSlots = 16;  // slots; all but kWinStable are cleared at the start of every call
