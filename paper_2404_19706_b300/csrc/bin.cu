@@ -325,15 +325,19 @@ __global__ void __launch_bounds__(256) k_cull(GaussPtrs g, Work w, Prm prm, int 
 // Every pair (candidate, masked tile) is staged as (tile, slot, key): the block reserves its
 // staging range with one atomic, and each pair's slot in its tile bucket is the value the
 // tile counter returns, so the later scatter into buckets needs no atomics.
+// With `ids` (the precomputed unstable list, nids entries) the kernel walks every (frame,
+// listed Gaussian) itself instead of the cull's candidates: the exact projection culls them,
+// one launch fewer for a short list.
 template <int C, int kMode>
-__global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, int T, int64_t max_pairs) {
+__global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, int T, int64_t max_pairs,
+                                                 const int32_t *__restrict__ ids, int64_t nids, int F) {
   grid_dep_wait();
   constexpr int H4 = (C <= 4) ? 3 : 4;
   constexpr int G2 = (C <= 5) ? 16 : 20;
   __shared__ uint32_t s_w[16];
   __shared__ unsigned long long s_base;
   const int64_t N = g.n;
-  const int64_t ncand = (int64_t)w.counters[kCand];
+  const int64_t ncand = ids != nullptr ? (int64_t)F * nids : (int64_t)w.counters[kCand];
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < ncand; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = base + threadIdx.x;
     uint32_t e = 0;
@@ -344,9 +348,15 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
     GParams P;
     float col[C];
     if (k < ncand) {
-      e = w.cand[k];
-      f = (int)(e / (uint64_t)N);
-      i = (int64_t)e - (int64_t)f * N;
+      if (ids != nullptr) {
+        f = (int)(k / nids);
+        i = (int64_t)ids[k - (int64_t)f * nids];
+        e = (uint32_t)((int64_t)f * N + i);
+      } else {
+        e = w.cand[k];
+        f = (int)(e / (uint64_t)N);
+        i = (int64_t)e - (int64_t)f * N;
+      }
       ok = load_params(g, w.rank, i, P);
       const float *cp = color_ptr(g, w.rank, i);
       if (C == 3 && g.sh_degree > 0) {  // the colour seen from this frame's camera
@@ -652,11 +662,21 @@ void launch_rank(const uint8_t *unstable, int64_t n, int32_t *block_cnt, int32_t
   launch(k_rank_write, nb, kRankThreads, 0, s, unstable, n, block_cnt, rank, ids, nu_counter, nu_out);
 }
 
+// Lists of the unstable Gaussians at most this long (times the frames) are projected
+// without the cull pass.
+constexpr int64_t kDirectProjectMax = 1 << 18;
+
 void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, int T, int mode, int cull_set,
                     int64_t max_pairs, cudaStream_t s) {
   if (g.n <= 0) return;
   const unsigned nb = (unsigned)((g.n + 255) / 256);
-  if (cull_set == kCullUnstable) {
+  const bool direct = cull_set == kCullUnstable && g.rank_map != nullptr &&
+                      (mode == kProjForward || mode == kProjMask) && (int64_t)F * g.n_unstable <= kDirectProjectMax;
+  const int32_t *dids = direct ? g.unstable_ids : nullptr;
+  const int64_t dn = direct ? g.n_unstable : 0;
+  if (direct) {
+    // the projection walks the unstable list itself
+  } else if (cull_set == kCullUnstable) {
     if (g.rank_map != nullptr) {
       if (g.n_unstable > 0)
         launch(k_cull<kCullUnstable>, (unsigned)((g.n_unstable + 255) / 256), 256, 0, s, g, w, prm, F, g.unstable_ids,
@@ -671,7 +691,7 @@ void launch_project(const GaussPtrs &g, const Work &w, const Prm &prm, int F, in
   }
 #define RTG_PROJ(CC, MM)                                                                  \
   launch(k_project<CC, MM>, resident_grid((const void *)k_project<CC, MM>, 256), 256, 0, s, g, w, prm, T, \
-                                                                                         max_pairs)
+         max_pairs, dids, dn, F)
 #define RTG_PROJ_C(CC)                              \
   switch (mode) {                                   \
     case kProjForward: RTG_PROJ(CC, kProjForward); break; \
