@@ -857,7 +857,8 @@ def run_ours(args, kw=TARGET, lite=False):
                     "d2h_bytes_per_step": d2h, "pipelined": "next step's upload overlaps this step's compute"},
             # SH: the coefficient backward, and the regulariser's reduce and gradient kernels
             "gpu_launches": (plain_kernels_per_step(1, H, W, ctx.get_tuning(), window=True,
-                                                    window_lists=stats["window_pairs"] > 0, decode=True) +
+                                                    window_lists=stats["window_pairs"] > 0, decode=True,
+                                                    direct=N_u_direct(stats)) +
                              (3 if sh else 0)) * args.steps,
             "clocks": clk,
         }
@@ -872,15 +873,22 @@ def run_ours(args, kw=TARGET, lite=False):
 
 
 def plain_kernels_per_step(F, H, W, tuning, window_lists=False, window=False, decode=True, adam=True,
-                           backward=True):
+                           backward=True, direct=False):
     """Kernels of one iteration whose forward takes its mask as an input (or renders every
-    pixel): tile mask, cull, project, the window's stable bin when it has no cached lists,
-    the tile scan with the scatter into the buckets, sort, composite (and, with the loss,
-    its finalize under the CTA-per-tile schedule); backward 2; the frame decode; Adam."""
+    pixel): tile mask, cull (not when the projection walks a short unstable list itself),
+    project, the window's stable bin when it has no cached lists, the tile scan with the
+    scatter into the buckets, sort, composite (and, with the loss, its finalize under the
+    CTA-per-tile schedule); backward 2; the frame decode; Adam."""
     FT = F * ((W + tuning.tile_w - 1) // tuning.tile_w) * ((H + tuning.tile_h - 1) // tuning.tile_h)
-    fwd = 3 + (1 if window and not window_lists else 0) + scan_emit_launches(FT) + 2 + \
+    fwd = (2 if direct else 3) + (1 if window and not window_lists else 0) + scan_emit_launches(FT) + 2 + \
         (0 if tuning.schedule == 1 or not backward else 1)
     return fwd + (2 if backward else 0) + (1 if decode else 0) + (1 if adam else 0)
+
+
+def N_u_direct(stats, frames=1):
+    """The projection walks the unstable list itself, without the cull pass, for at most
+    2^18 (frame, unstable Gaussian) entries."""
+    return 0 < frames * stats["n_unstable"] <= (1 << 18)
 
 
 def run_full_frame(args, kw=FULL):
