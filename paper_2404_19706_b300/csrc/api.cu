@@ -136,7 +136,7 @@ struct Layout {
   size_t cams, counters, rank, ids, block_cnt, cand, rec_hot, rec_cold, rec_box, ntiles, tile_npix, tile_count, tile_offset,
       tile_cursor, keys, keys_alt, stage, sorted, px_T, px_last, px_hit, grad2d, loss_part, loss_scal, loss_done, tile_loss,
       px_list, items, scand, win_scount, win_soff, win_skeys, scan_part, scan_hist, sel_keys, sel_small, sel_state,
-      sel_tie, gauss_bits, loss_acc, total;
+      sel_tie, gauss_bits, loss_acc, ckpt, bseg, total;
 };
 
 bool capacity_ok(const rtg_capacity *c) {
@@ -209,6 +209,8 @@ Layout layout_of(const rtg_capacity *c) {
   L.sel_tie = take(Fm * sel_blocks * 4);
   L.gauss_bits = take(N * 4);
   L.loss_acc = take(4 * 8);
+  L.ckpt = take((size_t)kSegMax * P * (size_t)ck4_of(c->max_channels) * 16);
+  L.bseg = take((size_t)kSegBins * groups * kSegMax * 4);
   L.total = o;
   return L;
 }
@@ -485,6 +487,14 @@ rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap) {
   w.scan_part = (unsigned long long *)(b + L.scan_part);
   w.scan_hist = (uint32_t *)(b + L.scan_hist);
   w.status = status_dev;
+  w.ckpt = (float4 *)(b + L.ckpt);
+  w.bseg = (uint32_t *)(b + L.bseg);
+  w.px_cap = (int64_t)ctx->cap.max_frames * ctx->cap.max_width * ctx->cap.max_height;
+  {
+    const size_t padded = (size_t)ctx->cap.max_frames * (size_t)(ctx->cap.max_width + 31) *
+                          (size_t)(ctx->cap.max_height + 15);
+    w.bseg_cap = (int64_t)(padded / 32 + 1) * kSegMax;
+  }
   ctx->sel.keys = (uint32_t *)(b + L.sel_keys);
   ctx->sel.hist = (uint32_t *)(b + L.sel_small);
   ctx->sel.state = (uint32_t *)(b + L.sel_state);
@@ -842,7 +852,7 @@ rtg_status rtg_render_backward_l1(rtg_ctx *ctx, float *g_means, float *g_scales,
   {
     ProfScope ps(ctx, kPBackward, s);
     launch_backward(ctx->C, ctx->w_fwd, ctx->prm, n, ctx->F, ctx->T, ctx->tune_fwd, nullptr, nullptr, ctx->l1,
-                    fwd_masks(ctx), s);
+                    fwd_masks(ctx), true, s);
   }
   {
     ProfScope ps(ctx, kPProjectBackward, s);
@@ -890,7 +900,7 @@ rtg_status rtg_render_backward(rtg_ctx *ctx, const float *dL_dcolor, const float
   {
     ProfScope ps(ctx, kPBackward, s);
     launch_backward(ctx->C, ctx->w_fwd, ctx->prm, n, ctx->F, ctx->T, ctx->tune_fwd, dL_dcolor, dL_ddepth,
-                    L1Fused{nullptr, nullptr, nullptr, nullptr}, fwd_masks(ctx), s);
+                    L1Fused{nullptr, nullptr, nullptr, nullptr}, fwd_masks(ctx), true, s);
   }
   {
     ProfScope ps(ctx, kPProjectBackward, s);

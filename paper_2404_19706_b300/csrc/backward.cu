@@ -107,8 +107,7 @@ __device__ __forceinline__ void flush_rows(const BwdWarpSmem<C, B> &sm, int n, i
 
 // A lane's pixel of group `grp` of render tile `tile` (the forward's pixel grouping) and its
 // loss gradients, with the group's pixel centres and colour gradients stored in s_px / s_dc
-// for the row sums; also adds the depth gradient of the pixels' hit Gaussians (Eq. 4/5),
-// the depth depending on f only through the choice of the hit.
+// for the row sums (the depth gradient goes to the hit Gaussian in bwd_depth_grad).
 template <int C>
 struct BwdPixel {
   bool has;
@@ -118,6 +117,8 @@ struct BwdPixel {
   float T_;
   float dC[C];
   float *g2base;
+  int hit;     // the pixel's hit Gaussian (-1: none)
+  float dLdD;  // the loss gradient of its depth
 };
 
 template <int C>
@@ -169,7 +170,33 @@ __device__ __forceinline__ void bwd_pixel_prologue(const Work &w, const Prm &prm
 #pragma unroll
   for (int c = 0; c < C; ++c) s_dc[c][lane] = o.dC[c];
 
-  // ---- depth: gradient to the hit Gaussian's plane record or centre depth (Eq. 4/5)
+  o.has = has;
+  o.f = f;
+  o.px = px;
+  o.py = py;
+  o.fpx = fpx;
+  o.fpy = fpy;
+  o.off = w.tile_offset[tile];
+  o.last = last;
+  o.T_ = T_;
+  o.g2base = g2base;
+  o.hit = hit;
+  o.dLdD = dLdD;
+}
+
+// The depth gradient of a group's pixels to their hit Gaussians' plane records or centre
+// depths (Eq. 4/5; the depth depends on f only through the choice of the hit), one atomic
+// group per distinct Gaussian.  Called by the whole warp after its list walk, so the walk's
+// first loads are not queued behind this one's.
+template <int C>
+__device__ __forceinline__ void bwd_depth_grad(const Work &w, const Prm &prm, int64_t N, const BwdPixel<C> &o) {
+  constexpr int G2 = (C <= 5) ? 16 : 20;
+  const int lane = threadIdx.x & 31;
+  const int f = o.f, hit = o.hit;
+  const bool has = o.has;
+  const float fpx = o.fpx, fpy = o.fpy, dLdD = o.dLdD;
+  const DevCam &cam = w.cams[f];
+  float *__restrict__ g2base = o.g2base;
   {
     int key = -1;
     float gd0 = 0.f, gn0 = 0.f, gn1 = 0.f, gn2 = 0.f, gz = 0.f;
@@ -214,16 +241,6 @@ __device__ __forceinline__ void bwd_pixel_prologue(const Work &w, const Prm &prm
       pending &= ~__ballot_sync(0xffffffffu, in);
     }
   }
-  o.has = has;
-  o.f = f;
-  o.px = px;
-  o.py = py;
-  o.fpx = fpx;
-  o.fpy = fpy;
-  o.off = w.tile_offset[tile];
-  o.last = last;
-  o.T_ = T_;
-  o.g2base = g2base;
 }
 
 // Replays the pixels of group `grp` of render tile `tile` (the forward's pixel grouping)
@@ -392,6 +409,7 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
       valid[u] = vnext[u];
     }
   }
+  bwd_depth_grad<C>(w, prm, N, pxs);
   __syncwarp();  // the next group rewrites the warp's pixel arrays
 }
 
@@ -401,15 +419,16 @@ __device__ __forceinline__ void backward_group(const Work &w, const Prm &prm, in
 // walks the list in batches of 32 entries back to front, stages only the entries some lane
 // composited, and each lane replays its own fragments only (its bit of each staged mask),
 // so no lane steps through fragments it did not composite.  The unstable records' rows are
-// then summed one record a lane, as in flush_rows.
+// then summed over their composited pixels, 32 / nu lanes a record (rounded down to a power
+// of two), and added to the 2D gradient rows with one atomic per four values.
 template <int C>
 struct BwdFlSmem {
   static constexpr int H4 = (C <= 4) ? 3 : 4;
-  float4 rec[H4][32];    // the batch's composited entries' records, in list order
+  float4 rec[H4][32];    // records of the batch's composited entries, at their batch position
   int2 jr[32];           // their list position and unstable rank
   uint32_t am[32];       // their composited lanes
-  uint8_t us[32];        // staged slot -> row slot of an unstable record
-  uint8_t uk[32];        // row slot -> staged slot
+  uint8_t us[32];        // batch position -> row slot of an unstable record
+  uint8_t uk[32];        // row slot -> batch position
   float2 wg[32][33];     // row slot x pixel: (f T, dL/dalpha); zero where not composited
   float2 px[32];
   float dc[C][32];
@@ -418,9 +437,12 @@ struct BwdFlSmem {
 template <int C>
 constexpr size_t bwd_fl_smem_bytes() { return 8 * sizeof(BwdFlSmem<C>); }
 
+// seg >= 0: only segment `seg` of the list (entries [seg kSeg, seg kSeg + kSeg), the last
+// segment to the end), each lane starting from the forward's checkpoint at the segment's
+// back end; seg < 0: the whole list.
 template <int C>
 __device__ __forceinline__ void backward_group_fl(const Work &w, const Prm &prm, int64_t N, int T, int tile, int grp,
-                                                  BwdFlSmem<C> &sm, const uint32_t *__restrict__ fmask,
+                                                  int seg, BwdFlSmem<C> &sm, const uint32_t *__restrict__ fmask,
                                                   const float *__restrict__ dL_dcolor,
                                                   const float *__restrict__ dL_ddepth, const L1Fused &l1) {
   constexpr int H4 = (C <= 4) ? 3 : 4;
@@ -443,62 +465,89 @@ __device__ __forceinline__ void backward_group_fl(const Work &w, const Prm &prm,
   float S[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) S[c] = 0.f;
-
-  // entry b_end - 32 + lane of the list: its mask and, when some lane composited it, its
-  // record and unstable rank (fetched one batch ahead)
-  auto fetch = [&](int b_end_, uint32_t &am_, float4 (&rr)[H4], int &rank_) {
-    const int jq = b_end_ - 32 + lane;
-    am_ = jq >= 0 ? fmask[(int64_t)(off + (uint32_t)jq) * ngrp + grp] : 0u;
-    rank_ = -1;
-    if (am_ != 0u) {
-      const uint32_t gid = w.sorted[off + jq];
+  // the entries [lo, hi) replayed here
+  int lo = 0, hi = (int)maxlast;
+  if (seg >= 0) {
+    lo = seg * kSeg;
+    if (seg < kSegMax - 1) hi = min(hi, lo + kSeg);
+    hi = max(hi, lo);
+    if (pxs.last > (uint32_t)hi) {
+      // the lane composited entries behind the segment: the transmission in front of entry
+      // hi and the colour behind it (final colour - colour in front) from the checkpoints
+      constexpr int CK4 = (C + 4) / 4;
+      const int64_t pix = (int64_t)f * cam.H * cam.W + (int64_t)pxs.py * cam.W + pxs.px;
+      const float4 *ck = w.ckpt + ((int64_t)seg * w.px_cap + pix) * CK4;
+      const float4 *fin = w.ckpt + ((int64_t)(kSegMax - 1) * w.px_cap + pix) * CK4;
+      float vs[4 * CK4], vf[4 * CK4];
 #pragma unroll
-      for (int k = 0; k < H4; ++k) rr[k] = rec[(int64_t)gid * H4 + k];
-      rank_ = (H4 == 3) ? __float_as_int(rr[2].w) : __float_as_int(w.rec_cold[((int64_t)f * N + gid) * 2 + 1].y);
+      for (int k = 0; k < CK4; ++k) {
+        const float4 a = ck[k], b = fin[k];
+        vs[4 * k] = a.x; vs[4 * k + 1] = a.y; vs[4 * k + 2] = a.z; vs[4 * k + 3] = a.w;
+        vf[4 * k] = b.x; vf[4 * k + 1] = b.y; vf[4 * k + 2] = b.z; vf[4 * k + 3] = b.w;
+      }
+      T_ = vs[0];
+#pragma unroll
+      for (int c = 0; c < C; ++c) S[c] = vf[1 + c] - vs[1 + c];
+    }
+  }
+
+  // entry b_end - 32 + lane of the list: its mask and Gaussian id (fetched two batches
+  // ahead), then, when some lane composited it, its record and unstable rank (one batch
+  // ahead), so each batch's replay covers one load latency instead of a chain of three
+  auto fetch_idx = [&](int b_end_, uint32_t &am_, uint32_t &gid_) {
+    const int jq = b_end_ - 32 + lane;
+    am_ = 0u;
+    gid_ = 0u;
+    if (jq >= lo) {
+      am_ = fmask[(int64_t)(off + (uint32_t)jq) * ngrp + grp];
+      gid_ = w.sorted[off + jq];
     }
   };
-  uint32_t am = 0u, nsteps = 0u;
+  auto fetch_rec = [&](uint32_t am_, uint32_t gid_, float4 (&rr)[H4], int &rank_) {
+    rank_ = -1;
+    if (am_ != 0u) {
+#pragma unroll
+      for (int k = 0; k < H4; ++k) rr[k] = rec[(int64_t)gid_ * H4 + k];
+      rank_ = (H4 == 3) ? __float_as_int(rr[2].w) : __float_as_int(w.rec_cold[((int64_t)f * N + gid_) * 2 + 1].y);
+    }
+  };
+  uint32_t am = 0u, gid = 0u, am1 = 0u, gid1 = 0u, nsteps = 0u;
   float4 r[H4];
   int rk = -1;
-  fetch((int)maxlast, am, r, rk);
-  for (int b_end = (int)maxlast; b_end > 0; b_end -= 32) {
-    uint32_t amn = 0u;
+  fetch_idx(hi, am, gid);
+  if (hi > lo + 32) fetch_idx(hi - 32, am1, gid1);
+  fetch_rec(am, gid, r, rk);
+  for (int b_end = hi; b_end > lo; b_end -= 32) {
+    const uint32_t amn = am1;
     float4 rn[H4];
     int rkn = -1;
-    if (b_end > 32) fetch(b_end - 32, amn, rn, rkn);
-    // stage the composited entries in list order; number the unstable ones
-    const unsigned bal = __ballot_sync(0xffffffffu, am != 0u);
-    const int slot = __popc(bal & lanemask_lt());
+    fetch_rec(am1, gid1, rn, rkn);
+    uint32_t am2 = 0u, gid2 = 0u;
+    if (b_end > lo + 64) fetch_idx(b_end - 64, am2, gid2);
+    // stage the composited entries at their batch position (entry b_end - 32 + k at k),
+    // numbering the unstable ones in list order; this lane's fragments in the batch are
+    // bit k = its bit of entry k's mask, a bit transpose of the lanes' masks.  (The row
+    // slots need no clearing: the row sums read slot (u, p) only for pixels p that
+    // composited record u, and lane p's replay writes exactly those.)
     const unsigned ubal = __ballot_sync(0xffffffffu, am != 0u && rk >= 0);
     const int nu = __popc(ubal);
+    uint32_t mine = bit_transpose32(am, lane);
     if (am != 0u) {
 #pragma unroll
-      for (int k = 0; k < H4; ++k) sm.rec[k][slot] = r[k];
-      sm.jr[slot] = make_int2(b_end - 32 + lane, rk);
-      sm.am[slot] = am;
+      for (int k = 0; k < H4; ++k) sm.rec[k][lane] = r[k];
+      sm.jr[lane] = make_int2(b_end - 32 + lane, rk);
+      sm.am[lane] = am;
       if (rk >= 0) {
         const int u = __popc(ubal & lanemask_lt());
-        sm.us[slot] = (uint8_t)u;
-        sm.uk[u] = (uint8_t)slot;
+        sm.us[lane] = (uint8_t)u;
+        sm.uk[u] = (uint8_t)lane;
       }
     }
-    // the rows of this batch's unstable records start at zero for every pixel
-    for (int u = 0; u < nu; ++u) sm.wg[u][lane] = make_float2(0.f, 0.f);
     __syncwarp();
-    // this lane's fragments among the staged entries: bit k = lane's bit of mask k
-    const int cnt = __popc(bal);
-    uint32_t mine = 0u;
-    for (int k = 0; k < cnt; ++k) mine |= ((sm.am[k] >> lane) & 1u) << k;
     nsteps += __reduce_max_sync(0xffffffffu, (unsigned)__popc(mine));
     // back to front over this lane's own fragments: the transmission in front of each by
     // division, dL/df from the colour behind it, and for an unstable record (f T, dL/dalpha)
-    while (mine) {
-      const int k = 31 - __clz(mine);
-      mine ^= 1u << k;
-      const float4 a0 = sm.rec[0][k], a1 = sm.rec[1][k];
-      float dx, dy, t1, t2, g;
-      const float fa = footprint(fpx, fpy, a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, prm.f_max, dx, dy, t1, t2,
-                                 g);
+    auto replay = [&](int k, float fa, float g, float alpha) {
       const float iom = __fdividef(1.f, 1.f - fa);  // 1 - f >= 1 - f_max: a normal divisor
       T_ = T_ * iom;
       const float wgt = fa * T_;
@@ -515,60 +564,114 @@ __device__ __forceinline__ void backward_group_fl(const Work &w, const Prm &prm,
         S[c] = fmaf(cw[c], wgt, S[c]);
       }
       if (sm.jr[k].y >= 0) {
-        const float G = a1.w * g < prm.f_max ? dLdf * g : 0.f;  // unclamped branch of min(f_max, alpha g)
+        const float G = alpha * g < prm.f_max ? dLdf * g : 0.f;  // unclamped branch of min(f_max, alpha g)
         sm.wg[sm.us[k]][lane] = make_float2(wgt, G);
       }
+    };
+    // two fragments at a time: their footprints are independent, the recurrences then take
+    // them in order
+    while (mine) {
+      const int kA = 31 - __clz(mine);
+      mine ^= 1u << kA;
+      const int kB = mine ? 31 - __clz(mine) : kA;
+      mine &= ~(1u << kB);
+      const float4 a0 = sm.rec[0][kA], a1 = sm.rec[1][kA], b0 = sm.rec[0][kB], b1 = sm.rec[1][kB];
+      float dx, dy, t1, t2, gA, gB;
+      const float faA = footprint(fpx, fpy, a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, prm.f_max, dx, dy, t1,
+                                  t2, gA);
+      const float faB = footprint(fpx, fpy, b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w, prm.f_max, dx, dy, t1,
+                                  t2, gB);
+      replay(kA, faA, gA, a1.w);
+      if (kB != kA) replay(kB, faB, gB, b1.w);
     }
     __syncwarp();
-    // the rows of the unstable records, one a lane, over each record's composited pixels
-    if (lane < nu) {
-      const int k = sm.uk[lane];
-      const float4 a0 = sm.rec[0][k], a1 = sm.rec[1][k];
-      const int rank = sm.jr[k].y;
+    // the rows of the unstable records: L lanes a record (L = 32 / nu rounded down to a
+    // power of two), each lane over every L-th pixel of the record's composited ones, the
+    // L partial rows then summed across the lanes
+    if (nu > 0) {
+      const int lg = 5 - (32 - __clz(nu - 1));  // L = 2^lg: nu <= 32 / L
+      const int u = lane >> lg, sub = lane & ((1 << lg) - 1);
+      // pixels p = sub (mod L)
+      const unsigned pat = lg == 0 ? 0xffffffffu : lg == 1 ? 0x55555555u : lg == 2 ? 0x11111111u
+                         : lg == 3 ? 0x01010101u : lg == 4 ? 0x00010001u : 0x00000001u;
       float acc[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[v] = 0.f;
-      unsigned m = sm.am[k];
-      while (m) {
-        const int p = __ffs(m) - 1;
-        m &= m - 1u;
-        const float2 w_ = sm.wg[lane][p];
-        const float2 pp = sm.px[p];
-        const float dx = (pp.x - a0.x) - a0.z, dy = (pp.y - a0.y) - a0.w;
-        const float t1 = fmaf(a1.x, dx, a1.y * dy), t2 = a1.z * dy;
-        const float G = w_.y, Gx = G * dx;
-        acc[0] = fmaf(G, t1, acc[0]);
-        acc[1] = fmaf(G, t2, acc[1]);
-        acc[2] = fmaf(Gx, dx, acc[2]);
-        acc[3] = fmaf(Gx, dy, acc[3]);
-        acc[4] = fmaf(G * dy, dy, acc[4]);
-        acc[5] += G;
+      float4 a1 = make_float4(0.f, 0.f, 0.f, 0.f);
+      int rank = 0;
+      if (u < nu) {
+        const int k = sm.uk[u];
+        const float4 a0 = sm.rec[0][k];
+        a1 = sm.rec[1][k];
+        rank = sm.jr[k].y;
+        unsigned m = sm.am[k] & (pat << sub);
+        // four pixels an iteration, their loads issued together (a missing one adds zeros)
+        while (m) {
+          int pq[4];
+          bool ok[4];
 #pragma unroll
-        for (int c = 0; c < C; ++c) acc[6 + c] = fmaf(w_.x, sm.dc[c][p], acc[6 + c]);
+          for (int q = 0; q < 4; ++q) {
+            ok[q] = m != 0u;
+            pq[q] = ok[q] ? __ffs(m) - 1 : 0;
+            m &= m - 1u;
+          }
+          float2 wq[4], ppq[4];
+          float dq[4][C];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            wq[q] = sm.wg[u][pq[q]];
+            ppq[q] = sm.px[pq[q]];
+#pragma unroll
+            for (int c = 0; c < C; ++c) dq[q][c] = sm.dc[c][pq[q]];
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float dx = (ppq[q].x - a0.x) - a0.z, dy = (ppq[q].y - a0.y) - a0.w;
+            const float t1 = fmaf(a1.x, dx, a1.y * dy), t2 = a1.z * dy;
+            const float G = ok[q] ? wq[q].y : 0.f, wx = ok[q] ? wq[q].x : 0.f, Gx = G * dx;
+            acc[0] = fmaf(G, t1, acc[0]);
+            acc[1] = fmaf(G, t2, acc[1]);
+            acc[2] = fmaf(Gx, dx, acc[2]);
+            acc[3] = fmaf(Gx, dy, acc[3]);
+            acc[4] = fmaf(G * dy, dy, acc[4]);
+            acc[5] += G;
+#pragma unroll
+            for (int c = 0; c < C; ++c) acc[6 + c] = fmaf(wx, dq[q][c], acc[6 + c]);
+          }
+        }
       }
-      const float al = a1.w * kLn2, c2 = 2.f * al, kc = -al * kQScale2;
-      float v[4 * ((NV + 3) / 4)];
-      v[0] = c2 * a1.x * acc[0];
-      v[1] = c2 * fmaf(a1.y, acc[0], a1.z * acc[1]);
-      v[2] = kc * acc[2];
-      v[3] = 2.f * kc * acc[3];
-      v[4] = kc * acc[4];
+      for (int o = (1 << lg) >> 1; o > 0; o >>= 1) {
 #pragma unroll
-      for (int qv = 5; qv < NV; ++qv) v[qv] = acc[qv];
+        for (int v = 0; v < NV; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+      }
+      if (u < nu && sub == 0) {
+        const float al = a1.w * kLn2, c2 = 2.f * al, kc = -al * kQScale2;
+        float v[4 * ((NV + 3) / 4)];
+        v[0] = c2 * a1.x * acc[0];
+        v[1] = c2 * fmaf(a1.y, acc[0], a1.z * acc[1]);
+        v[2] = kc * acc[2];
+        v[3] = 2.f * kc * acc[3];
+        v[4] = kc * acc[4];
 #pragma unroll
-      for (int qv = NV; qv < 4 * ((NV + 3) / 4); ++qv) v[qv] = 0.f;
-      float4 *row = reinterpret_cast<float4 *>(g2base + (int64_t)rank * G2);
+        for (int qv = 5; qv < NV; ++qv) v[qv] = acc[qv];
 #pragma unroll
-      for (int qv = 0; qv < (NV + 3) / 4; ++qv)
-        atomicAdd(row + qv, make_float4(v[4 * qv], v[4 * qv + 1], v[4 * qv + 2], v[4 * qv + 3]));
+        for (int qv = NV; qv < 4 * ((NV + 3) / 4); ++qv) v[qv] = 0.f;
+        float4 *row = reinterpret_cast<float4 *>(g2base + (int64_t)rank * G2);
+#pragma unroll
+        for (int qv = 0; qv < (NV + 3) / 4; ++qv)
+          atomicAdd(row + qv, make_float4(v[4 * qv], v[4 * qv + 1], v[4 * qv + 2], v[4 * qv + 3]));
+      }
     }
     __syncwarp();  // the next batch rewrites the staging
     am = amn;
     rk = rkn;
 #pragma unroll
     for (int k = 0; k < H4; ++k) r[k] = rn[k];
+    am1 = am2;
+    gid1 = gid2;
   }
   if (lane == 0 && nsteps) atomicAdd(w.counters + kBwdSteps, (unsigned long long)nsteps);
+  if (seg <= 0) bwd_depth_grad<C>(w, prm, N, pxs);
   __syncwarp();  // the next group rewrites the warp's pixel arrays
 }
 
@@ -576,6 +679,7 @@ struct BwdIn {
   const float *dL_dcolor, *dL_ddepth;
   L1Fused l1;
   const uint32_t *fmask;  // the forward's composited-lane masks (nullptr: walk with the culling)
+  int segments;           // non-zero: the forward queued its segments (persistent schedule)
 };
 
 // Schedule 0: CTA `tile` with one warp per 32-pixel group of the tile's pixel list.
@@ -619,7 +723,7 @@ __global__ void __launch_bounds__(kMaxTilePix, 2) k_backward_fl(Work w, Prm prm,
   const int tile = blockIdx.x, wid = threadIdx.x >> 5;
   if (wid * 32 >= (int)w.tile_npix[tile]) return;
   BwdFlSmem<C> *sm = reinterpret_cast<BwdFlSmem<C> *>(bwd_dyn_smem) + wid;
-  backward_group_fl<C>(w, prm, N, T, tile, wid, *sm, in.fmask, in.dL_dcolor, in.dL_ddepth, in.l1);
+  backward_group_fl<C>(w, prm, N, T, tile, wid, -1, *sm, in.fmask, in.dL_dcolor, in.dL_ddepth, in.l1);
 }
 
 template <int C>
@@ -635,11 +739,49 @@ __global__ void __launch_bounds__(256, 2) k_backward_fl_queue(Work w, Prm prm, i
   uint32_t it = first_item(w, wid, spread);
   while (it < nitems) {
     const uint32_t item = w.items[it];
-    backward_group_fl<C>(w, prm, N, T, (int)(item >> 3), (int)(item & 7u), *sm, in.fmask, in.dL_dcolor,
+    backward_group_fl<C>(w, prm, N, T, (int)(item >> 3), (int)(item & 7u), -1, *sm, in.fmask, in.dL_dcolor,
                          in.dL_ddepth, in.l1);
     uint32_t nx = 0;
     if (lane == 0) nx = nwarps + (uint32_t)atomicAdd(w.counters + kQBwd, 1ull);
     it = __shfl_sync(0xffffffffu, nx, 0);
+  }
+}
+
+// Schedule 1 over the forward's queued segments: the bins in decreasing cost, each a warp's
+// (group, segment) unit.  A warp's first unit is static (warp k of CTA b takes unit
+// k * grid + b, spreading the costliest units over the SMs); later ones come from the
+// shared counter.
+template <int C>
+__global__ void __launch_bounds__(256, 2) k_backward_seg_queue(Work w, Prm prm, int64_t N, int T, BwdIn in) {
+  grid_dep_wait();
+  extern __shared__ float4 bwd_dyn_smem[];
+  if (w.counters[kSkip] != 0ull) return;
+  uint32_t cnt[kSegBins], total = 0;
+#pragma unroll
+  for (int b = 0; b < kSegBins; ++b) {
+    const unsigned long long c = w.counters[kBSeg0 + b * kCounterStride];
+    cnt[b] = (uint32_t)(c < (unsigned long long)w.bseg_cap ? c : (unsigned long long)w.bseg_cap);
+    total += cnt[b];
+  }
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  BwdFlSmem<C> *sm = reinterpret_cast<BwdFlSmem<C> *>(bwd_dyn_smem) + wid;
+  const uint32_t nwarps = gridDim.x * 8u;
+  uint32_t t = (uint32_t)wid * gridDim.x + blockIdx.x;
+  while (t < total) {
+    uint32_t r = t;
+    int b = 0;
+#pragma unroll
+    for (int k = 0; k < kSegBins - 1; ++k)
+      if (b == k && r >= cnt[k]) {
+        r -= cnt[k];
+        b = k + 1;
+      }
+    const uint32_t code = w.bseg[(int64_t)b * w.bseg_cap + r];
+    backward_group_fl<C>(w, prm, N, T, (int)(code >> 6), (int)(code & 7u), (int)((code >> 3) & 7u), *sm, in.fmask,
+                         in.dL_dcolor, in.dL_ddepth, in.l1);
+    uint32_t nx = 0;
+    if (lane == 0) nx = nwarps + (uint32_t)atomicAdd(w.counters + kQBwd, 1ull);
+    t = __shfl_sync(0xffffffffu, nx, 0);
   }
 }
 
@@ -1024,7 +1166,9 @@ __global__ void __launch_bounds__(256) k_sh_backward(GaussPtrs g, Work w, int F,
 template <int C>
 static void launch_backward_fl(const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn,
                                const BwdIn &in, cudaStream_t s) {
-  if (tn.schedule == 1)
+  if (tn.schedule == 1 && in.segments)
+    launch(k_backward_seg_queue<C>, tn.num_sms * tn.ctas_per_sm, 256, bwd_fl_smem_bytes<C>(), s, w, prm, N, T, in);
+  else if (tn.schedule == 1)
     launch(k_backward_fl_queue<C>, tn.num_sms * tn.ctas_per_sm, 256, bwd_fl_smem_bytes<C>(), s, w, prm, N, T, in,
            tn.ctas_per_sm <= 2 ? 1 : 0);
   else
@@ -1057,6 +1201,10 @@ void init_backward_attributes() {
   cudaFuncSetAttribute(k_backward_fl_queue<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)bwd_fl_smem_bytes<8>());
   cudaFuncSetAttribute(k_backward_fl<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_fl_smem_bytes<8>());
+  cudaFuncSetAttribute(k_backward_seg_queue<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)bwd_fl_smem_bytes<3>());
+  cudaFuncSetAttribute(k_backward_seg_queue<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)bwd_fl_smem_bytes<8>());
   set_backward_attributes<3, 32>();
   set_backward_attributes<3, 64>();
   set_backward_attributes<8, 32>();
@@ -1065,8 +1213,8 @@ void init_backward_attributes() {
 
 void launch_backward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn,
                      const float *dL_dcolor, const float *dL_ddepth, const L1Fused &l1, const uint32_t *fmask,
-                     cudaStream_t s) {
-  const BwdIn in{dL_dcolor, dL_ddepth, l1, fmask};
+                     bool segments, cudaStream_t s) {
+  const BwdIn in{dL_dcolor, dL_ddepth, l1, fmask, (fmask != nullptr && segments) ? 1 : 0};
   if (fmask != nullptr) {
     if (C == 3) launch_backward_fl<3>(w, prm, N, F, T, tn, in, s);
     else launch_backward_fl<8>(w, prm, N, F, T, tn, in, s);

@@ -622,6 +622,7 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Work w, int FT, int64_t max
     w.counters[kItems] = r;
     w.counters[kQFwd] = 0ull;
     w.counters[kQBwd] = 0ull;
+    for (int b = 0; b < kSegBins; ++b) w.counters[kBSeg0 + b * kCounterStride] = 0ull;
   }
   __syncthreads();
 #pragma unroll
@@ -828,6 +829,7 @@ __global__ void __launch_bounds__(1024) k_scan_bases(Work w, int FT, int64_t max
     w.counters[kItems] = run;
     w.counters[kQFwd] = 0ull;
     w.counters[kQBwd] = 0ull;
+    for (int b = 0; b < kSegBins; ++b) w.counters[kBSeg0 + b * kCounterStride] = 0ull;
   }
   __syncthreads();
   if (tid < kQueueClasses) {

@@ -26,6 +26,7 @@ struct FwdOut {
   float *loss_out;               // non-null: the persistent forward finalizes the L1 loss
   float w_c, w_d;
   uint32_t *fmask;               // non-null: the composited-lane masks for the backward
+  int segments;                  // non-zero: checkpoints and queued segments for the persistent backward
 };
 
 // Renders the pixels of group `grp` (32 consecutive entries of the tile's pixel list) of
@@ -58,6 +59,7 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
   const uint32_t n = w.tile_offset[tile + 1] - off;
   const float4 *__restrict__ rec = w.rec_hot + (int64_t)f * N * H4;
   const float2 *__restrict__ box = w.rec_box + (int64_t)f * N;
+  const int64_t pix = (int64_t)f * cam.H * cam.W + (int64_t)py * cam.W + px;
 
   float T_ = 1.f;
   float acc[C];
@@ -73,6 +75,33 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
   const int ngrp = 1 << (tws + ths - 5);
   using Bits = typename std::conditional<(B > 32), unsigned long long, uint32_t>::type;
   Bits ebits = 0;  // the batch's entries (list position - b0) this lane composited
+  // backward segments: the segment being walked and this lane's fragments in it
+  static_assert(kSeg % B == 0, "segment boundaries fall on batch ends");
+  constexpr int CK4 = (C + 4) / 4;
+  int cur_seg = 0;
+  uint32_t segfrag = 0;
+  auto write_ckpt = [&](int idx) {  // (T, colour composited so far) at checkpoint idx
+    if (!has) return;
+    float v[4 * CK4];
+    v[0] = T_;
+#pragma unroll
+    for (int c = 0; c < C; ++c) v[1 + c] = acc[c];
+#pragma unroll
+    for (int c = C + 1; c < 4 * CK4; ++c) v[c] = 0.f;
+    float4 *dst = w.ckpt + ((int64_t)idx * w.px_cap + pix) * CK4;
+#pragma unroll
+    for (int k = 0; k < CK4; ++k) dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+  };
+  auto emit_segment = [&](int sidx) {  // queue segment sidx of this group in its cost bin
+    const uint32_t m = __reduce_max_sync(0xffffffffu, segfrag);
+    if (lane == 0 && (m != 0u || sidx == 0)) {  // segment 0 also carries the depth gradient
+      const int bin = m >= 32u ? 0 : (m >= 16u ? 1 : (m >= 8u ? 2 : 3));
+      const unsigned long long at = atomicAdd(w.counters + kBSeg0 + bin * kCounterStride, 1ull);
+      if (at < (unsigned long long)w.bseg_cap)
+        w.bseg[(int64_t)bin * w.bseg_cap + (int64_t)at] = ((uint32_t)tile << 6) | ((uint32_t)sidx << 3) | (uint32_t)grp;
+    }
+    segfrag = 0u;
+  };
   // the records of batch b0 + B, and the indices of batch b0 + 2B, are fetched while batch
   // b0 is composited, so a batch waits on one L2 round trip rather than index -> record
   float4 r[R][H4];
@@ -150,6 +179,7 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
         T_ = Tn;
         last = jj + 1;
         ++nfrag;
+        ++segfrag;
         ebits |= (Bits)1 << (jj - b0);
         return true;
       };
@@ -171,22 +201,25 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
     }
     __syncwarp();
     if (out.fmask != nullptr) {
-      // lane L gets the composited lanes of entry b0 + 32u + L (a bit transpose by ballots;
-      // culled entries get none) and stores them, one coalesced store per 32 entries
+      // lane L gets the composited lanes of entry b0 + 32u + L (a bit transpose of the
+      // lanes' entry bits; culled entries get none) and stores them, one coalesced store per
+      // 32 entries
 #pragma unroll
       for (int u = 0; u < R; ++u) {
         const uint32_t wv = (uint32_t)(ebits >> (32 * u));
         uint32_t am = 0u;
-        if (__any_sync(0xffffffffu, wv != 0u)) {
-#pragma unroll
-          for (int e = 0; e < 32; ++e) {
-            const unsigned m = __ballot_sync(0xffffffffu, (wv >> e) & 1u);
-            am = lane == e ? m : am;
-          }
-        }
+        if (__any_sync(0xffffffffu, wv != 0u)) am = bit_transpose32(wv, lane);
         if (valid[u]) out.fmask[(int64_t)(off + b0 + (uint32_t)(u * 32 + lane)) * ngrp + grp] = am;
       }
       ebits = 0;
+    }
+    if (out.segments) {  // a segment boundary at the batch's end: checkpoint, queue the segment
+      const uint32_t e = b0 + (uint32_t)B;
+      if (e % kSeg == 0u && e / kSeg <= (uint32_t)(kSegMax - 1)) {
+        write_ckpt((int)(e / kSeg) - 1);
+        emit_segment(cur_seg);
+        cur_seg = (int)(e / kSeg);
+      }
     }
 #pragma unroll
     for (int u = 0; u < R; ++u) {
@@ -196,10 +229,13 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
       valid[u] = vn[u];
     }
   }
+  if (out.segments) {  // the final (T, colour), and the segment the walk ended in
+    write_ckpt(kSegMax - 1);
+    emit_segment(cur_seg);
+  }
   float lc = 0.f, ld = 0.f, nd = 0.f;
   if (has) {
     const int64_t HW = (int64_t)cam.H * cam.W;
-    const int64_t pix = (int64_t)f * HW + (int64_t)py * cam.W + px;
 #pragma unroll
     for (int c = 0; c < C; ++c) out.color[((int64_t)f * C + c) * HW + (int64_t)py * cam.W + px] = acc[c];
     out.alpha[pix] = 1.f - T_;
@@ -343,8 +379,10 @@ static void launch_forward_cb(const Work &w, const Prm &prm, int64_t N, int F, i
 void launch_forward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn, float *color,
                     float *depth, float *alpha, int32_t *index_map, const float *tcolor, const float *tdepth,
                     float *loss_out, float w_c, float w_d, uint32_t *fmask, cudaStream_t s) {
+  // the persistent schedule with composited-lane masks also leaves the backward's segments
   const FwdOut out{color, depth, alpha, index_map, tcolor, tdepth,
-                   (tn.schedule == 1 && tcolor != nullptr) ? loss_out : nullptr, w_c, w_d, fmask};
+                   (tn.schedule == 1 && tcolor != nullptr) ? loss_out : nullptr, w_c, w_d, fmask,
+                   (tn.schedule == 1 && fmask != nullptr) ? 1 : 0};
   if (C == 3) {
     if (tn.batch == 64) launch_forward_cb<3, 64>(w, prm, N, F, T, tn, out, s);
     else launch_forward_cb<3, 32>(w, prm, N, F, T, tn, out, s);

@@ -138,6 +138,22 @@ __device__ __forceinline__ uint32_t first_item(const Work &w, int wid, int sprea
   return (k / P) * P * gridDim.x + P * blockIdx.x + k % P;
 }
 
+// 32 x 32 bit-matrix transpose across a warp: lane i passes row i (bit j = element (i, j))
+// and gets column i back (bit j = element (j, i)).  Five butterfly stages: stage s swaps the
+// off-diagonal s x s blocks of every 2s x 2s block between lanes i and i ^ s, so after the
+// stages for s = 16, 8, 4, 2, 1 every block has been transposed in place.
+__device__ __forceinline__ uint32_t bit_transpose32(uint32_t x, int lane) {
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    // low s bits of every 2s-bit group: 0x0000ffff, 0x00ff00ff, 0x0f0f0f0f, 0x33333333, 0x55555555
+    const uint32_t m = s == 16 ? 0x0000ffffu : s == 8 ? 0x00ff00ffu : s == 4 ? 0x0f0f0f0fu : s == 2 ? 0x33333333u
+                                                                                                   : 0x55555555u;
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, s);
+    x = (lane & s) ? ((x & ~m) | ((y & ~m) >> s)) : ((x & m) | ((y & m) << s));
+  }
+  return x;
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -225,7 +241,7 @@ void launch_forward(int C, const Work &w, const Prm &prm, int64_t N, int F, int 
 // a pixel subset: the groups changed, so the backward walks the lists with the culling).
 void launch_backward(int C, const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn,
                      const float *dL_dcolor, const float *dL_ddepth, const L1Fused &l1, const uint32_t *fmask,
-                     cudaStream_t s);
+                     bool segments, cudaStream_t s);
 void init_backward_attributes();
 void launch_loss_finalize(const Work &w, int FT, int gshift, int C, float w_c, float w_d, float *loss_out,
                           cudaStream_t s);

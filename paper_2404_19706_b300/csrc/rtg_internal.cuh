@@ -60,8 +60,9 @@ enum Counter {
   kBwdSteps = 13 * kCounterStride,    // steps of the backward's per-lane fragment replay (warp-wide)
   kDepthPix = 14 * kCounterStride,    // pixels in the last fused L1 loss's depth term (D_hat != -1, D > 0)
   kWinStable = 15 * kCounterStride,   // projected (frame, stable Gaussian) entries of the open window (kept)
+  kBSeg0 = 16 * kCounterStride,       // backward segments queued in cost bins 0..kSegBins-1 (one slot each)
 };
-constexpr int kNumCounterSlots = 16;  // slots; all but kWinStable are cleared at the start of every call
+constexpr int kNumCounterSlots = 20;  // slots; all but kWinStable are cleared at the start of every call
 constexpr int kNumCounters = kNumCounterSlots * kCounterStride;  // array length
 
 struct DevCam {
@@ -96,6 +97,18 @@ struct L1Fused {
   const float *tcolor, *tdepth;  // targets [F,C,H,W], [F,H,W]
   const float *color, *depth;    // the forward's rendered colour and depth
 };
+
+// Backward segments.  The persistent backward takes a 32-pixel group's list in segments of
+// kSeg entries (the last of kSegMax segments runs to the end of the list), so that no warp
+// replays a whole long list alone.  The forward leaves, for each pixel and each segment
+// boundary it walked past, the transmission and the colour composited in front of it
+// (Eq. 1 and 3 over the entries before the boundary), and the final pair after its walk;
+// the backward starts a segment from them.  Finished segments go to one of kSegBins queues
+// by their cost (the most fragments a lane composited in them), the costliest first.
+constexpr int kSeg = 64;
+constexpr int kSegMax = 8;
+constexpr int kSegBins = 4;
+__host__ __device__ inline int ck4_of(int C) { return (C + 4) / 4; }  // float4 per checkpoint: T, C colours
 
 struct Work {
   DevCam *cams;
@@ -132,6 +145,11 @@ struct Work {
   double *loss_acc;     // [4] FP64 sums of the persistent forward's fused L1 (colour, depth, depth
                         // count); the CTA that finalizes the loss returns them to zero
   uint32_t *status;     // host-mapped status word (device pointer)
+  float4 *ckpt;         // [kSegMax][px_cap][ck4]: (T, colour in front) at entry boundaries
+                        // kSeg, 2 kSeg, ..., then the pixel's final (T, colour) at index kSegMax - 1
+  uint32_t *bseg;       // [kSegBins][bseg_cap] queued backward segments: tile << 6 | segment << 3 | group
+  int64_t px_cap;       // pixels of the capacity (frames x width x height)
+  int64_t bseg_cap;     // entries per segment bin
 };
 
 // ----------------------------------------------------------------------------- sizes

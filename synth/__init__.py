@@ -22,5 +22,6 @@ from .scenes import (  # noqa: F401
     room_camera_candidates,
     room_scene,
     scatter_scene,
+    stack_scene,
     sh_coefficients,
 )

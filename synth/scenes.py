@@ -192,6 +192,26 @@ def scatter_scene(seed: int, n: int = 2000) -> Tuple[Scene, Camera]:
     return scene, cam
 
 
+def stack_scene(seed: int, n: int = 1600, size: int = 32, f: float = 60.0) -> Tuple[Scene, Camera]:
+    """A deep stack of faint, wide ellipsoids on the optical axis of a small identity camera:
+    the pixels near the centre composite hundreds of fragments before their transmission
+    runs out, so the render tiles there hold lists of several hundred entries.
+
+    Means: x, y ~ N(0, 0.04) m, z ~ U[1.5, 3] m; scales log-uniform in [0.08, 0.2] m per
+    axis; uniform random rotations; opacity ~ U[0.015, 0.04]; RGB ~ U[0, 1]; every other
+    Gaussian unstable.  Camera size x size, focal length f, centred principal point.
+    """
+    rng = np.random.default_rng(seed)
+    means = np.stack([rng.normal(0, 0.04, n), rng.normal(0, 0.04, n), rng.uniform(1.5, 3.0, n)], 1)
+    scales = np.exp(rng.uniform(math.log(0.08), math.log(0.2), (n, 3)))
+    quats = _shoemake_quats(rng, n)
+    scene = Scene(means=means.astype(F32), scales=scales.astype(F32), quats=quats.astype(F32),
+                  opacity=rng.uniform(0.015, 0.04, n).astype(F32), colors=rng.uniform(0, 1, (n, 3)).astype(F32),
+                  unstable=(np.arange(n) % 2 == 0).astype(np.uint8))
+    c = 0.5 * (size - 1)
+    return scene, identity_camera(size, size, f, c, c)
+
+
 # ----------------------------------------------------------------------------- rooms
 
 @dataclasses.dataclass

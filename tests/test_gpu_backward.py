@@ -46,10 +46,12 @@ def crop_problem(seed, n_keep=200, win=48, frac_unstable=0.5):
     return crop, wcam, tc, td
 
 
-def gpu_grads(scene, cam, mask, tc, td, w_c=1.0, w_d=1.0):
+def gpu_grads(scene, cam, mask, tc, td, w_c=1.0, w_d=1.0, tuning=None, stats=None):
     m = rtg()
     H, W = cam.height, cam.width
     ctx = ctx_for(scene.n, cam)
+    if tuning is not None:
+        ctx.set_tuning(tuning)
     g = m.Gaussians.from_scene(scene)
     color = torch.zeros(1, 3, H, W, device="cuda")
     depth = torch.full((1, H, W), -1.0, device="cuda")
@@ -67,6 +69,8 @@ def gpu_grads(scene, cam, mask, tc, td, w_c=1.0, w_d=1.0):
     m.render_backward(ctx, dc, dd, *grads)
     torch.cuda.synchronize()
     assert m.get_status(ctx) == 0
+    if stats is not None:
+        stats.update(m.get_stats(ctx))
     return {k: t.cpu().numpy().astype(np.float64) for k, t in zip(GROUPS, grads)}, loss.cpu().numpy()
 
 
@@ -93,6 +97,37 @@ def test_gradients_match_oracle_analytic(seed):
     got, loss = gpu_grads(crop, cam, mask, tc, td)
     assert loss[0] == pytest.approx(ref["loss"], rel=1e-4)
     compare_groups(got, ref["grads"])
+
+
+@pytest.mark.parametrize("batch", [32, 64])
+def test_long_lists_replayed_in_segments_match_oracle(batch):
+    """The persistent backward takes each 32-pixel group's list in segments of 64 entries
+    (the eighth running to the end of the list), each started from the forward's checkpoint
+    of the transmission and of the colour in front of it.  On a deep stack of faint
+    Gaussians, where pixels walk 500-900 list entries before their transmission runs out,
+    its gradients match the FP64 oracle's, and those of the whole-list replay of the
+    per-tile schedule to float32 rounding."""
+    m = rtg()
+    scene, cam = synth.stack_scene(4100)
+    H, W = cam.height, cam.width
+    pre = oracle.render_image(scene, cam, ST)
+    assert pre["n_proc"].max() > 8 * 64  # fragments reach the open-ended last segment
+    mask = ~pre["grad_borderline"] & (pre["alpha"] > 0)
+    rng = np.random.default_rng(4101)
+    tc = rng.uniform(0, 1, (3, H, W))
+    td = rng.uniform(1.5, 3.0, (H, W))
+    ys, xs = np.nonzero(mask)
+    ref = oracle.loss_and_grads(scene, cam, ST, np.stack([xs, ys], 1), tc[:, ys, xs].T, td[ys, xs])
+    st = {}
+    seg, loss = gpu_grads(scene, cam, mask, tc, td, tuning=m.Tuning(8, 8, batch, 1, 2, 8, 512), stats=st)
+    assert st["max_tile_pairs"] > 8 * 64
+    assert loss[0] == pytest.approx(ref["loss"], rel=1e-4)
+    compare_groups(seg, ref["grads"])
+    whole, _ = gpu_grads(scene, cam, mask, tc, td, tuning=m.Tuning(8, 8, batch, 0, 4, 8, 512))
+    for k in GROUPS:
+        scale = np.abs(whole[k]).max()
+        assert scale > 0
+        assert np.abs(seg[k] - whole[k]).max() <= 1e-4 * scale, (k, np.abs(seg[k] - whole[k]).max(), scale)
 
 
 def test_gradients_match_finite_differences():
