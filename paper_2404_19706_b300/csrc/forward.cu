@@ -159,13 +159,18 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
     }
     nrec += (uint32_t)cnt;
     __syncwarp();
-    if (!done) {
-      // composites fragment k (footprint fa) in list order; false once the pixel stops
-      auto blend = [&](int k, float fa) -> bool {
-        if (fa < prm.alpha_min) return true;
+    if (!__all_sync(0xffffffffu, done)) {
+      // composites fragment k (footprint fa) in list order, without branches: a fragment
+      // below alpha_min, the fragment that would take the transmission below t_eps (the
+      // pixel stops before it) and every fragment after the stop leave the pixel's state as
+      // it is (weight 0, and fmaf(c, 0, a) = a)
+      auto blend = [&](int k, float fa) {
         const float Tn = T_ * (1.f - fa);
-        if (Tn < prm.t_eps) return false;
-        const float wgt = fa * T_;
+        const bool live = !done && fa >= prm.alpha_min;
+        const bool stop = live && Tn < prm.t_eps;
+        const bool comp = live && !stop;
+        done = done || stop;
+        const float wgt = comp ? fa * T_ : 0.f;
         const float4 c0 = s_rec[2][k];
         float cw[8] = {c0.x, c0.y, c0.z, c0.w, 0.f, 0.f, 0.f, 0.f};
         if (H4 == 4) {
@@ -175,31 +180,35 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
 #pragma unroll
         for (int c = 0; c < C; ++c) acc[c] = fmaf(cw[c], wgt, acc[c]);
         const uint32_t jj = s_j[k];
-        if (hit_j < 0 && fa > prm.delta_alpha) hit_j = (int)jj;
-        T_ = Tn;
-        last = jj + 1;
-        ++nfrag;
-        ++segfrag;
-        ebits |= (Bits)1 << (jj - b0);
-        return true;
+        hit_j = (comp && hit_j < 0 && fa > prm.delta_alpha) ? (int)jj : hit_j;
+        T_ = comp ? Tn : T_;
+        ebits |= comp ? ((Bits)1 << (jj - b0)) : (Bits)0;
       };
       auto alpha_of = [&](int k) {
         const float4 r0 = s_rec[0][k], r1 = s_rec[1][k];
         float dx, dy, t1, t2, g;
         return footprint(fpx, fpy, r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, prm.f_max, dx, dy, t1, t2, g);
       };
-      // two footprints at a time: they are independent, only the blending is in order
-      int k = 0;
-      for (; k + 1 < cnt; k += 2) {
-        const float fa0 = alpha_of(k), fa1 = alpha_of(k + 1);
-        if (!blend(k, fa0) || !blend(k + 1, fa1)) {
-          done = true;
-          break;
+      // eight records a round, two footprints at a time (they are independent; only the
+      // blending is in order); the warp leaves the batch once all its pixels stopped
+      for (int k0 = 0; k0 < cnt; k0 += 8) {
+#pragma unroll
+        for (int q = 0; q < 8; q += 2) {
+          const int ka = min(k0 + q, cnt - 1), kb = min(k0 + q + 1, cnt - 1);
+          const float fa0 = alpha_of(ka), fa1 = alpha_of(kb);
+          if (k0 + q < cnt) blend(ka, fa0);
+          if (k0 + q + 1 < cnt) blend(kb, fa1);
         }
+        if (__all_sync(0xffffffffu, done)) break;
       }
-      if (!done && k < cnt && !blend(k, alpha_of(k))) done = true;
     }
     __syncwarp();
+    if (ebits != (Bits)0) {  // the batch's fragments of this lane: count, and the last one
+      const uint32_t nb = (uint32_t)(sizeof(Bits) == 8 ? __popcll((unsigned long long)ebits) : __popc((uint32_t)ebits));
+      nfrag += nb;
+      segfrag += nb;
+      last = b0 + (uint32_t)(sizeof(Bits) == 8 ? 64 - __clzll((long long)ebits) : 32 - __clz((int)ebits));
+    }
     if (out.fmask != nullptr) {
       // lane L gets the composited lanes of entry b0 + 32u + L (a bit transpose of the
       // lanes' entry bits; culled entries get none) and stores them, one coalesced store per
@@ -211,8 +220,8 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
         if (__any_sync(0xffffffffu, wv != 0u)) am = bit_transpose32(wv, lane);
         if (valid[u]) out.fmask[(int64_t)(off + b0 + (uint32_t)(u * 32 + lane)) * ngrp + grp] = am;
       }
-      ebits = 0;
     }
+    ebits = 0;
     if (out.segments) {  // a segment boundary at the batch's end: checkpoint, queue the segment
       const uint32_t e = b0 + (uint32_t)B;
       if (e % kSeg == 0u && e / kSeg <= (uint32_t)(kSegMax - 1)) {
@@ -291,11 +300,11 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
 }
 
 // Schedule 0: CTA `tile` with one warp per 32-pixel group of the tile's pixel list.
-// Registers for the occupancy the tuned schedules use: three CTAs per SM for C <= 4 with
-// 32-record batches (80 registers), two with 64-record batches (128); C = 8 keeps the
-// registers it needs.
+// Registers: two CTAs per SM for C <= 4 (up to 128 a thread, enough to keep the compositing
+// state and the prefetched batch out of local memory; a third CTA at 80 registers spilled
+// inside the blending loop and was slower); C = 8 keeps the registers it needs.
 template <int C, int B>
-constexpr int fwd_min_ctas() { return C <= 4 ? (B == 32 ? 3 : 2) : 1; }
+constexpr int fwd_min_ctas() { return C <= 4 ? 2 : 1; }
 
 template <int C, int B>
 __global__ void __launch_bounds__(kMaxTilePix, fwd_min_ctas<C, B>()) k_forward(Work w, Prm prm, int64_t N, int T,
