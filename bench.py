@@ -444,7 +444,10 @@ def step_sum(alg, per_launch, extra=()):
 # filled only when the run's workload, dominant kernel and tuning match a captured one of
 # the kernel as it is now.  Source and command: the profiles/ summary named beside each.
 NCU_TRAFFIC = {
-    ("masked-step", "backward", 8, 8, 64, 1): 17_403_904,  # k_backward_fl_queue<3> (compositing_fwd_bwd_1M_640x480_ncu.md)
+    # k_backward_seg_queue<3>, dram__bytes_read.sum + dram__bytes_write.sum of one launch
+    # (masked_step_300k_640x480_launches.md, masked_step_1M_640x480_launches.md)
+    ("target", "backward", 8, 8, 32, 1): 10_586_112,
+    ("masked-step", "backward", 8, 8, 32, 1): 20_423_168,
 }
 
 
