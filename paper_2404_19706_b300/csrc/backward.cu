@@ -886,7 +886,9 @@ __device__ __forceinline__ void project_backward_one(const GaussPtrs &g, const W
       gpc[2] = gJ[0] * (-cam.fx * iz * iz) + gJ[2] * (2.f * cam.fx * X * iz * iz * iz) +
                gJ[4] * (-cam.fy * iz * iz) + gJ[5] * (2.f * cam.fy * Y * iz * iz * iz) -
                (gmx * cam.fx * X + gmy * cam.fy * Y) * iz * iz + gz;
-      const float nc[3] = {A[kmin], A[3 + kmin], A[6 + kmin]};
+      float nc[3];  // column kmin of A, by selects (a run-time index would put A in local memory)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) nc[r] = kmin == 0 ? A[3 * r] : (kmin == 1 ? A[3 * r + 1] : A[3 * r + 2]);
 #pragma unroll
       for (int r = 0; r < 3; ++r) gpc[r] += gd0 * nc[r];
       float gnc[3];
@@ -929,8 +931,12 @@ __device__ __forceinline__ void project_backward_one(const GaussPtrs &g, const W
       }
       // n_c = W R e_k -> dL/dR[:, k] += W^T dL/dn_c = R_g dL/dn_c
 #pragma unroll
-      for (int r = 0; r < 3; ++r)
-        gR[3 * r + kmin] += cam.R[3 * r] * gnc[0] + cam.R[3 * r + 1] * gnc[1] + cam.R[3 * r + 2] * gnc[2];
+      for (int r = 0; r < 3; ++r) {
+        const float v = cam.R[3 * r] * gnc[0] + cam.R[3 * r + 1] * gnc[1] + cam.R[3 * r + 2] * gnc[2];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (kmin == c) gR[3 * r + c] += v;
+      }
     }
     // R(q) -> unit quaternion -> raw quaternion
     const float G01 = gR[1], G02 = gR[2], G10 = gR[3], G12 = gR[5], G20 = gR[6], G21 = gR[7];

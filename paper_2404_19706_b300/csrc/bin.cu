@@ -501,6 +501,35 @@ __device__ __forceinline__ uint32_t list_len(const Work &w, const uint32_t *extr
   return w.tile_count[t] + ((extra != nullptr && w.tile_npix[t] != 0u) ? extra[t] : 0u);
 }
 
+// Starts of the queue's cost classes, costliest (highest class) first: s_cls holds each
+// class's count on entry and its first queue position on return.  One warp: lane l takes
+// kPer consecutive classes from the top, the lanes' sums are scanned with shuffles.
+// Returns the total in every lane.
+__device__ __forceinline__ uint32_t class_starts(uint32_t *s_cls, int lane) {
+  constexpr int kPer = (kQueueClasses + 31) / 32;
+  uint32_t c[kPer], local = 0u;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int k = kQueueClasses - 1 - (lane * kPer + j);
+    c[j] = k >= 0 ? s_cls[k] : 0u;
+    local += c[j];
+  }
+  uint32_t inc = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
+  }
+  uint32_t run = inc - local;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int k = kQueueClasses - 1 - (lane * kPer + j);
+    if (k >= 0) s_cls[k] = run;
+    run += c[j];
+  }
+  return __shfl_sync(0xffffffffu, inc, 31);
+}
+
 // Thread t owns tiles [t * per, t * per + per) (per <= kScanSingleMax / 1024): their counts
 // are loaded once, all at once, and kept in registers for the offsets and the queue.
 // kEmit: the scatter of the staged pairs into their buckets is fused in.  Every CTA scans
@@ -612,17 +641,14 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Work w, int FT, int64_t max
   for (int u = 0; u < kScanPer; ++u)
     if (npx[u] != 0u) atomicAdd(&s_cls[queue_class(len[u])], (npx[u] + 31u) >> 5);
   __syncthreads();
-  if (tid == 0) {  // start of each class, classes in decreasing cost
-    uint32_t r = 0;
-    for (int k = kQueueClasses - 1; k >= 0; --k) {
-      const uint32_t c = s_cls[k];
-      s_cls[k] = r;
-      r += c;
+  if (wid == 0) {  // start of each class, classes in decreasing cost
+    const uint32_t r = class_starts(s_cls, lane);
+    if (lane == 0) {
+      w.counters[kItems] = r;
+      w.counters[kQFwd] = 0ull;
+      w.counters[kQBwd] = 0ull;
+      for (int b = 0; b < kSegBins; ++b) w.counters[kBSeg0 + b * kCounterStride] = 0ull;
     }
-    w.counters[kItems] = r;
-    w.counters[kQFwd] = 0ull;
-    w.counters[kQBwd] = 0ull;
-    for (int b = 0; b < kSegBins; ++b) w.counters[kBSeg0 + b * kCounterStride] = 0ull;
   }
   __syncthreads();
 #pragma unroll
@@ -819,17 +845,14 @@ __global__ void __launch_bounds__(1024) k_scan_bases(Work w, int FT, int64_t max
     s_start[tid] = c;
   }
   __syncthreads();
-  if (tid == 0) {
-    uint32_t run = 0;
-    for (int k = kQueueClasses - 1; k >= 0; --k) {
-      const uint32_t c = s_start[k];
-      s_start[k] = run;
-      run += c;
+  if (tid < 32) {
+    const uint32_t run = class_starts(s_start, tid);
+    if (tid == 0) {
+      w.counters[kItems] = run;
+      w.counters[kQFwd] = 0ull;
+      w.counters[kQBwd] = 0ull;
+      for (int b = 0; b < kSegBins; ++b) w.counters[kBSeg0 + b * kCounterStride] = 0ull;
     }
-    w.counters[kItems] = run;
-    w.counters[kQFwd] = 0ull;
-    w.counters[kQBwd] = 0ull;
-    for (int b = 0; b < kSegBins; ++b) w.counters[kBSeg0 + b * kCounterStride] = 0ull;
   }
   __syncthreads();
   if (tid < kQueueClasses) {

@@ -178,9 +178,9 @@ __device__ __forceinline__ bool project_gaussian(const DevCam &cam, const Prm &p
   fy1 = fminf(fy1, (float)(cam.H - 1));
   if (!(fx0 <= fx1) || !(fy0 <= fy1)) return false;
   o.x0 = (int)fx0; o.x1 = (int)fx1; o.y0 = (int)fy0; o.y1 = (int)fy1;
-  o.n[0] = A[kmin];
-  o.n[1] = A[3 + kmin];
-  o.n[2] = A[6 + kmin];
+  // column kmin of A, chosen by selects (a run-time index would put A in local memory)
+#pragma unroll
+  for (int r = 0; r < 3; ++r) o.n[r] = kmin == 0 ? A[3 * r] : (kmin == 1 ? A[3 * r + 1] : A[3 * r + 2]);
   o.d0 = Xf * o.n[0] + Yf * o.n[1] + Zf * o.n[2];
   return true;
 }

@@ -192,6 +192,65 @@ class MaskedStep:
         self.graph = graph
         return graph
 
+    def capture_frames(self, frames: Sequence, uploads: Optional[Sequence] = None,
+                       loss_host: Optional[Sequence[torch.Tensor]] = None, upload_streams: int = 4):
+        """One CUDA graph per sensor-frame buffer set, for a frame loop: ``frames`` holds (rgb,
+        depth) device tensors shaped like the step's frame (its depth scale is kept), and
+        ``replay(k)`` runs the iteration on set k and returns set k's own loss buffer.
+
+        With ``uploads`` (one pinned host (rgb, depth) pair per set), graph k also copies
+        uploads[k] into frame set (k + 1) % len(frames) while it computes (each array in two
+        halves over ``upload_streams`` side branches of the graph: one copy alone does not fill
+        the host link), so replaying graph i % 2 for frame i moves frame i + 1 in during step
+        i.  With ``loss_host`` (one pinned float[3] per set), graph k then copies its loss
+        there.  A frame loop is then one launch per frame.  step() keeps its own graph, frame
+        and loss buffer."""
+        if self.frame is None:
+            raise ValueError("capture_frames needs a step built with frame=")
+        n = len(frames)
+        torch.cuda.synchronize()
+        own = (self.frame, self.loss)
+        scale = self.frame[2]
+        side = [torch.cuda.Stream() for _ in range(upload_streams)] if uploads is not None else []
+        self.frame_graphs, self.frame_losses = [], []
+        for k, (rgb, dep) in enumerate(frames):
+            if rgb.shape != own[0][0].shape or dep.shape != own[0][1].shape:
+                raise ValueError("each frame set must match the step's frame shapes")
+            self.frame = (rgb, dep, scale)
+            self.loss = torch.zeros(3, device=self.loss.device)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                cur = torch.cuda.current_stream()
+                if uploads is not None:
+                    fork = torch.cuda.Event()
+                    fork.record(cur)
+                    pieces = []
+                    for d, h in zip(frames[(k + 1) % n], uploads[k]):
+                        db, hb = d.reshape(-1).view(torch.uint8), h.reshape(-1).view(torch.uint8)
+                        half = (db.numel() // 2) & ~15
+                        pieces += [(db[:half], hb[:half]), (db[half:], hb[half:])] if half else [(db, hb)]
+                    for st in side:
+                        st.wait_event(fork)
+                    for j, (d, h) in enumerate(pieces):
+                        with torch.cuda.stream(side[j % len(side)]):
+                            d.copy_(h, non_blocking=True)
+                self._body()
+                if loss_host is not None:
+                    loss_host[k].copy_(self.loss, non_blocking=True)
+                for st in side:  # join the upload branches
+                    e = torch.cuda.Event()
+                    e.record(st)
+                    cur.wait_event(e)
+            self.frame_graphs.append(graph)
+            self.frame_losses.append(self.loss)
+        self.frame, self.loss = own
+        torch.cuda.synchronize()
+
+    def replay(self, k: int):
+        """One iteration on frame set k of capture_frames; returns that set's device loss."""
+        self.frame_graphs[k].replay()
+        return self.frame_losses[k]
+
     def write_back(self, stream=None):
         """Scatter the optimised compact parameters into the full arrays."""
         api.scatter_unstable(self.ids, self.u, self.full, stream)

@@ -86,3 +86,70 @@ def test_masked_step_from_sensor_frame_equals_decoded_targets():
     # varies between runs
     for a_, b_ in zip(out[0][3], out[1][3]):
         np.testing.assert_allclose(b_, a_, rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("uploads", [False, True])
+def test_graphs_per_frame_set_equal_eager_steps(uploads):
+    """MaskedStep.capture_frames: one graph per sensor-frame buffer set; replay(k) runs the
+    iteration on set k and returns that set's loss.  Alternating two sets holding frames A and
+    B gives the losses and parameters of eager steps on A, B, A, B; step() keeps its own
+    graph and loss buffer.  With uploads, set 1 starts empty: graph 0 uploads B into it from
+    pinned host memory while it computes on A, graph 1 uploads A back into set 0, and each
+    graph copies its loss to its pinned host slot."""
+    import synth
+    m = rtg()
+    scene, layout = synth.room_scene(535, 20000)
+    cam = next(synth.room_camera_candidates(536, layout, 96, 72, 90.0))
+    scene.unstable = synth.flag_blobs(scene, [cam], 3000, 2, seed=7)
+    H, W = cam.height, cam.width
+    rng = np.random.default_rng(537)
+    frames = []
+    for _ in range(2):
+        rgb = torch.from_numpy(rng.integers(0, 256, (1, H, W, 3), dtype=np.uint8)).cuda()
+        dep = torch.from_numpy(rng.integers(4000, 20000, (1, H, W)).astype(np.uint16)).cuda()
+        frames.append((rgb, dep))
+    runs = []
+    for graphed in (False, True):
+        ctx = m.Context(max_gaussians=scene.n, max_width=W, max_height=H)
+        g = m.Gaussians.from_scene(scene)
+        mask = torch.zeros(1, H, W, dtype=torch.uint8, device="cuda")
+        m.unstable_mask(ctx, cam, g, m.RenderSettings(), mask)
+        tc, td = torch.zeros(1, 3, H, W, device="cuda"), torch.zeros(1, H, W, device="cuda")
+        own = (frames[0][0].clone(), frames[0][1].clone())
+        step = m.MaskedStep(ctx, g, [cam], mask, tc, td, frame=(own[0], own[1], 5000.0))
+        losses = []
+        if graphed:
+            sets = [[torch.zeros_like(f[0]), torch.zeros_like(f[1])] for f in frames]
+            sets[0][0].copy_(frames[0][0])
+            sets[0][1].copy_(frames[0][1])
+            if uploads:
+                hosts = [[frames[1][0].cpu().pin_memory(), frames[1][1].cpu().pin_memory()],
+                         [frames[0][0].cpu().pin_memory(), frames[0][1].cpu().pin_memory()]]
+                lh = [torch.full((3,), -1.0).pin_memory() for _ in range(2)]
+                step.capture_frames(sets, uploads=hosts, loss_host=lh)
+            else:
+                sets[1][0].copy_(frames[1][0])
+                sets[1][1].copy_(frames[1][1])
+                step.capture_frames(sets)
+            for k in (0, 1, 0, 1):
+                out = step.replay(k)
+                torch.cuda.synchronize()
+                losses.append(out.cpu().numpy().copy())
+                if uploads:
+                    assert np.array_equal(lh[k].numpy(), losses[-1])
+            if uploads:
+                assert torch.equal(sets[1][0], frames[1][0]) and torch.equal(sets[0][1], frames[0][1])
+            assert step.loss.data_ptr() not in [x.data_ptr() for x in step.frame_losses]
+        else:
+            for k in (0, 1, 0, 1):
+                own[0].copy_(frames[k][0])
+                own[1].copy_(frames[k][1])
+                losses.append(step.step().cpu().numpy().copy())
+        torch.cuda.synchronize()
+        runs.append((losses, [t.cpu().numpy().copy() for t in step.u]))
+        ctx.close()
+    np.testing.assert_array_equal(runs[0][0][0], runs[1][0][0])  # the first forward: same parameters
+    for a_, b_ in zip(runs[0][0][1:], runs[1][0][1:]):
+        np.testing.assert_allclose(b_, a_, rtol=1e-5)
+    for a_, b_ in zip(runs[0][1], runs[1][1]):  # float32 atomics order the gradient sums differently
+        np.testing.assert_allclose(b_, a_, rtol=1e-4, atol=1e-6)
