@@ -447,6 +447,7 @@ NCU_TRAFFIC = {
     # k_backward_seg_queue<3>, dram__bytes_read.sum + dram__bytes_write.sum of one launch
     # (masked_step_300k_640x480_launches.md, masked_step_1M_640x480_launches.md)
     ("target", "backward", 8, 8, 32, 1): 10_586_112,
+    ("target", "forward", 8, 8, 32, 1): 7_217_152,  # k_forward_queue<3, 32> (compositing_fwd_bwd_300k_640x480_ncu.md)
     ("masked-step", "backward", 8, 8, 32, 1): 20_423_168,
 }
 
@@ -1047,8 +1048,8 @@ def run_forward_only(args, kw=FWD):
     g = rtg.Gaussians.from_scene(scene, device=dev)
     # the unstable index is fixed (every Gaussian of this scene is unstable): computed once,
     # as an optimisation window does, not by every forward
-    rank, ids, nu = rtg.unstable_rank(ctx, g.unstable)
-    g = dataclasses.replace(g, rank_map=rank, unstable_ids=ids, n_unstable=nu)
+    urank, uids, nu = rtg.unstable_rank(ctx, g.unstable)
+    g = dataclasses.replace(g, rank_map=urank, unstable_ids=uids, n_unstable=nu)
     color = torch.zeros(1, C, H, W, device=dev)
     depth = torch.full((1, H, W), -1.0, device=dev)
     alpha = torch.zeros(1, H, W, device=dev)
