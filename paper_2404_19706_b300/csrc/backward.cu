@@ -547,8 +547,9 @@ __device__ __forceinline__ void backward_group_fl(const Work &w, const Prm &prm,
     nsteps += __reduce_max_sync(0xffffffffu, (unsigned)__popc(mine));
     // back to front over this lane's own fragments: the transmission in front of each by
     // division, dL/df from the colour behind it, and for an unstable record (f T, dL/dalpha)
-    auto replay = [&](int k, float fa, float g, float alpha) {
-      const float iom = __fdividef(1.f, 1.f - fa);  // 1 - f >= 1 - f_max: a normal divisor
+    // a fragment replayed as invalid (past this lane's last one) leaves T and S as they are
+    auto replay = [&](int k, float fa, float g, float alpha, bool valid) {
+      const float iom = valid ? __fdividef(1.f, 1.f - fa) : 1.f;  // 1 - f >= 1 - f_max: a normal divisor
       T_ = T_ * iom;
       const float wgt = fa * T_;
       const float4 c0 = sm.rec[2][k];
@@ -561,28 +562,31 @@ __device__ __forceinline__ void backward_group_fl(const Work &w, const Prm &prm,
 #pragma unroll
       for (int c = 0; c < C; ++c) {
         dLdf = fmaf(dC[c], fmaf(cw[c], T_, -S[c] * iom), dLdf);
-        S[c] = fmaf(cw[c], wgt, S[c]);
+        const float Sn = fmaf(cw[c], wgt, S[c]);
+        S[c] = valid ? Sn : S[c];
       }
-      if (sm.jr[k].y >= 0) {
+      if (valid && sm.jr[k].y >= 0) {
         const float G = alpha * g < prm.f_max ? dLdf * g : 0.f;  // unclamped branch of min(f_max, alpha g)
         sm.wg[sm.us[k]][lane] = make_float2(wgt, G);
       }
     };
-    // two fragments at a time: their footprints are independent, the recurrences then take
-    // them in order
+    // two fragments a round in one block of straight-line code (a missing second one
+    // replays as invalid, not branched around), so the compiler overlaps their loads and
+    // footprints; the recurrences then take them in order
     while (mine) {
       const int kA = 31 - __clz(mine);
       mine ^= 1u << kA;
-      const int kB = mine ? 31 - __clz(mine) : kA;
-      mine &= ~(1u << kB);
+      const bool vB = mine != 0u;
+      const int kB = vB ? 31 - __clz(mine) : kA;
+      mine ^= vB ? (1u << kB) : 0u;
       const float4 a0 = sm.rec[0][kA], a1 = sm.rec[1][kA], b0 = sm.rec[0][kB], b1 = sm.rec[1][kB];
       float dx, dy, t1, t2, gA, gB;
       const float faA = footprint(fpx, fpy, a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, prm.f_max, dx, dy, t1,
                                   t2, gA);
       const float faB = footprint(fpx, fpy, b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w, prm.f_max, dx, dy, t1,
                                   t2, gB);
-      replay(kA, faA, gA, a1.w);
-      if (kB != kA) replay(kB, faB, gB, b1.w);
+      replay(kA, faA, gA, a1.w, true);
+      replay(kB, faB, gB, b1.w, vB);
     }
     __syncwarp();
     // the rows of the unstable records: L lanes a record (L = 32 / nu rounded down to a

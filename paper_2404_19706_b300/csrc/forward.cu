@@ -164,9 +164,9 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
       // below alpha_min, the fragment that would take the transmission below t_eps (the
       // pixel stops before it) and every fragment after the stop leave the pixel's state as
       // it is (weight 0, and fmaf(c, 0, a) = a)
-      auto blend = [&](int k, float fa) {
+      auto blend = [&](int k, float fa, bool valid) {
         const float Tn = T_ * (1.f - fa);
-        const bool live = !done && fa >= prm.alpha_min;
+        const bool live = valid && !done && fa >= prm.alpha_min;
         const bool stop = live && Tn < prm.t_eps;
         const bool comp = live && !stop;
         done = done || stop;
@@ -189,15 +189,15 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
         float dx, dy, t1, t2, g;
         return footprint(fpx, fpy, r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, prm.f_max, dx, dy, t1, t2, g);
       };
-      // eight records a round, two footprints at a time (they are independent; only the
-      // blending is in order); the warp leaves the batch once all its pixels stopped
+      // eight records a round in one block of straight-line code (a record past the batch's
+      // end is blended as invalid, not branched around), so the compiler overlaps the
+      // records' loads and footprints and only the transmission recurrence stays serial;
+      // the warp leaves the batch once all its pixels stopped
       for (int k0 = 0; k0 < cnt; k0 += 8) {
 #pragma unroll
-        for (int q = 0; q < 8; q += 2) {
-          const int ka = min(k0 + q, cnt - 1), kb = min(k0 + q + 1, cnt - 1);
-          const float fa0 = alpha_of(ka), fa1 = alpha_of(kb);
-          if (k0 + q < cnt) blend(ka, fa0);
-          if (k0 + q + 1 < cnt) blend(kb, fa1);
+        for (int q = 0; q < 8; ++q) {
+          const int k = min(k0 + q, cnt - 1);
+          blend(k, alpha_of(k), k0 + q < cnt);
         }
         if (__all_sync(0xffffffffu, done)) break;
       }
