@@ -30,10 +30,10 @@ struct FwdOut {
 };
 
 // Renders the pixels of group `grp` (32 consecutive entries of the tile's pixel list) of
-// render tile `tile`.  Called by a whole warp; s_rec / s_j are the warp's own staging.
+// render tile `tile`.  Called by a whole warp; s_rec / s_jg are the warp's own staging.
 template <int C, int B>
 __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int64_t N, int T, int tile, int grp,
-                                              float4 (*s_rec)[B], uint32_t *s_j, const FwdOut &out,
+                                              float4 (*s_rec)[B], uint2 *s_jg, const FwdOut &out,
                                               double *s_loss = nullptr) {
   constexpr int H4 = (C <= 4) ? 3 : 4;
   constexpr int R = B / 32;  // records per lane per batch
@@ -66,7 +66,7 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
 #pragma unroll
   for (int c = 0; c < C; ++c) acc[c] = 0.f;
   uint32_t last = 0, nfrag = 0, nrec = 0;
-  int hit_j = -1;
+  int hit_gid = -1;  // the first fragment with f > delta_alpha (Eq. 4), its Gaussian
   bool done = !has;
   // With out.fmask, entry j of the tile's list gets, for this group, the mask of the lanes
   // that composited it (0 where culled or composited by none), at (off + j) * groups + grp:
@@ -107,14 +107,16 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
   float4 r[R][H4];
   float2 bb[R];
   bool valid[R];
-  uint32_t gnext[R];
+  uint32_t gnext[R], gcur[R];  // Gaussian ids of batch b0 + 2B and of the batch in r
 #pragma unroll
   for (int u = 0; u < R; ++u) {
     const uint32_t j = (uint32_t)(u * 32 + lane);
     valid[u] = j < n;
     bb[u] = make_float2(0.f, 0.f);
+    gcur[u] = 0u;
     if (valid[u]) {
       const uint32_t gid = w.sorted[off + j];
+      gcur[u] = gid;
 #pragma unroll
       for (int k = 0; k < H4; ++k) r[u][k] = rec[(int64_t)gid * H4 + k];
       bb[u] = box[gid];
@@ -127,11 +129,13 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
     float4 rn[R][H4];
     float2 bn[R];
     bool vn[R];
+    uint32_t gn[R];
 #pragma unroll
     for (int u = 0; u < R; ++u) {
       const uint32_t jn = b0 + B + (uint32_t)(u * 32 + lane);
       vn[u] = jn < n;
       bn[u] = make_float2(0.f, 0.f);
+      gn[u] = gnext[u];
       if (vn[u]) {
         const uint32_t gid = gnext[u];
 #pragma unroll
@@ -153,7 +157,7 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
         const int slot = cnt + __popc(bal & lanemask_lt());
 #pragma unroll
         for (int k = 0; k < H4; ++k) s_rec[k][slot] = r[u][k];
-        s_j[slot] = b0 + (uint32_t)(u * 32 + lane);
+        s_jg[slot] = make_uint2(b0 + (uint32_t)(u * 32 + lane), gcur[u]);
       }
       cnt += __popc(bal);
     }
@@ -179,8 +183,9 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
         }
 #pragma unroll
         for (int c = 0; c < C; ++c) acc[c] = fmaf(cw[c], wgt, acc[c]);
-        const uint32_t jj = s_j[k];
-        hit_j = (comp && hit_j < 0 && fa > prm.delta_alpha) ? (int)jj : hit_j;
+        const uint2 jg = s_jg[k];
+        const uint32_t jj = jg.x;
+        hit_gid = (comp && hit_gid < 0 && fa > prm.delta_alpha) ? (int)jg.y : hit_gid;
         T_ = comp ? Tn : T_;
         ebits |= comp ? ((Bits)1 << (jj - b0)) : (Bits)0;
       };
@@ -236,6 +241,7 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
       for (int k = 0; k < H4; ++k) r[u][k] = rn[u][k];
       bb[u] = bn[u];
       valid[u] = vn[u];
+      gcur[u] = gn[u];
     }
   }
   if (out.segments) {  // the final (T, colour), and the segment the walk ended in
@@ -248,10 +254,8 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
 #pragma unroll
     for (int c = 0; c < C; ++c) out.color[((int64_t)f * C + c) * HW + (int64_t)py * cam.W + px] = acc[c];
     out.alpha[pix] = 1.f - T_;
-    int hit_gid = -1;
     float D = -1.f;
-    if (hit_j >= 0) {
-      hit_gid = (int)w.sorted[off + hit_j];
+    if (hit_gid >= 0) {
       const float4 c0 = w.rec_cold[((int64_t)f * N + hit_gid) * 2];
       const float4 c1 = w.rec_cold[((int64_t)f * N + hit_gid) * 2 + 1];
       const float ux = (fpx - cam.cx) / cam.fx, uy = (fpy - cam.cy) / cam.fy;
@@ -312,11 +316,11 @@ __global__ void __launch_bounds__(kMaxTilePix, fwd_min_ctas<C, B>()) k_forward(W
   grid_dep_wait();
   constexpr int H4 = (C <= 4) ? 3 : 4;
   __shared__ float4 s_rec[kMaxTilePix / 32][H4][B];
-  __shared__ uint32_t s_j[kMaxTilePix / 32][B];
+  __shared__ uint2 s_jg[kMaxTilePix / 32][B];
   if (w.counters[kSkip] != 0ull) return;
   const int tile = blockIdx.x, wid = threadIdx.x >> 5;
   if (wid * 32 >= (int)w.tile_npix[tile]) return;
-  forward_group<C, B>(w, prm, N, T, tile, wid, s_rec[wid], s_j[wid], out);
+  forward_group<C, B>(w, prm, N, T, tile, wid, s_rec[wid], s_jg[wid], out);
 }
 
 // Schedule 1: persistent warps.  Each warp starts with one of the first items; later items come
@@ -328,7 +332,7 @@ __global__ void __launch_bounds__(256, fwd_min_ctas<C, B>()) k_forward_queue(Wor
   grid_dep_wait();
   constexpr int H4 = (C <= 4) ? 3 : 4;
   __shared__ float4 s_rec[8][H4][B];
-  __shared__ uint32_t s_j[8][B];
+  __shared__ uint2 s_jg[8][B];
   __shared__ double s_loss[3];
   if (w.counters[kSkip] != 0ull) return;
   if (threadIdx.x < 3) s_loss[threadIdx.x] = 0.0;
@@ -339,7 +343,7 @@ __global__ void __launch_bounds__(256, fwd_min_ctas<C, B>()) k_forward_queue(Wor
   uint32_t it = first_item(w, wid, spread);
   while (it < nitems) {
     const uint32_t item = w.items[it];
-    forward_group<C, B>(w, prm, N, T, (int)(item >> 3), (int)(item & 7u), s_rec[wid], s_j[wid], out,
+    forward_group<C, B>(w, prm, N, T, (int)(item >> 3), (int)(item & 7u), s_rec[wid], s_jg[wid], out,
                         out.loss_out != nullptr ? s_loss : nullptr);
     uint32_t nx = 0;
     if (lane == 0) nx = nwarps + (uint32_t)atomicAdd(w.counters + kQFwd, 1ull);
