@@ -228,8 +228,12 @@ def test_precomputed_unstable_index_is_bitwise_identical():
     for a, b in zip(outs[0][:3], outs[1][:3]):
         assert torch.equal(a, b)
     assert outs[0][0].float().mean() > 0.05
-    for a, b in zip(outs[0][3:], outs[1][3:]):  # atomics: equal up to summation order
-        np.testing.assert_allclose(b.numpy(), a.numpy(), rtol=1e-5, atol=1e-9)
+    # the gradient rows are float32 atomic sums whose order differs between the two runs; an
+    # element whose contributions cancel can differ relatively more, so the bound is relative
+    # to each group's largest magnitude
+    for a, b in zip(outs[0][3:], outs[1][3:]):
+        a, b = a.numpy().astype(np.float64), b.numpy().astype(np.float64)
+        assert np.abs(b - a).max() <= 1e-5 * np.abs(a).max()
 
 
 def test_fused_l1_forward_backward_match_separate_calls():
