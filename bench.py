@@ -444,11 +444,11 @@ def step_sum(alg, per_launch, extra=()):
 # filled only when the run's workload, dominant kernel and tuning match a captured one of
 # the kernel as it is now.  Source and command: the profiles/ summary named beside each.
 NCU_TRAFFIC = {
-    # k_backward_seg_queue<3>, dram__bytes_read.sum + dram__bytes_write.sum of one launch
-    # (masked_step_300k_640x480_launches.md, masked_step_1M_640x480_launches.md)
-    ("target", "backward", 8, 8, 32, 1): 10_586_112,
-    ("target", "forward", 8, 8, 32, 1): 7_217_152,  # k_forward_queue<3, 32> (compositing_fwd_bwd_300k_640x480_ncu.md)
-    ("masked-step", "backward", 8, 8, 32, 1): 20_423_168,
+    # dram__bytes_read.sum + dram__bytes_write.sum of one launch (masked_step_300k_640x480_launches.md,
+    # masked_step_1M_640x480_launches.md, compositing_fwd_bwd_300k_640x480_ncu.md)
+    ("target", "backward", 8, 8, 32, 1): 10_595_328,  # k_backward_seg_queue<3>
+    ("target", "forward", 8, 8, 32, 1): 7_216_896,  # k_forward_queue<3, 32>
+    ("masked-step", "backward", 8, 8, 32, 1): 20_412_672,  # k_backward_seg_queue<3>
 }
 
 
