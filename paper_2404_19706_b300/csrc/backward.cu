@@ -185,13 +185,12 @@ __device__ __forceinline__ void bwd_pixel_prologue(const Work &w, const Prm &prm
 }
 
 // The depth gradient of a group's pixels to their hit Gaussians' plane records or centre
-// depths (Eq. 4/5; the depth depends on f only through the choice of the hit), one atomic
-// group per distinct Gaussian.  Called by the whole warp after its list walk, so the walk's
-// first loads are not queued behind this one's.
+// depths (Eq. 4/5; the depth depends on f only through the choice of the hit), added by
+// each pixel's lane.  Called by the whole warp after its list walk, so the walk's first
+// loads are not queued behind this one's.
 template <int C>
 __device__ __forceinline__ void bwd_depth_grad(const Work &w, const Prm &prm, int64_t N, const BwdPixel<C> &o) {
   constexpr int G2 = (C <= 5) ? 16 : 20;
-  const int lane = threadIdx.x & 31;
   const int f = o.f, hit = o.hit;
   const bool has = o.has;
   const float fpx = o.fpx, fpy = o.fpy, dLdD = o.dLdD;
@@ -222,23 +221,19 @@ __device__ __forceinline__ void bwd_depth_grad(const Work &w, const Prm &prm, in
         }
       }
     }
-    // aggregate lanes that share a hit Gaussian, one atomic group per distinct Gaussian
-    unsigned pending = __ballot_sync(0xffffffffu, key >= 0);
-    while (pending) {
-      const int leader = __ffs(pending) - 1;
-      const int k = __shfl_sync(0xffffffffu, key, leader);
-      const bool in = key == k;
-      const float a0 = warp_sum(in ? gd0 : 0.f), a1 = warp_sum(in ? gn0 : 0.f), a2 = warp_sum(in ? gn1 : 0.f),
-                  a3 = warp_sum(in ? gn2 : 0.f), a4 = warp_sum(in ? gz : 0.f);
-      if (lane == leader) {
-        float *row = g2base + (int64_t)k * G2;
-        atomicAdd(row + g2_d0(C), a0);
-        atomicAdd(row + g2_nc(C) + 0, a1);
-        atomicAdd(row + g2_nc(C) + 1, a2);
-        atomicAdd(row + g2_nc(C) + 2, a3);
-        atomicAdd(row + g2_z(C), a4);
+    // each lane adds its own terms (fire-and-forget atomics, no return awaited): a group's
+    // pixels mostly hit many distinct Gaussians, and aggregating lanes per Gaussian first
+    // (five warp sums per distinct one) cost more than it saved
+    if (key >= 0) {
+      float *row = g2base + (int64_t)key * G2;
+      if (gz != 0.f) {
+        atomicAdd(row + g2_z(C), gz);
+      } else {
+        atomicAdd(row + g2_d0(C), gd0);
+        atomicAdd(row + g2_nc(C) + 0, gn0);
+        atomicAdd(row + g2_nc(C) + 1, gn1);
+        atomicAdd(row + g2_nc(C) + 2, gn2);
       }
-      pending &= ~__ballot_sync(0xffffffffu, in);
     }
   }
 }

