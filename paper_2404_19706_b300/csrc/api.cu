@@ -136,7 +136,7 @@ struct Layout {
   size_t cams, counters, rank, ids, block_cnt, cand, rec_hot, rec_cold, rec_box, ntiles, tile_npix, tile_count, tile_offset,
       tile_cursor, keys, keys_alt, stage, sorted, px_T, px_last, px_hit, grad2d, loss_part, loss_scal, loss_done, tile_loss,
       px_list, items, scand, win_scount, win_soff, win_skeys, scan_part, scan_hist, sel_keys, sel_small, sel_state,
-      sel_tie, gauss_bits, loss_acc, ckpt, bseg, total;
+      sel_tie, gauss_bits, loss_acc, ckpt, bseg, gstate, gsign, total;
 };
 
 bool capacity_ok(const rtg_capacity *c) {
@@ -211,6 +211,8 @@ Layout layout_of(const rtg_capacity *c) {
   L.loss_acc = take(4 * 8);
   L.ckpt = take((size_t)kSegMax * P * (size_t)ck4_of(c->max_channels) * 16);
   L.bseg = take((size_t)kSegBins * groups * kSegMax * 4);
+  L.gstate = take(groups * 32 * 16);
+  L.gsign = take(groups * 32 * 4);
   L.total = o;
   return L;
 }
@@ -489,6 +491,8 @@ rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap) {
   w.status = status_dev;
   w.ckpt = (float4 *)(b + L.ckpt);
   w.bseg = (uint32_t *)(b + L.bseg);
+  w.gstate = (uint4 *)(b + L.gstate);
+  w.gsign = (uint32_t *)(b + L.gsign);
   w.px_cap = (int64_t)ctx->cap.max_frames * ctx->cap.max_width * ctx->cap.max_height;
   {
     const size_t padded = (size_t)ctx->cap.max_frames * (size_t)(ctx->cap.max_width + 31) *

@@ -121,16 +121,61 @@ struct BwdPixel {
   float dLdD;  // the loss gradient of its depth
 };
 
+// With `state` (the composited-lane backward of a fused-loss forward) the lane's pixel, T,
+// last entry, hit and L1 signs come from the forward's group state in one load; otherwise
+// from the tile's pixel list and the per-pixel arrays.
 template <int C>
 __device__ __forceinline__ void bwd_pixel_prologue(const Work &w, const Prm &prm, int64_t N, int T, int tile, int grp,
                                                    const float *__restrict__ dL_dcolor,
                                                    const float *__restrict__ dL_ddepth, const L1Fused &l1,
-                                                   float2 *s_px, float (*s_dc)[32], BwdPixel<C> &o) {
+                                                   float2 *s_px, float (*s_dc)[32], BwdPixel<C> &o,
+                                                   bool state = false) {
   constexpr int G2 = (C <= 5) ? 16 : 20;
   const int lane = threadIdx.x & 31;
   const int f = tile / T, lt = tile - f * T;
   const DevCam &cam = w.cams[f];
   const int tws = cam.tws, ths = cam.ths;
+  float T_ = 1.f, dLdD = 0.f;
+  uint32_t last = 0;
+  int hit = -1;
+#pragma unroll
+  for (int c = 0; c < C; ++c) o.dC[c] = 0.f;
+  if (state) {
+    const int64_t gslot = (((int64_t)tile << (tws + ths - 5)) + grp) * 32 + lane;
+    const uint4 st = w.gstate[gslot];
+    const uint32_t sg = w.gsign[gslot];
+    const bool has = st.x != 0xffffffffu;
+    const int px = has ? (int)(st.x & 0xffffu) : 0, py = has ? (int)(st.x >> 16) : 0;
+    if (has) {
+      T_ = __uint_as_float(st.y);
+      last = st.z;
+      hit = (int)st.w;
+      const float sc = w.loss_scal[4], sd = w.loss_scal[5];
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const uint32_t code = (sg >> (2 * c)) & 3u;
+        o.dC[c] = code == 1u ? sc : (code == 2u ? -sc : 0.f);
+      }
+      const uint32_t code = (sg >> (2 * C)) & 3u;
+      dLdD = code == 1u ? sd : (code == 2u ? -sd : 0.f);
+    }
+    s_px[lane] = make_float2((float)px, (float)py);
+#pragma unroll
+    for (int c = 0; c < C; ++c) s_dc[c][lane] = o.dC[c];
+    o.has = has;
+    o.f = f;
+    o.px = px;
+    o.py = py;
+    o.fpx = (float)px;
+    o.fpy = (float)py;
+    o.off = w.tile_offset[tile];
+    o.last = last;
+    o.T_ = T_;
+    o.g2base = w.grad2d + (int64_t)f * N * G2;
+    o.hit = hit;
+    o.dLdD = dLdD;
+    return;
+  }
   const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
   const int q = grp * 32 + lane;
   const bool has = q < (int)w.tile_npix[tile];
@@ -139,11 +184,6 @@ __device__ __forceinline__ void bwd_pixel_prologue(const Work &w, const Prm &prm
   const float fpx = (float)px, fpy = (float)py;
   const int64_t HW = (int64_t)cam.H * cam.W;
   const int64_t pix = (int64_t)f * HW + (int64_t)py * cam.W + px;
-  float T_ = 1.f, dLdD = 0.f;
-  uint32_t last = 0;
-  int hit = -1;
-#pragma unroll
-  for (int c = 0; c < C; ++c) o.dC[c] = 0.f;
   if (has) {
     T_ = w.px_T[pix];
     last = w.px_last[pix];
@@ -444,7 +484,7 @@ __device__ __forceinline__ void backward_group_fl(const Work &w, const Prm &prm,
   constexpr int NV = 6 + C, G2 = (C <= 5) ? 16 : 20;
   const int lane = threadIdx.x & 31;
   BwdPixel<C> pxs;
-  bwd_pixel_prologue<C>(w, prm, N, T, tile, grp, dL_dcolor, dL_ddepth, l1, sm.px, sm.dc, pxs);
+  bwd_pixel_prologue<C>(w, prm, N, T, tile, grp, dL_dcolor, dL_ddepth, l1, sm.px, sm.dc, pxs, l1.tcolor != nullptr);
   const float fpx = pxs.fpx, fpy = pxs.fpy;
   const uint32_t off = pxs.off;
   const int f = pxs.f;

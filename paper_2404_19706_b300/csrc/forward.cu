@@ -249,6 +249,7 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
     emit_segment(cur_seg);
   }
   float lc = 0.f, ld = 0.f, nd = 0.f;
+  uint32_t signs = 0u;  // the L1 signs for the backward: 2 bits a channel, then depth (1: +, 2: -)
   if (has) {
     const int64_t HW = (int64_t)cam.H * cam.W;
 #pragma unroll
@@ -270,14 +271,25 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
     w.px_hit[pix] = hit_gid;
     if (out.tcolor != nullptr) {  // fused L1 terms of this pixel (Eq. 7)
 #pragma unroll
-      for (int c = 0; c < C; ++c)
-        lc += fabsf(acc[c] - out.tcolor[((int64_t)f * C + c) * HW + (int64_t)py * cam.W + px]);
+      for (int c = 0; c < C; ++c) {
+        const float d = acc[c] - out.tcolor[((int64_t)f * C + c) * HW + (int64_t)py * cam.W + px];
+        lc += fabsf(d);
+        signs |= (d > 0.f ? 1u : (d < 0.f ? 2u : 0u)) << (2 * c);
+      }
       const float td = out.tdepth[pix];
       if (D != -1.f && td > 0.f) {
-        ld = fabsf(D - td);
+        const float d = D - td;
+        ld = fabsf(d);
         nd = 1.f;
+        signs |= (d > 0.f ? 1u : (d < 0.f ? 2u : 0u)) << (2 * C);
       }
     }
+  }
+  if (out.tcolor != nullptr && out.fmask != nullptr) {  // the group's pixel state for the backward
+    const int64_t gslot = (((int64_t)tile << (tws + ths - 5)) + grp) * 32 + lane;
+    w.gstate[gslot] = has ? make_uint4((uint32_t)px | ((uint32_t)py << 16), __float_as_uint(T_), last, (uint32_t)hit_gid)
+                          : make_uint4(0xffffffffu, 0u, 0u, 0xffffffffu);
+    w.gsign[gslot] = signs;
   }
   if (out.tcolor != nullptr) {  // fixed-order per-group partials, summed by k_loss_finalize
     for (int o = 16; o > 0; o >>= 1) {

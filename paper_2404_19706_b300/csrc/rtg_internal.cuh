@@ -148,6 +148,9 @@ struct Work {
   float4 *ckpt;         // [kSegMax][px_cap][ck4]: (T, colour in front) at entry boundaries
                         // kSeg, 2 kSeg, ..., then the pixel's final (T, colour) at index kSegMax - 1
   uint32_t *bseg;       // [kSegBins][bseg_cap] queued backward segments: tile << 6 | segment << 3 | group
+  uint4 *gstate;        // [groups][32] a fused-loss forward's pixel state for the backward:
+                        // (px | py << 16, or ~0 without a pixel; T bits; last; hit)
+  uint32_t *gsign;      // [groups][32] its L1 signs, 2 bits a channel then depth (1: +, 2: -)
   int64_t px_cap;       // pixels of the capacity (frames x width x height)
   int64_t bseg_cap;     // entries per segment bin
 };
