@@ -67,10 +67,12 @@ def test_one_rank_equals_masked_step():
     sh.step()
     torch.cuda.synchronize()
     assert m.get_status(ctx) == 0
+    # the same kernels on the same inputs, but the gradient rows are float32 atomic sums whose
+    # order changes from run to run, so two runs agree to that rounding only
     for a, b in zip(sh.grads, ref["grads"]):
-        group_close(a, b, rel=1e-6)
+        group_close(a, b)
     for a, b in zip(sh.params, ref["params"]):
-        group_close(a, b, rel=1e-6)
+        group_close(a, b, rel=1e-5)
     np.testing.assert_allclose(sh.loss.cpu().numpy(), ref["loss"].cpu().numpy(), rtol=1e-6)
     ctx.close()
 
