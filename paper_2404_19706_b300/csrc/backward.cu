@@ -23,11 +23,6 @@
 
 namespace rtg {
 
-__device__ __forceinline__ float warp_sum(float v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 // Per-warp shared memory of the backward compositing.  The replay runs with one pixel a lane
 // (the transmission and the colour behind a fragment are per-pixel recurrences), but the
 // gradient rows are sums over pixels for one record: so the replay leaves, for each unstable

@@ -343,6 +343,7 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
     uint32_t e = 0;
     int f = 0, tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
     int64_t i = 0;
+    int rkk = -1;  // the compact unstable row, known when walking the unstable list (rank[ids[j]] = j)
     bool ok = false;
     Projected o;
     GParams P;
@@ -350,15 +351,17 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
     if (k < ncand) {
       if (ids != nullptr) {
         f = (int)(k / nids);
-        i = (int64_t)ids[k - (int64_t)f * nids];
+        rkk = (int)(k - (int64_t)f * nids);
+        i = (int64_t)ids[rkk];
         e = (uint32_t)((int64_t)f * N + i);
       } else {
         e = w.cand[k];
         f = (int)(e / (uint64_t)N);
         i = (int64_t)e - (int64_t)f * N;
+        rkk = w.rank[i];
       }
-      ok = load_params(g, w.rank, i, P);
-      const float *cp = color_ptr(g, w.rank, i);
+      ok = load_params_r(g, i, rkk, P);
+      const float *cp = color_ptr_r(g, i, rkk);
       if (C == 3 && g.sh_degree > 0) {  // the colour seen from this frame's camera
         float c3[3];
         sh_color(g.sh_degree, cp, P.p, w.cams[f].t, c3);
@@ -405,7 +408,7 @@ __global__ void __launch_bounds__(256) k_project(GaussPtrs g, Work w, Prm prm, i
                       kMode == kProjForward ? w.counters + kVisible : nullptr, visible ? 1u : 0u),
         0);
     if (ok && (visible || kMode == kProjFused || kMode == kProjWindow)) {
-      const int rk = w.rank[i];
+      const int rk = rkk;
       float4 *hot = w.rec_hot + ((int64_t)f * N + i) * H4;
       hot[0] = make_float4(o.mux.hi, o.muy.hi, o.mux.lo, o.muy.lo);
       hot[1] = make_float4(o.u11, o.u12, o.u22, P.alpha);

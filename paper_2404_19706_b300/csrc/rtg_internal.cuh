@@ -243,10 +243,11 @@ struct GParams {
   float p[3], s[3], q[4], alpha;
 };
 
-__device__ __forceinline__ bool load_params(const GaussPtrs &g, const int32_t *rank, int64_t i, GParams &P) {
+// Gaussian i's parameters; with the optimiser's compact arrays (u_*), an unstable one's come
+// from its row r = rank[i] (load_params_r: r given, -1 for a stable Gaussian).
+__device__ __forceinline__ bool load_params_r(const GaussPtrs &g, int64_t i, int r, GParams &P) {
   const float *pm = g.means + 3 * i, *ps = g.scales + 3 * i, *pq = g.quats + 4 * i, *po = g.opacity + i;
   if (g.u_means != nullptr) {
-    int r = rank[i];
     if (r >= 0) {
       pm = g.u_means + 3 * (int64_t)r;
       ps = g.u_scales + 3 * (int64_t)r;
@@ -265,12 +266,17 @@ __device__ __forceinline__ bool load_params(const GaussPtrs &g, const int32_t *r
   return ok && qq > 0.f;
 }
 
-__device__ __forceinline__ const float *color_ptr(const GaussPtrs &g, const int32_t *rank, int64_t i) {
-  if (g.u_colors != nullptr) {
-    int r = rank[i];
-    if (r >= 0) return g.u_colors + (int64_t)g.col_stride * r;
-  }
+__device__ __forceinline__ bool load_params(const GaussPtrs &g, const int32_t *rank, int64_t i, GParams &P) {
+  return load_params_r(g, i, g.u_means != nullptr ? rank[i] : -1, P);
+}
+
+__device__ __forceinline__ const float *color_ptr_r(const GaussPtrs &g, int64_t i, int r) {
+  if (g.u_colors != nullptr && r >= 0) return g.u_colors + (int64_t)g.col_stride * r;
   return g.colors + (int64_t)g.col_stride * i;
+}
+
+__device__ __forceinline__ const float *color_ptr(const GaussPtrs &g, const int32_t *rank, int64_t i) {
+  return color_ptr_r(g, i, g.u_colors != nullptr ? rank[i] : -1);
 }
 
 }  // namespace rtg
