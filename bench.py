@@ -446,9 +446,9 @@ def step_sum(alg, per_launch, extra=()):
 NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch (masked_step_300k_640x480_launches.md,
     # masked_step_1M_640x480_launches.md, compositing_fwd_bwd_300k_640x480_ncu.md)
-    ("target", "backward", 8, 8, 32, 1): 10_595_328,  # k_backward_seg_queue<3>
-    ("target", "forward", 8, 8, 32, 1): 7_216_896,  # k_forward_queue<3, 32>
-    ("masked-step", "backward", 8, 8, 32, 1): 20_412_672,  # k_backward_seg_queue<3>
+    ("target", "backward", 8, 8, 32, 1): 8_345_856,  # k_backward_seg_queue<3>
+    ("target", "forward", 8, 8, 32, 1): 7_218_944,  # k_forward_queue<3, 32>
+    ("masked-step", "backward", 8, 8, 32, 1): 17_901_824,  # k_backward_seg_queue<3>
 }
 
 
