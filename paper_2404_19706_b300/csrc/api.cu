@@ -133,7 +133,7 @@ rtg_status check_launch(rtg_ctx *ctx, const char *what) {
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t cams, counters, rank, ids, block_cnt, cand, rec_hot, rec_cold, rec_box, ntiles, tile_npix, tile_count, tile_offset,
+  size_t cams, counters, rank, ids, block_cnt, cand, rec_hot, rec_cold, rec_box, ntiles, tile_npix, tile_count, tile_offset, tile_order,
       tile_cursor, keys, keys_alt, stage, sorted, px_T, px_last, px_hit, grad2d, loss_part, loss_scal, loss_done, tile_loss,
       px_list, items, scand, win_scount, win_soff, win_skeys, scan_part, scan_hist, sel_keys, sel_small, sel_state,
       sel_tie, gauss_bits, loss_acc, ckpt, bseg, gstate, gsign, total;
@@ -180,6 +180,7 @@ Layout layout_of(const rtg_capacity *c) {
   L.tile_npix = take((FT + 1) * 4);
   L.tile_count = take((FT + 1) * 4);
   L.tile_offset = take((FT + 1) * 4);
+  L.tile_order = take((FT + 1) * 4);
   L.tile_cursor = take((FT + 1) * 4);
   L.keys = take(K * 8);
   L.keys_alt = take(K * 8);
@@ -393,7 +394,7 @@ rtg_status build_window_lists(rtg_ctx *ctx) {
   launch_bin(w, gp.n, T, ctx->cap.max_pairs, false, true, s);
   launch_scan_tiles(w, FT, ctx->cap.max_pairs, -1, nullptr, s, true);
   launch_sort_tiles(w, FT, tn.sort_bits, tn.sort_rank_max, StableLists{nullptr, nullptr, nullptr}, ctx->win_skeys,
-                    tn.tws + tn.ths <= 6, s);
+                    tn.tws + tn.ths <= 6, nullptr, s);
   cudaMemcpyAsync(ctx->win_scount, w.tile_count, (size_t)FT * 4, cudaMemcpyDeviceToDevice, s);
   cudaMemcpyAsync(ctx->win_soff, w.tile_offset, (size_t)FT * 4, cudaMemcpyDeviceToDevice, s);
   if ((st = check_launch(ctx, "window lists")) != RTG_OK) return st;
@@ -466,6 +467,7 @@ rtg_status rtg_create(rtg_ctx **out, const rtg_capacity *cap) {
   w.tile_npix = (uint32_t *)(b + L.tile_npix);
   w.tile_count = (uint32_t *)(b + L.tile_count);
   w.tile_offset = (uint32_t *)(b + L.tile_offset);
+  w.tile_order = (uint32_t *)(b + L.tile_order);
   w.tile_cursor = (uint32_t *)(b + L.tile_cursor);
   w.keys = (unsigned long long *)(b + L.keys);
   w.keys_alt = (unsigned long long *)(b + L.keys_alt);
@@ -709,7 +711,9 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
   }
   {
     ProfScope ps(ctx, kPSortTiles, s);
-    launch_sort_tiles(w, FT, tn.sort_bits, tn.sort_rank_max, sl, nullptr, tn.tws + tn.ths <= 6, s);
+    // the persistent schedule's single-CTA scan also lists the tiles with keys, longest first
+    launch_sort_tiles(w, FT, tn.sort_bits, tn.sort_rank_max, sl, nullptr, tn.tws + tn.ths <= 6,
+                      tn.schedule == 1 && FT <= kScanSingleMax ? w.tile_order : nullptr, s);
   }
   {
     ProfScope ps(ctx, kPForward, s);

@@ -628,21 +628,29 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Work w, int FT, int64_t max
   if (kEmit) {
     __syncthreads();
     if (s_total <= (unsigned long long)max_pairs && s_total <= 0xffffffffull) {
-      const int64_t npairs = (int64_t)w.counters[kStaged];
-      for (int64_t k = (int64_t)blockIdx.x * blockDim.x + tid; k < npairs; k += (int64_t)gridDim.x * blockDim.x) {
-        const uint4 st = w.stage[k];
-        w.keys[(int64_t)s_off[st.x] + st.y] = ((unsigned long long)st.w << 32) | (unsigned long long)st.z;
+      // with a queue to lay out, the lead CTA (whose queue ends the kernel) leaves the
+      // scatter to the others
+      const bool aside = gshift >= 0 && gridDim.x > 1;
+      if (!(aside && lead)) {
+        const int64_t nb = aside ? gridDim.x - 1 : gridDim.x, bi = aside ? blockIdx.x - 1 : blockIdx.x;
+        const int64_t npairs = (int64_t)w.counters[kStaged];
+        for (int64_t k = bi * blockDim.x + tid; k < npairs; k += nb * blockDim.x) {
+          const uint4 st = w.stage[k];
+          w.keys[(int64_t)s_off[st.x] + st.y] = ((unsigned long long)st.w << 32) | (unsigned long long)st.z;
+        }
       }
     }
   }
   if (gshift < 0 || !lead) return;
-  // ---- item queue
-  __shared__ uint32_t s_cls[kQueueClasses];
-  for (int k = tid; k < kQueueClasses; k += 1024) s_cls[k] = 0u;
+  // ---- item queue, and the sort's tile order (the tiles with keys, by the same classes)
+  __shared__ uint32_t s_cls[kQueueClasses], s_tcls[kQueueClasses];
+  for (int k = tid; k < kQueueClasses; k += 1024) s_cls[k] = s_tcls[k] = 0u;
   __syncthreads();
 #pragma unroll
-  for (int u = 0; u < kScanPer; ++u)
+  for (int u = 0; u < kScanPer; ++u) {
     if (npx[u] != 0u) atomicAdd(&s_cls[queue_class(len[u])], (npx[u] + 31u) >> 5);
+    if (len[u] != 0u) atomicAdd(&s_tcls[queue_class(len[u])], 1u);
+  }
   __syncthreads();
   if (wid == 0) {  // start of each class, classes in decreasing cost
     const uint32_t r = class_starts(s_cls, lane);
@@ -652,10 +660,14 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Work w, int FT, int64_t max
       w.counters[kQBwd] = 0ull;
       for (int b = 0; b < kSegBins; ++b) w.counters[kBSeg0 + b * kCounterStride] = 0ull;
     }
+  } else if (wid == 1) {
+    const uint32_t r = class_starts(s_tcls, lane);
+    if (lane == 0) w.counters[kSortTiles] = r;
   }
   __syncthreads();
 #pragma unroll
   for (int u = 0; u < kScanPer; ++u) {
+    if (len[u] != 0u) w.tile_order[atomicAdd(&s_tcls[queue_class(len[u])], 1u)] = (uint32_t)(b + u);
     if (npx[u] == 0u) continue;
     const uint32_t ng = (npx[u] + 31u) >> 5;
     const uint32_t pos = atomicAdd(&s_cls[queue_class(len[u])], ng);

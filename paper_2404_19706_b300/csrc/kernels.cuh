@@ -221,8 +221,10 @@ struct StableLists {
 };
 // keys_out != nullptr: write each tile's sorted keys there instead of the index lists.
 // small: the tiles have at most 64 pixels (short lists; a variant with smaller buffers).
+// order (or nullptr): CTA b sorts tile order[b] for b < counters[kSortTiles] (the tiles
+// with keys, listed by the single-CTA scan with a persistent queue); the others return
 void launch_sort_tiles(const Work &w, int FT, int bits, int rank_max, const StableLists &sl,
-                       unsigned long long *keys_out, bool small, cudaStream_t s);
+                       unsigned long long *keys_out, bool small, const uint32_t *order, cudaStream_t s);
 void init_sort_attributes();
 // frame.cu
 void launch_decode_rgbd(int F, int H, int W, const uint8_t *rgb, const uint16_t *depth, float depth_scale,

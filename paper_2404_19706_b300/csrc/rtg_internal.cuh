@@ -61,8 +61,9 @@ enum Counter {
   kDepthPix = 14 * kCounterStride,    // pixels in the last fused L1 loss's depth term (D_hat != -1, D > 0)
   kWinStable = 15 * kCounterStride,   // projected (frame, stable Gaussian) entries of the open window (kept)
   kBSeg0 = 16 * kCounterStride,       // backward segments queued in cost bins 0..kSegBins-1 (one slot each)
+  kSortTiles = 20 * kCounterStride,   // tiles with keys, listed in tile_order for the sort
 };
-constexpr int kNumCounterSlots = 20;  // slots; all but kWinStable are cleared at the start of every call
+constexpr int kNumCounterSlots = 21;  // slots; all but kWinStable are cleared at the start of every call
 constexpr int kNumCounters = kNumCounterSlots * kCounterStride;  // array length
 
 struct DevCam {
@@ -131,6 +132,7 @@ struct Work {
   uint4 *stage;         // [pairs] (global tile, slot in its bucket, key lo, key hi)
   uint8_t *px_list;     // [F*T << (tws + ths)] masked pixels of each render tile
   uint32_t *items;      // [groups] work items of the persistent schedule
+  uint32_t *tile_order; // [F*T] the tiles with keys, longest list first (the sort's CTA order)
   unsigned long long *scan_part;  // [scan blocks][4] partials of the multi-block tile scan
   uint32_t *scan_hist;            // [scan blocks][queue classes] per-block class counts, then starts
   uint32_t *sorted;

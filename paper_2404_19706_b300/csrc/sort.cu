@@ -166,14 +166,20 @@ __device__ __forceinline__ void put(const Work &w, unsigned long long *keys_out,
 // its own list plus the number of smaller keys in the other (all keys are distinct).
 template <int kBits, int kCap>
 __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(Work w, int rank_max, StableLists sl,
-                                                             unsigned long long *keys_out) {
+                                                             unsigned long long *keys_out,
+                                                             const uint32_t *__restrict__ order) {
   grid_dep_wait();
   constexpr int kRadix = 1 << kBits;
   constexpr unsigned long long kMask = (unsigned long long)(kRadix - 1);
   if (w.counters[kSkip] != 0ull) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SortSmem<kCap> &s = *reinterpret_cast<SortSmem<kCap> *>(smem_raw);
-  const int tile = blockIdx.x;
+  int tile = blockIdx.x;
+  if (order != nullptr) {  // the tiles with keys, longest first: the heavy sorts start in the first wave
+    const uint32_t listed = (uint32_t)w.counters[kSortTiles], t = order[blockIdx.x];
+    if (blockIdx.x >= listed) return;
+    tile = (int)t;
+  }
   const uint32_t off = w.tile_offset[tile];
   const uint32_t n = w.tile_offset[tile + 1] - off;
   if (n == 0) return;
@@ -270,21 +276,23 @@ void init_sort_attributes() {
 }
 
 void launch_sort_tiles(const Work &w, int FT, int bits, int rank_max, const StableLists &sl,
-                       unsigned long long *keys_out, bool small, cudaStream_t s) {
+                       unsigned long long *keys_out, bool small, const uint32_t *order, cudaStream_t s) {
   // Tiles of at most 64 pixels have short lists: the variant whose buffers hold kSortCapSmall
   // keys fits twice as many CTAs on an SM (longer buckets take the chunked global-memory
   // path, longer stable lists are searched in place).
   if (small) {
     if (bits == 4)
       launch(k_sort_tiles<4, kSortCapSmall>, FT, kSortThreads, sizeof(SortSmem<kSortCapSmall>), s, w, rank_max, sl,
-             keys_out);
+             keys_out, order);
     else
       launch(k_sort_tiles<8, kSortCapSmall>, FT, kSortThreads, sizeof(SortSmem<kSortCapSmall>), s, w, rank_max, sl,
-             keys_out);
+             keys_out, order);
   } else if (bits == 4) {
-    launch(k_sort_tiles<4, kSortCap>, FT, kSortThreads, sizeof(SortSmem<kSortCap>), s, w, rank_max, sl, keys_out);
+    launch(k_sort_tiles<4, kSortCap>, FT, kSortThreads, sizeof(SortSmem<kSortCap>), s, w, rank_max, sl, keys_out,
+           order);
   } else {
-    launch(k_sort_tiles<8, kSortCap>, FT, kSortThreads, sizeof(SortSmem<kSortCap>), s, w, rank_max, sl, keys_out);
+    launch(k_sort_tiles<8, kSortCap>, FT, kSortThreads, sizeof(SortSmem<kSortCap>), s, w, rank_max, sl, keys_out,
+           order);
   }
 }
 
