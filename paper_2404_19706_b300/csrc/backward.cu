@@ -1025,13 +1025,21 @@ __global__ void __launch_bounds__(256) k_project_backward(GaussPtrs g, Work w, P
                                                           float *__restrict__ g_means, float *__restrict__ g_scales,
                                                           float *__restrict__ g_quats, float *__restrict__ g_opacity,
                                                           float *__restrict__ g_colors, int accumulate) {
-  grid_dep_wait();
+  // The light pass reads only the unstable list and the projection's visibility flags and
+  // writes only gradient rows, none of which the compositing backward in front of this
+  // kernel touches, so a CTA runs it before waiting on that kernel (its CTAs get an SM as
+  // the backward's retire); the chain rule, which reads the 2D rows, comes after the wait.
   __shared__ int s_k[256 * kPbRounds], s_i[256 * kPbRounds];
   __shared__ int s_n;
   const int64_t nu = (int64_t)w.counters[kNumUnstable];
   const int64_t N = g.n;
   const bool sh = C == 3 && g.sh_degree > 0;  // k_sh_backward writes the colour rows
-  if (blockIdx.x == 0 && threadIdx.x == 0) w.counters[kQBwd] = 0ull;
+  bool waited = false;
+  auto wait_backward = [&]() {
+    grid_dep_wait();
+    waited = true;
+    if (blockIdx.x == 0 && threadIdx.x == 0) w.counters[kQBwd] = 0ull;
+  };
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   // the grid-stride rounds, grouped evenly: no CTA ends with a short group while others still
   // run a full one
@@ -1074,6 +1082,7 @@ __global__ void __launch_bounds__(256) k_project_backward(GaussPtrs g, Work w, P
       }
     }
     __syncthreads();
+    if (!waited) wait_backward();
     const int nv = s_n;
     if (2 * nv > (int)per * (int)blockDim.x) {
       // dense (most Gaussians seen): each thread keeps its own entries, as a plain
@@ -1090,6 +1099,7 @@ __global__ void __launch_bounds__(256) k_project_backward(GaussPtrs g, Work w, P
     }
     __syncthreads();
   }
+  if (!waited) wait_backward();  // a CTA without entries still completes only after the backward
 }
 
 // SH colour backward (Section 3.1 colour from the view direction): 4 lanes per optimised
