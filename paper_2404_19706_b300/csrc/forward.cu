@@ -34,7 +34,7 @@ struct FwdOut {
 template <int C, int B>
 __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int64_t N, int T, int tile, int grp,
                                               float4 (*s_rec)[B], uint2 *s_jg, const FwdOut &out,
-                                              double *s_loss = nullptr) {
+                                              double *s_loss = nullptr, bool *pending_wait = nullptr) {
   constexpr int H4 = (C <= 4) ? 3 : 4;
   constexpr int R = B / 32;  // records per lane per batch
   const int lane = threadIdx.x & 31;
@@ -102,6 +102,12 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
     }
     segfrag = 0u;
   };
+  // everything above reads what the kernels before the sort wrote; the sorted list is the
+  // sort's (pending_wait: this warp has not yet waited on it)
+  if (pending_wait != nullptr && *pending_wait) {
+    grid_dep_wait();
+    *pending_wait = false;
+  }
   // the records of batch b0 + B, and the indices of batch b0 + 2B, are fetched while batch
   // b0 is composited, so a batch waits on one L2 round trip rather than index -> record
   float4 r[R][H4];
@@ -341,12 +347,18 @@ __global__ void __launch_bounds__(kMaxTilePix, fwd_min_ctas<C, B>()) k_forward(W
 template <int C, int B>
 __global__ void __launch_bounds__(256, fwd_min_ctas<C, B>()) k_forward_queue(Work w, Prm prm, int64_t N, int T,
                                                                             FwdOut out, int spread) {
-  grid_dep_wait();
+  // The kernel in front is the call's tile sort, which writes only the sorted lists: a warp
+  // takes its first item and sets up its pixels (queue, pixel lists, tile offsets, records,
+  // all written earlier) before it waits on the sort, just before its first list read.
+  bool pending = true;
   constexpr int H4 = (C <= 4) ? 3 : 4;
   __shared__ float4 s_rec[8][H4][B];
   __shared__ uint2 s_jg[8][B];
   __shared__ double s_loss[3];
-  if (w.counters[kSkip] != 0ull) return;
+  if (w.counters[kSkip] != 0ull) {
+    grid_dep_wait();
+    return;
+  }
   if (threadIdx.x < 3) s_loss[threadIdx.x] = 0.0;
   __syncthreads();
   const uint32_t nitems = (uint32_t)w.counters[kItems];
@@ -356,11 +368,12 @@ __global__ void __launch_bounds__(256, fwd_min_ctas<C, B>()) k_forward_queue(Wor
   while (it < nitems) {
     const uint32_t item = w.items[it];
     forward_group<C, B>(w, prm, N, T, (int)(item >> 3), (int)(item & 7u), s_rec[wid], s_jg[wid], out,
-                        out.loss_out != nullptr ? s_loss : nullptr);
+                        out.loss_out != nullptr ? s_loss : nullptr, &pending);
     uint32_t nx = 0;
     if (lane == 0) nx = nwarps + (uint32_t)atomicAdd(w.counters + kQFwd, 1ull);
     it = __shfl_sync(0xffffffffu, nx, 0);
   }
+  if (pending) grid_dep_wait();  // a warp without an item still waits before the kernel completes
   if (out.loss_out != nullptr) {  // the last CTA to finish finalizes the L1 loss (Eq. 7)
     __shared__ bool s_last;
     __syncthreads();
