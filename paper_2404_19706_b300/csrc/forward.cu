@@ -258,13 +258,24 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
   uint32_t signs = 0u;  // the L1 signs for the backward: 2 bits a channel, then depth (1: +, 2: -)
   if (has) {
     const int64_t HW = (int64_t)cam.H * cam.W;
+    // the epilogue's loads (the hit's depth plane, the targets) are issued together, ahead
+    // of its stores, so they take one round trip
+    float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = c0;
+    if (hit_gid >= 0) {
+      c0 = w.rec_cold[((int64_t)f * N + hit_gid) * 2];
+      c1 = w.rec_cold[((int64_t)f * N + hit_gid) * 2 + 1];
+    }
+    float tc[C], td = 0.f;
+    if (out.tcolor != nullptr) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) tc[c] = out.tcolor[((int64_t)f * C + c) * HW + (int64_t)py * cam.W + px];
+      td = out.tdepth[pix];
+    }
 #pragma unroll
     for (int c = 0; c < C; ++c) out.color[((int64_t)f * C + c) * HW + (int64_t)py * cam.W + px] = acc[c];
     out.alpha[pix] = 1.f - T_;
     float D = -1.f;
     if (hit_gid >= 0) {
-      const float4 c0 = w.rec_cold[((int64_t)f * N + hit_gid) * 2];
-      const float4 c1 = w.rec_cold[((int64_t)f * N + hit_gid) * 2 + 1];
       const float ux = (fpx - cam.cx) / cam.fx, uy = (fpy - cam.cy) / cam.fy;
       const float den = fmaf(c0.x, ux, fmaf(c0.y, uy, c0.z));
       const float nu = sqrtf(fmaf(ux, ux, fmaf(uy, uy, 1.f)));
@@ -278,11 +289,10 @@ __device__ __forceinline__ void forward_group(const Work &w, const Prm &prm, int
     if (out.tcolor != nullptr) {  // fused L1 terms of this pixel (Eq. 7)
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        const float d = acc[c] - out.tcolor[((int64_t)f * C + c) * HW + (int64_t)py * cam.W + px];
+        const float d = acc[c] - tc[c];
         lc += fabsf(d);
         signs |= (d > 0.f ? 1u : (d < 0.f ? 2u : 0u)) << (2 * c);
       }
-      const float td = out.tdepth[pix];
       if (D != -1.f && td > 0.f) {
         const float d = D - td;
         ld = fabsf(d);
