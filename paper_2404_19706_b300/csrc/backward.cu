@@ -136,6 +136,9 @@ __device__ __forceinline__ void bwd_pixel_prologue(const Work &w, const Prm &prm
 #pragma unroll
   for (int c = 0; c < C; ++c) o.dC[c] = 0.f;
   if (state) {
+    // the tile's list offset (the unit's first list read needs it) is loaded with the group
+    // state, not after the shared-memory writes below
+    const uint32_t toff = w.tile_offset[tile];
     const int64_t gslot = (((int64_t)tile << (tws + ths - 5)) + grp) * 32 + lane;
     const uint4 st = w.gstate[gslot];
     const uint32_t sg = w.gsign[gslot];
@@ -163,7 +166,7 @@ __device__ __forceinline__ void bwd_pixel_prologue(const Work &w, const Prm &prm
     o.py = py;
     o.fpx = (float)px;
     o.fpy = (float)py;
-    o.off = w.tile_offset[tile];
+    o.off = toff;
     o.last = last;
     o.T_ = T_;
     o.g2base = w.grad2d + (int64_t)f * N * G2;
