@@ -342,20 +342,24 @@ def kernel_profile(rtg, ctx, step, steps, flush, stream):
     graph, step.graph = step.graph, None
     adam_ev = []
     lib = _lib.load()
-    orig_adam = lib.rtg_adam_step_counted
+    names = ("rtg_adam_step_counted", "rtg_adam_step_counted_after_gradients")
+    originals = {n: getattr(lib, n) for n in names}
     import torch
     pending = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
 
-    def adam_timed(*a):
-        e0, e1 = pending[len(adam_ev)] if len(adam_ev) < len(pending) else (
-            torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-        e0.record(stream)
-        st = orig_adam(*a)
-        e1.record(stream)
-        adam_ev.append((e0, e1))
-        return st
+    def timed(orig):
+        def adam_timed(*a):
+            e0, e1 = pending[len(adam_ev)] if len(adam_ev) < len(pending) else (
+                torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            e0.record(stream)
+            st = orig(*a)
+            e1.record(stream)
+            adam_ev.append((e0, e1))
+            return st
+        return adam_timed
 
-    lib.rtg_adam_step_counted = adam_timed
+    for n in names:
+        setattr(lib, n, timed(originals[n]))
     try:
         rtg.profile_enable(ctx, True)
         rtg.profile_read(ctx)
@@ -366,7 +370,8 @@ def kernel_profile(rtg, ctx, step, steps, flush, stream):
         prof = rtg.profile_read(ctx)
         rtg.profile_enable(ctx, False)
     finally:
-        lib.rtg_adam_step_counted = orig_adam
+        for n in names:
+            setattr(lib, n, originals[n])
         step.graph = graph
     prof["adam"] = (len(adam_ev), sum(a.elapsed_time(b) for a, b in adam_ev))
     return {k: (v[1] / v[0] if v[0] else 0.0) for k, v in prof.items()}
@@ -1188,7 +1193,7 @@ class PerFrameStep:
                                       self.depth, self.alpha, self.tcol[f:f + 1], self.tdep[f:f + 1], 1.0, 1.0,
                                       self.loss[f], None, stream)
             api.render_backward_l1(self.ctxs[f], *s.grads, accumulate=f > 0, stream=stream)
-        api.adam_step_counted(s.u, s.grads, s.m, s.v, s.step_counter, s.adam, stream)
+        api.adam_step_counted(s.u, s.grads, s.m, s.v, s.step_counter, s.adam, stream, after_gradients=True)
         return self.loss
 
     def step(self):

@@ -467,6 +467,18 @@ rtg_status rtg_adam_step_counted(int64_t nu, int32_t C, float *means, float *sca
                                  const float *g_opacity, const float *g_colors, float *m, float *v,
                                  int32_t *step_counter, const rtg_adam_params *hp, void *stream);
 
+/* rtg_adam_step_counted for a stream on which the kernel just in front of this call writes
+ * neither the parameters nor m, v nor the step counter (it may write the gradients: a
+ * backward, a regulariser's gradient).  Under that contract the step starts loading the
+ * parameters and moments while that kernel finishes; the results are those of
+ * rtg_adam_step_counted.  If the kernel in front does write any of them, the results are
+ * undefined: use rtg_adam_step_counted.  Arguments and errors as rtg_adam_step_counted. */
+rtg_status rtg_adam_step_counted_after_gradients(int64_t nu, int32_t C, float *means, float *scales, float *quats,
+                                                float *opacity, float *colors, const float *g_means,
+                                                const float *g_scales, const float *g_quats, const float *g_opacity,
+                                                const float *g_colors, float *m, float *v, int32_t *step_counter,
+                                                const rtg_adam_params *hp, void *stream);
+
 /* Unstable-subset helpers: ids[k] = index of the k-th unstable Gaussian (ascending),
  * *nu_out (device int64) = their count.  gather copies full rows into compact arrays;
  * scatter writes compact rows back into the full arrays. */

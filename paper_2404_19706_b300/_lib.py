@@ -127,6 +127,8 @@ SIGNATURES = [
                                                                        c_void_p]),
     ("rtg_adam_step_counted", c_int32, [c_int64, c_int32] + [c_void_p] * 13 + [POINTER(rtg_adam_params),
                                                                                 c_void_p]),
+    ("rtg_adam_step_counted_after_gradients", c_int32, [c_int64, c_int32] + [c_void_p] * 13 +
+     [POINTER(rtg_adam_params), c_void_p]),
     ("rtg_unstable_index", c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("rtg_unstable_rank", c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("rtg_unstable_index_static", c_int32, [c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),

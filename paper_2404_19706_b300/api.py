@@ -610,9 +610,12 @@ def adam_step(params: Sequence[torch.Tensor], grads: Sequence[torch.Tensor], m: 
 
 
 def adam_step_counted(params: Sequence[torch.Tensor], grads: Sequence[torch.Tensor], m: torch.Tensor,
-                      v: torch.Tensor, step_counter: torch.Tensor, hp: AdamSettings = AdamSettings(), stream=None):
+                      v: torch.Tensor, step_counter: torch.Tensor, hp: AdamSettings = AdamSettings(), stream=None,
+                      after_gradients: bool = False):
     """Adam with the step count in device memory: step_counter is int32 [2] (completed steps,
-    and scratch that the call returns to 0); the call increments [0]."""
+    and scratch that the call returns to 0); the call increments [0].  after_gradients: the
+    kernel just in front on the stream writes none of params, m, v, step_counter
+    (rtg_adam_step_counted_after_gradients: the loads start while it finishes)."""
     if step_counter.numel() < 2:
         raise ValueError("step_counter must hold 2 int32 (completed steps, scratch)")
     means, scales, quats, opacity, colors = params
@@ -620,9 +623,10 @@ def adam_step_counted(params: Sequence[torch.Tensor], grads: Sequence[torch.Tens
     C = int(colors.numel()) // max(nu, 1)
     c = hp.to_c()
     ptrs = [_ptr(t, torch.float32, "param") for t in params] + [_ptr(t, torch.float32, "grad") for t in grads]
-    st = _lib.load().rtg_adam_step_counted(nu, C, *ptrs, _ptr(m, torch.float32, "m"), _ptr(v, torch.float32, "v"),
-                                           _ptr(step_counter, torch.int32, "step_counter"), ctypes.byref(c),
-                                           _stream(stream))
+    lib = _lib.load()
+    fn = lib.rtg_adam_step_counted_after_gradients if after_gradients else lib.rtg_adam_step_counted
+    st = fn(nu, C, *ptrs, _ptr(m, torch.float32, "m"), _ptr(v, torch.float32, "v"),
+            _ptr(step_counter, torch.int32, "step_counter"), ctypes.byref(c), _stream(stream))
     _check(st, "rtg_adam_step_counted")
 
 

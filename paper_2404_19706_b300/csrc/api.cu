@@ -1186,6 +1186,21 @@ rtg_status rtg_adam_step_counted(int64_t nu, int32_t C, float *means, float *sca
   return cudaGetLastError() == cudaSuccess ? RTG_OK : RTG_ERR_CUDA;
 }
 
+rtg_status rtg_adam_step_counted_after_gradients(int64_t nu, int32_t C, float *means, float *scales, float *quats,
+                                                float *opacity, float *colors, const float *g_means,
+                                                const float *g_scales, const float *g_quats, const float *g_opacity,
+                                                const float *g_colors, float *m, float *v, int32_t *step_counter,
+                                                const rtg_adam_params *hp, void *stream) {
+  if (nu < 0 || C < 1 || C > 64 || hp == nullptr || step_counter == nullptr) return RTG_ERR_ARG;
+  if (nu == 0) return RTG_OK;
+  if (!means || !scales || !quats || !opacity || !colors || !g_means || !g_scales || !g_quats || !g_opacity ||
+      !g_colors || !m || !v)
+    return RTG_ERR_ARG;
+  launch_adam(nu, C, means, scales, quats, opacity, colors, g_means, g_scales, g_quats, g_opacity, g_colors, m, v,
+              *hp, 1.f, 1.f, step_counter, (cudaStream_t)stream, true);
+  return cudaGetLastError() == cudaSuccess ? RTG_OK : RTG_ERR_CUDA;
+}
+
 rtg_status rtg_unstable_index(rtg_ctx *ctx, int64_t n, const uint8_t *unstable, int32_t *ids, int64_t *nu_out,
                               void *stream) {
   if (ctx == nullptr) return RTG_ERR_ARG;

@@ -272,7 +272,7 @@ void launch_transparent_reg(const RegArgs &a, float *loss_out, cudaStream_t s);
 void launch_adam(int64_t nu, int C, float *means, float *scales, float *quats, float *opacity, float *colors,
                  const float *g_means, const float *g_scales, const float *g_quats, const float *g_opacity,
                  const float *g_colors, float *m, float *v, const rtg_adam_params &hp, float bc1, float bc2_sqrt,
-                 int32_t *step_dev, cudaStream_t s);
+                 int32_t *step_dev, cudaStream_t s, bool early = false);
 void launch_gather(int64_t nu, int C, const int32_t *ids, const float *means, const float *scales,
                    const float *quats, const float *opacity, const float *colors, float *um, float *us, float *uq,
                    float *uo, float *uc, cudaStream_t s);

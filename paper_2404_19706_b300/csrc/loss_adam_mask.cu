@@ -409,10 +409,15 @@ __device__ __forceinline__ void st4(float *p, int64_t e, int cnt, bool vec, cons
   if (cnt > 3) p[e + 3] = r.w;
 }
 
+// early: the kernel in front on the stream writes neither the parameters nor the moments
+// (the projection backward, which writes the gradients): a thread's first round of
+// parameter and moment loads, and the bias corrections, go out before the wait on that
+// kernel, so they overlap its tail; the gradient loads come after it.
 __global__ void __launch_bounds__(256) k_adam(AdamGroups G, float *__restrict__ m, float *__restrict__ v,
                                               rtg_adam_params hp, float bc1, float bc2_sqrt,
-                                              int32_t *__restrict__ step_dev) {
-  grid_dep_wait();
+                                              int32_t *__restrict__ step_dev, int early) {
+  bool waited = early == 0;
+  if (waited) grid_dep_wait();
   // Device step counter: step_dev[0] completed steps, step_dev[1] a ticket.  Every block
   // takes t = step_dev[0] + 1 when it starts; the last block to finish stores t, after
   // every block has read the old value.
@@ -450,10 +455,15 @@ __global__ void __launch_bounds__(256) k_adam(AdamGroups G, float *__restrict__ 
       const int k = grp[r];
       const bool vec = G.vec[k] != 0;
       x[r] = ld4(G.param[k], e[r], cnt[r], vec);
-      g[r] = ld4(G.grad[k], e[r], cnt[r], vec);
       mm[r] = ld4(m + G.begin[k], e[r], cnt[r], vec);
       vv[r] = ld4(v + G.begin[k], e[r], cnt[r], vec);
     }
+    if (!waited) {
+      grid_dep_wait();
+      waited = true;
+    }
+#pragma unroll
+    for (int r = 0; r < kAdamRounds; ++r) g[r] = ld4(G.grad[grp[r]], e[r], cnt[r], G.vec[grp[r]] != 0);
 #pragma unroll
     for (int r = 0; r < kAdamRounds; ++r) {
       if (cnt[r] == 0) continue;
@@ -482,6 +492,7 @@ __global__ void __launch_bounds__(256) k_adam(AdamGroups G, float *__restrict__ 
       st4(v + G.begin[k], e[r], cnt[r], vec, make_float4(vs[0], vs[1], vs[2], vs[3]));
     }
   }
+  if (!waited) grid_dep_wait();  // a thread without quads still completes only after the kernel in front
   if (step_dev != nullptr) {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -654,7 +665,7 @@ void launch_l1_loss(const Work &w, int F, int C, int H, int W, const float *colo
 void launch_adam(int64_t nu, int C, float *means, float *scales, float *quats, float *opacity, float *colors,
                  const float *g_means, const float *g_scales, const float *g_quats, const float *g_opacity,
                  const float *g_colors, float *m, float *v, const rtg_adam_params &hp, float bc1, float bc2_sqrt,
-                 int32_t *step_dev, cudaStream_t s) {
+                 int32_t *step_dev, cudaStream_t s, bool early) {
   if (nu <= 0) return;
   AdamGroups G;
   float *params[5] = {means, scales, quats, opacity, colors};
@@ -680,7 +691,7 @@ void launch_adam(int64_t nu, int C, float *means, float *scales, float *quats, f
   }
   const int64_t rounds = (G.quad[5] + 256 * kAdamRounds - 1) / (256 * kAdamRounds);
   const unsigned blocks = (unsigned)std::min<int64_t>(rounds, (int64_t)resident_grid((const void *)k_adam, 256));
-  launch(k_adam, blocks, 256, 0, s, G, m, v, hp, bc1, bc2_sqrt, step_dev);
+  launch(k_adam, blocks, 256, 0, s, G, m, v, hp, bc1, bc2_sqrt, step_dev, early ? 1 : 0);
 }
 
 void launch_gather(int64_t nu, int C, const int32_t *ids, const float *means, const float *scales,

@@ -170,7 +170,10 @@ class MaskedStep:
             api.confidence_update(self.ids, self.grads[4], self.map_state.eta, stream)
         if self.u0 is not None:
             api.transparent_reg(self.ctx, self.u, self.u0, self.grads, self.loss_reg, self.w_reg, stream=stream)
-        api.adam_step_counted(self.u, self.grads, self.m, self.v, self.step_counter, self.adam, stream)
+        # the kernel in front (projection backward, confidence update or regulariser) writes
+        # gradients at most, so Adam's parameter and moment loads overlap it
+        api.adam_step_counted(self.u, self.grads, self.m, self.v, self.step_counter, self.adam, stream,
+                              after_gradients=True)
         if self.scatter_every_step:
             api.scatter_unstable(self.ids, self.u, self.full, stream)
         return self.loss

@@ -172,6 +172,37 @@ def test_masked_step_graph_replay_matches_eager():
     assert graphed.step_counter.tolist() == [6, 0] and eager.step_counter.tolist() == [6, 0]
 
 
+def test_adam_after_gradients_equals_adam_step_counted():
+    """rtg_adam_step_counted_after_gradients (parameter and moment loads issued before the
+    wait on the kernel in front, which here writes the gradients) gives
+    rtg_adam_step_counted's result bit for bit, ragged group ends and several rounds of the
+    grid included."""
+    m = rtg()
+    rng = np.random.default_rng(7)
+    for nu, C in ((1, 3), (1237, 3), (333_331, 3), (50_001, 8)):
+        p = [torch.tensor(rng.normal(size=s).astype(np.float32)).cuda()
+             for s in ((nu, 3), (nu, 3), (nu, 4), (nu,), (nu, C))]
+        p[1] = p[1].abs() + 0.01
+        mm = torch.tensor(rng.normal(size=nu * (11 + C)).astype(np.float32)).cuda() * 1e-3
+        vv = torch.tensor(rng.uniform(0, 1e-4, nu * (11 + C)).astype(np.float32)).cuda()
+        grads = [torch.zeros_like(t) for t in p]
+        out = []
+        for after in (False, True):
+            q, a_m, a_v = [t.clone() for t in p], mm.clone(), vv.clone()
+            cnt = torch.tensor([4, 0], dtype=torch.int32, device="cuda")
+            for step in range(2):
+                # the kernel in front writes the gradients (a fill per group)
+                for k, g in enumerate(grads):
+                    g.copy_(torch.sin(torch.arange(g.numel(), device="cuda", dtype=torch.float32) * (k + 1 + step))
+                            .reshape(g.shape))
+                m.adam_step_counted(q, grads, a_m, a_v, cnt, after_gradients=after)
+            torch.cuda.synchronize()
+            out.append((q, a_m, a_v, cnt.tolist()))
+        for a, b in zip(out[0][0] + [out[0][1], out[0][2]], out[1][0] + [out[1][1], out[1][2]]):
+            assert torch.equal(a, b)
+        assert out[0][3] == out[1][3] == [6, 0]
+
+
 def test_masked_step_scatter_every_step_keeps_full_arrays_current():
     """The renderer reads the unstable Gaussians from the optimiser's compact arrays; with
     scatter_every_step the full arrays follow them after every step, otherwise write_back()
