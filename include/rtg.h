@@ -238,6 +238,18 @@ rtg_status rtg_render_forward_l1(rtg_ctx *ctx, const rtg_camera *cams, int32_t F
                                  const uint8_t *mask, const rtg_render_params *prm, const float *target_color,
                                  const float *target_depth, float w_color, float w_depth, float *color, float *depth,
                                  float *alpha, int32_t *index_map, float *loss_out, void *stream);
+/* rtg_decode_rgbd and rtg_render_forward_l1 in one call: the RGB-D sensor frame (rgb
+ * [F,H,W,3] 8-bit, depth16 [F,H,W] 16-bit, depth_scale units a metre; device) is decoded into
+ * target_color [F,3,H,W] and target_depth [F,H,W] exactly as rtg_decode_rgbd decodes it, and
+ * the fused-L1 forward of rtg_render_forward_l1 runs against them (H, W the cameras'). The
+ * call's tile-mask pass reads only the mask, so it runs while the decode does.  Results
+ * equal the two calls'.  Needs 3 colour channels without SH, the target planes and loss_out;
+ * a NULL frame or a depth scale that is not positive and finite: RTG_ERR_ARG. */
+rtg_status rtg_render_forward_l1_frame(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, const rtg_gaussians *g,
+                                       const uint8_t *mask, const rtg_render_params *prm, const uint8_t *rgb,
+                                       const uint16_t *depth16, float depth_scale, float *target_color,
+                                       float *target_depth, float w_color, float w_depth, float *color, float *depth,
+                                       float *alpha, int32_t *index_map, float *loss_out, void *stream);
 rtg_status rtg_render_backward_l1(rtg_ctx *ctx, float *g_means, float *g_scales, float *g_quats, float *g_opacity,
                                   float *g_colors, int32_t accumulate, void *stream);
 

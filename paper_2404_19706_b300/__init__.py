@@ -44,6 +44,7 @@ from .api import (  # noqa: E402,F401
     render_backward,
     render_backward_l1,
     render_forward_l1,
+    render_forward_l1_frame,
     render_forward_masked,
     render_forward,
     reset_status,

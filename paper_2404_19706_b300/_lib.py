@@ -123,6 +123,10 @@ SIGNATURES = [
     ("rtg_get_tuning", c_int32, [c_void_p, POINTER(rtg_tuning)]),
     ("rtg_decode_rgbd", c_int32, [c_int32, c_int32, c_int32, c_void_p, c_void_p, c_float, c_void_p, c_void_p,
                                   c_void_p]),
+    ("rtg_render_forward_l1_frame", c_int32, [c_void_p, POINTER(rtg_camera), c_int32, POINTER(rtg_gaussians), c_void_p,
+                                              POINTER(rtg_render_params), c_void_p, c_void_p, c_float, c_void_p,
+                                              c_void_p, c_float, c_float, c_void_p, c_void_p, c_void_p, c_void_p,
+                                              c_void_p, c_void_p]),
     ("rtg_adam_step", c_int32, [c_int64, c_int32] + [c_void_p] * 12 + [c_int32, POINTER(rtg_adam_params),
                                                                        c_void_p]),
     ("rtg_adam_step_counted", c_int32, [c_int64, c_int32] + [c_void_p] * 13 + [POINTER(rtg_adam_params),

@@ -333,6 +333,25 @@ def render_forward_l1(ctx: Context, cams, g: Gaussians, mask: Optional[torch.Ten
     _check(st, "rtg_render_forward_l1", ctx.ptr)
 
 
+def render_forward_l1_frame(ctx: Context, cams, g: Gaussians, mask: Optional[torch.Tensor], settings: RenderSettings,
+                            rgb: torch.Tensor, depth16: torch.Tensor, depth_scale: float, target_color, target_depth,
+                            w_color: float, w_depth: float, color, depth, alpha, loss_out,
+                            index_map: Optional[torch.Tensor] = None, stream=None):
+    """rtg_render_forward_l1_frame: decode the RGB-D sensor frame (rgb uint8 [F,H,W,3], depth16
+    uint16 [F,H,W]) into target_color / target_depth, then render_forward_l1 against them."""
+    arr, F = _cams(cams)
+    gc = g.to_c()
+    prm = settings.to_c()
+    st = _lib.load().rtg_render_forward_l1_frame(
+        ctx.ptr, arr, F, ctypes.byref(gc), _ptr(mask, torch.uint8, "mask"), ctypes.byref(prm),
+        _ptr(rgb, torch.uint8, "rgb"), _ptr(depth16, torch.uint16, "depth16"), float(depth_scale),
+        _ptr(target_color, torch.float32, "target_color"), _ptr(target_depth, torch.float32, "target_depth"),
+        float(w_color), float(w_depth), _ptr(color, torch.float32, "color"), _ptr(depth, torch.float32, "depth"),
+        _ptr(alpha, torch.float32, "alpha"), _ptr(index_map, torch.int32, "index_map"),
+        _ptr(loss_out, torch.float32, "loss_out"), _stream(stream))
+    _check(st, "rtg_render_forward_l1_frame", ctx.ptr)
+
+
 def render_forward_masked(ctx: Context, cams, g: Gaussians, settings: RenderSettings, mask_out, color, depth, alpha,
                           target_color=None, target_depth=None, w_color: float = 1.0, w_depth: float = 1.0,
                           loss_out=None, index_map: Optional[torch.Tensor] = None, stream=None):

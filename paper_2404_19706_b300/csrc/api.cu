@@ -60,13 +60,14 @@ struct rtg_ctx {
 // Kernel kinds reported by the tracing interface (one launcher each).
 enum ProfKind {
   kPTileMask, kPUnstableIndex, kPProject, kPScanTiles, kPEmit, kPSortTiles, kPForward, kPL1Loss, kPBackward,
-  kPProjectBackward, kPUnstableMask, kPBin, kPSelect, kPNarrow, kPAdd, kPErrorCount, kPCompact, kPNumKinds
+  kPProjectBackward, kPUnstableMask, kPBin, kPSelect, kPNarrow, kPAdd, kPErrorCount, kPCompact, kPDecode,
+  kPNumKinds
 };
 static const char *kProfNames[kPNumKinds] = {"tile_mask", "unstable_index", "project", "scan_tiles",
                                              "emit", "sort_tiles", "forward", "l1_loss",
                                              "backward", "project_backward", "unstable_mask", "bin",
                                              "select_top_error", "narrow_pixels", "add_candidates",
-                                             "error_count", "compact_gaussians"};
+                                             "error_count", "compact_gaussians", "decode"};
 constexpr int kProfMaxRecords = 1 << 16;
 
 struct ProfRec {
@@ -627,11 +628,18 @@ rtg_status rtg_reset_status(rtg_ctx *ctx) {
 
 }  // extern "C"
 
+// A sensor frame decoded into the targets at the start of a forward (rtg_render_forward_l1_frame).
+struct FrameIn {
+  const uint8_t *rgb;
+  const uint16_t *depth;
+  float scale;
+};
+
 static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, const rtg_gaussians *g,
                                const uint8_t *mask, uint8_t *mask_out, const rtg_render_params *prm, float *color,
                                float *depth,
                                float *alpha, int32_t *index_map, const float *tcolor, const float *tdepth, float w_c,
-                               float w_d, float *loss_out, void *stream) {
+                               float w_d, float *loss_out, void *stream, const FrameIn *frame = nullptr) {
   if (ctx == nullptr) return RTG_ERR_ARG;
   ctx->has_fwd = false;
   Prm P;
@@ -690,9 +698,15 @@ static rtg_status forward_impl(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, 
       launch_bin(w, n, T, ctx->cap.max_pairs, true, win && !lists, s);
     }
   } else {
+    if (frame != nullptr) {
+      ProfScope ps(ctx, kPDecode, s);
+      launch_decode_rgbd(F, c0.H, c0.W, frame->rgb, frame->depth, frame->scale, const_cast<float *>(tcolor),
+                         const_cast<float *>(tdepth), s);
+    }
     {
       ProfScope ps(ctx, kPTileMask, s);
-      launch_tile_mask(fs, w, mask, T, c0.tiles_x, tn.tws, tn.ths, true, true, nu_preset, s);
+      // after the call's own decode, the pass runs whole before waiting on it
+      launch_tile_mask(fs, w, mask, T, c0.tiles_x, tn.tws, tn.ths, true, true, nu_preset, s, frame != nullptr);
     }
     if (gp.rank_map == nullptr)
       if ((st = rank_pass(ctx, gp.unstable, n, w.rank, w.ids, w.counters, nullptr, s)) != RTG_OK) return st;
@@ -830,6 +844,23 @@ rtg_status rtg_render_forward_l1(rtg_ctx *ctx, const rtg_camera *cams, int32_t F
     return fail(ctx, RTG_ERR_ARG, "render_forward_l1: NULL target or loss_out");
   return forward_impl(ctx, cams, F, g, mask, nullptr, prm, color, depth, alpha, index_map, target_color,
                       target_depth, w_color, w_depth, loss_out, stream);
+}
+
+rtg_status rtg_render_forward_l1_frame(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, const rtg_gaussians *g,
+                                       const uint8_t *mask, const rtg_render_params *prm, const uint8_t *rgb,
+                                       const uint16_t *depth16, float depth_scale, float *target_color,
+                                       float *target_depth, float w_color, float w_depth, float *color, float *depth,
+                                       float *alpha, int32_t *index_map, float *loss_out, void *stream) {
+  if (ctx == nullptr) return RTG_ERR_ARG;
+  if (rgb == nullptr || depth16 == nullptr || !(depth_scale > 0.f) || !isfinite(depth_scale))
+    return fail(ctx, RTG_ERR_ARG, "render_forward_l1_frame: NULL frame or bad depth scale");
+  if (target_color == nullptr || target_depth == nullptr || loss_out == nullptr)
+    return fail(ctx, RTG_ERR_ARG, "render_forward_l1_frame: give the target planes and loss_out");
+  if (g == nullptr || g->channels != 3 || g->sh_degree != 0)
+    return fail(ctx, RTG_ERR_ARG, "render_forward_l1_frame: the sensor frame has 3 colour channels");
+  const FrameIn fr{rgb, depth16, depth_scale};
+  return forward_impl(ctx, cams, F, g, mask, nullptr, prm, color, depth, alpha, index_map, target_color, target_depth,
+                      w_color, w_depth, loss_out, stream, &fr);
 }
 
 rtg_status rtg_render_forward_masked(rtg_ctx *ctx, const rtg_camera *cams, int32_t F, const rtg_gaussians *g,

@@ -19,10 +19,14 @@ namespace rtg {
 // (raster index within the tile) compacted in the tile's Z order (tile_order_pixel): the
 // forward and backward give each 32 of them to one warp.  With `setup`, block 0 also
 // publishes the cameras and clears the per-call counters.
+// early: the kernel in front is the call's own frame decode, which reads only the sensor
+// frame and writes only the targets; this pass reads the mask and writes the tile arrays,
+// cameras and counters, so it runs whole before the wait on the decode (which it still
+// makes before completing, so that later kernels find the targets written).
 __global__ void __launch_bounds__(kMaxTilePix) k_tile_mask(FrameSet fs, Work w, const uint8_t *__restrict__ mask,
                                                            int T, int tiles_x, int tws, int ths, int setup,
-                                                           int lists, long long nu_preset) {
-  grid_dep_wait();
+                                                           int lists, long long nu_preset, int early) {
+  if (!early) grid_dep_wait();
   __shared__ int s_wcnt[kMaxTilePix / 32];
   if (setup && blockIdx.x == 0) {
     for (int i = threadIdx.x; i < fs.F; i += blockDim.x) w.cams[i] = fs.cam[i];
@@ -58,6 +62,7 @@ __global__ void __launch_bounds__(kMaxTilePix) k_tile_mask(FrameSet fs, Work w, 
     w.tile_npix[tile] = (uint32_t)total;
     w.tile_count[tile] = 0u;
   }
+  if (early) grid_dep_wait();
 }
 
 // --------------------------------------------------------------------------- unstable index
@@ -690,10 +695,10 @@ __global__ void __launch_bounds__(256) k_emit(Work w) {
 }
 
 void launch_tile_mask(const FrameSet &fs, const Work &w, const uint8_t *mask, int T, int tiles_x, int tws, int ths,
-                      bool setup, bool lists, long long nu_preset, cudaStream_t s) {
+                      bool setup, bool lists, long long nu_preset, cudaStream_t s, bool early) {
   const int per = kMaxTilePix >> (tws + ths);  // tiles per CTA
   launch(k_tile_mask, (fs.F * T + per - 1) / per, kMaxTilePix, 0, s, fs, w, mask, T, tiles_x, tws, ths, setup ? 1 : 0,
-         lists ? 1 : 0, nu_preset);
+         lists ? 1 : 0, nu_preset, early ? 1 : 0);
 }
 
 void launch_rank(const uint8_t *unstable, int64_t n, int32_t *block_cnt, int32_t *rank, int32_t *ids,

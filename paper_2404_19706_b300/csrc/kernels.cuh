@@ -188,7 +188,7 @@ __device__ __forceinline__ int tile_order_pixel(int t, int tws, int ths) {
 // with `lists`, the compacted pixel lists.  `setup`: also publish the cameras and clear
 // the per-call counters (the first kernel of every call).
 void launch_tile_mask(const FrameSet &fs, const Work &w, const uint8_t *mask, int T, int tiles_x, int tws, int ths,
-                      bool setup, bool lists, long long nu_preset, cudaStream_t s);
+                      bool setup, bool lists, long long nu_preset, cudaStream_t s, bool early = false);
 void launch_rank(const uint8_t *unstable, int64_t n, int32_t *block_cnt, int32_t *rank, int32_t *ids,
                  unsigned long long *nu_counter, int64_t *nu_out, cudaStream_t s);
 enum ProjMode { kProjForward = 0, kProjMask = 1, kProjFused = 2, kProjWindow = 3 };

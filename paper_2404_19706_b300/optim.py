@@ -153,6 +153,14 @@ class MaskedStep:
 
     def _body(self, stream=None):
         s = self.state
+        if self.frame is not None and not self.recompute_mask and self.g.sh_degree == 0 and self.g.channels == 3:
+            # the sensor frame decoded by the forward call itself (its tile-mask pass overlaps
+            # the decode), the L1 loss fused in
+            api.render_forward_l1_frame(self.ctx, self.cams, self.g, self.mask, self.settings, self.frame[0],
+                                        self.frame[1], self.frame[2], self.target_color, self.target_depth,
+                                        self.w_color, self.w_depth, s.color, s.depth, s.alpha, self.loss, None,
+                                        stream)
+            return self._backward_adam(stream)
         if self.frame is not None:
             api.decode_rgbd(self.frame[0], self.frame[1], self.frame[2], self.target_color, self.target_depth, stream)
         if self.recompute_mask:
@@ -165,6 +173,9 @@ class MaskedStep:
             api.render_forward_l1(self.ctx, self.cams, self.g, self.mask, self.settings, self.target_color,
                                   self.target_depth, self.w_color, self.w_depth, s.color, s.depth, s.alpha,
                                   self.loss, None, stream)
+        return self._backward_adam(stream)
+
+    def _backward_adam(self, stream=None):
         api.render_backward_l1(self.ctx, *self.grads, stream=stream)
         if self.map_state is not None:
             api.confidence_update(self.ids, self.grads[4], self.map_state.eta, stream)

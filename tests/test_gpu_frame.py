@@ -153,3 +153,66 @@ def test_graphs_per_frame_set_equal_eager_steps(uploads):
         np.testing.assert_allclose(b_, a_, rtol=1e-5)
     for a_, b_ in zip(runs[0][1], runs[1][1]):  # float32 atomics order the gradient sums differently
         np.testing.assert_allclose(b_, a_, rtol=1e-4, atol=1e-6)
+
+
+@pytest.mark.parametrize("tuning", [None, (8, 8, 32, 1, 2, 8, 512)])
+def test_forward_l1_frame_equals_decode_then_forward(tuning):
+    """rtg_render_forward_l1_frame (decode inside the forward call, the tile-mask pass
+    running beside it) gives the targets of rtg_decode_rgbd and the render and loss of
+    rtg_render_forward_l1 on them, bit for bit; two frames, a mask."""
+    import synth
+    m = rtg()
+    scene, layout = synth.room_scene(616, 20000)
+    cams = [c for _, c in zip(range(2), synth.room_camera_candidates(617, layout, 112, 80, 100.0))]
+    scene.unstable = synth.flag_blobs(scene, cams, 3000, 3, seed=618)
+    F, H, W = 2, 80, 112
+    rng = np.random.default_rng(619)
+    rgb = torch.from_numpy(rng.integers(0, 256, (F, H, W, 3), dtype=np.uint8)).cuda()
+    dep = torch.from_numpy(rng.integers(0, 40000, (F, H, W), dtype=np.uint16)).cuda()
+    g = m.Gaussians.from_scene(scene)
+    outs = []
+    for fused in (False, True):
+        ctx = m.Context(max_gaussians=scene.n, max_frames=F, max_width=W, max_height=H)
+        if tuning is not None:
+            ctx.set_tuning(m.Tuning(*tuning))
+        mask = torch.zeros(F, H, W, dtype=torch.uint8, device="cuda")
+        m.unstable_mask(ctx, cams, g, m.RenderSettings(), mask)
+        tc, td = torch.full((F, 3, H, W), -5.0, device="cuda"), torch.full((F, H, W), -5.0, device="cuda")
+        c, d, a = torch.zeros(F, 3, H, W, device="cuda"), torch.zeros(F, H, W, device="cuda"), torch.zeros(F, H, W,
+                                                                                                        device="cuda")
+        idx = torch.full((F, H, W), -7, dtype=torch.int32, device="cuda")
+        loss = torch.zeros(3, device="cuda")
+        if fused:
+            m.render_forward_l1_frame(ctx, cams, g, mask, m.RenderSettings(), rgb, dep, 5000.0, tc, td, 1.0, 0.5, c, d,
+                                      a, loss, idx)
+        else:
+            m.decode_rgbd(rgb, dep, 5000.0, tc, td)
+            m.render_forward_l1(ctx, cams, g, mask, m.RenderSettings(), tc, td, 1.0, 0.5, c, d, a, loss, idx)
+        torch.cuda.synchronize()
+        assert m.get_status(ctx) == 0 and int(mask.sum()) > 0
+        outs.append([mask, tc, td, c, d, a, idx, loss])
+        ctx.close()
+    for x, y in zip(*outs):
+        assert torch.equal(x, y)
+    ref_c, ref_d = host_decode(rgb.cpu().numpy(), dep.cpu().numpy(), 5000.0)
+    assert np.array_equal(outs[1][1].cpu().numpy(), ref_c) and np.array_equal(outs[1][2].cpu().numpy(), ref_d)
+
+
+def test_forward_l1_frame_rejects_bad_frames():
+    import synth
+    m = rtg()
+    cam = synth.identity_camera(32, 24, 30.0, 16.0, 12.0)
+    scene, _ = synth.room_scene(620, 500)
+    g = m.Gaussians.from_scene(scene)
+    ctx = m.Context(max_gaussians=scene.n, max_width=32, max_height=24)
+    rgb = torch.zeros(1, 24, 32, 3, dtype=torch.uint8, device="cuda")
+    dep = torch.zeros(1, 24, 32, dtype=torch.uint16, device="cuda")
+    planes = [torch.zeros(1, 3, 24, 32, device="cuda"), torch.zeros(1, 24, 32, device="cuda")]
+    outs = [torch.zeros(1, 3, 24, 32, device="cuda"), torch.zeros(1, 24, 32, device="cuda"),
+            torch.zeros(1, 24, 32, device="cuda"), torch.zeros(3, device="cuda")]
+    with pytest.raises(m.RTGError):
+        m.render_forward_l1_frame(ctx, cam, g, None, m.RenderSettings(), rgb, dep, 0.0, *planes, 1.0, 1.0, *outs)
+    with pytest.raises(m.RTGError):
+        m.render_forward_l1_frame(ctx, cam, g, None, m.RenderSettings(), rgb, dep, float("nan"), *planes, 1.0, 1.0,
+                                  *outs)
+    ctx.close()
