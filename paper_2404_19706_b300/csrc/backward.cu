@@ -787,9 +787,9 @@ __global__ void __launch_bounds__(256, 2) k_backward_fl_queue(Work w, Prm prm, i
 // Schedule 1 over the forward's queued segments: the bins in decreasing cost, each a warp's
 // (group, segment) unit.  A warp's first unit is static (warp k of CTA b takes unit
 // k * grid + b, spreading the costliest units over the SMs); later ones come from the
-// shared counter.
-template <int C>
-__global__ void __launch_bounds__(256, 2) k_backward_seg_queue(Work w, Prm prm, int64_t N, int T, BwdIn in) {
+// shared counter.  kW warps a CTA (8, or 10 for calls of many tiles, see the launcher).
+template <int C, int kW>
+__global__ void __launch_bounds__(32 * kW, 2) k_backward_seg_queue(Work w, Prm prm, int64_t N, int T, BwdIn in) {
   grid_dep_wait();
   extern __shared__ float4 bwd_dyn_smem[];
   if (w.counters[kSkip] != 0ull) return;
@@ -802,7 +802,7 @@ __global__ void __launch_bounds__(256, 2) k_backward_seg_queue(Work w, Prm prm, 
   }
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   BwdFlSmem<C> *sm = reinterpret_cast<BwdFlSmem<C> *>(bwd_dyn_smem) + wid;
-  const uint32_t nwarps = gridDim.x * 8u;
+  const uint32_t nwarps = gridDim.x * (uint32_t)kW;
   uint32_t t = (uint32_t)wid * gridDim.x + blockIdx.x;
   while (t < total) {
     uint32_t r = t;
@@ -1219,9 +1219,23 @@ __global__ void __launch_bounds__(256) k_sh_backward(GaussPtrs g, Work w, int F,
 template <int C>
 static void launch_backward_fl(const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn,
                                const BwdIn &in, cudaStream_t s) {
-  if (tn.schedule == 1 && in.segments)
-    launch(k_backward_seg_queue<C>, tn.num_sms * tn.ctas_per_sm, 256, bwd_fl_smem_bytes<C>(), s, w, prm, N, T, in);
-  else if (tn.schedule == 1)
+  if (tn.schedule == 1 && in.segments) {
+    // A call of many tiles (batched keyframes) has many short units against the warps: the
+    // kernel is bound by throughput there, and ten warps a CTA (two CTAs an SM still fit at
+    // C = 3: at most 88 registers, 221 KB of shared memory) hide more latency (config 4
+    // backward 0.750 -> 0.699 ms).  A single frame's step is bound by its longest units
+    // instead, and eight warps were as fast or faster there.
+    bool ten = false;
+    if constexpr (C == 3) ten = (int64_t)F * T > kScanSingleMax;
+    if constexpr (C == 3) {
+      if (ten) {
+        launch(k_backward_seg_queue<C, 10>, tn.num_sms * tn.ctas_per_sm, 320, 10 * sizeof(BwdFlSmem<C>), s, w, prm,
+               N, T, in);
+        return;
+      }
+    }
+    launch(k_backward_seg_queue<C, 8>, tn.num_sms * tn.ctas_per_sm, 256, bwd_fl_smem_bytes<C>(), s, w, prm, N, T, in);
+  } else if (tn.schedule == 1)
     launch(k_backward_fl_queue<C>, tn.num_sms * tn.ctas_per_sm, 256, bwd_fl_smem_bytes<C>(), s, w, prm, N, T, in,
            tn.ctas_per_sm <= 2 ? 1 : 0);
   else
@@ -1254,9 +1268,11 @@ void init_backward_attributes() {
   cudaFuncSetAttribute(k_backward_fl_queue<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)bwd_fl_smem_bytes<8>());
   cudaFuncSetAttribute(k_backward_fl<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_fl_smem_bytes<8>());
-  cudaFuncSetAttribute(k_backward_seg_queue<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_backward_seg_queue<3, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)bwd_fl_smem_bytes<3>());
-  cudaFuncSetAttribute(k_backward_seg_queue<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_backward_seg_queue<3, 10>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(10 * sizeof(BwdFlSmem<3>)));
+  cudaFuncSetAttribute(k_backward_seg_queue<8, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)bwd_fl_smem_bytes<8>());
   set_backward_attributes<3, 32>();
   set_backward_attributes<3, 64>();

@@ -248,3 +248,47 @@ def test_autotuner_picks_a_timed_candidate_and_checks_renders():
     assert len(res.table) == 1 + 40 + 5 and len(timed) == len(res.table)
     assert res.best_ms == min(r["ms"] for r in timed if r["tuning"] == res.best.as_dict())
     assert res.best_ms <= res.default_ms * 1.0001 or res.best.as_dict() == res.table[0]["tuning"]
+
+
+def test_many_tile_call_backward_matches_per_tile_schedule():
+    """A call of more than 8,192 render tiles (four 480x360 keyframes in 8x8 tiles) takes the
+    segmented backward with ten warps a CTA: its renders equal the per-tile schedule's bit
+    for bit, its gradients those of the per-tile whole-list replay to float32 rounding."""
+    m = rtg()
+    nF, hh, ww = 4, 360, 480
+    scene, layout = synth.room_scene(3500, 60000)
+    cams = [c for _, c in zip(range(nF), synth.room_camera_candidates(3501, layout, ww, hh, 360.0))]
+    scene.unstable = synth.flag_blobs(scene, cams, 12000, 4, seed=3502)
+    mask = torch.as_tensor(synth.random_masks(3503, nF, hh, ww, 0.3, 0.8)).reshape(nF, hh, ww).cuda()
+    ref = gpu_forward(synth.jitter_scene(scene, 3504), cams)
+    tc = torch.tensor(ref["color"]).cuda()
+    td = torch.tensor(np.where(ref["depth"] > 0, ref["depth"], 0)).cuda()
+    ref["ctx"].close()
+    g = m.Gaussians.from_scene(scene)
+    nu = int(scene.unstable.astype(bool).sum())
+    outs = []
+    for tune in (m.Tuning(8, 8, 32, 1, 2, 8, 512), m.Tuning(8, 8, 32, 0, 4, 8, 512)):
+        ctx = ctx_for(scene.n, cams)
+        ctx.set_tuning(tune)
+        img = [torch.zeros(nF, 3, hh, ww, device="cuda"), torch.full((nF, hh, ww), -1.0, device="cuda"),
+               torch.zeros(nF, hh, ww, device="cuda"), torch.full((nF, hh, ww), -1, dtype=torch.int32, device="cuda")]
+        loss = torch.zeros(3, device="cuda")
+        grads = [torch.zeros(nu, k, device="cuda") for k in (3, 3, 4)] + \
+                [torch.zeros(nu, device="cuda"), torch.zeros(nu, 3, device="cuda")]
+        m.render_forward_l1(ctx, cams, g, mask, m.RenderSettings(), tc, td, 1.0, 1.0, img[0], img[1], img[2], loss,
+                            img[3])
+        m.render_backward_l1(ctx, *grads)
+        torch.cuda.synchronize()
+        st = m.get_stats(ctx)
+        assert st["status"] == 0
+        outs.append((img, loss, grads, st))
+        ctx.close()
+    (ia, la, ga, sa), (ib, lb, gb, sb) = outs
+    assert sa["pairs"] > 0 and sa["fragments"] == sb["fragments"]
+    for x, y in zip(ia, ib):
+        assert torch.equal(x, y)
+    np.testing.assert_allclose(la.cpu().numpy(), lb.cpu().numpy(), rtol=1e-5)
+    for x, y in zip(ga, gb):
+        x, y = x.cpu().numpy(), y.cpu().numpy()
+        scale = max(np.abs(x).max(), np.abs(y).max())
+        assert scale > 0 and np.abs(x - y).max() <= 1e-4 * scale, (np.abs(x - y).max(), scale)
