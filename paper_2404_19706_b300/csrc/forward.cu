@@ -353,17 +353,17 @@ __global__ void __launch_bounds__(kMaxTilePix, fwd_min_ctas<C, B>()) k_forward(W
 
 // Schedule 1: persistent warps.  Each warp starts with one of the first items; later items come
 // from a shared counter, so warps that finish early take the remaining work.  The queue
-// holds the longest lists first.
-template <int C, int B>
-__global__ void __launch_bounds__(256, fwd_min_ctas<C, B>()) k_forward_queue(Work w, Prm prm, int64_t N, int T,
-                                                                            FwdOut out, int spread) {
+// holds the longest lists first.  kW warps a CTA (8, or 10 for calls of many tiles).
+template <int C, int B, int kW>
+__global__ void __launch_bounds__(32 * kW, fwd_min_ctas<C, B>()) k_forward_queue(Work w, Prm prm, int64_t N, int T,
+                                                                                 FwdOut out, int spread) {
   // The kernel in front is the call's tile sort, which writes only the sorted lists: a warp
   // takes its first item and sets up its pixels (queue, pixel lists, tile offsets, records,
   // all written earlier) before it waits on the sort, just before its first list read.
   bool pending = true;
   constexpr int H4 = (C <= 4) ? 3 : 4;
-  __shared__ float4 s_rec[8][H4][B];
-  __shared__ uint2 s_jg[8][B];
+  __shared__ float4 s_rec[kW][H4][B];
+  __shared__ uint2 s_jg[kW][B];
   __shared__ double s_loss[3];
   if (w.counters[kSkip] != 0ull) {
     grid_dep_wait();
@@ -373,8 +373,9 @@ __global__ void __launch_bounds__(256, fwd_min_ctas<C, B>()) k_forward_queue(Wor
   __syncthreads();
   const uint32_t nitems = (uint32_t)w.counters[kItems];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t nwarps = gridDim.x * 8u;
-  uint32_t it = first_item(w, wid, spread);
+  const uint32_t nwarps = gridDim.x * (uint32_t)kW;
+  // the first eight warps of each CTA as first_item lays them out, the others after them
+  uint32_t it = wid < 8 ? first_item(w, wid, spread) : (uint32_t)wid * gridDim.x + blockIdx.x;
   while (it < nitems) {
     const uint32_t item = w.items[it];
     forward_group<C, B>(w, prm, N, T, (int)(item >> 3), (int)(item & 7u), s_rec[wid], s_jg[wid], out,
@@ -417,10 +418,19 @@ __global__ void __launch_bounds__(256, fwd_min_ctas<C, B>()) k_forward_queue(Wor
 template <int C, int B>
 static void launch_forward_cb(const Work &w, const Prm &prm, int64_t N, int F, int T, const Tuning &tn,
                               const FwdOut &out, cudaStream_t s) {
-  if (tn.schedule == 1)
-    launch(k_forward_queue<C, B>, tn.num_sms * tn.ctas_per_sm, 256, 0, s, w, prm, N, T, out,
+  if (tn.schedule == 1) {
+    // a call of many tiles (batched keyframes) is bound by throughput: ten warps a CTA
+    // there, as for its segmented backward; single-frame steps keep eight
+    if constexpr (C <= 4 && B == 32) {
+      if ((int64_t)F * T > kScanSingleMax) {
+        launch(k_forward_queue<C, B, 10>, tn.num_sms * tn.ctas_per_sm, 320, 0, s, w, prm, N, T, out,
+               tn.ctas_per_sm <= 2 ? 1 : 0);
+        return;
+      }
+    }
+    launch(k_forward_queue<C, B, 8>, tn.num_sms * tn.ctas_per_sm, 256, 0, s, w, prm, N, T, out,
            tn.ctas_per_sm <= 2 ? 1 : 0);
-  else
+  } else
     launch(k_forward<C, B>, F * T, 1 << (tn.tws + tn.ths), 0, s, w, prm, N, T, out);
 }
 
