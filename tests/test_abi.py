@@ -63,6 +63,16 @@ def test_host_side_argument_errors_without_gpu():
     assert lib.rtg_alu_probe(0, 0, 1, ctypes.byref(ops), None) == _lib.RTG_ERR_ARG   # no iterations
     assert lib.rtg_alu_probe(1, 10, None, ctypes.byref(ops), None) == _lib.RTG_ERR_ARG
     assert ops.value == -7
+    # the Adam step that starts under the kernel in front, and the frame-decoding forward:
+    # argument errors found on the host, before any launch
+    adam_args = [None] * 13
+    assert lib.rtg_adam_step_counted_after_gradients(-1, 3, *adam_args, ctypes.byref(hp), None) == _lib.RTG_ERR_ARG
+    assert lib.rtg_adam_step_counted_after_gradients(10, 3, *adam_args, None, None) == _lib.RTG_ERR_ARG
+    assert lib.rtg_adam_step_counted_after_gradients(10, 0, *adam_args, ctypes.byref(hp), None) == _lib.RTG_ERR_ARG
+    assert lib.rtg_adam_step_counted_after_gradients(0, 3, *adam_args[:12], ctypes.c_void_p(8),
+                                                     ctypes.byref(hp), None) == _lib.RTG_OK  # nothing to do
+    assert lib.rtg_render_forward_l1_frame(None, None, 1, None, None, None, None, None, 1.0, None, None, 1.0, 1.0,
+                                           None, None, None, None, None, None) == _lib.RTG_ERR_ARG
 
 
 def test_struct_layouts_match_header():
