@@ -456,9 +456,10 @@ def step_sum(alg, per_launch, extra=()):
 NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch (masked_step_300k_640x480_launches.md,
     # masked_step_1M_640x480_launches.md, compositing_fwd_bwd_300k_640x480_ncu.md)
-    ("target", "backward", 8, 8, 32, 1): 8_354_048,  # k_backward_seg_queue<3>
-    ("target", "forward", 8, 8, 32, 1): 7_221_248,  # k_forward_queue<3, 32>
-    ("masked-step", "backward", 8, 8, 32, 1): 17_897_984,  # k_backward_seg_queue<3>
+    ("target", "backward", 8, 8, 32, 1): 8_351_744,  # k_backward_seg_queue<3, 8>
+    ("target", "forward", 8, 8, 32, 1): 7_220_992,  # k_forward_queue<3, 32, 8>
+    ("masked-step", "backward", 8, 8, 32, 1): 17_894_656,  # k_backward_seg_queue<3, 8>
+    ("masked-step", "forward", 8, 8, 32, 1): 13_686_016,  # k_forward_queue<3, 32, 8>
 }
 
 
