@@ -44,10 +44,10 @@ TARGET = dict(name="masked-step room 300k Gaussians (20% unstable, 3 blobs) 640x
               coverage=(0.25, 0.40), key="target", candidate=10)  # first pose with 25-40% (GPU-measured)
 FULL_METRIC = "full-frame fwd+bwd iterations/sec and fragments/sec at 640×480 (300k Gaussians, all optimised)"
 FULL = dict(name="full frame: room 300k Gaussians, every Gaussian optimised, 640x480 (f 600), forward + L1 + "
-                 "backward + Adam", seed=2000, n=300_000, width=640, height=480, f=600.0, key="config2")
+                 "backward + Adam", seed=2000, n=300_000, width=640, height=480, f=600.0, key="full-frame")
 FWD_METRIC = "forward frames/sec at 160×120 (2k Gaussians, full frame)"
 FWD = dict(name="forward only: 2,000 random ellipsoids (half opaque 0.99, half transparent 0.05), 160x120 "
-                "(f 150), full frame", seed=1000, n=2000, key="config1")
+                "(f 150), full frame", seed=1000, n=2000, key="forward-2k")
 # Supplement C: 50 optimisation iterations per window (Replica, the Azure scenes, TUM-RGBD);
 # work the window does once (the stable Gaussians' projections and sorted lists) is charged
 # to each iteration at 1/50
@@ -97,15 +97,15 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--candidate", type=int, default=-1, help="camera candidate index (-1: search)")
     ap.add_argument("--workload", default="target",
-                    choices=["target", "masked-step", "config2", "config1", "keyframes", "large", "global", "adding",
+                    choices=["target", "masked-step", "full-frame", "forward-2k", "keyframes", "large", "global", "adding",
                              "state", "sh"],
                     help="target: the 640x480 masked iteration at 300k Gaussians (default); masked-step: the "
-                         "same at 1M Gaussians; config2: full-frame forward + backward + Adam at 300k "
-                         "Gaussians, every one optimised; config1: the 2k-Gaussian 160x120 forward; keyframes: 8 "
+                         "same at 1M Gaussians; full-frame: full-frame forward + backward + Adam at 300k "
+                         "Gaussians, every one optimised; forward-2k: the 2k-Gaussian 160x120 forward; keyframes: 8 "
                          "batched 1200x680 keyframes vs per-frame launches; large: 32 batched 1200x680 "
                          "keyframes, 5M Gaussians, 8 channels; global: the global keyframe optimisation step "
-                         "(4 keyframes, top-40% pixels, every Gaussian); adding: the Gaussian-adding pass "
-                         "(full-frame render, Eq. 6 masks, 5% draw); state: fusion and state management "
+                         "(4 keyframes, top-40%% pixels, every Gaussian); adding: the Gaussian-adding pass "
+                         "(full-frame render, Eq. 6 masks, 5%% draw); state: fusion and state management "
                          "(render, error counts, transitions, pruning, Eq. 9 fusion); sh: the 1M masked step "
                          "with SH degree-3 colour and the transparent regulariser")
     ap.add_argument("--no-checks", action="store_true",
@@ -2119,7 +2119,7 @@ def main():
     args = parse()
     if args.steps <= 0:
         args.steps = {"keyframes": 60, "large": 20, "global": 100, "adding": 200, "state": 200,
-                      "config2": 100, "config1": 400}.get(args.workload, 400)
+                      "full-frame": 100, "forward-2k": 400}.get(args.workload, 400)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         out = run_reference(args, WORKLOAD if args.workload == "masked-step" else TARGET)
@@ -2138,9 +2138,9 @@ def main():
         out = run_adding(args)
     elif args.workload == "state":
         out = run_state(args)
-    elif args.workload == "config2":
+    elif args.workload == "full-frame":
         out = run_full_frame(args)
-    elif args.workload == "config1":
+    elif args.workload == "forward-2k":
         out = run_forward_only(args)
     else:  # masked-step, sh
         out = run_ours(args, WORKLOAD)

@@ -39,7 +39,7 @@ typedef enum {
   RTG_ERR_CUDA = -2,        /* a CUDA runtime call failed; see rtg_last_error */
   RTG_ERR_WORKSPACE = -3,   /* the (Gaussian, tile) pairs exceeded the capacity */
   RTG_ERR_TIMEOUT = -4,     /* reserved: a bounded device-side wait gave up */
-  RTG_ERR_UNSUPPORTED = -5, /* a configuration this build does not implement */
+  RTG_ERR_UNSUPPORTED = -5, /* a configuration the library does not implement */
   RTG_ERR_STATE = -6        /* call order violated (backward without a forward) */
 } rtg_status;
 

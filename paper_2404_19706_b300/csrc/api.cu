@@ -272,7 +272,7 @@ bool window_matches(const rtg_ctx *ctx, const rtg_camera *cams, int F, const rtg
          g->unstable_ids == a.unstable_ids && g->n_unstable == a.n_unstable;
 }
 
-// rtg_tuning -> Tuning, or false if the setting is not one this build implements
+// rtg_tuning -> Tuning, or false if the setting is not one the library implements
 bool make_tuning(const rtg_tuning *t, int num_sms, Tuning &o) {
   if (t == nullptr) return false;
   const int tws = log2_exact(t->tile_w), ths = log2_exact(t->tile_h);

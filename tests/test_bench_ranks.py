@@ -1,5 +1,5 @@
 """The N > 1 path of bench.py on CPU: two gloo ranks agree on the max-over-ranks time and the
-whole-job rate, and the reference arm runs on rank 0 alone."""
+whole-job rate, and the reference arm runs on rank 0 alone; and its command line."""
 
 import os
 import socket
@@ -56,3 +56,18 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     monkeypatch.setenv("WORLD_SIZE", "2")
     args = bench.argparse.Namespace(steps=1, warmup=0, candidate=-1)
     assert bench.run_reference(args) is None
+
+
+def test_command_line_help_and_workload_names(monkeypatch, capsys):
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--help"])
+    with pytest.raises(SystemExit) as e:
+        bench.parse()
+    assert e.value.code == 0
+    text = capsys.readouterr().out
+    for name in ("target", "masked-step", "full-frame", "forward-2k", "keyframes", "large", "global", "adding",
+                 "state", "sh"):
+        assert name in text
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "full-frame", "--steps", "3", "--warmup", "3"])
+    args = bench.parse()
+    assert (args.workload, args.steps, args.warmup, args.gpus, args.impl) == ("full-frame", 3, 3, 1, "ours")

@@ -97,7 +97,7 @@ def sample_masked(mask, k, rng):
     return np.stack([xs[sel], ys[sel]], 1)
 
 
-def test_config3_masked_step_1M_sampled():
+def test_masked_step_1M_sampled():
     """1M Gaussians, 20% unstable in 3 blobs, 640x480, mask with the tile rule (the bench's
     camera candidate), the bench's tuning: 8x8 / batch 64 / persistent at 2 CTAs per SM /
     ranking sort <= 512."""
@@ -115,7 +115,7 @@ def test_config3_masked_step_1M_sampled():
     assert n >= 46
 
 
-def test_config4_keyframes_2M_sampled():
+def test_batched_keyframes_2M_sampled():
     """2M Gaussians on a 2x2 grid of rooms, 10% unstable in 8 blobs, 8 keyframes at
     1200x680 in one call, the bench's tuning: 8x16 / batch 32 / CTA per tile / ranking sort
     <= 512."""
@@ -133,7 +133,7 @@ def test_config4_keyframes_2M_sampled():
         assert n >= 14
 
 
-def test_config5_large_floor_5M_32_keyframes_8_channels_sampled():
+def test_large_floor_5M_32_keyframes_8_channels_sampled():
     """5M Gaussians on a 30x20x3 m floor (5x4 rooms), 90% opaque, 8 colour channels, 10%
     unstable, 32 keyframes at 1200x680 in one call, the bench's tuning: 8x8 / batch 32 /
     persistent at 2 CTAs per SM / ranking sort <= 512."""
@@ -156,8 +156,8 @@ def test_config5_large_floor_5M_32_keyframes_8_channels_sampled():
 GROUPS = ("means", "scales", "quats", "opacity", "colors")
 
 
-def test_config3_gradients_sampled_pixels():
-    """The backward at full size, in the bench's tuning: the 1M-Gaussian config-3 scene with
+def test_masked_step_1M_gradients_sampled_pixels():
+    """The backward at full size, in the bench's tuning: the 1M-Gaussian masked-step scene with
     the loss restricted to sampled masked pixels, against the FP64 oracle's analytic
     gradient on the Gaussians that can reach those pixels; every other unstable Gaussian
     must get exactly zero."""
