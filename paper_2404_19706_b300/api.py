@@ -563,7 +563,7 @@ def compact_gaussians(ctx: Context, remove: torch.Tensor, src: MapArrays, dst: M
                       stream=None):
     """Copy the rows of src not flagged in remove, in order, to dst; count_out [1] int64."""
     n = int(remove.numel())
-    C = int(src.colors.numel()) // max(int(src.colors.shape[0]), 1)
+    C = _row_width(src.colors)
     a, b = src.to_c(), dst.to_c()
     st = _lib.load().rtg_compact_gaussians(ctx.ptr, n, C, _ptr(remove, torch.uint8, "remove"), ctypes.byref(a),
                                            ctypes.byref(b), _ptr(count_out, torch.int64, "count_out"),
@@ -614,13 +614,18 @@ def decode_rgbd(rgb: torch.Tensor, depth: torch.Tensor, depth_scale: float, colo
     _check(st, "rtg_decode_rgbd")
 
 
+def _row_width(colors: torch.Tensor) -> int:
+    """Values per Gaussian of a colour array [n, ...], from its shape (so also when n = 0)."""
+    return int(math.prod(colors.shape[1:])) if colors.dim() > 1 else 1
+
+
 def adam_step(params: Sequence[torch.Tensor], grads: Sequence[torch.Tensor], m: torch.Tensor, v: torch.Tensor,
               step: int, hp: AdamSettings = AdamSettings(), stream=None):
     """params/grads: compact (means, scales, quats, opacity, colors); m, v: nu * (11 + C) floats
     each, zero at the start, laid out group by group like the parameters."""
     means, scales, quats, opacity, colors = params
     nu = int(means.shape[0])
-    C = int(colors.numel()) // max(nu, 1)
+    C = _row_width(colors)
     c = hp.to_c()
     ptrs = [_ptr(t, torch.float32, "param") for t in params] + [_ptr(t, torch.float32, "grad") for t in grads]
     st = _lib.load().rtg_adam_step(nu, C, *ptrs, _ptr(m, torch.float32, "m"), _ptr(v, torch.float32, "v"),
@@ -639,7 +644,7 @@ def adam_step_counted(params: Sequence[torch.Tensor], grads: Sequence[torch.Tens
         raise ValueError("step_counter must hold 2 int32 (completed steps, scratch)")
     means, scales, quats, opacity, colors = params
     nu = int(means.shape[0])
-    C = int(colors.numel()) // max(nu, 1)
+    C = _row_width(colors)
     c = hp.to_c()
     ptrs = [_ptr(t, torch.float32, "param") for t in params] + [_ptr(t, torch.float32, "grad") for t in grads]
     lib = _lib.load()

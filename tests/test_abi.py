@@ -142,3 +142,15 @@ def test_global_optimisation_entry_points_reject_bad_arguments_without_gpu():
     p = _lib.rtg_add_params(0.5, 0.1, 0.1, 0.05, 0.99, 0.1, 0)
     assert lib.rtg_add_candidates(None, None, 1, 3, *([None] * 7), 0, ctypes.byref(p), 0,
                                   *([None] * 6), None) == _lib.RTG_ERR_ARG
+
+
+def test_colour_row_width_comes_from_the_shape_even_without_rows():
+    # the binding passes C (values per Gaussian) to Adam and the compaction; with no unstable
+    # Gaussian the arrays have no rows, and C must still be the row width, not 0
+    import torch
+    from paper_2404_19706_b300 import api
+    assert api._row_width(torch.empty(0, 3)) == 3
+    assert api._row_width(torch.empty(0, 8)) == 8
+    assert api._row_width(torch.empty(7, 16, 3)) == 48
+    assert api._row_width(torch.empty(0, 16, 3)) == 48
+    assert api._row_width(torch.empty(5)) == 1
