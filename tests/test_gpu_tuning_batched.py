@@ -117,14 +117,19 @@ def test_fused_mask_under_every_tile_matches_default():
         assert_grads_close(got["grads"], ref["grads"])
 
 
+@pytest.mark.parametrize("empty_frame", [None, 1])
 @pytest.mark.parametrize("schedule", [0, 1])
-def test_batched_keyframes_equal_per_frame_calls(schedule):
+def test_batched_keyframes_equal_per_frame_calls(schedule, empty_frame):
     """One call over F keyframes renders each frame bit for bit like a call with that frame
     alone; its gradients (explicit per-pixel dL images, so no loss normalisation couples
-    the frames) equal the per-frame gradients summed with accumulate."""
+    the frames) equal the per-frame gradients summed with accumulate.  empty_frame: that
+    keyframe's mask is empty (it adds no work item; its outputs keep their contents)."""
     m = rtg()
     scene, cams, masks = scene_and_cams(3, seed=3300)
     mask = torch.as_tensor(masks).reshape(F, H, W).cuda()
+    if empty_frame is not None:
+        mask[empty_frame] = 0
+    assert int(mask.sum()) > 0
     g = m.Gaussians.from_scene(scene)
     nu = int(scene.unstable.astype(bool).sum())
     rng = np.random.default_rng(3301)
