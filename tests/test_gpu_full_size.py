@@ -222,3 +222,77 @@ def test_masked_step_1M_gradients_sampled_pixels():
         assert np.linalg.norm(gg - r) <= 1e-3 * np.linalg.norm(r), (k, np.linalg.norm(gg - r) / np.linalg.norm(r))
         assert (np.abs(gg - r) <= 1e-3 * np.abs(r) + 1e-3 * scale).all(), (k, np.abs(gg - r).max(), scale)
         assert not got[k].reshape(nu, -1)[others].any(), k  # no influence on these pixels
+
+
+def test_target_300k_fused_step_sampled_pixels():
+    """The 300k masked step in the launch configuration the bench times: precomputed unstable
+    index, window open (cached stable lists), the fused L1 forward and its backward, 8x8
+    tiles, 32-record batches, the persistent schedule at 2 CTAs per SM, 8-bit digits,
+    ranking sort up to 256 keys.  The unstable mask's coverage, then on sampled masked pixels
+    the render, the loss and every gradient against the FP64 oracle; the unstable Gaussians
+    that cannot reach those pixels get exactly zero."""
+    m = rtg()
+    scene, layout = synth.room_scene(2000, 300_000)
+    cams = synth.room_camera_candidates(2001, layout, 640, 480, 600.0)
+    for _ in range(11):
+        cam = next(cams)  # candidate 10
+    scene.unstable = synth.flag_blobs(scene, [cam], 60_000, 3, seed=2000 + 100 + 10, n_in_view=1)
+    H, W = cam.height, cam.width
+    ctx = m.Context(max_gaussians=scene.n, max_width=W, max_height=H)
+    ctx.set_tuning(m.Tuning(8, 8, 32, 1, 2, 8, 256))
+    g = m.Gaussians.from_scene(scene)
+    rank, ids, nu = m.unstable_rank(ctx, g.unstable)
+    g = dataclasses.replace(g, rank_map=rank, unstable_ids=ids, n_unstable=nu)
+    mask = torch.zeros(1, H, W, dtype=torch.uint8, device="cuda")
+    m.unstable_mask(ctx, cam, g, m.RenderSettings(), mask)
+    cov = float(mask.float().mean())
+    assert 0.25 <= cov <= 0.40, cov
+    m.window_begin(ctx, [cam], g, m.RenderSettings())
+    rng = np.random.default_rng(2010)
+    pix = sample_masked(mask[0].cpu().numpy(), 64, rng)
+    sub_idx = reach_subset(scene, cam, pix)
+    sub = scene.subset(sub_idx)
+    tc = rng.uniform(0.0, 1.0, (len(pix), 3))
+    td = rng.uniform(1.0, 5.0, len(pix))
+    pre = oracle.loss_and_grads(sub, cam, ST, pix, tc, td)
+    keep = ~pre["grad_borderline"]
+    assert keep.sum() >= 56
+    pix, tc, td = pix[keep], tc[keep], td[keep]
+    ref = oracle.loss_and_grads(sub, cam, ST, pix, tc, td)
+    ms = torch.zeros(1, H, W, dtype=torch.uint8, device="cuda")
+    tcol = torch.zeros(1, 3, H, W, device="cuda")
+    tdep = torch.zeros(1, H, W, device="cuda")
+    xs, ys = torch.as_tensor(pix[:, 0]).cuda(), torch.as_tensor(pix[:, 1]).cuda()
+    ms[0, ys, xs] = 1
+    tcol[0, :, ys, xs] = torch.as_tensor(tc.T, dtype=torch.float32).cuda()
+    tdep[0, ys, xs] = torch.as_tensor(td, dtype=torch.float32).cuda()
+    color = torch.zeros(1, 3, H, W, device="cuda")
+    depth = torch.full((1, H, W), -1.0, device="cuda")
+    alpha = torch.zeros(1, H, W, device="cuda")
+    index = torch.full((1, H, W), -1, dtype=torch.int32, device="cuda")
+    loss = torch.zeros(3, device="cuda")
+    m.render_forward_l1(ctx, [cam], g, ms, m.RenderSettings(), tcol, tdep, 1.0, 1.0, color, depth, alpha, loss,
+                        index)
+    grads = [torch.zeros(nu, 3, device="cuda"), torch.zeros(nu, 3, device="cuda"), torch.zeros(nu, 4, device="cuda"),
+             torch.zeros(nu, device="cuda"), torch.zeros(nu, 3, device="cuda")]
+    m.render_backward_l1(ctx, *grads)
+    torch.cuda.synchronize()
+    assert m.get_status(ctx) == 0 and m.window_is_open(ctx)
+    n = check_pixels(scene, cam, color[0].cpu().numpy(), depth[0].cpu().numpy(), alpha[0].cpu().numpy(),
+                     index[0].cpu().numpy(), pix)
+    assert n >= len(pix) - 2
+    assert float(loss[0]) == pytest.approx(ref["loss"], rel=1e-4)
+    got = {k: t.cpu().numpy().astype(np.float64) for k, t in zip(GROUPS, grads)}
+    rank_np = np.cumsum(scene.unstable.astype(np.int64)) - 1
+    rows = rank_np[sub_idx[scene.unstable[sub_idx] != 0]]
+    others = np.ones(nu, dtype=bool)
+    others[rows] = False
+    for k in GROUPS:
+        r = ref["grads"][k].reshape(len(rows), -1)
+        gg = got[k].reshape(nu, -1)[rows]
+        scale = np.abs(r).max()
+        assert scale > 0, k
+        assert np.linalg.norm(gg - r) <= 1e-3 * np.linalg.norm(r), (k, np.linalg.norm(gg - r) / np.linalg.norm(r))
+        assert (np.abs(gg - r) <= 1e-3 * np.abs(r) + 1e-3 * scale).all(), (k, np.abs(gg - r).max(), scale)
+        assert not got[k].reshape(nu, -1)[others].any(), k
+    ctx.close()
